@@ -1,0 +1,124 @@
+"""Pins of the oracle's Krylov pieces: textbook CG properties, the Lanczos
+estimate on a known spectrum, and the paper's own iteration counts and
+condition estimates (Sec. 6, Tables 1 and 3) as soft pins."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import sg_inputs as S
+from oracle import chaos, hsc, krylov, sg_operator as so
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_cg_on_known_spectrum_and_lanczos_estimate():
+    """CG on diag(1..m) converges in at most m steps and the Lanczos estimate
+    after convergence is the exact condition number m."""
+    m = 12
+    d = np.arange(1, m + 1, dtype=np.float64)
+    f = np.ones(m)
+    x, info = krylov.fcg(lambda v: d * v, f, None, tol=1e-14, maxit=50, flexible=False)
+    assert info["iters"] <= m
+    assert np.allclose(x, 1.0 / d, atol=1e-12)
+    assert krylov.lanczos_kappa(info["alpha"], info["beta"]) == pytest.approx(m, rel=1e-8)
+
+
+def test_exact_preconditioner_converges_in_one_step():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((20, 20))
+    A = X @ X.T + 20 * np.eye(20)
+    f = rng.standard_normal(20)
+    Ainv = np.linalg.inv(A)
+    for flexible in (True, False):
+        x, info = krylov.fcg(lambda v: A @ v, f, lambda r: Ainv @ r, tol=1e-12, flexible=flexible)
+        assert info["iters"] == 1
+        assert np.allclose(A @ x, f, atol=1e-10)
+
+
+def test_fcg_sg_solution_matches_direct_solve():
+    prob = S.make_problem(8, 2, 0.3, 0.5)
+    M, p = 2, 3
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(M, p)
+    _, off = chaos.multi_indices(M, p)
+    F = S.make_rhs(prob, p)
+    U_ref = so.direct_solve(A, G, F)
+    ap = lambda U: so.sg_apply(A, G, U)
+    for prec in (None, lambda R: hsc.hsc_apply(A, G, off, R), lambda R: hsc.mean_apply(A, R)):
+        U, info = krylov.fcg(ap, F, prec, tol=1e-13, maxit=2000)
+        assert info["converged"]
+        assert np.abs(U - U_ref).max() < 1e-10 * np.abs(U_ref).max()
+
+
+def _read(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+def _paper_run(M, p, cov):
+    """Sec. 6 setting: 10x10 Q1 mesh, L = 0.5, k0 = 1. The reading of the
+    garbled distribution of xi (printed ``U[0,1]``) is ``U(-1, 1)``: in this
+    build's unit-variance variables that is sigma = CoV / sqrt(3)."""
+    prob = S.make_problem(10, M, cov / math.sqrt(3.0), 0.5)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(M, p)
+    _, off = chaos.multi_indices(M, p)
+    F = S.make_rhs(prob, p)
+    a0 = hsc.A0Solver(A[0])
+    ap = lambda U: so.sg_apply(A, G, U)
+    out = {}
+    for name, prec in (("mean", lambda R: hsc.mean_apply(A, R, a0)),
+                       ("hsc", lambda R: hsc.hsc_apply(A, G, off, R, a0solve=a0))):
+        _, info = krylov.fcg(ap, F, prec, tol=1e-8, maxit=500)
+        out[name] = (info["iters"], krylov.lanczos_kappa(info["alpha"], info["beta"]))
+    return out
+
+
+@pytest.mark.parametrize("row", _read("table3_cov.txt"))
+def test_paper_table3_soft(row):
+    """Iterations within 2 and kappa within 10 % of Table 3 (the paper's KL is
+    a discrete eigenproblem on its mesh and its dof count includes boundary
+    nodes, so equality is not expected)."""
+    cov, m_it, m_k, h_it, h_k = row
+    out = _paper_run(4, 4, cov / 100.0)
+    assert abs(out["mean"][0] - m_it) <= 2
+    assert abs(out["hsc"][0] - h_it) <= 2
+    assert out["mean"][1] == pytest.approx(m_k, rel=0.10)
+    assert out["hsc"][1] == pytest.approx(h_k, rel=0.10)
+    # the method's claim: HSC needs fewer iterations than the mean-based one
+    assert out["hsc"][0] < out["mean"][0]
+
+
+@pytest.mark.parametrize("row", _read("table1_vary_N.txt"))
+def test_paper_table1_soft(row):
+    N, m_it, m_k, _, _, h_it, h_k = row
+    out = _paper_run(int(N), 4, 0.5)
+    assert abs(out["mean"][0] - m_it) <= 2
+    assert abs(out["hsc"][0] - h_it) <= 2
+    assert out["mean"][1] == pytest.approx(m_k, rel=0.10)
+    assert out["hsc"][1] == pytest.approx(h_k, rel=0.10)
+
+
+def test_pcg_columns_conventions():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((15, 15))
+    A = X @ X.T + 15 * np.eye(15)
+    Ainv = np.linalg.inv(A)
+    B = rng.standard_normal((15, 4))
+    B[:, 2] = 0.0
+    Xs, it = krylov.pcg_columns(lambda v: A @ v, B, lambda r: Ainv @ r, tol=1e-10, maxit=30)
+    assert list(it) == [1, 1, 0, 1]               # exact M0: one step; zero column done at entry
+    assert np.allclose(A @ Xs, B, atol=1e-10)
+    # unpreconditioned, fixed iteration count runs exactly that many steps
+    Xs, it = krylov.pcg_columns(lambda v: A @ v, B, lambda r: r.copy(), tol=0.0, maxit=30, fixed_iters=3)
+    assert list(it) == [3, 3, 0, 3]
+    # tolerance test per column: residual below tol * ||b||
+    Xs, it = krylov.pcg_columns(lambda v: A @ v, B, lambda r: r.copy(), tol=1e-3, maxit=100)
+    for s in (0, 1, 3):
+        assert np.linalg.norm(B[:, s] - A @ Xs[:, s]) <= 1e-3 * np.linalg.norm(B[:, s]) * (1 + 1e-9)
