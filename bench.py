@@ -1,0 +1,367 @@
+"""Benchmark: time-to-solve of the stochastic Galerkin system at relative
+residual 1e-8 with the hierarchical Schur complement preconditioner
+(mixed precision: FP32 inner loops, FP64 outer), against the all-FP64
+mean-based preconditioner on the same GPU, plus the SG matvec roofline.
+
+Workload (default): 128 x 128 Q1 grid (16129 interior dofs), M = 6 Legendre
+variables, p = 4 (P = 210, 3.39M unknowns), sigma = 0.3, correlation length
+1.0, f = 1; inner A_0 PCG with a multigrid V-cycle to 1e-2.
+
+One step = one full sg_solve (K1 SG matvec, K2 level products, K3/K4 batched
+inner PCG + V-cycle, K5 outer FCG) with F resident in HBM. L2 is flushed
+(256 MiB write) between timed steps, outside the timed events.
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload; that arm is the deliberately slow
+baseline, not a target.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import sg_inputs as S  # noqa: E402
+
+METRIC = "time-to-solve at rel.res 1e-8, HSC-PCG vs mean-based PCG; SG matvec HBM GB/s"
+WORKLOADS = {
+    "cfg2": dict(name="cfg2_mixed_128x128_M6_p4", **S.CONFIGS["cfg2_mixed_128x128_M6_p4"]),
+    "cfg1": dict(name="cfg1_fp64_16x16_M3_p3", **S.CONFIGS["cfg1_fp64_16x16_M3_p3"]),
+    "cfg4": dict(name="cfg4_64x64_M4_p3", **S.CONFIGS["cfg4_grad_64x64_M4_p3"]),
+    "cfg5": dict(name="cfg5_large_512x512_M10_p4", **S.CONFIGS["cfg5_large_512x512_M10_p4"]),
+}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 ALU peak used for the FP64-bound kernels: the nominal GB300 FP64 rate
+# (1.25 TFLOP/s) from the hardware table of the profiling recipe.
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sg_matvec_bytes(n, nnz, M, P, es):
+    """Algorithmic bytes of one SG product: pattern once, M+1 values per
+    nonzero, U read once, Y written once."""
+    return 4 * (n + 1) + 4 * nnz + es * (M + 1) * nnz + 2 * es * n * P
+
+
+def sg_matvec_flops(nnz, P, n_m):
+    """Gather-form multiply-adds per nonzero: P (G_0 = I) + n_m (off-diagonal G entries)."""
+    return 2 * nnz * (P + n_m)
+
+
+def build_problem(cfg):
+    prob = S.make_problem(cfg["ne"], cfg["M"], cfg["sigma"], cfg["corr_len"])
+    return prob
+
+
+def run_ours(args, rank, world, dev):
+    import torch
+
+    import paper_1205_1864_gb300 as L
+    cfg = WORKLOADS[args.workload]
+    t0 = time.time()
+    prob = build_problem(cfg)
+    p = cfg["p"]
+    h = L.SGProblem.from_inputs(prob, p)
+    setup_s = time.time() - t0
+    n, P, M, nnz = h.n, h.P, h.M, h.nnz
+    alpha, off = h.chaos_table()
+    n_m = int(2 * M * math.comb(M + p - 1, M))
+    F_np = S.make_rhs(prob, p)
+    F = torch.tensor(F_np, dtype=torch.float64, device=dev)
+    U = torch.empty_like(F)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    hsc_opts = L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=1e-2),
+                            precond=L.SG_PREC_HSC, tol=1e-8, maxit=500, check_true_residual=0)
+    mean_opts = L.solve_opts(L.prec_opts(precision=L.SG_F64, inner_tol=1e-2), precond=L.SG_PREC_MEAN,
+                             tol=1e-8, maxit=500, check_true_residual=0)
+
+    def timed_solves(opts, steps, warmup, count_launches=False):
+        for _ in range(warmup):
+            L.sg_solve(h, F, opts, U)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ts, stats = [], None
+        l0 = L._lib.LIB.sg_kernel_launches()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, stats = L.sg_solve(h, F, opts, U)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        launches = L._lib.LIB.sg_kernel_launches() - l0
+        return ts, stats, launches
+
+    if args.profile:
+        ts, st_h, launches = timed_solves(hsc_opts, args.steps, args.warmup)
+        return {"profile": True, "workload": cfg["name"], "ms": float(np.mean(ts)), "iterations": st_h.iterations,
+                "launches_per_solve": int(launches / max(args.steps, 1))}
+    # headline: mixed HSC-PCG
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        ts, st_h, launches = timed_solves(hsc_opts, args.steps, args.warmup)
+    ms = float(np.mean(ts))
+    # validation solve (untimed): the true FP64 residual of the same HSC solve
+    _, st_true = L.sg_solve(h, F, L.solve_opts(hsc_opts.prec, precond=L.SG_PREC_HSC, tol=1e-8, maxit=500,
+                                               check_true_residual=1), U)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    # oracle-independent check of the result: true FP64 residual from the library
+    U_h = U.clone()
+    # comparator: all-FP64 mean-based PCG on the same GPU
+    ts_m, st_m, _ = timed_solves(mean_opts, max(1, min(args.steps, 3)), 1)
+    ms_mean = float(np.mean(ts_m))
+
+    # SG matvec roofline: K1 timed alone with events on the launching stream
+    def time_apply(dtype, reps=20):
+        Ut = torch.tensor(S.random_block(n, P, seed=1205), dtype=dtype, device=dev)
+        Yt = torch.empty_like(Ut)
+        for _ in range(3):
+            L.sg_apply(h, Ut, Yt)
+        times = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.sg_apply(h, Ut, Yt)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return float(np.mean(times))
+
+    k1_64 = time_apply(torch.float64)
+    k1_32 = time_apply(torch.float32)
+    hbm, hbm_src = _peaks()
+    b64 = sg_matvec_bytes(n, nnz, M, P, 8)
+    b32 = sg_matvec_bytes(n, nnz, M, P, 4)
+    fl = sg_matvec_flops(nnz, P, n_m)
+    matvec = {
+        "fp64": {"ms": k1_64, "GB_s": b64 / k1_64 / 1e6, "TFLOP_s": fl / k1_64 / 1e9, "bytes": b64, "flops": fl},
+        "fp32": {"ms": k1_32, "GB_s": b32 / k1_32 / 1e6, "TFLOP_s": fl / k1_32 / 1e9, "bytes": b32, "flops": fl},
+        "hbm_peak_GB_s": hbm,
+    }
+    roofline = {"kernel": "k_block_matvec<double> (K1 FP64 SG product, outer CG)", "bound": "alu",
+                "achieved": fl / k1_64 / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (fl / k1_64 / 1e9) / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
+
+    # end to end through the public API: host (pinned) F in, host U out
+    F_host = torch.tensor(F_np, dtype=torch.float64).pin_memory()
+    U_host = torch.empty_like(F_host).pin_memory()
+    e2e_t = []
+    for i in range(max(1, min(args.steps, 3)) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        Fd = F_host.to(dev, non_blocking=True)
+        Ud, _ = L.sg_solve(h, Fd, hsc_opts)
+        U_host.copy_(Ud, non_blocking=True)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_t.append((time.perf_counter() - t_a) * 1e3)
+    e2e_ms = float(np.mean(e2e_t))
+
+    out = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 outer / f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
+        "config": {"workload": cfg["name"], "ne": cfg["ne"], "M": M, "p": p, "P": P, "n": n,
+                   "unknowns": n * P, "sigma": cfg["sigma"], "corr_len": cfg["corr_len"], "inner_tol": 1e-2,
+                   "tol": 1e-8, "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "hsc": {"ms": ms, "iterations": st_h.iterations, "true_rel_res": st_true.true_rel_res,
+                "kappa_est": st_h.kappa_est, "inner_iters_total": st_h.inner_iters_total,
+                "inner_iters_max": st_h.inner_iters_max, "step_ms": ts},
+        "mean_fp64": {"ms": ms_mean, "iterations": st_m.iterations, "rel_res": st_m.rel_res,
+                      "kappa_est": st_m.kappa_est, "speedup_hsc_vs_mean": ms_mean / ms},
+        "sg_matvec": matvec,
+        "roofline": roofline,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(F_host.numel() * 8),
+                "d2h_bytes_per_step": int(U_host.numel() * 8)},
+        "gpu_launches": int(launches / max(args.steps, 1)),
+        "gpu_launches_note": "kernels launched by libsghsc per timed step (library counter)",
+        "clocks": clk.summary(),
+        "setup_s": setup_s,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, iterations=st_h.iterations, budget_s=args.cpu_budget)
+    return out
+
+
+def cpu_baseline(cfg, iterations, budget_s=20.0, prob=None):
+    """The FP64 oracle (exact inner solves) timed on the host on a bounded
+    sample: as many outer HSC-FCG iterations as fit the budget, scaled to the
+    iteration count of the full solve."""
+    from oracle import chaos, hsc, krylov, sg_operator as so
+    prob = prob or build_problem(cfg)
+    p = cfg["p"]
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(cfg["M"], p)
+    _, off = chaos.multi_indices(cfg["M"], p)
+    F = S.make_rhs(prob, p)
+    a0 = hsc.A0Solver(A[0])
+    ap = lambda X: so.sg_apply(A, G, X)
+    pre = lambda R: hsc.hsc_apply(A, G, off, R, a0solve=a0)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        k += 1
+        t1 = time.perf_counter()
+        krylov.fcg(ap, F, pre, tol=0.0, maxit=k)
+        dt = time.perf_counter() - t1
+        if dt * (k + 1) / k > budget_s or k >= iterations:
+            break
+    per_iter = dt / k
+    value_ms = per_iter * max(iterations, 1) * 1e3
+    cores = 1
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([1] + [i.get("num_threads", 1) for i in threadpool_info()])
+    except Exception:
+        pass
+    return {"value": value_ms, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"{k} outer HSC-FCG iterations of the FP64 oracle (exact sparse-LU inner solves) on "
+                      f"{cfg['name']}, {per_iter * 1e3:.1f} ms each, scaled to {iterations} iterations",
+            "wall_s": time.perf_counter() - t0}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cfg = WORKLOADS[args.workload]
+    prob = build_problem(cfg)
+    iters = 7 if args.workload == "cfg2" else 6     # HSC-FCG iteration count of the full solve at 1e-8
+    vals = []
+    budget = max(5.0, 150.0 / max(args.steps + args.warmup, 1))
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(cfg, iterations=iters, budget_s=budget, prob=prob)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
+            "config": {"workload": cfg["name"]},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="only the warm-up and timed HSC solves (for an ncu launch list); prints one short line")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=dev)
+    out = run_ours(args, rank, world, dev)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * sghsc.h -- C ABI of the GB300 stochastic Galerkin solver with the
+ * hierarchical Schur complement (HSC) preconditioner.
+ *
+ * Method: B. Sousedik, R. G. Ghanem, E. T. Phipps, "Hierarchical Schur
+ * complement preconditioner for the stochastic Galerkin finite element
+ * methods" (arXiv 1205.1864).
+ *
+ * The system is eq. (global-system) of Sec. 2,
+ *     sum_k  G_k (x) A_k  u = f,        k = 0..M,
+ * with A_0..A_M the Karhunen-Loeve stiffness matrices (the paper's K_i) on one
+ * shared sparsity pattern and (G_k)_{jl} = E[xi_k psi_j psi_l], G_0 = I, for
+ * the normalised chaos basis of total degree <= p in M variables
+ * (P = (M+p)!/(M! p!) polynomials, eq. (gPC-u)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout of a coefficient block: "n x P row-major" -- element (r, l) at
+ *   offset r*P + l, r the spatial row (0..n-1), l the chaos index (0..P-1).
+ *   In this layout the operator reads Y = sum_k A_k U G_k^T.
+ * Chaos order: degrees ascending (graded, as Sec. 3 requires); inside one
+ *   degree, descending lexicographic order of (alpha_1, ..., alpha_M). So
+ *   l = 0 is the mean, l = 1..M are xi_1..xi_M. sg_chaos_table() exports it.
+ * Memory: arguments named "host" are host pointers; every vector argument of
+ *   an apply/solve call is a DEVICE pointer on the current CUDA device. The
+ *   caller owns all buffers it passes; sg_setup copies what it needs and the
+ *   handle owns its device copies and workspace until sg_destroy.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream). Work is enqueued on it; calls that report per-iteration results
+ *   synchronise it. Calls on one handle must not overlap (the handle's
+ *   workspace is shared by all its calls).
+ * Errors: every call returns an sg_status; invalid arguments are rejected
+ *   before any launch; sg_last_error() returns a thread-local message for the
+ *   last failure. Nothing traps or aborts; device loops have iteration caps
+ *   and report through the status.
+ */
+#ifndef SGHSC_H
+#define SGHSC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_problem sg_problem;
+
+typedef enum {
+  SG_OK = 0,
+  SG_ERR_INVALID_ARG = 1,     /* a pointer, size, pattern or option is invalid */
+  SG_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+  SG_ERR_OOM = 3,             /* device allocation failed */
+  SG_ERR_NOT_SPD = 4,         /* an inner solve met p^T A_0 p <= 0 */
+  SG_ERR_BREAKDOWN = 5,       /* the outer solve met p^T A p <= 0 or a non-finite value */
+  SG_ERR_NO_CONVERGENCE = 6,  /* the outer solve reached maxit */
+  SG_ERR_UNSUPPORTED = 7      /* valid input outside what this build implements */
+} sg_status;
+
+enum { SG_F64 = 0, SG_F32 = 1 };                     /* element type of a block */
+enum { SG_LEGENDRE = 0, SG_HERMITE = 1 };            /* chaos family */
+enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_HSC = 2 };
+
+/* Uniform grid of ne_x x ne_y bilinear (Q1) elements on the unit square with
+ * Dirichlet nodes eliminated: n = (ne_x-1)(ne_y-1) interior nodes, numbered
+ * lexicographically with x fastest (Sec. 6 discretisation). The multigrid
+ * inner preconditioner needs ne_x == ne_y, a power of two. */
+typedef struct { int ne_x, ne_y; } sg_mesh;
+
+/* Options of one preconditioner application (Algorithm 1, Sec. 4; inner
+ * loops of Sec. 5). */
+typedef struct {
+  int precision;          /* SG_F32: inner solves and level products in FP32 (mixed);
+                             SG_F64: everything in FP64 */
+  int top_level_f64;      /* with SG_F32: the level-p off-diagonal products of
+                             Algorithm 1 are computed in FP64 */
+  double inner_tol;       /* per-column relative residual of the inner PCG on A_0 */
+  int inner_maxit;        /* cap on inner iterations (status bit set when reached) */
+  int inner_fixed_iters;  /* > 0: run exactly this many inner iterations, no tolerance test */
+  int nu;                 /* V-cycle: weighted-Jacobi sweeps before and after */
+  double omega;           /* V-cycle: Jacobi damping */
+} sg_prec_opts;
+
+/* Options of the outer flexible CG (Sec. 5-6). */
+typedef struct {
+  int precond;            /* SG_PREC_NONE, SG_PREC_MEAN (I (x) A_0^{-1}, Sec. 6) or SG_PREC_HSC */
+  sg_prec_opts prec;
+  double tol;             /* stop at ||r||_2 <= tol ||f||_2 (recursive residual) */
+  int maxit;
+  int flexible;           /* 1: beta = z_{k+1}^T (r_{k+1}-r_k)/(z_k^T r_k); 0: standard CG */
+  int use_x0;             /* 1: U holds the initial guess on entry */
+  int check_true_residual;/* 1: recompute ||f - A u|| / ||f|| in FP64 after the loop
+                             (one more SG product) into stats->true_rel_res */
+} sg_solve_opts;
+
+#define SG_MAX_HIST 1024
+
+typedef struct {
+  int status;             /* sg_status of the solve */
+  int iterations;         /* outer operator applications */
+  double rel_res;         /* final recursive relative residual */
+  double true_rel_res;    /* ||f - A u|| / ||f|| recomputed in FP64 at the end
+                             (-1 when check_true_residual is 0) */
+  double kappa_est;       /* Lanczos estimate from the CG coefficients (Sec. 6) */
+  long long inner_iters_total;   /* sum over all inner column solves */
+  int inner_iters_max;    /* largest inner iteration count of one column */
+  double solve_ms;        /* host wall time of the call */
+  int n_hist;             /* entries of res_hist (iterations + 1) */
+  double res_hist[SG_MAX_HIST + 1];
+  double alpha[SG_MAX_HIST];
+  double beta[SG_MAX_HIST];
+} sg_solve_stats;
+
+void sg_default_prec_opts(sg_prec_opts* o);
+void sg_default_solve_opts(sg_solve_opts* o);
+
+/* sg_setup -- build a problem handle (Sec. 2, eq. (global-system); Sec. 3).
+ * mesh      host, may be NULL: needed for the multigrid inner solves.
+ * M, p      number of random variables and total chaos degree (M >= 0, p >= 0).
+ * family    SG_LEGENDRE (xi ~ U(-sqrt3, sqrt3)) or SG_HERMITE (xi ~ N(0,1)).
+ * n, nnz    spatial size and nonzeros of the shared CSR pattern.
+ * rowptr    host int[n+1], colidx host int[nnz] (sorted, in range).
+ * vals      host double[nnz][M+1]: entry e of A_k at vals[e*(M+1) + k].
+ * mass_vals host double[nnz] or NULL: consistent mass matrix on the same
+ *           pattern (needed by sg_qoi / sg_qoi_grad).
+ * out       receives the handle. The chaos tables (multi-indices, the sparse
+ *           G_k) and the multigrid hierarchy are built here.
+ * Returns SG_ERR_INVALID_ARG for a malformed pattern or sizes, SG_ERR_OOM if
+ * device memory runs out. */
+int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz,
+             const int* rowptr, const int* colidx, const double* vals,
+             const double* mass_vals, sg_problem** out);
+
+void sg_destroy(sg_problem* h);
+
+/* Sizes of a handle (host outputs, any may be NULL). */
+int sg_problem_dims(const sg_problem* h, int* n, int* P, int* M, int* p, int* nnz);
+
+/* The chaos order: alpha host int[P*M] (row l is the multi-index of psi_l)
+ * and level_offsets host int[p+2] (degree d occupies [off[d], off[d+1])). */
+int sg_chaos_table(const sg_problem* h, int* alpha, int* level_offsets);
+
+/* sg_apply -- MAT-VEC of eq. (global-system) (the remark after
+ * eq. (global-matrix-block)): Y = sum_k A_k U G_k^T.
+ * U, Y: device n x P row-major of element type dtype (SG_F64 or SG_F32);
+ * Y must not alias U. */
+int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream);
+
+/* sg_level_apply -- one off-diagonal block product of the hierarchy
+ * (eq. (global-matrix-hierarchy)): Yout = Yin - sum_k A_k X G_k[out, in]^T
+ * with out, in two adjacent degree levels (|lvl_out - lvl_in| = 1): the
+ * pre-correction product B_l (out = l-1, in = l) and the post-correction
+ * product C_l (out = l, in = l-1) of Algorithm 1.
+ * X: device n x w_in packed; Yin, Yout: device n x w_out packed (may alias);
+ * w_d = number of chaos polynomials of degree d. */
+int sg_level_apply(sg_problem* h, int lvl_out, int lvl_in, const void* X, const void* Yin,
+                   void* Yout, int dtype, void* stream);
+
+/* sg_vcycle_apply -- one multigrid V-cycle with zero initial guess for A_0
+ * applied independently to the w columns of B (the mean-value
+ * preconditioner M_0 of Sec. 4-5). B, X: device n x w packed, w <= 1024. */
+int sg_vcycle_apply(sg_problem* h, const void* B, void* X, int w, int dtype,
+                    const sg_prec_opts* opts, void* stream);
+
+/* sg_inner_solve -- the batched inner PCG on A_0 (Sec. 5: independent
+ * Krylov loops for the diagonal blocks of D_l), V-cycle preconditioned,
+ * per-column convergence: column s stops once ||r_s|| <= inner_tol ||b_s||;
+ * zero columns are done at entry with x = 0. B, X: device n x w packed,
+ * w <= 1024. iters: host int[w] or NULL (per-column iteration counts;
+ * synchronises the stream). */
+int sg_inner_solve(sg_problem* h, const void* B, void* X, int w, int dtype,
+                   const sg_prec_opts* opts, int* iters, void* stream);
+
+/* hsc_precond_apply -- Algorithm 1 (Sec. 4): Z = M_P R with the D_l^{-1}
+ * and A_0^{-1} actions replaced by the batched inner PCG.
+ * R, Z: device n x P row-major FP64; must not alias. */
+int hsc_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts,
+                      void* stream);
+
+/* mean_precond_apply -- mean-based preconditioner I (x) A_0^{-1} (Sec. 6,
+ * Powell-Elman) with the same inner PCG. R, Z: device n x P FP64. */
+int mean_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts,
+                       void* stream);
+
+/* sg_solve -- flexible CG on eq. (global-system) preconditioned by
+ * opts->precond (Sec. 5-6), outer iteration in FP64.
+ * F: device n x P FP64 right-hand side; U: device n x P FP64 solution (initial
+ * guess on entry when opts->use_x0). stats: host, may be NULL.
+ * Returns SG_ERR_NO_CONVERGENCE if maxit is reached (U holds the last
+ * iterate), SG_ERR_BREAKDOWN / SG_ERR_NOT_SPD on loss of definiteness. */
+int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opts,
+             sg_solve_stats* stats, void* stream);
+
+/* sg_qoi -- Q = sum_j u_j^T M_h u_j = E[int u^2] for the orthonormal chaos
+ * basis; also writes dQ/dU = 2 M_h U to dQdU when not NULL.
+ * U, dQdU: device n x P FP64; q_out: device double[1]. Needs mass_vals. */
+int sg_qoi(sg_problem* h, const double* U, double* dQdU, double* q_out, void* stream);
+
+/* sg_qoi_grad -- adjoint gradient contraction: with h_k = <Lam, A_k U G_k^T>_F,
+ * grad[t] = sum_k W[t*(M+1) + k] h_k for t = 0..nparam-1 (W host, for
+ * A_k(theta) = theta-scaled KL matrices W = -d log A_k / d theta).
+ * U, Lam: device n x P FP64; grad: device double[nparam]; hk_out: device
+ * double[M+1] or NULL. */
+int sg_qoi_grad(sg_problem* h, const double* U, const double* Lam, int nparam, const double* W,
+                double* grad, double* hk_out, void* stream);
+
+/* Thread-local message of the last failure ("" if none). */
+const char* sg_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (a monotone counter for measurement). */
+long long sg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGHSC_H */

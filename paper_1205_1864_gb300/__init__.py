@@ -1,0 +1,225 @@
+"""GB300 stochastic Galerkin solver with the hierarchical Schur complement
+preconditioner (Sousedik, Ghanem, Phipps; arXiv 1205.1864).
+
+Thin Python binding over the C ABI of ``libsghsc.so`` (``include/sghsc.h``).
+The functions keep the C names (``sg_setup``, ``sg_apply``,
+``hsc_precond_apply``, ``sg_solve``, ...) and only marshal arguments: every
+step of the method runs in the library's CUDA kernels. PyTorch supplies
+device memory and the current stream. There is no CPU fallback: importing the
+package fails if the library has not been built.
+
+Blocks are ``n x P`` row-major CUDA tensors (spatial index slow, chaos index
+fast), ``torch.float64`` unless a call says otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (SG_F32, SG_F64, SG_HERMITE, SG_LEGENDRE, SG_PREC_HSC, SG_PREC_MEAN, SG_PREC_NONE, SGError,
+                   check)
+
+__all__ = [
+    "SGProblem", "sg_setup", "sg_apply", "sg_level_apply", "sg_vcycle_apply", "sg_inner_solve",
+    "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_qoi_grad", "prec_opts", "solve_opts",
+    "SGError", "SG_F32", "SG_F64", "SG_PREC_HSC", "SG_PREC_MEAN", "SG_PREC_NONE", "SG_LEGENDRE", "SG_HERMITE",
+]
+
+_DT = {torch.float64: SG_F64, torch.float32: SG_F32}
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[C.c_void_p]:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def prec_opts(**kw) -> _lib.sg_prec_opts:
+    """Preconditioner options with the library defaults, overridden by ``kw``
+    (precision, top_level_f64, inner_tol, inner_maxit, inner_fixed_iters, nu, omega)."""
+    o = _lib.sg_prec_opts()
+    _lib.LIB.sg_default_prec_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def solve_opts(prec: Optional[_lib.sg_prec_opts] = None, **kw) -> _lib.sg_solve_opts:
+    """Outer solver options (precond, tol, maxit, flexible, use_x0) with defaults."""
+    o = _lib.sg_solve_opts()
+    _lib.LIB.sg_default_solve_opts(C.byref(o))
+    if prec is not None:
+        o.prec = prec
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class SolveStats:
+    status: int
+    iterations: int
+    rel_res: float
+    true_rel_res: float
+    kappa_est: float
+    inner_iters_total: int
+    inner_iters_max: int
+    solve_ms: float
+    res_hist: list
+    alpha: list
+    beta: list
+
+
+class SGProblem:
+    """Owner of an ``sg_problem`` handle (``sg_setup`` / ``sg_destroy``)."""
+
+    def __init__(self, ne_x: int, ne_y: int, M: int, p: int, rowptr, colidx, vals, mass=None,
+                 family: int = SG_LEGENDRE):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        n = rowptr.shape[0] - 1
+        nnz = colidx.shape[0]
+        if vals.shape != (nnz, M + 1):
+            raise ValueError(f"vals must have shape (nnz, M+1) = ({nnz}, {M + 1})")
+        mesh = _lib.sg_mesh(ne_x, ne_y)
+        mp = None
+        if mass is not None:
+            mass = np.ascontiguousarray(mass, dtype=np.float64)
+            mp = mass.ctypes.data_as(C.POINTER(C.c_double))
+        h = C.c_void_p()
+        torch.cuda.init()
+        check(_lib.LIB.sg_setup(C.byref(mesh), M, p, family, n, nnz,
+                                rowptr.ctypes.data_as(C.POINTER(C.c_int)), colidx.ctypes.data_as(C.POINTER(C.c_int)),
+                                vals.ctypes.data_as(C.POINTER(C.c_double)), mp, C.byref(h)), "sg_setup")
+        self.h = h
+        dims = [C.c_int() for _ in range(5)]
+        check(_lib.LIB.sg_problem_dims(h, *[C.byref(x) for x in dims]), "sg_problem_dims")
+        self.n, self.P, self.M, self.p, self.nnz = (d.value for d in dims)
+
+    @classmethod
+    def from_inputs(cls, prob, p: int, family: int = SG_LEGENDRE) -> "SGProblem":
+        """From an ``sg_inputs.Problem`` (seeded synthetic problem)."""
+        return cls(prob.ne, prob.ne, prob.M, p, prob.rowptr, prob.colidx, prob.vals, prob.mass, family)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.LIB.sg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def chaos_table(self):
+        alpha = np.zeros(self.P * max(self.M, 1), dtype=np.int32)
+        off = np.zeros(self.p + 2, dtype=np.int32)
+        check(_lib.LIB.sg_chaos_table(self.h, alpha.ctypes.data_as(C.POINTER(C.c_int)),
+                                      off.ctypes.data_as(C.POINTER(C.c_int))), "sg_chaos_table")
+        return alpha[: self.P * self.M].reshape(self.P, self.M), off
+
+    def empty(self, cols: Optional[int] = None, dtype=torch.float64):
+        return torch.empty((self.n, self.P if cols is None else cols), dtype=dtype, device="cuda")
+
+
+def sg_setup(ne_x, ne_y, M, p, rowptr, colidx, vals, mass=None, family=SG_LEGENDRE) -> SGProblem:
+    return SGProblem(ne_x, ne_y, M, p, rowptr, colidx, vals, mass, family)
+
+
+def sg_apply(h: SGProblem, U: torch.Tensor, Y: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Y = sum_k A_k U G_k^T (K1)."""
+    Y = torch.empty_like(U) if Y is None else Y
+    check(_lib.LIB.sg_apply(h.h, _ptr(U), _ptr(Y), _DT[U.dtype], _stream()), "sg_apply")
+    return Y
+
+
+def sg_level_apply(h: SGProblem, lvl_out: int, lvl_in: int, X: torch.Tensor, Yin: Optional[torch.Tensor],
+                   Yout: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Yout = Yin - sum_k A_k X G_k[out, in]^T between adjacent degree levels (K2)."""
+    if Yout is None:
+        _, off = h.chaos_table()
+        Yout = torch.empty((h.n, int(off[lvl_out + 1] - off[lvl_out])), dtype=X.dtype, device="cuda")
+    check(_lib.LIB.sg_level_apply(h.h, lvl_out, lvl_in, _ptr(X), _ptr(Yin), _ptr(Yout), _DT[X.dtype], _stream()),
+          "sg_level_apply")
+    return Yout
+
+
+def sg_vcycle_apply(h: SGProblem, B: torch.Tensor, opts=None) -> torch.Tensor:
+    X = torch.empty_like(B)
+    o = opts or prec_opts()
+    check(_lib.LIB.sg_vcycle_apply(h.h, _ptr(B), _ptr(X), B.shape[1], _DT[B.dtype], C.byref(o), _stream()),
+          "sg_vcycle_apply")
+    return X
+
+
+def sg_inner_solve(h: SGProblem, B: torch.Tensor, opts=None):
+    X = torch.empty_like(B)
+    o = opts or prec_opts()
+    it = np.zeros(B.shape[1], dtype=np.int32)
+    check(_lib.LIB.sg_inner_solve(h.h, _ptr(B), _ptr(X), B.shape[1], _DT[B.dtype], C.byref(o),
+                                  it.ctypes.data_as(C.POINTER(C.c_int)), _stream()), "sg_inner_solve")
+    return X, it
+
+
+def hsc_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Z = M_P R (Algorithm 1)."""
+    Z = torch.empty_like(R) if Z is None else Z
+    o = opts or prec_opts()
+    check(_lib.LIB.hsc_precond_apply(h.h, _ptr(R), _ptr(Z), C.byref(o), _stream()), "hsc_precond_apply")
+    return Z
+
+
+def mean_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Z = (I (x) A_0^{-1}) R with the inner PCG."""
+    Z = torch.empty_like(R) if Z is None else Z
+    o = opts or prec_opts()
+    check(_lib.LIB.mean_precond_apply(h.h, _ptr(R), _ptr(Z), C.byref(o), _stream()), "mean_precond_apply")
+    return Z
+
+
+def sg_solve(h: SGProblem, F: torch.Tensor, opts=None, U: Optional[torch.Tensor] = None, raise_on_error=True):
+    """Flexible CG on the SG system; returns ``(U, SolveStats)``."""
+    U = torch.empty_like(F) if U is None else U
+    o = opts or solve_opts()
+    st = _lib.sg_solve_stats()
+    status = _lib.LIB.sg_solve(h.h, _ptr(F), _ptr(U), C.byref(o), C.byref(st), _stream())
+    stats = SolveStats(status=status, iterations=st.iterations, rel_res=st.rel_res, true_rel_res=st.true_rel_res,
+                       kappa_est=st.kappa_est, inner_iters_total=st.inner_iters_total,
+                       inner_iters_max=st.inner_iters_max, solve_ms=st.solve_ms,
+                       res_hist=list(st.res_hist[: st.n_hist]), alpha=list(st.alpha[: st.iterations]),
+                       beta=list(st.beta[: max(st.iterations - 1, 0)]))
+    if raise_on_error:
+        check(status, "sg_solve")
+    return U, stats
+
+
+def sg_qoi(h: SGProblem, U: torch.Tensor, want_grad: bool = True):
+    """``Q = sum_j u_j^T M_h u_j`` (device scalar) and ``dQ/dU = 2 M_h U``."""
+    q = torch.empty(1, dtype=torch.float64, device="cuda")
+    dq = torch.empty_like(U) if want_grad else None
+    check(_lib.LIB.sg_qoi(h.h, _ptr(U), _ptr(dq), _ptr(q), _stream()), "sg_qoi")
+    return q, dq
+
+
+def sg_qoi_grad(h: SGProblem, U: torch.Tensor, Lam: torch.Tensor, W: np.ndarray):
+    """``grad[t] = sum_k W[t,k] <Lam, A_k U G_k^T>``; returns ``(grad, h_k)``."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    nparam = W.shape[0]
+    grad = torch.empty(nparam, dtype=torch.float64, device="cuda")
+    hk = torch.empty(h.M + 1, dtype=torch.float64, device="cuda")
+    check(_lib.LIB.sg_qoi_grad(h.h, _ptr(U), _ptr(Lam), nparam, W.ctypes.data_as(C.POINTER(C.c_double)),
+                               _ptr(grad), _ptr(hk), _stream()), "sg_qoi_grad")
+    return grad, hk

@@ -1,0 +1,227 @@
+// Algorithm 1 (Sec. 4): the hierarchical Schur complement preconditioner
+// M_P : r_P -> u_P, and the mean-based preconditioner I (x) A_0^{-1} (Sec. 6).
+//
+// Storage reading of Algorithm 1: one working residual holds r_P; the
+// pre-correction at level l overwrites its degree-(l-1) columns with
+// g_{l-1} = r_l^{l-1} - B_l D_l^{-1} r_l^l (for the linear KL expansion B_l
+// reaches degree l-1 only); the post-correction at level l uses the degree-l
+// columns of that working residual. The D_l^{-1} actions are batched inner
+// PCG solves on A_0 (all columns of one degree level in one batch); the loops
+// over levels stay sequential, as Sec. 6 notes.
+//
+// Mixed precision (precision == SG_F32): the working residual, the inner
+// solves and the level products run in FP32; with top_level_f64 the two
+// level-p products read the FP64 input and accumulate in FP64.
+//
+// Everything here is enqueued inside a CUDA graph capture (the inner solves
+// are device-controlled WHILE loops); the public entry points build the graph
+// once per option set and replay it.
+#include <cstdio>
+
+#include "graph.cuh"
+#include "sghsc_internal.cuh"
+
+namespace sghsc {
+
+static int ensure_hsc32(sg_problem* h) {
+  if (h->R32) return SG_OK;
+  const size_t np = (size_t)h->n * h->P;
+  SG_TRY_CUDA(cudaMalloc((void**)&h->R32, np * sizeof(float)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->Z32, np * sizeof(float)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->T32, (size_t)h->n * std::max(h->wmax, 1) * sizeof(float)));
+  return SG_OK;
+}
+
+static int ensure_hsc64(sg_problem* h) {
+  if (h->R64w) return SG_OK;
+  const size_t np = (size_t)h->n * h->P;
+  SG_TRY_CUDA(cudaMalloc((void**)&h->R64w, np * sizeof(double)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->T64, (size_t)h->n * std::max(h->wmax, 1) * sizeof(double)));
+  return SG_OK;
+}
+
+// Allocate everything a preconditioner application needs (before any capture).
+int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o) {
+  SG_TRY(check_prec_opts(o));
+  const int dt = o.precision == SG_F32 ? SG_F32 : SG_F64;
+  if (kind == SG_PREC_HSC) {
+    SG_TRY(ensure_inner_work(h, dt, h->wmax));
+    SG_TRY(dt == SG_F32 ? ensure_hsc32(h) : ensure_hsc64(h));
+  } else if (kind == SG_PREC_MEAN) {
+    SG_TRY(ensure_inner_work(h, dt, std::max(std::min(h->P, 1024), h->wmax)));
+  }
+  return SG_OK;
+}
+
+int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
+  const int P = h->P, p = h->p, n = h->n;
+  const std::vector<int>& off = h->off;
+  if (o.precision == SG_F32) {
+    float* R32 = h->R32;
+    float* Z32 = h->Z32;
+    const bool top64 = o.top_level_f64 != 0;
+    SG_TRY(launch_cast(R, SG_F64, P, R32, SG_F32, P, n, P, s));
+    // first loop, l = p..1: D_l^{-1} on the degree-l columns, then the pre-correction
+    for (int l = p; l >= 1; --l) {
+      const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1];
+      SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
+      if (l == p && top64)
+        SG_TRY(launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, Z32 + lo, P, w, h->pre[l], false, R + lo1, P,
+                                   -1.0, 1.0, R32 + lo1, P, s));
+      else
+        SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo, P, w, h->pre[l], false, R32 + lo1, P,
+                                   -1.0, 1.0, R32 + lo1, P, s));
+    }
+    // mean-value problem A_0 u_0 = g_0
+    SG_TRY(inner_solve(h, SG_F32, R32, P, SG_F32, Z32, P, SG_F32, off[1] - off[0], o, s));
+    // second loop, l = 1..p: post-correction, then D_l^{-1}
+    for (int l = 1; l <= p; ++l) {
+      const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1], w1 = off[l] - off[l - 1];
+      if (l == p && top64)
+        SG_TRY(launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, Z32 + lo1, P, w1, h->post[l], false, R + lo, P,
+                                   -1.0, 1.0, h->T32, w, s));
+      else
+        SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo1, P, w1, h->post[l], false, R32 + lo,
+                                   P, -1.0, 1.0, h->T32, w, s));
+      SG_TRY(inner_solve(h, SG_F32, h->T32, w, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
+    }
+    SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));
+    return SG_OK;
+  }
+  // all FP64
+  double* Rw = h->R64w;
+  SG_TRY_CUDA(cudaMemcpyAsync(Rw, R, (size_t)n * P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (int l = p; l >= 1; --l) {
+    const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1];
+    SG_TRY(inner_solve(h, SG_F64, Rw + lo, P, SG_F64, Z + lo, P, SG_F64, w, o, s));
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo, P, w, h->pre[l], false, Rw + lo1, P, -1.0,
+                               1.0, Rw + lo1, P, s));
+  }
+  SG_TRY(inner_solve(h, SG_F64, Rw, P, SG_F64, Z, P, SG_F64, off[1] - off[0], o, s));
+  for (int l = 1; l <= p; ++l) {
+    const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1], w1 = off[l] - off[l - 1];
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo1, P, w1, h->post[l], false, Rw + lo, P, -1.0,
+                               1.0, h->T64, w, s));
+    SG_TRY(inner_solve(h, SG_F64, h->T64, w, SG_F64, Z + lo, P, SG_F64, w, o, s));
+  }
+  return SG_OK;
+}
+
+int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
+  const int P = h->P;
+  const int chunk = std::min(P, 1024);
+  const int dt = o.precision == SG_F32 ? SG_F32 : SG_F64;
+  for (int c0 = 0; c0 < P; c0 += chunk) {
+    const int w = std::min(chunk, P - c0);
+    SG_TRY(inner_solve(h, dt, R + c0, P, SG_F64, Z + c0, P, SG_F64, w, o, s));
+  }
+  return SG_OK;
+}
+
+static int check_prec_call(sg_problem* h, const void* R, const void* Z, const sg_prec_opts* o, const char* name) {
+  if (!h || !R || !Z || !o || R == Z || (o->precision != SG_F32 && o->precision != SG_F64)) {
+    set_error("%s: invalid arguments", name);
+    return SG_ERR_INVALID_ARG;
+  }
+  SG_TRY(check_prec_opts(*o));
+  if (h->grids.empty()) {
+    set_error("%s: the inner solves need the multigrid hierarchy (power-of-two square mesh)", name);
+    return SG_ERR_UNSUPPORTED;
+  }
+  return SG_OK;
+}
+
+static int finish_status(sg_problem* h, cudaStream_t s) {
+  SG_TRY_CUDA(cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SG_TRY_CUDA(cudaStreamSynchronize(s));
+  if (*h->status_host & ST_INNER_NOT_SPD) {
+    set_error("inner solve lost definiteness (p^T A_0 p <= 0 or non-finite residual)");
+    return SG_ERR_NOT_SPD;
+  }
+  return SG_OK;
+}
+
+// Graph-run preconditioner application: R is staged into the outer residual
+// buffer, the result comes back from the outer preconditioned-residual buffer.
+static int precond_entry(sg_problem* h, int kind, const double* R, double* Z, const sg_prec_opts& o,
+                         cudaStream_t s) {
+  SG_TRY(ensure_outer(h));
+  SG_TRY(prepare_precond(h, kind, o));
+  const size_t bytes = (size_t)h->n * h->P * sizeof(double);
+  SG_TRY_CUDA(cudaMemcpyAsync(h->fr, R, bytes, cudaMemcpyDeviceToDevice, s));
+  SG_TRY_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+  const std::string key = std::string(kind == SG_PREC_HSC ? "hsc|" : "mean|") + opts_key(o);
+  SG_TRY(run_graph(h, key, [&](cudaStream_t cs) {
+    return kind == SG_PREC_HSC ? hsc_apply_impl(h, h->fr, h->fz, o, cs) : mean_apply_impl(h, h->fr, h->fz, o, cs);
+  }, s));
+  SG_TRY_CUDA(cudaMemcpyAsync(Z, h->fz, bytes, cudaMemcpyDeviceToDevice, s));
+  return finish_status(h, s);
+}
+
+}  // namespace sghsc
+
+using namespace sghsc;
+
+extern "C" {
+
+int hsc_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts, void* stream) {
+  set_error("");
+  SG_TRY(check_prec_call(h, R, Z, opts, "hsc_precond_apply"));
+  return precond_entry(h, SG_PREC_HSC, R, Z, *opts, (cudaStream_t)stream);
+}
+
+int mean_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts, void* stream) {
+  set_error("");
+  SG_TRY(check_prec_call(h, R, Z, opts, "mean_precond_apply"));
+  return precond_entry(h, SG_PREC_MEAN, R, Z, *opts, (cudaStream_t)stream);
+}
+
+int sg_vcycle_apply(sg_problem* h, const void* B, void* X, int w, int dtype, const sg_prec_opts* opts,
+                    void* stream) {
+  set_error("");
+  if (!h || !B || !X || !opts || w <= 0 || w > 1024 || (dtype != SG_F64 && dtype != SG_F32)) {
+    set_error("sg_vcycle_apply: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  return inner_vcycle(h, dtype, B, X, w, *opts, (cudaStream_t)stream);
+}
+
+int sg_inner_solve(sg_problem* h, const void* B, void* X, int w, int dtype, const sg_prec_opts* opts, int* iters,
+                   void* stream) {
+  set_error("");
+  if (!h || !B || !X || !opts || w <= 0 || w > 1024 || (dtype != SG_F64 && dtype != SG_F32)) {
+    set_error("sg_inner_solve: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  SG_TRY(check_prec_opts(*opts));
+  cudaStream_t s = (cudaStream_t)stream;
+  SG_TRY(ensure_inner_work(h, dtype, std::max(w, h->wmax)));
+  const size_t es = dtype == SG_F64 ? 8 : 4;
+  const size_t bytes = (size_t)h->n * w * es;
+  if (h->io_bytes < bytes) {
+    clear_graphs(h);
+    SG_TRY_CUDA(cudaDeviceSynchronize());
+    cudaFree(h->io_in);
+    cudaFree(h->io_out);
+    h->io_in = h->io_out = nullptr;
+    SG_TRY_CUDA(cudaMalloc(&h->io_in, bytes));
+    SG_TRY_CUDA(cudaMalloc(&h->io_out, bytes));
+    h->io_bytes = bytes;
+  }
+  SG_TRY_CUDA(cudaMemcpyAsync(h->io_in, B, bytes, cudaMemcpyDeviceToDevice, s));
+  SG_TRY_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+  char key[320];
+  snprintf(key, sizeof key, "inner|d%d|w%d|%s", dtype, w, opts_key(*opts).c_str());
+  const sg_prec_opts o = *opts;
+  SG_TRY(run_graph(h, key, [&](cudaStream_t cs) {
+    return inner_solve(h, dtype, h->io_in, w, dtype, h->io_out, w, dtype, w, o, cs);
+  }, s));
+  SG_TRY_CUDA(cudaMemcpyAsync(X, h->io_out, bytes, cudaMemcpyDeviceToDevice, s));
+  if (iters) {
+    const InnerWork& iw = dtype == SG_F64 ? h->iw64 : h->iw32;
+    SG_TRY_CUDA(cudaMemcpyAsync(iters, iw.iters, sizeof(int) * w, cudaMemcpyDeviceToHost, s));
+  }
+  return finish_status(h, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,282 @@
+// K1 (fused SG matrix-vector product, eq. (global-system) in MAT-VEC form)
+// and K2 (off-diagonal level products B_l, C_l of Algorithm 1).
+//
+// One thread block owns one spatial row r at a time (grid-stride over rows,
+// consecutive blocks on consecutive rows so the 9 neighbour rows of U are
+// shared through L2). For each chunk of the row's nonzeros it stages the
+// neighbour rows U(c, :) and the M+1 values a_k(r, c) of every nonzero in
+// shared memory -- the shared CSR pattern is read once and all KL matrices
+// ride along -- and each thread then forms its output columns l by the
+// gather form of the sparse G couplings:
+//   Y(r,l) = sum_c a_0(r,c) U(c,l) + sum_{(k,j): alpha_j = alpha_l +- e_k}
+//            (G_k)_{lj} sum_c a_k(r,c) U(c,j).
+// Per nonzero that is P + n_m multiply-adds (n_m the off-diagonal G entries),
+// the smallest count of the contraction orders.
+#include <algorithm>
+
+#include "sghsc_internal.cuh"
+#include "vec.cuh"
+
+namespace sghsc {
+
+// Accumulate the gather form for this thread's outputs over one staged chunk.
+template <typename TAcc, int MAXO, bool DIAG>
+__device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __restrict__ Vs,
+                                             const TAcc* __restrict__ Xs, int wx, const int* __restrict__ eptr,
+                                             const int* __restrict__ ek, const int* __restrict__ ej,
+                                             const TAcc* __restrict__ ec, int wy, TAcc (&acc)[MAXO]) {
+#pragma unroll
+  for (int i = 0; i < MAXO; ++i) {
+    const int l = threadIdx.x + i * blockDim.x;
+    if (l < wy) {
+      TAcc a = TAcc(0);
+      if (DIAG) {
+        for (int e = 0; e < nzc; ++e) a += Vs[e * M1] * Xs[e * wx + l];
+      }
+      const int t1 = eptr[l + 1];
+      for (int t = eptr[l]; t < t1; ++t) {
+        const int k = ek[t], j = ej[t];
+        TAcc s = TAcc(0);
+        for (int e = 0; e < nzc; ++e) s += Vs[e * M1 + k] * Xs[e * wx + j];
+        a += ec[t] * s;
+      }
+      acc[i] += a;
+    }
+  }
+}
+
+template <typename TIn, typename TAcc, typename TB, typename TO, bool DIAG, int MAXO>
+__global__ void __launch_bounds__(256) k_block_matvec(
+    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const TAcc* __restrict__ vals,
+    int M1, const TIn* __restrict__ X, int ldx, int wx, const int* __restrict__ eptr,
+    const int* __restrict__ ek, const int* __restrict__ ej, const TAcc* __restrict__ ec, int wy,
+    const TB* Yin, int ldyin, TAcc alpha, TAcc beta, TO* Y, int ldy, int chunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TAcc* Xs = reinterpret_cast<TAcc*>(smem_raw);
+  TAcc* Vs = Xs + (size_t)chunk * wx;
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    TAcc acc[MAXO];
+#pragma unroll
+    for (int i = 0; i < MAXO; ++i) acc[i] = TAcc(0);
+    const int rb = rowptr[r], re = rowptr[r + 1];
+    for (int cs = rb; cs < re; cs += chunk) {
+      const int nzc = min(chunk, re - cs);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nzc * wx; idx += blockDim.x) {
+        const int e = idx / wx, j = idx - e * wx;
+        Xs[idx] = (TAcc)X[(size_t)colidx[cs + e] * ldx + j];
+      }
+      for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
+      __syncthreads();
+      gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, wy, acc);
+    }
+#pragma unroll
+    for (int i = 0; i < MAXO; ++i) {
+      const int l = threadIdx.x + i * blockDim.x;
+      if (l < wy) {
+        TAcc v = alpha * acc[i];
+        if (Yin) v += beta * (TAcc)Yin[(size_t)r * ldyin + l];
+        Y[(size_t)r * ldy + l] = (TO)v;
+      }
+    }
+  }
+}
+
+// Outer CG step: p_new = z + beta p_old (p_new = z on the first iteration)
+// staged on the fly, q = A p_new, p_new written for the block's own rows,
+// p_new . q reduced and alpha = rho / (p_new . q) set by the last block.
+template <int MAXO>
+__global__ void __launch_bounds__(256) k_outer_matvec(
+    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const double* __restrict__ vals,
+    int M1, int P, const double* __restrict__ z, double* pA, double* pB, const int* __restrict__ eptr,
+    const int* __restrict__ ek, const int* __restrict__ ej, const double* __restrict__ ec,
+    double* __restrict__ q, int chunk, OuterArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Xs = reinterpret_cast<double*>(smem_raw);
+  double* Vs = Xs + (size_t)chunk * P;
+  const int it = a.ctl->it;
+  const bool first = it == 0;
+  const double beta = first ? 0.0 : a.sc[SC_BETA];
+  const double* __restrict__ pold = (it & 1) ? pB : pA;
+  double* __restrict__ pnew = (it & 1) ? pA : pB;
+  double dot = 0.0;
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    double acc[MAXO];
+#pragma unroll
+    for (int i = 0; i < MAXO; ++i) acc[i] = 0.0;
+    const int rb = rowptr[r], re = rowptr[r + 1];
+    for (int cs = rb; cs < re; cs += chunk) {
+      const int nzc = min(chunk, re - cs);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nzc * P; idx += blockDim.x) {
+        const int e = idx / P, j = idx - e * P;
+        const size_t g = (size_t)colidx[cs + e] * P + j;
+        Xs[idx] = first ? z[g] : z[g] + beta * pold[g];
+      }
+      for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
+      __syncthreads();
+      gather_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, P, acc);
+    }
+#pragma unroll
+    for (int i = 0; i < MAXO; ++i) {
+      const int l = threadIdx.x + i * blockDim.x;
+      if (l < P) {
+        const size_t g = (size_t)r * P + l;
+        const double pv = first ? z[g] : z[g] + beta * pold[g];
+        pnew[g] = pv;
+        q[g] = acc[i];
+        dot += pv * acc[i];
+      }
+    }
+  }
+  double pq, unused;
+  if (outer_reduce_last(dot, 0.0, a, pq, unused) && threadIdx.x == 0) {
+    a.sc[SC_PQ] = pq;
+    if (!(pq > 0.0)) {
+      atomicOr(a.status, ST_OUTER_BREAKDOWN);
+      a.sc[SC_ALPHA] = 0.0;
+    } else {
+      a.sc[SC_ALPHA] = a.sc[SC_RHO] / pq;
+    }
+    a.hist_alpha[it] = a.sc[SC_ALPHA];
+  }
+}
+
+static int pick_threads(int wy) {
+  int t = 32;  // a power of two (the fused dot uses a tree reduction)
+  while (t < wy && t < 256) t *= 2;
+  return t;
+}
+
+static int pick_chunk(const sg_problem* h, int wx, size_t es, int M1, size_t* smem) {
+  const size_t smem_cap = 96 * 1024;
+  const size_t per_nz = (size_t)(wx + M1) * es;
+  const int chunk = (int)std::min<size_t>((size_t)std::max(h->max_row_nnz, 1), smem_cap / per_nz);
+  *smem = (size_t)std::max(chunk, 1) * per_nz;
+  return chunk;
+}
+
+template <typename TIn, typename TAcc, typename TB, typename TO, bool DIAG>
+static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList& E, const TB* Yin, int ldyin,
+                    double alpha, double beta, TO* Y, int ldy, cudaStream_t s) {
+  const int wy = E.nout;
+  if (wy == 0) return SG_OK;
+  const int M1 = h->M + 1;
+  const TAcc* vals = nullptr;
+  const TAcc* ec = nullptr;
+  if constexpr (sizeof(TAcc) == 8) {
+    vals = (const TAcc*)h->vals64;
+    ec = (const TAcc*)E.c64;
+  } else {
+    vals = (const TAcc*)h->vals32;
+    ec = (const TAcc*)E.c32;
+  }
+  const int threads = pick_threads(wy);
+  const int maxo = (wy + threads - 1) / threads;
+  size_t smem = 0;
+  const int chunk = pick_chunk(h, wx, sizeof(TAcc), M1, &smem);
+  if (chunk < 1) {
+    set_error("block matvec: row of %d values does not fit in shared memory", wx);
+    return SG_ERR_UNSUPPORTED;
+  }
+  auto go = [&](auto kern) -> int {
+    SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    const int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, vals, M1, X, ldx, wx, E.ptr, E.k, E.j, ec, wy, Yin, ldyin, (TAcc)alpha, (TAcc)beta, Y, ldy, chunk); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+    return SG_OK;
+  };
+  if (maxo <= 1) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 1>);
+  if (maxo <= 2) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 2>);
+  if (maxo <= 4) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 4>);
+  if (maxo <= 8) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 8>);
+  set_error("block matvec: %d output columns exceed the supported 2048", wy);
+  return SG_ERR_UNSUPPORTED;
+}
+
+int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, const void* X, int ldx, int wx,
+                        const EdgeList& E, bool diag, const void* Yin, int ldyin, double alpha, double beta,
+                        void* Y, int ldy, cudaStream_t s) {
+  if (tin == SG_F64 && tacc == SG_F64 && tb == SG_F64 && tout == SG_F64) {
+    auto Xp = (const double*)X;
+    auto Bp = (const double*)Yin;
+    auto Yp = (double*)Y;
+    if (diag) return launch_t<double, double, double, double, true>(h, Xp, ldx, wx, E, Bp, ldyin, alpha, beta, Yp, ldy, s);
+    return launch_t<double, double, double, double, false>(h, Xp, ldx, wx, E, Bp, ldyin, alpha, beta, Yp, ldy, s);
+  }
+  if (tin == SG_F32 && tacc == SG_F32 && tb == SG_F32 && tout == SG_F32) {
+    auto Xp = (const float*)X;
+    auto Bp = (const float*)Yin;
+    auto Yp = (float*)Y;
+    if (diag) return launch_t<float, float, float, float, true>(h, Xp, ldx, wx, E, Bp, ldyin, alpha, beta, Yp, ldy, s);
+    return launch_t<float, float, float, float, false>(h, Xp, ldx, wx, E, Bp, ldyin, alpha, beta, Yp, ldy, s);
+  }
+  if (tin == SG_F32 && tacc == SG_F64 && tb == SG_F64 && tout == SG_F32 && !diag) {
+    return launch_t<float, double, double, float, false>(h, (const float*)X, ldx, wx, E, (const double*)Yin, ldyin,
+                                                         alpha, beta, (float*)Y, ldy, s);
+  }
+  set_error("block matvec: unsupported type combination");
+  return SG_ERR_UNSUPPORTED;
+}
+
+int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
+  const int P = h->P, M1 = h->M + 1;
+  const int threads = 256;  // the fused reduction assumes 256 threads
+  const int maxo = (P + threads - 1) / threads;
+  size_t smem = 0;
+  const int chunk = pick_chunk(h, P, sizeof(double), M1, &smem);
+  if (chunk < 1) {
+    set_error("outer matvec: P = %d does not fit in shared memory", P);
+    return SG_ERR_UNSUPPORTED;
+  }
+  auto go = [&](auto kern) -> int {
+    SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    const int grid = std::min(std::min(h->n, h->num_sms * std::max(per_sm, 1)), h->opart_blocks);
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, h->vals64, M1, P, h->fz, h->fpA, h->fpB, h->all.ptr, h->all.k, h->all.j, h->all.c64, h->fq, chunk, a); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+    return SG_OK;
+  };
+  if (maxo <= 1) return go(k_outer_matvec<1>);
+  if (maxo <= 2) return go(k_outer_matvec<2>);
+  if (maxo <= 4) return go(k_outer_matvec<4>);
+  if (maxo <= 8) return go(k_outer_matvec<8>);
+  set_error("outer matvec: P = %d exceeds the supported 2048", P);
+  return SG_ERR_UNSUPPORTED;
+}
+
+}  // namespace sghsc
+
+using namespace sghsc;
+
+extern "C" {
+
+int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream) {
+  set_error("");
+  if (!h || !U || !Y || (dtype != SG_F64 && dtype != SG_F32) || U == Y) {
+    set_error("sg_apply: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  return launch_block_matvec(h, dtype, dtype, dtype, dtype, U, h->P, h->P, h->all, true, nullptr, 0, 1.0, 0.0, Y,
+                             h->P, (cudaStream_t)stream);
+}
+
+int sg_level_apply(sg_problem* h, int lvl_out, int lvl_in, const void* X, const void* Yin, void* Yout, int dtype,
+                   void* stream) {
+  set_error("");
+  if (!h || !X || !Yout || (dtype != SG_F64 && dtype != SG_F32) || lvl_out < 0 || lvl_in < 0 || lvl_out > h->p ||
+      lvl_in > h->p || (lvl_out - lvl_in != 1 && lvl_in - lvl_out != 1)) {
+    set_error("sg_level_apply: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  const EdgeList& E = lvl_in > lvl_out ? h->pre[lvl_in] : h->post[lvl_out];
+  const int win = h->off[lvl_in + 1] - h->off[lvl_in];
+  const int wout = h->off[lvl_out + 1] - h->off[lvl_out];
+  return launch_block_matvec(h, dtype, dtype, dtype, dtype, X, win, win, E, false, Yin, wout, -1.0, 1.0, Yout, wout,
+                             (cudaStream_t)stream);
+}
+
+}  // extern "C"

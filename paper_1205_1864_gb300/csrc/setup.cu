@@ -1,0 +1,398 @@
+// Problem setup: validation of the inputs, the chaos tables and the sparse G_k
+// couplings (Sec. 2, eq. (gPC-u), (global-system); Sec. 3), and the Galerkin
+// multigrid hierarchy of the mean-value matrix A_0 used by the inner solves.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <map>
+
+#include "graph.cuh"
+#include "sghsc_internal.cuh"
+
+namespace sghsc {
+
+static thread_local char g_err[1024] = "";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+// Graded multi-indices; inside one degree, descending lexicographic order.
+static void emit_degree(int M, int pos, int remaining, std::vector<int>& cur, std::vector<int>& out) {
+  if (pos == M - 1) {
+    cur[pos] = remaining;
+    out.insert(out.end(), cur.begin(), cur.end());
+    return;
+  }
+  for (int a = remaining; a >= 0; --a) {
+    cur[pos] = a;
+    emit_degree(M, pos + 1, remaining - a, cur, out);
+  }
+}
+
+// E[xi psi_m psi_{m+1}] for the orthonormal 1-D family. Legendre with
+// xi ~ U(-sqrt3, sqrt3): sqrt3 (m+1) / sqrt((2m+1)(2m+3)); Hermite with
+// xi ~ N(0,1): sqrt(m+1).
+static double xi_coupling(int m, int family) {
+  if (family == SG_HERMITE) return std::sqrt((double)m + 1.0);
+  return std::sqrt(3.0) * (m + 1.0) / std::sqrt((2.0 * m + 1.0) * (2.0 * m + 3.0));
+}
+
+template <typename T>
+static int upload(T** dst, const T* src, size_t count) {
+  if (count == 0) {
+    *dst = nullptr;
+    return SG_OK;
+  }
+  SG_TRY_CUDA(cudaMalloc((void**)dst, count * sizeof(T)));
+  SG_TRY_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  return SG_OK;
+}
+
+struct HostEdges {
+  std::vector<int> ptr{0}, k, j;
+  std::vector<double> c;
+};
+
+static int upload_edges(const HostEdges& he, EdgeList& E) {
+  E.nout = (int)he.ptr.size() - 1;
+  E.nedges = (int)he.k.size();
+  std::vector<float> c32(he.c.begin(), he.c.end());
+  SG_TRY(upload(&E.ptr, he.ptr.data(), he.ptr.size()));
+  SG_TRY(upload(&E.k, he.k.data(), he.k.size()));
+  SG_TRY(upload(&E.j, he.j.data(), he.j.size()));
+  SG_TRY(upload(&E.c64, he.c.data(), he.c.size()));
+  SG_TRY(upload(&E.c32, c32.data(), c32.size()));
+  return SG_OK;
+}
+
+static void free_edges(EdgeList& E) {
+  cudaFree(E.ptr);
+  cudaFree(E.k);
+  cudaFree(E.j);
+  cudaFree(E.c64);
+  cudaFree(E.c32);
+  E = EdgeList();
+}
+
+// Build the gather-form couplings. For every output column l of [lo_out, hi_out)
+// and every KL index k, the neighbours alpha_l +- e_k inside [lo_in, hi_in).
+static HostEdges build_edges(const sg_problem* h, const std::map<std::vector<int>, int>& index, int lo_out,
+                             int hi_out, int lo_in, int hi_in) {
+  HostEdges he;
+  const int M = h->M;
+  std::vector<int> b(M);
+  for (int l = lo_out; l < hi_out; ++l) {
+    const int* a = h->alpha.data() + (size_t)l * M;
+    for (int k = 0; k < M; ++k) {
+      for (int step = -1; step <= 1; step += 2) {
+        for (int i = 0; i < M; ++i) b[i] = a[i];
+        b[k] += step;
+        if (b[k] < 0) continue;
+        auto it = index.find(b);
+        if (it == index.end()) continue;
+        int j = it->second;
+        if (j < lo_in || j >= hi_in) continue;
+        he.k.push_back(k + 1);
+        he.j.push_back(j - lo_in);
+        he.c.push_back(xi_coupling(std::min(a[k], b[k]), h->family));
+      }
+    }
+    he.ptr.push_back((int)he.k.size());
+  }
+  return he;
+}
+
+// Bilinear prolongation weight of coarse node X (fine position 2X+1) at fine node x.
+static inline double w1(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
+
+// Galerkin coarse stencil P^T A P for full coarsening with bilinear P.
+static void galerkin_coarsen(int nx, int ny, const std::vector<double>& st, int nxc, int nyc,
+                             std::vector<double>& stc) {
+  stc.assign((size_t)nxc * nyc * 9, 0.0);
+  for (int Y = 0; Y < nyc; ++Y) {
+    for (int X = 0; X < nxc; ++X) {
+      const size_t C = (size_t)Y * nxc + X;
+      const int cxf = 2 * X + 1, cyf = 2 * Y + 1;
+      for (int fy = cyf - 1; fy <= cyf + 1; ++fy) {
+        for (int fx = cxf - 1; fx <= cxf + 1; ++fx) {
+          const double wf = w1(fx - cxf) * w1(fy - cyf);
+          const size_t f = (size_t)fy * nx + fx;
+          for (int s = 0; s < 9; ++s) {
+            const double a = st[f * 9 + s];
+            if (a == 0.0) continue;
+            const int gx = fx + (s % 3 - 1), gy = fy + (s / 3 - 1);
+            int Xs[2], Ys[2];
+            double wx[2], wy[2];
+            int nxs = 0, nys = 0;
+            if (gx & 1) { Xs[nxs] = (gx - 1) / 2; wx[nxs++] = 1.0; }
+            else { Xs[nxs] = gx / 2 - 1; wx[nxs++] = 0.5; Xs[nxs] = gx / 2; wx[nxs++] = 0.5; }
+            if (gy & 1) { Ys[nys] = (gy - 1) / 2; wy[nys++] = 1.0; }
+            else { Ys[nys] = gy / 2 - 1; wy[nys++] = 0.5; Ys[nys] = gy / 2; wy[nys++] = 0.5; }
+            for (int iy = 0; iy < nys; ++iy) {
+              if (Ys[iy] < 0 || Ys[iy] >= nyc) continue;
+              for (int ix = 0; ix < nxs; ++ix) {
+                if (Xs[ix] < 0 || Xs[ix] >= nxc) continue;
+                const int dX = Xs[ix] - X, dY = Ys[iy] - Y;
+                stc[C * 9 + (dY + 1) * 3 + (dX + 1)] += wf * a * wx[ix] * wy[iy];
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+static int upload_grid(GridLevel& g, const std::vector<double>& st) {
+  std::vector<float> st32(st.begin(), st.end());
+  std::vector<double> dinv(g.n);
+  for (int i = 0; i < g.n; ++i) dinv[i] = 1.0 / st[(size_t)i * 9 + 4];
+  std::vector<float> dinv32(dinv.begin(), dinv.end());
+  SG_TRY(upload(&g.st64, st.data(), st.size()));
+  SG_TRY(upload(&g.st32, st32.data(), st32.size()));
+  SG_TRY(upload(&g.dinv64, dinv.data(), dinv.size()));
+  SG_TRY(upload(&g.dinv32, dinv32.data(), dinv32.size()));
+  return SG_OK;
+}
+
+static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int nnz, const int* rowptr,
+                      const int* colidx, const double* vals, const double* mass_vals, sg_problem* h) {
+  if (M < 0 || p < 0 || n <= 0 || nnz <= 0 || !rowptr || !colidx || !vals) {
+    set_error("sg_setup: invalid sizes or null pointers (M=%d p=%d n=%d nnz=%d)", M, p, n, nnz);
+    return SG_ERR_INVALID_ARG;
+  }
+  if (family != SG_LEGENDRE && family != SG_HERMITE) {
+    set_error("sg_setup: unknown chaos family %d", family);
+    return SG_ERR_INVALID_ARG;
+  }
+  if (rowptr[0] != 0 || rowptr[n] != nnz) {
+    set_error("sg_setup: rowptr[0] must be 0 and rowptr[n] == nnz");
+    return SG_ERR_INVALID_ARG;
+  }
+  int max_row = 0;
+  for (int r = 0; r < n; ++r) {
+    if (rowptr[r + 1] < rowptr[r]) {
+      set_error("sg_setup: rowptr not monotone at row %d", r);
+      return SG_ERR_INVALID_ARG;
+    }
+    max_row = std::max(max_row, rowptr[r + 1] - rowptr[r]);
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+      if (colidx[e] < 0 || colidx[e] >= n || (e > rowptr[r] && colidx[e] <= colidx[e - 1])) {
+        set_error("sg_setup: column index out of range or unsorted in row %d", r);
+        return SG_ERR_INVALID_ARG;
+      }
+    }
+  }
+  const size_t nv = (size_t)nnz * (M + 1);
+  for (size_t i = 0; i < nv; ++i) {
+    if (!std::isfinite(vals[i])) {
+      set_error("sg_setup: non-finite matrix value at %zu", i);
+      return SG_ERR_INVALID_ARG;
+    }
+  }
+  h->n = n;
+  h->nnz = nnz;
+  h->M = M;
+  h->p = p;
+  h->family = family;
+  h->max_row_nnz = max_row;
+  SG_TRY_CUDA(cudaGetDevice(&h->device));
+  SG_TRY_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+
+  // chaos table
+  h->off.assign(1, 0);
+  std::vector<int> cur(std::max(M, 1));
+  for (int d = 0; d <= p; ++d) {
+    if (M == 0) {  // the constant polynomial only
+      h->off.push_back(1);
+      continue;
+    }
+    emit_degree(M, 0, d, cur, h->alpha);
+    h->off.push_back((int)(h->alpha.size() / M));
+  }
+  h->P = h->off.back();
+  if (M == 0) h->alpha.clear();
+  h->wmax = 0;
+  for (int d = 0; d <= p; ++d) h->wmax = std::max(h->wmax, h->off[d + 1] - h->off[d]);
+  if (h->P > 2048) {
+    set_error("sg_setup: P = %d chaos polynomials exceeds the supported 2048", h->P);
+    return SG_ERR_UNSUPPORTED;
+  }
+
+  std::map<std::vector<int>, int> index;
+  for (int l = 0; l < h->P; ++l)
+    index[std::vector<int>(h->alpha.begin() + (size_t)l * M, h->alpha.begin() + (size_t)(l + 1) * M)] = l;
+  SG_TRY(upload_edges(build_edges(h, index, 0, h->P, 0, h->P), h->all));
+  h->pre.resize(p + 1);
+  h->post.resize(p + 1);
+  for (int l = 1; l <= p; ++l) {
+    SG_TRY(upload_edges(build_edges(h, index, h->off[l - 1], h->off[l], h->off[l], h->off[l + 1]), h->pre[l]));
+    SG_TRY(upload_edges(build_edges(h, index, h->off[l], h->off[l + 1], h->off[l - 1], h->off[l]), h->post[l]));
+  }
+
+  // matrices
+  SG_TRY(upload(&h->rowptr, rowptr, (size_t)n + 1));
+  SG_TRY(upload(&h->colidx, colidx, (size_t)nnz));
+  SG_TRY(upload(&h->vals64, vals, nv));
+  {
+    std::vector<float> v32(vals, vals + nv);
+    SG_TRY(upload(&h->vals32, v32.data(), nv));
+  }
+  if (mass_vals) SG_TRY(upload(&h->mass64, mass_vals, (size_t)nnz));
+
+  // multigrid hierarchy of A_0 on the structured grid
+  if (mesh && mesh->ne_x > 1 && mesh->ne_y > 1) {
+    const int nx = mesh->ne_x - 1, ny = mesh->ne_y - 1;
+    if ((long long)nx * ny != n) {
+      set_error("sg_setup: mesh %dx%d has %d interior nodes, n = %d", mesh->ne_x, mesh->ne_y, nx * ny, n);
+      return SG_ERR_INVALID_ARG;
+    }
+    const int ne = mesh->ne_x;
+    bool ok = mesh->ne_x == mesh->ne_y && (ne & (ne - 1)) == 0;
+    std::vector<double> st((size_t)n * 9, 0.0);
+    for (int r = 0; r < n && ok; ++r) {
+      const int x = r % nx, y = r / nx;
+      for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        const int c = colidx[e], cx = c % nx, cy = c / nx;
+        const int dx = cx - x, dy = cy - y;
+        if (dx < -1 || dx > 1 || dy < -1 || dy > 1) { ok = false; break; }
+        st[(size_t)r * 9 + (dy + 1) * 3 + (dx + 1)] += vals[(size_t)e * (M + 1)];
+      }
+      if (ok && !(st[(size_t)r * 9 + 4] > 0.0)) ok = false;
+    }
+    if (ok) {
+      h->nx = nx;
+      h->ny = ny;
+      int gx = nx, gy = ny;
+      while (true) {
+        GridLevel g;
+        g.nx = gx; g.ny = gy; g.n = gx * gy;
+        SG_TRY(upload_grid(g, st));
+        h->grids.push_back(g);
+        if (gx <= 1) break;
+        const int nxc = (gx - 1) / 2, nyc = (gy - 1) / 2;
+        std::vector<double> stc;
+        galerkin_coarsen(gx, gy, st, nxc, nyc, stc);
+        st.swap(stc);
+        gx = nxc; gy = nyc;
+      }
+    }
+  }
+  // the in-block coarse V-cycle takes over at the first grid with <= 1024 nodes
+  h->cb_level = (int)h->grids.size();
+  for (int g = 0; g < (int)h->grids.size(); ++g)
+    if (h->grids[g].n <= 1024) { h->cb_level = g; break; }
+  for (auto& cs : h->cap) SG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->status, sizeof(int)));
+  SG_TRY_CUDA(cudaMemset(h->status, 0, sizeof(int)));
+  SG_TRY_CUDA(cudaMallocHost((void**)&h->status_host, sizeof(int)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->iacc, 2 * sizeof(long long)));
+  SG_TRY_CUDA(cudaMemset(h->iacc, 0, 2 * sizeof(long long)));
+  return SG_OK;
+}
+
+}  // namespace sghsc
+
+using namespace sghsc;
+
+extern "C" {
+
+const char* sg_last_error(void) { return sghsc::g_err; }
+
+long long sg_kernel_launches(void) { return sghsc::g_launches.load(); }
+
+void sg_default_prec_opts(sg_prec_opts* o) {
+  if (!o) return;
+  o->precision = SG_F32;
+  o->top_level_f64 = 1;
+  o->inner_tol = 1e-2;
+  o->inner_maxit = 200;
+  o->inner_fixed_iters = 0;
+  o->nu = 2;
+  o->omega = 0.8;
+}
+
+void sg_default_solve_opts(sg_solve_opts* o) {
+  if (!o) return;
+  o->precond = SG_PREC_HSC;
+  sg_default_prec_opts(&o->prec);
+  o->tol = 1e-8;
+  o->maxit = 500;
+  o->flexible = 1;
+  o->use_x0 = 0;
+  o->check_true_residual = 1;
+}
+
+int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz, const int* rowptr,
+             const int* colidx, const double* vals, const double* mass_vals, sg_problem** out) {
+  set_error("");
+  if (!out) {
+    set_error("sg_setup: out is null");
+    return SG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  sg_problem* h = new sg_problem();
+  int st = setup_impl(mesh, M, p, family, n, nnz, rowptr, colidx, vals, mass_vals, h);
+  if (st != SG_OK) {
+    sg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return SG_OK;
+}
+
+void sg_destroy(sg_problem* h) {
+  if (!h) return;
+  free_edges(h->all);
+  for (auto& e : h->pre) free_edges(e);
+  for (auto& e : h->post) free_edges(e);
+  for (auto& g : h->grids) {
+    cudaFree(g.st64); cudaFree(g.st32); cudaFree(g.dinv64); cudaFree(g.dinv32);
+  }
+  if (h->cap[0]) cudaDeviceSynchronize();
+  clear_graphs(h);
+  free_inner_work(h);
+  void* bufs[] = {h->rowptr, h->colidx, h->vals64, h->vals32, h->mass64, h->R32, h->Z32, h->T32, h->R64w,
+                  h->T64, h->fF, h->fx, h->fr, h->fz, h->fpA, h->fpB, h->fq, h->opart, h->osc, h->octl,
+                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev};
+  for (void* b : bufs) cudaFree(b);
+  for (auto& cs : h->cap)
+    if (cs) cudaStreamDestroy(cs);
+  if (h->osc_host) cudaFreeHost(h->osc_host);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  delete h;
+}
+
+int sg_problem_dims(const sg_problem* h, int* n, int* P, int* M, int* p, int* nnz) {
+  if (!h) {
+    set_error("sg_problem_dims: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (n) *n = h->n;
+  if (P) *P = h->P;
+  if (M) *M = h->M;
+  if (p) *p = h->p;
+  if (nnz) *nnz = h->nnz;
+  return SG_OK;
+}
+
+int sg_chaos_table(const sg_problem* h, int* alpha, int* level_offsets) {
+  if (!h) {
+    set_error("sg_chaos_table: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (alpha && !h->alpha.empty()) std::memcpy(alpha, h->alpha.data(), h->alpha.size() * sizeof(int));
+  if (level_offsets) std::memcpy(level_offsets, h->off.data(), h->off.size() * sizeof(int));
+  return SG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Internal declarations of libsghsc: the problem handle, device tables and
+// the kernels' host-side launchers. Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sghsc.h"
+
+namespace sghsc {
+
+void set_error(const char* fmt, ...);
+// Process-wide count of kernel launches made by this library (sg_kernel_launches()).
+void note_launch();
+struct GraphEntry;
+void clear_graphs(sg_problem* h);
+
+#define SG_TRY_CUDA(call)                                                           \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ::sghsc::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                  \
+                         cudaGetErrorString(e_));                                   \
+      return e_ == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA;            \
+    }                                                                               \
+  } while (0)
+
+#define SG_TRY(call)                    \
+  do {                                  \
+    int s_ = (call);                    \
+    if (s_ != SG_OK) return s_;         \
+  } while (0)
+
+#define SG_CHECK_LAUNCH() SG_TRY_CUDA(cudaGetLastError())
+
+// Bits of the device status word written by kernels.
+enum : int {
+  ST_INNER_NOT_SPD = 1,
+  ST_INNER_MAXIT = 2,
+  ST_OUTER_BREAKDOWN = 4,
+};
+
+// Sparse G coupling in gather form: for output chaos column l (local index in
+// the output range), edges ptr[l]..ptr[l+1] with KL index k (1..M), input
+// column j (local index in the input range) and coefficient c = (G_k)_{lj}.
+struct EdgeList {
+  int nout = 0, nedges = 0;
+  int* ptr = nullptr;
+  int* k = nullptr;
+  int* j = nullptr;
+  double* c64 = nullptr;
+  float* c32 = nullptr;
+};
+
+// One grid of the geometric multigrid hierarchy: interior nodes nx*ny, x
+// fastest; 9-point stencil [n][9], slot (dy+1)*3 + (dx+1), zero where the
+// neighbour is outside the interior.
+struct GridLevel {
+  int nx = 0, ny = 0, n = 0;
+  double* st64 = nullptr;
+  float* st32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+};
+
+// Device control block of one batched inner solve.
+struct InnerCtl {
+  int it;            // batch iteration counter (selects the p ping-pong buffer)
+  unsigned ticket;   // last-block detection of the reduction kernels
+  int active;        // columns still iterating
+  int pad;
+};
+
+// Workspace of the batched inner PCG / V-cycle for one element size; blocks
+// are n_g x wcap packed, wcap the widest batch of one launch.
+struct InnerWork {
+  int wcap = 0;
+  size_t esize = 0;
+  void *x = nullptr, *r = nullptr, *z = nullptr, *zt = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr;
+  std::vector<void*> cb, cx, cxt;         // per coarse grid g >= 1: rhs, iterate, ping-pong
+  double* part = nullptr;                 // block partial sums [nblk][wcap]
+  int part_blocks = 0;
+  double *rho = nullptr, *pq = nullptr, *rr = nullptr, *bb = nullptr, *alpha = nullptr, *beta = nullptr;
+  int *done = nullptr, *iters = nullptr;
+  InnerCtl* ctl = nullptr;
+};
+
+// Device control block of the outer solve.
+struct OuterCtl {
+  int it;            // outer iterations done
+  unsigned ticket;
+  int maxit;
+  int pad;
+  double tol;
+};
+
+struct GraphEntry {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace sghsc
+
+struct sg_problem {
+  int n = 0, nnz = 0, M = 0, p = 0, P = 0, family = 0;
+  int nx = 0, ny = 0;                 // mesh interior size (0 if no mesh)
+  int device = 0, num_sms = 0;
+  std::vector<int> alpha;             // host P*M
+  std::vector<int> off;               // host p+2
+  // shared CSR pattern and KL values [nnz][M+1]
+  int* rowptr = nullptr;
+  int* colidx = nullptr;
+  double* vals64 = nullptr;
+  float* vals32 = nullptr;
+  double* mass64 = nullptr;
+  int max_row_nnz = 0;
+  // G couplings: all edges (for the full operator) and per adjacent level pair
+  sghsc::EdgeList all;                      // outputs 0..P-1, inputs 0..P-1
+  std::vector<sghsc::EdgeList> pre;         // pre[l]:  out level l-1, in level l   (B_l), l = 1..p
+  std::vector<sghsc::EdgeList> post;        // post[l]: out level l,   in level l-1 (C_l), l = 1..p
+  // multigrid
+  std::vector<sghsc::GridLevel> grids;
+  int cb_level = 0;                         // first grid handled by the in-block coarse V-cycle
+  // workspace
+  sghsc::InnerWork iw32, iw64;
+  float* R32 = nullptr;                     // n x P working residual (mixed HSC)
+  float* Z32 = nullptr;                     // n x P preconditioner output (mixed HSC)
+  float* T32 = nullptr;                     // n x wmax packed post-correction rhs
+  double* R64w = nullptr;                   // n x P working residual (FP64 HSC)
+  double* T64 = nullptr;                    // n x wmax packed
+  int wmax = 0;                             // widest degree level
+  // outer solver (n x P FP64 each)
+  double *fF = nullptr, *fx = nullptr, *fr = nullptr, *fz = nullptr, *fpA = nullptr, *fpB = nullptr, *fq = nullptr;
+  double* opart = nullptr;                  // [nblk][2] partial dots
+  int opart_blocks = 0;
+  double* osc = nullptr;                    // device scalars
+  double* osc_host = nullptr;               // pinned mirror
+  sghsc::OuterCtl* octl = nullptr;
+  double *hist_alpha = nullptr, *hist_beta = nullptr, *hist_res = nullptr;
+  // staging for the standalone inner-solve entry point
+  void *io_in = nullptr, *io_out = nullptr;
+  size_t io_bytes = 0;
+  int* status = nullptr;                    // device status word
+  int* status_host = nullptr;               // pinned
+  long long* iacc = nullptr;                // device: [total inner iterations, max per column]
+  double* wdev = nullptr;                   // device copy of gradient weights
+  int wdev_cap = 0;
+  // graphs
+  cudaStream_t cap[4] = {nullptr, nullptr, nullptr, nullptr};
+  int cap_depth = 0;
+  bool capturing = false;
+  std::map<std::string, sghsc::GraphEntry> graphs;
+};
+
+namespace sghsc {
+
+// ---- launchers (matvec.cu) ----
+// Generic block product used for the full operator (K1) and the level products (K2):
+//   Y[r, l] = beta * Yin[r, l] + alpha * ( diag ? sum_c a_0(r,c) X[c, l] : 0
+//                                          + sum_{(k,j,c)} c sum_c' a_k(r,c') X[c', j] )
+// TIn: element type of X; TAcc: arithmetic and value type; TB: type of Yin; TO: type of Y.
+int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, const void* X, int ldx,
+                        int wx, const EdgeList& E, bool diag, const void* Yin, int ldyin,
+                        double alpha, double beta, void* Y, int ldy, cudaStream_t s);
+
+// ---- inner solver (inner.cu) ----
+int ensure_inner_work(sg_problem* h, int dtype, int wcap);
+void free_inner_work(sg_problem* h);
+int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const sg_prec_opts& o,
+                 cudaStream_t s);
+// Solve A_0 X = B columnwise inside a graph capture on s. B read from src
+// (ld_src, element type src_t), solution written to dst (ld_dst, type dst_t).
+int inner_solve(sg_problem* h, int dtype, const void* src, int ld_src, int src_t, void* dst,
+                int ld_dst, int dst_t, int w, const sg_prec_opts& o, cudaStream_t s);
+int check_prec_opts(const sg_prec_opts& o);
+
+// ---- HSC / mean preconditioner (hsc.cu) ----
+int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o);
+int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
+int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
+
+// ---- outer solver buffers (fcg.cu) ----
+int ensure_outer(sg_problem* h);
+
+// ---- small elementwise kernels (vec.cu) ----
+int launch_cast(const void* src, int src_t, int lds, void* dst, int dst_t, int ldd, int rows,
+                int cols, cudaStream_t s);
+
+std::string opts_key(const sg_prec_opts& o);
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace sghsc

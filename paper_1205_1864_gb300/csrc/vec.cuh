@@ -1,0 +1,87 @@
+// Outer-solver kernels shared by the FCG driver (vec.cu, matvec.cu, fcg.cu).
+#pragma once
+
+#include "sghsc_internal.cuh"
+
+namespace sghsc {
+
+// Slots of the device scalar array of the outer solver.
+enum { SC_RHO = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RR, SC_FF, SC_REL, SC_TRUE, SC_COUNT };
+
+// Arguments of the outer kernels that finish with a last-block update of the
+// CG scalars (passed by value).
+struct OuterArgs {
+  double* part;             // [nblk][2] block partials
+  OuterCtl* ctl;
+  double* sc;               // SC_* scalars
+  double *hist_alpha, *hist_beta, *hist_res;
+  int* status;
+  int flexible;
+  int maxit;
+  double tol;
+  cudaGraphConditionalHandle cond;
+  int has_cond;
+};
+
+__global__ void k_outer_init(long long N, const double* F, const double* Y, double* r, OuterArgs a);
+__global__ void k_outer_dots(long long N, const double* z, const double* r, const double* q, OuterArgs a);
+__global__ void k_outer_update(long long N, const double* pA, const double* pB, const double* q, double* x,
+                               double* r, OuterArgs a);
+__global__ void k_outer_true(long long N, const double* F, const double* Y, OuterArgs a);
+
+// Fixed-order block sum of (v0, v1) to part[blockIdx]; returns true in the last
+// block, whose threads then hold the totals (t0, t1) over all blocks (summed in
+// block order). // blockDim must be 256 (a power of two) for the tree below.
+__device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const OuterArgs& a, double& t0, double& t1) {
+  __shared__ double r0[256], r1[256];
+  __shared__ bool last;
+  r0[threadIdx.x] = v0;
+  r1[threadIdx.x] = v1;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      r0[threadIdx.x] += r0[threadIdx.x + s];
+      r1[threadIdx.x] += r1[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.part[(size_t)blockIdx.x * 2 + 0] = r0[0];
+    a.part[(size_t)blockIdx.x * 2 + 1] = r1[0];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&a.ctl->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    s0 += __ldcg(&a.part[(size_t)b * 2 + 0]);
+    s1 += __ldcg(&a.part[(size_t)b * 2 + 1]);
+  }
+  r0[threadIdx.x] = s0;
+  r1[threadIdx.x] = s1;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      r0[threadIdx.x] += r0[threadIdx.x + s];
+      r1[threadIdx.x] += r1[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  t0 = r0[0];
+  t1 = r1[0];
+  if (threadIdx.x == 0) a.ctl->ticket = 0;
+  return true;
+}
+
+
+int vec_grid(long long N);
+
+// The outer CG step q = A p_new with p_new = z + beta p_old staged on the fly
+// (ping-pong p buffers chosen by the device iteration counter), the fused
+// p_new . q reduction and the alpha update by the last block (matvec.cu).
+int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s);
+
+}  // namespace sghsc
