@@ -119,6 +119,7 @@ static OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o) {
   a.tol = o.tol;
   a.cond = 0;
   a.has_cond = 0;
+  a.flag = nullptr;
   return a;
 }
 
@@ -127,10 +128,11 @@ static int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) 
   const long long N = (long long)h->n * h->P;
   const int vg = std::min(vec_grid(N), h->opart_blocks);
   OuterArgs a0 = outer_args(h, o);
-  auto pre = [&](cudaStream_t ps, cudaGraphConditionalHandle cond) -> int {
+  auto pre = [&](cudaStream_t ps, const LoopCtl& lc) -> int {
     OuterArgs a = a0;
-    a.cond = cond;
-    a.has_cond = 1;
+    a.cond = lc.cond;
+    a.has_cond = lc.has_cond;
+    a.flag = lc.flag;
     if (o.use_x0) {
       SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, h->fx, h->P, h->P, h->all, true, nullptr, 0, 1.0,
                                  0.0, h->fq, h->P, ps));
@@ -142,10 +144,11 @@ static int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) 
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
-  auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle cond) -> int {
+  auto body = [&](cudaStream_t bs, const LoopCtl& lc) -> int {
     OuterArgs a = a0;
-    a.cond = cond;
-    a.has_cond = 1;
+    a.cond = lc.cond;
+    a.has_cond = lc.has_cond;
+    a.flag = lc.flag;
     SG_TRY(precond(h, o.precond, h->fr, h->fz, o.prec, bs));
     { k_outer_dots<<<vg, 256, 0, bs>>>(N, h->fz, h->fr, h->fq, a); ::sghsc::note_launch(); }
     SG_TRY(launch_outer_matvec(h, a, bs));

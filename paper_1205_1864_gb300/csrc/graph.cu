@@ -4,7 +4,31 @@
 
 namespace sghsc {
 
+static int eager_while(sg_problem* h, cudaStream_t s, const EnqueueCond& pre, const EnqueueCond& body) {
+  if (h->loop_depth >= 8) {
+    set_error("eager loop: nested too deeply");
+    return SG_ERR_UNSUPPORTED;
+  }
+  LoopCtl lc{0, 0, h->loopflags + h->loop_depth};
+  ++h->loop_depth;
+  int r = pre(s, lc);
+  while (r == SG_OK) {
+    cudaError_t e = cudaMemcpyAsync(h->loopflag_host, lc.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("eager loop: %s", cudaGetErrorString(e));
+      r = SG_ERR_CUDA;
+      break;
+    }
+    if (!*h->loopflag_host) break;
+    r = body(s, lc);
+  }
+  --h->loop_depth;
+  return r;
+}
+
 int capture_while(sg_problem* h, cudaStream_t s, const EnqueueCond& pre, const EnqueueCond& body) {
+  if (!h->capturing) return eager_while(h, s, pre, body);
   if (h->cap_depth + 1 >= (int)(sizeof(h->cap) / sizeof(h->cap[0]))) {
     set_error("graph capture: loops nested too deeply");
     return SG_ERR_UNSUPPORTED;
@@ -18,7 +42,8 @@ int capture_while(sg_problem* h, cudaStream_t s, const EnqueueCond& pre, const E
   }
   cudaGraphConditionalHandle cond;
   SG_TRY_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
-  SG_TRY(pre(s, cond));
+  const LoopCtl lc{cond, 1, nullptr};
+  SG_TRY(pre(s, lc));
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
   SG_TRY_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
@@ -32,7 +57,7 @@ int capture_while(sg_problem* h, cudaStream_t s, const EnqueueCond& pre, const E
   cudaGraph_t bodyg = np.conditional.phGraph_out[0];
   cudaStream_t bs = h->cap[++h->cap_depth];
   SG_TRY_CUDA(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  int r = body(bs, cond);
+  int r = body(bs, lc);
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(bs, &out);
   --h->cap_depth;
@@ -51,6 +76,10 @@ void clear_graphs(sg_problem* h) {
 }
 
 int run_graph(sg_problem* h, const std::string& key, const Enqueue& build, cudaStream_t launch) {
+  if (h->eager) {
+    h->loop_depth = 0;
+    return build(launch);
+  }
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaStream_t cs = h->cap[0];

@@ -11,7 +11,7 @@
 // scalars and a done flag; a column is finished when ||r|| <= tol ||b||
 // (zero columns at entry), and finished columns are skipped by every kernel.
 //
-// Thread mapping: a block has k*w threads (k = max(1, 256 / w)), thread t
+// Thread mapping: a block has k*w threads (k = max(1, 1024 / w)), thread t
 // always handles column t mod w and nodes (blockIdx*k + t / w) + m * grid*k,
 // so per-column partial sums are register accumulations followed by a
 // fixed-order block reduction; the last block to finish a reduction kernel
@@ -37,20 +37,21 @@
 
 namespace sghsc {
 
-constexpr int CB_MAX_NODES = 1024;
-constexpr int CPB = 4;
 constexpr int MAX_LEVELS = 16;
 
 struct Shape {
   int w, k, bdim, grid;
 };
 
-static Shape make_shape(const sg_problem* h, int nodes, int w) {
+// k*w threads per block (up to 1024), at most `per_sm` blocks per SM. The
+// reduction kernels use one block per SM: few block partials per column, so
+// the last-block reduction stays short.
+static Shape make_shape(const sg_problem* h, int nodes, int w, int per_sm = 2) {
   Shape s;
   s.w = w;
-  s.k = w <= 256 ? std::max(1, 256 / w) : 1;
+  s.k = std::max(1, 1024 / w);
   s.bdim = s.k * w;
-  s.grid = std::max(1, std::min(ceil_div(nodes, s.k), h->num_sms * 8));
+  s.grid = std::max(1, std::min(ceil_div(nodes, s.k), h->num_sms * per_sm));
   return s;
 }
 
@@ -68,16 +69,19 @@ struct Acc<double> {
 enum { FIN_INIT = 0, FIN_RHO = 1, FIN_ALPHA = 2, FIN_CONV = 3 };
 
 struct FinArgs {
-  double* part;
+  void* part;        // block partials [nblk][ldp] in the solver's accumulation type
   int ldp;
   InnerCtl* ctl;
   double *rho, *pq, *rr, *bb, *alpha, *beta;
+  float *alphaf, *betaf;  // FP32 copies read by the FP32 kernels
   int *done, *iters;
   int* status;
   double tol2;
   int maxit, fixed;
   cudaGraphConditionalHandle cond;
   int has_cond;
+  int* flag;
+  long long* iacc;  // running [total, max] of per-column iteration counts
 };
 
 __device__ __forceinline__ void thread_pos(int w, int k, int& col, int& node0, int& nstep) {
@@ -86,46 +90,105 @@ __device__ __forceinline__ void thread_pos(int w, int k, int& col, int& node0, i
   nstep = gridDim.x * k;
 }
 
-// Per-column block partial: the k threads of column c sum in a fixed order.
-__device__ __forceinline__ void block_col_reduce(double v, int w, int k, double* part, int ldp) {
-  __shared__ double red[1024];
+// Lanes per column group: the largest power of two g <= 32 with g*w <= bdim.
+// Column c is reduced by the g consecutive threads c*g .. c*g+g-1, which lie in
+// one warp, so a group finishes with g-wide shuffles (fixed order, no block
+// barrier); threads beyond w*g only take part in the shuffles.
+__device__ __forceinline__ int group_lanes(int w, int bdim) {
+  int g = 1;
+  while (g < 32 && 2 * g * w <= bdim) g *= 2;
+  return g;
+}
+
+template <typename A>
+__device__ __forceinline__ A group_shfl_sum(A s, int g) {
+  for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
+  return s;
+}
+
+// True for a warp that owns at least one column of the lane-group layout
+// (warp-uniform); the other warps skip the column arithmetic, which matters
+// because FP64 instructions issue at a fraction of the FP32 rate.
+__device__ __forceinline__ bool warp_owns_column(int w, int g) { return (int)((threadIdx.x & ~31u) / g) < w; }
+
+// Per-column block partial of the k threads of each column (thread t holds
+// column t mod w, slice t / w), summed in the accumulation type A of the
+// solver (FP32 for the FP32 inner solves) and stored as a double.
+template <typename A>
+__device__ __forceinline__ void block_col_reduce(A v, int w, int k, A* part, int ldp) {
+  __shared__ A red[1024];
   red[threadIdx.x] = v;
   __syncthreads();
-  if ((int)threadIdx.x < w) {
-    double s = 0.0;
-    for (int m = 0; m < k; ++m) s += red[threadIdx.x + m * w];
-    part[(size_t)blockIdx.x * ldp + threadIdx.x] = s;
+  const int g = group_lanes(w, blockDim.x);
+  if (!warp_owns_column(w, g)) return;
+  const int c = threadIdx.x / g, lane = threadIdx.x - c * g;
+  A s = A(0);
+  if (c < w)
+    for (int j = lane; j < k; j += g) s += red[j * w + c];
+  s = group_shfl_sum(s, g);
+  if (c < w && lane == 0) {
+    part[(size_t)blockIdx.x * ldp + c] = s;
+    __threadfence();  // only the writers of partials need the release fence
   }
 }
 
-// True in the last block to finish (threadFenceReduction pattern).
+// True in the last block to finish (threadFenceReduction pattern): the writers
+// of block partials have fenced; thread 0 takes a ticket, and the block whose
+// ticket is the last one reads every partial from L2.
 __device__ __forceinline__ bool last_block(unsigned* ticket) {
   __shared__ bool last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (last) __threadfence();
+  }
   __syncthreads();
-  if (last) __threadfence();
   return last;
 }
 
 // Column-wise CG scalar updates from the block partials (last block only).
-__device__ void fin_columns(const FinArgs& f, int op, int w, int nblk) {
+// Column c is summed by its lane group in the accumulation type A (blocks lane,
+// lane + g, ... with four interleaved accumulators, then the g-wide shuffle);
+// the column totals go through shared memory to threads 0..w-1, which update
+// the scalars in FP64 (so only the first ceil(w/32) warps issue FP64 work).
+// The order is fixed, so results are reproducible.
+template <typename A>
+__device__ void fin_columns(const FinArgs& f, int op, int w, int k, int nblk) {
   __shared__ int cnt;
+  __shared__ double colsum[1024];
   if (threadIdx.x == 0) cnt = 0;
+  const A* part = (const A*)f.part;
+  const int g = group_lanes(w, blockDim.x);
+  const int gc = threadIdx.x / g, lane = threadIdx.x - gc * g;
+  if (warp_owns_column(w, g)) {
+    A s0 = A(0), s1 = A(0), s2 = A(0), s3 = A(0);
+    if (gc < w) {
+      int b = lane;
+      for (; b + 3 * g < nblk; b += 4 * g) {
+        s0 += __ldcg(&part[(size_t)b * f.ldp + gc]);
+        s1 += __ldcg(&part[(size_t)(b + g) * f.ldp + gc]);
+        s2 += __ldcg(&part[(size_t)(b + 2 * g) * f.ldp + gc]);
+        s3 += __ldcg(&part[(size_t)(b + 3 * g) * f.ldp + gc]);
+      }
+      for (; b < nblk; b += g) s0 += __ldcg(&part[(size_t)b * f.ldp + gc]);
+    }
+    const A s = group_shfl_sum((s0 + s1) + (s2 + s3), g);
+    if (gc < w && lane == 0) colsum[gc] = (double)s;
+  }
   __syncthreads();
   const int c = threadIdx.x;
   if (c < w) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += __ldcg(&f.part[(size_t)b * f.ldp + c]);
+    const double s = colsum[c];
     if (op == FIN_INIT) {
       f.bb[c] = s;
       f.done[c] = !(s > 0.0);
       f.iters[c] = 0;
       f.beta[c] = 0.0;
+      f.betaf[c] = 0.0f;
     } else if (!f.done[c]) {
       if (op == FIN_RHO) {
         f.beta[c] = f.iters[c] == 0 ? 0.0 : s / f.rho[c];
+        f.betaf[c] = (float)f.beta[c];
         f.rho[c] = s;
       } else if (op == FIN_ALPHA) {
         f.pq[c] = s;
@@ -136,6 +199,7 @@ __device__ void fin_columns(const FinArgs& f, int op, int w, int nblk) {
         } else {
           f.alpha[c] = f.rho[c] / s;
         }
+        f.alphaf[c] = (float)f.alpha[c];
       } else if (op == FIN_CONV) {
         f.rr[c] = s;
         const int it = ++f.iters[c];
@@ -154,6 +218,10 @@ __device__ void fin_columns(const FinArgs& f, int op, int w, int nblk) {
           atomicOr(f.status, ST_INNER_NOT_SPD);
         }
         f.done[c] = fin;
+        if (fin) {
+          atomicAdd((unsigned long long*)&f.iacc[0], (unsigned long long)it);
+          atomicMax(&f.iacc[1], (long long)it);
+        }
       }
     }
     if (!f.done[c]) atomicAdd(&cnt, 1);
@@ -163,33 +231,18 @@ __device__ void fin_columns(const FinArgs& f, int op, int w, int nblk) {
     if (op == FIN_INIT) f.ctl->it = 0;
     if (op == FIN_CONV) f.ctl->it += 1;
     f.ctl->active = cnt;
-    if ((op == FIN_INIT || op == FIN_CONV) && f.has_cond) cudaGraphSetConditional(f.cond, cnt > 0 ? 1u : 0u);
+    if (op == FIN_INIT || op == FIN_CONV) {
+      if (f.has_cond) cudaGraphSetConditional(f.cond, cnt > 0 ? 1u : 0u);
+      if (f.flag) *f.flag = cnt > 0;
+    }
     f.ctl->ticket = 0;
   }
 }
 
-__device__ __forceinline__ void reduce_finalize(const FinArgs& f, double v, int w, int k, int op) {
-  block_col_reduce(v, w, k, f.part, f.ldp);
-  if (last_block(&f.ctl->ticket)) fin_columns(f, op, w, gridDim.x);
-}
-
-// sum_j a_ij v_j over the 9-point stencil of node (x, y) (v node-major, ld w)
-template <typename T>
-__device__ __forceinline__ T stencil_dot(const T* __restrict__ s9, int nx, int ny, int x, int y,
-                                         const T* __restrict__ v, int w, int col) {
-  T acc = T(0);
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-    const int yy = y + dy;
-    if (yy < 0 || yy >= ny) continue;
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int xx = x + dx;
-      if (xx < 0 || xx >= nx) continue;
-      acc += s9[(dy + 1) * 3 + (dx + 1)] * v[(size_t)(yy * nx + xx) * w + col];
-    }
-  }
-  return acc;
+template <typename A>
+__device__ __forceinline__ void reduce_finalize(const FinArgs& f, A v, int w, int k, int op) {
+  block_col_reduce(v, w, k, (A*)f.part, f.ldp);
+  if (last_block(&f.ctl->ticket)) fin_columns<A>(f, op, w, k, gridDim.x);
 }
 
 // (P xc) at fine node (fx, fy): bilinear interpolation from the coarse grid,
@@ -214,85 +267,123 @@ __device__ __forceinline__ T prolong_at(int fx, int fy, int nxc, int nyc, const 
   return acc;
 }
 
+// A thread's node sequence node0, node0 + nstep, ... with the grid coordinates
+// (x, y) kept incrementally (no division per node).
+struct NodeIter {
+  int node, x, y, nstep, dxs, dys, nx;
+  __device__ __forceinline__ NodeIter(int node0, int step, int nx_) : node(node0), nstep(step), nx(nx_) {
+    y = node0 / nx_;
+    x = node0 - y * nx_;
+    dys = step / nx_;
+    dxs = step - dys * nx_;
+  }
+  __device__ __forceinline__ void next() {
+    node += nstep;
+    x += dxs;
+    y += dys;
+    if (x >= nx) {
+      x -= nx;
+      ++y;
+    }
+  }
+};
+
+// sum_j a_ij val(e_j, j, dy, dx) over the 9-point stencil of node (x, y),
+// e_j = i + dy*rs + dx*w the element index of neighbour j = node + dy*nx + dx
+// (node-major blocks, rs = nx*w). Interior nodes take a branch-free path.
+template <typename T, typename F>
+__device__ __forceinline__ T stencil9(const T* __restrict__ s9, int i, int rs, int w, int node, int x, int y, int nx,
+                                      int ny, F val) {
+  T acc = T(0);
+  if (x > 0 && x < nx - 1 && y > 0 && y < ny - 1) {
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx)
+        acc += s9[(dy + 1) * 3 + (dx + 1)] * val(i + dy * rs + dx * w, node + dy * nx + dx, dy, dx);
+    return acc;
+  }
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    if (y + dy < 0 || y + dy >= ny) continue;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      if (x + dx < 0 || x + dx >= nx) continue;
+      acc += s9[(dy + 1) * 3 + (dx + 1)] * val(i + dy * rs + dx * w, node + dy * nx + dx, dy, dx);
+    }
+  }
+  return acc;
+}
+
 // ---------------------------------------------------------------- V-cycle ---
 
 // one sweep from zero: x = omega D^{-1} b
 template <typename T>
-__global__ void k_smooth0(int n, int w, int k, const T* __restrict__ dinv, const T* __restrict__ b,
-                          T* __restrict__ x, T om, const int* __restrict__ done) {
+__global__ void __launch_bounds__(1024) k_smooth0(int n, int w, int k, const T* __restrict__ dinv,
+                                                  const T* __restrict__ b, T* __restrict__ x, T om,
+                                                  const int* __restrict__ done) {
   int col, node, nstep;
   thread_pos(w, k, col, node, nstep);
   if (done[col]) return;
   for (; node < n; node += nstep) {
-    const size_t i = (size_t)node * w + col;
+    const int i = node * w + col;
     x[i] = om * dinv[node] * b[i];
   }
 }
 
 // two sweeps from zero: x1 = omega D^{-1} b, x2 = x1 + omega D^{-1} (b - A x1)
 template <typename T>
-__global__ void k_smooth00(int nx, int ny, int w, int k, const T* __restrict__ st, const T* __restrict__ dinv,
-                           const T* __restrict__ b, T* __restrict__ x, T om, const int* __restrict__ done) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
+__global__ void __launch_bounds__(1024) k_smooth00(int nx, int ny, int w, int k, const T* __restrict__ st,
+                                                   const T* __restrict__ dinv, const T* __restrict__ b,
+                                                   T* __restrict__ x, T om, const int* __restrict__ done) {
+  int col, node0, nstep;
+  thread_pos(w, k, col, node0, nstep);
   if (done[col]) return;
-  const int n = nx * ny;
-  for (; node < n; node += nstep) {
-    const int y = node / nx, xx0 = node - y * nx;
-    const T* s9 = st + (size_t)node * 9;
-    T ax1 = T(0);
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = y + dy;
-      if (yy < 0 || yy >= ny) continue;
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = xx0 + dx;
-        if (xx < 0 || xx >= nx) continue;
-        const int j = yy * nx + xx;
-        ax1 += s9[(dy + 1) * 3 + (dx + 1)] * (om * dinv[j] * b[(size_t)j * w + col]);
-      }
-    }
-    const size_t i = (size_t)node * w + col;
-    const T bi = b[i], di = dinv[node];
-    const T x1 = om * di * bi;
-    x[i] = x1 + om * di * (bi - ax1);
+  const int n = nx * ny, rs = nx * w;
+  for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+    const int i = it.node * w + col;
+    const T ax1 = om * stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
+                                [&](int e, int j, int, int) { return dinv[j] * b[e]; });
+    const T bi = b[i], di = dinv[it.node];
+    x[i] = om * di * bi + om * di * (bi - ax1);
   }
 }
 
 // xo = xi + omega D^{-1} (b - A xi); with DOT also the partials of b . xo and FIN_RHO
 template <typename T, bool DOT>
-__global__ void k_jacobi(int nx, int ny, int w, int k, const T* __restrict__ st, const T* __restrict__ dinv,
-                         const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo, T om, FinArgs f) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
+__global__ void __launch_bounds__(1024) k_jacobi(int nx, int ny, int w, int k, const T* __restrict__ st,
+                                                 const T* __restrict__ dinv, const T* __restrict__ b,
+                                                 const T* __restrict__ xi, T* __restrict__ xo, T om, FinArgs f) {
+  int col, node0, nstep;
+  thread_pos(w, k, col, node0, nstep);
   typename Acc<T>::type acc = 0;
   if (!f.done[col]) {
-    const int n = nx * ny;
-    for (; node < n; node += nstep) {
-      const int y = node / nx, x = node - y * nx;
-      const size_t i = (size_t)node * w + col;
+    const int n = nx * ny, rs = nx * w;
+    for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+      const int i = it.node * w + col;
       const T bi = b[i];
-      const T v = xi[i] + om * dinv[node] * (bi - stencil_dot(st + (size_t)node * 9, nx, ny, x, y, xi, w, col));
+      const T ax = stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
+                            [&](int e, int, int, int) { return xi[e]; });
+      const T v = xi[i] + om * dinv[it.node] * (bi - ax);
       xo[i] = v;
       if (DOT) acc += bi * v;
     }
   }
-  if (DOT) reduce_finalize(f, (double)acc, w, k, FIN_RHO);
+  if (DOT) reduce_finalize(f, acc, w, k, FIN_RHO);
 }
 
 // bc = P^T (b - A x): coarse node (X, Y) gathers the 3x3 fine residuals around (2X+1, 2Y+1)
 template <typename T>
-__global__ void k_resid_restrict(int nxf, int nyf, int nxc, int nyc, int w, int k, const T* __restrict__ st,
-                                 const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ bc,
-                                 const int* __restrict__ done) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
+__global__ void __launch_bounds__(1024) k_resid_restrict(int nxf, int nyf, int nxc, int nyc, int w, int k,
+                                                         const T* __restrict__ st, const T* __restrict__ b,
+                                                         const T* __restrict__ x, T* __restrict__ bc,
+                                                         const int* __restrict__ done) {
+  int col, node0, nstep;
+  thread_pos(w, k, col, node0, nstep);
   if (done[col]) return;
-  const int n = nxc * nyc;
-  for (; node < n; node += nstep) {
-    const int Y = node / nxc, X = node - Y * nxc;
-    const int cx = 2 * X + 1, cy = 2 * Y + 1;
+  const int n = nxc * nyc, rsf = nxf * w;
+  for (NodeIter it(node0, nstep, nxc); it.node < n; it.next()) {
+    const int cx = 2 * it.x + 1, cy = 2 * it.y + 1;
     T acc = T(0);
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
@@ -300,52 +391,84 @@ __global__ void k_resid_restrict(int nxf, int nyf, int nxc, int nyc, int w, int 
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         const T wx = dx == 0 ? T(1) : T(0.5);
-        const int fx = cx + dx, fy = cy + dy;
-        const int f = fy * nxf + fx;
-        const T r = b[(size_t)f * w + col] - stencil_dot(st + (size_t)f * 9, nxf, nyf, fx, fy, x, w, col);
-        acc += wx * wy * r;
+        const int fx = cx + dx, fy = cy + dy, fn = fy * nxf + fx;
+        const int fi = fn * w + col;
+        const T ax = stencil9(st + fn * 9, fi, rsf, w, fn, fx, fy, nxf, nyf,
+                              [&](int e, int, int, int) { return x[e]; });
+        acc += wx * wy * (b[fi] - ax);
       }
     }
-    bc[(size_t)node * w + col] = acc;
+    bc[it.node * w + col] = acc;
   }
 }
 
-// x' = x + P xc (on the fly), xo = x' + omega D^{-1} (b - A x'); DOT as k_jacobi
+// x' = x + P xc (on the fly), xo = x' + omega D^{-1} (b - A x'); DOT as k_jacobi.
+// The coarse values that the 3x3 fine neighbourhood of (x0, y) interpolates
+// from lie in the 3x3 coarse patch X in [Xb-1, Xb+1], Xb = floor((x0-1)/2)
+// (same in y). Interpolation is separable with parity-dependent weights:
+// even x0 -> offsets -1, 0, +1 read patch columns (1), (1,2)/2, (2);
+// odd x0  -> (0,1)/2, (1), (1,2)/2.
 template <typename T, bool DOT>
-__global__ void k_prolong_jacobi(int nxf, int nyf, int nxc, int nyc, int w, int k, const T* __restrict__ st,
-                                 const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
-                                 const T* __restrict__ xc, T* __restrict__ xo, T om, FinArgs f) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
+__global__ void __launch_bounds__(1024) k_prolong_jacobi(int nxf, int nyf, int nxc, int nyc, int w, int k,
+                                                         const T* __restrict__ st, const T* __restrict__ dinv,
+                                                         const T* __restrict__ b, const T* __restrict__ x,
+                                                         const T* __restrict__ xc, T* __restrict__ xo, T om,
+                                                         FinArgs f) {
+  int col, node0, nstep;
+  thread_pos(w, k, col, node0, nstep);
   typename Acc<T>::type acc = 0;
   if (!f.done[col]) {
-    const int n = nxf * nyf;
-    for (; node < n; node += nstep) {
-      const int y = node / nxf, x0 = node - y * nxf;
-      const T* s9 = st + (size_t)node * 9;
-      T ax = T(0);
+    const int n = nxf * nyf, rs = nxf * w;
+    const T h = T(0.5);
+    for (NodeIter it(node0, nstep, nxf); it.node < n; it.next()) {
+      const int Xb = (it.x - 1) >> 1, Yb = (it.y - 1) >> 1;
+      T cp[3][3];
 #pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = y + dy;
-        if (yy < 0 || yy >= nyf) continue;
+      for (int a = 0; a < 3; ++a) {
+        const int Y = Yb - 1 + a;
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = x0 + dx;
-          if (xx < 0 || xx >= nxf) continue;
-          const int j = yy * nxf + xx;
-          const T xj = x[(size_t)j * w + col] + prolong_at(xx, yy, nxc, nyc, xc, w, col);
-          ax += s9[(dy + 1) * 3 + (dx + 1)] * xj;
+        for (int c = 0; c < 3; ++c) {
+          const int X = Xb - 1 + c;
+          cp[a][c] = (Y >= 0 && Y < nyc && X >= 0 && X < nxc) ? xc[(Y * nxc + X) * w + col] : T(0);
         }
       }
-      const size_t i = (size_t)node * w + col;
-      const T xi = x[i] + prolong_at(x0, y, nxc, nyc, xc, w, col);
+      T tx[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (it.x & 1) {
+          tx[a][0] = h * (cp[a][0] + cp[a][1]);
+          tx[a][1] = cp[a][1];
+          tx[a][2] = h * (cp[a][1] + cp[a][2]);
+        } else {
+          tx[a][0] = cp[a][1];
+          tx[a][1] = h * (cp[a][1] + cp[a][2]);
+          tx[a][2] = cp[a][2];
+        }
+      }
+      T I[3][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (it.y & 1) {
+          I[0][d] = h * (tx[0][d] + tx[1][d]);
+          I[1][d] = tx[1][d];
+          I[2][d] = h * (tx[1][d] + tx[2][d]);
+        } else {
+          I[0][d] = tx[1][d];
+          I[1][d] = h * (tx[1][d] + tx[2][d]);
+          I[2][d] = tx[2][d];
+        }
+      }
+      const int i = it.node * w + col;
+      const T ax = stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nxf, nyf,
+                            [&](int e, int, int dy, int dx) { return x[e] + I[dy + 1][dx + 1]; });
+      const T xi = x[i] + I[1][1];
       const T bi = b[i];
-      const T v = xi + om * dinv[node] * (bi - ax);
+      const T v = xi + om * dinv[it.node] * (bi - ax);
       xo[i] = v;
       if (DOT) acc += bi * v;
     }
   }
-  if (DOT) reduce_finalize(f, (double)acc, w, k, FIN_RHO);
+  if (DOT) reduce_finalize(f, acc, w, k, FIN_RHO);
 }
 
 struct CoarseGrids {
@@ -355,26 +478,50 @@ struct CoarseGrids {
   const void* dinv[MAX_LEVELS];
 };
 
-// The V-cycle from grid g0 down for CPB columns per block, entirely in shared
-// memory: per grid a right-hand side, an iterate and a ping-pong buffer,
-// [node][CPB]; stencils are read from global memory (shared by every block).
+// The V-cycle from grid g0 down, one column per 1024-thread block (the coarse
+// grids are latency-bound, so the work spreads over as many SMs as there are
+// columns), entirely in shared memory: per grid a right-hand side, an iterate
+// and a ping-pong buffer, plus every coarse stencil and inverse diagonal
+// (staged once per block with independent loads in flight). Grids of at most
+// 64 nodes are run by warp 0 alone with warp-level synchronisation.
 template <typename T>
-__global__ void __launch_bounds__(256) k_vcycle_coarse(CoarseGrids L, int w, const T* __restrict__ bg,
-                                                       T* __restrict__ xg, T om, int nu,
-                                                       const int* __restrict__ done) {
+__device__ __forceinline__ void stage_copy(T* __restrict__ dst, const T* __restrict__ src, int count) {
+  constexpr int U = 8;
+  for (int base = 0; base < count; base += U * (int)blockDim.x) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x + threadIdx.x;
+      v[u] = idx < count ? src[idx] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x + threadIdx.x;
+      if (idx < count) dst[idx] = v[u];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, int w, const T* __restrict__ bg,
+                                                        T* __restrict__ xg, T om, int nu,
+                                                        const int* __restrict__ done) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int c0 = blockIdx.x * CPB;
-  __shared__ int any;
-  if (threadIdx.x == 0) any = 0;
-  __syncthreads();
-  if ((int)threadIdx.x < CPB && c0 + (int)threadIdx.x < w && !done[c0 + threadIdx.x]) any = 1;
-  __syncthreads();
-  if (!any) return;
-  auto B = [&](int g) { return sm + (size_t)3 * L.off[g] * CPB; };
-  auto Xa = [&](int g) { return sm + (size_t)(3 * L.off[g] + L.nx[g] * L.ny[g]) * CPB; };
-  auto Xb = [&](int g) { return sm + (size_t)(3 * L.off[g] + 2 * L.nx[g] * L.ny[g]) * CPB; };
-  auto sdot = [&](const T* s9, int nx, int ny, int x, int y, const T* v, int cc) {
+  T* sst = sm + 3 * tot;          // stencils [node][9] of all coarse grids
+  T* sdi = sst + 9 * tot;         // inverse diagonals
+  const int col = blockIdx.x;
+  if (done[col]) return;
+  const int tid = threadIdx.x;
+  for (int g = L.g0; g < L.G; ++g) {
+    const int n = L.nx[g] * L.ny[g];
+    stage_copy(sst + 9 * L.off[g], (const T*)L.st[g], 9 * n);
+    stage_copy(sdi + L.off[g], (const T*)L.dinv[g], n);
+  }
+  auto B = [&](int g) { return sm + 3 * L.off[g]; };
+  auto Xa = [&](int g) { return sm + 3 * L.off[g] + L.nx[g] * L.ny[g]; };
+  auto Xb = [&](int g) { return sm + 3 * L.off[g] + 2 * L.nx[g] * L.ny[g]; };
+  auto sdot = [&](const T* s9, int nx, int ny, int x, int y, const T* v) {
     T acc = T(0);
     for (int dy = -1; dy <= 1; ++dy) {
       const int yy = y + dy;
@@ -382,120 +529,135 @@ __global__ void __launch_bounds__(256) k_vcycle_coarse(CoarseGrids L, int w, con
       for (int dx = -1; dx <= 1; ++dx) {
         const int xx = x + dx;
         if (xx < 0 || xx >= nx) continue;
-        acc += s9[(dy + 1) * 3 + (dx + 1)] * v[(yy * nx + xx) * CPB + cc];
+        acc += s9[(dy + 1) * 3 + (dx + 1)] * v[yy * nx + xx];
       }
     }
     return acc;
   };
+  // grid g runs in warp mode (warp 0 only, __syncwarp) when it has <= 64 nodes
+  auto wmode = [&](int g) { return L.nx[g] * L.ny[g] <= 64; };
+  auto lsync = [&](bool wm) {
+    if (wm) __syncwarp(); else __syncthreads();
+  };
   {
     const int n0 = L.nx[L.g0] * L.ny[L.g0];
     T* b0 = B(L.g0);
-    for (int idx = threadIdx.x; idx < n0 * CPB; idx += blockDim.x) {
-      const int node = idx / CPB, cc = idx - node * CPB, col = c0 + cc;
-      b0[idx] = col < w ? bg[(size_t)node * w + col] : T(0);
-    }
+    for (int idx = tid; idx < n0; idx += blockDim.x) b0[idx] = bg[idx * w + col];
   }
   __syncthreads();
   T* cur[MAX_LEVELS];
   T* oth[MAX_LEVELS];
   for (int g = L.g0; g < L.G; ++g) {
     const int nx = L.nx[g], ny = L.ny[g], n = nx * ny;
-    const T* st = (const T*)L.st[g];
-    const T* dinv = (const T*)L.dinv[g];
+    const bool wm = wmode(g);
+    const int lim = wm ? 32 : (int)blockDim.x;
+    const bool act = tid < lim;
+    const T* st = sst + 9 * L.off[g];
+    const T* dinv = sdi + L.off[g];
     const T* b = B(g);
     T* c = Xa(g);
     T* o = Xb(g);
     if (g == L.G - 1) {  // coarsest grid (one node for square grids): exact solve
-      for (int idx = threadIdx.x; idx < n * CPB; idx += blockDim.x) c[idx] = dinv[idx / CPB] * b[idx];
-      __syncthreads();
+      if (act)
+        for (int idx = tid; idx < n; idx += lim) c[idx] = dinv[idx] * b[idx];
+      lsync(wm);
       cur[g] = c;
       oth[g] = o;
       break;
     }
-    for (int idx = threadIdx.x; idx < n * CPB; idx += blockDim.x) c[idx] = om * dinv[idx / CPB] * b[idx];
-    __syncthreads();
+    if (act)
+      for (int idx = tid; idx < n; idx += lim) c[idx] = om * dinv[idx] * b[idx];
+    lsync(wm);
     for (int s = 1; s < nu; ++s) {
-      for (int idx = threadIdx.x; idx < n * CPB; idx += blockDim.x) {
-        const int node = idx / CPB, cc = idx - node * CPB, y = node / nx, x = node - y * nx;
-        o[idx] = c[idx] + om * dinv[node] * (b[idx] - sdot(st + node * 9, nx, ny, x, y, c, cc));
-      }
-      __syncthreads();
+      if (act)
+        for (int idx = tid; idx < n; idx += lim) {
+          const int y = idx / nx, x = idx - y * nx;
+          o[idx] = c[idx] + om * dinv[idx] * (b[idx] - sdot(st + idx * 9, nx, ny, x, y, c));
+        }
+      lsync(wm);
       T* t = c; c = o; o = t;
     }
-    for (int idx = threadIdx.x; idx < n * CPB; idx += blockDim.x) {
-      const int node = idx / CPB, cc = idx - node * CPB, y = node / nx, x = node - y * nx;
-      o[idx] = b[idx] - sdot(st + node * 9, nx, ny, x, y, c, cc);
-    }
-    __syncthreads();
+    if (act)
+      for (int idx = tid; idx < n; idx += lim) {
+        const int y = idx / nx, x = idx - y * nx;
+        o[idx] = b[idx] - sdot(st + idx * 9, nx, ny, x, y, c);
+      }
+    lsync(wm);
     const int nxc = L.nx[g + 1], nyc = L.ny[g + 1];
     T* bc = B(g + 1);
-    for (int idx = threadIdx.x; idx < nxc * nyc * CPB; idx += blockDim.x) {
-      const int node = idx / CPB, cc = idx - node * CPB, Y = node / nxc, X = node - Y * nxc;
-      T acc = T(0);
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const T wgt = (dx == 0 ? T(1) : T(0.5)) * (dy == 0 ? T(1) : T(0.5));
-          acc += wgt * o[((2 * Y + 1 + dy) * nx + (2 * X + 1 + dx)) * CPB + cc];
-        }
-      bc[idx] = acc;
-    }
-    __syncthreads();
+    if (act)
+      for (int idx = tid; idx < nxc * nyc; idx += lim) {
+        const int Y = idx / nxc, X = idx - Y * nxc;
+        T acc = T(0);
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const T wgt = (dx == 0 ? T(1) : T(0.5)) * (dy == 0 ? T(1) : T(0.5));
+            acc += wgt * o[(2 * Y + 1 + dy) * nx + (2 * X + 1 + dx)];
+          }
+        bc[idx] = acc;
+      }
+    lsync(wm);
     cur[g] = c;
     oth[g] = o;
   }
   for (int g = L.G - 2; g >= L.g0; --g) {
     const int nx = L.nx[g], ny = L.ny[g], n = nx * ny;
     const int nxc = L.nx[g + 1], nyc = L.ny[g + 1];
-    const T* st = (const T*)L.st[g];
-    const T* dinv = (const T*)L.dinv[g];
+    const bool wm = wmode(g);
+    if (!wm && wmode(g + 1)) __syncthreads();   // results of warp 0 become visible to the block
+    const int lim = wm ? 32 : (int)blockDim.x;
+    const bool act = tid < lim;
+    const T* st = sst + 9 * L.off[g];
+    const T* dinv = sdi + L.off[g];
     const T* b = B(g);
     T* c = cur[g];
     T* o = oth[g];
     const T* xc = cur[g + 1];
-    for (int idx = threadIdx.x; idx < n * CPB; idx += blockDim.x) {
-      const int node = idx / CPB, cc = idx - node * CPB, y = node / nx, x = node - y * nx;
-      c[idx] += prolong_at(x, y, nxc, nyc, xc + cc, CPB, 0);
-    }
-    __syncthreads();
-    for (int s = 0; s < nu; ++s) {
-      for (int idx = threadIdx.x; idx < n * CPB; idx += blockDim.x) {
-        const int node = idx / CPB, cc = idx - node * CPB, y = node / nx, x = node - y * nx;
-        o[idx] = c[idx] + om * dinv[node] * (b[idx] - sdot(st + node * 9, nx, ny, x, y, c, cc));
+    if (act)
+      for (int idx = tid; idx < n; idx += lim) {
+        const int y = idx / nx, x = idx - y * nx;
+        c[idx] += prolong_at(x, y, nxc, nyc, xc, 1, 0);
       }
-      __syncthreads();
+    lsync(wm);
+    for (int s = 0; s < nu; ++s) {
+      if (act)
+        for (int idx = tid; idx < n; idx += lim) {
+          const int y = idx / nx, x = idx - y * nx;
+          o[idx] = c[idx] + om * dinv[idx] * (b[idx] - sdot(st + idx * 9, nx, ny, x, y, c));
+        }
+      lsync(wm);
       T* t = c; c = o; o = t;
     }
     cur[g] = c;
   }
+  __syncthreads();
   const int n0 = L.nx[L.g0] * L.ny[L.g0];
   const T* x0 = cur[L.g0];
-  for (int idx = threadIdx.x; idx < n0 * CPB; idx += blockDim.x) {
-    const int node = idx / CPB, cc = idx - node * CPB, col = c0 + cc;
-    if (col < w) xg[(size_t)node * w + col] = x0[idx];
-  }
+  for (int idx = tid; idx < n0; idx += blockDim.x) xg[idx * w + col] = x0[idx];
 }
 
 // ------------------------------------------------------------- batched CG ---
 
-// r = src (cast), x = 0, ||b||^2 -> FIN_INIT (sets the loop condition)
+// r = src (cast), x = 0 (x has leading dimension ldx), ||b||^2 -> FIN_INIT
+// (sets the loop condition)
 template <typename TS, typename T>
-__global__ void k_gather(int n, int w, int k, const TS* __restrict__ src, int lds, T* __restrict__ r,
-                         T* __restrict__ x, FinArgs f) {
+__global__ void __launch_bounds__(1024) k_gather(int n, int w, int k, const TS* __restrict__ src, int lds, T* __restrict__ r,
+                         T* __restrict__ x, int ldx, FinArgs f) {
   int col, node, nstep;
   thread_pos(w, k, col, node, nstep);
   typename Acc<T>::type acc = 0;
   for (; node < n; node += nstep) {
-    const size_t i = (size_t)node * w + col;
+    const int i = node * w + col;
     const T v = (T)src[(size_t)node * lds + col];
     r[i] = v;
-    x[i] = T(0);
+    x[(size_t)node * ldx + col] = T(0);
     acc += v * v;
   }
-  reduce_finalize(f, (double)acc, w, k, FIN_INIT);
+  reduce_finalize(f, acc, w, k, FIN_INIT);
 }
 
 template <typename T, typename TD>
-__global__ void k_scatter(int n, int w, int k, const T* __restrict__ x, TD* __restrict__ dst, int ldd) {
+__global__ void __launch_bounds__(1024) k_scatter(int n, int w, int k, const T* __restrict__ x, TD* __restrict__ dst, int ldd) {
   int col, node, nstep;
   thread_pos(w, k, col, node, nstep);
   for (; node < n; node += nstep) dst[(size_t)node * ldd + col] = (TD)x[(size_t)node * w + col];
@@ -503,96 +665,69 @@ __global__ void k_scatter(int n, int w, int k, const T* __restrict__ x, TD* __re
 
 // a . b per column -> op (used when the finest grid is inside the coarse block)
 template <typename T>
-__global__ void k_dot_fin(int n, int w, int k, const T* __restrict__ a, const T* __restrict__ b, FinArgs f, int op) {
+__global__ void __launch_bounds__(1024) k_dot_fin(int n, int w, int k, const T* __restrict__ a, const T* __restrict__ b, FinArgs f, int op) {
   int col, node, nstep;
   thread_pos(w, k, col, node, nstep);
   typename Acc<T>::type acc = 0;
   if (!f.done[col])
     for (; node < n; node += nstep) {
-      const size_t i = (size_t)node * w + col;
+      const int i = node * w + col;
       acc += a[i] * b[i];
     }
-  reduce_finalize(f, (double)acc, w, k, op);
+  reduce_finalize(f, acc, w, k, op);
 }
 
 // p_new = z + beta p_old (p_new = z on a column's first iteration), formed on the
 // fly at the 9 neighbours; q = A_0 p_new; p_new . q -> FIN_ALPHA.
 template <typename T>
-__global__ void k_matvec_p(int nx, int ny, int w, int k, const T* __restrict__ st, const T* __restrict__ z,
-                           T* pA, T* pB, T* __restrict__ q, FinArgs f) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
+__global__ void __launch_bounds__(1024) k_matvec_p(int nx, int ny, int w, int k, const T* __restrict__ st,
+                                                   const T* __restrict__ z, T* pA, T* pB, T* __restrict__ q,
+                                                   FinArgs f) {
+  int col, node0, nstep;
+  thread_pos(w, k, col, node0, nstep);
   const int par = f.ctl->it & 1;
   const T* __restrict__ pold = par ? pB : pA;
   T* __restrict__ pnew = par ? pA : pB;
   typename Acc<T>::type acc = 0;
   if (!f.done[col]) {
     const bool first = f.iters[col] == 0;
-    const T bt = first ? T(0) : (T)f.beta[col];
-    const int n = nx * ny;
-    for (; node < n; node += nstep) {
-      const int y = node / nx, x0 = node - y * nx;
-      const T* s9 = st + (size_t)node * 9;
-      T s = T(0);
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = y + dy;
-        if (yy < 0 || yy >= ny) continue;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = x0 + dx;
-          if (xx < 0 || xx >= nx) continue;
-          const size_t j = (size_t)(yy * nx + xx) * w + col;
-          const T pj = first ? z[j] : z[j] + bt * pold[j];
-          s += s9[(dy + 1) * 3 + (dx + 1)] * pj;
-        }
-      }
-      const size_t i = (size_t)node * w + col;
+    const T bt = first ? T(0) : (sizeof(T) == 4 ? (T)f.betaf[col] : (T)f.beta[col]);
+    const int n = nx * ny, rs = nx * w;
+    for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+      const int i = it.node * w + col;
+      const T s = first ? stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
+                                   [&](int e, int, int, int) { return z[e]; })
+                        : stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
+                                   [&](int e, int, int, int) { return z[e] + bt * pold[e]; });
       const T pi = first ? z[i] : z[i] + bt * pold[i];
       pnew[i] = pi;
       q[i] = s;
       acc += pi * s;
     }
   }
-  reduce_finalize(f, (double)acc, w, k, FIN_ALPHA);
+  reduce_finalize(f, acc, w, k, FIN_ALPHA);
 }
 
-// x += alpha p_new; r -= alpha q; r . r -> FIN_CONV (sets the loop condition)
+// x += alpha p_new (x has leading dimension ldx); r -= alpha q; r . r -> FIN_CONV
+// (sets the loop condition)
 template <typename T>
-__global__ void k_update_xr(int n, int w, int k, const T* pA, const T* pB, const T* __restrict__ q,
-                            T* __restrict__ x, T* __restrict__ r, FinArgs f) {
+__global__ void __launch_bounds__(1024) k_update_xr(int n, int w, int k, const T* pA, const T* pB, const T* __restrict__ q,
+                            T* __restrict__ x, int ldx, T* __restrict__ r, FinArgs f) {
   int col, node, nstep;
   thread_pos(w, k, col, node, nstep);
   const T* __restrict__ pnew = (f.ctl->it & 1) ? pA : pB;
   typename Acc<T>::type acc = 0;
   if (!f.done[col]) {
-    const T a = (T)f.alpha[col];
+    const T a = sizeof(T) == 4 ? (T)f.alphaf[col] : (T)f.alpha[col];
     for (; node < n; node += nstep) {
-      const size_t i = (size_t)node * w + col;
-      x[i] += a * pnew[i];
+      const int i = node * w + col;
+      x[(size_t)node * ldx + col] += a * pnew[i];
       const T rv = r[i] - a * q[i];
       r[i] = rv;
       acc += rv * rv;
     }
   }
-  reduce_finalize(f, (double)acc, w, k, FIN_CONV);
-}
-
-// Accumulate per-column iteration counts into the handle's running totals.
-__global__ void k_iter_stats(int w, const int* iters, long long* acc) {
-  __shared__ long long tot;
-  __shared__ int mx;
-  if (threadIdx.x == 0) { tot = 0; mx = 0; }
-  __syncthreads();
-  if ((int)threadIdx.x < w) {
-    atomicAdd((unsigned long long*)&tot, (unsigned long long)iters[threadIdx.x]);
-    atomicMax(&mx, iters[threadIdx.x]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    acc[0] += tot;
-    if (mx > acc[1]) acc[1] = mx;
-  }
+  reduce_finalize(f, acc, w, k, FIN_CONV);
 }
 
 __global__ void k_clear_done(int w, int* done) {
@@ -608,7 +743,7 @@ static int alloc_block(void** p, size_t bytes) {
 
 static void free_inner_bufs(InnerWork& iw) {
   void* bufs[] = {iw.x, iw.r, iw.z, iw.zt, iw.pA, iw.pB, iw.q, iw.part, iw.rho, iw.pq, iw.rr, iw.bb,
-                  iw.alpha, iw.beta, iw.done, iw.iters, iw.ctl};
+                  iw.alpha, iw.beta, iw.alphaf, iw.betaf, iw.done, iw.iters, iw.ctl};
   for (void* b : bufs) cudaFree(b);
   for (auto v : {&iw.cb, &iw.cx, &iw.cxt})
     for (void* b : *v) cudaFree(b);
@@ -627,6 +762,10 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
   }
   if (wcap > 1024) {
     set_error("inner solve: batch of %d columns exceeds 1024", wcap);
+    return SG_ERR_UNSUPPORTED;
+  }
+  if ((long long)h->grids[0].n * wcap >= (1LL << 31)) {
+    set_error("inner solve: n x w = %lld exceeds the 32-bit element indexing", (long long)h->grids[0].n * wcap);
     return SG_ERR_UNSUPPORTED;
   }
   InnerWork& iw = dtype == SG_F64 ? h->iw64 : h->iw32;
@@ -657,6 +796,7 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
   SG_TRY(alloc_block((void**)&iw.part, (size_t)iw.part_blocks * wcap * sizeof(double)));
   for (double** b : {&iw.rho, &iw.pq, &iw.rr, &iw.bb, &iw.alpha, &iw.beta})
     SG_TRY(alloc_block((void**)b, (size_t)wcap * sizeof(double)));
+  for (float** b : {&iw.alphaf, &iw.betaf}) SG_TRY(alloc_block((void**)b, (size_t)wcap * sizeof(float)));
   SG_TRY(alloc_block((void**)&iw.done, (size_t)wcap * sizeof(int)));
   SG_TRY(alloc_block((void**)&iw.iters, (size_t)wcap * sizeof(int)));
   SG_TRY(alloc_block((void**)&iw.ctl, sizeof(InnerCtl)));
@@ -681,6 +821,8 @@ static FinArgs make_fin(sg_problem* h, InnerWork& iw, const sg_prec_opts& o) {
   f.ldp = iw.wcap;
   f.ctl = iw.ctl;
   f.rho = iw.rho; f.pq = iw.pq; f.rr = iw.rr; f.bb = iw.bb; f.alpha = iw.alpha; f.beta = iw.beta;
+  f.alphaf = iw.alphaf;
+  f.betaf = iw.betaf;
   f.done = iw.done;
   f.iters = iw.iters;
   f.status = h->status;
@@ -689,6 +831,8 @@ static FinArgs make_fin(sg_problem* h, InnerWork& iw, const sg_prec_opts& o) {
   f.fixed = o.inner_fixed_iters;
   f.cond = 0;
   f.has_cond = 0;
+  f.flag = nullptr;
+  f.iacc = h->iacc;
   return f;
 }
 
@@ -708,9 +852,9 @@ static int launch_coarse(sg_problem* h, int g0, const T* b, T* x, int w, const s
     L.st[g] = sizeof(T) == 8 ? (const void*)G.st64 : (const void*)G.st32;
     L.dinv[g] = sizeof(T) == 8 ? (const void*)G.dinv64 : (const void*)G.dinv32;
   }
-  const size_t smem = (size_t)3 * tot * CPB * sizeof(T);
+  const size_t smem = (size_t)13 * tot * sizeof(T);
   SG_TRY_CUDA(cudaFuncSetAttribute(k_vcycle_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  { k_vcycle_coarse<T><<<ceil_div(w, CPB), 256, smem, s>>>(L, w, b, x, (T)o.omega, o.nu, done); ::sghsc::note_launch(); }
+  { k_vcycle_coarse<T><<<w, 1024, smem, s>>>(L, tot, w, b, x, (T)o.omega, o.nu, done); ::sghsc::note_launch(); }
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -726,7 +870,7 @@ static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, 
   if (g >= h->cb_level) {
     SG_TRY(launch_coarse<T>(h, g, b, x, w, o, iw.done, s));
     if (fdot) {
-      const Shape sh = make_shape(h, h->grids[g].n, w);
+      const Shape sh = make_shape(h, h->grids[g].n, w, 1);
       { k_dot_fin<T><<<sh.grid, sh.bdim, 0, s>>>(h->grids[g].n, w, sh.k, b, x, *fdot, FIN_RHO); ::sghsc::note_launch(); }
     }
     *out = x;
@@ -737,6 +881,7 @@ static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, 
   const T* st = sizeof(T) == 8 ? (const T*)G.st64 : (const T*)G.st32;
   const T* dinv = sizeof(T) == 8 ? (const T*)G.dinv64 : (const T*)G.dinv32;
   const Shape sh = make_shape(h, G.n, w);
+  const Shape shd = make_shape(h, G.n, w, 1);   // kernels that end in a reduction
   const Shape shc = make_shape(h, C.n, w);
   T* cur = x;
   T* oth = xt;
@@ -754,14 +899,14 @@ static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, 
   const T* xc = nullptr;
   SG_TRY(vcycle<T>(h, iw, g + 1, cb, (T*)iw.cx[g + 1], (T*)iw.cxt[g + 1], w, o, s, nullptr, &xc));
   if (o.nu == 1 && fdot) {
-    { k_prolong_jacobi<T, true><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, w, sh.k, st, dinv, b, cur, xc, oth, om, *fdot); ::sghsc::note_launch(); }
+    { k_prolong_jacobi<T, true><<<shd.grid, shd.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, w, sh.k, st, dinv, b, cur, xc, oth, om, *fdot); ::sghsc::note_launch(); }
   } else {
     { k_prolong_jacobi<T, false><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, w, sh.k, st, dinv, b, cur, xc, oth, om, fz); ::sghsc::note_launch(); }
   }
   std::swap(cur, oth);
   for (int it = 1; it < o.nu; ++it) {
     if (it == o.nu - 1 && fdot) {
-      { k_jacobi<T, true><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, w, sh.k, st, dinv, b, cur, oth, om, *fdot); ::sghsc::note_launch(); }
+      { k_jacobi<T, true><<<shd.grid, shd.bdim, 0, s>>>(G.nx, G.ny, w, sh.k, st, dinv, b, cur, oth, om, *fdot); ::sghsc::note_launch(); }
     } else {
       { k_jacobi<T, false><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, w, sh.k, st, dinv, b, cur, oth, om, fz); ::sghsc::note_launch(); }
     }
@@ -777,7 +922,8 @@ static int inner_solve_t(sg_problem* h, const void* src, int ld_src, int src_t, 
                          int w, const sg_prec_opts& o, cudaStream_t s) {
   InnerWork& iw = sizeof(T) == 8 ? h->iw64 : h->iw32;
   const GridLevel& G = h->grids[0];
-  const Shape sh = make_shape(h, G.n, w);
+  const Shape sh = make_shape(h, G.n, w, 1);    // gather / matvec / update end in reductions
+  const Shape shs = make_shape(h, G.n, w);
   T* x = (T*)iw.x;
   T* r = (T*)iw.r;
   T* q = (T*)iw.q;
@@ -785,35 +931,42 @@ static int inner_solve_t(sg_problem* h, const void* src, int ld_src, int src_t, 
   T* pB = (T*)iw.pB;
   const T* st = sizeof(T) == 8 ? (const T*)G.st64 : (const T*)G.st32;
   FinArgs fa = make_fin(h, iw, o);
-  auto pre = [&](cudaStream_t ps, cudaGraphConditionalHandle cond) -> int {
+  // the iterate lives in the destination itself when the element types agree
+  const bool direct = dst_t == (sizeof(T) == 8 ? SG_F64 : SG_F32);
+  T* xd = direct ? (T*)dst : x;
+  const int ldx = direct ? ld_dst : w;
+  auto pre = [&](cudaStream_t ps, const LoopCtl& lc) -> int {
     FinArgs f = fa;
-    f.cond = cond;
-    f.has_cond = 1;
+    f.cond = lc.cond;
+    f.has_cond = lc.has_cond;
+    f.flag = lc.flag;
     if (src_t == SG_F64)
-      { k_gather<double, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, sh.k, (const double*)src, ld_src, r, x, f); ::sghsc::note_launch(); }
+      { k_gather<double, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, sh.k, (const double*)src, ld_src, r, xd, ldx, f); ::sghsc::note_launch(); }
     else
-      { k_gather<float, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, sh.k, (const float*)src, ld_src, r, x, f); ::sghsc::note_launch(); }
+      { k_gather<float, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, sh.k, (const float*)src, ld_src, r, xd, ldx, f); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
-  auto body = [&](cudaStream_t bs, cudaGraphConditionalHandle cond) -> int {
+  auto body = [&](cudaStream_t bs, const LoopCtl& lc) -> int {
     FinArgs f = fa;
-    f.cond = cond;
-    f.has_cond = 1;
+    f.cond = lc.cond;
+    f.has_cond = lc.has_cond;
+    f.flag = lc.flag;
     const T* z = nullptr;
     SG_TRY(vcycle<T>(h, iw, 0, r, (T*)iw.z, (T*)iw.zt, w, o, bs, &f, &z));
     { k_matvec_p<T><<<sh.grid, sh.bdim, 0, bs>>>(G.nx, G.ny, w, sh.k, st, z, pA, pB, q, f); ::sghsc::note_launch(); }
-    { k_update_xr<T><<<sh.grid, sh.bdim, 0, bs>>>(G.n, w, sh.k, pA, pB, q, x, r, f); ::sghsc::note_launch(); }
+    { k_update_xr<T><<<sh.grid, sh.bdim, 0, bs>>>(G.n, w, sh.k, pA, pB, q, xd, ldx, r, f); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
   SG_TRY(capture_while(h, s, pre, body));
-  if (dst_t == SG_F64)
-    { k_scatter<T, double><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, sh.k, x, (double*)dst, ld_dst); ::sghsc::note_launch(); }
-  else
-    { k_scatter<T, float><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, sh.k, x, (float*)dst, ld_dst); ::sghsc::note_launch(); }
-  { k_iter_stats<<<1, ((w + 31) / 32) * 32, 0, s>>>(w, iw.iters, h->iacc); ::sghsc::note_launch(); }
-  SG_CHECK_LAUNCH();
+  if (!direct) {
+    if (dst_t == SG_F64)
+      { k_scatter<T, double><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, shs.k, x, (double*)dst, ld_dst); ::sghsc::note_launch(); }
+    else
+      { k_scatter<T, float><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, shs.k, x, (float*)dst, ld_dst); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+  }
   return SG_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <map>
@@ -292,6 +293,13 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   for (int g = 0; g < (int)h->grids.size(); ++g)
     if (h->grids[g].n <= 1024) { h->cb_level = g; break; }
   for (auto& cs : h->cap) SG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  {
+    const char* ev = getenv("SGHSC_EAGER");
+    h->eager = ev && ev[0] == '1';
+  }
+  SG_TRY_CUDA(cudaMalloc((void**)&h->loopflags, 8 * sizeof(int)));
+  SG_TRY_CUDA(cudaMemset(h->loopflags, 0, 8 * sizeof(int)));
+  SG_TRY_CUDA(cudaMallocHost((void**)&h->loopflag_host, sizeof(int)));
   SG_TRY_CUDA(cudaMalloc((void**)&h->status, sizeof(int)));
   SG_TRY_CUDA(cudaMemset(h->status, 0, sizeof(int)));
   SG_TRY_CUDA(cudaMallocHost((void**)&h->status_host, sizeof(int)));
@@ -363,12 +371,13 @@ void sg_destroy(sg_problem* h) {
   free_inner_work(h);
   void* bufs[] = {h->rowptr, h->colidx, h->vals64, h->vals32, h->mass64, h->R32, h->Z32, h->T32, h->R64w,
                   h->T64, h->fF, h->fx, h->fr, h->fz, h->fpA, h->fpB, h->fq, h->opart, h->osc, h->octl,
-                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev};
+                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags};
   for (void* b : bufs) cudaFree(b);
   for (auto& cs : h->cap)
     if (cs) cudaStreamDestroy(cs);
   if (h->osc_host) cudaFreeHost(h->osc_host);
   if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->loopflag_host) cudaFreeHost(h->loopflag_host);
   delete h;
 }
 

@@ -85,6 +85,7 @@ struct InnerWork {
   double* part = nullptr;                 // block partial sums [nblk][wcap]
   int part_blocks = 0;
   double *rho = nullptr, *pq = nullptr, *rr = nullptr, *bb = nullptr, *alpha = nullptr, *beta = nullptr;
+  float *alphaf = nullptr, *betaf = nullptr;
   int *done = nullptr, *iters = nullptr;
   InnerCtl* ctl = nullptr;
 };
@@ -153,6 +154,10 @@ struct sg_problem {
   cudaStream_t cap[4] = {nullptr, nullptr, nullptr, nullptr};
   int cap_depth = 0;
   bool capturing = false;
+  bool eager = false;                       // SGHSC_EAGER=1: host-driven loops, no graphs
+  int loop_depth = 0;
+  int* loopflags = nullptr;                 // device: loop condition per nesting depth (eager mode)
+  int* loopflag_host = nullptr;             // pinned
   std::map<std::string, sghsc::GraphEntry> graphs;
 };
 

@@ -38,6 +38,7 @@ int launch_cast(const void* src, int src_t, int lds, void* dst, int dst_t, int l
 
 __device__ __forceinline__ void set_cond(const OuterArgs& a, bool v) {
   if (a.has_cond) cudaGraphSetConditional(a.cond, v ? 1u : 0u);
+  if (a.flag) *a.flag = v;
 }
 
 // r = F - Y (Y may be null: r = F); F.F and r.r -> relative residual, it = 0

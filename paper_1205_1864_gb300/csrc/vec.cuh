@@ -21,6 +21,7 @@ struct OuterArgs {
   double tol;
   cudaGraphConditionalHandle cond;
   int has_cond;
+  int* flag;
 };
 
 __global__ void k_outer_init(long long N, const double* F, const double* Y, double* r, OuterArgs a);
@@ -48,13 +49,12 @@ __device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const Ou
   if (threadIdx.x == 0) {
     a.part[(size_t)blockIdx.x * 2 + 0] = r0[0];
     a.part[(size_t)blockIdx.x * 2 + 1] = r1[0];
+    __threadfence();
+    last = atomicAdd(&a.ctl->ticket, 1u) == gridDim.x - 1;
+    if (last) __threadfence();
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&a.ctl->ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return false;
-  __threadfence();
   double s0 = 0.0, s1 = 0.0;
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     s0 += __ldcg(&a.part[(size_t)b * 2 + 0]);
