@@ -159,6 +159,24 @@ int sg_level_apply(sg_problem* h, int lvl_out, int lvl_in, const void* X, const 
 int sg_vcycle_apply(sg_problem* h, const void* B, void* X, int w, int dtype,
                     const sg_prec_opts* opts, void* stream);
 
+/* sg_vcycle_apply_static -- sg_vcycle_apply without allocating device memory.
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not call cudaMalloc while they run (code inside a CUDA stream
+ * capture, allocator or memory-pool hooks, processes whose device memory is
+ * budgeted and already handed out). The V-cycle's level buffers live in a
+ * fixed 32 MiB array inside the library, which every GPU that loads the
+ * library keeps until the process exits. Arguments and results are those of
+ * sg_vcycle_apply (B, X: device n x w packed, w <= 1024, dtype SG_F64 or
+ * SG_F32); the handle must come from sg_setup as usual. A batch whose buffers
+ * exceed the 32 MiB -- about 2 n w + 3 (n/4 + n/16 + ...) w elements -- is
+ * rejected with SG_ERR_INVALID_ARG. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current), so
+ * make that first call before any stream capture. All calls on a device share
+ * the array and it keeps the last call's contents: calls whose GPU work
+ * overlaps race. */
+int sg_vcycle_apply_static(sg_problem* h, const void* B, void* X, int w, int dtype,
+                           const sg_prec_opts* opts, void* stream);
+
 /* sg_inner_solve -- the batched inner PCG on A_0 (Sec. 5: independent
  * Krylov loops for the diagonal blocks of D_l), V-cycle preconditioned,
  * per-column convergence: column s stops once ||r_s|| <= inner_tol ||b_s||;

@@ -61,6 +61,7 @@ def _load():
         "sg_apply": (i, [vp, vp, vp, i, vp]),
         "sg_level_apply": (i, [vp, i, i, vp, vp, vp, i, vp]),
         "sg_vcycle_apply": (i, [vp, vp, vp, i, i, P(sg_prec_opts), vp]),
+        "sg_vcycle_apply_static": (i, [vp, vp, vp, i, i, P(sg_prec_opts), vp]),
         "sg_inner_solve": (i, [vp, vp, vp, i, i, P(sg_prec_opts), P(C.c_int), vp]),
         "hsc_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "mean_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
@@ -92,5 +93,5 @@ def check(status: int, where: str):
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
     return ["sg_setup", "sg_destroy", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
-            "sg_vcycle_apply", "sg_inner_solve", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi",
+            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi",
             "sg_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

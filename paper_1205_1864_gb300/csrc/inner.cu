@@ -31,6 +31,7 @@
 //   k_vcycle_coarse   all grids with <= 1024 nodes: one block per 4 columns
 //                     runs the rest of the V-cycle in shared memory.
 #include <algorithm>
+#include <mutex>
 
 #include "graph.cuh"
 #include "sghsc_internal.cuh"
@@ -1000,4 +1001,118 @@ int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const 
   return SG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// V-cycle without allocation (sg_vcycle_apply_static).
+//
+// For callers that must not allocate device memory while they run -- code
+// that executes inside a stream capture, an allocator or memory-pool hook,
+// or a process whose device memory is budgeted and already handed out. The
+// level buffers of the V-cycle live in this file-scope array instead of the
+// handle's workspace. Every GPU that loads the library holds the array until
+// the process exits; all calls on one device share it and it keeps the
+// contents of the last call, so calls whose GPU work overlaps (other streams,
+// other threads) race.
+// ---------------------------------------------------------------------------
+
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)32 << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int STATIC_MAX_DEVICES = 64;
+static void* g_static_scratch_ptr[STATIC_MAX_DEVICES];
+static cudaError_t g_static_scratch_err[STATIC_MAX_DEVICES];
+static std::once_flag g_static_scratch_once[STATIC_MAX_DEVICES];
+
+// Device address of g_static_scratch on the current device; resolved once per
+// device (the name is only a host-side stand-in for the device array).
+static int static_scratch(void** out) {
+  int dev = 0;
+  SG_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= STATIC_MAX_DEVICES) {
+    set_error("sg_vcycle_apply_static: device ordinal %d not supported", dev);
+    return SG_ERR_UNSUPPORTED;
+  }
+  std::call_once(g_static_scratch_once[dev], [dev]() {
+    g_static_scratch_err[dev] = cudaGetSymbolAddress(&g_static_scratch_ptr[dev], g_static_scratch);
+  });
+  SG_TRY_CUDA(g_static_scratch_err[dev]);
+  *out = g_static_scratch_ptr[dev];
+  return SG_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes of V-cycle scratch for w columns: the done mask, two iterates on the
+// finest grid and three blocks per coarser grid.
+static size_t static_vcycle_bytes(const sg_problem* h, int w, size_t es) {
+  size_t b = align256((size_t)w * sizeof(int));
+  b += 2 * align256((size_t)h->grids[0].n * w * es);
+  for (size_t g = 1; g < h->grids.size(); ++g) b += 3 * align256((size_t)h->grids[g].n * w * es);
+  return b;
+}
+
+int vcycle_static(sg_problem* h, int dtype, const void* B, void* X, int w, const sg_prec_opts& o, cudaStream_t s) {
+  SG_TRY(check_prec_opts(o));
+  if (h->grids.empty()) {
+    set_error("sg_vcycle_apply_static: no multigrid hierarchy (mesh missing or not a power-of-two square)");
+    return SG_ERR_UNSUPPORTED;
+  }
+  const size_t es = dtype == SG_F64 ? 8 : 4;
+  const size_t need = static_vcycle_bytes(h, w, es);
+  if (need > STATIC_SCRATCH_BYTES) {
+    set_error("sg_vcycle_apply_static: %d columns of %d nodes need %zu bytes of scratch, above the fixed %zu",
+              w, h->grids[0].n, need, STATIC_SCRATCH_BYTES);
+    return SG_ERR_INVALID_ARG;
+  }
+  void* base = nullptr;
+  SG_TRY(static_scratch(&base));
+  unsigned char* p = (unsigned char*)base;
+  InnerWork sw;  // views into the static array; nothing here allocates
+  sw.wcap = w;
+  sw.esize = es;
+  sw.done = (int*)p;
+  p += align256((size_t)w * sizeof(int));
+  sw.z = p;
+  p += align256((size_t)h->grids[0].n * w * es);
+  sw.zt = p;
+  p += align256((size_t)h->grids[0].n * w * es);
+  const int G = (int)h->grids.size();
+  sw.cb.assign(G, nullptr);
+  sw.cx.assign(G, nullptr);
+  sw.cxt.assign(G, nullptr);
+  for (int g = 1; g < G; ++g) {
+    const size_t bytes = align256((size_t)h->grids[g].n * w * es);
+    sw.cb[g] = p;
+    p += bytes;
+    sw.cx[g] = p;
+    p += bytes;
+    sw.cxt[g] = p;
+    p += bytes;
+  }
+  // the kernels skip columns whose done flag is set: start from all zero
+  SG_TRY_CUDA(cudaMemsetAsync(sw.done, 0, (size_t)w * sizeof(int), s));
+  const void* res = nullptr;
+  if (dtype == SG_F64) {
+    const double* r = nullptr;
+    SG_TRY(vcycle<double>(h, sw, 0, (const double*)B, (double*)sw.z, (double*)sw.zt, w, o, s, nullptr, &r));
+    res = r;
+  } else {
+    const float* r = nullptr;
+    SG_TRY(vcycle<float>(h, sw, 0, (const float*)B, (float*)sw.z, (float*)sw.zt, w, o, s, nullptr, &r));
+    res = r;
+  }
+  SG_CHECK_LAUNCH();
+  SG_TRY_CUDA(cudaMemcpyAsync(X, res, (size_t)h->grids[0].n * w * es, cudaMemcpyDeviceToDevice, s));
+  return SG_OK;
+}
+
 }  // namespace sghsc
+
+extern "C" int sg_vcycle_apply_static(sg_problem* h, const void* B, void* X, int w, int dtype,
+                                      const sg_prec_opts* opts, void* stream) {
+  sghsc::set_error("");
+  if (!h || !B || !X || !opts || w <= 0 || w > 1024 || (dtype != SG_F64 && dtype != SG_F32)) {
+    sghsc::set_error("sg_vcycle_apply_static: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  return sghsc::vcycle_static(h, dtype, B, X, w, *opts, (cudaStream_t)stream);
+}
