@@ -130,6 +130,13 @@ int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz,
 
 void sg_destroy(sg_problem* h);
 
+/* sg_set_scales -- A_k := scale[k] * A_k(as given to sg_setup), k = 0..M, for
+ * parameterised KL matrices (A_0 = a_mean L_h, A_k = sigma s_k Phi_k): one
+ * handle then serves every parameter set. scale: host double[M+1], finite,
+ * scale[0] > 0 when the multigrid hierarchy exists (it is rescaled too).
+ * Synchronises the device. */
+int sg_set_scales(sg_problem* h, const double* scale);
+
 /* Sizes of a handle (host outputs, any may be NULL). */
 int sg_problem_dims(const sg_problem* h, int* n, int* P, int* M, int* p, int* nnz);
 

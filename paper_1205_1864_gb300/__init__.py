@@ -27,6 +27,7 @@ from ._lib import (SG_F32, SG_F64, SG_HERMITE, SG_LEGENDRE, SG_PREC_HSC, SG_PREC
 __all__ = [
     "SGProblem", "sg_setup", "sg_apply", "sg_level_apply", "sg_vcycle_apply", "sg_inner_solve",
     "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_qoi_grad", "prec_opts", "solve_opts",
+    "sg_set_scales", "SGQoI", "kl_scales", "kl_chain_weights", "sg_qoi_value_and_grad_batch",
     "SGError", "SG_F32", "SG_F64", "SG_PREC_HSC", "SG_PREC_MEAN", "SG_PREC_NONE", "SG_LEGENDRE", "SG_HERMITE",
 ]
 
@@ -223,3 +224,79 @@ def sg_qoi_grad(h: SGProblem, U: torch.Tensor, Lam: torch.Tensor, W: np.ndarray)
     check(_lib.LIB.sg_qoi_grad(h.h, _ptr(U), _ptr(Lam), nparam, W.ctypes.data_as(C.POINTER(C.c_double)),
                                _ptr(grad), _ptr(hk), _stream()), "sg_qoi_grad")
     return grad, hk
+
+
+def sg_set_scales(h: SGProblem, scale) -> None:
+    """``A_k := scale[k] * A_k`` (relative to the matrices given to sg_setup)."""
+    sc = np.ascontiguousarray(scale, dtype=np.float64)
+    if sc.shape != (h.M + 1,):
+        raise ValueError(f"need M+1 = {h.M + 1} scales")
+    check(_lib.LIB.sg_set_scales(h.h, sc.ctypes.data_as(C.POINTER(C.c_double))), "sg_set_scales")
+
+
+# ---------------------------------------------------------------------------
+# Quantity of interest Q = E[int u^2] and its adjoint gradient (K7)
+# ---------------------------------------------------------------------------
+
+def kl_scales(theta) -> np.ndarray:
+    """Scales of A_0..A_M for theta = (a_mean, sigma, s_1..s_M), relative to
+    matrices assembled with a_mean = 1, sigma = 1, s_k = 1: A_0 = a_mean L_h,
+    A_k = sigma s_k Phi_k."""
+    t = np.asarray(theta, dtype=np.float64)
+    return np.concatenate([[t[0]], t[1] * t[2:]])
+
+
+def kl_chain_weights(theta) -> np.ndarray:
+    """W[t][k] = -d log(scale_k) / d theta_t, so that
+    dQ/dtheta_t = sum_k W[t][k] <Lam, A_k U G_k^T>."""
+    t = np.asarray(theta, dtype=np.float64)
+    M = t.shape[0] - 2
+    W = np.zeros((M + 2, M + 1))
+    W[0, 0] = -1.0 / t[0]
+    W[1, 1:] = -1.0 / t[1]
+    for k in range(M):
+        W[2 + k, 1 + k] = -1.0 / t[2 + k]
+    return W
+
+
+class SGQoI(torch.autograd.Function):
+    """Q(theta) = sum_j u_j^T M_h u_j with (sum_k G_k (x) A_k(theta)) u = f.
+
+    Forward: one preconditioned solve and the mass contraction. Backward: the
+    operator is symmetric, so the adjoint Lam solves the same system with the
+    right-hand side dQ/du = 2 (M_h (x) I) u; the gradient is the fused K7
+    contraction sum_k W[t][k] <Lam, A_k U G_k^T>. The handle must hold the
+    unit-parameter matrices (a_mean = 1, sigma = 1, s_k = 1)."""
+
+    @staticmethod
+    def forward(ctx, theta, h, F, opts):
+        th = theta.detach().double().cpu().numpy()
+        sg_set_scales(h, kl_scales(th))
+        U, _ = sg_solve(h, F, opts)
+        q, dq = sg_qoi(h, U)
+        ctx.h, ctx.opts, ctx.th = h, opts, th
+        ctx.save_for_backward(U, dq)
+        return q[0].to(theta.dtype)
+
+    @staticmethod
+    def backward(ctx, gQ):
+        U, dq = ctx.saved_tensors
+        h = ctx.h
+        sg_set_scales(h, kl_scales(ctx.th))
+        Lam, _ = sg_solve(h, dq, ctx.opts)
+        grad, _ = sg_qoi_grad(h, U, Lam, kl_chain_weights(ctx.th))
+        return (gQ.to(grad.dtype) * grad).to(gQ.dtype), None, None, None
+
+
+def sg_qoi_value_and_grad_batch(h: SGProblem, thetas, F: torch.Tensor, opts=None):
+    """Q and dQ/dtheta for a batch of parameter sets (rows of ``thetas``),
+    one forward and one adjoint solve per set on the same handle."""
+    o = opts or solve_opts()
+    out_q, out_g = [], []
+    for th in np.asarray(thetas, dtype=np.float64):
+        t = torch.tensor(th, dtype=torch.float64, device=F.device, requires_grad=True)
+        q = SGQoI.apply(t, h, F, o)
+        q.backward()
+        out_q.append(q.detach())
+        out_g.append(t.grad.detach())
+    return torch.stack(out_q), torch.stack(out_g)

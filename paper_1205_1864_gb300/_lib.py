@@ -56,6 +56,7 @@ def _load():
     sig = {
         "sg_setup": (i, [P(sg_mesh), i, i, i, i, i, P(C.c_int), P(C.c_int), P(C.c_double), P(C.c_double), P(vp)]),
         "sg_destroy": (None, [vp]),
+        "sg_set_scales": (i, [vp, P(C.c_double)]),
         "sg_problem_dims": (i, [vp, P(i), P(i), P(i), P(i), P(i)]),
         "sg_chaos_table": (i, [vp, P(C.c_int), P(C.c_int)]),
         "sg_apply": (i, [vp, vp, vp, i, vp]),
@@ -92,6 +93,6 @@ def check(status: int, where: str):
 
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
-    return ["sg_setup", "sg_destroy", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
+    return ["sg_setup", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
             "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi",
             "sg_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

@@ -154,6 +154,7 @@ static void galerkin_coarsen(int nx, int ny, const std::vector<double>& st, int 
 }
 
 static int upload_grid(GridLevel& g, const std::vector<double>& st) {
+  SG_TRY(upload(&g.st_base, st.data(), st.size()));
   std::vector<float> st32(st.begin(), st.end());
   std::vector<double> dinv(g.n);
   for (int i = 0; i < g.n; ++i) dinv[i] = 1.0 / st[(size_t)i * 9 + 4];
@@ -244,6 +245,9 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   SG_TRY(upload(&h->rowptr, rowptr, (size_t)n + 1));
   SG_TRY(upload(&h->colidx, colidx, (size_t)nnz));
   SG_TRY(upload(&h->vals64, vals, nv));
+  SG_TRY(upload(&h->vals_base, vals, nv));
+  h->scales.assign(M + 1, 1.0);
+  SG_TRY(upload(&h->scales_dev, h->scales.data(), h->scales.size()));
   {
     std::vector<float> v32(vals, vals + nv);
     SG_TRY(upload(&h->vals32, v32.data(), nv));
@@ -308,11 +312,63 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   return SG_OK;
 }
 
+// vals = base * scale[k] for every nonzero (FP64 and FP32 copies)
+__global__ void k_scale_vals(long long count, int M1, const double* __restrict__ base, const double* __restrict__ scale,
+                             double* __restrict__ v64, float* __restrict__ v32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const double v = base[i] * scale[i % M1];
+    v64[i] = v;
+    v32[i] = (float)v;
+  }
+}
+
+// multigrid stencils of s * A_0: st = s * base, dinv = 1 / (s * base_centre)
+__global__ void k_scale_grid(int n, const double* __restrict__ base, double s, double* __restrict__ st64,
+                             float* __restrict__ st32, double* __restrict__ dinv64, float* __restrict__ dinv32) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * 9; i += gridDim.x * blockDim.x) {
+    const double v = s * base[i];
+    st64[i] = v;
+    st32[i] = (float)v;
+    if (i % 9 == 4) {
+      dinv64[i / 9] = 1.0 / v;
+      dinv32[i / 9] = (float)(1.0 / v);
+    }
+  }
+}
+
 }  // namespace sghsc
 
 using namespace sghsc;
 
 extern "C" {
+
+int sg_set_scales(sg_problem* h, const double* scale) {
+  set_error("");
+  if (!h || !scale) {
+    set_error("sg_set_scales: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k <= h->M; ++k)
+    if (!std::isfinite(scale[k])) {
+      set_error("sg_set_scales: non-finite scale %d", k);
+      return SG_ERR_INVALID_ARG;
+    }
+  if (!(scale[0] > 0.0) && !h->grids.empty()) {
+    set_error("sg_set_scales: the mean matrix needs a positive scale");
+    return SG_ERR_INVALID_ARG;
+  }
+  SG_TRY_CUDA(cudaDeviceSynchronize());   // no solve may be reading the values
+  h->scales.assign(scale, scale + h->M + 1);
+  SG_TRY_CUDA(cudaMemcpy(h->scales_dev, scale, (h->M + 1) * sizeof(double), cudaMemcpyHostToDevice));
+  const long long count = (long long)h->nnz * (h->M + 1);
+  { k_scale_vals<<<(int)std::min<long long>((count + 255) / 256, 4096), 256>>>(count, h->M + 1, h->vals_base, h->scales_dev, h->vals64, h->vals32); ::sghsc::note_launch(); }
+  for (auto& g : h->grids)
+    { k_scale_grid<<<std::min((g.n * 9 + 255) / 256, 4096), 256>>>(g.n, g.st_base, scale[0], g.st64, g.st32, g.dinv64, g.dinv32); ::sghsc::note_launch(); }
+  SG_TRY_CUDA(cudaGetLastError());
+  SG_TRY_CUDA(cudaDeviceSynchronize());
+  return SG_OK;
+}
+
 
 const char* sg_last_error(void) { return sghsc::g_err; }
 
@@ -364,14 +420,14 @@ void sg_destroy(sg_problem* h) {
   for (auto& e : h->pre) free_edges(e);
   for (auto& e : h->post) free_edges(e);
   for (auto& g : h->grids) {
-    cudaFree(g.st64); cudaFree(g.st32); cudaFree(g.dinv64); cudaFree(g.dinv32);
+    cudaFree(g.st_base); cudaFree(g.st64); cudaFree(g.st32); cudaFree(g.dinv64); cudaFree(g.dinv32);
   }
   if (h->cap[0]) cudaDeviceSynchronize();
   clear_graphs(h);
   free_inner_work(h);
   void* bufs[] = {h->rowptr, h->colidx, h->vals64, h->vals32, h->mass64, h->R32, h->Z32, h->T32, h->R64w,
                   h->T64, h->fF, h->fx, h->fr, h->fz, h->fpA, h->fpB, h->fq, h->opart, h->osc, h->octl,
-                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags};
+                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev};
   for (void* b : bufs) cudaFree(b);
   for (auto& cs : h->cap)
     if (cs) cudaStreamDestroy(cs);

@@ -61,6 +61,7 @@ struct EdgeList {
 // neighbour is outside the interior.
 struct GridLevel {
   int nx = 0, ny = 0, n = 0;
+  double* st_base = nullptr;   // stencil of A_0 as given to sg_setup (scale 1)
   double* st64 = nullptr;
   float* st32 = nullptr;
   double* dinv64 = nullptr;
@@ -117,6 +118,9 @@ struct sg_problem {
   int* colidx = nullptr;
   double* vals64 = nullptr;
   float* vals32 = nullptr;
+  double* vals_base = nullptr;        // [nnz][M+1] as given to sg_setup (scales 1)
+  double* scales_dev = nullptr;       // current scale of each A_k
+  std::vector<double> scales;         // host copy
   double* mass64 = nullptr;
   int max_row_nnz = 0;
   // G couplings: all edges (for the full operator) and per adjacent level pair

@@ -37,7 +37,7 @@ from scipy.optimize import brentq
 
 __all__ = [
     "kl_1d", "kl_2d", "Problem", "make_problem", "make_rhs", "random_block",
-    "CONFIGS", "draw_batch_configs", "draw_grad_params", "chaos_count",
+    "CONFIGS", "draw_batch_configs", "draw_grad_params", "chaos_count", "make_unit_problem", "theta_of",
 ]
 
 
@@ -238,6 +238,20 @@ def make_problem(ne: int, M: int, sigma: float, corr_len: float, a_mean: float =
     f0 = np.full(n, h * h)
     return Problem(ne=ne, M=M, sigma=sigma, corr_len=corr_len, a_mean=a_mean, sqrt_lambda=s,
                    rowptr=rowptr, colidx=colidx, vals=vals, mass=mass[:, 0].copy(), f0=f0)
+
+
+def make_unit_problem(ne: int, M: int, corr_len: float) -> Problem:
+    """KL matrices with unit parameters: A_0 = L_h (a_mean = 1) and
+    A_k = Phi_k (sigma = 1, s_k = 1); a parameter set theta = (a_mean, sigma,
+    s_1..s_M) then scales them as A_0 = a_mean L_h, A_k = sigma s_k Phi_k."""
+    kl = kl_2d(corr_len, M) if M > 0 else []
+    inv = [1.0 / math.sqrt(lam) for lam, _, _ in kl]
+    return make_problem(ne, M, 1.0, corr_len, a_mean=1.0, sqrt_lambda_scale=inv if M > 0 else None)
+
+
+def theta_of(prob: Problem) -> np.ndarray:
+    """theta = (a_mean, sigma, s_1..s_M) of an assembled problem."""
+    return np.concatenate([[prob.a_mean, prob.sigma], prob.sqrt_lambda])
 
 
 def chaos_count(M: int, p: int) -> int:
