@@ -40,6 +40,8 @@ WORKLOADS = {
     "cfg1": dict(name="cfg1_fp64_16x16_M3_p3", **S.CONFIGS["cfg1_fp64_16x16_M3_p3"]),
     "cfg4": dict(name="cfg4_64x64_M4_p3", **S.CONFIGS["cfg4_grad_64x64_M4_p3"]),
     "cfg5": dict(name="cfg5_large_512x512_M10_p4", **S.CONFIGS["cfg5_large_512x512_M10_p4"]),
+    # 64 independent systems (mesh, M, p, sigma, L drawn per system), one graph launch
+    "cfg3": dict(name="cfg3_batch64_mixed", batch=True, count=64, seed=1864),
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -284,6 +286,177 @@ def run_ours(args, rank, world, dev):
     return out
 
 
+def _hsc_opts(L, check=0):
+    return L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=1e-2),
+                        precond=L.SG_PREC_HSC, tol=1e-8, maxit=500, check_true_residual=check)
+
+
+def _events_time(fn, stream, flush):
+    import torch
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def run_batch(args, rank, world, dev):
+    """The batched workload: each rank solves its share of the 64 seeded
+    systems (longest-processing-time split, no data-path collective) with one
+    graph launch per step; the SG-product block size of every system is picked
+    by the autotuner first."""
+    import torch
+
+    import paper_1205_1864_gb300 as L
+    from paper_1205_1864_gb300 import shard
+    cfg = WORKLOADS[args.workload]
+    cfgs = S.draw_batch_configs(cfg["count"], seed=cfg["seed"])
+    costs = [shard.system_cost(c["ne"], c["M"], c["p"]) for c in cfgs]
+    mine = shard.my_systems(costs, rank, world)
+    t0 = time.time()
+    probs, hs, Fs, tuned = [], [], [], []
+    for i in mine:
+        c = cfgs[i]
+        prob = S.make_problem(c["ne"], c["M"], c["sigma"], c["corr_len"])
+        h = L.SGProblem.from_inputs(prob, c["p"])
+        tuned.append(L.sg_autotune(h))
+        probs.append(prob)
+        hs.append(h)
+        Fs.append(torch.tensor(S.make_rhs(prob, c["p"]), dtype=torch.float64, device=dev))
+    setup_s = time.time() - t0
+    Us = [torch.empty_like(F) for F in Fs]
+    batch = L.SGBatch(hs)
+    opts = _hsc_opts(L)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    unknowns = sum(h.n * h.P for h in hs)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ts, last = [], None
+        for _ in range(steps):
+            t, last = _events_time(fn, stream, flush)
+            ts.append(t)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return ts, last
+
+    solve_batch = lambda: batch.solve(Fs, opts, Us)[1]
+    if args.profile:
+        ts, st = timed(solve_batch, args.steps, args.warmup)
+        return {"profile": True, "workload": cfg["name"], "ms": float(np.mean(ts)),
+                "iterations": [s.iterations for s in st]}
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        ts, st = timed(solve_batch, args.steps, args.warmup)
+    ms = shard.max_over_ranks(float(np.mean(ts)), device=dev)
+    # validation (untimed): the true FP64 residual of every system
+    _, st_true = batch.solve(Fs, _hsc_opts(L, check=1), Us)
+    # comparator: the same systems one sg_solve (one graph launch) after another
+    seq = lambda: [L.sg_solve(h, F, opts, U)[1] for h, F, U in zip(hs, Fs, Us)]
+    ts_seq, _ = timed(seq, max(1, min(args.steps, 3)), 1)
+    ms_seq = float(np.mean(ts_seq))
+    # kernels per step, counted on eager twins of each handle (same kernels, host-driven loops)
+    launches = 0
+    for prob, i in zip(probs, mine):
+        os.environ["SGHSC_EAGER"] = "1"
+        he = L.SGProblem.from_inputs(prob, cfgs[i]["p"])
+        os.environ.pop("SGHSC_EAGER")
+        L.sg_autotune(he)
+        F = Fs[mine.index(i)]
+        L.sg_solve(he, F, opts)
+        l0 = L._lib.LIB.sg_kernel_launches()
+        L.sg_solve(he, F, opts)
+        launches += L._lib.LIB.sg_kernel_launches() - l0
+        he.close()
+    # K1 roofline on the largest system of this rank
+    big = max(range(len(hs)), key=lambda j: hs[j].n * hs[j].P)
+    hb = hs[big]
+    Ut = torch.tensor(S.random_block(hb.n, hb.P, seed=1205), dtype=torch.float64, device=dev)
+    Yt = torch.empty_like(Ut)
+    for _ in range(3):
+        L.sg_apply(hb, Ut, Yt)
+    k1 = float(np.mean([_events_time(lambda: L.sg_apply(hb, Ut, Yt), stream, flush)[0] for _ in range(20)]))
+    M_b, p_b = hb.M, cfgs[mine[big]]["p"]
+    fl = sg_matvec_flops(hb.nnz, hb.P, int(2 * M_b * math.comb(M_b + p_b - 1, M_b)))
+    roofline = {"kernel": f"k_block_matvec<double> (K1 FP64 SG product) on the largest system (n={hb.n}, P={hb.P})",
+                "bound": "alu", "achieved": fl / k1 / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (fl / k1 / 1e9) / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
+    # end to end through the public API: host (pinned) right-hand sides in, solutions out
+    F_host = [F.cpu().pin_memory() for F in Fs]
+    U_host = [torch.empty_like(F).pin_memory() for F in F_host]
+    e2e_t = []
+    for k in range(max(1, min(args.steps, 3)) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        Fd = [F.to(dev, non_blocking=True) for F in F_host]
+        Ud, _ = batch.solve(Fd, opts)
+        for a, b in zip(U_host, Ud):
+            a.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_t.append((time.perf_counter() - t_a) * 1e3)
+    e2e_ms = shard.max_over_ranks(float(np.mean(e2e_t)), device=dev)
+    nbytes = sum(F.numel() * 8 for F in F_host)
+    out = {
+        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f64 outer / f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
+        "config": {"workload": cfg["name"], "systems": len(cfgs), "systems_this_rank": len(mine),
+                   "unknowns_this_rank": unknowns, "draw_seed": cfg["seed"], "tol": 1e-8, "inner_tol": 1e-2,
+                   "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "parallelism": f"systems split over {world} ranks" if world > 1 else "single GPU"},
+        "batch": {"ms": ms, "step_ms": ts, "iterations": [s.iterations for s in st],
+                  "status": [s.status for s in st], "max_true_rel_res": max(s.true_rel_res for s in st_true),
+                  "autotuned_threads_f64_f32": tuned, "sequential_ms": ms_seq,
+                  "speedup_batch_vs_sequential": ms_seq / float(np.mean(ts))},
+        "roofline": roofline,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)},
+        "gpu_launches": int(launches),
+        "gpu_launches_note": "libsghsc kernels per batch step (launch counter on eager twins of every handle; "
+                             "the timed step replays them as one CUDA graph)",
+        "clocks": clk.summary(),
+        "setup_s": setup_s,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batch(cfgs, [s.iterations for s in st], budget_s=args.cpu_budget)
+    batch.close()
+    return out
+
+
+def cpu_baseline_batch(cfgs, iterations, budget_s=20.0):
+    """The oracle on a bounded sample of the batch: per mesh size, the first
+    system of that size in draw order, timed for one outer HSC-FCG iteration;
+    every system's full solve is then estimated from its class's time per unit
+    of cost, times its own cost and GPU iteration count."""
+    from paper_1205_1864_gb300 import shard
+    costs = [shard.system_cost(c["ne"], c["M"], c["p"]) for c in cfgs]
+    rate, sampled = {}, []
+    t0 = time.perf_counter()
+    for ne in sorted({c["ne"] for c in cfgs}):
+        i = next(j for j, c in enumerate(cfgs) if c["ne"] == ne)
+        c = cfgs[i]
+        cb = cpu_baseline(dict(name=f"system {i}", **c), iterations=1, budget_s=budget_s / 4,
+                          prob=S.make_problem(c["ne"], c["M"], c["sigma"], c["corr_len"]))
+        rate[ne] = cb["value"] / costs[i]
+        sampled.append(f"#{i} ({ne}x{ne}, M={c['M']}, p={c['p']}): {cb['value']:.0f} ms/iteration")
+        cores = cb["cores"]
+    value = sum(rate[c["ne"]] * costs[j] * max(iterations[j], 1) for j, c in enumerate(cfgs))
+    return {"value": value, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": "one outer HSC-FCG iteration of the FP64 oracle per mesh size (" + "; ".join(sampled) +
+                      "), scaled per system by cost and GPU iteration count to all systems",
+            "wall_s": time.perf_counter() - t0}
+
+
 def cpu_baseline(cfg, iterations, budget_s=20.0, prob=None):
     """The FP64 oracle (exact inner solves) timed on the host on a bounded
     sample: as many outer HSC-FCG iterations as fit the budget, scaled to the
@@ -325,14 +498,21 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     cfg = WORKLOADS[args.workload]
-    prob = build_problem(cfg)
-    iters = 7 if args.workload == "cfg2" else 6     # HSC-FCG iteration count of the full solve at 1e-8
     vals = []
     budget = max(5.0, 150.0 / max(args.steps + args.warmup, 1))
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(cfg, iterations=iters, budget_s=budget, prob=prob)
-        if i >= args.warmup:
-            vals.append(cb["value"])
+    if cfg.get("batch"):
+        cfgs = S.draw_batch_configs(cfg["count"], seed=cfg["seed"])
+        for i in range(args.warmup + args.steps):
+            cb = cpu_baseline_batch(cfgs, [6] * len(cfgs), budget_s=budget)   # ~6 HSC-FCG iterations at 1e-8
+            if i >= args.warmup:
+                vals.append(cb["value"])
+    else:
+        prob = build_problem(cfg)
+        iters = 7 if args.workload == "cfg2" else 6     # HSC-FCG iteration count of the full solve at 1e-8
+        for i in range(args.warmup + args.steps):
+            cb = cpu_baseline(cfg, iterations=iters, budget_s=budget, prob=prob)
+            if i >= args.warmup:
+                vals.append(cb["value"])
     v = float(np.mean(vals))
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
@@ -367,7 +547,8 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
-    out = run_ours(args, rank, world, dev)
+    out = run_batch(args, rank, world, dev) if WORKLOADS[args.workload].get("batch") else \
+        run_ours(args, rank, world, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -213,6 +213,27 @@ int mean_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_
 int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opts,
              sg_solve_stats* stats, void* stream);
 
+/* sg_autotune -- time the candidate block sizes (64, 128, 256 threads) of the
+ * full SG product in FP64 and FP32 on this problem and keep the fastest for
+ * all later calls (including the outer solver's fused product). Allocates two
+ * temporary n x P blocks; invalidates the handle's cached solve graphs. */
+int sg_autotune(sg_problem* h, void* stream);
+/* Block sizes chosen by sg_autotune (0: not tuned, the built-in choice). */
+int sg_autotune_result(const sg_problem* h, int* threads_f64, int* threads_f32);
+
+/* Batched solves of many independent systems (uneven n, M, p): one graph
+ * launch runs every system's whole solve (its outer flexible CG and nested
+ * inner loops) as an independent branch. The handles stay owned by the
+ * caller and must outlive the batch; a handle may belong to one batch. */
+typedef struct sg_batch sg_batch;
+int sg_batch_create(int count, sg_problem* const* problems, sg_batch** out);
+/* F, U: host arrays of count device pointers (n_i x P_i FP64 each);
+ * stats: host array of count entries or NULL. Returns SG_OK when every system
+ * converged, else the first failure (per-system status in stats). */
+int sg_batch_solve(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts* opts,
+                   sg_solve_stats* stats, void* stream);
+void sg_batch_destroy(sg_batch* b);
+
 /* sg_qoi -- Q = sum_j u_j^T M_h u_j = E[int u^2] for the orthonormal chaos
  * basis; also writes dQ/dU = 2 M_h U to dQdU when not NULL.
  * U, dQdU: device n x P FP64; q_out: device double[1]. Needs mass_vals. */

@@ -191,20 +191,72 @@ def mean_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[tor
     return Z
 
 
+def _stats(status, st) -> "SolveStats":
+    return SolveStats(status=status, iterations=st.iterations, rel_res=st.rel_res, true_rel_res=st.true_rel_res,
+                      kappa_est=st.kappa_est, inner_iters_total=st.inner_iters_total,
+                      inner_iters_max=st.inner_iters_max, solve_ms=st.solve_ms,
+                      res_hist=list(st.res_hist[: st.n_hist]), alpha=list(st.alpha[: st.iterations]),
+                      beta=list(st.beta[: max(st.iterations - 1, 0)]))
+
+
 def sg_solve(h: SGProblem, F: torch.Tensor, opts=None, U: Optional[torch.Tensor] = None, raise_on_error=True):
     """Flexible CG on the SG system; returns ``(U, SolveStats)``."""
     U = torch.empty_like(F) if U is None else U
     o = opts or solve_opts()
     st = _lib.sg_solve_stats()
     status = _lib.LIB.sg_solve(h.h, _ptr(F), _ptr(U), C.byref(o), C.byref(st), _stream())
-    stats = SolveStats(status=status, iterations=st.iterations, rel_res=st.rel_res, true_rel_res=st.true_rel_res,
-                       kappa_est=st.kappa_est, inner_iters_total=st.inner_iters_total,
-                       inner_iters_max=st.inner_iters_max, solve_ms=st.solve_ms,
-                       res_hist=list(st.res_hist[: st.n_hist]), alpha=list(st.alpha[: st.iterations]),
-                       beta=list(st.beta[: max(st.iterations - 1, 0)]))
+    stats = _stats(status, st)
     if raise_on_error:
         check(status, "sg_solve")
     return U, stats
+
+
+def sg_autotune(h: SGProblem):
+    """Time the SG product's candidate block sizes on this problem and keep the
+    fastest; returns ``(threads_f64, threads_f32)``."""
+    check(_lib.LIB.sg_autotune(h.h, _stream()), "sg_autotune")
+    a, b = C.c_int(0), C.c_int(0)
+    check(_lib.LIB.sg_autotune_result(h.h, C.byref(a), C.byref(b)), "sg_autotune_result")
+    return a.value, b.value
+
+
+class SGBatch:
+    """Many independent SG systems solved by one graph launch (``sg_batch_*``).
+    The problems stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h for p in self.problems])
+        out = C.c_void_p()
+        check(_lib.LIB.sg_batch_create(len(self.problems), arr, C.byref(out)), "sg_batch_create")
+        self.b = out.value
+
+    def solve(self, Fs, opts=None, Us=None, raise_on_error=True):
+        """Solve every system; returns ``(list of U, list of SolveStats)``."""
+        count = len(self.problems)
+        if len(Fs) != count:
+            raise ValueError(f"need {count} right-hand sides")
+        Us = [torch.empty_like(F) for F in Fs] if Us is None else list(Us)
+        o = opts or solve_opts()
+        st = (_lib.sg_solve_stats * count)()
+        fp = (C.c_void_p * count)(*[_ptr(F) for F in Fs])
+        up = (C.c_void_p * count)(*[_ptr(U) for U in Us])
+        status = _lib.LIB.sg_batch_solve(self.b, fp, up, C.byref(o), st, _stream())
+        stats = [_stats(st[i].status, st[i]) for i in range(count)]
+        if raise_on_error:
+            check(status, "sg_batch_solve")
+        return Us, stats
+
+    def close(self):
+        if getattr(self, "b", None):
+            _lib.LIB.sg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sg_qoi(h: SGProblem, U: torch.Tensor, want_grad: bool = True):

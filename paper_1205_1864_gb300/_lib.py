@@ -68,6 +68,11 @@ def _load():
         "mean_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "sg_solve": (i, [vp, vp, vp, P(sg_solve_opts), P(sg_solve_stats), vp]),
         "sg_qoi": (i, [vp, vp, vp, vp, vp]),
+        "sg_autotune": (i, [vp, vp]),
+        "sg_autotune_result": (i, [vp, P(i), P(i)]),
+        "sg_batch_create": (i, [i, P(vp), P(vp)]),
+        "sg_batch_solve": (i, [vp, P(vp), P(vp), P(sg_solve_opts), P(sg_solve_stats), vp]),
+        "sg_batch_destroy": (None, [vp]),
         "sg_qoi_grad": (i, [vp, vp, vp, i, P(C.c_double), vp, vp, vp]),
         "sg_last_error": (C.c_char_p, []),
         "sg_kernel_launches": (C.c_longlong, []),
@@ -94,5 +99,6 @@ def check(status: int, where: str):
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
     return ["sg_setup", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
-            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi",
+            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result",
+            "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",
             "sg_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

@@ -1,0 +1,248 @@
+// K6: many independent SG systems (uneven mesh size, M and p) solved by one
+// graph launch, and the autotuner that picks the block shape of the SG product
+// per problem.
+//
+// The batch graph has one branch per system: each branch is that system's
+// whole solve (outer flexible CG with its nested device-controlled inner
+// loops, graph.cu / fcg.cu), captured on its own stream between a fork and a
+// join event. One cudaGraphLaunch then runs every system; the branches are
+// independent, so the GPU schedules their kernels side by side and the small
+// systems fill the gaps of the large ones. Nothing returns to the host until
+// all systems are done.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <vector>
+
+#include "graph.cuh"
+#include "sghsc_internal.cuh"
+
+struct sg_batch {
+  std::vector<sg_problem*> hs;
+  std::vector<long long> gens;   // workspace generation of each handle when the graphs were built
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cs = nullptr;
+  std::map<std::string, sghsc::GraphEntry> graphs;
+};
+
+namespace sghsc {
+
+static void batch_clear(sg_batch* b) {
+  for (auto& kv : b->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
+  b->graphs.clear();
+}
+
+static int batch_build(sg_batch* b, const sg_solve_opts& o, cudaGraph_t* out) {
+  SG_TRY_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeRelaxed));
+  int r = SG_OK;
+  cudaError_t e = cudaEventRecord(b->fork, b->cs);
+  for (size_t i = 0; i < b->hs.size() && r == SG_OK && e == cudaSuccess; ++i) {
+    sg_problem* h = b->hs[i];
+    e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    if (e != cudaSuccess) break;
+    h->capturing = true;
+    h->cap_depth = 0;
+    r = enqueue_solve(h, o, b->branch[i]);
+    h->capturing = false;
+    if (r != SG_OK) break;
+    e = cudaEventRecord(b->join[i], b->branch[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cs, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(b->cs, &g);
+  if (r != SG_OK || e != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (r != SG_OK) return r;
+    SG_TRY_CUDA(e != cudaSuccess ? e : ee);
+  }
+  *out = g;
+  return SG_OK;
+}
+
+static int batch_solve(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts& o,
+                       sg_solve_stats* stats, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (sg_problem* h : b->hs) {
+    SG_TRY(check_solve_opts(h, &o));
+    SG_TRY(solve_prepare(h, o));
+  }
+  for (size_t i = 0; i < b->hs.size(); ++i) SG_TRY(solve_stage_in(b->hs[i], F[i], U[i], o, s));
+  // a workspace reallocation in any handle invalidates the captured graphs
+  bool stale = b->gens.size() != b->hs.size();
+  for (size_t i = 0; !stale && i < b->hs.size(); ++i) stale = b->gens[i] != b->hs[i]->ws_gen;
+  if (stale) {
+    batch_clear(b);
+    b->gens.clear();
+    for (sg_problem* h : b->hs) b->gens.push_back(h->ws_gen);
+  }
+  const std::string key = solve_key(o);
+  auto it = b->graphs.find(key);
+  if (it == b->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    SG_TRY(batch_build(b, o, &g));
+    cudaGraphExec_t ex;
+    cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    if (ei != cudaSuccess) {
+      cudaGraphDestroy(g);
+      SG_TRY_CUDA(ei);
+    }
+    it = b->graphs.emplace(key, GraphEntry{g, ex}).first;
+  }
+  { SG_TRY_CUDA(cudaGraphLaunch(it->second.exec, s)); }
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    sg_problem* h = b->hs[i];
+    SG_TRY_CUDA(cudaMemcpyAsync(U[i], h->fx, (size_t)h->n * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  SG_TRY_CUDA(cudaStreamSynchronize(s));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  int result = SG_OK;
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    const int r = solve_collect(b->hs[i], o, stats ? &stats[i] : nullptr, ms);
+    if (r != SG_OK && result == SG_OK) result = r;
+  }
+  if (result != SG_OK) set_error("sg_batch_solve: at least one system did not converge or broke down (see stats)");
+  return result;
+}
+
+// ---------------------------------------------------------------- autotune ---
+
+// Time the full SG product with each candidate block size and keep the fastest.
+static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
+  const size_t es = dtype == SG_F64 ? 8 : 4;
+  const size_t bytes = (size_t)h->n * h->P * es;
+  void *X = nullptr, *Y = nullptr;
+  SG_TRY_CUDA(cudaMalloc(&X, bytes));
+  cudaError_t e = cudaMalloc(&Y, bytes);
+  if (e != cudaSuccess) {
+    cudaFree(X);
+    SG_TRY_CUDA(e);
+  }
+  cudaMemsetAsync(X, 0, bytes, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cands[] = {64, 128, 256};
+  int best = 0;
+  float best_ms = 1e30f;
+  int r = SG_OK;
+  for (int c : cands) {
+    if ((h->P + c - 1) / c > 8) continue;   // at most 8 outputs per thread
+    h->k1_threads[dtype] = c;
+    r = launch_block_matvec(h, dtype, dtype, dtype, dtype, X, h->P, h->P, h->all, true, nullptr, 0, 1.0, 0.0, Y,
+                            h->P, s);
+    if (r != SG_OK) break;
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 5 && r == SG_OK; ++rep)
+      r = launch_block_matvec(h, dtype, dtype, dtype, dtype, X, h->P, h->P, h->all, true, nullptr, 0, 1.0, 0.0, Y,
+                              h->P, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r == SG_OK && ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  h->k1_threads[dtype] = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(X);
+  cudaFree(Y);
+  return r;
+}
+
+}  // namespace sghsc
+
+using namespace sghsc;
+
+extern "C" {
+
+int sg_autotune(sg_problem* h, void* stream) {
+  set_error("");
+  if (!h) {
+    set_error("sg_autotune: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  clear_graphs(h);  // captured graphs hold the old launch shapes
+  SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
+  SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
+  return SG_OK;
+}
+
+int sg_autotune_result(const sg_problem* h, int* threads_f64, int* threads_f32) {
+  if (!h) {
+    set_error("sg_autotune_result: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (threads_f64) *threads_f64 = h->k1_threads[SG_F64];
+  if (threads_f32) *threads_f32 = h->k1_threads[SG_F32];
+  return SG_OK;
+}
+
+int sg_batch_create(int count, sg_problem* const* problems, sg_batch** out) {
+  set_error("");
+  if (!out || count < 1 || !problems) {
+    set_error("sg_batch_create: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    for (int j = 0; j < i; ++j)
+      if (!problems[i] || problems[i] == problems[j]) {
+        set_error("sg_batch_create: null or repeated handle at %d", i);
+        return SG_ERR_INVALID_ARG;
+      }
+  sg_batch* b = new sg_batch();
+  b->hs.assign(problems, problems + count);
+  b->branch.assign(count, nullptr);
+  b->join.assign(count, nullptr);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    set_error("sg_batch_create: %s", cudaGetErrorString(e));
+    sg_batch_destroy(b);
+    return SG_ERR_CUDA;
+  }
+  *out = b;
+  return SG_OK;
+}
+
+int sg_batch_solve(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts* opts,
+                   sg_solve_stats* stats, void* stream) {
+  set_error("");
+  if (!b || !F || !U || !opts) {
+    set_error("sg_batch_solve: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (!F[i] || !U[i] || F[i] == U[i]) {
+      set_error("sg_batch_solve: invalid buffers for system %zu", i);
+      return SG_ERR_INVALID_ARG;
+    }
+  return batch_solve(b, F, U, *opts, stats, (cudaStream_t)stream);
+}
+
+void sg_batch_destroy(sg_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_clear(b);
+  for (auto s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  for (auto ev : b->join)
+    if (ev) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  delete b;
+}
+
+}  // extern "C"

@@ -51,6 +51,10 @@ int ensure_outer(sg_problem* h) {
       set_error("outer buffers must be allocated before graph capture");
       return SG_ERR_UNSUPPORTED;
     }
+    if (h->opart) {
+      clear_graphs(h);   // captured graphs hold the old partial-sum buffer
+      SG_TRY_CUDA(cudaDeviceSynchronize());
+    }
     cudaFree(h->opart);
     h->opart_blocks = need;
     SG_TRY_CUDA(cudaMalloc((void**)&h->opart, (size_t)h->opart_blocks * 2 * sizeof(double)));
@@ -124,7 +128,7 @@ static OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o) {
 }
 
 // The whole solve, enqueued on a capturing stream.
-static int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
+int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
   const long long N = (long long)h->n * h->P;
   const int vg = std::min(vec_grid(N), h->opart_blocks);
   OuterArgs a0 = outer_args(h, o);
@@ -173,27 +177,36 @@ std::string opts_key(const sg_prec_opts& o) {
   return buf;
 }
 
-static int solve_impl(sg_problem* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_stats* st,
-                      cudaStream_t s) {
-  const auto t0 = std::chrono::steady_clock::now();
+int solve_prepare(sg_problem* h, const sg_solve_opts& o) {
   SG_TRY(ensure_outer(h));
   if (o.precond != SG_PREC_NONE) SG_TRY(prepare_precond(h, o.precond, o.prec));
-  const size_t bytes = (size_t)h->n * h->P * sizeof(double);
+  return SG_OK;
+}
+
+std::string solve_key(const sg_solve_opts& o) {
   char key[512];
   snprintf(key, sizeof key, "solve|k%d|%s|tol%.17g|mi%d|fl%d|x0%d|tr%d", o.precond,
            o.precond == SG_PREC_NONE ? "-" : opts_key(o.prec).c_str(), o.tol, o.maxit, o.flexible, o.use_x0,
            o.check_true_residual);
+  return key;
+}
+
+// Copy the right-hand side (and the initial guess) into the handle's buffers.
+int solve_stage_in(sg_problem* h, const double* F, const double* U, const sg_solve_opts& o, cudaStream_t s) {
+  const size_t bytes = (size_t)h->n * h->P * sizeof(double);
   SG_TRY_CUDA(cudaMemcpyAsync(h->fF, F, bytes, cudaMemcpyDeviceToDevice, s));
   if (o.use_x0) SG_TRY_CUDA(cudaMemcpyAsync(h->fx, U, bytes, cudaMemcpyDeviceToDevice, s));
   SG_TRY_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), s));
   SG_TRY_CUDA(cudaMemsetAsync(h->iacc, 0, 2 * sizeof(long long), s));
-  SG_TRY(run_graph(h, key, [&](cudaStream_t cs) { return enqueue_solve(h, o, cs); }, s));
-  SG_TRY_CUDA(cudaMemcpyAsync(U, h->fx, bytes, cudaMemcpyDeviceToDevice, s));
+  return SG_OK;
+}
+
+// After the solve's work has completed: status and statistics.
+int solve_collect(sg_problem* h, const sg_solve_opts& o, sg_solve_stats* st, double wall_ms) {
   OuterCtl ctl;
-  SG_TRY_CUDA(cudaMemcpyAsync(&ctl, h->octl, sizeof ctl, cudaMemcpyDeviceToHost, s));
-  SG_TRY_CUDA(cudaMemcpyAsync(h->osc_host, h->osc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-  SG_TRY_CUDA(cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  SG_TRY_CUDA(cudaStreamSynchronize(s));
+  SG_TRY_CUDA(cudaMemcpy(&ctl, h->octl, sizeof ctl, cudaMemcpyDeviceToHost));
+  SG_TRY_CUDA(cudaMemcpy(h->osc_host, h->osc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost));
+  SG_TRY_CUDA(cudaMemcpy(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost));
   const int iters = ctl.it;
   const int status = *h->status_host;
   const double rel = h->osc_host[SC_REL];
@@ -223,7 +236,7 @@ static int solve_impl(sg_problem* h, const double* F, double* U, const sg_solve_
       st->beta[i] = i + 1 < iters ? b[i] : 0.0;
     }
     st->kappa_est = lanczos_kappa(a.data(), b.data(), iters);
-    st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    st->solve_ms = wall_ms;
   }
   if (result == SG_ERR_NO_CONVERGENCE) set_error("sg_solve: no convergence in %d iterations", iters);
   if (result == SG_ERR_BREAKDOWN) set_error("sg_solve: breakdown (p^T A p <= 0 or non-finite value)");
@@ -231,9 +244,45 @@ static int solve_impl(sg_problem* h, const double* F, double* U, const sg_solve_
   return result;
 }
 
+static int solve_impl(sg_problem* h, const double* F, double* U, const sg_solve_opts& o, sg_solve_stats* st,
+                      cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  SG_TRY(solve_prepare(h, o));
+  SG_TRY(solve_stage_in(h, F, U, o, s));
+  SG_TRY(run_graph(h, solve_key(o), [&](cudaStream_t cs) { return enqueue_solve(h, o, cs); }, s));
+  SG_TRY_CUDA(cudaMemcpyAsync(U, h->fx, (size_t)h->n * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  SG_TRY_CUDA(cudaStreamSynchronize(s));
+  return solve_collect(h, o, st,
+                       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+}
+
 }  // namespace sghsc
 
 using namespace sghsc;
+
+namespace sghsc {
+
+int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts) {
+  if (!h || !opts || opts->maxit < 1 || !(opts->tol >= 0.0) ||
+      (opts->precond != SG_PREC_NONE && opts->precond != SG_PREC_MEAN && opts->precond != SG_PREC_HSC)) {
+    set_error("sg_solve: invalid options");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (opts->precond != SG_PREC_NONE) {
+    if (opts->prec.precision != SG_F32 && opts->prec.precision != SG_F64) {
+      set_error("sg_solve: invalid preconditioner precision");
+      return SG_ERR_INVALID_ARG;
+    }
+    SG_TRY(check_prec_opts(opts->prec));
+    if (h->grids.empty()) {
+      set_error("sg_solve: the preconditioners need the multigrid hierarchy (power-of-two square mesh)");
+      return SG_ERR_UNSUPPORTED;
+    }
+  }
+  return SG_OK;
+}
+
+}  // namespace sghsc
 
 extern "C" {
 

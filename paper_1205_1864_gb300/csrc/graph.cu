@@ -68,6 +68,7 @@ int capture_while(sg_problem* h, cudaStream_t s, const EnqueueCond& pre, const E
 }
 
 void clear_graphs(sg_problem* h) {
+  ++h->ws_gen;
   for (auto& kv : h->graphs) {
     cudaGraphExecDestroy(kv.second.exec);
     cudaGraphDestroy(kv.second.graph);

@@ -171,7 +171,9 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
     vals = (const TAcc*)h->vals32;
     ec = (const TAcc*)E.c32;
   }
-  const int threads = pick_threads(wy);
+  int threads = pick_threads(wy);
+  const int tuned = h->k1_threads[sizeof(TAcc) == 8 ? SG_F64 : SG_F32];
+  if (DIAG && tuned > 0) threads = tuned;   // the full SG product: autotuned block size
   const int maxo = (wy + threads - 1) / threads;
   size_t smem = 0;
   const int chunk = pick_chunk(h, wx, sizeof(TAcc), M1, &smem);
@@ -223,7 +225,8 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
 
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
   const int P = h->P, M1 = h->M + 1;
-  const int threads = 256;  // the fused reduction assumes 256 threads
+  // a power of two <= 256 for the fused reduction: the autotuned block size or 256
+  const int threads = h->k1_threads[SG_F64] > 0 ? h->k1_threads[SG_F64] : 256;
   const int maxo = (P + threads - 1) / threads;
   size_t smem = 0;
   const int chunk = pick_chunk(h, P, sizeof(double), M1, &smem);

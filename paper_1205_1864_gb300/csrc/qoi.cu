@@ -117,6 +117,8 @@ __global__ void k_sum_fin(int nblk, const double* __restrict__ part, double* out
 
 static int ensure_part(sg_problem* h, size_t count) {
   if (h->opart && (size_t)h->opart_blocks * 2 >= count) return SG_OK;
+  clear_graphs(h);   // captured solve graphs use the partial-sum buffer
+  SG_TRY_CUDA(cudaDeviceSynchronize());
   cudaFree(h->opart);
   h->opart_blocks = (int)std::max<size_t>((count + 1) / 2, (size_t)h->num_sms * 16);
   SG_TRY_CUDA(cudaMalloc((void**)&h->opart, (size_t)h->opart_blocks * 2 * sizeof(double)));

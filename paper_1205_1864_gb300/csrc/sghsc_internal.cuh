@@ -163,6 +163,9 @@ struct sg_problem {
   int* loopflags = nullptr;                 // device: loop condition per nesting depth (eager mode)
   int* loopflag_host = nullptr;             // pinned
   std::map<std::string, sghsc::GraphEntry> graphs;
+  // autotuned block sizes of the full SG product (0: heuristic), per element type
+  int k1_threads[2] = {0, 0};
+  long long ws_gen = 0;                     // bumped whenever captured graphs become invalid
 };
 
 namespace sghsc {
@@ -192,8 +195,15 @@ int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o);
 int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 
-// ---- outer solver buffers (fcg.cu) ----
+// ---- outer solver (fcg.cu) ----
 int ensure_outer(sg_problem* h);
+int solve_prepare(sg_problem* h, const sg_solve_opts& o);
+std::string solve_key(const sg_solve_opts& o);
+int solve_stage_in(sg_problem* h, const double* F, const double* U, const sg_solve_opts& o, cudaStream_t s);
+// the whole solve (device-controlled loops), enqueued on a capturing stream
+int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s);
+int solve_collect(sg_problem* h, const sg_solve_opts& o, sg_solve_stats* st, double wall_ms);
+int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts);
 
 // ---- small elementwise kernels (vec.cu) ----
 int launch_cast(const void* src, int src_t, int lds, void* dst, int dst_t, int ldd, int rows,
