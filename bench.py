@@ -55,9 +55,15 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# FP64 ALU peak used for the FP64-bound kernels: the nominal GB300 FP64 rate
-# (1.25 TFLOP/s) from the hardware table of the profiling recipe.
-FP64_PEAK_TFLOPS = 1.25
+# FP64 ALU peak of the FP64-bound kernels: 152 SMs x 2070 MHz x 2 DFMA per
+# clock per SM x 2 flop = 1.259 TFLOP/s (the nominal GB300 FP64 rate of
+# 1.25 TFLOP/s at the maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12
+
+# DRAM bytes of one FP64 SG-product launch on the 128x128, M=6, p=4 workload:
+# dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of that launch
+# (L2 flushed before it, as before each timed launch here).
+K1_TRAFFIC = {"cfg2": 35807488 + 552960}
 
 
 class ClockSampler:
@@ -177,9 +183,32 @@ def run_ours(args, rank, world, dev):
         launches = L._lib.LIB.sg_kernel_launches() - l0
         return ts, stats, launches
 
+    if args.profile == "apply":
+        # the SG product alone, FP64 then FP32 (warm-up + timed launches each)
+        out = {"profile": "apply", "workload": cfg["name"], "n": n, "P": P, "nnz": nnz}
+        for name, dt, es in (("fp64", torch.float64, 8), ("fp32", torch.float32, 4)):
+            Ut = torch.tensor(S.random_block(n, P, seed=1205), dtype=dt, device=dev)
+            Yt = torch.empty_like(Ut)
+            for _ in range(args.warmup):
+                L.sg_apply(h, Ut, Yt)
+            ts = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                L.sg_apply(h, Ut, Yt)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            k = float(np.mean(ts))
+            b, fl = sg_matvec_bytes(n, nnz, M, P, es), sg_matvec_flops(nnz, P, n_m)
+            out[name] = {"ms": k, "GB_s": b / k / 1e6, "TFLOP_s": fl / k / 1e9, "bytes": b, "flops": fl}
+            del Ut, Yt
+        return out
     if args.profile:
         ts, st_h, launches = timed_solves(hsc_opts, args.steps, args.warmup)
-        return {"profile": True, "workload": cfg["name"], "ms": float(np.mean(ts)), "iterations": st_h.iterations,
+        return {"profile": "solve", "workload": cfg["name"], "ms": float(np.mean(ts)), "iterations": st_h.iterations,
                 "launches_per_solve": int(launches / max(args.steps, 1))}
     # headline: mixed HSC-PCG
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
@@ -239,8 +268,9 @@ def run_ours(args, rank, world, dev):
     }
     roofline = {"kernel": "k_block_matvec<double> (K1 FP64 SG product, outer CG)", "bound": "alu",
                 "achieved": fl / k1_64 / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (fl / k1_64 / 1e9) / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
+                "frac": (fl / k1_64 / 1e9) / FP64_PEAK_TFLOPS, "traffic": K1_TRAFFIC.get(args.workload),
+                "algorithmic_bytes": b64, "algorithmic_flops": fl,
+                "peak_source": "FP64 ALU: 152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop (nominal GB300 FP64 rate)"}
 
     # end to end through the public API: host (pinned) F in, host U out
     F_host = torch.tensor(F_np, dtype=torch.float64).pin_memory()
@@ -389,7 +419,7 @@ def run_batch(args, rank, world, dev):
     roofline = {"kernel": f"k_block_matvec<double> (K1 FP64 SG product) on the largest system (n={hb.n}, P={hb.P})",
                 "bound": "alu", "achieved": fl / k1 / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": (fl / k1 / 1e9) / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 FP64 rate (profiling recipe table)"}
+                "peak_source": "FP64 ALU: 152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop (nominal GB300 FP64 rate)"}
     # end to end through the public API: host (pinned) right-hand sides in, solutions out
     F_host = [F.cpu().pin_memory() for F in Fs]
     U_host = [torch.empty_like(F).pin_memory() for F in F_host]
@@ -531,8 +561,9 @@ def main():
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--profile", action="store_true",
-                    help="only the warm-up and timed HSC solves (for an ncu launch list); prints one short line")
+    ap.add_argument("--profile", nargs="?", const="solve", default=None, choices=["solve", "apply"],
+                    help="solve: only the warm-up and timed HSC solves; apply: only the SG product, FP64 then "
+                         "FP32 (for ncu captures); prints one short line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -28,7 +28,7 @@
 //                     first post-smoothing sweep applied to it
 //   k_jacobi          further sweeps; the last sweep of the finest grid also
 //                     reduces r . z for the CG
-//   k_vcycle_coarse   all grids with <= 1024 nodes: one block per 4 columns
+//   k_vcycle_coarse   all grids with <= 1024 nodes: one 1024-thread block per column
 //                     runs the rest of the V-cycle in shared memory.
 #include <algorithm>
 #include <mutex>

@@ -70,7 +70,7 @@ def test_theorem1_spectrum(ne, M, p, sigma):
     and c_{l,2} <= 1 (S_l = A_l - B D^{-1} B^T <= A_l) every eigenvalue of
     M_P A_P lies in [prod_l c_{l,1}, 1] and 1 is attained. The printed bound
     prod c_{l,2}/c_{l,1} omits the eigenvalue 1 of the D block; it is checked
-    here against the computed kappa as well (see the readings in the design doc).
+    here against the computed kappa as well: kappa <= 1 / prod c_{l,1} holds.
     """
     prob, A, G, off, K = _setup(ne, M, p, sigma)
     n = prob.n
