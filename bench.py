@@ -206,6 +206,25 @@ def run_ours(args, rank, world, dev):
             out[name] = {"ms": k, "GB_s": b / k / 1e6, "TFLOP_s": fl / k / 1e9, "bytes": b, "flops": fl}
             del Ut, Yt
         return out
+    if args.profile == "inner":
+        # the batched inner PCG on A_0 alone, FP32, one batch as wide as the widest degree level
+        wmax = max(int(math.comb(M + l - 1, l)) for l in range(1, p + 1))
+        B = torch.tensor(S.random_block(n, wmax, seed=1205), dtype=torch.float32, device=dev)
+        po = L.prec_opts(precision=L.SG_F32, inner_tol=1e-2)
+        for _ in range(args.warmup):
+            L.sg_inner_solve(h, B, po)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, its = L.sg_inner_solve(h, B, po)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return {"profile": "inner", "workload": cfg["name"], "w": wmax, "ms": float(np.mean(ts)),
+                "iterations": int(its.max())}
     if args.profile:
         ts, st_h, launches = timed_solves(hsc_opts, args.steps, args.warmup)
         return {"profile": "solve", "workload": cfg["name"], "ms": float(np.mean(ts)), "iterations": st_h.iterations,
@@ -561,9 +580,10 @@ def main():
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--profile", nargs="?", const="solve", default=None, choices=["solve", "apply"],
+    ap.add_argument("--profile", nargs="?", const="solve", default=None, choices=["solve", "apply", "inner"],
                     help="solve: only the warm-up and timed HSC solves; apply: only the SG product, FP64 then "
-                         "FP32 (for ncu captures); prints one short line")
+                         "FP32; inner: only the batched inner PCG on the widest level (for ncu captures); "
+                         "prints one short line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -11,10 +11,12 @@
 // scalars and a done flag; a column is finished when ||r|| <= tol ||b||
 // (zero columns at entry), and finished columns are skipped by every kernel.
 //
-// Thread mapping: a block has k*w threads (k = max(1, 1024 / w)), thread t
-// always handles column t mod w and nodes (blockIdx*k + t / w) + m * grid*k,
-// so per-column partial sums are register accumulations followed by a
-// fixed-order block reduction; the last block to finish a reduction kernel
+// Thread mapping: the blocks of a batch have a padded width wp (a multiple of
+// N = 16 bytes / element size); a thread owns a column group of N adjacent
+// columns, moved with 16-byte loads and stores. A block has k*ng threads
+// (ng = wp/N groups, k = max(1, 1024 / ng)), thread t always handles group
+// t mod ng and nodes (blockIdx*k + t / ng) + m * grid*k, so per-column partial
+// sums are register accumulations followed by a fixed-order block reduction; the last block to finish a reduction kernel
 // sums the block partials in block order and updates the CG scalars, so the
 // results do not depend on scheduling and no separate finalisation launch is
 // needed. The iteration loop is a CUDA graph WHILE node whose condition the
@@ -23,7 +25,8 @@
 // V-cycle kernels (weighted Jacobi, nu sweeps before and after, bilinear
 // transfers, Galerkin coarse operators built in setup.cu):
 //   k_smooth00        two sweeps from a zero iterate in one pass
-//   k_resid_restrict  the residual b - A x formed on the fly and restricted
+//   k_resid_restrict_t  the residual b - A x formed once per fine node in shared
+//                     memory (tiles of coarse nodes) and restricted
 //   k_prolong_jacobi  the coarse correction interpolated on the fly and the
 //                     first post-smoothing sweep applied to it
 //   k_jacobi          further sweeps; the last sweep of the finest grid also
@@ -40,32 +43,102 @@ namespace sghsc {
 
 constexpr int MAX_LEVELS = 16;
 
-struct Shape {
-  int w, k, bdim, grid;
+// Column groups: the batch buffers are node-major with a padded width wp (a
+// multiple of N = 16 bytes / sizeof(T)), and each thread owns N adjacent
+// columns of a node, moved with one 16-byte load or store. Per-node data
+// (stencil, inverse diagonal, grid position) is then read once per N columns
+// and the address arithmetic is shared by N elements.
+template <typename T>
+struct VW;
+template <>
+struct VW<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct VW<double> {
+  using type = double2;
+  static constexpr int N = 2;
 };
 
-// k*w threads per block (up to 1024), at most `per_sm` blocks per SM. The
-// reduction kernels use one block per SM: few block partials per column, so
-// the last-block reduction stays short.
-static Shape make_shape(const sg_problem* h, int nodes, int w, int per_sm = 2) {
+template <typename T>
+struct Vec {
+  static constexpr int N = VW<T>::N;
+  T a[N];
+};
+
+template <typename T>
+__device__ __forceinline__ Vec<T> vld(const T* p) {
+  const typename VW<T>::type v = *reinterpret_cast<const typename VW<T>::type*>(p);
+  Vec<T> r;
+  if constexpr (VW<T>::N == 4) {
+    r.a[0] = v.x; r.a[1] = v.y; r.a[2] = v.z; r.a[3] = v.w;
+  } else {
+    r.a[0] = v.x; r.a[1] = v.y;
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void vst(T* p, const Vec<T>& r) {
+  typename VW<T>::type v;
+  if constexpr (VW<T>::N == 4) {
+    v.x = r.a[0]; v.y = r.a[1]; v.z = r.a[2]; v.w = r.a[3];
+  } else {
+    v.x = r.a[0]; v.y = r.a[1];
+  }
+  *reinterpret_cast<typename VW<T>::type*>(p) = v;
+}
+
+template <typename T>
+__device__ __forceinline__ Vec<T> vzero() {
+  Vec<T> r;
+#pragma unroll
+  for (int u = 0; u < VW<T>::N; ++u) r.a[u] = T(0);
+  return r;
+}
+
+// bit u set when column c0 + u is finished
+template <int N>
+__device__ __forceinline__ unsigned done_mask(const int* __restrict__ done, int c0) {
+  unsigned m = 0;
+#pragma unroll
+  for (int u = 0; u < N; ++u) m |= (done[c0 + u] ? 1u : 0u) << u;
+  return m;
+}
+
+struct Shape {
+  int ng, k, bdim, grid;
+};
+
+// ng column groups per node, k = max(1, 1024 / ng) nodes per block pass,
+// at most `per_sm` blocks per SM. The reduction kernels use one block per SM:
+// few block partials per column, so the last-block reduction stays short.
+static Shape make_shape(const sg_problem* h, int nodes, int ng, int per_sm = 2) {
   Shape s;
-  s.w = w;
-  s.k = std::max(1, 1024 / w);
-  s.bdim = s.k * w;
+  s.ng = ng;
+  s.k = std::max(1, 1024 / ng);
+  s.bdim = s.k * ng;
   s.grid = std::max(1, std::min(ceil_div(nodes, s.k), h->num_sms * per_sm));
   return s;
 }
 
+// The grid of s clamped to what can be resident at once for kernel kern (its
+// register and shared-memory use), so no launch runs in two waves.
+template <typename K>
+static Shape fit(const sg_problem* h, Shape s, K kern) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.bdim, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  s.grid = std::max(1, std::min(s.grid, h->num_sms * per_sm));
+  return s;
+}
+
 template <typename T>
-struct Acc;
-template <>
-struct Acc<float> {
-  using type = float;
-};
-template <>
-struct Acc<double> {
-  using type = double;
-};
+static int padded_width(int w) {
+  constexpr int N = 16 / (int)sizeof(T);
+  return (w + N - 1) / N * N;
+}
 
 enum { FIN_INIT = 0, FIN_RHO = 1, FIN_ALPHA = 2, FIN_CONV = 3 };
 
@@ -85,51 +158,59 @@ struct FinArgs {
   long long* iacc;  // running [total, max] of per-column iteration counts
 };
 
-__device__ __forceinline__ void thread_pos(int w, int k, int& col, int& node0, int& nstep) {
-  col = threadIdx.x % w;
-  node0 = blockIdx.x * k + threadIdx.x / w;
+// Thread t of a block: column group t mod ng, node slice t / ng.
+__device__ __forceinline__ void thread_pos(int ng, int k, int& cg, int& node0, int& nstep) {
+  cg = threadIdx.x % ng;
+  node0 = blockIdx.x * k + threadIdx.x / ng;
   nstep = gridDim.x * k;
 }
 
-// Lanes per column group: the largest power of two g <= 32 with g*w <= bdim.
-// Column c is reduced by the g consecutive threads c*g .. c*g+g-1, which lie in
-// one warp, so a group finishes with g-wide shuffles (fixed order, no block
-// barrier); threads beyond w*g only take part in the shuffles.
-__device__ __forceinline__ int group_lanes(int w, int bdim) {
+// Lanes of this thread's warp that exist (the last warp of a block whose size
+// is not a multiple of 32 is partial).
+__device__ __forceinline__ unsigned warp_lanes() {
+  const unsigned left = blockDim.x - (threadIdx.x & ~31u);
+  return left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+}
+
+// Largest power of two g <= 32 with g * cols <= blockDim (at least 1): the
+// lanes that reduce one column, so one pass covers as many columns as fit.
+__device__ __forceinline__ int group_lanes(int cols) {
   int g = 1;
-  while (g < 32 && 2 * g * w <= bdim) g *= 2;
+  while (g < 32 && 2 * g * cols <= (int)blockDim.x) g *= 2;
   return g;
 }
 
 template <typename A>
 __device__ __forceinline__ A group_shfl_sum(A s, int g) {
-  for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
+  const unsigned m = warp_lanes();
+  for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_down_sync(m, s, o, g);
   return s;
 }
 
-// True for a warp that owns at least one column of the lane-group layout
-// (warp-uniform); the other warps skip the column arithmetic, which matters
-// because FP64 instructions issue at a fraction of the FP32 rate.
-__device__ __forceinline__ bool warp_owns_column(int w, int g) { return (int)((threadIdx.x & ~31u) / g) < w; }
-
-// Per-column block partial of the k threads of each column (thread t holds
-// column t mod w, slice t / w), summed in the accumulation type A of the
-// solver (FP32 for the FP32 inner solves) and stored as a double.
-template <typename A>
-__device__ __forceinline__ void block_col_reduce(A v, int w, int k, A* part, int ldp) {
-  __shared__ A red[1024];
-  red[threadIdx.x] = v;
+// Per-column block partial: thread (slice, cg) holds columns cg*N .. cg*N+N-1;
+// the k slices of each column are summed in the accumulation type A in a fixed
+// order and stored (block-major, leading dimension ldp).
+template <typename A, int N>
+__device__ __forceinline__ void block_col_reduce(const A (&v)[N], int wp, int k, A* part, int ldp) {
+  __shared__ A red[4096];
+  const int ng = wp / N;
+  const int cg = threadIdx.x % ng, slice = threadIdx.x / ng;
+#pragma unroll
+  for (int u = 0; u < N; ++u) red[slice * wp + cg * N + u] = v[u];
   __syncthreads();
-  const int g = group_lanes(w, blockDim.x);
-  if (!warp_owns_column(w, g)) return;
-  const int c = threadIdx.x / g, lane = threadIdx.x - c * g;
-  A s = A(0);
-  if (c < w)
-    for (int j = lane; j < k; j += g) s += red[j * w + c];
-  s = group_shfl_sum(s, g);
-  if (c < w && lane == 0) {
-    part[(size_t)blockIdx.x * ldp + c] = s;
-    __threadfence();  // only the writers of partials need the release fence
+  const int g = group_lanes(wp);
+  const int per_pass = blockDim.x / g;
+  const int lane = threadIdx.x % g;
+  for (int c0 = 0; c0 < wp; c0 += per_pass) {
+    const int c = c0 + (int)threadIdx.x / g;
+    A s = A(0);
+    if (c < wp)
+      for (int j = lane; j < k; j += g) s += red[j * wp + c];
+    s = group_shfl_sum(s, g);
+    if (c < wp && lane == 0) {
+      part[(size_t)blockIdx.x * ldp + c] = s;
+      __threadfence();  // only the writers of partials need the release fence
+    }
   }
 }
 
@@ -148,37 +229,42 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
 }
 
 // Column-wise CG scalar updates from the block partials (last block only).
-// Column c is summed by its lane group in the accumulation type A (blocks lane,
-// lane + g, ... with four interleaved accumulators, then the g-wide shuffle);
-// the column totals go through shared memory to threads 0..w-1, which update
-// the scalars in FP64 (so only the first ceil(w/32) warps issue FP64 work).
+// Column c is summed by a lane group in the accumulation type A (blocks lane,
+// lane + g, ... loaded 16 at a time, then the g-wide shuffle);
+// the column totals go through shared memory to threads 0..wp-1, which update
+// the scalars in FP64 (so only the first ceil(wp/32) warps issue FP64 work).
 // The order is fixed, so results are reproducible.
 template <typename A>
-__device__ void fin_columns(const FinArgs& f, int op, int w, int k, int nblk) {
+__device__ void fin_columns(const FinArgs& f, int op, int wp, int nblk) {
   __shared__ int cnt;
   __shared__ double colsum[1024];
   if (threadIdx.x == 0) cnt = 0;
   const A* part = (const A*)f.part;
-  const int g = group_lanes(w, blockDim.x);
-  const int gc = threadIdx.x / g, lane = threadIdx.x - gc * g;
-  if (warp_owns_column(w, g)) {
-    A s0 = A(0), s1 = A(0), s2 = A(0), s3 = A(0);
-    if (gc < w) {
-      int b = lane;
-      for (; b + 3 * g < nblk; b += 4 * g) {
-        s0 += __ldcg(&part[(size_t)b * f.ldp + gc]);
-        s1 += __ldcg(&part[(size_t)(b + g) * f.ldp + gc]);
-        s2 += __ldcg(&part[(size_t)(b + 2 * g) * f.ldp + gc]);
-        s3 += __ldcg(&part[(size_t)(b + 3 * g) * f.ldp + gc]);
+  const int g = group_lanes(wp);
+  const int per_pass = blockDim.x / g;
+  const int lane = threadIdx.x % g;
+  for (int c0 = 0; c0 < wp; c0 += per_pass) {
+    const int gc = c0 + (int)threadIdx.x / g;
+    A s = A(0);
+    if (gc < wp) {
+      // 16 independent loads in flight per lane, summed in block order
+      constexpr int B = 16;
+      for (int b0 = lane; b0 < nblk; b0 += B * g) {
+        A v[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          const int b = b0 + u * g;
+          v[u] = b < nblk ? __ldcg(&part[(size_t)b * f.ldp + gc]) : A(0);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) s += v[u];
       }
-      for (; b < nblk; b += g) s0 += __ldcg(&part[(size_t)b * f.ldp + gc]);
     }
-    const A s = group_shfl_sum((s0 + s1) + (s2 + s3), g);
-    if (gc < w && lane == 0) colsum[gc] = (double)s;
+    s = group_shfl_sum(s, g);
+    if (gc < wp && lane == 0) colsum[gc] = (double)s;
   }
   __syncthreads();
-  const int c = threadIdx.x;
-  if (c < w) {
+  for (int c = threadIdx.x; c < wp; c += blockDim.x) {
     const double s = colsum[c];
     if (op == FIN_INIT) {
       f.bb[c] = s;
@@ -240,16 +326,17 @@ __device__ void fin_columns(const FinArgs& f, int op, int w, int k, int nblk) {
   }
 }
 
-template <typename A>
-__device__ __forceinline__ void reduce_finalize(const FinArgs& f, A v, int w, int k, int op) {
-  block_col_reduce(v, w, k, (A*)f.part, f.ldp);
-  if (last_block(&f.ctl->ticket)) fin_columns<A>(f, op, w, k, gridDim.x);
+template <typename A, int N>
+__device__ __forceinline__ void reduce_finalize(const FinArgs& f, const A (&v)[N], int wp, int k, int op) {
+  block_col_reduce<A, N>(v, wp, k, (A*)f.part, f.ldp);
+  if (last_block(&f.ctl->ticket)) fin_columns<A>(f, op, wp, gridDim.x);
 }
 
 // (P xc) at fine node (fx, fy): bilinear interpolation from the coarse grid,
-// coarse node (X, Y) sitting on fine node (2X+1, 2Y+1), zero outside.
+// coarse node (X, Y) sitting on fine node (2X+1, 2Y+1), zero outside
+// (one column, used by the coarse-grid kernel).
 template <typename T>
-__device__ __forceinline__ T prolong_at(int fx, int fy, int nxc, int nyc, const T* __restrict__ xc, int w, int col) {
+__device__ __forceinline__ T prolong_at(int fx, int fy, int nxc, int nyc, const T* __restrict__ xc) {
   int Xs[2], Ys[2];
   T wx[2], wy[2];
   int nxs, nys;
@@ -262,7 +349,7 @@ __device__ __forceinline__ T prolong_at(int fx, int fy, int nxc, int nyc, const 
     if (Ys[iy] < 0 || Ys[iy] >= nyc) continue;
     for (int ix = 0; ix < nxs; ++ix) {
       if (Xs[ix] < 0 || Xs[ix] >= nxc) continue;
-      acc += wy[iy] * wx[ix] * xc[(size_t)(Ys[iy] * nxc + Xs[ix]) * w + col];
+      acc += wy[iy] * wx[ix] * xc[Ys[iy] * nxc + Xs[ix]];
     }
   }
   return acc;
@@ -289,19 +376,25 @@ struct NodeIter {
   }
 };
 
-// sum_j a_ij val(e_j, j, dy, dx) over the 9-point stencil of node (x, y),
-// e_j = i + dy*rs + dx*w the element index of neighbour j = node + dy*nx + dx
-// (node-major blocks, rs = nx*w). Interior nodes take a branch-free path.
+// sum_j a_ij val(e_j, j) over the 9-point stencil of node (x, y) for the N
+// columns of a group; e_j = i + dy*rs + dx*wp is the element index of the
+// group at neighbour j = node + dy*nx + dx (rs = nx*wp). Interior nodes take a
+// branch-free path.
 template <typename T, typename F>
-__device__ __forceinline__ T stencil9(const T* __restrict__ s9, int i, int rs, int w, int node, int x, int y, int nx,
-                                      int ny, F val) {
-  T acc = T(0);
+__device__ __forceinline__ Vec<T> stencil9(const T* __restrict__ s9, int i, int rs, int wp, int node, int x, int y,
+                                           int nx, int ny, F val) {
+  constexpr int N = VW<T>::N;
+  Vec<T> acc = vzero<T>();
   if (x > 0 && x < nx - 1 && y > 0 && y < ny - 1) {
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx)
-        acc += s9[(dy + 1) * 3 + (dx + 1)] * val(i + dy * rs + dx * w, node + dy * nx + dx, dy, dx);
+      for (int dx = -1; dx <= 1; ++dx) {
+        const T a = s9[(dy + 1) * 3 + (dx + 1)];
+        const Vec<T> v = val(i + dy * rs + dx * wp, node + dy * nx + dx);
+#pragma unroll
+        for (int u = 0; u < N; ++u) acc.a[u] += a * v.a[u];
+      }
     return acc;
   }
 #pragma unroll
@@ -310,7 +403,10 @@ __device__ __forceinline__ T stencil9(const T* __restrict__ s9, int i, int rs, i
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
       if (x + dx < 0 || x + dx >= nx) continue;
-      acc += s9[(dy + 1) * 3 + (dx + 1)] * val(i + dy * rs + dx * w, node + dy * nx + dx, dy, dx);
+      const T a = s9[(dy + 1) * 3 + (dx + 1)];
+      const Vec<T> v = val(i + dy * rs + dx * wp, node + dy * nx + dx);
+#pragma unroll
+      for (int u = 0; u < N; ++u) acc.a[u] += a * v.a[u];
     }
   }
   return acc;
@@ -320,156 +416,241 @@ __device__ __forceinline__ T stencil9(const T* __restrict__ s9, int i, int rs, i
 
 // one sweep from zero: x = omega D^{-1} b
 template <typename T>
-__global__ void __launch_bounds__(1024) k_smooth0(int n, int w, int k, const T* __restrict__ dinv,
+__global__ void __launch_bounds__(1024) k_smooth0(int n, int wp, int k, const T* __restrict__ dinv,
                                                   const T* __restrict__ b, T* __restrict__ x, T om,
                                                   const int* __restrict__ done) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
-  if (done[col]) return;
+  constexpr int N = VW<T>::N;
+  int cg, node, nstep;
+  thread_pos(wp / N, k, cg, node, nstep);
+  const int c0 = cg * N;
+  if (done_mask<N>(done, c0) == (1u << N) - 1) return;
   for (; node < n; node += nstep) {
-    const int i = node * w + col;
-    x[i] = om * dinv[node] * b[i];
+    const int i = node * wp + c0;
+    const T d = om * dinv[node];
+    const Vec<T> bv = vld(b + i);
+    Vec<T> xv;
+#pragma unroll
+    for (int u = 0; u < N; ++u) xv.a[u] = d * bv.a[u];
+    vst(x + i, xv);
   }
 }
 
 // two sweeps from zero: x1 = omega D^{-1} b, x2 = x1 + omega D^{-1} (b - A x1)
 template <typename T>
-__global__ void __launch_bounds__(1024) k_smooth00(int nx, int ny, int w, int k, const T* __restrict__ st,
+__global__ void __launch_bounds__(1024) k_smooth00(int nx, int ny, int wp, int k, const T* __restrict__ st,
                                                    const T* __restrict__ dinv, const T* __restrict__ b,
                                                    T* __restrict__ x, T om, const int* __restrict__ done) {
-  int col, node0, nstep;
-  thread_pos(w, k, col, node0, nstep);
-  if (done[col]) return;
-  const int n = nx * ny, rs = nx * w;
+  constexpr int N = VW<T>::N;
+  int cg, node0, nstep;
+  thread_pos(wp / N, k, cg, node0, nstep);
+  const int c0 = cg * N;
+  if (done_mask<N>(done, c0) == (1u << N) - 1) return;
+  const int n = nx * ny, rs = nx * wp;
   for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
-    const int i = it.node * w + col;
-    const T ax1 = om * stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
-                                [&](int e, int j, int, int) { return dinv[j] * b[e]; });
-    const T bi = b[i], di = dinv[it.node];
-    x[i] = om * di * bi + om * di * (bi - ax1);
+    const int i = it.node * wp + c0;
+    const Vec<T> ax1 = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny, [&](int e, int j) {
+      const T d = dinv[j];
+      Vec<T> v = vld(b + e);
+#pragma unroll
+      for (int u = 0; u < N; ++u) v.a[u] *= d;
+      return v;
+    });
+    const Vec<T> bv = vld(b + i);
+    const T di = om * dinv[it.node];
+    Vec<T> xv;
+#pragma unroll
+    for (int u = 0; u < N; ++u) xv.a[u] = di * bv.a[u] + di * (bv.a[u] - om * ax1.a[u]);
+    vst(x + i, xv);
   }
 }
 
 // xo = xi + omega D^{-1} (b - A xi); with DOT also the partials of b . xo and FIN_RHO
 template <typename T, bool DOT>
-__global__ void __launch_bounds__(1024) k_jacobi(int nx, int ny, int w, int k, const T* __restrict__ st,
+__global__ void __launch_bounds__(1024) k_jacobi(int nx, int ny, int wp, int k, const T* __restrict__ st,
                                                  const T* __restrict__ dinv, const T* __restrict__ b,
                                                  const T* __restrict__ xi, T* __restrict__ xo, T om, FinArgs f) {
-  int col, node0, nstep;
-  thread_pos(w, k, col, node0, nstep);
-  typename Acc<T>::type acc = 0;
-  if (!f.done[col]) {
-    const int n = nx * ny, rs = nx * w;
+  constexpr int N = VW<T>::N;
+  using A = T;
+  int cg, node0, nstep;
+  thread_pos(wp / N, k, cg, node0, nstep);
+  const int c0 = cg * N;
+  A acc[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = A(0);
+  if (done_mask<N>(f.done, c0) != (1u << N) - 1) {
+    const int n = nx * ny, rs = nx * wp;
     for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
-      const int i = it.node * w + col;
-      const T bi = b[i];
-      const T ax = stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
-                            [&](int e, int, int, int) { return xi[e]; });
-      const T v = xi[i] + om * dinv[it.node] * (bi - ax);
-      xo[i] = v;
-      if (DOT) acc += bi * v;
+      const int i = it.node * wp + c0;
+      const Vec<T> ax = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
+                                 [&](int e, int) { return vld(xi + e); });
+      const Vec<T> bv = vld(b + i), xv = vld(xi + i);
+      const T d = om * dinv[it.node];
+      Vec<T> v;
+#pragma unroll
+      for (int u = 0; u < N; ++u) {
+        v.a[u] = xv.a[u] + d * (bv.a[u] - ax.a[u]);
+        if (DOT) acc[u] += bv.a[u] * v.a[u];
+      }
+      vst(xo + i, v);
     }
   }
-  if (DOT) reduce_finalize(f, acc, w, k, FIN_RHO);
+  if (DOT) reduce_finalize<A, N>(f, acc, wp, k, FIN_RHO);
 }
 
-// bc = P^T (b - A x): coarse node (X, Y) gathers the 3x3 fine residuals around (2X+1, 2Y+1)
+// bc = P^T (b - A x), tiled: a block owns a TC x TC tile of coarse nodes. Its
+// threads first form the fine residuals b - A x of the tile's (2TC+1)^2 fine
+// footprint once each, for every column group, into shared memory; each coarse
+// node then sums its 3x3 weighted fine residuals from there. Grid-stride over
+// the tiles.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_resid_restrict(int nxf, int nyf, int nxc, int nyc, int w, int k,
-                                                         const T* __restrict__ st, const T* __restrict__ b,
-                                                         const T* __restrict__ x, T* __restrict__ bc,
-                                                         const int* __restrict__ done) {
-  int col, node0, nstep;
-  thread_pos(w, k, col, node0, nstep);
-  if (done[col]) return;
-  const int n = nxc * nyc, rsf = nxf * w;
-  for (NodeIter it(node0, nstep, nxc); it.node < n; it.next()) {
-    const int cx = 2 * it.x + 1, cy = 2 * it.y + 1;
-    T acc = T(0);
+__global__ void __launch_bounds__(1024) k_resid_restrict_t(int nxf, int nyf, int nxc, int nyc, int wp, int TC,
+                                                           const T* __restrict__ st, const T* __restrict__ b,
+                                                           const T* __restrict__ x, T* __restrict__ bc,
+                                                           const int* __restrict__ done) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int N = VW<T>::N;
+  using V = typename VW<T>::type;
+  V* res = reinterpret_cast<V*>(smem_raw);   // [fine footprint node][column group]
+  const int ng = wp / N;
+  const int ntx = (nxc + TC - 1) / TC, nty = (nyc + TC - 1) / TC;
+  const int FW = 2 * TC + 1;
+  const int rsf = nxf * wp;
+  for (int t = blockIdx.x; t < ntx * nty; t += gridDim.x) {
+    const int X0 = (t % ntx) * TC, Y0 = (t / ntx) * TC;
+    const int fx0 = 2 * X0, fy0 = 2 * Y0;
+    for (int idx = threadIdx.x; idx < FW * FW * ng; idx += blockDim.x) {
+      const int cg = idx % ng, fl = idx / ng;
+      const int fx = fx0 + fl % FW, fy = fy0 + fl / FW;
+      Vec<T> r = vzero<T>();
+      if (fx < nxf && fy < nyf && done_mask<N>(done, cg * N) != (1u << N) - 1) {
+        const int fn = fy * nxf + fx, fi = fn * wp + cg * N;
+        const Vec<T> ax = stencil9(st + fn * 9, fi, rsf, wp, fn, fx, fy, nxf, nyf,
+                                   [&](int e, int) { return vld(x + e); });
+        const Vec<T> bv = vld(b + fi);
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      const T wy = dy == 0 ? T(1) : T(0.5);
+        for (int u = 0; u < N; ++u) r.a[u] = bv.a[u] - ax.a[u];
+      }
+      vst(reinterpret_cast<T*>(res + idx), r);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < TC * TC * ng; idx += blockDim.x) {
+      const int cg = idx % ng, cl = idx / ng;
+      const int lx = cl % TC, ly = cl / TC;
+      const int X = X0 + lx, Y = Y0 + ly;
+      if (X < nxc && Y < nyc) {
+        Vec<T> acc = vzero<T>();
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const T wx = dx == 0 ? T(1) : T(0.5);
-        const int fx = cx + dx, fy = cy + dy, fn = fy * nxf + fx;
-        const int fi = fn * w + col;
-        const T ax = stencil9(st + fn * 9, fi, rsf, w, fn, fx, fy, nxf, nyf,
-                              [&](int e, int, int, int) { return x[e]; });
-        acc += wx * wy * (b[fi] - ax);
+        for (int dy = -1; dy <= 1; ++dy) {
+          const T wy = dy == 0 ? T(1) : T(0.5);
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const T wgt = (dx == 0 ? T(1) : T(0.5)) * wy;
+            const int fl = (2 * ly + 1 + dy) * FW + (2 * lx + 1 + dx);
+            const Vec<T> r = vld(reinterpret_cast<const T*>(res + fl * ng + cg));
+#pragma unroll
+            for (int u = 0; u < N; ++u) acc.a[u] += wgt * r.a[u];
+          }
+        }
+        vst(bc + (Y * nxc + X) * wp + cg * N, acc);
       }
     }
-    bc[it.node * w + col] = acc;
+    __syncthreads();
   }
 }
 
 // x' = x + P xc (on the fly), xo = x' + omega D^{-1} (b - A x'); DOT as k_jacobi.
-// The coarse values that the 3x3 fine neighbourhood of (x0, y) interpolates
-// from lie in the 3x3 coarse patch X in [Xb-1, Xb+1], Xb = floor((x0-1)/2)
-// (same in y). Interpolation is separable with parity-dependent weights:
-// even x0 -> offsets -1, 0, +1 read patch columns (1), (1,2)/2, (2);
-// odd x0  -> (0,1)/2, (1), (1,2)/2.
+// The coarse values that the 3x3 fine neighbourhood of node (x, y) interpolates
+// from lie in the 3x3 coarse patch cp[a][c], X = Xb - 1 + c, Xb = floor((x-1)/2)
+// (same in y). Interpolation is separable: fine offset dx in {-1, 0, 1} takes
+// the patch columns with weights Wx[dx][c], by the parity of x
+//   odd x:  (1/2, 1/2, 0), (0, 1, 0), (0, 1/2, 1/2)
+//   even x: (0, 1, 0), (0, 1/2, 1/2), (0, 0, 1)
+// so A (P xc) at the node is sum_{a,c} K[a][c] cp[a][c] with the per-node
+// weights K = Wy^T S Wx (S the 3x3 stencil, zero outside the grid), shared by
+// all columns, and (P xc) at the node itself uses Wy[0] (x) Wx[0] (centre rows).
 template <typename T, bool DOT>
-__global__ void __launch_bounds__(1024) k_prolong_jacobi(int nxf, int nyf, int nxc, int nyc, int w, int k,
+__global__ void __launch_bounds__(1024) k_prolong_jacobi(int nxf, int nyf, int nxc, int nyc, int wp, int k,
                                                          const T* __restrict__ st, const T* __restrict__ dinv,
                                                          const T* __restrict__ b, const T* __restrict__ x,
                                                          const T* __restrict__ xc, T* __restrict__ xo, T om,
                                                          FinArgs f) {
-  int col, node0, nstep;
-  thread_pos(w, k, col, node0, nstep);
-  typename Acc<T>::type acc = 0;
-  if (!f.done[col]) {
-    const int n = nxf * nyf, rs = nxf * w;
+  constexpr int N = VW<T>::N;
+  using A = T;
+  int cg, node0, nstep;
+  thread_pos(wp / N, k, cg, node0, nstep);
+  const int c0 = cg * N;
+  A acc[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = A(0);
+  if (done_mask<N>(f.done, c0) != (1u << N) - 1) {
+    const int n = nxf * nyf, rs = nxf * wp;
     const T h = T(0.5);
     for (NodeIter it(node0, nstep, nxf); it.node < n; it.next()) {
+      const T* s9 = st + it.node * 9;
+      // separable interpolation weights by parity (rows: offset -1, 0, +1; columns: patch 0..2)
+      T wxm[3][3], wym[3][3];
+      const bool ox = it.x & 1, oy = it.y & 1;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { wxm[d][c] = T(0); wym[d][c] = T(0); }
+      if (ox) { wxm[0][0] = h; wxm[0][1] = h; wxm[1][1] = T(1); wxm[2][1] = h; wxm[2][2] = h; }
+      else { wxm[0][1] = T(1); wxm[1][1] = h; wxm[1][2] = h; wxm[2][2] = T(1); }
+      if (oy) { wym[0][0] = h; wym[0][1] = h; wym[1][1] = T(1); wym[2][1] = h; wym[2][2] = h; }
+      else { wym[0][1] = T(1); wym[1][1] = h; wym[1][2] = h; wym[2][2] = T(1); }
+      // S masked to the grid, T1 = S Wx, K = Wy^T T1
+      T t1[3][3];
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const bool iny = it.y + dy - 1 >= 0 && it.y + dy - 1 < nyf;
+        T srow[3];
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const bool inx = it.x + dx - 1 >= 0 && it.x + dx - 1 < nxf;
+          srow[dx] = (iny && inx) ? s9[dy * 3 + dx] : T(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t1[dy][c] = srow[0] * wxm[0][c] + srow[1] * wxm[1][c] + srow[2] * wxm[2][c];
+      }
+      T K[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) K[a][c] = wym[0][a] * t1[0][c] + wym[1][a] * t1[1][c] + wym[2][a] * t1[2][c];
       const int Xb = (it.x - 1) >> 1, Yb = (it.y - 1) >> 1;
-      T cp[3][3];
+      Vec<T> apc = vzero<T>(), pc = vzero<T>();
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int Y = Yb - 1 + a;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const int X = Xb - 1 + c;
-          cp[a][c] = (Y >= 0 && Y < nyc && X >= 0 && X < nxc) ? xc[(Y * nxc + X) * w + col] : T(0);
-        }
-      }
-      T tx[3][3];
+          if (Y >= 0 && Y < nyc && X >= 0 && X < nxc) {
+            const Vec<T> v = vld(xc + (Y * nxc + X) * wp + c0);
+            const T wc = wym[1][a] * wxm[1][c];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (it.x & 1) {
-          tx[a][0] = h * (cp[a][0] + cp[a][1]);
-          tx[a][1] = cp[a][1];
-          tx[a][2] = h * (cp[a][1] + cp[a][2]);
-        } else {
-          tx[a][0] = cp[a][1];
-          tx[a][1] = h * (cp[a][1] + cp[a][2]);
-          tx[a][2] = cp[a][2];
+            for (int u = 0; u < N; ++u) {
+              apc.a[u] += K[a][c] * v.a[u];
+              pc.a[u] += wc * v.a[u];
+            }
+          }
         }
       }
-      T I[3][3];
+      const int i = it.node * wp + c0;
+      const Vec<T> ax = stencil9(s9, i, rs, wp, it.node, it.x, it.y, nxf, nyf,
+                                 [&](int e, int) { return vld(x + e); });
+      const Vec<T> bv = vld(b + i), xv = vld(x + i);
+      const T d = om * dinv[it.node];
+      Vec<T> v;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (it.y & 1) {
-          I[0][d] = h * (tx[0][d] + tx[1][d]);
-          I[1][d] = tx[1][d];
-          I[2][d] = h * (tx[1][d] + tx[2][d]);
-        } else {
-          I[0][d] = tx[1][d];
-          I[1][d] = h * (tx[1][d] + tx[2][d]);
-          I[2][d] = tx[2][d];
-        }
+      for (int u = 0; u < N; ++u) {
+        v.a[u] = (xv.a[u] + pc.a[u]) + d * (bv.a[u] - (ax.a[u] + apc.a[u]));
+        if (DOT) acc[u] += bv.a[u] * v.a[u];
       }
-      const int i = it.node * w + col;
-      const T ax = stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nxf, nyf,
-                            [&](int e, int, int dy, int dx) { return x[e] + I[dy + 1][dx + 1]; });
-      const T xi = x[i] + I[1][1];
-      const T bi = b[i];
-      const T v = xi + om * dinv[it.node] * (bi - ax);
-      xo[i] = v;
-      if (DOT) acc += bi * v;
+      vst(xo + i, v);
     }
   }
-  if (DOT) reduce_finalize(f, acc, w, k, FIN_RHO);
+  if (DOT) reduce_finalize<A, N>(f, acc, wp, k, FIN_RHO);
 }
 
 struct CoarseGrids {
@@ -504,7 +685,7 @@ __device__ __forceinline__ void stage_copy(T* __restrict__ dst, const T* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, int w, const T* __restrict__ bg,
+__global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, int wp, const T* __restrict__ bg,
                                                         T* __restrict__ xg, T om, int nu,
                                                         const int* __restrict__ done) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -543,7 +724,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, 
   {
     const int n0 = L.nx[L.g0] * L.ny[L.g0];
     T* b0 = B(L.g0);
-    for (int idx = tid; idx < n0; idx += blockDim.x) b0[idx] = bg[idx * w + col];
+    for (int idx = tid; idx < n0; idx += blockDim.x) b0[idx] = bg[idx * wp + col];
   }
   __syncthreads();
   T* cur[MAX_LEVELS];
@@ -617,7 +798,7 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, 
     if (act)
       for (int idx = tid; idx < n; idx += lim) {
         const int y = idx / nx, x = idx - y * nx;
-        c[idx] += prolong_at(x, y, nxc, nyc, xc, 1, 0);
+        c[idx] += prolong_at(x, y, nxc, nyc, xc);
       }
     lsync(wm);
     for (int s = 0; s < nu; ++s) {
@@ -634,101 +815,177 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, 
   __syncthreads();
   const int n0 = L.nx[L.g0] * L.ny[L.g0];
   const T* x0 = cur[L.g0];
-  for (int idx = tid; idx < n0; idx += blockDim.x) xg[idx * w + col] = x0[idx];
+  for (int idx = tid; idx < n0; idx += blockDim.x) xg[idx * wp + col] = x0[idx];
 }
 
 // ------------------------------------------------------------- batched CG ---
 
-// r = src (cast), x = 0 (x has leading dimension ldx), ||b||^2 -> FIN_INIT
-// (sets the loop condition)
+// r = src (cast; padded columns w..wp-1 zero), x = 0, ||b||^2 -> FIN_INIT
+// (sets the loop condition; zero columns, the padded ones included, are done)
 template <typename TS, typename T>
-__global__ void __launch_bounds__(1024) k_gather(int n, int w, int k, const TS* __restrict__ src, int lds, T* __restrict__ r,
-                         T* __restrict__ x, int ldx, FinArgs f) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
-  typename Acc<T>::type acc = 0;
+__global__ void __launch_bounds__(1024) k_gather(int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
+                                                 T* __restrict__ r, T* __restrict__ x, FinArgs f) {
+  constexpr int N = VW<T>::N;
+  using A = T;
+  int cg, node, nstep;
+  thread_pos(wp / N, k, cg, node, nstep);
+  const int c0 = cg * N;
+  A acc[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = A(0);
   for (; node < n; node += nstep) {
-    const int i = node * w + col;
-    const T v = (T)src[(size_t)node * lds + col];
-    r[i] = v;
-    x[(size_t)node * ldx + col] = T(0);
-    acc += v * v;
+    Vec<T> v;
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      v.a[u] = c0 + u < w ? (T)src[(size_t)node * lds + c0 + u] : T(0);
+      acc[u] += v.a[u] * v.a[u];
+    }
+    const int i = node * wp + c0;
+    vst(r + i, v);
+    vst(x + i, vzero<T>());
   }
-  reduce_finalize(f, acc, w, k, FIN_INIT);
+  reduce_finalize<A, N>(f, acc, wp, k, FIN_INIT);
 }
 
+// src (leading dimension lds, w columns) -> b (wp columns, padding zero)
+template <typename TS, typename T>
+__global__ void __launch_bounds__(1024) k_pack(int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
+                                               T* __restrict__ b) {
+  constexpr int N = VW<T>::N;
+  int cg, node, nstep;
+  thread_pos(wp / N, k, cg, node, nstep);
+  const int c0 = cg * N;
+  for (; node < n; node += nstep) {
+    Vec<T> v;
+#pragma unroll
+    for (int u = 0; u < N; ++u) v.a[u] = c0 + u < w ? (T)src[(size_t)node * lds + c0 + u] : T(0);
+    vst(b + node * wp + c0, v);
+  }
+}
+
+// x (wp columns) -> dst (leading dimension ldd, first w columns)
 template <typename T, typename TD>
-__global__ void __launch_bounds__(1024) k_scatter(int n, int w, int k, const T* __restrict__ x, TD* __restrict__ dst, int ldd) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
-  for (; node < n; node += nstep) dst[(size_t)node * ldd + col] = (TD)x[(size_t)node * w + col];
+__global__ void __launch_bounds__(1024) k_scatter(int n, int w, int wp, int k, const T* __restrict__ x,
+                                                  TD* __restrict__ dst, int ldd) {
+  constexpr int N = VW<T>::N;
+  int cg, node, nstep;
+  thread_pos(wp / N, k, cg, node, nstep);
+  const int c0 = cg * N;
+  for (; node < n; node += nstep) {
+    const Vec<T> v = vld(x + node * wp + c0);
+#pragma unroll
+    for (int u = 0; u < N; ++u)
+      if (c0 + u < w) dst[(size_t)node * ldd + c0 + u] = (TD)v.a[u];
+  }
 }
 
 // a . b per column -> op (used when the finest grid is inside the coarse block)
 template <typename T>
-__global__ void __launch_bounds__(1024) k_dot_fin(int n, int w, int k, const T* __restrict__ a, const T* __restrict__ b, FinArgs f, int op) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
-  typename Acc<T>::type acc = 0;
-  if (!f.done[col])
+__global__ void __launch_bounds__(1024) k_dot_fin(int n, int wp, int k, const T* __restrict__ a, const T* __restrict__ b,
+                                                  FinArgs f, int op) {
+  constexpr int N = VW<T>::N;
+  using A = T;
+  int cg, node, nstep;
+  thread_pos(wp / N, k, cg, node, nstep);
+  const int c0 = cg * N;
+  A acc[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = A(0);
+  if (done_mask<N>(f.done, c0) != (1u << N) - 1)
     for (; node < n; node += nstep) {
-      const int i = node * w + col;
-      acc += a[i] * b[i];
+      const int i = node * wp + c0;
+      const Vec<T> av = vld(a + i), bv = vld(b + i);
+#pragma unroll
+      for (int u = 0; u < N; ++u) acc[u] += av.a[u] * bv.a[u];
     }
-  reduce_finalize(f, acc, w, k, op);
+  reduce_finalize<A, N>(f, acc, wp, k, op);
 }
 
-// p_new = z + beta p_old (p_new = z on a column's first iteration), formed on the
+// p_new = z + beta p_old (p_new = z on the batch's first iteration), formed on the
 // fly at the 9 neighbours; q = A_0 p_new; p_new . q -> FIN_ALPHA.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_matvec_p(int nx, int ny, int w, int k, const T* __restrict__ st,
-                                                   const T* __restrict__ z, T* pA, T* pB, T* __restrict__ q,
-                                                   FinArgs f) {
-  int col, node0, nstep;
-  thread_pos(w, k, col, node0, nstep);
+__global__ void __launch_bounds__(1024) k_matvec_p(int nx, int ny, int wp, int k, const T* __restrict__ st,
+                                                   const T* __restrict__ z, T* __restrict__ pA,
+                                                   T* __restrict__ pB, T* __restrict__ q, FinArgs f) {
+  constexpr int N = VW<T>::N;
+  using A = T;
+  int cg, node0, nstep;
+  thread_pos(wp / N, k, cg, node0, nstep);
+  const int c0 = cg * N;
   const int par = f.ctl->it & 1;
   const T* __restrict__ pold = par ? pB : pA;
   T* __restrict__ pnew = par ? pA : pB;
-  typename Acc<T>::type acc = 0;
-  if (!f.done[col]) {
-    const bool first = f.iters[col] == 0;
-    const T bt = first ? T(0) : (sizeof(T) == 4 ? (T)f.betaf[col] : (T)f.beta[col]);
-    const int n = nx * ny, rs = nx * w;
+  A acc[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = A(0);
+  if (done_mask<N>(f.done, c0) != (1u << N) - 1) {
+    T bt[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) bt[u] = sizeof(T) == 4 ? (T)f.betaf[c0 + u] : (T)f.beta[c0 + u];
+    const int n = nx * ny, rs = nx * wp;
+    // iteration 0 of the batch: p_new = z, p_old is not read (it holds nothing yet)
+    const bool first = f.ctl->it == 0;
+    auto pv = [&](int e) {
+      Vec<T> v = vld(z + e);
+      if (!first) {
+        const Vec<T> po = vld(pold + e);
+#pragma unroll
+        for (int u = 0; u < N; ++u) v.a[u] += bt[u] * po.a[u];
+      }
+      return v;
+    };
     for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
-      const int i = it.node * w + col;
-      const T s = first ? stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
-                                   [&](int e, int, int, int) { return z[e]; })
-                        : stencil9(st + it.node * 9, i, rs, w, it.node, it.x, it.y, nx, ny,
-                                   [&](int e, int, int, int) { return z[e] + bt * pold[e]; });
-      const T pi = first ? z[i] : z[i] + bt * pold[i];
-      pnew[i] = pi;
-      q[i] = s;
-      acc += pi * s;
+      const int i = it.node * wp + c0;
+      const Vec<T> s = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
+                                [&](int e, int) { return pv(e); });
+      const Vec<T> p = pv(i);
+      vst(pnew + i, p);
+      vst(q + i, s);
+#pragma unroll
+      for (int u = 0; u < N; ++u) acc[u] += p.a[u] * s.a[u];
     }
   }
-  reduce_finalize(f, acc, w, k, FIN_ALPHA);
+  reduce_finalize<A, N>(f, acc, wp, k, FIN_ALPHA);
 }
 
-// x += alpha p_new (x has leading dimension ldx); r -= alpha q; r . r -> FIN_CONV
-// (sets the loop condition)
+// x += alpha p_new; r -= alpha q; r . r -> FIN_CONV (sets the loop condition).
+// Finished columns keep their x and r.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_update_xr(int n, int w, int k, const T* pA, const T* pB, const T* __restrict__ q,
-                            T* __restrict__ x, int ldx, T* __restrict__ r, FinArgs f) {
-  int col, node, nstep;
-  thread_pos(w, k, col, node, nstep);
+__global__ void __launch_bounds__(1024) k_update_xr(int n, int wp, int k, const T* __restrict__ pA,
+                                                    const T* __restrict__ pB, const T* __restrict__ q,
+                                                    T* __restrict__ x, T* __restrict__ r, FinArgs f) {
+  constexpr int N = VW<T>::N;
+  using A = T;
+  int cg, node, nstep;
+  thread_pos(wp / N, k, cg, node, nstep);
+  const int c0 = cg * N;
   const T* __restrict__ pnew = (f.ctl->it & 1) ? pA : pB;
-  typename Acc<T>::type acc = 0;
-  if (!f.done[col]) {
-    const T a = sizeof(T) == 4 ? (T)f.alphaf[col] : (T)f.alpha[col];
+  A acc[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = A(0);
+  const unsigned dm = done_mask<N>(f.done, c0);
+  if (dm != (1u << N) - 1) {
+    T a[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u)
+      a[u] = (dm >> u) & 1u ? T(0) : (sizeof(T) == 4 ? (T)f.alphaf[c0 + u] : (T)f.alpha[c0 + u]);
     for (; node < n; node += nstep) {
-      const int i = node * w + col;
-      x[(size_t)node * ldx + col] += a * pnew[i];
-      const T rv = r[i] - a * q[i];
-      r[i] = rv;
-      acc += rv * rv;
+      const int i = node * wp + c0;
+      Vec<T> xv = vld(x + i), rv = vld(r + i);
+      const Vec<T> pv = vld(pnew + i), qv = vld(q + i);
+#pragma unroll
+      for (int u = 0; u < N; ++u) {
+        if (!((dm >> u) & 1u)) {
+          xv.a[u] += a[u] * pv.a[u];
+          rv.a[u] -= a[u] * qv.a[u];
+        }
+        acc[u] += rv.a[u] * rv.a[u];
+      }
+      vst(x + i, xv);
+      vst(r + i, rv);
     }
   }
-  reduce_finalize(f, acc, w, k, FIN_CONV);
+  reduce_finalize<A, N>(f, acc, wp, k, FIN_CONV);
 }
 
 __global__ void k_clear_done(int w, int* done) {
@@ -770,6 +1027,7 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
     return SG_ERR_UNSUPPORTED;
   }
   InnerWork& iw = dtype == SG_F64 ? h->iw64 : h->iw32;
+  wcap = (wcap + 3) / 4 * 4;   // room for the padded width of either precision
   if (iw.wcap >= wcap) return SG_OK;
   if (h->capturing) {
     set_error("inner solve: workspace must be allocated before graph capture");
@@ -838,7 +1096,7 @@ static FinArgs make_fin(sg_problem* h, InnerWork& iw, const sg_prec_opts& o) {
 }
 
 template <typename T>
-static int launch_coarse(sg_problem* h, int g0, const T* b, T* x, int w, const sg_prec_opts& o, const int* done,
+static int launch_coarse(sg_problem* h, int g0, const T* b, T* x, int wp, const sg_prec_opts& o, const int* done,
                          cudaStream_t s) {
   CoarseGrids L;
   L.g0 = g0;
@@ -855,24 +1113,49 @@ static int launch_coarse(sg_problem* h, int g0, const T* b, T* x, int w, const s
   }
   const size_t smem = (size_t)13 * tot * sizeof(T);
   SG_TRY_CUDA(cudaFuncSetAttribute(k_vcycle_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  { k_vcycle_coarse<T><<<w, 1024, smem, s>>>(L, tot, w, b, x, (T)o.omega, o.nu, done); ::sghsc::note_launch(); }
+  { k_vcycle_coarse<T><<<wp, 1024, smem, s>>>(L, tot, wp, b, x, (T)o.omega, o.nu, done); ::sghsc::note_launch(); }
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-// One V-cycle on grid g applied to b (zero initial guess). *out receives the
-// buffer holding the result (x or xt). With fdot (finest grid only) the last
-// kernel also reduces b . result into FIN_RHO.
+// Tiled residual + restriction: the coarse tile edge TC is the largest (<= 16)
+// whose fine footprint (2TC+1)^2 times the column groups stays within 2048
+// residuals per block, shrunk while that leaves fewer tiles than SMs.
 template <typename T>
-static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, int w, const sg_prec_opts& o,
+static int launch_resid_restrict(sg_problem* h, const GridLevel& G, const GridLevel& C, int wp, const T* st,
+                                 const T* b, const T* x, T* bc, const int* done, cudaStream_t s) {
+  const int ng = wp / VW<T>::N;
+  auto items = [&](int tc) { return (2 * tc + 1) * (2 * tc + 1) * ng; };
+  auto tiles = [&](int tc) { return ceil_div(C.nx, tc) * ceil_div(C.ny, tc); };
+  int tc = 16;
+  while (tc > 1 && items(tc) > 2048) --tc;
+  while (tc > 1 && tiles(tc) < h->num_sms) --tc;
+  const int bdim = std::min(1024, (items(tc) + 31) / 32 * 32);
+  const size_t smem = (size_t)items(tc) * 16;
+  SG_TRY_CUDA(cudaFuncSetAttribute(k_resid_restrict_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_t<T>, bdim, smem));
+  const int grid = std::max(1, std::min(tiles(tc), h->num_sms * std::max(per_sm, 1)));
+  { k_resid_restrict_t<T><<<grid, bdim, smem, s>>>(G.nx, G.ny, C.nx, C.ny, wp, tc, st, b, x, bc, done); ::sghsc::note_launch(); }
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+// One V-cycle on grid g applied to b (zero initial guess), all blocks with the
+// padded width wp. *out receives the buffer holding the result (x or xt). With
+// fdot (finest grid only) the last kernel also reduces b . result into FIN_RHO.
+template <typename T>
+static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, int wp, const sg_prec_opts& o,
                   cudaStream_t s, const FinArgs* fdot, const T** out) {
+  constexpr int N = VW<T>::N;
+  const int ng = wp / N;
   const T om = (T)o.omega;
   FinArgs fz = make_fin(h, iw, o);
   if (g >= h->cb_level) {
-    SG_TRY(launch_coarse<T>(h, g, b, x, w, o, iw.done, s));
+    SG_TRY(launch_coarse<T>(h, g, b, x, wp, o, iw.done, s));
     if (fdot) {
-      const Shape sh = make_shape(h, h->grids[g].n, w, 1);
-      { k_dot_fin<T><<<sh.grid, sh.bdim, 0, s>>>(h->grids[g].n, w, sh.k, b, x, *fdot, FIN_RHO); ::sghsc::note_launch(); }
+      const Shape sh = make_shape(h, h->grids[g].n, ng, 1);
+      { k_dot_fin<T><<<sh.grid, sh.bdim, 0, s>>>(h->grids[g].n, wp, sh.k, b, x, *fdot, FIN_RHO); ::sghsc::note_launch(); }
     }
     *out = x;
     return SG_OK;
@@ -881,35 +1164,34 @@ static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, 
   const GridLevel& C = h->grids[g + 1];
   const T* st = sizeof(T) == 8 ? (const T*)G.st64 : (const T*)G.st32;
   const T* dinv = sizeof(T) == 8 ? (const T*)G.dinv64 : (const T*)G.dinv32;
-  const Shape sh = make_shape(h, G.n, w);
-  const Shape shd = make_shape(h, G.n, w, 1);   // kernels that end in a reduction
-  const Shape shc = make_shape(h, C.n, w);
+  const Shape sh = make_shape(h, G.n, ng);
+  const Shape shd = make_shape(h, G.n, ng, 1);   // kernels that end in a reduction
   T* cur = x;
   T* oth = xt;
   if (o.nu == 1) {
-    { k_smooth0<T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, sh.k, dinv, b, cur, om, iw.done); ::sghsc::note_launch(); }
+    { const Shape f_ = fit(h, sh, k_smooth0<T>); k_smooth0<T><<<f_.grid, f_.bdim, 0, s>>>(G.n, wp, f_.k, dinv, b, cur, om, iw.done); ::sghsc::note_launch(); }
   } else {
-    { k_smooth00<T><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, w, sh.k, st, dinv, b, cur, om, iw.done); ::sghsc::note_launch(); }
+    { const Shape f_ = fit(h, sh, k_smooth00<T>); k_smooth00<T><<<f_.grid, f_.bdim, 0, s>>>(G.nx, G.ny, wp, f_.k, st, dinv, b, cur, om, iw.done); ::sghsc::note_launch(); }
     for (int it = 2; it < o.nu; ++it) {
-      { k_jacobi<T, false><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, w, sh.k, st, dinv, b, cur, oth, om, fz); ::sghsc::note_launch(); }
+      { const Shape f_ = fit(h, sh, k_jacobi<T, false>); k_jacobi<T, false><<<f_.grid, f_.bdim, 0, s>>>(G.nx, G.ny, wp, f_.k, st, dinv, b, cur, oth, om, fz); ::sghsc::note_launch(); }
       std::swap(cur, oth);
     }
   }
   T* cb = (T*)iw.cb[g + 1];
-  { k_resid_restrict<T><<<shc.grid, shc.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, w, shc.k, st, b, cur, cb, iw.done); ::sghsc::note_launch(); }
+  SG_TRY(launch_resid_restrict<T>(h, G, C, wp, st, b, cur, cb, iw.done, s));
   const T* xc = nullptr;
-  SG_TRY(vcycle<T>(h, iw, g + 1, cb, (T*)iw.cx[g + 1], (T*)iw.cxt[g + 1], w, o, s, nullptr, &xc));
+  SG_TRY(vcycle<T>(h, iw, g + 1, cb, (T*)iw.cx[g + 1], (T*)iw.cxt[g + 1], wp, o, s, nullptr, &xc));
   if (o.nu == 1 && fdot) {
-    { k_prolong_jacobi<T, true><<<shd.grid, shd.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, w, sh.k, st, dinv, b, cur, xc, oth, om, *fdot); ::sghsc::note_launch(); }
+    { k_prolong_jacobi<T, true><<<shd.grid, shd.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, wp, shd.k, st, dinv, b, cur, xc, oth, om, *fdot); ::sghsc::note_launch(); }
   } else {
-    { k_prolong_jacobi<T, false><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, w, sh.k, st, dinv, b, cur, xc, oth, om, fz); ::sghsc::note_launch(); }
+    { const Shape f_ = fit(h, sh, k_prolong_jacobi<T, false>); k_prolong_jacobi<T, false><<<f_.grid, f_.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, wp, f_.k, st, dinv, b, cur, xc, oth, om, fz); ::sghsc::note_launch(); }
   }
   std::swap(cur, oth);
   for (int it = 1; it < o.nu; ++it) {
     if (it == o.nu - 1 && fdot) {
-      { k_jacobi<T, true><<<shd.grid, shd.bdim, 0, s>>>(G.nx, G.ny, w, sh.k, st, dinv, b, cur, oth, om, *fdot); ::sghsc::note_launch(); }
+      { k_jacobi<T, true><<<shd.grid, shd.bdim, 0, s>>>(G.nx, G.ny, wp, shd.k, st, dinv, b, cur, oth, om, *fdot); ::sghsc::note_launch(); }
     } else {
-      { k_jacobi<T, false><<<sh.grid, sh.bdim, 0, s>>>(G.nx, G.ny, w, sh.k, st, dinv, b, cur, oth, om, fz); ::sghsc::note_launch(); }
+      { const Shape f_ = fit(h, sh, k_jacobi<T, false>); k_jacobi<T, false><<<f_.grid, f_.bdim, 0, s>>>(G.nx, G.ny, wp, f_.k, st, dinv, b, cur, oth, om, fz); ::sghsc::note_launch(); }
     }
     std::swap(cur, oth);
   }
@@ -921,10 +1203,12 @@ static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, 
 template <typename T>
 static int inner_solve_t(sg_problem* h, const void* src, int ld_src, int src_t, void* dst, int ld_dst, int dst_t,
                          int w, const sg_prec_opts& o, cudaStream_t s) {
+  constexpr int N = VW<T>::N;
   InnerWork& iw = sizeof(T) == 8 ? h->iw64 : h->iw32;
   const GridLevel& G = h->grids[0];
-  const Shape sh = make_shape(h, G.n, w, 1);    // gather / matvec / update end in reductions
-  const Shape shs = make_shape(h, G.n, w);
+  const int wp = padded_width<T>(w), ng = wp / N;
+  const Shape sh = make_shape(h, G.n, ng, 1);    // gather / matvec / update end in reductions
+  const Shape shs = make_shape(h, G.n, ng);
   T* x = (T*)iw.x;
   T* r = (T*)iw.r;
   T* q = (T*)iw.q;
@@ -932,19 +1216,15 @@ static int inner_solve_t(sg_problem* h, const void* src, int ld_src, int src_t, 
   T* pB = (T*)iw.pB;
   const T* st = sizeof(T) == 8 ? (const T*)G.st64 : (const T*)G.st32;
   FinArgs fa = make_fin(h, iw, o);
-  // the iterate lives in the destination itself when the element types agree
-  const bool direct = dst_t == (sizeof(T) == 8 ? SG_F64 : SG_F32);
-  T* xd = direct ? (T*)dst : x;
-  const int ldx = direct ? ld_dst : w;
   auto pre = [&](cudaStream_t ps, const LoopCtl& lc) -> int {
     FinArgs f = fa;
     f.cond = lc.cond;
     f.has_cond = lc.has_cond;
     f.flag = lc.flag;
     if (src_t == SG_F64)
-      { k_gather<double, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, sh.k, (const double*)src, ld_src, r, xd, ldx, f); ::sghsc::note_launch(); }
+      { k_gather<double, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, wp, sh.k, (const double*)src, ld_src, r, x, f); ::sghsc::note_launch(); }
     else
-      { k_gather<float, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, sh.k, (const float*)src, ld_src, r, xd, ldx, f); ::sghsc::note_launch(); }
+      { k_gather<float, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, wp, sh.k, (const float*)src, ld_src, r, x, f); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
@@ -954,20 +1234,18 @@ static int inner_solve_t(sg_problem* h, const void* src, int ld_src, int src_t, 
     f.has_cond = lc.has_cond;
     f.flag = lc.flag;
     const T* z = nullptr;
-    SG_TRY(vcycle<T>(h, iw, 0, r, (T*)iw.z, (T*)iw.zt, w, o, bs, &f, &z));
-    { k_matvec_p<T><<<sh.grid, sh.bdim, 0, bs>>>(G.nx, G.ny, w, sh.k, st, z, pA, pB, q, f); ::sghsc::note_launch(); }
-    { k_update_xr<T><<<sh.grid, sh.bdim, 0, bs>>>(G.n, w, sh.k, pA, pB, q, xd, ldx, r, f); ::sghsc::note_launch(); }
+    SG_TRY(vcycle<T>(h, iw, 0, r, (T*)iw.z, (T*)iw.zt, wp, o, bs, &f, &z));
+    { k_matvec_p<T><<<sh.grid, sh.bdim, 0, bs>>>(G.nx, G.ny, wp, sh.k, st, z, pA, pB, q, f); ::sghsc::note_launch(); }
+    { k_update_xr<T><<<sh.grid, sh.bdim, 0, bs>>>(G.n, wp, sh.k, pA, pB, q, x, r, f); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
   SG_TRY(capture_while(h, s, pre, body));
-  if (!direct) {
-    if (dst_t == SG_F64)
-      { k_scatter<T, double><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, shs.k, x, (double*)dst, ld_dst); ::sghsc::note_launch(); }
-    else
-      { k_scatter<T, float><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, shs.k, x, (float*)dst, ld_dst); ::sghsc::note_launch(); }
-    SG_CHECK_LAUNCH();
-  }
+  if (dst_t == SG_F64)
+    { k_scatter<T, double><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, wp, shs.k, x, (double*)dst, ld_dst); ::sghsc::note_launch(); }
+  else
+    { k_scatter<T, float><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, wp, shs.k, x, (float*)dst, ld_dst); ::sghsc::note_launch(); }
+  SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
@@ -980,25 +1258,31 @@ int inner_solve(sg_problem* h, int dtype, const void* src, int ld_src, int src_t
   return inner_solve_t<float>(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);
 }
 
+// One V-cycle on the packed n x w block B into the packed block X: B is
+// packed into the padded workspace, the cycle runs there, the result is
+// unpacked into X.
+template <typename T>
+static int vcycle_packed(sg_problem* h, InnerWork& iw, const T* B, T* bpad, T* X, int w, const sg_prec_opts& o,
+                         cudaStream_t s) {
+  constexpr int N = VW<T>::N;
+  const GridLevel& G = h->grids[0];
+  const int wp = padded_width<T>(w);
+  const Shape sh = make_shape(h, G.n, wp / N);
+  { k_pack<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, B, w, bpad); ::sghsc::note_launch(); }
+  const T* res = nullptr;
+  SG_TRY(vcycle<T>(h, iw, 0, bpad, (T*)iw.z, (T*)iw.zt, wp, o, s, nullptr, &res));
+  { k_scatter<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, res, X, w); ::sghsc::note_launch(); }
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
 int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const sg_prec_opts& o, cudaStream_t s) {
   SG_TRY(check_prec_opts(o));
   SG_TRY(ensure_inner_work(h, dtype, std::max(w, h->wmax)));
-  const size_t es = dtype == SG_F64 ? 8 : 4;
   InnerWork& iw = dtype == SG_F64 ? h->iw64 : h->iw32;
-  { k_clear_done<<<1, 1024, 0, s>>>(w, iw.done); ::sghsc::note_launch(); }
-  const void* res = nullptr;
-  if (dtype == SG_F64) {
-    const double* r = nullptr;
-    SG_TRY(vcycle<double>(h, iw, 0, (const double*)B, (double*)iw.z, (double*)iw.zt, w, o, s, nullptr, &r));
-    res = r;
-  } else {
-    const float* r = nullptr;
-    SG_TRY(vcycle<float>(h, iw, 0, (const float*)B, (float*)iw.z, (float*)iw.zt, w, o, s, nullptr, &r));
-    res = r;
-  }
-  SG_CHECK_LAUNCH();
-  SG_TRY_CUDA(cudaMemcpyAsync(X, res, (size_t)h->grids[0].n * w * es, cudaMemcpyDeviceToDevice, s));
-  return SG_OK;
+  { k_clear_done<<<1, 1024, 0, s>>>(iw.wcap, iw.done); ::sghsc::note_launch(); }
+  if (dtype == SG_F64) return vcycle_packed<double>(h, iw, (const double*)B, (double*)iw.r, (double*)X, w, o, s);
+  return vcycle_packed<float>(h, iw, (const float*)B, (float*)iw.r, (float*)X, w, o, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1041,12 +1325,13 @@ static int static_scratch(void** out) {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Bytes of V-cycle scratch for w columns: the done mask, two iterates on the
-// finest grid and three blocks per coarser grid.
-static size_t static_vcycle_bytes(const sg_problem* h, int w, size_t es) {
-  size_t b = align256((size_t)w * sizeof(int));
-  b += 2 * align256((size_t)h->grids[0].n * w * es);
-  for (size_t g = 1; g < h->grids.size(); ++g) b += 3 * align256((size_t)h->grids[g].n * w * es);
+// Bytes of V-cycle scratch for w columns (padded width wp): the done mask, the
+// packed right-hand side and two iterates on the finest grid, and three blocks
+// per coarser grid.
+static size_t static_vcycle_bytes(const sg_problem* h, int wp, size_t es) {
+  size_t b = align256((size_t)wp * sizeof(int));
+  b += 3 * align256((size_t)h->grids[0].n * wp * es);
+  for (size_t g = 1; g < h->grids.size(); ++g) b += 3 * align256((size_t)h->grids[g].n * wp * es);
   return b;
 }
 
@@ -1057,7 +1342,8 @@ int vcycle_static(sg_problem* h, int dtype, const void* B, void* X, int w, const
     return SG_ERR_UNSUPPORTED;
   }
   const size_t es = dtype == SG_F64 ? 8 : 4;
-  const size_t need = static_vcycle_bytes(h, w, es);
+  const int wp = dtype == SG_F64 ? padded_width<double>(w) : padded_width<float>(w);
+  const size_t need = static_vcycle_bytes(h, wp, es);
   if (need > STATIC_SCRATCH_BYTES) {
     set_error("sg_vcycle_apply_static: %d columns of %d nodes need %zu bytes of scratch, above the fixed %zu",
               w, h->grids[0].n, need, STATIC_SCRATCH_BYTES);
@@ -1067,20 +1353,22 @@ int vcycle_static(sg_problem* h, int dtype, const void* B, void* X, int w, const
   SG_TRY(static_scratch(&base));
   unsigned char* p = (unsigned char*)base;
   InnerWork sw;  // views into the static array; nothing here allocates
-  sw.wcap = w;
+  sw.wcap = wp;
   sw.esize = es;
   sw.done = (int*)p;
-  p += align256((size_t)w * sizeof(int));
+  p += align256((size_t)wp * sizeof(int));
+  sw.r = p;
+  p += align256((size_t)h->grids[0].n * wp * es);
   sw.z = p;
-  p += align256((size_t)h->grids[0].n * w * es);
+  p += align256((size_t)h->grids[0].n * wp * es);
   sw.zt = p;
-  p += align256((size_t)h->grids[0].n * w * es);
+  p += align256((size_t)h->grids[0].n * wp * es);
   const int G = (int)h->grids.size();
   sw.cb.assign(G, nullptr);
   sw.cx.assign(G, nullptr);
   sw.cxt.assign(G, nullptr);
   for (int g = 1; g < G; ++g) {
-    const size_t bytes = align256((size_t)h->grids[g].n * w * es);
+    const size_t bytes = align256((size_t)h->grids[g].n * wp * es);
     sw.cb[g] = p;
     p += bytes;
     sw.cx[g] = p;
@@ -1089,20 +1377,9 @@ int vcycle_static(sg_problem* h, int dtype, const void* B, void* X, int w, const
     p += bytes;
   }
   // the kernels skip columns whose done flag is set: start from all zero
-  SG_TRY_CUDA(cudaMemsetAsync(sw.done, 0, (size_t)w * sizeof(int), s));
-  const void* res = nullptr;
-  if (dtype == SG_F64) {
-    const double* r = nullptr;
-    SG_TRY(vcycle<double>(h, sw, 0, (const double*)B, (double*)sw.z, (double*)sw.zt, w, o, s, nullptr, &r));
-    res = r;
-  } else {
-    const float* r = nullptr;
-    SG_TRY(vcycle<float>(h, sw, 0, (const float*)B, (float*)sw.z, (float*)sw.zt, w, o, s, nullptr, &r));
-    res = r;
-  }
-  SG_CHECK_LAUNCH();
-  SG_TRY_CUDA(cudaMemcpyAsync(X, res, (size_t)h->grids[0].n * w * es, cudaMemcpyDeviceToDevice, s));
-  return SG_OK;
+  SG_TRY_CUDA(cudaMemsetAsync(sw.done, 0, (size_t)wp * sizeof(int), s));
+  if (dtype == SG_F64) return vcycle_packed<double>(h, sw, (const double*)B, (double*)sw.r, (double*)X, w, o, s);
+  return vcycle_packed<float>(h, sw, (const float*)B, (float*)sw.r, (float*)X, w, o, s);
 }
 
 }  // namespace sghsc
