@@ -664,24 +664,27 @@ struct CoarseGrids {
 // grids are latency-bound, so the work spreads over as many SMs as there are
 // columns), entirely in shared memory: per grid a right-hand side, an iterate
 // and a ping-pong buffer, plus every coarse stencil and inverse diagonal
-// (staged once per block with independent loads in flight). Grids of at most
+// (staged once per block by asynchronous copies, all in flight together). Grids of at most
 // 64 nodes are run by warp 0 alone with warp-level synchronisation.
+// Asynchronous global -> shared copy of one element (cp.async, completed by
+// cp_async_wait_all); all of a block's copies are in flight together.
 template <typename T>
-__device__ __forceinline__ void stage_copy(T* __restrict__ dst, const T* __restrict__ src, int count) {
-  constexpr int U = 8;
-  for (int base = 0; base < count; base += U * (int)blockDim.x) {
-    T v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * blockDim.x + threadIdx.x;
-      v[u] = idx < count ? src[idx] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * blockDim.x + threadIdx.x;
-      if (idx < count) dst[idx] = v[u];
-    }
-  }
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_async(T* __restrict__ dst, const T* __restrict__ src, int count) {
+  for (int idx = threadIdx.x; idx < count; idx += blockDim.x) cp_async_elem(dst + idx, src + idx);
 }
 
 template <typename T>
@@ -697,8 +700,8 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, 
   const int tid = threadIdx.x;
   for (int g = L.g0; g < L.G; ++g) {
     const int n = L.nx[g] * L.ny[g];
-    stage_copy(sst + 9 * L.off[g], (const T*)L.st[g], 9 * n);
-    stage_copy(sdi + L.off[g], (const T*)L.dinv[g], n);
+    stage_async(sst + 9 * L.off[g], (const T*)L.st[g], 9 * n);
+    stage_async(sdi + L.off[g], (const T*)L.dinv[g], n);
   }
   auto B = [&](int g) { return sm + 3 * L.off[g]; };
   auto Xa = [&](int g) { return sm + 3 * L.off[g] + L.nx[g] * L.ny[g]; };
@@ -724,8 +727,9 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, 
   {
     const int n0 = L.nx[L.g0] * L.ny[L.g0];
     T* b0 = B(L.g0);
-    for (int idx = tid; idx < n0; idx += blockDim.x) b0[idx] = bg[idx * wp + col];
+    for (int idx = tid; idx < n0; idx += blockDim.x) cp_async_elem(b0 + idx, bg + idx * wp + col);
   }
+  cp_async_wait_all();   // stencils, diagonals and the right-hand side
   __syncthreads();
   T* cur[MAX_LEVELS];
   T* oth[MAX_LEVELS];

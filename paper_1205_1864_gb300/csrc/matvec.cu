@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) k_block_matvec(
       __syncthreads();
       for (int idx = threadIdx.x; idx < nzc * wx; idx += blockDim.x) {
         const int e = idx / wx, j = idx - e * wx;
-        Xs[idx] = (TAcc)X[(size_t)colidx[cs + e] * ldx + j];
+        Xs[idx] = widen<TAcc>(X[(size_t)colidx[cs + e] * ldx + j]);
       }
       for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
       __syncthreads();
@@ -82,9 +82,11 @@ __global__ void __launch_bounds__(256) k_block_matvec(
   }
 }
 
-// Outer CG step: p_new = z + beta p_old (p_new = z on the first iteration)
-// staged on the fly, q = A p_new, p_new written for the block's own rows,
-// p_new . q reduced and alpha = rho / (p_new . q) set by the last block.
+// Outer CG step: p_new = z + beta p_old (p_new = z on the first iteration),
+// q = A p_new formed as A z + beta q_old (linearity: z is staged as it is, so
+// the FP64 update is done once per output rather than once per staged
+// neighbour), p_new and q written for the block's own rows, p_new . q reduced
+// and alpha = rho / (p_new . q) set by the last block.
 template <int MAXO>
 __global__ void __launch_bounds__(256) k_outer_matvec(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const double* __restrict__ vals,
@@ -110,8 +112,7 @@ __global__ void __launch_bounds__(256) k_outer_matvec(
       __syncthreads();
       for (int idx = threadIdx.x; idx < nzc * P; idx += blockDim.x) {
         const int e = idx / P, j = idx - e * P;
-        const size_t g = (size_t)colidx[cs + e] * P + j;
-        Xs[idx] = first ? z[g] : z[g] + beta * pold[g];
+        Xs[idx] = z[(size_t)colidx[cs + e] * P + j];
       }
       for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
       __syncthreads();
@@ -123,9 +124,10 @@ __global__ void __launch_bounds__(256) k_outer_matvec(
       if (l < P) {
         const size_t g = (size_t)r * P + l;
         const double pv = first ? z[g] : z[g] + beta * pold[g];
+        const double qv = first ? acc[i] : acc[i] + beta * q[g];
         pnew[g] = pv;
-        q[g] = acc[i];
-        dot += pv * acc[i];
+        q[g] = qv;
+        dot += pv * qv;
       }
     }
   }

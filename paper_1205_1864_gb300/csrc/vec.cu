@@ -15,7 +15,7 @@ __global__ void k_cast(const TS* __restrict__ src, int lds, TD* __restrict__ dst
   const long long total = (long long)rows * cols;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / cols), c = (int)(i - (long long)r * cols);
-    dst[(size_t)r * ldd + c] = (TD)src[(size_t)r * lds + c];
+    dst[(size_t)r * ldd + c] = widen<TD>(src[(size_t)r * lds + c]);
   }
 }
 

@@ -77,6 +77,26 @@ __device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const Ou
 }
 
 
+// Exact FP32 -> FP64 conversion from the IEEE-754 layouts (sign kept,
+// exponent rebiased by 1023 - 127, mantissa shifted into the top bits), on the
+// integer pipe; subnormal inputs take the hardware conversion. The FP64 pipe
+// of this GPU is narrow, and the hardware conversion issues there.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  if (e == 0u && m != 0u) return (double)f;
+  const unsigned ed = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+  const unsigned hi = (u & 0x80000000u) | (ed << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+
+// v converted to TD; float -> double through f2d_bits.
+template <typename TD, typename TS>
+__device__ __forceinline__ TD widen(TS v) {
+  if constexpr (sizeof(TD) == 8 && sizeof(TS) == 4) return f2d_bits(v);
+  else return (TD)v;
+}
+
 int vec_grid(long long N);
 
 // The outer CG step q = A p_new with p_new = z + beta p_old staged on the fly
