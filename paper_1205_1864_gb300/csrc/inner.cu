@@ -38,6 +38,7 @@
 
 #include "graph.cuh"
 #include "sghsc_internal.cuh"
+#include "vec.cuh"
 
 namespace sghsc {
 
@@ -142,6 +143,8 @@ static int padded_width(int w) {
 
 enum { FIN_INIT = 0, FIN_RHO = 1, FIN_ALPHA = 2, FIN_CONV = 3 };
 
+// Per-column CG state (global memory; the last block of each reduction
+// updates it) and the reduction target.
 struct FinArgs {
   void* part;        // block partials [nblk][ldp] in the solver's accumulation type
   int ldp;
@@ -156,13 +159,24 @@ struct FinArgs {
   int has_cond;
   int* flag;
   long long* iacc;  // running [total, max] of per-column iteration counts
+  int count_iacc;   // this block adds finished columns to iacc
 };
 
-// Thread t of a block: column group t mod ng, node slice t / ng.
-__device__ __forceinline__ void thread_pos(int ng, int k, int& cg, int& node0, int& nstep) {
+// The blocks doing one phase: this block's index and their number.
+struct Blk {
+  int bid, nb;
+};
+
+__device__ __forceinline__ Blk this_grid() { return Blk{(int)blockIdx.x, (int)gridDim.x}; }
+
+// Thread t of a block: column group t mod ng, node slice t / ng; false for
+// threads past k*ng (blocks wider than the phase needs).
+__device__ __forceinline__ bool thread_pos(int ng, int k, Blk B, int& cg, int& node0, int& nstep) {
+  if ((int)threadIdx.x >= k * ng) return false;
   cg = threadIdx.x % ng;
-  node0 = blockIdx.x * k + threadIdx.x / ng;
-  nstep = gridDim.x * k;
+  node0 = B.bid * k + threadIdx.x / ng;
+  nstep = B.nb * k;
+  return true;
 }
 
 // Lanes of this thread's warp that exist (the last warp of a block whose size
@@ -189,14 +203,16 @@ __device__ __forceinline__ A group_shfl_sum(A s, int g) {
 
 // Per-column block partial: thread (slice, cg) holds columns cg*N .. cg*N+N-1;
 // the k slices of each column are summed in the accumulation type A in a fixed
-// order and stored (block-major, leading dimension ldp).
+// order and stored at part[bid][c] (leading dimension ldp).
 template <typename A, int N>
-__device__ __forceinline__ void block_col_reduce(const A (&v)[N], int wp, int k, A* part, int ldp) {
-  __shared__ A red[4096];
+__device__ __forceinline__ void block_col_reduce(const A (&v)[N], int wp, int k, A* part, int ldp, int bid) {
+  __shared__ A red[4096 / (sizeof(A) / 4)];   // k * wp <= 1024 * N elements
   const int ng = wp / N;
-  const int cg = threadIdx.x % ng, slice = threadIdx.x / ng;
+  if ((int)threadIdx.x < k * ng) {
+    const int cg = threadIdx.x % ng, slice = threadIdx.x / ng;
 #pragma unroll
-  for (int u = 0; u < N; ++u) red[slice * wp + cg * N + u] = v[u];
+    for (int u = 0; u < N; ++u) red[slice * wp + cg * N + u] = v[u];
+  }
   __syncthreads();
   const int g = group_lanes(wp);
   const int per_pass = blockDim.x / g;
@@ -208,7 +224,7 @@ __device__ __forceinline__ void block_col_reduce(const A (&v)[N], int wp, int k,
       for (int j = lane; j < k; j += g) s += red[j * wp + c];
     s = group_shfl_sum(s, g);
     if (c < wp && lane == 0) {
-      part[(size_t)blockIdx.x * ldp + c] = s;
+      part[(size_t)bid * ldp + c] = s;
       __threadfence();  // only the writers of partials need the release fence
     }
   }
@@ -228,18 +244,12 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
   return last;
 }
 
-// Column-wise CG scalar updates from the block partials (last block only).
-// Column c is summed by a lane group in the accumulation type A (blocks lane,
-// lane + g, ... loaded 16 at a time, then the g-wide shuffle);
-// the column totals go through shared memory to threads 0..wp-1, which update
-// the scalars in FP64 (so only the first ceil(wp/32) warps issue FP64 work).
-// The order is fixed, so results are reproducible.
+// Column totals of the block partials into colsum[0..wp). Column c is summed
+// by a lane group in the accumulation type A (blocks lane, lane + g, ...
+// loaded 16 at a time, then the g-wide shuffle): a fixed order, so every
+// caller gets the same bits. Ends with a block barrier.
 template <typename A>
-__device__ void fin_columns(const FinArgs& f, int op, int wp, int nblk) {
-  __shared__ int cnt;
-  __shared__ double colsum[1024];
-  if (threadIdx.x == 0) cnt = 0;
-  const A* part = (const A*)f.part;
+__device__ void col_totals(const A* part, int ldp, int nblk, int wp, double* colsum) {
   const int g = group_lanes(wp);
   const int per_pass = blockDim.x / g;
   const int lane = threadIdx.x % g;
@@ -247,14 +257,13 @@ __device__ void fin_columns(const FinArgs& f, int op, int wp, int nblk) {
     const int gc = c0 + (int)threadIdx.x / g;
     A s = A(0);
     if (gc < wp) {
-      // 16 independent loads in flight per lane, summed in block order
       constexpr int B = 16;
       for (int b0 = lane; b0 < nblk; b0 += B * g) {
         A v[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) {
           const int b = b0 + u * g;
-          v[u] = b < nblk ? __ldcg(&part[(size_t)b * f.ldp + gc]) : A(0);
+          v[u] = b < nblk ? __ldcg(&part[(size_t)b * ldp + gc]) : A(0);
         }
 #pragma unroll
         for (int u = 0; u < B; ++u) s += v[u];
@@ -264,6 +273,12 @@ __device__ void fin_columns(const FinArgs& f, int op, int wp, int nblk) {
     if (gc < wp && lane == 0) colsum[gc] = (double)s;
   }
   __syncthreads();
+}
+
+// The CG scalar updates of every column from its total colsum[c], done by
+// threads 0..wp-1 in FP64 (so only the first ceil(wp/32) warps issue FP64
+// work); *cnt (zeroed by the caller before a barrier) counts the columns left.
+__device__ void col_update(const FinArgs& f, int op, int wp, const double* colsum, int* cnt) {
   for (int c = threadIdx.x; c < wp; c += blockDim.x) {
     const double s = colsum[c];
     if (op == FIN_INIT) {
@@ -305,14 +320,25 @@ __device__ void fin_columns(const FinArgs& f, int op, int wp, int nblk) {
           atomicOr(f.status, ST_INNER_NOT_SPD);
         }
         f.done[c] = fin;
-        if (fin) {
+        if (fin && f.count_iacc) {
           atomicAdd((unsigned long long*)&f.iacc[0], (unsigned long long)it);
           atomicMax(&f.iacc[1], (long long)it);
         }
       }
     }
-    if (!f.done[c]) atomicAdd(&cnt, 1);
+    if (!f.done[c]) atomicAdd(cnt, 1);
   }
+}
+
+// Last block of a stand-alone reduction kernel: totals, scalar updates, the
+// iteration counter and the loop condition of the graph WHILE node.
+template <typename A>
+__device__ void fin_columns(const FinArgs& f, int op, int wp, int nblk) {
+  __shared__ int cnt;
+  __shared__ double colsum[1024];
+  if (threadIdx.x == 0) cnt = 0;
+  col_totals<A>((const A*)f.part, f.ldp, nblk, wp, colsum);
+  col_update(f, op, wp, colsum, &cnt);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (op == FIN_INIT) f.ctl->it = 0;
@@ -328,13 +354,13 @@ __device__ void fin_columns(const FinArgs& f, int op, int wp, int nblk) {
 
 template <typename A, int N>
 __device__ __forceinline__ void reduce_finalize(const FinArgs& f, const A (&v)[N], int wp, int k, int op) {
-  block_col_reduce<A, N>(v, wp, k, (A*)f.part, f.ldp);
+  block_col_reduce<A, N>(v, wp, k, (A*)f.part, f.ldp, blockIdx.x);
   if (last_block(&f.ctl->ticket)) fin_columns<A>(f, op, wp, gridDim.x);
 }
 
 // (P xc) at fine node (fx, fy): bilinear interpolation from the coarse grid,
 // coarse node (X, Y) sitting on fine node (2X+1, 2Y+1), zero outside
-// (one column, used by the coarse-grid kernel).
+// (one column, used by the coarse-grid phase).
 template <typename T>
 __device__ __forceinline__ T prolong_at(int fx, int fy, int nxc, int nyc, const T* __restrict__ xc) {
   int Xs[2], Ys[2];
@@ -412,16 +438,18 @@ __device__ __forceinline__ Vec<T> stencil9(const T* __restrict__ s9, int i, int 
   return acc;
 }
 
-// ---------------------------------------------------------------- V-cycle ---
+// ---------------------------------------------------------------- phases ---
+// Each phase is the body of one stand-alone kernel, over the blocks B; the
+// reduction phases return the thread's per-column partial sums in acc.
 
 // one sweep from zero: x = omega D^{-1} b
 template <typename T>
-__global__ void __launch_bounds__(1024) k_smooth0(int n, int wp, int k, const T* __restrict__ dinv,
-                                                  const T* __restrict__ b, T* __restrict__ x, T om,
-                                                  const int* __restrict__ done) {
+__device__ __forceinline__ void ph_smooth0(Blk B, int n, int wp, int k, const T* __restrict__ dinv,
+                                           const T* __restrict__ b, T* __restrict__ x, T om,
+                                           const int* __restrict__ done) {
   constexpr int N = VW<T>::N;
   int cg, node, nstep;
-  thread_pos(wp / N, k, cg, node, nstep);
+  if (!thread_pos(wp / N, k, B, cg, node, nstep)) return;
   const int c0 = cg * N;
   if (done_mask<N>(done, c0) == (1u << N) - 1) return;
   for (; node < n; node += nstep) {
@@ -437,12 +465,12 @@ __global__ void __launch_bounds__(1024) k_smooth0(int n, int wp, int k, const T*
 
 // two sweeps from zero: x1 = omega D^{-1} b, x2 = x1 + omega D^{-1} (b - A x1)
 template <typename T>
-__global__ void __launch_bounds__(1024) k_smooth00(int nx, int ny, int wp, int k, const T* __restrict__ st,
-                                                   const T* __restrict__ dinv, const T* __restrict__ b,
-                                                   T* __restrict__ x, T om, const int* __restrict__ done) {
+__device__ __forceinline__ void ph_smooth00(Blk B, int nx, int ny, int wp, int k, const T* __restrict__ st,
+                                            const T* __restrict__ dinv, const T* __restrict__ b,
+                                            T* __restrict__ x, T om, const int* __restrict__ done) {
   constexpr int N = VW<T>::N;
   int cg, node0, nstep;
-  thread_pos(wp / N, k, cg, node0, nstep);
+  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
   const int c0 = cg * N;
   if (done_mask<N>(done, c0) == (1u << N) - 1) return;
   const int n = nx * ny, rs = nx * wp;
@@ -464,58 +492,54 @@ __global__ void __launch_bounds__(1024) k_smooth00(int nx, int ny, int wp, int k
   }
 }
 
-// xo = xi + omega D^{-1} (b - A xi); with DOT also the partials of b . xo and FIN_RHO
+// xo = xi + omega D^{-1} (b - A xi); with DOT also the partials of b . xo
 template <typename T, bool DOT>
-__global__ void __launch_bounds__(1024) k_jacobi(int nx, int ny, int wp, int k, const T* __restrict__ st,
-                                                 const T* __restrict__ dinv, const T* __restrict__ b,
-                                                 const T* __restrict__ xi, T* __restrict__ xo, T om, FinArgs f) {
+__device__ __forceinline__ void ph_jacobi(Blk B, int nx, int ny, int wp, int k, const T* __restrict__ st,
+                                          const T* __restrict__ dinv, const T* __restrict__ b,
+                                          const T* __restrict__ xi, T* __restrict__ xo, T om,
+                                          const int* __restrict__ done, T (&acc)[VW<T>::N]) {
   constexpr int N = VW<T>::N;
-  using A = T;
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = T(0);
   int cg, node0, nstep;
-  thread_pos(wp / N, k, cg, node0, nstep);
+  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
   const int c0 = cg * N;
-  A acc[N];
+  if (done_mask<N>(done, c0) == (1u << N) - 1) return;
+  const int n = nx * ny, rs = nx * wp;
+  for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+    const int i = it.node * wp + c0;
+    const Vec<T> ax = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
+                               [&](int e, int) { return vld(xi + e); });
+    const Vec<T> bv = vld(b + i), xv = vld(xi + i);
+    const T d = om * dinv[it.node];
+    Vec<T> v;
 #pragma unroll
-  for (int u = 0; u < N; ++u) acc[u] = A(0);
-  if (done_mask<N>(f.done, c0) != (1u << N) - 1) {
-    const int n = nx * ny, rs = nx * wp;
-    for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
-      const int i = it.node * wp + c0;
-      const Vec<T> ax = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
-                                 [&](int e, int) { return vld(xi + e); });
-      const Vec<T> bv = vld(b + i), xv = vld(xi + i);
-      const T d = om * dinv[it.node];
-      Vec<T> v;
-#pragma unroll
-      for (int u = 0; u < N; ++u) {
-        v.a[u] = xv.a[u] + d * (bv.a[u] - ax.a[u]);
-        if (DOT) acc[u] += bv.a[u] * v.a[u];
-      }
-      vst(xo + i, v);
+    for (int u = 0; u < N; ++u) {
+      v.a[u] = xv.a[u] + d * (bv.a[u] - ax.a[u]);
+      if (DOT) acc[u] += bv.a[u] * v.a[u];
     }
+    vst(xo + i, v);
   }
-  if (DOT) reduce_finalize<A, N>(f, acc, wp, k, FIN_RHO);
 }
 
 // bc = P^T (b - A x), tiled: a block owns a TC x TC tile of coarse nodes. Its
 // threads first form the fine residuals b - A x of the tile's (2TC+1)^2 fine
-// footprint once each, for every column group, into shared memory; each coarse
-// node then sums its 3x3 weighted fine residuals from there. Grid-stride over
-// the tiles.
+// footprint once each, for every column group, into shared memory (res); each
+// coarse node then sums its 3x3 weighted fine residuals from there. The blocks
+// stride over the tiles.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_resid_restrict_t(int nxf, int nyf, int nxc, int nyc, int wp, int TC,
-                                                           const T* __restrict__ st, const T* __restrict__ b,
-                                                           const T* __restrict__ x, T* __restrict__ bc,
-                                                           const int* __restrict__ done) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void ph_resid_restrict(Blk B, int nxf, int nyf, int nxc, int nyc, int wp, int TC,
+                                                  const T* __restrict__ st, const T* __restrict__ b,
+                                                  const T* __restrict__ x, T* __restrict__ bc,
+                                                  const int* __restrict__ done, unsigned char* smem) {
   constexpr int N = VW<T>::N;
   using V = typename VW<T>::type;
-  V* res = reinterpret_cast<V*>(smem_raw);   // [fine footprint node][column group]
+  V* res = reinterpret_cast<V*>(smem);   // [fine footprint node][column group]
   const int ng = wp / N;
   const int ntx = (nxc + TC - 1) / TC, nty = (nyc + TC - 1) / TC;
   const int FW = 2 * TC + 1;
   const int rsf = nxf * wp;
-  for (int t = blockIdx.x; t < ntx * nty; t += gridDim.x) {
+  for (int t = B.bid; t < ntx * nty; t += B.nb) {
     const int X0 = (t % ntx) * TC, Y0 = (t / ntx) * TC;
     const int fx0 = 2 * X0, fy0 = 2 * Y0;
     for (int idx = threadIdx.x; idx < FW * FW * ng; idx += blockDim.x) {
@@ -558,7 +582,7 @@ __global__ void __launch_bounds__(1024) k_resid_restrict_t(int nxf, int nyf, int
   }
 }
 
-// x' = x + P xc (on the fly), xo = x' + omega D^{-1} (b - A x'); DOT as k_jacobi.
+// x' = x + P xc (on the fly), xo = x' + omega D^{-1} (b - A x'); DOT as ph_jacobi.
 // The coarse values that the 3x3 fine neighbourhood of node (x, y) interpolates
 // from lie in the 3x3 coarse patch cp[a][c], X = Xb - 1 + c, Xb = floor((x-1)/2)
 // (same in y). Interpolation is separable: fine offset dx in {-1, 0, 1} takes
@@ -569,88 +593,84 @@ __global__ void __launch_bounds__(1024) k_resid_restrict_t(int nxf, int nyf, int
 // weights K = Wy^T S Wx (S the 3x3 stencil, zero outside the grid), shared by
 // all columns, and (P xc) at the node itself uses Wy[0] (x) Wx[0] (centre rows).
 template <typename T, bool DOT>
-__global__ void __launch_bounds__(1024) k_prolong_jacobi(int nxf, int nyf, int nxc, int nyc, int wp, int k,
-                                                         const T* __restrict__ st, const T* __restrict__ dinv,
-                                                         const T* __restrict__ b, const T* __restrict__ x,
-                                                         const T* __restrict__ xc, T* __restrict__ xo, T om,
-                                                         FinArgs f) {
+__device__ __forceinline__ void ph_prolong_jacobi(Blk B, int nxf, int nyf, int nxc, int nyc, int wp, int k,
+                                                  const T* __restrict__ st, const T* __restrict__ dinv,
+                                                  const T* __restrict__ b, const T* __restrict__ x,
+                                                  const T* __restrict__ xc, T* __restrict__ xo, T om,
+                                                  const int* __restrict__ done, T (&acc)[VW<T>::N]) {
   constexpr int N = VW<T>::N;
-  using A = T;
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = T(0);
   int cg, node0, nstep;
-  thread_pos(wp / N, k, cg, node0, nstep);
+  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
   const int c0 = cg * N;
-  A acc[N];
+  if (done_mask<N>(done, c0) == (1u << N) - 1) return;
+  const int n = nxf * nyf, rs = nxf * wp;
+  const T h = T(0.5);
+  for (NodeIter it(node0, nstep, nxf); it.node < n; it.next()) {
+    const T* s9 = st + it.node * 9;
+    // separable interpolation weights by parity (rows: offset -1, 0, +1; columns: patch 0..2)
+    T wxm[3][3], wym[3][3];
+    const bool ox = it.x & 1, oy = it.y & 1;
 #pragma unroll
-  for (int u = 0; u < N; ++u) acc[u] = A(0);
-  if (done_mask<N>(f.done, c0) != (1u << N) - 1) {
-    const int n = nxf * nyf, rs = nxf * wp;
-    const T h = T(0.5);
-    for (NodeIter it(node0, nstep, nxf); it.node < n; it.next()) {
-      const T* s9 = st + it.node * 9;
-      // separable interpolation weights by parity (rows: offset -1, 0, +1; columns: patch 0..2)
-      T wxm[3][3], wym[3][3];
-      const bool ox = it.x & 1, oy = it.y & 1;
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) { wxm[d][c] = T(0); wym[d][c] = T(0); }
+    if (ox) { wxm[0][0] = h; wxm[0][1] = h; wxm[1][1] = T(1); wxm[2][1] = h; wxm[2][2] = h; }
+    else { wxm[0][1] = T(1); wxm[1][1] = h; wxm[1][2] = h; wxm[2][2] = T(1); }
+    if (oy) { wym[0][0] = h; wym[0][1] = h; wym[1][1] = T(1); wym[2][1] = h; wym[2][2] = h; }
+    else { wym[0][1] = T(1); wym[1][1] = h; wym[1][2] = h; wym[2][2] = T(1); }
+    // S masked to the grid, T1 = S Wx, K = Wy^T T1
+    T t1[3][3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { wxm[d][c] = T(0); wym[d][c] = T(0); }
-      if (ox) { wxm[0][0] = h; wxm[0][1] = h; wxm[1][1] = T(1); wxm[2][1] = h; wxm[2][2] = h; }
-      else { wxm[0][1] = T(1); wxm[1][1] = h; wxm[1][2] = h; wxm[2][2] = T(1); }
-      if (oy) { wym[0][0] = h; wym[0][1] = h; wym[1][1] = T(1); wym[2][1] = h; wym[2][2] = h; }
-      else { wym[0][1] = T(1); wym[1][1] = h; wym[1][2] = h; wym[2][2] = T(1); }
-      // S masked to the grid, T1 = S Wx, K = Wy^T T1
-      T t1[3][3];
+    for (int dy = 0; dy < 3; ++dy) {
+      const bool iny = it.y + dy - 1 >= 0 && it.y + dy - 1 < nyf;
+      T srow[3];
 #pragma unroll
-      for (int dy = 0; dy < 3; ++dy) {
-        const bool iny = it.y + dy - 1 >= 0 && it.y + dy - 1 < nyf;
-        T srow[3];
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          const bool inx = it.x + dx - 1 >= 0 && it.x + dx - 1 < nxf;
-          srow[dx] = (iny && inx) ? s9[dy * 3 + dx] : T(0);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) t1[dy][c] = srow[0] * wxm[0][c] + srow[1] * wxm[1][c] + srow[2] * wxm[2][c];
+      for (int dx = 0; dx < 3; ++dx) {
+        const bool inx = it.x + dx - 1 >= 0 && it.x + dx - 1 < nxf;
+        srow[dx] = (iny && inx) ? s9[dy * 3 + dx] : T(0);
       }
-      T K[3][3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) t1[dy][c] = srow[0] * wxm[0][c] + srow[1] * wxm[1][c] + srow[2] * wxm[2][c];
+    }
+    T K[3][3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) K[a][c] = wym[0][a] * t1[0][c] + wym[1][a] * t1[1][c] + wym[2][a] * t1[2][c];
-      const int Xb = (it.x - 1) >> 1, Yb = (it.y - 1) >> 1;
-      Vec<T> apc = vzero<T>(), pc = vzero<T>();
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int Y = Yb - 1 + a;
+      for (int c = 0; c < 3; ++c) K[a][c] = wym[0][a] * t1[0][c] + wym[1][a] * t1[1][c] + wym[2][a] * t1[2][c];
+    const int Xb = (it.x - 1) >> 1, Yb = (it.y - 1) >> 1;
+    Vec<T> apc = vzero<T>(), pc = vzero<T>();
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int X = Xb - 1 + c;
-          if (Y >= 0 && Y < nyc && X >= 0 && X < nxc) {
-            const Vec<T> v = vld(xc + (Y * nxc + X) * wp + c0);
-            const T wc = wym[1][a] * wxm[1][c];
+    for (int a = 0; a < 3; ++a) {
+      const int Y = Yb - 1 + a;
 #pragma unroll
-            for (int u = 0; u < N; ++u) {
-              apc.a[u] += K[a][c] * v.a[u];
-              pc.a[u] += wc * v.a[u];
-            }
+      for (int c = 0; c < 3; ++c) {
+        const int X = Xb - 1 + c;
+        if (Y >= 0 && Y < nyc && X >= 0 && X < nxc) {
+          const Vec<T> v = vld(xc + (Y * nxc + X) * wp + c0);
+          const T wc = wym[1][a] * wxm[1][c];
+#pragma unroll
+          for (int u = 0; u < N; ++u) {
+            apc.a[u] += K[a][c] * v.a[u];
+            pc.a[u] += wc * v.a[u];
           }
         }
       }
-      const int i = it.node * wp + c0;
-      const Vec<T> ax = stencil9(s9, i, rs, wp, it.node, it.x, it.y, nxf, nyf,
-                                 [&](int e, int) { return vld(x + e); });
-      const Vec<T> bv = vld(b + i), xv = vld(x + i);
-      const T d = om * dinv[it.node];
-      Vec<T> v;
-#pragma unroll
-      for (int u = 0; u < N; ++u) {
-        v.a[u] = (xv.a[u] + pc.a[u]) + d * (bv.a[u] - (ax.a[u] + apc.a[u]));
-        if (DOT) acc[u] += bv.a[u] * v.a[u];
-      }
-      vst(xo + i, v);
     }
+    const int i = it.node * wp + c0;
+    const Vec<T> ax = stencil9(s9, i, rs, wp, it.node, it.x, it.y, nxf, nyf,
+                               [&](int e, int) { return vld(x + e); });
+    const Vec<T> bv = vld(b + i), xv = vld(x + i);
+    const T d = om * dinv[it.node];
+    Vec<T> v;
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      v.a[u] = (xv.a[u] + pc.a[u]) + d * (bv.a[u] - (ax.a[u] + apc.a[u]));
+      if (DOT) acc[u] += bv.a[u] * v.a[u];
+    }
+    vst(xo + i, v);
   }
-  if (DOT) reduce_finalize<A, N>(f, acc, wp, k, FIN_RHO);
 }
 
 struct CoarseGrids {
@@ -660,12 +680,6 @@ struct CoarseGrids {
   const void* dinv[MAX_LEVELS];
 };
 
-// The V-cycle from grid g0 down, one column per 1024-thread block (the coarse
-// grids are latency-bound, so the work spreads over as many SMs as there are
-// columns), entirely in shared memory: per grid a right-hand side, an iterate
-// and a ping-pong buffer, plus every coarse stencil and inverse diagonal
-// (staged once per block by asynchronous copies, all in flight together). Grids of at most
-// 64 nodes are run by warp 0 alone with warp-level synchronisation.
 // Asynchronous global -> shared copy of one element (cp.async, completed by
 // cp_async_wait_all); all of a block's copies are in flight together.
 template <typename T>
@@ -687,22 +701,29 @@ __device__ __forceinline__ void stage_async(T* __restrict__ dst, const T* __rest
   for (int idx = threadIdx.x; idx < count; idx += blockDim.x) cp_async_elem(dst + idx, src + idx);
 }
 
+// Shared memory of the coarse-grid phase: per grid a right-hand side, an
+// iterate and a ping-pong buffer, plus the stencils and inverse diagonals.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, int wp, const T* __restrict__ bg,
-                                                        T* __restrict__ xg, T om, int nu,
-                                                        const int* __restrict__ done) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+static size_t coarse_smem_bytes(int tot) {
+  return (size_t)13 * tot * sizeof(T);
+}
+
+// The V-cycle from grid g0 down, one column at a time per block (the blocks
+// stride over the columns; the coarse grids are latency-bound, so the work
+// spreads over as many SMs as there are columns), entirely in shared memory.
+// Every coarse stencil and inverse diagonal is staged once per block, with the
+// first column's right-hand side, by asynchronous copies all in flight
+// together. Grids of at most 64 nodes are run by warp 0 alone with warp-level
+// synchronisation. blockDim must be 1024.
+template <typename T>
+__device__ void ph_coarse(Blk Bk, const CoarseGrids& L, int tot, int wp, const T* __restrict__ bg,
+                          T* __restrict__ xg, T om, int nu, const int* __restrict__ done, unsigned char* smem) {
+  T* sm = reinterpret_cast<T*>(smem);
   T* sst = sm + 3 * tot;          // stencils [node][9] of all coarse grids
   T* sdi = sst + 9 * tot;         // inverse diagonals
-  const int col = blockIdx.x;
-  if (done[col]) return;
+  auto stg = [&](int g) { return (const T*)(sst + 9 * L.off[g]); };
+  auto dig = [&](int g) { return (const T*)(sdi + L.off[g]); };
   const int tid = threadIdx.x;
-  for (int g = L.g0; g < L.G; ++g) {
-    const int n = L.nx[g] * L.ny[g];
-    stage_async(sst + 9 * L.off[g], (const T*)L.st[g], 9 * n);
-    stage_async(sdi + L.off[g], (const T*)L.dinv[g], n);
-  }
   auto B = [&](int g) { return sm + 3 * L.off[g]; };
   auto Xa = [&](int g) { return sm + 3 * L.off[g] + L.nx[g] * L.ny[g]; };
   auto Xb = [&](int g) { return sm + 3 * L.off[g] + 2 * L.nx[g] * L.ny[g]; };
@@ -724,156 +745,146 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, 
   auto lsync = [&](bool wm) {
     if (wm) __syncwarp(); else __syncthreads();
   };
-  {
-    const int n0 = L.nx[L.g0] * L.ny[L.g0];
-    T* b0 = B(L.g0);
-    for (int idx = tid; idx < n0; idx += blockDim.x) cp_async_elem(b0 + idx, bg + idx * wp + col);
-  }
-  cp_async_wait_all();   // stencils, diagonals and the right-hand side
-  __syncthreads();
-  T* cur[MAX_LEVELS];
-  T* oth[MAX_LEVELS];
-  for (int g = L.g0; g < L.G; ++g) {
-    const int nx = L.nx[g], ny = L.ny[g], n = nx * ny;
-    const bool wm = wmode(g);
-    const int lim = wm ? 32 : (int)blockDim.x;
-    const bool act = tid < lim;
-    const T* st = sst + 9 * L.off[g];
-    const T* dinv = sdi + L.off[g];
-    const T* b = B(g);
-    T* c = Xa(g);
-    T* o = Xb(g);
-    if (g == L.G - 1) {  // coarsest grid (one node for square grids): exact solve
+  const int n0 = L.nx[L.g0] * L.ny[L.g0];
+  bool staged = false;
+  for (int col = Bk.bid; col < wp; col += Bk.nb) {
+    if (done[col]) continue;
+    if (!staged) {
+      for (int g = L.g0; g < L.G; ++g) {
+        const int n = L.nx[g] * L.ny[g];
+        stage_async(sst + 9 * L.off[g], (const T*)L.st[g], 9 * n);
+        stage_async(sdi + L.off[g], (const T*)L.dinv[g], n);
+      }
+      staged = true;
+    }
+    {
+      T* b0 = B(L.g0);
+      for (int idx = tid; idx < n0; idx += blockDim.x) cp_async_elem(b0 + idx, bg + idx * wp + col);
+    }
+    cp_async_wait_all();   // stencils, diagonals and the right-hand side
+    __syncthreads();
+    T* cur[MAX_LEVELS];
+    T* oth[MAX_LEVELS];
+    for (int g = L.g0; g < L.G; ++g) {
+      const int nx = L.nx[g], ny = L.ny[g], n = nx * ny;
+      const bool wm = wmode(g);
+      const int lim = wm ? 32 : (int)blockDim.x;
+      const bool act = tid < lim;
+      const T* st = stg(g);
+      const T* dinv = dig(g);
+      const T* b = B(g);
+      T* c = Xa(g);
+      T* o = Xb(g);
+      if (g == L.G - 1) {  // coarsest grid (one node for square grids): exact solve
+        if (act)
+          for (int idx = tid; idx < n; idx += lim) c[idx] = dinv[idx] * b[idx];
+        lsync(wm);
+        cur[g] = c;
+        oth[g] = o;
+        break;
+      }
       if (act)
-        for (int idx = tid; idx < n; idx += lim) c[idx] = dinv[idx] * b[idx];
+        for (int idx = tid; idx < n; idx += lim) c[idx] = om * dinv[idx] * b[idx];
+      lsync(wm);
+      for (int s = 1; s < nu; ++s) {
+        if (act)
+          for (int idx = tid; idx < n; idx += lim) {
+            const int y = idx / nx, x = idx - y * nx;
+            o[idx] = c[idx] + om * dinv[idx] * (b[idx] - sdot(st + idx * 9, nx, ny, x, y, c));
+          }
+        lsync(wm);
+        T* t = c; c = o; o = t;
+      }
+      if (act)
+        for (int idx = tid; idx < n; idx += lim) {
+          const int y = idx / nx, x = idx - y * nx;
+          o[idx] = b[idx] - sdot(st + idx * 9, nx, ny, x, y, c);
+        }
+      lsync(wm);
+      const int nxc = L.nx[g + 1], nyc = L.ny[g + 1];
+      T* bc = B(g + 1);
+      if (act)
+        for (int idx = tid; idx < nxc * nyc; idx += lim) {
+          const int Y = idx / nxc, X = idx - Y * nxc;
+          T acc = T(0);
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const T wgt = (dx == 0 ? T(1) : T(0.5)) * (dy == 0 ? T(1) : T(0.5));
+              acc += wgt * o[(2 * Y + 1 + dy) * nx + (2 * X + 1 + dx)];
+            }
+          bc[idx] = acc;
+        }
       lsync(wm);
       cur[g] = c;
       oth[g] = o;
-      break;
     }
-    if (act)
-      for (int idx = tid; idx < n; idx += lim) c[idx] = om * dinv[idx] * b[idx];
-    lsync(wm);
-    for (int s = 1; s < nu; ++s) {
+    for (int g = L.G - 2; g >= L.g0; --g) {
+      const int nx = L.nx[g], ny = L.ny[g], n = nx * ny;
+      const int nxc = L.nx[g + 1], nyc = L.ny[g + 1];
+      const bool wm = wmode(g);
+      if (!wm && wmode(g + 1)) __syncthreads();   // results of warp 0 become visible to the block
+      const int lim = wm ? 32 : (int)blockDim.x;
+      const bool act = tid < lim;
+      const T* st = stg(g);
+      const T* dinv = dig(g);
+      const T* b = B(g);
+      T* c = cur[g];
+      T* o = oth[g];
+      const T* xc = cur[g + 1];
       if (act)
         for (int idx = tid; idx < n; idx += lim) {
           const int y = idx / nx, x = idx - y * nx;
-          o[idx] = c[idx] + om * dinv[idx] * (b[idx] - sdot(st + idx * 9, nx, ny, x, y, c));
+          c[idx] += prolong_at(x, y, nxc, nyc, xc);
         }
       lsync(wm);
-      T* t = c; c = o; o = t;
-    }
-    if (act)
-      for (int idx = tid; idx < n; idx += lim) {
-        const int y = idx / nx, x = idx - y * nx;
-        o[idx] = b[idx] - sdot(st + idx * 9, nx, ny, x, y, c);
-      }
-    lsync(wm);
-    const int nxc = L.nx[g + 1], nyc = L.ny[g + 1];
-    T* bc = B(g + 1);
-    if (act)
-      for (int idx = tid; idx < nxc * nyc; idx += lim) {
-        const int Y = idx / nxc, X = idx - Y * nxc;
-        T acc = T(0);
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const T wgt = (dx == 0 ? T(1) : T(0.5)) * (dy == 0 ? T(1) : T(0.5));
-            acc += wgt * o[(2 * Y + 1 + dy) * nx + (2 * X + 1 + dx)];
+      for (int s = 0; s < nu; ++s) {
+        if (act)
+          for (int idx = tid; idx < n; idx += lim) {
+            const int y = idx / nx, x = idx - y * nx;
+            o[idx] = c[idx] + om * dinv[idx] * (b[idx] - sdot(st + idx * 9, nx, ny, x, y, c));
           }
-        bc[idx] = acc;
+        lsync(wm);
+        T* t = c; c = o; o = t;
       }
-    lsync(wm);
-    cur[g] = c;
-    oth[g] = o;
-  }
-  for (int g = L.G - 2; g >= L.g0; --g) {
-    const int nx = L.nx[g], ny = L.ny[g], n = nx * ny;
-    const int nxc = L.nx[g + 1], nyc = L.ny[g + 1];
-    const bool wm = wmode(g);
-    if (!wm && wmode(g + 1)) __syncthreads();   // results of warp 0 become visible to the block
-    const int lim = wm ? 32 : (int)blockDim.x;
-    const bool act = tid < lim;
-    const T* st = sst + 9 * L.off[g];
-    const T* dinv = sdi + L.off[g];
-    const T* b = B(g);
-    T* c = cur[g];
-    T* o = oth[g];
-    const T* xc = cur[g + 1];
-    if (act)
-      for (int idx = tid; idx < n; idx += lim) {
-        const int y = idx / nx, x = idx - y * nx;
-        c[idx] += prolong_at(x, y, nxc, nyc, xc);
-      }
-    lsync(wm);
-    for (int s = 0; s < nu; ++s) {
-      if (act)
-        for (int idx = tid; idx < n; idx += lim) {
-          const int y = idx / nx, x = idx - y * nx;
-          o[idx] = c[idx] + om * dinv[idx] * (b[idx] - sdot(st + idx * 9, nx, ny, x, y, c));
-        }
-      lsync(wm);
-      T* t = c; c = o; o = t;
+      cur[g] = c;
     }
-    cur[g] = c;
+    __syncthreads();
+    const T* x0 = cur[L.g0];
+    for (int idx = tid; idx < n0; idx += blockDim.x) xg[idx * wp + col] = x0[idx];
+    __syncthreads();   // the next column reuses the buffers
   }
-  __syncthreads();
-  const int n0 = L.nx[L.g0] * L.ny[L.g0];
-  const T* x0 = cur[L.g0];
-  for (int idx = tid; idx < n0; idx += blockDim.x) xg[idx * wp + col] = x0[idx];
 }
 
-// ------------------------------------------------------------- batched CG ---
-
-// r = src (cast; padded columns w..wp-1 zero), x = 0, ||b||^2 -> FIN_INIT
-// (sets the loop condition; zero columns, the padded ones included, are done)
+// r = src (cast; padded columns w..wp-1 zero), x = 0; acc = ||b||^2 partials
 template <typename TS, typename T>
-__global__ void __launch_bounds__(1024) k_gather(int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
-                                                 T* __restrict__ r, T* __restrict__ x, FinArgs f) {
+__device__ __forceinline__ void ph_gather(Blk B, int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
+                                          T* __restrict__ r, T* __restrict__ x, T (&acc)[VW<T>::N]) {
   constexpr int N = VW<T>::N;
-  using A = T;
-  int cg, node, nstep;
-  thread_pos(wp / N, k, cg, node, nstep);
-  const int c0 = cg * N;
-  A acc[N];
 #pragma unroll
-  for (int u = 0; u < N; ++u) acc[u] = A(0);
+  for (int u = 0; u < N; ++u) acc[u] = T(0);
+  int cg, node, nstep;
+  if (!thread_pos(wp / N, k, B, cg, node, nstep)) return;
+  const int c0 = cg * N;
   for (; node < n; node += nstep) {
     Vec<T> v;
 #pragma unroll
     for (int u = 0; u < N; ++u) {
-      v.a[u] = c0 + u < w ? (T)src[(size_t)node * lds + c0 + u] : T(0);
+      v.a[u] = c0 + u < w ? widen<T>(src[(size_t)node * lds + c0 + u]) : T(0);
       acc[u] += v.a[u] * v.a[u];
     }
     const int i = node * wp + c0;
     vst(r + i, v);
     vst(x + i, vzero<T>());
   }
-  reduce_finalize<A, N>(f, acc, wp, k, FIN_INIT);
-}
-
-// src (leading dimension lds, w columns) -> b (wp columns, padding zero)
-template <typename TS, typename T>
-__global__ void __launch_bounds__(1024) k_pack(int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
-                                               T* __restrict__ b) {
-  constexpr int N = VW<T>::N;
-  int cg, node, nstep;
-  thread_pos(wp / N, k, cg, node, nstep);
-  const int c0 = cg * N;
-  for (; node < n; node += nstep) {
-    Vec<T> v;
-#pragma unroll
-    for (int u = 0; u < N; ++u) v.a[u] = c0 + u < w ? (T)src[(size_t)node * lds + c0 + u] : T(0);
-    vst(b + node * wp + c0, v);
-  }
 }
 
 // x (wp columns) -> dst (leading dimension ldd, first w columns)
 template <typename T, typename TD>
-__global__ void __launch_bounds__(1024) k_scatter(int n, int w, int wp, int k, const T* __restrict__ x,
-                                                  TD* __restrict__ dst, int ldd) {
+__device__ __forceinline__ void ph_scatter(Blk B, int n, int w, int wp, int k, const T* __restrict__ x,
+                                           TD* __restrict__ dst, int ldd) {
   constexpr int N = VW<T>::N;
   int cg, node, nstep;
-  thread_pos(wp / N, k, cg, node, nstep);
+  if (!thread_pos(wp / N, k, B, cg, node, nstep)) return;
   const int c0 = cg * N;
   for (; node < n; node += nstep) {
     const Vec<T> v = vld(x + node * wp + c0);
@@ -883,113 +894,224 @@ __global__ void __launch_bounds__(1024) k_scatter(int n, int w, int wp, int k, c
   }
 }
 
+// acc = a . b partials per column
+template <typename T>
+__device__ __forceinline__ void ph_dot(Blk B, int n, int wp, int k, const T* __restrict__ a, const T* __restrict__ b,
+                                       const int* __restrict__ done, T (&acc)[VW<T>::N]) {
+  constexpr int N = VW<T>::N;
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = T(0);
+  int cg, node, nstep;
+  if (!thread_pos(wp / N, k, B, cg, node, nstep)) return;
+  const int c0 = cg * N;
+  if (done_mask<N>(done, c0) == (1u << N) - 1) return;
+  for (; node < n; node += nstep) {
+    const int i = node * wp + c0;
+    const Vec<T> av = vld(a + i), bv = vld(b + i);
+#pragma unroll
+    for (int u = 0; u < N; ++u) acc[u] += av.a[u] * bv.a[u];
+  }
+}
+
+// p_new = z + beta p_old (p_new = z on the batch's first iteration, p_old not
+// read), formed on the fly at the 9 neighbours; q = A_0 p_new; acc = p_new . q
+template <typename T>
+__device__ __forceinline__ void ph_matvec_p(Blk B, int nx, int ny, int wp, int k, const T* __restrict__ st,
+                                            const T* __restrict__ z, const T* __restrict__ pold,
+                                            T* __restrict__ pnew, T* __restrict__ q, bool first,
+                                            const T* __restrict__ beta, const int* __restrict__ done,
+                                            T (&acc)[VW<T>::N]) {
+  constexpr int N = VW<T>::N;
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = T(0);
+  int cg, node0, nstep;
+  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
+  const int c0 = cg * N;
+  if (done_mask<N>(done, c0) == (1u << N) - 1) return;
+  T bt[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) bt[u] = beta[c0 + u];
+  const int n = nx * ny, rs = nx * wp;
+  auto pv = [&](int e) {
+    Vec<T> v = vld(z + e);
+    if (!first) {
+      const Vec<T> po = vld(pold + e);
+#pragma unroll
+      for (int u = 0; u < N; ++u) v.a[u] += bt[u] * po.a[u];
+    }
+    return v;
+  };
+  for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+    const int i = it.node * wp + c0;
+    const Vec<T> s = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
+                              [&](int e, int) { return pv(e); });
+    const Vec<T> p = pv(i);
+    vst(pnew + i, p);
+    vst(q + i, s);
+#pragma unroll
+    for (int u = 0; u < N; ++u) acc[u] += p.a[u] * s.a[u];
+  }
+}
+
+// x += alpha p_new; r -= alpha q; acc = r . r. Finished columns keep x and r.
+template <typename T>
+__device__ __forceinline__ void ph_update_xr(Blk B, int n, int wp, int k, const T* __restrict__ pnew,
+                                             const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
+                                             const T* __restrict__ alpha, const int* __restrict__ done,
+                                             T (&acc)[VW<T>::N]) {
+  constexpr int N = VW<T>::N;
+#pragma unroll
+  for (int u = 0; u < N; ++u) acc[u] = T(0);
+  int cg, node, nstep;
+  if (!thread_pos(wp / N, k, B, cg, node, nstep)) return;
+  const int c0 = cg * N;
+  const unsigned dm = done_mask<N>(done, c0);
+  if (dm == (1u << N) - 1) return;
+  T a[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) a[u] = (dm >> u) & 1u ? T(0) : alpha[c0 + u];
+  for (; node < n; node += nstep) {
+    const int i = node * wp + c0;
+    Vec<T> xv = vld(x + i), rv = vld(r + i);
+    const Vec<T> pv = vld(pnew + i), qv = vld(q + i);
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      if (!((dm >> u) & 1u)) {
+        xv.a[u] += a[u] * pv.a[u];
+        rv.a[u] -= a[u] * qv.a[u];
+      }
+      acc[u] += rv.a[u] * rv.a[u];
+    }
+    vst(x + i, xv);
+    vst(r + i, rv);
+  }
+}
+
+// The per-column CG scalars the FP32 / FP64 kernels read.
+template <typename T>
+__device__ __forceinline__ const T* alpha_of(const FinArgs& f) {
+  if constexpr (sizeof(T) == 4) return f.alphaf; else return f.alpha;
+}
+template <typename T>
+__device__ __forceinline__ const T* beta_of(const FinArgs& f) {
+  if constexpr (sizeof(T) == 4) return f.betaf; else return f.beta;
+}
+
+// ------------------------------------------------------- stand-alone kernels ---
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_smooth0(int n, int wp, int k, const T* __restrict__ dinv,
+                                                  const T* __restrict__ b, T* __restrict__ x, T om,
+                                                  const int* __restrict__ done) {
+  ph_smooth0<T>(this_grid(), n, wp, k, dinv, b, x, om, done);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_smooth00(int nx, int ny, int wp, int k, const T* __restrict__ st,
+                                                   const T* __restrict__ dinv, const T* __restrict__ b,
+                                                   T* __restrict__ x, T om, const int* __restrict__ done) {
+  ph_smooth00<T>(this_grid(), nx, ny, wp, k, st, dinv, b, x, om, done);
+}
+
+// with DOT also b . xo -> FIN_RHO
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(1024) k_jacobi(int nx, int ny, int wp, int k, const T* __restrict__ st,
+                                                 const T* __restrict__ dinv, const T* __restrict__ b,
+                                                 const T* __restrict__ xi, T* __restrict__ xo, T om, FinArgs f) {
+  T acc[VW<T>::N];
+  ph_jacobi<T, DOT>(this_grid(), nx, ny, wp, k, st, dinv, b, xi, xo, om, f.done, acc);
+  if (DOT) reduce_finalize<T, VW<T>::N>(f, acc, wp, k, FIN_RHO);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_resid_restrict_t(int nxf, int nyf, int nxc, int nyc, int wp, int TC,
+                                                           const T* __restrict__ st, const T* __restrict__ b,
+                                                           const T* __restrict__ x, T* __restrict__ bc,
+                                                           const int* __restrict__ done) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ph_resid_restrict<T>(this_grid(), nxf, nyf, nxc, nyc, wp, TC, st, b, x, bc, done, smem_raw);
+}
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(1024) k_prolong_jacobi(int nxf, int nyf, int nxc, int nyc, int wp, int k,
+                                                         const T* __restrict__ st, const T* __restrict__ dinv,
+                                                         const T* __restrict__ b, const T* __restrict__ x,
+                                                         const T* __restrict__ xc, T* __restrict__ xo, T om,
+                                                         FinArgs f) {
+  T acc[VW<T>::N];
+  ph_prolong_jacobi<T, DOT>(this_grid(), nxf, nyf, nxc, nyc, wp, k, st, dinv, b, x, xc, xo, om, f.done, acc);
+  if (DOT) reduce_finalize<T, VW<T>::N>(f, acc, wp, k, FIN_RHO);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, int wp, const T* __restrict__ bg,
+                                                        T* __restrict__ xg, T om, int nu,
+                                                        const int* __restrict__ done) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ph_coarse<T>(this_grid(), L, tot, wp, bg, xg, om, nu, done, smem_raw);
+}
+
+// r = src, x = 0, ||b||^2 -> FIN_INIT (sets the loop condition; zero columns,
+// the padded ones included, are done)
+template <typename TS, typename T>
+__global__ void __launch_bounds__(1024) k_gather(int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
+                                                 T* __restrict__ r, T* __restrict__ x, FinArgs f) {
+  T acc[VW<T>::N];
+  ph_gather<TS, T>(this_grid(), n, w, wp, k, src, lds, r, x, acc);
+  reduce_finalize<T, VW<T>::N>(f, acc, wp, k, FIN_INIT);
+}
+
+// src (leading dimension lds, w columns) -> b (wp columns, padding zero)
+template <typename TS, typename T>
+__global__ void __launch_bounds__(1024) k_pack(int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
+                                               T* __restrict__ b) {
+  constexpr int N = VW<T>::N;
+  int cg, node, nstep;
+  if (!thread_pos(wp / N, k, this_grid(), cg, node, nstep)) return;
+  const int c0 = cg * N;
+  for (; node < n; node += nstep) {
+    Vec<T> v;
+#pragma unroll
+    for (int u = 0; u < N; ++u) v.a[u] = c0 + u < w ? (T)src[(size_t)node * lds + c0 + u] : T(0);
+    vst(b + node * wp + c0, v);
+  }
+}
+
+template <typename T, typename TD>
+__global__ void __launch_bounds__(1024) k_scatter(int n, int w, int wp, int k, const T* __restrict__ x,
+                                                  TD* __restrict__ dst, int ldd) {
+  ph_scatter<T, TD>(this_grid(), n, w, wp, k, x, dst, ldd);
+}
+
 // a . b per column -> op (used when the finest grid is inside the coarse block)
 template <typename T>
 __global__ void __launch_bounds__(1024) k_dot_fin(int n, int wp, int k, const T* __restrict__ a, const T* __restrict__ b,
                                                   FinArgs f, int op) {
-  constexpr int N = VW<T>::N;
-  using A = T;
-  int cg, node, nstep;
-  thread_pos(wp / N, k, cg, node, nstep);
-  const int c0 = cg * N;
-  A acc[N];
-#pragma unroll
-  for (int u = 0; u < N; ++u) acc[u] = A(0);
-  if (done_mask<N>(f.done, c0) != (1u << N) - 1)
-    for (; node < n; node += nstep) {
-      const int i = node * wp + c0;
-      const Vec<T> av = vld(a + i), bv = vld(b + i);
-#pragma unroll
-      for (int u = 0; u < N; ++u) acc[u] += av.a[u] * bv.a[u];
-    }
-  reduce_finalize<A, N>(f, acc, wp, k, op);
+  T acc[VW<T>::N];
+  ph_dot<T>(this_grid(), n, wp, k, a, b, f.done, acc);
+  reduce_finalize<T, VW<T>::N>(f, acc, wp, k, op);
 }
 
-// p_new = z + beta p_old (p_new = z on the batch's first iteration), formed on the
-// fly at the 9 neighbours; q = A_0 p_new; p_new . q -> FIN_ALPHA.
+// p_new (ping-pong by the iteration parity), q = A_0 p_new, p_new . q -> FIN_ALPHA
 template <typename T>
 __global__ void __launch_bounds__(1024) k_matvec_p(int nx, int ny, int wp, int k, const T* __restrict__ st,
                                                    const T* __restrict__ z, T* __restrict__ pA,
                                                    T* __restrict__ pB, T* __restrict__ q, FinArgs f) {
-  constexpr int N = VW<T>::N;
-  using A = T;
-  int cg, node0, nstep;
-  thread_pos(wp / N, k, cg, node0, nstep);
-  const int c0 = cg * N;
-  const int par = f.ctl->it & 1;
-  const T* __restrict__ pold = par ? pB : pA;
-  T* __restrict__ pnew = par ? pA : pB;
-  A acc[N];
-#pragma unroll
-  for (int u = 0; u < N; ++u) acc[u] = A(0);
-  if (done_mask<N>(f.done, c0) != (1u << N) - 1) {
-    T bt[N];
-#pragma unroll
-    for (int u = 0; u < N; ++u) bt[u] = sizeof(T) == 4 ? (T)f.betaf[c0 + u] : (T)f.beta[c0 + u];
-    const int n = nx * ny, rs = nx * wp;
-    // iteration 0 of the batch: p_new = z, p_old is not read (it holds nothing yet)
-    const bool first = f.ctl->it == 0;
-    auto pv = [&](int e) {
-      Vec<T> v = vld(z + e);
-      if (!first) {
-        const Vec<T> po = vld(pold + e);
-#pragma unroll
-        for (int u = 0; u < N; ++u) v.a[u] += bt[u] * po.a[u];
-      }
-      return v;
-    };
-    for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
-      const int i = it.node * wp + c0;
-      const Vec<T> s = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
-                                [&](int e, int) { return pv(e); });
-      const Vec<T> p = pv(i);
-      vst(pnew + i, p);
-      vst(q + i, s);
-#pragma unroll
-      for (int u = 0; u < N; ++u) acc[u] += p.a[u] * s.a[u];
-    }
-  }
-  reduce_finalize<A, N>(f, acc, wp, k, FIN_ALPHA);
+  const int it = f.ctl->it;
+  T acc[VW<T>::N];
+  ph_matvec_p<T>(this_grid(), nx, ny, wp, k, st, z, (it & 1) ? pB : pA, (it & 1) ? pA : pB, q, it == 0,
+                 beta_of<T>(f), f.done, acc);
+  reduce_finalize<T, VW<T>::N>(f, acc, wp, k, FIN_ALPHA);
 }
 
-// x += alpha p_new; r -= alpha q; r . r -> FIN_CONV (sets the loop condition).
-// Finished columns keep their x and r.
+// x += alpha p_new; r -= alpha q; r . r -> FIN_CONV (sets the loop condition)
 template <typename T>
 __global__ void __launch_bounds__(1024) k_update_xr(int n, int wp, int k, const T* __restrict__ pA,
                                                     const T* __restrict__ pB, const T* __restrict__ q,
                                                     T* __restrict__ x, T* __restrict__ r, FinArgs f) {
-  constexpr int N = VW<T>::N;
-  using A = T;
-  int cg, node, nstep;
-  thread_pos(wp / N, k, cg, node, nstep);
-  const int c0 = cg * N;
-  const T* __restrict__ pnew = (f.ctl->it & 1) ? pA : pB;
-  A acc[N];
-#pragma unroll
-  for (int u = 0; u < N; ++u) acc[u] = A(0);
-  const unsigned dm = done_mask<N>(f.done, c0);
-  if (dm != (1u << N) - 1) {
-    T a[N];
-#pragma unroll
-    for (int u = 0; u < N; ++u)
-      a[u] = (dm >> u) & 1u ? T(0) : (sizeof(T) == 4 ? (T)f.alphaf[c0 + u] : (T)f.alpha[c0 + u]);
-    for (; node < n; node += nstep) {
-      const int i = node * wp + c0;
-      Vec<T> xv = vld(x + i), rv = vld(r + i);
-      const Vec<T> pv = vld(pnew + i), qv = vld(q + i);
-#pragma unroll
-      for (int u = 0; u < N; ++u) {
-        if (!((dm >> u) & 1u)) {
-          xv.a[u] += a[u] * pv.a[u];
-          rv.a[u] -= a[u] * qv.a[u];
-        }
-        acc[u] += rv.a[u] * rv.a[u];
-      }
-      vst(x + i, xv);
-      vst(r + i, rv);
-    }
-  }
-  reduce_finalize<A, N>(f, acc, wp, k, FIN_CONV);
+  T acc[VW<T>::N];
+  ph_update_xr<T>(this_grid(), n, wp, k, (f.ctl->it & 1) ? pA : pB, q, x, r, alpha_of<T>(f), f.done, acc);
+  reduce_finalize<T, VW<T>::N>(f, acc, wp, k, FIN_CONV);
 }
 
 __global__ void k_clear_done(int w, int* done) {
@@ -1096,6 +1218,7 @@ static FinArgs make_fin(sg_problem* h, InnerWork& iw, const sg_prec_opts& o) {
   f.has_cond = 0;
   f.flag = nullptr;
   f.iacc = h->iacc;
+  f.count_iacc = 1;
   return f;
 }
 
@@ -1115,27 +1238,35 @@ static int launch_coarse(sg_problem* h, int g0, const T* b, T* x, int wp, const 
     L.st[g] = sizeof(T) == 8 ? (const void*)G.st64 : (const void*)G.st32;
     L.dinv[g] = sizeof(T) == 8 ? (const void*)G.dinv64 : (const void*)G.dinv32;
   }
-  const size_t smem = (size_t)13 * tot * sizeof(T);
+  const size_t smem = coarse_smem_bytes<T>(tot);
   SG_TRY_CUDA(cudaFuncSetAttribute(k_vcycle_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   { k_vcycle_coarse<T><<<wp, 1024, smem, s>>>(L, tot, wp, b, x, (T)o.omega, o.nu, done); ::sghsc::note_launch(); }
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
 
-// Tiled residual + restriction: the coarse tile edge TC is the largest (<= 16)
-// whose fine footprint (2TC+1)^2 times the column groups stays within 2048
-// residuals per block, shrunk while that leaves fewer tiles than SMs.
-template <typename T>
-static int launch_resid_restrict(sg_problem* h, const GridLevel& G, const GridLevel& C, int wp, const T* st,
-                                 const T* b, const T* x, T* bc, const int* done, cudaStream_t s) {
-  const int ng = wp / VW<T>::N;
+// Tile edge of the tiled restriction from grid G to grid C: the largest
+// (<= 16) whose fine footprint (2TC+1)^2 times the column groups stays within
+// 2048 residuals per block, shrunk while that leaves fewer tiles than SMs.
+static int restrict_tile(const sg_problem* h, const GridLevel& C, int ng) {
   auto items = [&](int tc) { return (2 * tc + 1) * (2 * tc + 1) * ng; };
   auto tiles = [&](int tc) { return ceil_div(C.nx, tc) * ceil_div(C.ny, tc); };
   int tc = 16;
   while (tc > 1 && items(tc) > 2048) --tc;
   while (tc > 1 && tiles(tc) < h->num_sms) --tc;
-  const int bdim = std::min(1024, (items(tc) + 31) / 32 * 32);
-  const size_t smem = (size_t)items(tc) * 16;
+  return tc;
+}
+
+// Tiled residual + restriction (k_resid_restrict_t).
+template <typename T>
+static int launch_resid_restrict(sg_problem* h, const GridLevel& G, const GridLevel& C, int wp, const T* st,
+                                 const T* b, const T* x, T* bc, const int* done, cudaStream_t s) {
+  const int ng = wp / VW<T>::N;
+  const int tc = restrict_tile(h, C, ng);
+  const int items = (2 * tc + 1) * (2 * tc + 1) * ng;
+  const int bdim = std::min(1024, (items + 31) / 32 * 32);
+  const size_t smem = (size_t)items * 16;
+  auto tiles = [&](int t) { return ceil_div(C.nx, t) * ceil_div(C.ny, t); };
   SG_TRY_CUDA(cudaFuncSetAttribute(k_resid_restrict_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resid_restrict_t<T>, bdim, smem));
