@@ -146,6 +146,7 @@ def run_ours(args, rank, world, dev):
     prob = build_problem(cfg)
     p = cfg["p"]
     h = L.SGProblem.from_inputs(prob, p)
+    tuned = L.sg_autotune(h)   # block sizes of the SG product (FP64, FP32), part of setup
     setup_s = time.time() - t0
     n, P, M, nnz = h.n, h.P, h.M, h.nnz
     alpha, off = h.chaos_table()
@@ -237,6 +238,7 @@ def run_ours(args, rank, world, dev):
     os.environ["SGHSC_EAGER"] = "1"
     h_e = L.SGProblem.from_inputs(prob, p)
     os.environ.pop("SGHSC_EAGER")
+    L.sg_autotune(h_e)
     L.sg_solve(h_e, F, hsc_opts)
     l0 = L._lib.LIB.sg_kernel_launches()
     L.sg_solve(h_e, F, hsc_opts)
@@ -314,6 +316,7 @@ def run_ours(args, rank, world, dev):
         "config": {"workload": cfg["name"], "ne": cfg["ne"], "M": M, "p": p, "P": P, "n": n,
                    "unknowns": n * P, "sigma": cfg["sigma"], "corr_len": cfg["corr_len"], "inner_tol": 1e-2,
                    "tol": 1e-8, "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                   "autotuned_threads_f64_f32": list(tuned),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "hsc": {"ms": ms, "iterations": st_h.iterations, "true_rel_res": st_true.true_rel_res,
                 "kappa_est": st_h.kappa_est, "inner_iters_total": st_h.inner_iters_total,

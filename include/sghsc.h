@@ -213,7 +213,7 @@ int mean_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_
 int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opts,
              sg_solve_stats* stats, void* stream);
 
-/* sg_autotune -- time the candidate block sizes (64, 128, 256 threads) of the
+/* sg_autotune -- time the candidate block sizes (64 to 1024 threads) of the
  * full SG product in FP64 and FP32 on this problem and keep the fastest for
  * all later calls (including the outer solver's fused product). Allocates two
  * temporary n x P blocks; invalidates the handle's cached solve graphs. */

@@ -126,7 +126,7 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cands[] = {64, 128, 256};
+  const int cands[] = {64, 128, 256, 512, 1024};
   int best = 0;
   float best_ms = 1e30f;
   int r = SG_OK;

@@ -45,8 +45,15 @@ __device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __rest
   }
 }
 
-template <typename TIn, typename TAcc, typename TB, typename TO, bool DIAG, int MAXO>
-__global__ void __launch_bounds__(256) k_block_matvec(
+// LB: the largest block the instantiation is launched with. Blocks of up to
+// 256 threads with fewer than 4 outputs per thread keep the compiler's
+// register choice; with 4 or more (large P) they may use up to 64 registers
+// (4 blocks per SM) instead of spilling; blocks of up to 1024 threads may use
+// 64 (one block per SM).
+#define SG_MATVEC_BOUNDS(LB, MAXO) __launch_bounds__(LB, (LB) > 256 ? 1 : ((MAXO) >= 4 ? 4 : 0))
+
+template <typename TIn, typename TAcc, typename TB, typename TO, bool DIAG, int MAXO, int LB>
+__global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const TAcc* __restrict__ vals,
     int M1, const TIn* __restrict__ X, int ldx, int wx, const int* __restrict__ eptr,
     const int* __restrict__ ek, const int* __restrict__ ej, const TAcc* __restrict__ ec, int wy,
@@ -87,8 +94,8 @@ __global__ void __launch_bounds__(256) k_block_matvec(
 // the FP64 update is done once per output rather than once per staged
 // neighbour), p_new and q written for the block's own rows, p_new . q reduced
 // and alpha = rho / (p_new . q) set by the last block.
-template <int MAXO>
-__global__ void __launch_bounds__(256) k_outer_matvec(
+template <int MAXO, int LB>
+__global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const double* __restrict__ vals,
     int M1, int P, const double* __restrict__ z, double* pA, double* pB, const int* __restrict__ eptr,
     const int* __restrict__ ek, const int* __restrict__ ej, const double* __restrict__ ec,
@@ -192,10 +199,16 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
-  if (maxo <= 1) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 1>);
-  if (maxo <= 2) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 2>);
-  if (maxo <= 4) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 4>);
-  if (maxo <= 8) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 8>);
+  if (threads > 256) {
+    if (maxo <= 1) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 1, 1024>);
+    if (maxo <= 2) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 2, 1024>);
+    if (maxo <= 4) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 4, 1024>);
+  } else {
+    if (maxo <= 1) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 1, 256>);
+    if (maxo <= 2) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 2, 256>);
+    if (maxo <= 4) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 4, 256>);
+    if (maxo <= 8) return go(k_block_matvec<TIn, TAcc, TB, TO, DIAG, 8, 256>);
+  }
   set_error("block matvec: %d output columns exceed the supported 2048", wy);
   return SG_ERR_UNSUPPORTED;
 }
@@ -227,7 +240,7 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
 
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
   const int P = h->P, M1 = h->M + 1;
-  // a power of two <= 256 for the fused reduction: the autotuned block size or 256
+  // a power of two <= 1024 for the fused reduction: the autotuned block size or 256
   const int threads = h->k1_threads[SG_F64] > 0 ? h->k1_threads[SG_F64] : 256;
   const int maxo = (P + threads - 1) / threads;
   size_t smem = 0;
@@ -245,10 +258,16 @@ int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
-  if (maxo <= 1) return go(k_outer_matvec<1>);
-  if (maxo <= 2) return go(k_outer_matvec<2>);
-  if (maxo <= 4) return go(k_outer_matvec<4>);
-  if (maxo <= 8) return go(k_outer_matvec<8>);
+  if (threads > 256) {
+    if (maxo <= 1) return go(k_outer_matvec<1, 1024>);
+    if (maxo <= 2) return go(k_outer_matvec<2, 1024>);
+    if (maxo <= 4) return go(k_outer_matvec<4, 1024>);
+  } else {
+    if (maxo <= 1) return go(k_outer_matvec<1, 256>);
+    if (maxo <= 2) return go(k_outer_matvec<2, 256>);
+    if (maxo <= 4) return go(k_outer_matvec<4, 256>);
+    if (maxo <= 8) return go(k_outer_matvec<8, 256>);
+  }
   set_error("outer matvec: P = %d exceeds the supported 2048", P);
   return SG_ERR_UNSUPPORTED;
 }

@@ -32,9 +32,9 @@ __global__ void k_outer_true(long long N, const double* F, const double* Y, Oute
 
 // Fixed-order block sum of (v0, v1) to part[blockIdx]; returns true in the last
 // block, whose threads then hold the totals (t0, t1) over all blocks (summed in
-// block order). blockDim must be a power of two <= 256 for the tree below.
+// block order). blockDim must be a power of two <= 1024 for the tree below.
 __device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const OuterArgs& a, double& t0, double& t1) {
-  __shared__ double r0[256], r1[256];
+  __shared__ double r0[1024], r1[1024];
   __shared__ bool last;
   r0[threadIdx.x] = v0;
   r1[threadIdx.x] = v1;
