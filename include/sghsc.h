@@ -214,9 +214,10 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
              sg_solve_stats* stats, void* stream);
 
 /* sg_autotune -- time the candidate block sizes (64 to 1024 threads) of the
- * full SG product in FP64 and FP32 on this problem and keep the fastest for
- * all later calls (including the outer solver's fused product). Allocates two
- * temporary n x P blocks; invalidates the handle's cached solve graphs. */
+ * full SG product in FP64 and FP32, and separately of the outer solver's fused
+ * product (SG product + CG update + p.q), on this problem and keep the fastest
+ * for all later calls. Allocates two temporary n x P blocks and, if absent,
+ * the outer solve buffers; invalidates the handle's cached solve graphs. */
 int sg_autotune(sg_problem* h, void* stream);
 /* Block sizes chosen by sg_autotune (0: not tuned, the built-in choice). */
 int sg_autotune_result(const sg_problem* h, int* threads_f64, int* threads_f32);

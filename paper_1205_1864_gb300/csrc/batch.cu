@@ -16,6 +16,7 @@
 
 #include "graph.cuh"
 #include "sghsc_internal.cuh"
+#include "vec.cuh"
 
 struct sg_batch {
   std::vector<sg_problem*> hs;
@@ -157,6 +158,45 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
   return r;
 }
 
+// Time the fused outer product (K1 with the CG update and p . q) with each
+// candidate block size on the handle's own outer buffers and keep the
+// fastest. It runs on whatever the buffers hold; every solve stages its
+// right-hand side and resets the outer state before it starts.
+static int autotune_outer(sg_problem* h, cudaStream_t s) {
+  SG_TRY(ensure_outer(h));
+  sg_solve_opts o;
+  sg_default_solve_opts(&o);
+  const OuterArgs a = outer_args(h, o);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cands[] = {64, 128, 256, 512, 1024};
+  int best = 0;
+  float best_ms = 1e30f;
+  int r = SG_OK;
+  for (int c : cands) {
+    const int maxo = (h->P + c - 1) / c;
+    if (maxo > 8 || (c > 256 && maxo > 4)) continue;
+    h->outer_threads = c;
+    r = launch_outer_matvec(h, a, s);
+    if (r != SG_OK) break;
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 5 && r == SG_OK; ++rep) r = launch_outer_matvec(h, a, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r == SG_OK && ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  h->outer_threads = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
+}
+
 }  // namespace sghsc
 
 using namespace sghsc;
@@ -172,6 +212,7 @@ int sg_autotune(sg_problem* h, void* stream) {
   clear_graphs(h);  // captured graphs hold the old launch shapes
   SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
   SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
+  SG_TRY(autotune_outer(h, (cudaStream_t)stream));
   return SG_OK;
 }
 

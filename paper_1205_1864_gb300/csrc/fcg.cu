@@ -109,7 +109,7 @@ static int precond(sg_problem* h, int kind, const double* r, double* z, const sg
   return SG_OK;
 }
 
-static OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o) {
+OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o) {
   OuterArgs a;
   a.part = h->opart;
   a.ctl = h->octl;

@@ -1015,7 +1015,7 @@ __global__ void __launch_bounds__(1024) k_smooth00(int nx, int ny, int wp, int k
 
 // with DOT also b . xo -> FIN_RHO
 template <typename T, bool DOT>
-__global__ void __launch_bounds__(1024) k_jacobi(int nx, int ny, int wp, int k, const T* __restrict__ st,
+__global__ void __launch_bounds__(1024, DOT ? 1 : 2) k_jacobi(int nx, int ny, int wp, int k, const T* __restrict__ st,
                                                  const T* __restrict__ dinv, const T* __restrict__ b,
                                                  const T* __restrict__ xi, T* __restrict__ xo, T om, FinArgs f) {
   T acc[VW<T>::N];

@@ -241,7 +241,7 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
   const int P = h->P, M1 = h->M + 1;
   // a power of two <= 1024 for the fused reduction: the autotuned block size or 256
-  const int threads = h->k1_threads[SG_F64] > 0 ? h->k1_threads[SG_F64] : 256;
+  const int threads = h->outer_threads > 0 ? h->outer_threads : 256;
   const int maxo = (P + threads - 1) / threads;
   size_t smem = 0;
   const int chunk = pick_chunk(h, P, sizeof(double), M1, &smem);

@@ -165,6 +165,7 @@ struct sg_problem {
   std::map<std::string, sghsc::GraphEntry> graphs;
   // autotuned block sizes of the full SG product (0: heuristic), per element type
   int k1_threads[2] = {0, 0};
+  int outer_threads = 0;                    // block size of the fused outer product (0: 256)
   long long ws_gen = 0;                     // bumped whenever captured graphs become invalid
 };
 

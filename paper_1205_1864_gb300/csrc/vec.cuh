@@ -103,5 +103,7 @@ int vec_grid(long long N);
 // (ping-pong p buffers chosen by the device iteration counter), the fused
 // p_new . q reduction and the alpha update by the last block (matvec.cu).
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s);
+// Arguments of the outer-iteration kernels for this handle and options (fcg.cu).
+OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o);
 
 }  // namespace sghsc
