@@ -67,7 +67,7 @@ K1_TRAFFIC = {"cfg2": 35810048 + 602880}
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms) during the timed region."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -81,7 +81,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                          "-lms", "50", "-i", str(self.index)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -577,11 +577,14 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ne", type=int, default=None,
+                    help="mesh override (elements per side, a power of two) for profiling a workload's kernel "
+                         "shapes on a smaller case; the name gets an @ne suffix")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--profile", nargs="?", const="solve", default=None, choices=["solve", "apply", "inner"],
                     help="solve: only the warm-up and timed HSC solves; apply: only the SG product, FP64 then "
@@ -590,6 +593,13 @@ def main():
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.ne is not None:
+        w = dict(WORKLOADS[args.workload])
+        if w.get("batch"):
+            ap.error("--ne applies to single-system workloads")
+        w["ne"] = args.ne
+        w["name"] = f"{w['name']}@ne{args.ne}"
+        WORKLOADS[args.workload] = w
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
