@@ -60,11 +60,20 @@ int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts
     float* R32 = h->R32;
     float* Z32 = h->Z32;
     const bool top64 = o.top_level_f64 != 0;
-    SG_TRY(launch_cast(R, SG_F64, P, R32, SG_F32, P, n, P, s));
+    // With the FP64 top level only levels 0..p-2 of R are needed in FP32 (the
+    // pre-correction at level l reads level l-1 in place): the degree-p solve
+    // gathers its columns from R (converting on the way), and the top-level
+    // pre-correction writes level p-1 from R itself.
+    const bool cast_all = !(top64 && p >= 1);
+    const int cast_cols = cast_all ? P : off[std::max(p - 1, 0)];
+    if (cast_cols > 0) SG_TRY(launch_cast(R, SG_F64, P, R32, SG_F32, P, n, cast_cols, s));
     // first loop, l = p..1: D_l^{-1} on the degree-l columns, then the pre-correction
     for (int l = p; l >= 1; --l) {
       const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1];
-      SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
+      if (l == p && !cast_all)
+        SG_TRY(inner_solve(h, SG_F32, R + lo, P, SG_F64, Z32 + lo, P, SG_F32, w, o, s));
+      else
+        SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
       if (l == p && top64)
         SG_TRY(launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, Z32 + lo, P, w, h->pre[l], false, R + lo1, P,
                                    -1.0, 1.0, R32 + lo1, P, s));
