@@ -19,16 +19,29 @@
 
 namespace sghsc {
 
+// This thread's output columns: slot threadIdx + i * blockDim takes column
+// eperm[slot] (outputs ordered by coupling count, so the lanes of a warp run
+// coupling loops of equal length); -1 past the last output.
+template <int MAXO>
+__device__ __forceinline__ void output_columns(const int* __restrict__ eperm, int wy, int (&lcol)[MAXO]) {
+#pragma unroll
+  for (int i = 0; i < MAXO; ++i) {
+    const int slot = threadIdx.x + i * blockDim.x;
+    lcol[i] = slot < wy ? eperm[slot] : -1;
+  }
+}
+
 // Accumulate the gather form for this thread's outputs over one staged chunk.
 template <typename TAcc, int MAXO, bool DIAG>
 __device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __restrict__ Vs,
                                              const TAcc* __restrict__ Xs, int wx, const int* __restrict__ eptr,
                                              const int* __restrict__ ek, const int* __restrict__ ej,
-                                             const TAcc* __restrict__ ec, int wy, TAcc (&acc)[MAXO]) {
+                                             const TAcc* __restrict__ ec, const int (&lcol)[MAXO],
+                                             TAcc (&acc)[MAXO]) {
 #pragma unroll
   for (int i = 0; i < MAXO; ++i) {
-    const int l = threadIdx.x + i * blockDim.x;
-    if (l < wy) {
+    const int l = lcol[i];
+    if (l >= 0) {
       TAcc a = TAcc(0);
       if (DIAG) {
         for (int e = 0; e < nzc; ++e) a += Vs[e * M1] * Xs[e * wx + l];
@@ -56,11 +69,13 @@ template <typename TIn, typename TAcc, typename TB, typename TO, bool DIAG, int 
 __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const TAcc* __restrict__ vals,
     int M1, const TIn* __restrict__ X, int ldx, int wx, const int* __restrict__ eptr,
-    const int* __restrict__ ek, const int* __restrict__ ej, const TAcc* __restrict__ ec, int wy,
-    const TB* Yin, int ldyin, TAcc alpha, TAcc beta, TO* Y, int ldy, int chunk) {
+    const int* __restrict__ eperm, const int* __restrict__ ek, const int* __restrict__ ej,
+    const TAcc* __restrict__ ec, int wy, const TB* Yin, int ldyin, TAcc alpha, TAcc beta, TO* Y, int ldy, int chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TAcc* Xs = reinterpret_cast<TAcc*>(smem_raw);
   TAcc* Vs = Xs + (size_t)chunk * wx;
+  int lcol[MAXO];
+  output_columns<MAXO>(eperm, wy, lcol);
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
     TAcc acc[MAXO];
 #pragma unroll
@@ -75,12 +90,12 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
       }
       for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
       __syncthreads();
-      gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, wy, acc);
+      gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
     }
 #pragma unroll
     for (int i = 0; i < MAXO; ++i) {
-      const int l = threadIdx.x + i * blockDim.x;
-      if (l < wy) {
+      const int l = lcol[i];
+      if (l >= 0) {
         TAcc v = alpha * acc[i];
         if (Yin) v += beta * (TAcc)Yin[(size_t)r * ldyin + l];
         Y[(size_t)r * ldy + l] = (TO)v;
@@ -98,11 +113,13 @@ template <int MAXO, int LB>
 __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const double* __restrict__ vals,
     int M1, int P, const double* __restrict__ z, double* pA, double* pB, const int* __restrict__ eptr,
-    const int* __restrict__ ek, const int* __restrict__ ej, const double* __restrict__ ec,
-    double* __restrict__ q, int chunk, OuterArgs a) {
+    const int* __restrict__ eperm, const int* __restrict__ ek, const int* __restrict__ ej,
+    const double* __restrict__ ec, double* __restrict__ q, int chunk, OuterArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* Xs = reinterpret_cast<double*>(smem_raw);
   double* Vs = Xs + (size_t)chunk * P;
+  int lcol[MAXO];
+  output_columns<MAXO>(eperm, P, lcol);
   const int it = a.ctl->it;
   const bool first = it == 0;
   const double beta = first ? 0.0 : a.sc[SC_BETA];
@@ -123,12 +140,12 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
       }
       for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
       __syncthreads();
-      gather_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, P, acc);
+      gather_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
     }
 #pragma unroll
     for (int i = 0; i < MAXO; ++i) {
-      const int l = threadIdx.x + i * blockDim.x;
-      if (l < P) {
+      const int l = lcol[i];
+      if (l >= 0) {
         const size_t g = (size_t)r * P + l;
         const double pv = first ? z[g] : z[g] + beta * pold[g];
         const double qv = first ? acc[i] : acc[i] + beta * q[g];
@@ -195,7 +212,7 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
-    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, vals, M1, X, ldx, wx, E.ptr, E.k, E.j, ec, wy, Yin, ldyin, (TAcc)alpha, (TAcc)beta, Y, ldy, chunk); ::sghsc::note_launch(); }
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, vals, M1, X, ldx, wx, E.ptr, E.perm, E.k, E.j, ec, wy, Yin, ldyin, (TAcc)alpha, (TAcc)beta, Y, ldy, chunk); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
@@ -254,7 +271,7 @@ int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int grid = std::min(std::min(h->n, h->num_sms * std::max(per_sm, 1)), h->opart_blocks);
-    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, h->vals64, M1, P, h->fz, h->fpA, h->fpB, h->all.ptr, h->all.k, h->all.j, h->all.c64, h->fq, chunk, a); ::sghsc::note_launch(); }
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, h->vals64, M1, P, h->fz, h->fpA, h->fpB, h->all.ptr, h->all.perm, h->all.k, h->all.j, h->all.c64, h->fq, chunk, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };

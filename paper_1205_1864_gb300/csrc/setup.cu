@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <map>
 
@@ -67,6 +68,14 @@ static int upload_edges(const HostEdges& he, EdgeList& E) {
   E.nout = (int)he.ptr.size() - 1;
   E.nedges = (int)he.k.size();
   std::vector<float> c32(he.c.begin(), he.c.end());
+  // Outputs ordered by their number of couplings, so the lanes of a warp run
+  // coupling loops of equal length (equal counts keep column order).
+  std::vector<int> perm(E.nout);
+  for (int l = 0; l < E.nout; ++l) perm[l] = l;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+    return he.ptr[a + 1] - he.ptr[a] > he.ptr[b + 1] - he.ptr[b];
+  });
+  SG_TRY(upload(&E.perm, perm.data(), perm.size()));
   SG_TRY(upload(&E.ptr, he.ptr.data(), he.ptr.size()));
   SG_TRY(upload(&E.k, he.k.data(), he.k.size()));
   SG_TRY(upload(&E.j, he.j.data(), he.j.size()));
@@ -76,6 +85,7 @@ static int upload_edges(const HostEdges& he, EdgeList& E) {
 }
 
 static void free_edges(EdgeList& E) {
+  cudaFree(E.perm);
   cudaFree(E.ptr);
   cudaFree(E.k);
   cudaFree(E.j);

@@ -50,6 +50,7 @@ enum : int {
 struct EdgeList {
   int nout = 0, nedges = 0;
   int* ptr = nullptr;
+  int* perm = nullptr;   // thread slot -> output column, by coupling count (descending, stable)
   int* k = nullptr;
   int* j = nullptr;
   double* c64 = nullptr;
