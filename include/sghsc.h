@@ -193,6 +193,21 @@ int sg_vcycle_apply_static(sg_problem* h, const void* B, void* X, int w, int dty
 int sg_inner_solve(sg_problem* h, const void* B, void* X, int w, int dtype,
                    const sg_prec_opts* opts, int* iters, void* stream);
 
+/* sg_inner_cluster -- 1 when the FP32 inner solves of h (sg_inner_solve, and
+ * the D_l and A_0 solves inside hsc_precond_apply, mean_precond_apply and
+ * sg_solve) run on the cluster-resident solver: one launch per solve, the
+ * multigrid hierarchy of each group of 4 columns held in the shared memory of
+ * a cluster of 8 thread blocks. 0 when they run on the stand-alone kernels:
+ * FP64 solves always do, and so does a grid hierarchy too large for one
+ * block's shared memory (finest grids above 127 x 127 nodes), a device that
+ * cannot hold such a cluster, or a handle created while the environment
+ * variable SGHSC_NO_CLUSTER was 1. A batch of w columns uses the cluster
+ * solver only when its ceil(w/4) clusters are all resident at once (on a
+ * GB300, up to 60 columns); wider batches take the stand-alone kernels. Both
+ * solvers compute the same method; their results differ by FP32 rounding
+ * (summation order). h NULL: 0. */
+int sg_inner_cluster(const sg_problem* h);
+
 /* hsc_precond_apply -- Algorithm 1 (Sec. 4): Z = M_P R with the D_l^{-1}
  * and A_0^{-1} actions replaced by the batched inner PCG.
  * R, Z: device n x P row-major FP64; must not alias. */

@@ -114,6 +114,11 @@ class SGProblem:
         """From an ``sg_inputs.Problem`` (seeded synthetic problem)."""
         return cls(prob.ne, prob.ne, prob.M, p, prob.rowptr, prob.colidx, prob.vals, prob.mass, family)
 
+    @property
+    def inner_cluster(self) -> bool:
+        """True when the FP32 inner solves run on the cluster-resident solver."""
+        return bool(_lib.LIB.sg_inner_cluster(self.h))
+
     def close(self):
         if getattr(self, "h", None):
             _lib.LIB.sg_destroy(self.h)

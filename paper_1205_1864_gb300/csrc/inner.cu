@@ -1388,6 +1388,7 @@ int inner_solve(sg_problem* h, int dtype, const void* src, int ld_src, int src_t
                 int w, const sg_prec_opts& o, cudaStream_t s) {
   SG_TRY(check_prec_opts(o));
   if (w <= 0) return SG_OK;
+  if (cluster_usable(h, dtype, w)) return inner_solve_cluster(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);
   SG_TRY(ensure_inner_work(h, dtype, std::max(w, h->wmax)));
   if (dtype == SG_F64) return inner_solve_t<double>(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);
   return inner_solve_t<float>(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);

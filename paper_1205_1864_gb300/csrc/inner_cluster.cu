@@ -1,0 +1,892 @@
+// K3 + K4 on chip: the batched inner PCG on A_0 with its V-cycle, one launch
+// per solve, the whole multigrid hierarchy of a column group held in the
+// shared memory of one thread-block cluster.
+//
+// Same method as the stand-alone kernels of inner.cu (Sec. 5: independent
+// preconditioned CG loops on A_0 for the columns of a degree level; the
+// V-cycle with weighted Jacobi, nu sweeps before and after, bilinear
+// transfers and the Galerkin coarse operators of setup.cu as M_0), same
+// per-column stopping rule, status bits and iteration counts. What differs is
+// where the data lives:
+//
+// - A cluster of CLN = 8 CTAs owns 4 columns (one float4 per node). Every
+//   grid with at least CLN rows is split into row strips, strip c on CTA c;
+//   the smaller grids sit in CTA 0 alone. Each strip is stored with a ghost
+//   row above and below and a ghost column left and right; ghosts outside the
+//   grid stay zero, so every stencil phase is branch-free.
+// - A phase that reads neighbours first copies the boundary rows it needs
+//   from the neighbouring CTAs' shared memory (distributed shared memory)
+//   into its ghost rows. Phases that depend on each other are separated by
+//   cluster barriers; the grids held by CTA 0 alone use block barriers.
+// - Per-column sums: the block's sum goes to a slot of its own (one slot per
+//   kind of sum, so a slot is never rewritten while another CTA may read it);
+//   after the cluster barrier every CTA adds the 8 slots in rank order, so all
+//   CTAs hold identical CG scalars and take the same loop decisions.
+// - On the finest grid each thread owns FINE_ITEMS nodes and keeps their
+//   r, x and p in registers; the shared-memory vectors there are the V-cycle
+//   iterate and one more (smoother ping-pong, residual, p_new, q).
+//
+// Eligibility (cluster_setup): a square hierarchy (power-of-two elements)
+// whose shared-memory plan fits one CTA, at least one cluster resident, FP32.
+// Anything else takes the stand-alone kernels.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "sghsc_internal.cuh"
+#include "vec.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sghsc {
+
+constexpr int CLN = 8;          // CTAs per cluster (portable cluster size)
+constexpr int CNT = 1024;       // threads per CTA
+constexpr int CMAXG = 8;        // grids of the hierarchy (127 x 127 has 7)
+constexpr int FINE_ITEMS = 2;   // finest-grid nodes per thread
+
+// One grid of the hierarchy as laid out in every CTA's shared memory. Vector
+// buffers are float4 [(rows + 2) x (nx + 2)] (padded: ghost rows and columns);
+// the stencil holds the strip's own nodes [rows * nx][9]; the inverse diagonal
+// is padded like the vectors (its ghost rows are needed by the fused first
+// two sweeps). The finest grid has no b buffer and no inverse diagonal in
+// shared memory (both are per-thread registers there).
+struct CLevel {
+  int nx, ny, rows, single;
+  unsigned b, x, y, st, di;   // byte offsets into the dynamic shared memory
+  const float* gst;           // stencil [n][9] in global memory
+  const float* gdi;           // inverse diagonal [n]
+};
+
+struct CPlan {
+  int G, gs;        // number of grids; first grid held by CTA 0 alone
+  unsigned bytes;   // dynamic shared memory per CTA
+  int maxcl;        // clusters resident at once (host side: one-wave rule)
+  CLevel L[CMAXG];
+};
+
+struct CArgs {
+  float om;
+  int nu;
+  double tol2;
+  int maxit, fixed;
+  int* status;
+  long long* iacc;
+  int* iters;   // per-column iteration counts out (global column index), or null
+};
+
+namespace {
+
+struct ColState {
+  double rho, bb;
+  int iters, done;
+};
+
+enum { RK_INIT = 0, RK_RHO, RK_PQ, RK_RR, RK_COUNT };
+
+struct Own {
+  int r0, nr;
+};
+
+__device__ __forceinline__ Own own_rows(const CLevel& l, int rank) {
+  if (l.single) return Own{0, rank == 0 ? l.ny : 0};
+  const int r0 = rank * l.rows;
+  return Own{r0, max(0, min(l.ny - r0, l.rows))};
+}
+
+// padded index of local row ly (-1 .. rows) and column x (-1 .. nx)
+__device__ __forceinline__ int pidx(const CLevel& l, int ly, int x) { return (ly + 1) * (l.nx + 2) + x + 1; }
+
+template <typename T>
+__device__ __forceinline__ T* sp(unsigned char* sm, unsigned off) {
+  return reinterpret_cast<T*>(sm + off);
+}
+
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+
+__device__ __forceinline__ void fma4(float4& acc, float a, const float4& v) {
+  acc.x = fmaf(a, v.x, acc.x);
+  acc.y = fmaf(a, v.y, acc.y);
+  acc.z = fmaf(a, v.z, acc.z);
+  acc.w = fmaf(a, v.w, acc.w);
+}
+
+__device__ __forceinline__ float4 add4(const float4& a, const float4& b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+__device__ __forceinline__ float4 sub4(const float4& a, const float4& b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+
+// acc += a * b componentwise (fused)
+__device__ __forceinline__ void dot4(float4& acc, const float4& a, const float4& b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.y = fmaf(a.y, b.y, acc.y);
+  acc.z = fmaf(a.z, b.z, acc.z);
+  acc.w = fmaf(a.w, b.w, acc.w);
+}
+
+__device__ __forceinline__ float comp(const float4& v, int u) {
+  return u == 0 ? v.x : u == 1 ? v.y : u == 2 ? v.z : v.w;
+}
+
+// sum_j a_ij v_j over the 9-point stencil s9 of the node at padded index c
+// (row length W of the padded buffer)
+__device__ __forceinline__ float4 apply9(const float* __restrict__ s9, const float4* v, int W, int c) {
+  float4 acc = f4(0.f);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) fma4(acc, s9[(dy + 1) * 3 + (dx + 1)], v[c + dy * W + dx]);
+  return acc;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Store v at own node (ly, x) of buffer off of grid l; on a distributed grid
+// also into the ghost row of the neighbouring strip that sees this node (the
+// first own row is the ghost row below of CTA rank - 1, the last one the ghost
+// row above of CTA rank + 1). The next cluster barrier publishes both, so a
+// phase never reads the buffer it writes and needs no copy step of its own.
+__device__ __forceinline__ void put(const cg::cluster_group& cl, unsigned char* sm, const CLevel& l, unsigned off,
+                                    int rank, const Own& o, int ly, int x, const float4& v) {
+  float4* b = sp<float4>(sm, off);
+  b[pidx(l, ly, x)] = v;
+  if (l.single) return;
+  if (ly == 0 && o.r0 > 0) cl.map_shared_rank(b, rank - 1)[pidx(l, l.rows, x)] = v;
+  if (ly == o.nr - 1 && o.r0 + o.nr < l.ny) cl.map_shared_rank(b, rank + 1)[pidx(l, -1, x)] = v;
+}
+
+// Interpolation weight of coarse patch entry a (0..2: coarse offset a - 1
+// from floor((f - 1) / 2)) at the fine point f + d (d = -1..1), for a fine
+// coordinate f of parity odd. Coarse node X sits on fine node 2X + 1, so an
+// odd fine point takes its coarse node with weight 1 and an even one the two
+// coarse nodes beside it with weight 1/2 (bilinear interpolation is the
+// product of the x and y weights).
+__device__ __forceinline__ float tw(bool odd, int d, int a) {
+  if (odd) return d < 0 ? (a < 2 ? 0.5f : 0.f) : d == 0 ? (a == 1 ? 1.f : 0.f) : (a > 0 ? 0.5f : 0.f);
+  return d < 0 ? (a == 1 ? 1.f : 0.f) : d == 0 ? (a > 0 ? 0.5f : 0.f) : (a == 2 ? 1.f : 0.f);
+}
+
+// The coarse correction at a fine node (y, x) with stencil s9: pc = (P xc) at
+// the node and apc = sum_j a_ij (P xc)_j over its stencil, from the 3 x 3
+// coarse patch around padded coarse index cc = (floor((y-1)/2), floor((x-1)/2)).
+// A(P xc) = sum_{a,c} K[a][c] xc[a][c] with K = Wy^T S Wx (the x and y
+// interpolation weights of the three fine rows / columns). Patch entries whose
+// weights are all zero (row a = 0 for even y, column 0 for even x) would lie
+// outside the padded strip at the grid edge: they read entry 1 instead, with
+// weight zero.
+__device__ __forceinline__ void coarse_corr(const float* __restrict__ s9, const float4* XC, int Wc, int cc, bool oy,
+                                            bool ox, float4& apc, float4& pc) {
+  float t1[3][3];   // t1[dy][c] = sum_dx s[dy][dx] wx(dx, c)
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      t1[dy][c] = s9[dy * 3 + 0] * tw(ox, -1, c) + s9[dy * 3 + 1] * tw(ox, 0, c) + s9[dy * 3 + 2] * tw(ox, 1, c);
+  apc = f4(0.f);
+  pc = f4(0.f);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ar = (oy || a > 0) ? a : 1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int cr = (ox || c > 0) ? c : 1;
+      const float K = tw(oy, -1, a) * t1[0][c] + tw(oy, 0, a) * t1[1][c] + tw(oy, 1, a) * t1[2][c];
+      const float4 v = XC[cc + (ar - 1) * Wc + (cr - 1)];
+      fma4(apc, K, v);
+      fma4(pc, tw(oy, 0, a) * tw(ox, 0, c), v);
+    }
+  }
+}
+
+// x + om d (b - A x) at the node of padded index c
+__device__ __forceinline__ float4 jacobi_node(const float* __restrict__ s9, const float4* X, int W, int c,
+                                              const float4& b, float d, float om) {
+  const float4 ax = apply9(s9, X, W, c);
+  const float4 xv = X[c];
+  const float dd = om * d;
+  return make_float4(fmaf(dd, b.x - ax.x, xv.x), fmaf(dd, b.y - ax.y, xv.y), fmaf(dd, b.z - ax.z, xv.z),
+                     fmaf(dd, b.w - ax.w, xv.w));
+}
+
+// x' = x + P xc, then x' + om d (b - A x') at fine node (y, x) of padded index c
+__device__ __forceinline__ float4 prolong_jacobi_node(const float* __restrict__ s9, const float4* X, int W, int c,
+                                                      const float4& b, float d, float om, const float4* XC,
+                                                      int Wc, int cc, bool oy, bool ox) {
+  float4 apc, pc;
+  coarse_corr(s9, XC, Wc, cc, oy, ox, apc, pc);
+  const float4 ax = apply9(s9, X, W, c);
+  const float4 xv = add4(X[c], pc);
+  const float dd = om * d;
+  return make_float4(fmaf(dd, b.x - (ax.x + apc.x), xv.x), fmaf(dd, b.y - (ax.y + apc.y), xv.y),
+                     fmaf(dd, b.z - (ax.z + apc.z), xv.z), fmaf(dd, b.w - (ax.w + apc.w), xv.w));
+}
+
+// padded index, in the coarse grid lc as held by CTA rank, of the coarse patch
+// centre of fine node (y, x)
+__device__ __forceinline__ int patch_centre(const CLevel& lc, int rank, int y, int x) {
+  const int r0c = lc.single ? 0 : rank * lc.rows;
+  return pidx(lc, ((y - 1) >> 1) - r0c, (x - 1) >> 1);
+}
+
+// bc = P^T R on the coarse rows Y whose centre fine row 2Y + 1 is one of this
+// CTA's rows of grid l (the fine rows 2Y and 2Y + 2 are own rows or ghosts),
+// stored into the coarse right-hand side of the CTA that owns row Y (and the
+// ghost rows of its neighbours, as put() does). Weights
+// 1 (centre), 1/2 (edge) and 1/4 (corner): the transpose of the bilinear
+// interpolation.
+__device__ void restrict_rows(const cg::cluster_group& cl, unsigned char* sm, const CLevel& l, const Own& o,
+                              unsigned roff, const CLevel& lc, int rank) {
+  const int top = o.r0 + o.nr - 2;
+  if (o.nr == 0 || top < 0) return;
+  const int ylo = o.r0 / 2, yhi = min(top / 2, lc.ny - 1);
+  const float4* R = sp<float4>(sm, roff);
+  const int W = l.nx + 2;
+  const int items = (yhi - ylo + 1) * lc.nx;
+  for (int i = threadIdx.x; i < items; i += blockDim.x) {
+    const int Y = ylo + i / lc.nx, X = i % lc.nx;
+    const int c = pidx(l, 2 * Y + 1 - o.r0, 2 * X + 1);
+    float4 acc = f4(0.f);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) fma4(acc, (dy == 0 ? 1.f : 0.5f) * (dx == 0 ? 1.f : 0.5f), R[c + dy * W + dx]);
+    const int ow = lc.single ? 0 : Y / lc.rows, lr = Y - ow * lc.rows;
+    float4* Bc = sp<float4>(sm, lc.b);
+    cl.map_shared_rank(Bc, ow)[pidx(lc, lr, X)] = acc;
+    if (!lc.single) {
+      if (lr == 0 && ow > 0) cl.map_shared_rank(Bc, ow - 1)[pidx(lc, lc.rows, X)] = acc;
+      if (lr == min(lc.rows, lc.ny - ow * lc.rows) - 1 && Y + 1 < lc.ny)
+        cl.map_shared_rank(Bc, ow + 1)[pidx(lc, -1, X)] = acc;
+    }
+  }
+}
+
+// Fixed-order block sum of the per-thread partials v into *slot (written by
+// thread 0): warp butterflies, then warp 0 over the warp sums.
+__device__ void block_sum4(float4 v, float4* wred, float4* slot) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
+    v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wred[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    float4 s = lane < (int)(blockDim.x >> 5) ? wred[lane] : f4(0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+      s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+    }
+    if (lane == 0) *slot = s;
+  }
+}
+
+// Shared state of one CTA: per-column CG scalars (identical in all CTAs of the
+// cluster), the FP32 step lengths the kernels use, the loop flag, and the
+// reduction scratch.
+struct CShared {
+  float4 wred[CNT / 32];
+  float4 slot[RK_COUNT];
+  ColState cs[4];
+  float alpha[4], beta[4];
+  int active;
+};
+
+// After the cluster barrier that follows the slot writes: lanes 0..3 of warp 0
+// each add the 8 CTAs' slots in rank order and update their column (the
+// scalar updates of the stand-alone finaliser: FP64 from the FP32 totals);
+// rank 0 reports status bits and iteration counts. Ends with a block barrier.
+__device__ void col_step(const cg::cluster_group& cl, CShared& S, int kind, const CArgs& a, int rank) {
+  const int lane = threadIdx.x;
+  if (lane < 4) {
+    float4 tot = f4(0.f);
+#pragma unroll
+    for (int r = 0; r < CLN; ++r) tot = add4(tot, *cl.map_shared_rank(&S.slot[kind], r));
+    const double s = (double)comp(tot, lane);
+    const bool report = rank == 0;
+    ColState c = S.cs[lane];
+    if (kind == RK_INIT) {
+      c.bb = s;
+      c.done = !(s > 0.0);
+      c.iters = 0;
+      S.beta[lane] = 0.f;
+    } else if (!c.done) {
+      if (kind == RK_RHO) {
+        const double beta = c.iters == 0 ? 0.0 : s / c.rho;
+        S.beta[lane] = (float)beta;
+        c.rho = s;
+      } else if (kind == RK_PQ) {
+        double alpha = 0.0;
+        if (!(s > 0.0)) {
+          if (report) atomicOr(a.status, ST_INNER_NOT_SPD);
+          c.done = 1;
+        } else {
+          alpha = c.rho / s;
+        }
+        S.alpha[lane] = (float)alpha;
+      } else {
+        const int it = ++c.iters;
+        bool fin;
+        if (a.fixed > 0) {
+          fin = it >= a.fixed;
+        } else {
+          fin = s <= a.tol2 * c.bb;
+          if (!fin && it >= a.maxit) {
+            fin = true;
+            if (report) atomicOr(a.status, ST_INNER_MAXIT);
+          }
+        }
+        if (!(s == s)) {   // non-finite residual: stop the column and flag it
+          fin = true;
+          if (report) atomicOr(a.status, ST_INNER_NOT_SPD);
+        }
+        c.done = fin;
+        if (fin && report) {
+          atomicAdd((unsigned long long*)&a.iacc[0], (unsigned long long)it);
+          atomicMax(&a.iacc[1], (long long)it);
+        }
+      }
+    }
+    S.cs[lane] = c;
+  }
+  __syncwarp();
+  if (lane == 0) S.active = !(S.cs[0].done && S.cs[1].done && S.cs[2].done && S.cs[3].done);
+  __syncthreads();
+}
+
+// Sum of the per-thread partials v over the cluster into the column scalars
+// (slot kind), then the column update: block sum, cluster barrier, col_step.
+__device__ __forceinline__ void cluster_reduce(const cg::cluster_group& cl, CShared& S, int kind, const float4& v,
+                                               const CArgs& a, int rank) {
+  block_sum4(v, S.wred, &S.slot[kind]);
+  cluster_sync_all();
+  col_step(cl, S, kind, a, rank);
+}
+
+
+// Buffer holding the iterate of grid l after its pre-smoothing (the smoother
+// alternates between x and y: max(0, nu - 2) exchanges) ...
+__device__ __forceinline__ unsigned after_down(const CLevel& l, int nu) { return (max(0, nu - 2) & 1) ? l.y : l.x; }
+
+// ... and after its post-smoothing (nu more); the coarsest grid is solved into x.
+__device__ __forceinline__ unsigned final_buf(const CLevel& l, bool coarsest, int nu) {
+  if (coarsest) return l.x;
+  return ((max(0, nu - 2) + nu) & 1) ? l.y : l.x;
+}
+
+template <bool BLK>
+__device__ __forceinline__ void level_sync() {
+  if (BLK) __syncthreads();
+  else cluster_sync_all();
+}
+
+// f(i, ly, x) for this CTA's nodes of grid l (i: own node index)
+template <typename F>
+__device__ __forceinline__ void for_own(const CLevel& l, const Own& o, F f) {
+  const int n = o.nr * l.nx;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int ly = i / l.nx;
+    f(i, ly, i - ly * l.nx);
+  }
+}
+
+// Restriction side of the V-cycle on a coarse grid g (right-hand side in its
+// b buffer, zero initial iterate): nu sweeps, the residual, and its
+// restriction into grid g + 1. BLK: a grid held by CTA 0 alone, run by CTA 0
+// with block barriers.
+template <bool BLK>
+__device__ void level_down(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int g, int rank, int nu,
+                           float om) {
+  const CLevel& l = L[g];
+  const Own o = own_rows(l, rank);
+  const int W = l.nx + 2;
+  const float* ST = sp<float>(sm, l.st);
+  const float* DI = sp<float>(sm, l.di);
+  const float4* B = sp<float4>(sm, l.b);
+  unsigned xo = l.x, yo = l.y;
+  if (nu >= 2) {
+    // the first two sweeps in one pass: x1 = om D^-1 b at the 9 neighbours,
+    // x2 = x1 + om D^-1 (b - A x1)
+    for_own(l, o, [&](int i, int ly, int x) {
+      const int c = pidx(l, ly, x);
+      const float* s9 = ST + i * 9;
+      float4 ax1 = f4(0.f);
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int j = c + dy * W + dx;
+          fma4(ax1, s9[(dy + 1) * 3 + (dx + 1)] * DI[j], B[j]);
+        }
+      const float dd = om * DI[c];
+      const float4 b = B[c];
+      put(cl, sm, l, xo, rank, o, ly, x,
+          make_float4(dd * b.x + dd * (b.x - om * ax1.x), dd * b.y + dd * (b.y - om * ax1.y),
+                      dd * b.z + dd * (b.z - om * ax1.z), dd * b.w + dd * (b.w - om * ax1.w)));
+    });
+    level_sync<BLK>();
+    for (int s = 2; s < nu; ++s) {
+      const float4* Xi = sp<float4>(sm, xo);
+      for_own(l, o, [&](int i, int ly, int x) {
+        const int c = pidx(l, ly, x);
+        put(cl, sm, l, yo, rank, o, ly, x, jacobi_node(ST + i * 9, Xi, W, c, B[c], DI[c], om));
+      });
+      level_sync<BLK>();
+      const unsigned t = xo; xo = yo; yo = t;
+    }
+  } else {
+    for_own(l, o, [&](int, int ly, int x) {
+      const int c = pidx(l, ly, x);
+      const float dd = om * DI[c];
+      const float4 b = B[c];
+      put(cl, sm, l, xo, rank, o, ly, x, make_float4(dd * b.x, dd * b.y, dd * b.z, dd * b.w));
+    });
+    level_sync<BLK>();
+  }
+  // residual b - A x into the other buffer, then its restriction
+  {
+    const float4* X = sp<float4>(sm, xo);
+    for_own(l, o, [&](int i, int ly, int x) {
+      const int c = pidx(l, ly, x);
+      put(cl, sm, l, yo, rank, o, ly, x, sub4(B[c], apply9(ST + i * 9, X, W, c)));
+    });
+  }
+  level_sync<BLK>();
+  restrict_rows(cl, sm, l, o, yo, L[g + 1], rank);
+  level_sync<BLK>();
+}
+
+// Prolongation side on a coarse grid g: the correction from grid g + 1 with
+// the first post-smoothing sweep in one pass, then nu - 1 more sweeps.
+template <bool BLK>
+__device__ void level_up(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int g, int G, int rank,
+                         int nu, float om) {
+  const CLevel& l = L[g];
+  const CLevel& lc = L[g + 1];
+  const Own o = own_rows(l, rank);
+  const int W = l.nx + 2, Wc = lc.nx + 2;
+  const float* ST = sp<float>(sm, l.st);
+  const float* DI = sp<float>(sm, l.di);
+  const float4* B = sp<float4>(sm, l.b);
+  unsigned xo = after_down(l, nu);
+  unsigned yo = xo == l.x ? l.y : l.x;
+  {
+    const float4* X = sp<float4>(sm, xo);
+    const float4* XC = sp<float4>(sm, final_buf(lc, g + 1 == G - 1, nu));
+    for_own(l, o, [&](int i, int ly, int x) {
+      const int c = pidx(l, ly, x), y = o.r0 + ly;
+      put(cl, sm, l, yo, rank, o, ly, x,
+          prolong_jacobi_node(ST + i * 9, X, W, c, B[c], DI[c], om, XC, Wc, patch_centre(lc, rank, y, x), y & 1,
+                              x & 1));
+    });
+  }
+  level_sync<BLK>();
+  {
+    const unsigned t = xo; xo = yo; yo = t;
+  }
+  for (int s = 1; s < nu; ++s) {
+    const float4* Xi = sp<float4>(sm, xo);
+    for_own(l, o, [&](int i, int ly, int x) {
+      const int c = pidx(l, ly, x);
+      put(cl, sm, l, yo, rank, o, ly, x, jacobi_node(ST + i * 9, Xi, W, c, B[c], DI[c], om));
+    });
+    level_sync<BLK>();
+    const unsigned t = xo; xo = yo; yo = t;
+  }
+}
+
+// The grids gs .. G-1 held by CTA 0: the rest of the V-cycle with block
+// barriers; the coarsest grid (one node) is solved exactly, x = D^-1 b. The
+// result on grid gs is then copied into the other CTAs (the prolongation onto
+// grid gs - 1 reads it everywhere); the caller's cluster barrier publishes it.
+__device__ void block_levels(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int gs, int G, int nu,
+                             float om) {
+  for (int g = gs; g < G - 1; ++g) level_down<true>(cl, sm, L, g, 0, nu, om);
+  {
+    const CLevel& l = L[G - 1];
+    const Own o = own_rows(l, 0);
+    const float* DI = sp<float>(sm, l.di);
+    const float4* B = sp<float4>(sm, l.b);
+    float4* X = sp<float4>(sm, l.x);
+    for_own(l, o, [&](int, int ly, int x) {
+      const int c = pidx(l, ly, x);
+      const float d = DI[c];
+      const float4 b = B[c];
+      X[c] = make_float4(d * b.x, d * b.y, d * b.z, d * b.w);
+    });
+    __syncthreads();
+  }
+  for (int g = G - 2; g >= gs; --g) level_up<true>(cl, sm, L, g, G, 0, nu, om);
+  const CLevel& l = L[gs];
+  float4* v = sp<float4>(sm, final_buf(l, gs == G - 1, nu));
+  const int W = l.nx + 2, m = l.ny * W;
+  for (int i = threadIdx.x; i < (CLN - 1) * m; i += blockDim.x) {
+    const int r = 1 + i / m, j = W + i % m;
+    cl.map_shared_rank(v, r)[j] = v[j];
+  }
+}
+
+// One column group's whole inner solve: gather, PCG iterations with the
+// V-cycle, scatter. Grid: CLN CTAs per 4 columns, clusters of CLN.
+template <typename TS, typename TD>
+__global__ void __launch_bounds__(CNT, 1)
+    k_inner_cluster(const CPlan P, const TS* __restrict__ src, int lds, TD* __restrict__ dst, int ldd, int w,
+                    const CArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ CLevel L[CMAXG];
+  __shared__ CShared S;
+  const cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int col0 = (int)(blockIdx.x / CLN) * 4;
+  const int G = P.G, gs = P.gs, nu = a.nu;
+  const float om = a.om;
+
+  // ---- set-up: grid table, zeroed buffers (ghosts outside the grids stay
+  // zero), own-row stencils, inverse diagonals with their ghost rows
+#pragma unroll
+  for (int g = 0; g < CMAXG; ++g)
+    if ((int)threadIdx.x == g) L[g] = P.L[g];
+  {
+    float4* z = reinterpret_cast<float4*>(sm);
+    for (int i = threadIdx.x; i < (int)(P.bytes / 16); i += CNT) z[i] = f4(0.f);
+  }
+  if (threadIdx.x < 4) {
+    S.cs[threadIdx.x] = ColState{0.0, 0.0, 0, 1};
+    S.alpha[threadIdx.x] = 0.f;
+    S.beta[threadIdx.x] = 0.f;
+  }
+  __syncthreads();
+  for (int g = 0; g < G; ++g) {
+    const CLevel& l = L[g];
+    const Own o = own_rows(l, rank);
+    if (o.nr == 0) continue;
+    float* st = sp<float>(sm, l.st);
+    const float* gst = l.gst + (size_t)o.r0 * l.nx * 9;
+    for (int i = threadIdx.x; i < o.nr * l.nx * 9; i += CNT) st[i] = gst[i];
+    if (g > 0) {
+      float* di = sp<float>(sm, l.di);
+      const int lo = max(o.r0 - 1, 0) - o.r0, hi = min(o.r0 + o.nr + 1, l.ny) - o.r0;
+      for (int i = threadIdx.x; i < (hi - lo) * l.nx; i += CNT) {
+        const int ly = lo + i / l.nx, x = i % l.nx;
+        di[pidx(l, ly, x)] = l.gdi[(size_t)(o.r0 + ly) * l.nx + x];
+      }
+    }
+  }
+
+  // ---- finest grid: r = b, x = 0, p = 0 in registers; ||b||^2; the first
+  // smoothing sweep from zero (om D^-1 r) into the iterate buffer
+  const CLevel& L0 = L[0];
+  const Own o0 = own_rows(L0, rank);
+  const int nx0 = L0.nx, W0 = nx0 + 2, n0 = o0.nr * nx0;
+  const float* ST0 = sp<float>(sm, L0.st);
+  float4 r[FINE_ITEMS], xs[FINE_ITEMS], po[FINE_ITEMS];
+  float d0[FINE_ITEMS];
+  int lyx[FINE_ITEMS];   // own row << 16 | column of each item
+  unsigned zo = L0.x, so = L0.y;
+  float4 part = f4(0.f);
+#pragma unroll
+  for (int k = 0; k < FINE_ITEMS; ++k) {
+    const int i = threadIdx.x + k * CNT;
+    r[k] = f4(0.f);
+    xs[k] = f4(0.f);
+    po[k] = f4(0.f);
+    d0[k] = 0.f;
+    lyx[k] = 0;
+    if (i < n0) {
+      const int ly = i / nx0, x = i - ly * nx0;
+      lyx[k] = (ly << 16) | x;
+      const size_t node = (size_t)o0.r0 * nx0 + i;
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = col0 + u < w ? (float)src[node * lds + col0 + u] : 0.f;
+      r[k] = make_float4(v[0], v[1], v[2], v[3]);
+      d0[k] = L0.gdi[node];
+      dot4(part, r[k], r[k]);
+      const float dd = om * d0[k];
+      put(cl, sm, L0, zo, rank, o0, ly, x, make_float4(dd * v[0], dd * v[1], dd * v[2], dd * v[3]));
+    }
+  }
+  cluster_reduce(cl, S, RK_INIT, part, a, rank);
+#define FINE_ITEM(k)                                   \
+  const int i = threadIdx.x + (k) * CNT;               \
+  if (i >= n0) continue;                               \
+  const int ly = lyx[k] >> 16, x = lyx[k] & 0xffff;    \
+  const int c = (ly + 1) * W0 + x + 1;
+
+  const int cap = (a.fixed > 0 ? a.fixed : a.maxit) + 1;
+  for (int it = 0; it < cap && S.active; ++it) {
+    // ---- V-cycle, finest grid down: sweeps 2..nu, residual, restriction
+    for (int s = 1; s < nu; ++s) {
+      const float4* Z = sp<float4>(sm, zo);
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        FINE_ITEM(k)
+        put(cl, sm, L0, so, rank, o0, ly, x, jacobi_node(ST0 + i * 9, Z, W0, c, r[k], d0[k], om));
+      }
+      cluster_sync_all();
+      const unsigned t = zo; zo = so; so = t;
+    }
+    {
+      const float4* Z = sp<float4>(sm, zo);
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        FINE_ITEM(k)
+        put(cl, sm, L0, so, rank, o0, ly, x, sub4(r[k], apply9(ST0 + i * 9, Z, W0, c)));
+      }
+    }
+    cluster_sync_all();
+    restrict_rows(cl, sm, L0, o0, so, L[1], rank);
+    cluster_sync_all();
+    // ---- coarse grids
+    for (int g = 1; g < gs; ++g) level_down<false>(cl, sm, L, g, rank, nu, om);
+    if (rank == 0) block_levels(cl, sm, L, gs, G, nu, om);
+    cluster_sync_all();
+    for (int g = gs - 1; g >= 1; --g) level_up<false>(cl, sm, L, g, G, rank, nu, om);
+    // ---- finest grid up: correction + sweep, nu - 1 more sweeps; the last
+    // one also sums r . z
+    const float4* XC = sp<float4>(sm, final_buf(L[1], G == 2, nu));
+    const int Wc = L[1].nx + 2;
+    for (int s = 1; s <= nu; ++s) {
+      const float4* Z = sp<float4>(sm, zo);
+      part = f4(0.f);
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        FINE_ITEM(k)
+        float4 v;
+        if (s == 1) {
+          const int y = o0.r0 + ly;
+          v = prolong_jacobi_node(ST0 + i * 9, Z, W0, c, r[k], d0[k], om, XC, Wc, patch_centre(L[1], rank, y, x),
+                                  y & 1, x & 1);
+        } else {
+          v = jacobi_node(ST0 + i * 9, Z, W0, c, r[k], d0[k], om);
+        }
+        put(cl, sm, L0, so, rank, o0, ly, x, v);
+        dot4(part, r[k], v);
+      }
+      if (s == nu) cluster_reduce(cl, S, RK_RHO, part, a, rank);
+      else cluster_sync_all();
+      const unsigned t = zo; zo = so; so = t;
+    }
+    // ---- p = z + beta p (registers and the other buffer), q = A p, p . q
+    {
+      const float4 bt = make_float4(S.beta[0], S.beta[1], S.beta[2], S.beta[3]);
+      const float4* Z = sp<float4>(sm, zo);
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        FINE_ITEM(k)
+        const float4 z = Z[c];
+        po[k] = make_float4(fmaf(bt.x, po[k].x, z.x), fmaf(bt.y, po[k].y, z.y), fmaf(bt.z, po[k].z, z.z),
+                            fmaf(bt.w, po[k].w, z.w));
+        put(cl, sm, L0, so, rank, o0, ly, x, po[k]);
+      }
+    }
+    cluster_sync_all();
+    part = f4(0.f);
+    {
+      const float4* Pn = sp<float4>(sm, so);
+      float4* Z = sp<float4>(sm, zo);
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        FINE_ITEM(k)
+        const float4 q = apply9(ST0 + i * 9, Pn, W0, c);
+        dot4(part, po[k], q);
+        Z[c] = q;
+      }
+    }
+    cluster_reduce(cl, S, RK_PQ, part, a, rank);
+    // ---- x += alpha p, r -= alpha q on the unfinished columns; r . r; the
+    // next V-cycle's first sweep om D^-1 r
+    {
+      const float al0 = S.alpha[0], al1 = S.alpha[1], al2 = S.alpha[2], al3 = S.alpha[3];
+      const bool dn0 = S.cs[0].done, dn1 = S.cs[1].done, dn2 = S.cs[2].done, dn3 = S.cs[3].done;
+      const float4* Z = sp<float4>(sm, zo);
+      part = f4(0.f);
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        FINE_ITEM(k)
+        const float4 q = Z[c];
+        if (!dn0) { xs[k].x = fmaf(al0, po[k].x, xs[k].x); r[k].x = fmaf(-al0, q.x, r[k].x); }
+        if (!dn1) { xs[k].y = fmaf(al1, po[k].y, xs[k].y); r[k].y = fmaf(-al1, q.y, r[k].y); }
+        if (!dn2) { xs[k].z = fmaf(al2, po[k].z, xs[k].z); r[k].z = fmaf(-al2, q.z, r[k].z); }
+        if (!dn3) { xs[k].w = fmaf(al3, po[k].w, xs[k].w); r[k].w = fmaf(-al3, q.w, r[k].w); }
+        dot4(part, r[k], r[k]);
+        const float dd = om * d0[k];
+        put(cl, sm, L0, zo, rank, o0, ly, x, make_float4(dd * r[k].x, dd * r[k].y, dd * r[k].z, dd * r[k].w));
+      }
+    }
+    cluster_reduce(cl, S, RK_RR, part, a, rank);
+  }
+#undef FINE_ITEM
+
+  // ---- scatter the solution
+#pragma unroll
+  for (int k = 0; k < FINE_ITEMS; ++k) {
+    const int i = threadIdx.x + k * CNT;
+    if (i < n0) {
+      const size_t node = (size_t)o0.r0 * nx0 + i;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (col0 + u < w) dst[node * ldd + col0 + u] = (TD)comp(xs[k], u);
+    }
+  }
+  if (rank == 0 && threadIdx.x < 4 && a.iters && col0 + (int)threadIdx.x < w)
+    a.iters[col0 + threadIdx.x] = S.cs[threadIdx.x].iters;
+  // no CTA leaves while another may still read its shared memory
+  cluster_sync_all();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side ---
+
+template <typename TS, typename TD>
+static int cluster_kernel_ok(unsigned bytes, int optin) {
+  auto kern = k_inner_cluster<TS, TD>;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 0;
+  if ((long long)bytes + (long long)fa.sharedSizeBytes > optin) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CLN);
+  cfg.blockDim = dim3(CNT);
+  cfg.dynamicSmemBytes = bytes;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CLN;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) return 0;
+  return nclusters;
+}
+
+// Build the shared-memory plan of the hierarchy and decide whether the
+// cluster solver can run it (h->cl_plan stays null when it cannot). Any CUDA
+// error on this path only disables the cluster solver; it is cleared.
+int cluster_setup(sg_problem* h) {
+  const char* ev = getenv("SGHSC_NO_CLUSTER");
+  if (ev && ev[0] == '1') return SG_OK;
+  const int G = (int)h->grids.size();
+  if (G < 2 || G > CMAXG) return SG_OK;
+  CPlan P{};
+  unsigned off = 0;
+  auto take = [&](size_t bytes) {
+    const unsigned o = off;
+    off += (unsigned)((bytes + 15) & ~(size_t)15);
+    return o;
+  };
+  int gs = G;
+  for (int g = 0; g < G; ++g) {
+    const GridLevel& gr = h->grids[g];
+    CLevel& l = P.L[g];
+    if (gr.nx != gr.ny || !gr.st32 || !gr.dinv32) return SG_OK;
+    l.nx = gr.nx;
+    l.ny = gr.ny;
+    l.single = gr.ny < CLN;
+    l.rows = l.single ? gr.ny : (gr.ny + CLN - 1) / CLN;
+    if (l.single) {
+      if (gs == G) gs = g;
+    } else {
+      if (gs < G) return SG_OK;                 // strips below a grid held by CTA 0
+      if (2 * l.nx > CNT) return SG_OK;         // ghost copy: one thread per ghost node
+    }
+    const size_t vec = (size_t)(l.rows + 2) * (l.nx + 2) * 16;
+    l.b = g > 0 ? take(vec) : 0;
+    l.x = take(vec);
+    l.y = take(vec);
+    l.st = take((size_t)l.rows * l.nx * 9 * sizeof(float));
+    l.di = g > 0 ? take((size_t)(l.rows + 2) * (l.nx + 2) * sizeof(float)) : 0;
+    l.gst = gr.st32;
+    l.gdi = gr.dinv32;
+  }
+  if (gs == 0 || gs == G) return SG_OK;
+  if ((long long)P.L[0].rows * P.L[0].nx > (long long)FINE_ITEMS * CNT) return SG_OK;
+  for (int g = 0; g + 1 < gs; ++g)   // strips of consecutive grids line up (row 2Y+1 over row Y)
+    if (P.L[g].rows != 2 * P.L[g + 1].rows || P.L[g + 1].nx != (P.L[g].nx - 1) / 2) return SG_OK;
+  P.G = G;
+  P.gs = gs;
+  P.bytes = off;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_OK;
+  }
+  const int maxcl = std::min(std::min(cluster_kernel_ok<double, float>(off, optin), cluster_kernel_ok<float, float>(off, optin)),
+                             std::min(cluster_kernel_ok<double, double>(off, optin), cluster_kernel_ok<float, double>(off, optin)));
+  cudaGetLastError();
+  if (maxcl < 1) return SG_OK;
+  P.maxcl = maxcl;
+  h->cl_plan = new CPlan(P);
+  return SG_OK;
+}
+
+void cluster_free(sg_problem* h) {
+  delete (CPlan*)h->cl_plan;
+  h->cl_plan = nullptr;
+}
+
+// A batch takes the cluster solver when all its clusters are resident at once:
+// the solve of one cluster is latency-bound, so a second wave would double the
+// time, and the stand-alone kernels are then faster.
+bool cluster_usable(const sg_problem* h, int dtype, int w) {
+  return dtype == SG_F32 && h->cl_plan != nullptr && ceil_div(w, 4) <= ((const CPlan*)h->cl_plan)->maxcl;
+}
+
+}  // namespace sghsc
+
+extern "C" int sg_inner_cluster(const sg_problem* h) { return h && h->cl_plan ? 1 : 0; }
+
+namespace sghsc {
+
+int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void* dst, int ldd, int dst_t, int w,
+                        const sg_prec_opts& o, cudaStream_t s) {
+  const CPlan& P = *(const CPlan*)h->cl_plan;
+  CArgs a;
+  a.om = (float)o.omega;
+  a.nu = o.nu;
+  a.tol2 = o.inner_tol * o.inner_tol;
+  a.maxit = o.inner_maxit;
+  a.fixed = o.inner_fixed_iters;
+  a.status = h->status;
+  a.iacc = h->iacc;
+  a.iters = h->iw32.iters && h->iw32.wcap >= w ? h->iw32.iters : nullptr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ceil_div(w, 4) * CLN));
+  cfg.blockDim = dim3(CNT);
+  cfg.dynamicSmemBytes = P.bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CLN;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (src_t == SG_F64 && dst_t == SG_F64)
+    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<double, double>, P, (const double*)src, lds, (double*)dst, ldd, w, a));
+  else if (src_t == SG_F64)
+    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<double, float>, P, (const double*)src, lds, (float*)dst, ldd, w, a));
+  else if (dst_t == SG_F64)
+    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<float, double>, P, (const float*)src, lds, (double*)dst, ldd, w, a));
+  else
+    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<float, float>, P, (const float*)src, lds, (float*)dst, ldd, w, a));
+  note_launch();
+  return SG_OK;
+}
+
+}  // namespace sghsc

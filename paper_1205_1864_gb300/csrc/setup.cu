@@ -306,6 +306,7 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   h->cb_level = (int)h->grids.size();
   for (int g = 0; g < (int)h->grids.size(); ++g)
     if (h->grids[g].n <= 1024) { h->cb_level = g; break; }
+  SG_TRY(cluster_setup(h));
   for (auto& cs : h->cap) SG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   {
     const char* ev = getenv("SGHSC_EAGER");
@@ -435,6 +436,7 @@ void sg_destroy(sg_problem* h) {
   if (h->cap[0]) cudaDeviceSynchronize();
   clear_graphs(h);
   free_inner_work(h);
+  cluster_free(h);
   void* bufs[] = {h->rowptr, h->colidx, h->vals64, h->vals32, h->mass64, h->R32, h->Z32, h->T32, h->R64w,
                   h->T64, h->fF, h->fx, h->fr, h->fz, h->fpA, h->fpB, h->fq, h->opart, h->osc, h->octl,
                   h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev};

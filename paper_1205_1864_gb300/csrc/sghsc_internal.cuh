@@ -131,6 +131,7 @@ struct sg_problem {
   // multigrid
   std::vector<sghsc::GridLevel> grids;
   int cb_level = 0;                         // first grid handled by the in-block coarse V-cycle
+  void* cl_plan = nullptr;                  // shared-memory plan of the cluster inner solver (null: not usable)
   // workspace
   sghsc::InnerWork iw32, iw64;
   float* R32 = nullptr;                     // n x P working residual (mixed HSC)
@@ -191,6 +192,17 @@ int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const 
 int inner_solve(sg_problem* h, int dtype, const void* src, int ld_src, int src_t, void* dst,
                 int ld_dst, int dst_t, int w, const sg_prec_opts& o, cudaStream_t s);
 int check_prec_opts(const sg_prec_opts& o);
+
+// ---- cluster-resident inner solver (inner_cluster.cu) ----
+// Plan the on-chip hierarchy after the grids are built (leaves cl_plan null
+// when the hierarchy does not fit, or SGHSC_NO_CLUSTER=1).
+int cluster_setup(sg_problem* h);
+void cluster_free(sg_problem* h);
+// True when an FP32 batch of w columns takes the cluster solver.
+bool cluster_usable(const sg_problem* h, int dtype, int w);
+// inner_solve for FP32 on a usable handle: one cluster launch per solve.
+int inner_solve_cluster(sg_problem* h, const void* src, int ld_src, int src_t, void* dst, int ld_dst, int dst_t,
+                        int w, const sg_prec_opts& o, cudaStream_t s);
 
 // ---- HSC / mean preconditioner (hsc.cu) ----
 int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o);

@@ -1,0 +1,147 @@
+"""The cluster-resident inner solver (one launch per batched inner PCG, the
+multigrid hierarchy in the shared memory of 8-block clusters) against the
+FP64 oracle and against the stand-alone kernels, on seeded inputs: fixed
+iteration counts element by element, tolerance-driven solves by their true
+residuals and iteration counts, Algorithm 1 and the outer solve."""
+import os
+
+import numpy as np
+import pytest
+
+import sg_inputs as S
+from oracle import gmg, hsc, krylov, sg_operator as so
+from tests.gpu_common import problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1205_1864_gb300 as L
+    return L
+
+
+def _t(x, dtype=None):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype or torch.float64, device="cuda")
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+def _pair(lib, prob, p):
+    """(handle on the cluster solver, handle on the stand-alone kernels)."""
+    h1 = lib.SGProblem.from_inputs(prob, p)
+    os.environ["SGHSC_NO_CLUSTER"] = "1"
+    try:
+        h0 = lib.SGProblem.from_inputs(prob, p)
+    finally:
+        del os.environ["SGHSC_NO_CLUSTER"]
+    return h1, h0
+
+
+@pytest.mark.parametrize("ne", [16, 32, 64, 128])
+def test_cluster_solver_selected(lib, ne):
+    prob, A, G, off = problem(ne, 2, 1)
+    h1, h0 = _pair(lib, prob, 1)
+    assert h1.inner_cluster and not h0.inner_cluster
+
+
+@pytest.mark.parametrize("ne,w,nu,omega", [(16, 7, 2, 0.8), (32, 13, 1, 0.8), (64, 9, 3, 0.7), (128, 37, 2, 0.8)])
+def test_cluster_fixed_iterations_parity(lib, ne, w, nu, omega):
+    """Three V-cycle-preconditioned CG steps per column (nu sweeps, weight
+    omega) against the column-wise oracle; a zero column stays zero; the
+    padded columns of the last group (w not a multiple of 4) are not written."""
+    import torch
+    prob, A, G, off = problem(ne, 2, 1)
+    h = lib.SGProblem.from_inputs(prob, 1)
+    assert h.inner_cluster
+    lv = gmg.hierarchy(A[0], ne)
+    B = S.random_block(prob.n, w, seed=21 + ne).astype(np.float32).astype(np.float64)
+    B[:, 2] = 0.0
+    o = lib.prec_opts(inner_fixed_iters=3, nu=nu, omega=omega)
+    X, it = lib.sg_inner_solve(h, _t(B, torch.float32), o)
+    ref, it_ref = krylov.pcg_columns(lambda v: A[0] @ v, B, lambda r: gmg.vcycle(lv, r, nu=nu, omega=omega),
+                                     tol=0.0, maxit=3, fixed_iters=3)
+    assert list(it) == list(it_ref)
+    X = _np(X)
+    scale = np.abs(ref).max(axis=0, keepdims=True) + 1e-300
+    assert np.all(np.abs(X - ref) <= 1e-4 * scale)
+    assert np.all(X[:, 2] == 0.0)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4])
+def test_cluster_tolerance_matches_stand_alone(lib, tol):
+    """Degree-level widths of the 128x128, M=6 workload: every column reaches
+    its tolerance (true residual, FP64), and the iteration counts of the two
+    solvers agree to within one (FP32 rounding can move a column across the
+    threshold)."""
+    import torch
+    prob, A, G, off = problem(128, 2, 1)
+    h1, h0 = _pair(lib, prob, 1)
+    for w, seed in [(1, 31), (6, 32), (21, 33), (56, 34)]:
+        B = S.random_block(prob.n, w, seed=seed)
+        B[:, ::5] *= 1e-3
+        o = lib.prec_opts(inner_tol=tol)
+        X1, it1 = lib.sg_inner_solve(h1, _t(B, torch.float32), o)
+        X0, it0 = lib.sg_inner_solve(h0, _t(B, torch.float32), o)
+        X1 = _np(X1)
+        B32 = B.astype(np.float32).astype(np.float64)
+        res = np.linalg.norm(B32 - A[0] @ X1, axis=0) / np.linalg.norm(B32, axis=0)
+        assert np.all(res <= 2 * tol), (w, res.max())
+        assert np.all(np.abs(np.asarray(it1) - np.asarray(it0)) <= 1), (w, it1, it0)
+        assert np.all(np.asarray(it1) >= 1)
+
+
+def test_cluster_maxit_caps_every_column(lib):
+    """inner_maxit ends every unfinished column after that many iterations (a
+    capped inner loop is not an error); both solvers give the same iterate up
+    to FP32 rounding."""
+    import torch
+    prob, A, G, off = problem(64, 2, 1)
+    h1, h0 = _pair(lib, prob, 1)
+    B = S.random_block(prob.n, 10, seed=41)
+    o = lib.prec_opts(inner_tol=1e-12, inner_maxit=2)
+    X1, it1 = lib.sg_inner_solve(h1, _t(B, torch.float32), o)
+    X0, it0 = lib.sg_inner_solve(h0, _t(B, torch.float32), o)
+    assert list(it1) == [2] * 10 and list(it0) == [2] * 10
+    X1, X0 = _np(X1), _np(X0)
+    assert np.abs(X1 - X0).max() <= 1e-5 * np.abs(X0).max()
+
+
+def test_cluster_hsc_matches_oracle_and_stand_alone(lib):
+    """Algorithm 1 with FP32 inner solves of fixed length: oracle within the
+    mixed-precision bound; the two inner solvers within FP32 rounding."""
+    prob, A, G, off = problem(32, 3, 3)
+    h1, h0 = _pair(lib, prob, 3)
+    lv = gmg.hierarchy(A[0], 32)
+    R = S.random_block(prob.n, h1.P, seed=42)
+    o = lib.prec_opts(precision=lib.SG_F32, inner_fixed_iters=4)
+    Z1 = _np(lib.hsc_precond_apply(h1, _t(R), o))
+    Z0 = _np(lib.hsc_precond_apply(h0, _t(R), o))
+
+    def dsolve(l, X):
+        return krylov.pcg_columns(lambda v: A[0] @ v, X, lambda r: gmg.vcycle(lv, r), tol=0.0, maxit=4,
+                                  fixed_iters=4)[0]
+    ref = hsc.hsc_apply(A, G, off, R, dsolve=dsolve)
+    assert np.abs(Z1 - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert np.abs(Z1 - Z0).max() <= 2e-5 * np.abs(ref).max()
+
+
+def test_cluster_solve_to_1e8_matches_direct(lib):
+    """The mixed-precision HSC-FCG solve on the cluster solver reaches the
+    relative residual 1e-8 and matches the oracle's direct solve."""
+    prob, A, G, off = problem(16, 3, 3, 0.2, 0.5)
+    h1, h0 = _pair(lib, prob, 3)
+    F = S.make_rhs(prob, 3)
+    ref = so.direct_solve(A, G, F)
+    o = lib.solve_opts(lib.prec_opts(precision=lib.SG_F32), precond=lib.SG_PREC_HSC, tol=1e-8)
+    U1, s1 = lib.sg_solve(h1, _t(F), o)
+    U0, s0 = lib.sg_solve(h0, _t(F), o)
+    assert s1.true_rel_res <= 1e-8 * 1.01
+    assert np.abs(_np(U1) - ref).max() <= 1e-6 * np.abs(ref).max()
+    assert abs(s1.iterations - s0.iterations) <= 1
+    assert s1.inner_iters_total > 0 and s1.inner_iters_max >= 1
