@@ -22,9 +22,11 @@
 //   kind of sum, so a slot is never rewritten while another CTA may read it);
 //   after the cluster barrier every CTA adds the 8 slots in rank order, so all
 //   CTAs hold identical CG scalars and take the same loop decisions.
-// - On the finest grid each thread owns FINE_ITEMS nodes and keeps their
-//   r, x and p in registers; the shared-memory vectors there are the V-cycle
-//   iterate and one more (smoother ping-pong, residual, p_new, q).
+// - On the finest grid each thread owns FINE_ITEMS nodes and keeps their r
+//   and p in registers; the solution accumulates in the output block (x += alpha
+//   p once per iteration, in the output's precision); the shared-memory vectors
+//   there are the V-cycle iterate and one more (smoother ping-pong, residual,
+//   p_new, q).
 //
 // Eligibility (cluster_setup): a square hierarchy (power-of-two elements)
 // whose shared-memory plan fits one CTA, at least one cluster resident, FP32.
@@ -42,9 +44,9 @@ namespace cg = cooperative_groups;
 namespace sghsc {
 
 constexpr int CLN = 8;          // CTAs per cluster (portable cluster size)
-constexpr int CNT = 1024;       // threads per CTA
+constexpr int CNT = 512;        // threads per CTA (128 registers each: no spills)
 constexpr int CMAXG = 8;        // grids of the hierarchy (127 x 127 has 7)
-constexpr int FINE_ITEMS = 2;   // finest-grid nodes per thread
+constexpr int FINE_ITEMS = 4;   // finest-grid nodes per thread
 
 // One grid of the hierarchy as laid out in every CTA's shared memory. Vector
 // buffers are float4 [(rows + 2) x (nx + 2)] (padded: ghost rows and columns);
@@ -74,6 +76,7 @@ struct CArgs {
   int* status;
   long long* iacc;
   int* iters;   // per-column iteration counts out (global column index), or null
+  float4* xs;   // solution scratch [cluster][n]: one float4 (4 columns) per node
 };
 
 namespace {
@@ -143,6 +146,18 @@ __device__ __forceinline__ float4 apply9(const float* __restrict__ s9, const flo
   return acc;
 }
 
+// 4-byte global -> shared copy without a register round trip (cp.async);
+// copy_async_wait completes this thread's copies.
+__device__ __forceinline__ void copy_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void copy_async_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
@@ -161,6 +176,12 @@ __device__ __forceinline__ void put(const cg::cluster_group& cl, unsigned char* 
   if (ly == 0 && o.r0 > 0) cl.map_shared_rank(b, rank - 1)[pidx(l, l.rows, x)] = v;
   if (ly == o.nr - 1 && o.r0 + o.nr < l.ny) cl.map_shared_rank(b, rank + 1)[pidx(l, -1, x)] = v;
 }
+
+// Compiler scheduling fence: memory accesses are not moved across it. Placed
+// between the finest-grid nodes of a thread and between the parts of the
+// prolongation, so not all their loads are in flight at once (their
+// registers would spill).
+__device__ __forceinline__ void item_fence() { asm volatile("" ::: "memory"); }
 
 // Interpolation weight of coarse patch entry a (0..2: coarse offset a - 1
 // from floor((f - 1) / 2)) at the fine point f + d (d = -1..1), for a fine
@@ -193,6 +214,7 @@ __device__ __forceinline__ void coarse_corr(const float* __restrict__ s9, const 
   pc = f4(0.f);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    item_fence();
     const int ar = (oy || a > 0) ? a : 1;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -219,9 +241,10 @@ __device__ __forceinline__ float4 jacobi_node(const float* __restrict__ s9, cons
 __device__ __forceinline__ float4 prolong_jacobi_node(const float* __restrict__ s9, const float4* X, int W, int c,
                                                       const float4& b, float d, float om, const float4* XC,
                                                       int Wc, int cc, bool oy, bool ox) {
+  const float4 ax = apply9(s9, X, W, c);
+  item_fence();
   float4 apc, pc;
   coarse_corr(s9, XC, Wc, cc, oy, ox, apc, pc);
-  const float4 ax = apply9(s9, X, W, c);
   const float4 xv = add4(X[c], pc);
   const float dd = om * d;
   return make_float4(fmaf(dd, b.x - (ax.x + apc.x), xv.x), fmaf(dd, b.y - (ax.y + apc.y), xv.y),
@@ -569,22 +592,25 @@ __global__ void __launch_bounds__(CNT, 1)
     S.beta[threadIdx.x] = 0.f;
   }
   __syncthreads();
+  // (asynchronous copies, all in flight together; completed before the first
+  // reduction's barrier)
   for (int g = 0; g < G; ++g) {
     const CLevel& l = L[g];
     const Own o = own_rows(l, rank);
     if (o.nr == 0) continue;
     float* st = sp<float>(sm, l.st);
     const float* gst = l.gst + (size_t)o.r0 * l.nx * 9;
-    for (int i = threadIdx.x; i < o.nr * l.nx * 9; i += CNT) st[i] = gst[i];
+    for (int i = threadIdx.x; i < o.nr * l.nx * 9; i += CNT) copy_async4(st + i, gst + i);
     if (g > 0) {
       float* di = sp<float>(sm, l.di);
       const int lo = max(o.r0 - 1, 0) - o.r0, hi = min(o.r0 + o.nr + 1, l.ny) - o.r0;
       for (int i = threadIdx.x; i < (hi - lo) * l.nx; i += CNT) {
         const int ly = lo + i / l.nx, x = i % l.nx;
-        di[pidx(l, ly, x)] = l.gdi[(size_t)(o.r0 + ly) * l.nx + x];
+        copy_async4(di + pidx(l, ly, x), l.gdi + (size_t)(o.r0 + ly) * l.nx + x);
       }
     }
   }
+  copy_async_wait();
 
   // ---- finest grid: r = b, x = 0, p = 0 in registers; ||b||^2; the first
   // smoothing sweep from zero (om D^-1 r) into the iterate buffer
@@ -592,7 +618,9 @@ __global__ void __launch_bounds__(CNT, 1)
   const Own o0 = own_rows(L0, rank);
   const int nx0 = L0.nx, W0 = nx0 + 2, n0 = o0.nr * nx0;
   const float* ST0 = sp<float>(sm, L0.st);
-  float4 r[FINE_ITEMS], xs[FINE_ITEMS], po[FINE_ITEMS];
+  float4 r[FINE_ITEMS], po[FINE_ITEMS];   // the solution accumulates in a.xs
+  // this CTA's nodes of the cluster's solution scratch (recomputed where used)
+#define XG (a.xs + (size_t)(blockIdx.x / CLN) * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
   float d0[FINE_ITEMS];
   int lyx[FINE_ITEMS];   // own row << 16 | column of each item
   unsigned zo = L0.x, so = L0.y;
@@ -601,7 +629,6 @@ __global__ void __launch_bounds__(CNT, 1)
   for (int k = 0; k < FINE_ITEMS; ++k) {
     const int i = threadIdx.x + k * CNT;
     r[k] = f4(0.f);
-    xs[k] = f4(0.f);
     po[k] = f4(0.f);
     d0[k] = 0.f;
     lyx[k] = 0;
@@ -612,6 +639,7 @@ __global__ void __launch_bounds__(CNT, 1)
       float v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = col0 + u < w ? (float)src[node * lds + col0 + u] : 0.f;
+      XG[i] = f4(0.f);
       r[k] = make_float4(v[0], v[1], v[2], v[3]);
       d0[k] = L0.gdi[node];
       dot4(part, r[k], r[k]);
@@ -635,6 +663,7 @@ __global__ void __launch_bounds__(CNT, 1)
       for (int k = 0; k < FINE_ITEMS; ++k) {
         FINE_ITEM(k)
         put(cl, sm, L0, so, rank, o0, ly, x, jacobi_node(ST0 + i * 9, Z, W0, c, r[k], d0[k], om));
+        item_fence();
       }
       cluster_sync_all();
       const unsigned t = zo; zo = so; so = t;
@@ -645,6 +674,7 @@ __global__ void __launch_bounds__(CNT, 1)
       for (int k = 0; k < FINE_ITEMS; ++k) {
         FINE_ITEM(k)
         put(cl, sm, L0, so, rank, o0, ly, x, sub4(r[k], apply9(ST0 + i * 9, Z, W0, c)));
+        item_fence();
       }
     }
     cluster_sync_all();
@@ -675,6 +705,7 @@ __global__ void __launch_bounds__(CNT, 1)
         }
         put(cl, sm, L0, so, rank, o0, ly, x, v);
         dot4(part, r[k], v);
+        item_fence();
       }
       if (s == nu) cluster_reduce(cl, S, RK_RHO, part, a, rank);
       else cluster_sync_all();
@@ -704,6 +735,7 @@ __global__ void __launch_bounds__(CNT, 1)
         const float4 q = apply9(ST0 + i * 9, Pn, W0, c);
         dot4(part, po[k], q);
         Z[c] = q;
+        item_fence();
       }
     }
     cluster_reduce(cl, S, RK_PQ, part, a, rank);
@@ -713,15 +745,37 @@ __global__ void __launch_bounds__(CNT, 1)
       const float al0 = S.alpha[0], al1 = S.alpha[1], al2 = S.alpha[2], al3 = S.alpha[3];
       const bool dn0 = S.cs[0].done, dn1 = S.cs[1].done, dn2 = S.cs[2].done, dn3 = S.cs[3].done;
       const float4* Z = sp<float4>(sm, zo);
+      const bool up[4] = {!dn0 && col0 < w, !dn1 && col0 + 1 < w, !dn2 && col0 + 2 < w, !dn3 && col0 + 3 < w};
+      const float al[4] = {al0, al1, al2, al3};
+      // x += alpha p in the scratch (coalesced float4 per node; the loads
+      // first, so they are in flight together)
+      float4 xv[FINE_ITEMS];
+      float4* xg = XG;
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        const int i = threadIdx.x + k * CNT;
+        if (i < n0) xv[k] = xg[i];
+      }
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        const int i = threadIdx.x + k * CNT;
+        if (i >= n0) continue;
+        float4 v = xv[k];
+        if (up[0]) v.x = fmaf(al[0], po[k].x, v.x);
+        if (up[1]) v.y = fmaf(al[1], po[k].y, v.y);
+        if (up[2]) v.z = fmaf(al[2], po[k].z, v.z);
+        if (up[3]) v.w = fmaf(al[3], po[k].w, v.w);
+        xg[i] = v;
+      }
       part = f4(0.f);
 #pragma unroll
       for (int k = 0; k < FINE_ITEMS; ++k) {
         FINE_ITEM(k)
         const float4 q = Z[c];
-        if (!dn0) { xs[k].x = fmaf(al0, po[k].x, xs[k].x); r[k].x = fmaf(-al0, q.x, r[k].x); }
-        if (!dn1) { xs[k].y = fmaf(al1, po[k].y, xs[k].y); r[k].y = fmaf(-al1, q.y, r[k].y); }
-        if (!dn2) { xs[k].z = fmaf(al2, po[k].z, xs[k].z); r[k].z = fmaf(-al2, q.z, r[k].z); }
-        if (!dn3) { xs[k].w = fmaf(al3, po[k].w, xs[k].w); r[k].w = fmaf(-al3, q.w, r[k].w); }
+        if (!dn0) r[k].x = fmaf(-al0, q.x, r[k].x);
+        if (!dn1) r[k].y = fmaf(-al1, q.y, r[k].y);
+        if (!dn2) r[k].z = fmaf(-al2, q.z, r[k].z);
+        if (!dn3) r[k].w = fmaf(-al3, q.w, r[k].w);
         dot4(part, r[k], r[k]);
         const float dd = om * d0[k];
         put(cl, sm, L0, zo, rank, o0, ly, x, make_float4(dd * r[k].x, dd * r[k].y, dd * r[k].z, dd * r[k].w));
@@ -731,15 +785,18 @@ __global__ void __launch_bounds__(CNT, 1)
   }
 #undef FINE_ITEM
 
-  // ---- scatter the solution
+  // ---- the solution into the output block
+  const float4* xg = XG;
+#undef XG
 #pragma unroll
   for (int k = 0; k < FINE_ITEMS; ++k) {
     const int i = threadIdx.x + k * CNT;
     if (i < n0) {
+      const float4 v = xg[i];
       const size_t node = (size_t)o0.r0 * nx0 + i;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (col0 + u < w) dst[node * ldd + col0 + u] = (TD)comp(xs[k], u);
+        if (col0 + u < w) dst[node * ldd + col0 + u] = (TD)comp(v, u);
     }
   }
   if (rank == 0 && threadIdx.x < 4 && a.iters && col0 + (int)threadIdx.x < w)
@@ -803,7 +860,6 @@ int cluster_setup(sg_problem* h) {
       if (gs == G) gs = g;
     } else {
       if (gs < G) return SG_OK;                 // strips below a grid held by CTA 0
-      if (2 * l.nx > CNT) return SG_OK;         // ghost copy: one thread per ghost node
     }
     const size_t vec = (size_t)(l.rows + 2) * (l.nx + 2) * 16;
     l.b = g > 0 ? take(vec) : 0;
@@ -831,6 +887,7 @@ int cluster_setup(sg_problem* h) {
   cudaGetLastError();
   if (maxcl < 1) return SG_OK;
   P.maxcl = maxcl;
+  SG_TRY_CUDA(cudaMalloc(&h->cl_xs, (size_t)maxcl * P.L[0].nx * P.L[0].ny * sizeof(float4)));
   h->cl_plan = new CPlan(P);
   return SG_OK;
 }
@@ -838,6 +895,8 @@ int cluster_setup(sg_problem* h) {
 void cluster_free(sg_problem* h) {
   delete (CPlan*)h->cl_plan;
   h->cl_plan = nullptr;
+  cudaFree(h->cl_xs);
+  h->cl_xs = nullptr;
 }
 
 // A batch takes the cluster solver when all its clusters are resident at once:
@@ -865,6 +924,7 @@ int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void
   a.status = h->status;
   a.iacc = h->iacc;
   a.iters = h->iw32.iters && h->iw32.wcap >= w ? h->iw32.iters : nullptr;
+  a.xs = (float4*)h->cl_xs;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ceil_div(w, 4) * CLN));
   cfg.blockDim = dim3(CNT);

@@ -132,6 +132,7 @@ struct sg_problem {
   std::vector<sghsc::GridLevel> grids;
   int cb_level = 0;                         // first grid handled by the in-block coarse V-cycle
   void* cl_plan = nullptr;                  // shared-memory plan of the cluster inner solver (null: not usable)
+  void* cl_xs = nullptr;                    // its solution scratch: n float4 per resident cluster
   // workspace
   sghsc::InnerWork iw32, iw64;
   float* R32 = nullptr;                     // n x P working residual (mixed HSC)
