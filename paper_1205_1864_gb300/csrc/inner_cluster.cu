@@ -23,10 +23,10 @@
 //   after the cluster barrier every CTA adds the 8 slots in rank order, so all
 //   CTAs hold identical CG scalars and take the same loop decisions.
 // - On the finest grid each thread owns FINE_ITEMS nodes and keeps their r
-//   and p in registers; the solution accumulates in the output block (x += alpha
-//   p once per iteration, in the output's precision); the shared-memory vectors
-//   there are the V-cycle iterate and one more (smoother ping-pong, residual,
-//   p_new, q).
+//   and p in registers; the solution (x += alpha
+//   p once per iteration) and q = A p of the last step go to a per-cluster
+//   scratch in global memory (one coalesced float4 per node); the shared-memory
+//   vectors there are the V-cycle iterate and its ping-pong partner.
 //
 // Eligibility (cluster_setup): a square hierarchy (power-of-two elements)
 // whose shared-memory plan fits one CTA, at least one cluster resident, FP32.
@@ -77,6 +77,7 @@ struct CArgs {
   long long* iacc;
   int* iters;   // per-column iteration counts out (global column index), or null
   float4* xs;   // solution scratch [cluster][n]: one float4 (4 columns) per node
+  float4* qs;   // A p of the last step, same layout
 };
 
 namespace {
@@ -151,6 +152,12 @@ __device__ __forceinline__ float4 apply9(const float* __restrict__ s9, const flo
 __device__ __forceinline__ void copy_async4(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// 16-byte copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void copy_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ void copy_async_wait() {
@@ -600,7 +607,12 @@ __global__ void __launch_bounds__(CNT, 1)
     if (o.nr == 0) continue;
     float* st = sp<float>(sm, l.st);
     const float* gst = l.gst + (size_t)o.r0 * l.nx * 9;
-    for (int i = threadIdx.x; i < o.nr * l.nx * 9; i += CNT) copy_async4(st + i, gst + i);
+    const int cnt = o.nr * l.nx * 9;
+    if ((((size_t)gst | (size_t)st) & 15) == 0 && (cnt & 3) == 0) {
+      for (int i = threadIdx.x; i < cnt / 4; i += CNT) copy_async16(st + 4 * i, gst + 4 * i);
+    } else {
+      for (int i = threadIdx.x; i < cnt; i += CNT) copy_async4(st + i, gst + i);
+    }
     if (g > 0) {
       float* di = sp<float>(sm, l.di);
       const int lo = max(o.r0 - 1, 0) - o.r0, hi = min(o.r0 + o.nr + 1, l.ny) - o.r0;
@@ -621,6 +633,7 @@ __global__ void __launch_bounds__(CNT, 1)
   float4 r[FINE_ITEMS], po[FINE_ITEMS];   // the solution accumulates in a.xs
   // this CTA's nodes of the cluster's solution scratch (recomputed where used)
 #define XG (a.xs + (size_t)(blockIdx.x / CLN) * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
+#define QG (a.qs + (size_t)(blockIdx.x / CLN) * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
   float d0[FINE_ITEMS];
   int lyx[FINE_ITEMS];   // own row << 16 | column of each item
   unsigned zo = L0.x, so = L0.y;
@@ -711,30 +724,31 @@ __global__ void __launch_bounds__(CNT, 1)
       else cluster_sync_all();
       const unsigned t = zo; zo = so; so = t;
     }
-    // ---- p = z + beta p (registers and the other buffer), q = A p, p . q
+    // ---- p = z + beta p (registers), q = A p = A z + beta q_old (linearity:
+    // the z of this step is complete with its ghost rows, so no p_new buffer
+    // and no extra phase), p . q; q kept in registers and in the scratch
+    float4 qv[FINE_ITEMS];
     {
       const float4 bt = make_float4(S.beta[0], S.beta[1], S.beta[2], S.beta[3]);
       const float4* Z = sp<float4>(sm, zo);
+      float4* qg = QG;
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        const int i = threadIdx.x + k * CNT;
+        qv[k] = (it > 0 && i < n0) ? qg[i] : f4(0.f);
+      }
+      part = f4(0.f);
 #pragma unroll
       for (int k = 0; k < FINE_ITEMS; ++k) {
         FINE_ITEM(k)
+        const float4 az = apply9(ST0 + i * 9, Z, W0, c);
         const float4 z = Z[c];
         po[k] = make_float4(fmaf(bt.x, po[k].x, z.x), fmaf(bt.y, po[k].y, z.y), fmaf(bt.z, po[k].z, z.z),
                             fmaf(bt.w, po[k].w, z.w));
-        put(cl, sm, L0, so, rank, o0, ly, x, po[k]);
-      }
-    }
-    cluster_sync_all();
-    part = f4(0.f);
-    {
-      const float4* Pn = sp<float4>(sm, so);
-      float4* Z = sp<float4>(sm, zo);
-#pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        FINE_ITEM(k)
-        const float4 q = apply9(ST0 + i * 9, Pn, W0, c);
-        dot4(part, po[k], q);
-        Z[c] = q;
+        qv[k] = make_float4(fmaf(bt.x, qv[k].x, az.x), fmaf(bt.y, qv[k].y, az.y), fmaf(bt.z, qv[k].z, az.z),
+                            fmaf(bt.w, qv[k].w, az.w));
+        dot4(part, po[k], qv[k]);
+        qg[i] = qv[k];
         item_fence();
       }
     }
@@ -744,7 +758,6 @@ __global__ void __launch_bounds__(CNT, 1)
     {
       const float al0 = S.alpha[0], al1 = S.alpha[1], al2 = S.alpha[2], al3 = S.alpha[3];
       const bool dn0 = S.cs[0].done, dn1 = S.cs[1].done, dn2 = S.cs[2].done, dn3 = S.cs[3].done;
-      const float4* Z = sp<float4>(sm, zo);
       const bool up[4] = {!dn0 && col0 < w, !dn1 && col0 + 1 < w, !dn2 && col0 + 2 < w, !dn3 && col0 + 3 < w};
       const float al[4] = {al0, al1, al2, al3};
       // x += alpha p in the scratch (coalesced float4 per node; the loads
@@ -771,7 +784,7 @@ __global__ void __launch_bounds__(CNT, 1)
 #pragma unroll
       for (int k = 0; k < FINE_ITEMS; ++k) {
         FINE_ITEM(k)
-        const float4 q = Z[c];
+        const float4 q = qv[k];
         if (!dn0) r[k].x = fmaf(-al0, q.x, r[k].x);
         if (!dn1) r[k].y = fmaf(-al1, q.y, r[k].y);
         if (!dn2) r[k].z = fmaf(-al2, q.z, r[k].z);
@@ -788,6 +801,7 @@ __global__ void __launch_bounds__(CNT, 1)
   // ---- the solution into the output block
   const float4* xg = XG;
 #undef XG
+#undef QG
 #pragma unroll
   for (int k = 0; k < FINE_ITEMS; ++k) {
     const int i = threadIdx.x + k * CNT;
@@ -887,7 +901,7 @@ int cluster_setup(sg_problem* h) {
   cudaGetLastError();
   if (maxcl < 1) return SG_OK;
   P.maxcl = maxcl;
-  SG_TRY_CUDA(cudaMalloc(&h->cl_xs, (size_t)maxcl * P.L[0].nx * P.L[0].ny * sizeof(float4)));
+  SG_TRY_CUDA(cudaMalloc(&h->cl_xs, 2 * (size_t)maxcl * P.L[0].nx * P.L[0].ny * sizeof(float4)));
   h->cl_plan = new CPlan(P);
   return SG_OK;
 }
@@ -925,6 +939,7 @@ int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void
   a.iacc = h->iacc;
   a.iters = h->iw32.iters && h->iw32.wcap >= w ? h->iw32.iters : nullptr;
   a.xs = (float4*)h->cl_xs;
+  a.qs = a.xs + (size_t)P.maxcl * P.L[0].nx * P.L[0].ny;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ceil_div(w, 4) * CLN));
   cfg.blockDim = dim3(CNT);
