@@ -22,8 +22,9 @@
 //   kind of sum, so a slot is never rewritten while another CTA may read it);
 //   after the cluster barrier every CTA adds the 8 slots in rank order, so all
 //   CTAs hold identical CG scalars and take the same loop decisions.
-// - On the finest grid each thread owns FINE_ITEMS nodes and keeps their r
-//   and p in registers; the solution (x += alpha
+// - On the finest grid each thread owns up to FINE_ITEMS nodes, one below the
+//   other (a stencil sweep rolls its 3 x 3 window down: 3 new loads per node),
+//   and keeps their r and p in registers; the solution (x += alpha
 //   p once per iteration) and q = A p of the last step go to a per-cluster
 //   scratch in global memory (one coalesced float4 per node); the shared-memory
 //   vectors there are the V-cycle iterate and its ping-pong partner.
@@ -65,6 +66,7 @@ struct CPlan {
   int G, gs;        // number of grids; first grid held by CTA 0 alone
   unsigned bytes;   // dynamic shared memory per CTA
   int maxcl;        // clusters resident at once (host side: one-wave rule)
+  int fine_h;       // finest-grid rows per thread (a column segment of fine_h nodes)
   CLevel L[CMAXG];
 };
 
@@ -158,6 +160,21 @@ __device__ __forceinline__ void copy_async4(float* dst, const float* src) {
 __device__ __forceinline__ void copy_async16(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// cnt floats global -> shared: 16-byte copies where the two addresses share
+// their alignment (a 4-byte head up to the boundary and a 4-byte tail), 4-byte
+// copies otherwise; the block's threads share the work.
+__device__ __forceinline__ void stage_floats(float* dst, const float* src, int cnt) {
+  if ((((size_t)dst ^ (size_t)src) & 15) == 0) {
+    const int head = min(cnt, (int)(((16 - ((size_t)dst & 15)) & 15) / 4));
+    const int body = (cnt - head) / 4;
+    for (int i = threadIdx.x; i < head; i += blockDim.x) copy_async4(dst + i, src + i);
+    for (int i = threadIdx.x; i < body; i += blockDim.x) copy_async16(dst + head + 4 * i, src + head + 4 * i);
+    for (int i = head + 4 * body + threadIdx.x; i < cnt; i += blockDim.x) copy_async4(dst + i, src + i);
+  } else {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) copy_async4(dst + i, src + i);
+  }
 }
 
 __device__ __forceinline__ void copy_async_wait() {
@@ -417,9 +434,9 @@ __device__ __forceinline__ unsigned final_buf(const CLevel& l, bool coarsest, in
   return ((max(0, nu - 2) + nu) & 1) ? l.y : l.x;
 }
 
-template <bool BLK>
-__device__ __forceinline__ void level_sync() {
-  if (BLK) __syncthreads();
+// blk: a grid held by CTA 0 alone (block barrier), else the cluster barrier
+__device__ __forceinline__ void level_sync(bool blk) {
+  if (blk) __syncthreads();
   else cluster_sync_all();
 }
 
@@ -435,12 +452,14 @@ __device__ __forceinline__ void for_own(const CLevel& l, const Own& o, F f) {
 
 // Restriction side of the V-cycle on a coarse grid g (right-hand side in its
 // b buffer, zero initial iterate): nu sweeps, the residual, and its
-// restriction into grid g + 1. BLK: a grid held by CTA 0 alone, run by CTA 0
-// with block barriers.
-template <bool BLK>
-__device__ void level_down(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int g, int rank, int nu,
-                           float om) {
+// restriction into grid g + 1. A grid held by CTA 0 alone is run by CTA 0
+// with block barriers (one copy of the code serves both kinds of grid: the
+// kernel's phases each run once per iteration, and its size decides how much
+// of it the instruction cache keeps).
+__device__ __noinline__ void level_down(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int g,
+                                        int rank, int nu, float om) {
   const CLevel& l = L[g];
+  const bool blk = l.single;
   const Own o = own_rows(l, rank);
   const int W = l.nx + 2;
   const float* ST = sp<float>(sm, l.st);
@@ -467,14 +486,14 @@ __device__ void level_down(const cg::cluster_group& cl, unsigned char* sm, const
           make_float4(dd * b.x + dd * (b.x - om * ax1.x), dd * b.y + dd * (b.y - om * ax1.y),
                       dd * b.z + dd * (b.z - om * ax1.z), dd * b.w + dd * (b.w - om * ax1.w)));
     });
-    level_sync<BLK>();
+    level_sync(blk);
     for (int s = 2; s < nu; ++s) {
       const float4* Xi = sp<float4>(sm, xo);
       for_own(l, o, [&](int i, int ly, int x) {
         const int c = pidx(l, ly, x);
         put(cl, sm, l, yo, rank, o, ly, x, jacobi_node(ST + i * 9, Xi, W, c, B[c], DI[c], om));
       });
-      level_sync<BLK>();
+      level_sync(blk);
       const unsigned t = xo; xo = yo; yo = t;
     }
   } else {
@@ -484,7 +503,7 @@ __device__ void level_down(const cg::cluster_group& cl, unsigned char* sm, const
       const float4 b = B[c];
       put(cl, sm, l, xo, rank, o, ly, x, make_float4(dd * b.x, dd * b.y, dd * b.z, dd * b.w));
     });
-    level_sync<BLK>();
+    level_sync(blk);
   }
   // residual b - A x into the other buffer, then its restriction
   {
@@ -494,17 +513,17 @@ __device__ void level_down(const cg::cluster_group& cl, unsigned char* sm, const
       put(cl, sm, l, yo, rank, o, ly, x, sub4(B[c], apply9(ST + i * 9, X, W, c)));
     });
   }
-  level_sync<BLK>();
+  level_sync(blk);
   restrict_rows(cl, sm, l, o, yo, L[g + 1], rank);
-  level_sync<BLK>();
+  level_sync(blk);
 }
 
 // Prolongation side on a coarse grid g: the correction from grid g + 1 with
 // the first post-smoothing sweep in one pass, then nu - 1 more sweeps.
-template <bool BLK>
-__device__ void level_up(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int g, int G, int rank,
-                         int nu, float om) {
+__device__ __noinline__ void level_up(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int g, int G,
+                                      int rank, int nu, float om) {
   const CLevel& l = L[g];
+  const bool blk = l.single;
   const CLevel& lc = L[g + 1];
   const Own o = own_rows(l, rank);
   const int W = l.nx + 2, Wc = lc.nx + 2;
@@ -523,7 +542,7 @@ __device__ void level_up(const cg::cluster_group& cl, unsigned char* sm, const C
                               x & 1));
     });
   }
-  level_sync<BLK>();
+  level_sync(blk);
   {
     const unsigned t = xo; xo = yo; yo = t;
   }
@@ -533,7 +552,7 @@ __device__ void level_up(const cg::cluster_group& cl, unsigned char* sm, const C
       const int c = pidx(l, ly, x);
       put(cl, sm, l, yo, rank, o, ly, x, jacobi_node(ST + i * 9, Xi, W, c, B[c], DI[c], om));
     });
-    level_sync<BLK>();
+    level_sync(blk);
     const unsigned t = xo; xo = yo; yo = t;
   }
 }
@@ -544,7 +563,7 @@ __device__ void level_up(const cg::cluster_group& cl, unsigned char* sm, const C
 // grid gs - 1 reads it everywhere); the caller's cluster barrier publishes it.
 __device__ void block_levels(const cg::cluster_group& cl, unsigned char* sm, const CLevel* L, int gs, int G, int nu,
                              float om) {
-  for (int g = gs; g < G - 1; ++g) level_down<true>(cl, sm, L, g, 0, nu, om);
+  for (int g = gs; g < G - 1; ++g) level_down(cl, sm, L, g, 0, nu, om);
   {
     const CLevel& l = L[G - 1];
     const Own o = own_rows(l, 0);
@@ -559,13 +578,51 @@ __device__ void block_levels(const cg::cluster_group& cl, unsigned char* sm, con
     });
     __syncthreads();
   }
-  for (int g = G - 2; g >= gs; --g) level_up<true>(cl, sm, L, g, G, 0, nu, om);
+  for (int g = G - 2; g >= gs; --g) level_up(cl, sm, L, g, G, 0, nu, om);
   const CLevel& l = L[gs];
   float4* v = sp<float4>(sm, final_buf(l, gs == G - 1, nu));
   const int W = l.nx + 2, m = l.ny * W;
   for (int i = threadIdx.x; i < (CLN - 1) * m; i += blockDim.x) {
     const int r = 1 + i / m, j = W + i % m;
     cl.map_shared_rank(v, r)[j] = v[j];
+  }
+}
+
+// The finest-grid stencil sweep of one thread over its fn nodes (fy0 + k, fx),
+// k = 0 .. fn-1, one below the other: the 3 x 3 window of X around the node
+// rolls down one row per node, so a node costs 3 new loads instead of 9.
+// f(k, c, ax, xc) receives the padded index, (A X) and X at node k.
+template <typename F>
+__device__ __forceinline__ void fine_sweep(const float* __restrict__ ST, const float4* X, int W, int nx, int fy0,
+                                           int fx, int fn, F f) {
+  if (fn <= 0) return;
+  const int c0 = (fy0 + 1) * W + fx + 1;
+  float4 w0[3], w1[3], w2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    w0[d] = X[c0 - W + d - 1];
+    w1[d] = X[c0 + d - 1];
+  }
+#pragma unroll
+  for (int k = 0; k < FINE_ITEMS; ++k) {
+    if (k >= fn) break;
+    const int c = c0 + k * W;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) w2[d] = X[c + W + d - 1];
+    const float* s9 = ST + ((fy0 + k) * nx + fx) * 9;
+    float4 ax = f4(0.f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fma4(ax, s9[d], w0[d]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fma4(ax, s9[3 + d], w1[d]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fma4(ax, s9[6 + d], w2[d]);
+    f(k, c, ax, w1[1]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      w0[d] = w1[d];
+      w1[d] = w2[d];
+    }
   }
 }
 
@@ -584,70 +641,71 @@ __global__ void __launch_bounds__(CNT, 1)
   const int G = P.G, gs = P.gs, nu = a.nu;
   const float om = a.om;
 
-  // ---- set-up: grid table, zeroed buffers (ghosts outside the grids stay
-  // zero), own-row stencils, inverse diagonals with their ghost rows
+  // ---- set-up: grid table; own-row stencils (asynchronous copies, in
+  // flight during the rest of the set-up); zeroed vectors and diagonals
+  // (ghosts outside the grids stay zero); diagonals with their ghost rows
 #pragma unroll
   for (int g = 0; g < CMAXG; ++g)
     if ((int)threadIdx.x == g) L[g] = P.L[g];
-  {
-    float4* z = reinterpret_cast<float4*>(sm);
-    for (int i = threadIdx.x; i < (int)(P.bytes / 16); i += CNT) z[i] = f4(0.f);
-  }
   if (threadIdx.x < 4) {
     S.cs[threadIdx.x] = ColState{0.0, 0.0, 0, 1};
     S.alpha[threadIdx.x] = 0.f;
     S.beta[threadIdx.x] = 0.f;
   }
   __syncthreads();
-  // (asynchronous copies, all in flight together; completed before the first
-  // reduction's barrier)
   for (int g = 0; g < G; ++g) {
     const CLevel& l = L[g];
     const Own o = own_rows(l, rank);
     if (o.nr == 0) continue;
-    float* st = sp<float>(sm, l.st);
-    const float* gst = l.gst + (size_t)o.r0 * l.nx * 9;
-    const int cnt = o.nr * l.nx * 9;
-    if ((((size_t)gst | (size_t)st) & 15) == 0 && (cnt & 3) == 0) {
-      for (int i = threadIdx.x; i < cnt / 4; i += CNT) copy_async16(st + 4 * i, gst + 4 * i);
-    } else {
-      for (int i = threadIdx.x; i < cnt; i += CNT) copy_async4(st + i, gst + i);
-    }
-    if (g > 0) {
-      float* di = sp<float>(sm, l.di);
-      const int lo = max(o.r0 - 1, 0) - o.r0, hi = min(o.r0 + o.nr + 1, l.ny) - o.r0;
-      for (int i = threadIdx.x; i < (hi - lo) * l.nx; i += CNT) {
-        const int ly = lo + i / l.nx, x = i % l.nx;
-        copy_async4(di + pidx(l, ly, x), l.gdi + (size_t)(o.r0 + ly) * l.nx + x);
-      }
+    stage_floats(sp<float>(sm, l.st), l.gst + (size_t)o.r0 * l.nx * 9, o.nr * l.nx * 9);
+  }
+  for (int g = 0; g < G; ++g) {
+    const CLevel& l = L[g];
+    const unsigned lo = g > 0 ? l.b : l.x;
+    const unsigned end = g + 1 < G ? L[g + 1].b : P.bytes;
+    float4* z = reinterpret_cast<float4*>(sm);
+    for (int i = (int)(lo / 16) + threadIdx.x; i < (int)(l.st / 16); i += CNT) z[i] = f4(0.f);
+    if (g > 0)
+      for (int i = (int)(l.di / 16) + threadIdx.x; i < (int)(end / 16); i += CNT) z[i] = f4(0.f);
+  }
+  __syncthreads();
+  for (int g = 1; g < G; ++g) {
+    const CLevel& l = L[g];
+    const Own o = own_rows(l, rank);
+    if (o.nr == 0) continue;
+    float* di = sp<float>(sm, l.di);
+    const int lo = max(o.r0 - 1, 0) - o.r0, hi = min(o.r0 + o.nr + 1, l.ny) - o.r0;
+    for (int i = threadIdx.x; i < (hi - lo) * l.nx; i += CNT) {
+      const int ly = lo + i / l.nx, x = i % l.nx;
+      copy_async4(di + pidx(l, ly, x), l.gdi + (size_t)(o.r0 + ly) * l.nx + x);
     }
   }
-  copy_async_wait();
 
-  // ---- finest grid: r = b, x = 0, p = 0 in registers; ||b||^2; the first
-  // smoothing sweep from zero (om D^-1 r) into the iterate buffer
+  // ---- finest grid. Thread t owns column fx = t mod nx0 of the rows fy0 ..
+  // fy0 + fn - 1 (fy0 = fine_h (t div nx0)): vertically adjacent nodes, so a
+  // stencil sweep rolls its window down (fine_sweep). r = b, x = 0, p = 0;
+  // ||b||^2; the first smoothing sweep from zero (om D^-1 r) into the iterate.
   const CLevel& L0 = L[0];
   const Own o0 = own_rows(L0, rank);
-  const int nx0 = L0.nx, W0 = nx0 + 2, n0 = o0.nr * nx0;
+  const int nx0 = L0.nx, W0 = nx0 + 2;
+  const int fx = threadIdx.x % nx0, fy0 = P.fine_h * ((int)threadIdx.x / nx0);
+  const int fn = (int)threadIdx.x < (CNT / nx0) * nx0 ? max(0, min(P.fine_h, o0.nr - fy0)) : 0;
   const float* ST0 = sp<float>(sm, L0.st);
   float4 r[FINE_ITEMS], po[FINE_ITEMS];   // the solution accumulates in a.xs
-  // this CTA's nodes of the cluster's solution scratch (recomputed where used)
+  float d0[FINE_ITEMS];
+  // this CTA's nodes of the cluster's solution and A p scratch (recomputed where used)
 #define XG (a.xs + (size_t)(blockIdx.x / CLN) * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
 #define QG (a.qs + (size_t)(blockIdx.x / CLN) * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
-  float d0[FINE_ITEMS];
-  int lyx[FINE_ITEMS];   // own row << 16 | column of each item
+#define FI(k) ((fy0 + (k)) * nx0 + fx)
   unsigned zo = L0.x, so = L0.y;
   float4 part = f4(0.f);
 #pragma unroll
   for (int k = 0; k < FINE_ITEMS; ++k) {
-    const int i = threadIdx.x + k * CNT;
     r[k] = f4(0.f);
     po[k] = f4(0.f);
     d0[k] = 0.f;
-    lyx[k] = 0;
-    if (i < n0) {
-      const int ly = i / nx0, x = i - ly * nx0;
-      lyx[k] = (ly << 16) | x;
+    if (k < fn) {
+      const int i = FI(k);
       const size_t node = (size_t)o0.r0 * nx0 + i;
       float v[4];
 #pragma unroll
@@ -657,69 +715,59 @@ __global__ void __launch_bounds__(CNT, 1)
       d0[k] = L0.gdi[node];
       dot4(part, r[k], r[k]);
       const float dd = om * d0[k];
-      put(cl, sm, L0, zo, rank, o0, ly, x, make_float4(dd * v[0], dd * v[1], dd * v[2], dd * v[3]));
+      put(cl, sm, L0, zo, rank, o0, fy0 + k, fx, make_float4(dd * v[0], dd * v[1], dd * v[2], dd * v[3]));
     }
   }
+  copy_async_wait();
   cluster_reduce(cl, S, RK_INIT, part, a, rank);
-#define FINE_ITEM(k)                                   \
-  const int i = threadIdx.x + (k) * CNT;               \
-  if (i >= n0) continue;                               \
-  const int ly = lyx[k] >> 16, x = lyx[k] & 0xffff;    \
-  const int c = (ly + 1) * W0 + x + 1;
 
   const int cap = (a.fixed > 0 ? a.fixed : a.maxit) + 1;
   for (int it = 0; it < cap && S.active; ++it) {
     // ---- V-cycle, finest grid down: sweeps 2..nu, residual, restriction
     for (int s = 1; s < nu; ++s) {
-      const float4* Z = sp<float4>(sm, zo);
-#pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        FINE_ITEM(k)
-        put(cl, sm, L0, so, rank, o0, ly, x, jacobi_node(ST0 + i * 9, Z, W0, c, r[k], d0[k], om));
-        item_fence();
-      }
+      fine_sweep(ST0, sp<float4>(sm, zo), W0, nx0, fy0, fx, fn, [&](int k, int, const float4& ax, const float4& xc) {
+        const float dd = om * d0[k];
+        put(cl, sm, L0, so, rank, o0, fy0 + k, fx,
+            make_float4(fmaf(dd, r[k].x - ax.x, xc.x), fmaf(dd, r[k].y - ax.y, xc.y), fmaf(dd, r[k].z - ax.z, xc.z),
+                        fmaf(dd, r[k].w - ax.w, xc.w)));
+      });
       cluster_sync_all();
       const unsigned t = zo; zo = so; so = t;
     }
-    {
-      const float4* Z = sp<float4>(sm, zo);
-#pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        FINE_ITEM(k)
-        put(cl, sm, L0, so, rank, o0, ly, x, sub4(r[k], apply9(ST0 + i * 9, Z, W0, c)));
-        item_fence();
-      }
-    }
+    fine_sweep(ST0, sp<float4>(sm, zo), W0, nx0, fy0, fx, fn, [&](int k, int, const float4& ax, const float4&) {
+      put(cl, sm, L0, so, rank, o0, fy0 + k, fx, sub4(r[k], ax));
+    });
     cluster_sync_all();
     restrict_rows(cl, sm, L0, o0, so, L[1], rank);
     cluster_sync_all();
     // ---- coarse grids
-    for (int g = 1; g < gs; ++g) level_down<false>(cl, sm, L, g, rank, nu, om);
+    for (int g = 1; g < gs; ++g) level_down(cl, sm, L, g, rank, nu, om);
     if (rank == 0) block_levels(cl, sm, L, gs, G, nu, om);
     cluster_sync_all();
-    for (int g = gs - 1; g >= 1; --g) level_up<false>(cl, sm, L, g, G, rank, nu, om);
+    for (int g = gs - 1; g >= 1; --g) level_up(cl, sm, L, g, G, rank, nu, om);
     // ---- finest grid up: correction + sweep, nu - 1 more sweeps; the last
     // one also sums r . z
     const float4* XC = sp<float4>(sm, final_buf(L[1], G == 2, nu));
     const int Wc = L[1].nx + 2;
     for (int s = 1; s <= nu; ++s) {
-      const float4* Z = sp<float4>(sm, zo);
       part = f4(0.f);
-#pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        FINE_ITEM(k)
+      fine_sweep(ST0, sp<float4>(sm, zo), W0, nx0, fy0, fx, fn, [&](int k, int, const float4& ax, const float4& xc) {
+        const float dd = om * d0[k];
         float4 v;
         if (s == 1) {
-          const int y = o0.r0 + ly;
-          v = prolong_jacobi_node(ST0 + i * 9, Z, W0, c, r[k], d0[k], om, XC, Wc, patch_centre(L[1], rank, y, x),
-                                  y & 1, x & 1);
+          const int y = o0.r0 + fy0 + k;
+          float4 apc, pc;
+          coarse_corr(ST0 + FI(k) * 9, XC, Wc, patch_centre(L[1], rank, y, fx), y & 1, fx & 1, apc, pc);
+          const float4 xv = add4(xc, pc);
+          v = make_float4(fmaf(dd, r[k].x - (ax.x + apc.x), xv.x), fmaf(dd, r[k].y - (ax.y + apc.y), xv.y),
+                          fmaf(dd, r[k].z - (ax.z + apc.z), xv.z), fmaf(dd, r[k].w - (ax.w + apc.w), xv.w));
         } else {
-          v = jacobi_node(ST0 + i * 9, Z, W0, c, r[k], d0[k], om);
+          v = make_float4(fmaf(dd, r[k].x - ax.x, xc.x), fmaf(dd, r[k].y - ax.y, xc.y), fmaf(dd, r[k].z - ax.z, xc.z),
+                          fmaf(dd, r[k].w - ax.w, xc.w));
         }
-        put(cl, sm, L0, so, rank, o0, ly, x, v);
+        put(cl, sm, L0, so, rank, o0, fy0 + k, fx, v);
         dot4(part, r[k], v);
-        item_fence();
-      }
+      });
       if (s == nu) cluster_reduce(cl, S, RK_RHO, part, a, rank);
       else cluster_sync_all();
       const unsigned t = zo; zo = so; so = t;
@@ -730,27 +778,18 @@ __global__ void __launch_bounds__(CNT, 1)
     float4 qv[FINE_ITEMS];
     {
       const float4 bt = make_float4(S.beta[0], S.beta[1], S.beta[2], S.beta[3]);
-      const float4* Z = sp<float4>(sm, zo);
       float4* qg = QG;
 #pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        const int i = threadIdx.x + k * CNT;
-        qv[k] = (it > 0 && i < n0) ? qg[i] : f4(0.f);
-      }
+      for (int k = 0; k < FINE_ITEMS; ++k) qv[k] = (it > 0 && k < fn) ? qg[FI(k)] : f4(0.f);
       part = f4(0.f);
-#pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        FINE_ITEM(k)
-        const float4 az = apply9(ST0 + i * 9, Z, W0, c);
-        const float4 z = Z[c];
+      fine_sweep(ST0, sp<float4>(sm, zo), W0, nx0, fy0, fx, fn, [&](int k, int, const float4& az, const float4& z) {
         po[k] = make_float4(fmaf(bt.x, po[k].x, z.x), fmaf(bt.y, po[k].y, z.y), fmaf(bt.z, po[k].z, z.z),
                             fmaf(bt.w, po[k].w, z.w));
         qv[k] = make_float4(fmaf(bt.x, qv[k].x, az.x), fmaf(bt.y, qv[k].y, az.y), fmaf(bt.z, qv[k].z, az.z),
                             fmaf(bt.w, qv[k].w, az.w));
         dot4(part, po[k], qv[k]);
-        qg[i] = qv[k];
-        item_fence();
-      }
+        qg[FI(k)] = qv[k];
+      });
     }
     cluster_reduce(cl, S, RK_PQ, part, a, rank);
     // ---- x += alpha p, r -= alpha q on the unfinished columns; r . r; the
@@ -758,32 +797,25 @@ __global__ void __launch_bounds__(CNT, 1)
     {
       const float al0 = S.alpha[0], al1 = S.alpha[1], al2 = S.alpha[2], al3 = S.alpha[3];
       const bool dn0 = S.cs[0].done, dn1 = S.cs[1].done, dn2 = S.cs[2].done, dn3 = S.cs[3].done;
-      const bool up[4] = {!dn0 && col0 < w, !dn1 && col0 + 1 < w, !dn2 && col0 + 2 < w, !dn3 && col0 + 3 < w};
-      const float al[4] = {al0, al1, al2, al3};
+      const bool up0 = !dn0 && col0 < w, up1 = !dn1 && col0 + 1 < w, up2 = !dn2 && col0 + 2 < w,
+                 up3 = !dn3 && col0 + 3 < w;
       // x += alpha p in the scratch (coalesced float4 per node; the loads
       // first, so they are in flight together)
       float4 xv[FINE_ITEMS];
       float4* xg = XG;
 #pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        const int i = threadIdx.x + k * CNT;
-        if (i < n0) xv[k] = xg[i];
-      }
-#pragma unroll
-      for (int k = 0; k < FINE_ITEMS; ++k) {
-        const int i = threadIdx.x + k * CNT;
-        if (i >= n0) continue;
-        float4 v = xv[k];
-        if (up[0]) v.x = fmaf(al[0], po[k].x, v.x);
-        if (up[1]) v.y = fmaf(al[1], po[k].y, v.y);
-        if (up[2]) v.z = fmaf(al[2], po[k].z, v.z);
-        if (up[3]) v.w = fmaf(al[3], po[k].w, v.w);
-        xg[i] = v;
-      }
+      for (int k = 0; k < FINE_ITEMS; ++k)
+        if (k < fn) xv[k] = xg[FI(k)];
       part = f4(0.f);
 #pragma unroll
       for (int k = 0; k < FINE_ITEMS; ++k) {
-        FINE_ITEM(k)
+        if (k >= fn) break;
+        float4 v = xv[k];
+        if (up0) v.x = fmaf(al0, po[k].x, v.x);
+        if (up1) v.y = fmaf(al1, po[k].y, v.y);
+        if (up2) v.z = fmaf(al2, po[k].z, v.z);
+        if (up3) v.w = fmaf(al3, po[k].w, v.w);
+        xg[FI(k)] = v;
         const float4 q = qv[k];
         if (!dn0) r[k].x = fmaf(-al0, q.x, r[k].x);
         if (!dn1) r[k].y = fmaf(-al1, q.y, r[k].y);
@@ -791,28 +823,27 @@ __global__ void __launch_bounds__(CNT, 1)
         if (!dn3) r[k].w = fmaf(-al3, q.w, r[k].w);
         dot4(part, r[k], r[k]);
         const float dd = om * d0[k];
-        put(cl, sm, L0, zo, rank, o0, ly, x, make_float4(dd * r[k].x, dd * r[k].y, dd * r[k].z, dd * r[k].w));
+        put(cl, sm, L0, zo, rank, o0, fy0 + k, fx, make_float4(dd * r[k].x, dd * r[k].y, dd * r[k].z, dd * r[k].w));
       }
     }
     cluster_reduce(cl, S, RK_RR, part, a, rank);
   }
-#undef FINE_ITEM
 
   // ---- the solution into the output block
   const float4* xg = XG;
-#undef XG
-#undef QG
 #pragma unroll
   for (int k = 0; k < FINE_ITEMS; ++k) {
-    const int i = threadIdx.x + k * CNT;
-    if (i < n0) {
-      const float4 v = xg[i];
-      const size_t node = (size_t)o0.r0 * nx0 + i;
+    if (k >= fn) break;
+    const int i = FI(k);
+    const float4 v = xg[i];
+    const size_t node = (size_t)o0.r0 * nx0 + i;
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (col0 + u < w) dst[node * ldd + col0 + u] = (TD)comp(v, u);
-    }
+    for (int u = 0; u < 4; ++u)
+      if (col0 + u < w) dst[node * ldd + col0 + u] = (TD)comp(v, u);
   }
+#undef XG
+#undef QG
+#undef FI
   if (rank == 0 && threadIdx.x < 4 && a.iters && col0 + (int)threadIdx.x < w)
     a.iters[col0 + threadIdx.x] = S.cs[threadIdx.x].iters;
   // no CTA leaves while another may still read its shared memory
@@ -885,7 +916,9 @@ int cluster_setup(sg_problem* h) {
     l.gdi = gr.dinv32;
   }
   if (gs == 0 || gs == G) return SG_OK;
-  if ((long long)P.L[0].rows * P.L[0].nx > (long long)FINE_ITEMS * CNT) return SG_OK;
+  if (P.L[0].nx > CNT) return SG_OK;
+  P.fine_h = (P.L[0].rows + CNT / P.L[0].nx - 1) / (CNT / P.L[0].nx);   // finest-grid rows per thread
+  if (P.fine_h > FINE_ITEMS) return SG_OK;
   for (int g = 0; g + 1 < gs; ++g)   // strips of consecutive grids line up (row 2Y+1 over row Y)
     if (P.L[g].rows != 2 * P.L[g + 1].rows || P.L[g + 1].nx != (P.L[g].nx - 1) / 2) return SG_OK;
   P.G = G;
