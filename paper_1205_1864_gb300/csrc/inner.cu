@@ -15,8 +15,10 @@
 // N = 16 bytes / element size); a thread owns a column group of N adjacent
 // columns, moved with 16-byte loads and stores. A block has k*ng threads
 // (ng = wp/N groups, k = max(1, 1024 / ng)), thread t always handles group
-// t mod ng and nodes (blockIdx*k + t / ng) + m * grid*k, so per-column partial
-// sums are register accumulations followed by a fixed-order block reduction; the last block to finish a reduction kernel
+// t mod ng and node t / ng of each block pass (pointwise kernels: passes in
+// grid-stride order; stencil kernels: down a column strip, StripIter), so
+// per-column partial sums are register accumulations followed by a fixed-order
+// block reduction; the last block to finish a reduction kernel
 // sums the block partials in block order and updates the CG scalars, so the
 // results do not depend on scheduling and no separate finalisation launch is
 // needed. The iteration loop is a CUDA graph WHILE node whose condition the
@@ -381,26 +383,46 @@ __device__ __forceinline__ T prolong_at(int fx, int fy, int nxc, int nyc, const 
   return acc;
 }
 
-// A thread's node sequence node0, node0 + nstep, ... with the grid coordinates
-// (x, y) kept incrementally (no division per node).
-struct NodeIter {
-  int node, x, y, nstep, dxs, dys, nx;
-  __device__ __forceinline__ NodeIter(int node0, int step, int nx_) : node(node0), nstep(step), nx(nx_) {
-    y = node0 / nx_;
-    x = node0 - y * nx_;
-    dys = step / nx_;
-    dxs = step - dys * nx_;
+// Node order of the 9-point stencil phases. The grid is cut into column strips
+// k nodes wide (the nodes of one block pass); the (strip, row) units are split
+// into one contiguous share per block, and a block walks its share row by row
+// down a strip, so the rows y - 1 and y that the stencils of row y + 1 read are
+// still in L1 from the two passes before (a grid-stride order along x would
+// fetch every row three times from L2, once per neighbouring row). lx: this
+// thread's node within the pass.
+struct StripIter {
+  int x, y, node, u, u1, cx, lx, k, nx, ny;
+  __device__ __forceinline__ StripIter(Blk B, int lx_, int k_, int nx_, int ny_)
+      : lx(lx_), k(k_), nx(nx_), ny(ny_) {
+    const long long tot = (long long)((nx + k - 1) / k) * ny;
+    u = (int)(tot * B.bid / B.nb);
+    u1 = (int)(tot * (B.bid + 1) / B.nb);
+    cx = u / ny;
+    y = u - cx * ny;
+    x = cx * k + lx;
+    node = y * nx + x;
   }
+  __device__ __forceinline__ bool valid() const { return u < u1; }
+  __device__ __forceinline__ bool inside() const { return x < nx; }
   __device__ __forceinline__ void next() {
-    node += nstep;
-    x += dxs;
-    y += dys;
-    if (x >= nx) {
-      x -= nx;
-      ++y;
+    ++u;
+    if (++y == ny) {
+      y = 0;
+      ++cx;
+      x = cx * k + lx;
     }
+    node = y * nx + x;
   }
 };
+
+// Thread t of a block in the stencil phases: column group t mod ng, node t / ng
+// of each pass; false for threads past k*ng.
+__device__ __forceinline__ bool strip_pos(int ng, int k, int& cg, int& lx) {
+  if ((int)threadIdx.x >= k * ng) return false;
+  cg = threadIdx.x % ng;
+  lx = threadIdx.x / ng;
+  return true;
+}
 
 // sum_j a_ij val(e_j, j) over the 9-point stencil of node (x, y) for the N
 // columns of a group; e_j = i + dy*rs + dx*wp is the element index of the
@@ -469,12 +491,13 @@ __device__ __forceinline__ void ph_smooth00(Blk B, int nx, int ny, int wp, int k
                                             const T* __restrict__ dinv, const T* __restrict__ b,
                                             T* __restrict__ x, T om, const int* __restrict__ done) {
   constexpr int N = VW<T>::N;
-  int cg, node0, nstep;
-  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
+  int cg, lx;
+  if (!strip_pos(wp / N, k, cg, lx)) return;
   const int c0 = cg * N;
   if (done_mask<N>(done, c0) == (1u << N) - 1) return;
-  const int n = nx * ny, rs = nx * wp;
-  for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+  const int rs = nx * wp;
+  for (StripIter it(B, lx, k, nx, ny); it.valid(); it.next()) {
+    if (!it.inside()) continue;
     const int i = it.node * wp + c0;
     const Vec<T> ax1 = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny, [&](int e, int j) {
       const T d = dinv[j];
@@ -501,12 +524,13 @@ __device__ __forceinline__ void ph_jacobi(Blk B, int nx, int ny, int wp, int k, 
   constexpr int N = VW<T>::N;
 #pragma unroll
   for (int u = 0; u < N; ++u) acc[u] = T(0);
-  int cg, node0, nstep;
-  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
+  int cg, lx;
+  if (!strip_pos(wp / N, k, cg, lx)) return;
   const int c0 = cg * N;
   if (done_mask<N>(done, c0) == (1u << N) - 1) return;
-  const int n = nx * ny, rs = nx * wp;
-  for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+  const int rs = nx * wp;
+  for (StripIter it(B, lx, k, nx, ny); it.valid(); it.next()) {
+    if (!it.inside()) continue;
     const int i = it.node * wp + c0;
     const Vec<T> ax = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
                                [&](int e, int) { return vld(xi + e); });
@@ -601,13 +625,14 @@ __device__ __forceinline__ void ph_prolong_jacobi(Blk B, int nxf, int nyf, int n
   constexpr int N = VW<T>::N;
 #pragma unroll
   for (int u = 0; u < N; ++u) acc[u] = T(0);
-  int cg, node0, nstep;
-  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
+  int cg, lx;
+  if (!strip_pos(wp / N, k, cg, lx)) return;
   const int c0 = cg * N;
   if (done_mask<N>(done, c0) == (1u << N) - 1) return;
-  const int n = nxf * nyf, rs = nxf * wp;
+  const int rs = nxf * wp;
   const T h = T(0.5);
-  for (NodeIter it(node0, nstep, nxf); it.node < n; it.next()) {
+  for (StripIter it(B, lx, k, nxf, nyf); it.valid(); it.next()) {
+    if (!it.inside()) continue;
     const T* s9 = st + it.node * 9;
     // separable interpolation weights by parity (rows: offset -1, 0, +1; columns: patch 0..2)
     T wxm[3][3], wym[3][3];
@@ -924,14 +949,14 @@ __device__ __forceinline__ void ph_matvec_p(Blk B, int nx, int ny, int wp, int k
   constexpr int N = VW<T>::N;
 #pragma unroll
   for (int u = 0; u < N; ++u) acc[u] = T(0);
-  int cg, node0, nstep;
-  if (!thread_pos(wp / N, k, B, cg, node0, nstep)) return;
+  int cg, lx;
+  if (!strip_pos(wp / N, k, cg, lx)) return;
   const int c0 = cg * N;
   if (done_mask<N>(done, c0) == (1u << N) - 1) return;
   T bt[N];
 #pragma unroll
   for (int u = 0; u < N; ++u) bt[u] = beta[c0 + u];
-  const int n = nx * ny, rs = nx * wp;
+  const int rs = nx * wp;
   auto pv = [&](int e) {
     Vec<T> v = vld(z + e);
     if (!first) {
@@ -941,7 +966,8 @@ __device__ __forceinline__ void ph_matvec_p(Blk B, int nx, int ny, int wp, int k
     }
     return v;
   };
-  for (NodeIter it(node0, nstep, nx); it.node < n; it.next()) {
+  for (StripIter it(B, lx, k, nx, ny); it.valid(); it.next()) {
+    if (!it.inside()) continue;
     const int i = it.node * wp + c0;
     const Vec<T> s = stencil9(st + it.node * 9, i, rs, wp, it.node, it.x, it.y, nx, ny,
                               [&](int e, int) { return pv(e); });
