@@ -312,6 +312,10 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
     const char* ev = getenv("SGHSC_EAGER");
     h->eager = ev && ev[0] == '1';
   }
+  {
+    const char* ev = getenv("SGHSC_NO_PIPE");
+    h->pipe_off = ev && ev[0] == '1';
+  }
   SG_TRY_CUDA(cudaMalloc((void**)&h->loopflags, 8 * sizeof(int)));
   SG_TRY_CUDA(cudaMemset(h->loopflags, 0, 8 * sizeof(int)));
   SG_TRY_CUDA(cudaMallocHost((void**)&h->loopflag_host, sizeof(int)));
