@@ -208,6 +208,14 @@ int sg_inner_solve(sg_problem* h, const void* B, void* X, int w, int dtype,
  * (summation order). h NULL: 0. */
 int sg_inner_cluster(const sg_problem* h);
 
+/* sg_inner_path -- which solver a batched inner solve of w columns of element
+ * type dtype takes on h: 0 the stand-alone kernels, 1 the cluster solver with
+ * the whole multigrid hierarchy in shared memory (ceil(w/4) clusters of 8
+ * blocks, all resident at once), 2 the cluster solver with the finest grid in
+ * global memory and the coarse grids in shared memory (two blocks per SM, for
+ * batches too wide for 1). h NULL or w <= 0: 0. */
+int sg_inner_path(const sg_problem* h, int w, int dtype);
+
 /* hsc_precond_apply -- Algorithm 1 (Sec. 4): Z = M_P R with the D_l^{-1}
  * and A_0^{-1} actions replaced by the batched inner PCG.
  * R, Z: device n x P row-major FP64; must not alias. */

@@ -119,6 +119,11 @@ class SGProblem:
         """True when the FP32 inner solves run on the cluster-resident solver."""
         return bool(_lib.LIB.sg_inner_cluster(self.h))
 
+    def inner_path(self, w: int, dtype: int = SG_F32) -> int:
+        """Solver of a batched inner solve of w columns: 0 stand-alone kernels,
+        1 cluster solver on chip, 2 cluster solver with the finest grid in HBM."""
+        return int(_lib.LIB.sg_inner_path(self.h, w, dtype))
+
     def close(self):
         if getattr(self, "h", None):
             _lib.LIB.sg_destroy(self.h)

@@ -65,6 +65,7 @@ def _load():
         "sg_vcycle_apply_static": (i, [vp, vp, vp, i, i, P(sg_prec_opts), vp]),
         "sg_inner_solve": (i, [vp, vp, vp, i, i, P(sg_prec_opts), P(C.c_int), vp]),
         "sg_inner_cluster": (i, [vp]),
+        "sg_inner_path": (i, [vp, i, i]),
         "hsc_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "mean_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "sg_solve": (i, [vp, vp, vp, P(sg_solve_opts), P(sg_solve_stats), vp]),
@@ -100,6 +101,6 @@ def check(status: int, where: str):
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
     return ["sg_setup", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
-            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result",
+            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result",
             "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",
             "sg_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

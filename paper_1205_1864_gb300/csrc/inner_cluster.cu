@@ -288,12 +288,13 @@ __device__ __forceinline__ int patch_centre(const CLevel& lc, int rank, int y, i
 // ghost rows of its neighbours, as put() does). Weights
 // 1 (centre), 1/2 (edge) and 1/4 (corner): the transpose of the bilinear
 // interpolation.
+// R: the residual as padded rows of this CTA (local row 0 = grid row o.r0),
+// in shared memory or, on the finest grid of the wide solver, in global memory.
 __device__ void restrict_rows(const cg::cluster_group& cl, unsigned char* sm, const CLevel& l, const Own& o,
-                              unsigned roff, const CLevel& lc, int rank) {
+                              const float4* R, const CLevel& lc, int rank) {
   const int top = o.r0 + o.nr - 2;
   if (o.nr == 0 || top < 0) return;
   const int ylo = o.r0 / 2, yhi = min(top / 2, lc.ny - 1);
-  const float4* R = sp<float4>(sm, roff);
   const int W = l.nx + 2;
   const int items = (yhi - ylo + 1) * lc.nx;
   for (int i = threadIdx.x; i < items; i += blockDim.x) {
@@ -514,7 +515,7 @@ __device__ __noinline__ void level_down(const cg::cluster_group& cl, unsigned ch
     });
   }
   level_sync(blk);
-  restrict_rows(cl, sm, l, o, yo, L[g + 1], rank);
+  restrict_rows(cl, sm, l, o, sp<float4>(sm, yo), L[g + 1], rank);
   level_sync(blk);
 }
 
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(CNT, 1)
       put(cl, sm, L0, so, rank, o0, fy0 + k, fx, sub4(r[k], ax));
     });
     cluster_sync_all();
-    restrict_rows(cl, sm, L0, o0, so, L[1], rank);
+    restrict_rows(cl, sm, L0, o0, sp<float4>(sm, so), L[1], rank);
     cluster_sync_all();
     // ---- coarse grids
     for (int g = 1; g < gs; ++g) level_down(cl, sm, L, g, rank, nu, om);
@@ -850,13 +851,269 @@ __global__ void __launch_bounds__(CNT, 1)
   cluster_sync_all();
 }
 
+
+// The finest-grid sweep of the wide solver: its nodes one at a time, the 9
+// neighbours loaded per node (L1 serves the re-reads); a rolling window as in
+// fine_sweep would hold 9 more float4 registers across the nodes, which the
+// 64-register budget of two CTAs per SM cannot spare.
+template <typename F>
+__device__ __forceinline__ void wide_sweep(const float* __restrict__ ST, const float4* X, int W, int nx, int fy0,
+                                           int fx, int fn, F f) {
+#pragma unroll
+  for (int k = 0; k < FINE_ITEMS; ++k) {
+    if (k >= fn) break;
+    const int c = (fy0 + k + 1) * W + fx + 1;
+    const float4 ax = apply9(ST + ((fy0 + k) * nx + fx) * 9, X, W, c);
+    f(k, c, ax, X[c]);
+    item_fence();
+  }
+}
+
+// Global working set of the wide solver, per cluster: the finest grid's iterate
+// and its partner as padded float4 grids [(ny + 2) x (nx + 2)] (zero border,
+// never written), and r, p, x, A p as float4 per node.
+struct WideArgs {
+  float4* zs;       // [cluster][2][(ny+2)(nx+2)]
+  float4* vecs;     // [cluster][4][n]: r, p, x, q
+};
+
+// The solver for batches wider than one wave of k_inner_cluster: the same
+// method and the same coarse-grid code, with the finest grid in global memory
+// (L2-resident at the sizes the plan admits) instead of shared memory, so a CTA
+// needs only the coarse grids on chip (two CTAs per SM, 64 registers each) and
+// all clusters of a 126-column batch are resident at once. Each CTA computes
+// its strip of the finest grid reading its neighbours' rows directly; the
+// cluster barrier (release/acquire at cluster scope) orders those accesses. r,
+// p, x and A p live per node in the cluster's vectors; the strip's nodes stay
+// with their thread as in k_inner_cluster.
+template <typename TS, typename TD>
+__global__ void __launch_bounds__(CNT, 2)
+    k_inner_cluster_wide(const CPlan P, const TS* __restrict__ src, int lds, TD* __restrict__ dst, int ldd, int w,
+                         const CArgs a, const WideArgs wa) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ CLevel L[CMAXG];
+  __shared__ CShared S;
+  const cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int cid = (int)(blockIdx.x / CLN);
+  const int col0 = cid * 4;
+  const int G = P.G, gs = P.gs, nu = a.nu;
+  const float om = a.om;
+
+  // ---- set-up of the coarse grids (as in k_inner_cluster, level 0 excluded)
+#pragma unroll
+  for (int g = 0; g < CMAXG; ++g)
+    if ((int)threadIdx.x == g) L[g] = P.L[g];
+  if (threadIdx.x < 4) {
+    S.cs[threadIdx.x] = ColState{0.0, 0.0, 0, 1};
+    S.alpha[threadIdx.x] = 0.f;
+    S.beta[threadIdx.x] = 0.f;
+  }
+  __syncthreads();
+  for (int g = 1; g < G; ++g) {
+    const CLevel& l = L[g];
+    const Own o = own_rows(l, rank);
+    if (o.nr == 0) continue;
+    stage_floats(sp<float>(sm, l.st), l.gst + (size_t)o.r0 * l.nx * 9, o.nr * l.nx * 9);
+  }
+  for (int g = 1; g < G; ++g) {
+    const CLevel& l = L[g];
+    const unsigned end = g + 1 < G ? L[g + 1].b : P.bytes;
+    float4* z = reinterpret_cast<float4*>(sm);
+    for (int i = (int)(l.b / 16) + threadIdx.x; i < (int)(l.st / 16); i += CNT) z[i] = f4(0.f);
+    for (int i = (int)(l.di / 16) + threadIdx.x; i < (int)(end / 16); i += CNT) z[i] = f4(0.f);
+  }
+  __syncthreads();
+  for (int g = 1; g < G; ++g) {
+    const CLevel& l = L[g];
+    const Own o = own_rows(l, rank);
+    if (o.nr == 0) continue;
+    float* di = sp<float>(sm, l.di);
+    const int lo = max(o.r0 - 1, 0) - o.r0, hi = min(o.r0 + o.nr + 1, l.ny) - o.r0;
+    for (int i = threadIdx.x; i < (hi - lo) * l.nx; i += CNT) {
+      const int ly = lo + i / l.nx, x = i % l.nx;
+      copy_async4(di + pidx(l, ly, x), l.gdi + (size_t)(o.r0 + ly) * l.nx + x);
+    }
+  }
+
+  // ---- finest grid in global memory: this CTA's strip as local rows (row 0 =
+  // grid row r0); thread nodes as in k_inner_cluster
+  const CLevel& L0 = L[0];
+  const Own o0 = own_rows(L0, rank);
+  const int nx0 = L0.nx, W0 = nx0 + 2;
+  const size_t padn = (size_t)(L0.ny + 2) * W0, n0 = (size_t)L0.nx * L0.ny;
+  float4* const bufA = wa.zs + (size_t)cid * 2 * padn + (size_t)o0.r0 * W0;
+  float4* const bufB = bufA + padn;
+  float4* const GR = wa.vecs + (size_t)cid * 4 * n0 + (size_t)o0.r0 * nx0;
+  float4* const GP = GR + n0;
+  float4* const GX = GP + n0;
+  float4* const GQ = GX + n0;
+  const float* ST0 = L0.gst + (size_t)o0.r0 * nx0 * 9;
+  const float* DI0 = L0.gdi + (size_t)o0.r0 * nx0;
+  const int fx = threadIdx.x % nx0, fy0 = P.fine_h * ((int)threadIdx.x / nx0);
+  const int fn = (int)threadIdx.x < (CNT / nx0) * nx0 ? max(0, min(P.fine_h, o0.nr - fy0)) : 0;
+#define FI(k) ((fy0 + (k)) * nx0 + fx)
+#define FC(k) ((fy0 + (k) + 1) * W0 + fx + 1)
+  float4* Z = bufA;
+  float4* Sb = bufB;
+  float4 part = f4(0.f);
+#pragma unroll
+  for (int k = 0; k < FINE_ITEMS; ++k) {
+    if (k < fn) {
+      const int i = FI(k);
+      const size_t node = (size_t)o0.r0 * nx0 + i;
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = col0 + u < w ? (float)src[node * lds + col0 + u] : 0.f;
+      const float4 r = make_float4(v[0], v[1], v[2], v[3]);
+      GR[i] = r;
+      GP[i] = f4(0.f);
+      GX[i] = f4(0.f);
+      dot4(part, r, r);
+      const float dd = om * DI0[i];
+      Z[FC(k)] = make_float4(dd * v[0], dd * v[1], dd * v[2], dd * v[3]);
+    }
+  }
+  copy_async_wait();
+  cluster_reduce(cl, S, RK_INIT, part, a, rank);
+
+  const int cap = (a.fixed > 0 ? a.fixed : a.maxit) + 1;
+  for (int it = 0; it < cap && S.active; ++it) {
+    // ---- finest grid down: sweeps 2..nu, residual, restriction
+    for (int s = 1; s < nu; ++s) {
+      wide_sweep(ST0, Z, W0, nx0, fy0, fx, fn, [&](int k, int c, const float4& ax, const float4& xc) {
+        const float4 r = GR[FI(k)];
+        const float dd = om * DI0[FI(k)];
+        Sb[c] = make_float4(fmaf(dd, r.x - ax.x, xc.x), fmaf(dd, r.y - ax.y, xc.y), fmaf(dd, r.z - ax.z, xc.z),
+                            fmaf(dd, r.w - ax.w, xc.w));
+      });
+      cluster_sync_all();
+      float4* t = Z; Z = Sb; Sb = t;
+    }
+    wide_sweep(ST0, Z, W0, nx0, fy0, fx, fn, [&](int k, int c, const float4& ax, const float4&) {
+      Sb[c] = sub4(GR[FI(k)], ax);
+    });
+    cluster_sync_all();
+    restrict_rows(cl, sm, L0, o0, Sb, L[1], rank);
+    cluster_sync_all();
+    // ---- coarse grids
+    for (int g = 1; g < gs; ++g) level_down(cl, sm, L, g, rank, nu, om);
+    if (rank == 0) block_levels(cl, sm, L, gs, G, nu, om);
+    cluster_sync_all();
+    for (int g = gs - 1; g >= 1; --g) level_up(cl, sm, L, g, G, rank, nu, om);
+    // ---- finest grid up; the last sweep also sums r . z
+    const float4* XC = sp<float4>(sm, final_buf(L[1], G == 2, nu));
+    const int Wc = L[1].nx + 2;
+    for (int s = 1; s <= nu; ++s) {
+      part = f4(0.f);
+      wide_sweep(ST0, Z, W0, nx0, fy0, fx, fn, [&](int k, int c, const float4& ax, const float4& xc) {
+        const float4 r = GR[FI(k)];
+        const float dd = om * DI0[FI(k)];
+        float4 v;
+        if (s == 1) {
+          const int y = o0.r0 + fy0 + k;
+          float4 apc, pc;
+          coarse_corr(ST0 + FI(k) * 9, XC, Wc, patch_centre(L[1], rank, y, fx), y & 1, fx & 1, apc, pc);
+          const float4 xv = add4(xc, pc);
+          v = make_float4(fmaf(dd, r.x - (ax.x + apc.x), xv.x), fmaf(dd, r.y - (ax.y + apc.y), xv.y),
+                          fmaf(dd, r.z - (ax.z + apc.z), xv.z), fmaf(dd, r.w - (ax.w + apc.w), xv.w));
+        } else {
+          v = make_float4(fmaf(dd, r.x - ax.x, xc.x), fmaf(dd, r.y - ax.y, xc.y), fmaf(dd, r.z - ax.z, xc.z),
+                          fmaf(dd, r.w - ax.w, xc.w));
+        }
+        Sb[c] = v;
+        dot4(part, r, v);
+      });
+      if (s == nu) cluster_reduce(cl, S, RK_RHO, part, a, rank);
+      else cluster_sync_all();
+      float4* t = Z; Z = Sb; Sb = t;
+    }
+    // ---- p = z + beta p, q = A z + beta q_old, p . q
+    {
+      const float4 bt = make_float4(S.beta[0], S.beta[1], S.beta[2], S.beta[3]);
+      part = f4(0.f);
+      wide_sweep(ST0, Z, W0, nx0, fy0, fx, fn, [&](int k, int, const float4& az, const float4& z) {
+        const int i = FI(k);
+        const float4 po = GP[i];
+        const float4 qo = it > 0 ? GQ[i] : f4(0.f);
+        const float4 p = make_float4(fmaf(bt.x, po.x, z.x), fmaf(bt.y, po.y, z.y), fmaf(bt.z, po.z, z.z),
+                                     fmaf(bt.w, po.w, z.w));
+        const float4 q = make_float4(fmaf(bt.x, qo.x, az.x), fmaf(bt.y, qo.y, az.y), fmaf(bt.z, qo.z, az.z),
+                                     fmaf(bt.w, qo.w, az.w));
+        GP[i] = p;
+        GQ[i] = q;
+        dot4(part, p, q);
+      });
+    }
+    cluster_reduce(cl, S, RK_PQ, part, a, rank);
+    // ---- x += alpha p, r -= alpha q on the unfinished columns; r . r; the
+    // next V-cycle's first sweep om D^-1 r
+    {
+      const float al0 = S.alpha[0], al1 = S.alpha[1], al2 = S.alpha[2], al3 = S.alpha[3];
+      const bool dn0 = S.cs[0].done, dn1 = S.cs[1].done, dn2 = S.cs[2].done, dn3 = S.cs[3].done;
+      const bool up0 = !dn0 && col0 < w, up1 = !dn1 && col0 + 1 < w, up2 = !dn2 && col0 + 2 < w,
+                 up3 = !dn3 && col0 + 3 < w;
+      part = f4(0.f);
+#pragma unroll
+      for (int k = 0; k < FINE_ITEMS; ++k) {
+        if (k >= fn) break;
+        const int i = FI(k);
+        const float4 p = GP[i], q = GQ[i];
+        float4 x = GX[i], r = GR[i];
+        if (up0) x.x = fmaf(al0, p.x, x.x);
+        if (up1) x.y = fmaf(al1, p.y, x.y);
+        if (up2) x.z = fmaf(al2, p.z, x.z);
+        if (up3) x.w = fmaf(al3, p.w, x.w);
+        if (!dn0) r.x = fmaf(-al0, q.x, r.x);
+        if (!dn1) r.y = fmaf(-al1, q.y, r.y);
+        if (!dn2) r.z = fmaf(-al2, q.z, r.z);
+        if (!dn3) r.w = fmaf(-al3, q.w, r.w);
+        GX[i] = x;
+        GR[i] = r;
+        dot4(part, r, r);
+        const float dd = om * DI0[i];
+        Z[FC(k)] = make_float4(dd * r.x, dd * r.y, dd * r.z, dd * r.w);
+      }
+    }
+    cluster_reduce(cl, S, RK_RR, part, a, rank);
+  }
+
+  // ---- the solution into the output block
+#pragma unroll
+  for (int k = 0; k < FINE_ITEMS; ++k) {
+    if (k >= fn) break;
+    const int i = FI(k);
+    const float4 v = GX[i];
+    const size_t node = (size_t)o0.r0 * nx0 + i;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (col0 + u < w) dst[node * ldd + col0 + u] = (TD)comp(v, u);
+  }
+#undef FI
+#undef FC
+  if (rank == 0 && threadIdx.x < 4 && a.iters && col0 + (int)threadIdx.x < w)
+    a.iters[col0 + threadIdx.x] = S.cs[threadIdx.x].iters;
+  cluster_sync_all();
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ host side ---
 
-template <typename TS, typename TD>
-static int cluster_kernel_ok(unsigned bytes, int optin) {
-  auto kern = k_inner_cluster<TS, TD>;
+// Host-side state of the cluster solvers (h->cl_plan).
+struct ClusterSolver {
+  CPlan P{};                  // k_inner_cluster: the whole hierarchy on chip
+  CPlan Pw{};                 // k_inner_cluster_wide: the coarse grids on chip
+  int maxcl = 0, maxclw = 0;  // clusters resident at once
+  float4* xs = nullptr;       // k_inner_cluster: x and A p per cluster
+  float4* wzs = nullptr;      // k_inner_cluster_wide: padded finest-grid iterates
+  float4* wvecs = nullptr;    // k_inner_cluster_wide: r, p, x, A p
+};
+
+// Clusters of kernel kern resident at once with `bytes` of dynamic shared
+// memory (0 if it cannot run).
+template <typename K>
+static int max_clusters(K kern, unsigned bytes, int optin) {
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 0;
   if ((long long)bytes + (long long)fa.sharedSizeBytes > optin) return 0;
@@ -877,20 +1134,20 @@ static int cluster_kernel_ok(unsigned bytes, int optin) {
   return nclusters;
 }
 
-// Build the shared-memory plan of the hierarchy and decide whether the
-// cluster solver can run it (h->cl_plan stays null when it cannot). Any CUDA
-// error on this path only disables the cluster solver; it is cleared.
+// Build the shared-memory plans of the hierarchy and decide which cluster
+// solver can run it (h->cl_plan stays null when neither can). Any CUDA error
+// on this path only disables the cluster solvers; it is cleared.
 int cluster_setup(sg_problem* h) {
   const char* ev = getenv("SGHSC_NO_CLUSTER");
   if (ev && ev[0] == '1') return SG_OK;
   const int G = (int)h->grids.size();
   if (G < 2 || G > CMAXG) return SG_OK;
-  CPlan P{};
-  unsigned off = 0;
-  auto take = [&](size_t bytes) {
-    const unsigned o = off;
-    off += (unsigned)((bytes + 15) & ~(size_t)15);
-    return o;
+  CPlan P{}, Pw{};
+  unsigned off = 0, offw = 0;
+  auto take = [](unsigned& o, size_t bytes) {
+    const unsigned r = o;
+    o += (unsigned)((bytes + 15) & ~(size_t)15);
+    return r;
   };
   int gs = G;
   for (int g = 0; g < G; ++g) {
@@ -907,13 +1164,26 @@ int cluster_setup(sg_problem* h) {
       if (gs < G) return SG_OK;                 // strips below a grid held by CTA 0
     }
     const size_t vec = (size_t)(l.rows + 2) * (l.nx + 2) * 16;
-    l.b = g > 0 ? take(vec) : 0;
-    l.x = take(vec);
-    l.y = take(vec);
-    l.st = take((size_t)l.rows * l.nx * 9 * sizeof(float));
-    l.di = g > 0 ? take((size_t)(l.rows + 2) * (l.nx + 2) * sizeof(float)) : 0;
+    const size_t stb = (size_t)l.rows * l.nx * 9 * sizeof(float);
+    const size_t dib = (size_t)(l.rows + 2) * (l.nx + 2) * sizeof(float);
+    l.b = g > 0 ? take(off, vec) : 0;
+    l.x = take(off, vec);
+    l.y = take(off, vec);
+    l.st = take(off, stb);
+    l.di = g > 0 ? take(off, dib) : 0;
     l.gst = gr.st32;
     l.gdi = gr.dinv32;
+    CLevel& lw = Pw.L[g];
+    lw = l;
+    if (g == 0) {
+      lw.b = lw.x = lw.y = lw.st = lw.di = 0;   // the finest grid lives in global memory
+    } else {
+      lw.b = take(offw, vec);
+      lw.x = take(offw, vec);
+      lw.y = take(offw, vec);
+      lw.st = take(offw, stb);
+      lw.di = take(offw, dib);
+    }
   }
   if (gs == 0 || gs == G) return SG_OK;
   if (P.L[0].nx > CNT) return SG_OK;
@@ -921,47 +1191,87 @@ int cluster_setup(sg_problem* h) {
   if (P.fine_h > FINE_ITEMS) return SG_OK;
   for (int g = 0; g + 1 < gs; ++g)   // strips of consecutive grids line up (row 2Y+1 over row Y)
     if (P.L[g].rows != 2 * P.L[g + 1].rows || P.L[g + 1].nx != (P.L[g].nx - 1) / 2) return SG_OK;
-  P.G = G;
-  P.gs = gs;
+  P.G = Pw.G = G;
+  P.gs = Pw.gs = gs;
   P.bytes = off;
+  Pw.bytes = offw;
+  Pw.fine_h = P.fine_h;
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
     cudaGetLastError();
     return SG_OK;
   }
-  const int maxcl = std::min(std::min(cluster_kernel_ok<double, float>(off, optin), cluster_kernel_ok<float, float>(off, optin)),
-                             std::min(cluster_kernel_ok<double, double>(off, optin), cluster_kernel_ok<float, double>(off, optin)));
+  auto min4 = [](int a, int b, int c, int d) { return std::min(std::min(a, b), std::min(c, d)); };
+  const int maxcl = min4(max_clusters(k_inner_cluster<double, float>, off, optin),
+                         max_clusters(k_inner_cluster<float, float>, off, optin),
+                         max_clusters(k_inner_cluster<double, double>, off, optin),
+                         max_clusters(k_inner_cluster<float, double>, off, optin));
+  const int maxclw = min4(max_clusters(k_inner_cluster_wide<double, float>, offw, optin),
+                          max_clusters(k_inner_cluster_wide<float, float>, offw, optin),
+                          max_clusters(k_inner_cluster_wide<double, double>, offw, optin),
+                          max_clusters(k_inner_cluster_wide<float, double>, offw, optin));
   cudaGetLastError();
-  if (maxcl < 1) return SG_OK;
-  P.maxcl = maxcl;
-  SG_TRY_CUDA(cudaMalloc(&h->cl_xs, 2 * (size_t)maxcl * P.L[0].nx * P.L[0].ny * sizeof(float4)));
-  h->cl_plan = new CPlan(P);
+  if (maxcl < 1 && maxclw < 1) return SG_OK;
+  ClusterSolver* cs = new ClusterSolver();
+  cs->P = P;
+  cs->Pw = Pw;
+  cs->maxcl = std::max(maxcl, 0);
+  cs->maxclw = std::max(maxclw, 0);
+  P.maxcl = cs->maxcl;
+  cs->P.maxcl = cs->maxcl;
+  cs->Pw.maxcl = cs->maxclw;
+  h->cl_plan = cs;   // owned from here on (cluster_free)
+  const size_t n = (size_t)P.L[0].nx * P.L[0].ny, padn = (size_t)(P.L[0].ny + 2) * (P.L[0].nx + 2);
+  if (cs->maxcl > 0) SG_TRY_CUDA(cudaMalloc((void**)&cs->xs, 2 * (size_t)cs->maxcl * n * sizeof(float4)));
+  if (cs->maxclw > 0) {
+    SG_TRY_CUDA(cudaMalloc((void**)&cs->wzs, 2 * (size_t)cs->maxclw * padn * sizeof(float4)));
+    SG_TRY_CUDA(cudaMemset(cs->wzs, 0, 2 * (size_t)cs->maxclw * padn * sizeof(float4)));   // zero borders
+    SG_TRY_CUDA(cudaMalloc((void**)&cs->wvecs, 4 * (size_t)cs->maxclw * n * sizeof(float4)));
+  }
   return SG_OK;
 }
 
 void cluster_free(sg_problem* h) {
-  delete (CPlan*)h->cl_plan;
+  ClusterSolver* cs = (ClusterSolver*)h->cl_plan;
+  if (!cs) return;
+  cudaFree(cs->xs);
+  cudaFree(cs->wzs);
+  cudaFree(cs->wvecs);
+  delete cs;
   h->cl_plan = nullptr;
-  cudaFree(h->cl_xs);
-  h->cl_xs = nullptr;
 }
 
-// A batch takes the cluster solver when all its clusters are resident at once:
-// the solve of one cluster is latency-bound, so a second wave would double the
-// time, and the stand-alone kernels are then faster.
-bool cluster_usable(const sg_problem* h, int dtype, int w) {
-  return dtype == SG_F32 && h->cl_plan != nullptr && ceil_div(w, 4) <= ((const CPlan*)h->cl_plan)->maxcl;
+// Which cluster solver an FP32 batch of w columns takes: 1 = the on-chip one
+// when all its clusters are resident at once (a second wave would double the
+// latency-bound solve), 2 = the wide one (finest grid in global memory) when
+// its clusters are, 0 = neither (the stand-alone kernels).
+static int cluster_path(const sg_problem* h, int dtype, int w) {
+  const ClusterSolver* cs = (const ClusterSolver*)h->cl_plan;
+  if (dtype != SG_F32 || !cs) return 0;
+  const int ncl = ceil_div(w, 4);
+  if (ncl <= cs->maxcl) return 1;
+  if (ncl <= cs->maxclw) return 2;
+  return 0;
 }
+
+bool cluster_usable(const sg_problem* h, int dtype, int w) { return cluster_path(h, dtype, w) != 0; }
 
 }  // namespace sghsc
 
 extern "C" int sg_inner_cluster(const sg_problem* h) { return h && h->cl_plan ? 1 : 0; }
 
+extern "C" int sg_inner_path(const sg_problem* h, int w, int dtype) {
+  if (!h || w <= 0) return 0;
+  return sghsc::cluster_path(h, dtype, w);
+}
+
 namespace sghsc {
 
 int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void* dst, int ldd, int dst_t, int w,
                         const sg_prec_opts& o, cudaStream_t s) {
-  const CPlan& P = *(const CPlan*)h->cl_plan;
+  const ClusterSolver& cs = *(const ClusterSolver*)h->cl_plan;
+  const int path = cluster_path(h, SG_F32, w);
+  const CPlan& P = path == 2 ? cs.Pw : cs.P;
   CArgs a;
   a.om = (float)o.omega;
   a.nu = o.nu;
@@ -971,8 +1281,11 @@ int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void
   a.status = h->status;
   a.iacc = h->iacc;
   a.iters = h->iw32.iters && h->iw32.wcap >= w ? h->iw32.iters : nullptr;
-  a.xs = (float4*)h->cl_xs;
-  a.qs = a.xs + (size_t)P.maxcl * P.L[0].nx * P.L[0].ny;
+  a.xs = cs.xs;
+  a.qs = cs.xs ? cs.xs + (size_t)cs.maxcl * P.L[0].nx * P.L[0].ny : nullptr;
+  WideArgs wa;
+  wa.zs = cs.wzs;
+  wa.vecs = cs.wvecs;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ceil_div(w, 4) * CLN));
   cfg.blockDim = dim3(CNT);
@@ -985,14 +1298,26 @@ int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (src_t == SG_F64 && dst_t == SG_F64)
-    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<double, double>, P, (const double*)src, lds, (double*)dst, ldd, w, a));
-  else if (src_t == SG_F64)
-    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<double, float>, P, (const double*)src, lds, (float*)dst, ldd, w, a));
-  else if (dst_t == SG_F64)
-    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<float, double>, P, (const float*)src, lds, (double*)dst, ldd, w, a));
-  else
-    SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<float, float>, P, (const float*)src, lds, (float*)dst, ldd, w, a));
+  const bool s64 = src_t == SG_F64, d64 = dst_t == SG_F64;
+  if (path == 2) {
+    if (s64 && d64)
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster_wide<double, double>, P, (const double*)src, lds, (double*)dst, ldd, w, a, wa));
+    else if (s64)
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster_wide<double, float>, P, (const double*)src, lds, (float*)dst, ldd, w, a, wa));
+    else if (d64)
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster_wide<float, double>, P, (const float*)src, lds, (double*)dst, ldd, w, a, wa));
+    else
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster_wide<float, float>, P, (const float*)src, lds, (float*)dst, ldd, w, a, wa));
+  } else {
+    if (s64 && d64)
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<double, double>, P, (const double*)src, lds, (double*)dst, ldd, w, a));
+    else if (s64)
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<double, float>, P, (const double*)src, lds, (float*)dst, ldd, w, a));
+    else if (d64)
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<float, double>, P, (const float*)src, lds, (double*)dst, ldd, w, a));
+    else
+      SG_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_inner_cluster<float, float>, P, (const float*)src, lds, (float*)dst, ldd, w, a));
+  }
   note_launch();
   return SG_OK;
 }

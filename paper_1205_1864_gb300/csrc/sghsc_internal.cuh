@@ -131,8 +131,7 @@ struct sg_problem {
   // multigrid
   std::vector<sghsc::GridLevel> grids;
   int cb_level = 0;                         // first grid handled by the in-block coarse V-cycle
-  void* cl_plan = nullptr;                  // shared-memory plan of the cluster inner solver (null: not usable)
-  void* cl_xs = nullptr;                    // its solution scratch: n float4 per resident cluster
+  void* cl_plan = nullptr;                  // cluster inner solvers: plans and scratch (null: not usable)
   bool pipe_off = false;                    // SGHSC_NO_PIPE=1: no row-pipelined sweeps on large grids
   // workspace
   sghsc::InnerWork iw32, iw64;

@@ -145,3 +145,38 @@ def test_cluster_solve_to_1e8_matches_direct(lib):
     assert np.abs(_np(U1) - ref).max() <= 1e-6 * np.abs(ref).max()
     assert abs(s1.iterations - s0.iterations) <= 1
     assert s1.inner_iters_total > 0 and s1.inner_iters_max >= 1
+
+
+def test_wide_cluster_solver_parity(lib):
+    """The 126-column top level of the 128x128, M=6 workload: more clusters
+    than the on-chip solver keeps resident, so it takes the solver with the
+    finest grid in global memory (path 2) where the device holds its clusters.
+    Fixed iteration counts against the oracle and the stand-alone kernels; a
+    tolerance-driven solve by its true residuals."""
+    import torch
+    prob, A, G, off = problem(128, 2, 1)
+    h1, h0 = _pair(lib, prob, 1)
+    w = 126
+    path = h1.inner_path(w)
+    assert path in (0, 2)
+    if path == 0:
+        pytest.skip("the device holds too few clusters for the wide solver")
+    lv = gmg.hierarchy(A[0], 128)
+    B = S.random_block(prob.n, w, seed=71).astype(np.float32).astype(np.float64)
+    B[:, 9] = 0.0
+    o = lib.prec_opts(inner_fixed_iters=3)
+    X1, it1 = lib.sg_inner_solve(h1, _t(B, torch.float32), o)
+    ref, it_ref = krylov.pcg_columns(lambda v: A[0] @ v, B, lambda r: gmg.vcycle(lv, r), tol=0.0, maxit=3,
+                                     fixed_iters=3)
+    assert list(it1) == list(it_ref)
+    X1 = _np(X1)
+    scale = np.abs(ref).max(axis=0, keepdims=True) + 1e-300
+    assert np.all(np.abs(X1 - ref) <= 1e-4 * scale)
+    assert np.all(X1[:, 9] == 0.0)
+    X0, _ = lib.sg_inner_solve(h0, _t(B, torch.float32), o)
+    assert np.all(np.abs(X1 - _np(X0)) <= 2e-5 * scale)
+    Bt = S.random_block(prob.n, w, seed=72)
+    Xt, itt = lib.sg_inner_solve(h1, _t(Bt, torch.float32), lib.prec_opts(inner_tol=1e-2))
+    B32 = Bt.astype(np.float32).astype(np.float64)
+    res = np.linalg.norm(B32 - A[0] @ _np(Xt), axis=0) / np.linalg.norm(B32, axis=0)
+    assert np.all(res <= 2e-2)
