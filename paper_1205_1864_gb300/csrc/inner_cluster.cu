@@ -865,7 +865,6 @@ __device__ __forceinline__ void wide_sweep(const float* __restrict__ ST, const f
     const int c = (fy0 + k + 1) * W + fx + 1;
     const float4 ax = apply9(ST + ((fy0 + k) * nx + fx) * 9, X, W, c);
     f(k, c, ax, X[c]);
-    item_fence();
   }
 }
 
