@@ -1340,6 +1340,141 @@ __global__ void __launch_bounds__(pipe::NT, 1)
   }
 }
 
+// The residual and its restriction in the same row pipeline: bc = P^T (b - A x)
+// on the coarse grid of every other row. A block owns strips of 32 coarse nodes
+// (fine nodes x0 .. x0 + 64 of their restriction stencils, x0 = 64 * strip) by
+// 64 columns and a contiguous run of coarse rows [Ya, Yb); it walks the fine
+// rows 2 Ya .. 2 Yb, forms each residual row once into a ring of 3 rows, and
+// after fine row 2Y + 2 writes coarse row Y from rows 2Y, 2Y + 1, 2Y + 2.
+// Inputs per fine row: x on nodes x0 - 1 .. x0 + 65 (ring of 4, the row after
+// next in flight), b and the stencils on x0 .. x0 + 64.
+namespace rpipe {
+constexpr int RX = pipe::PX + 1;       // residual nodes of a strip: x0 .. x0 + 64
+constexpr int XX = RX + 2;             // x nodes: x0 - 1 .. x0 + 65
+constexpr int CX = pipe::PX / 2;       // coarse nodes per strip
+constexpr int PG = pipe::PG, RING = 4, NT = pipe::NT;
+constexpr int XSLOT = XX * PG, BSLOT = RX * PG, RSLOT = RX * PG;
+}  // namespace rpipe
+
+static constexpr size_t rpipe_smem_bytes() {
+  using namespace rpipe;
+  return (size_t)RING * XSLOT * 16 + (size_t)RING * BSLOT * 16 + (size_t)3 * RSLOT * 16 + (size_t)RING * RX * 9 * 4;
+}
+
+__global__ void __launch_bounds__(rpipe::NT, 1)
+    k_pipe_restrict(int nxf, int nyf, int nxc, int nyc, int wp, const float* __restrict__ st, const float* X,
+                    const float* Bv, float* bc) {
+  using namespace rpipe;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* xr = reinterpret_cast<float4*>(smem_raw);   // [RING][XX][PG]
+  float4* br = xr + RING * XSLOT;                      // [RING][RX][PG]
+  float4* rr = br + RING * BSLOT;                      // [3][RX][PG] residual rows
+  float* sr = reinterpret_cast<float*>(rr + 3 * RSLOT);   // [RING][RX * 9]
+  const int t = threadIdx.x;
+  const int nseg = (nxc + CX - 1) / CX, nch = (wp + 4 * PG - 1) / (4 * PG);
+  const long long tot = (long long)nch * nseg * nyc;
+  long long u = tot * blockIdx.x / gridDim.x;
+  const long long u1 = tot * (blockIdx.x + 1) / gridDim.x;
+  while (u < u1) {
+    const int strip = (int)(u / nyc);
+    const int Ya = (int)(u - (long long)strip * nyc);
+    const int Yb = (int)min((long long)nyc, (long long)Ya + (u1 - u));
+    const int ch = strip / nseg, sg = strip - ch * nseg;
+    const int c0 = ch * 4 * PG, x0 = sg * pipe::PX;
+    const int ya = 2 * Ya, yb = 2 * Yb;   // fine rows whose residuals are formed: ya .. yb
+    auto issue = [&](int r) {
+      const int sl = r & (RING - 1);
+      const bool rowok = r >= 0 && r < nyf;
+      for (int it = t; it < XSLOT; it += NT) {
+        const int j = it / PG, g = it - j * PG;
+        const int x = x0 - 1 + j, c = c0 + 4 * g;
+        const bool ok = rowok && x >= 0 && x < nxf && c < wp;
+        cp_async16_z(&xr[sl * XSLOT + it], X + (ok ? ((size_t)r * nxf + x) * wp + c : 0), ok);
+      }
+      for (int it = t; it < BSLOT; it += NT) {
+        const int j = it / PG, g = it - j * PG;
+        const int x = x0 + j, c = c0 + 4 * g;
+        const bool ok = rowok && x < nxf && c < wp;
+        cp_async16_z(&br[sl * BSLOT + it], Bv + (ok ? ((size_t)r * nxf + x) * wp + c : 0), ok);
+      }
+      for (int it = t; it < RX * 9; it += NT) {
+        const int j = it / 9, x = x0 + j;
+        const bool ok = rowok && x < nxf;
+        cp_async4_z(&sr[sl * RX * 9 + it], st + (ok ? ((size_t)r * nxf + x) * 9 + (it - j * 9) : 0), ok);
+      }
+    };
+    __syncthreads();   // the rings are free (previous strip done)
+    for (int r = ya - 1; r <= ya + 1; ++r) {
+      if (r <= yb + 1) issue(r);
+      cp_async_commit();
+    }
+    for (int y = ya; y <= yb; ++y) {
+      __syncthreads();   // the slot of row y - 2 is read no more
+      if (y + 2 <= yb + 1) issue(y + 2);
+      cp_async_commit();
+      cp_async_wait_ahead();
+      __syncthreads();
+      // residual row y (zero outside the fine grid)
+      const int s1 = y & (RING - 1), s0 = (y + RING - 1) & (RING - 1), s2 = (y + 1) & (RING - 1);
+      const int rs = y % 3;
+      for (int it = t; it < RSLOT; it += NT) {
+        const int j = it / PG, g = it - j * PG;
+        const int x = x0 + j;
+        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (y < nyf && x < nxf && c0 + 4 * g < wp) {
+          const float* s9 = sr + s1 * RX * 9 + j * 9;
+          float4 ax = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            const int sl = dy == 0 ? s0 : (dy == 1 ? s1 : s2);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+              const float a = s9[dy * 3 + dx];
+              const float4 v = xr[sl * XSLOT + (j + dx) * PG + g];
+              ax.x = fmaf(a, v.x, ax.x);
+              ax.y = fmaf(a, v.y, ax.y);
+              ax.z = fmaf(a, v.z, ax.z);
+              ax.w = fmaf(a, v.w, ax.w);
+            }
+          }
+          const float4 bv = br[s1 * BSLOT + j * PG + g];
+          res = make_float4(bv.x - ax.x, bv.y - ax.y, bv.z - ax.z, bv.w - ax.w);
+        }
+        rr[rs * RSLOT + it] = res;
+      }
+      // coarse row Y = y / 2 - 1 once fine rows 2Y .. 2Y + 2 are formed
+      if (!(y & 1) && y >= ya + 2) {
+        __syncthreads();
+        const int Y = y / 2 - 1;
+        const int ra = (y - 2) % 3, rb = (y - 1) % 3, rc = rs;
+        for (int it = t; it < CX * PG; it += NT) {
+          const int Xl = it / PG, g = it - Xl * PG;
+          const int Xc = x0 / 2 + Xl, c = c0 + 4 * g;
+          if (Xc >= nxc || c >= wp) continue;
+          const int jc = 2 * Xl + 1;   // fine node 2X + 1 within the strip
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            const int rsl = dy == 0 ? ra : (dy == 1 ? rb : rc);
+            const float wy = dy == 1 ? 1.f : 0.5f;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              const float wgt = wy * (dx == 0 ? 1.f : 0.5f);
+              const float4 v = rr[rsl * RSLOT + (jc + dx) * PG + g];
+              acc.x = fmaf(wgt, v.x, acc.x);
+              acc.y = fmaf(wgt, v.y, acc.y);
+              acc.z = fmaf(wgt, v.z, acc.z);
+              acc.w = fmaf(wgt, v.w, acc.w);
+            }
+          }
+          *reinterpret_cast<float4*>(bc + ((size_t)Y * nxc + Xc) * wp + c) = acc;
+        }
+      }
+    }
+    u += Yb - Ya;
+  }
+}
+
 // ------------------------------------------------------------ host side ---
 
 // Row-pipelined sweeps (k_pipe: the Jacobi sweeps and the two sweeps from
@@ -1505,6 +1640,15 @@ static int restrict_tile(const sg_problem* h, const GridLevel& C, int ng) {
 template <typename T>
 static int launch_resid_restrict(sg_problem* h, const GridLevel& G, const GridLevel& C, int wp, const T* st,
                                  const T* b, const T* x, T* bc, const int* done, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (use_pipe<T>(h, G, wp)) {
+      const size_t smem = rpipe_smem_bytes();
+      SG_TRY_CUDA(cudaFuncSetAttribute(k_pipe_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      { k_pipe_restrict<<<h->num_sms, rpipe::NT, smem, s>>>(G.nx, G.ny, C.nx, C.ny, wp, st, x, b, bc); ::sghsc::note_launch(); }
+      SG_CHECK_LAUNCH();
+      return SG_OK;
+    }
+  }
   const int ng = wp / VW<T>::N;
   const int tc = restrict_tile(h, C, ng);
   const int items = (2 * tc + 1) * (2 * tc + 1) * ng;
