@@ -1475,6 +1475,178 @@ __global__ void __launch_bounds__(rpipe::NT, 1)
   }
 }
 
+// The coarse correction with the first post-smoothing sweep in the row
+// pipeline: x' = x + P xc, xo = x' + om D^-1 (b - A x') (no dot). Besides the
+// fine rows (x with halo, b, stencils, diagonals: rings of 4 as in k_pipe) a
+// ring of 4 coarse rows holds xc on the coarse nodes x0/2 - 2 .. x0/2 + 32 that
+// the strip's interpolation patches touch; coarse rows advance one per two fine
+// rows, each fetched two fine steps before its first use. The correction is
+// formed as in the node-by-node kernel: per fine node the 3 x 3 coarse patch
+// and the weights K = Wy^T S Wx.
+namespace ppipe {
+constexpr int CN = pipe::PX / 2 + 3;   // coarse nodes of a strip's patches
+constexpr int CSLOT = CN * pipe::PG;
+}  // namespace ppipe
+
+static constexpr size_t ppipe_smem_bytes() {
+  return pipe_smem_bytes<PIPE_JACOBI>() + (size_t)pipe::RING * ppipe::CSLOT * 16;
+}
+
+// interpolation weight of patch entry a (0..2) for the fine point at offset d
+// (-1..1) from a fine coordinate of parity odd (coarse node X on fine 2X + 1)
+__device__ __forceinline__ float pp_w(bool odd, int d, int a) {
+  if (odd) return d < 0 ? (a < 2 ? 0.5f : 0.f) : d == 0 ? (a == 1 ? 1.f : 0.f) : (a > 0 ? 0.5f : 0.f);
+  return d < 0 ? (a == 1 ? 1.f : 0.f) : d == 0 ? (a > 0 ? 0.5f : 0.f) : (a == 2 ? 1.f : 0.f);
+}
+
+__global__ void __launch_bounds__(pipe::NT, 1)
+    k_pipe_prolong(int nx, int ny, int nxc, int nyc, int wp, const float* __restrict__ st,
+                   const float* __restrict__ dinv, const float* X, const float* Bv, const float* XC, float* out,
+                   float om) {
+  using namespace pipe;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* xr = reinterpret_cast<float4*>(smem_raw);
+  float4* br = xr + RING * SLOT4;
+  float* sr = reinterpret_cast<float*>(br + RING * BSLOT4);
+  float* dr = sr + RING * PX * 9;
+  float4* cr = reinterpret_cast<float4*>(dr + RING * HX);   // [RING][CN][PG] coarse rows
+  const int t = threadIdx.x, grp = t % PG, lx = t / PG;
+  const int nseg = (nx + PX - 1) / PX, nch = (wp + 4 * PG - 1) / (4 * PG);
+  const long long tot = (long long)nch * nseg * ny;
+  long long u = tot * blockIdx.x / gridDim.x;
+  const long long u1 = tot * (blockIdx.x + 1) / gridDim.x;
+  while (u < u1) {
+    const int strip = (int)(u / ny);
+    const int ya = (int)(u - (long long)strip * ny);
+    const int yb = (int)min((long long)ny, (long long)ya + (u1 - u));
+    const int ch = strip / nseg, sg = strip - ch * nseg;
+    const int c0 = ch * 4 * PG, x0 = sg * PX, X0 = x0 / 2 - 2;   // first coarse node of the patches
+    auto issue = [&](int r) {   // fine row r
+      const int sl = r & (RING - 1);
+      const bool rowok = r >= 0 && r < ny;
+      for (int it = t; it < SLOT4; it += NT) {
+        const int j = it / PG, g = it - j * PG;
+        const int x = x0 - 1 + j, c = c0 + 4 * g;
+        const bool ok = rowok && x >= 0 && x < nx && c < wp;
+        cp_async16_z(&xr[sl * SLOT4 + it], X + (ok ? ((size_t)r * nx + x) * wp + c : 0), ok);
+      }
+      for (int it = t; it < BSLOT4; it += NT) {
+        const int j = it / PG, g = it - j * PG;
+        const int x = x0 + j, c = c0 + 4 * g;
+        const bool ok = rowok && x < nx && c < wp;
+        cp_async16_z(&br[sl * BSLOT4 + it], Bv + (ok ? ((size_t)r * nx + x) * wp + c : 0), ok);
+      }
+      for (int it = t; it < PX * 9; it += NT) {
+        const int j = it / 9, x = x0 + j;
+        const bool ok = rowok && x < nx;
+        cp_async4_z(&sr[sl * PX * 9 + it], st + (ok ? ((size_t)r * nx + x) * 9 + (it - j * 9) : 0), ok);
+      }
+      for (int it = t; it < HX; it += NT) {
+        const int x = x0 - 1 + it;
+        const bool ok = rowok && x >= 0 && x < nx;
+        cp_async4_z(&dr[sl * HX + it], dinv + (ok ? (size_t)r * nx + x : 0), ok);
+      }
+    };
+    auto issue_c = [&](int R) {   // coarse row R
+      const int sl = R & (RING - 1);
+      const bool rowok = R >= 0 && R < nyc;
+      for (int it = t; it < ppipe::CSLOT; it += NT) {
+        const int j = it / PG, g = it - j * PG;
+        const int Xc = X0 + j, c = c0 + 4 * g;
+        const bool ok = rowok && Xc >= 0 && Xc < nxc && c < wp;
+        cp_async16_z(&cr[sl * ppipe::CSLOT + it], XC + (ok ? ((size_t)R * nxc + Xc) * wp + c : 0), ok);
+      }
+    };
+    // coarse rows needed by fine row y: ((y-1)>>1) - 1 .. ((y-1)>>1) + 1
+    int cnext = ((ya - 1) >> 1) - 1;
+    const int clast = ((yb - 2) >> 1) + 1;
+    __syncthreads();
+    for (int r = ya - 1; r <= ya + 1; ++r) {
+      if (r <= yb) issue(r);
+      const int need = ((r + 1 - 1) >> 1) + 1;   // coarse rows needed by fine row r + 1
+      while (cnext <= need && cnext <= clast) issue_c(cnext++);
+      cp_async_commit();
+    }
+    for (int y = ya; y < yb; ++y) {
+      __syncthreads();
+      if (y + 2 <= yb) issue(y + 2);
+      {
+        const int need = ((y + 3 - 1) >> 1) + 1;   // coarse rows needed by fine row y + 3
+        while (cnext <= need && cnext <= clast) issue_c(cnext++);
+      }
+      cp_async_commit();
+      cp_async_wait_ahead();
+      __syncthreads();
+      const int x = x0 + lx, c = c0 + 4 * grp;
+      if (x < nx && c < wp) {
+        const int s1 = y & (RING - 1);
+        const float* s9 = sr + s1 * PX * 9 + lx * 9;
+        float4 ax = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int sl = (y + dy + RING) & (RING - 1);
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const float a = s9[(dy + 1) * 3 + (dx + 1)];
+            const float4 v = xr[sl * SLOT4 + (lx + 1 + dx) * PG + grp];
+            ax.x = fmaf(a, v.x, ax.x);
+            ax.y = fmaf(a, v.y, ax.y);
+            ax.z = fmaf(a, v.z, ax.z);
+            ax.w = fmaf(a, v.w, ax.w);
+          }
+        }
+        // coarse correction: patch rows Yb - 1 + a, columns Xb - 1 + c
+        const bool oy = y & 1, ox = x & 1;
+        const int Yb = (y - 1) >> 1, Xb = (x - 1) >> 1;
+        float t1[3][3];   // t1[dy][cc] = sum_dx s[dy][dx] wx(dx, cc), s masked to the grid
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const bool iny = y + dy - 1 >= 0 && y + dy - 1 < ny;
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) {
+            float acc = 0.f;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+              const bool inx = x + dx - 1 >= 0 && x + dx - 1 < nx;
+              acc += (iny && inx ? s9[dy * 3 + dx] : 0.f) * pp_w(ox, dx - 1, cc);
+            }
+            t1[dy][cc] = acc;
+          }
+        }
+        float4 apc = make_float4(0.f, 0.f, 0.f, 0.f), pc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          const int ar = (oy || aa > 0) ? aa : 1;   // all-zero weights: a valid slot instead
+          const int sl = (Yb - 1 + ar + RING) & (RING - 1);
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) {
+            const int ccr = (ox || cc > 0) ? cc : 1;
+            const float K = pp_w(oy, -1, aa) * t1[0][cc] + pp_w(oy, 0, aa) * t1[1][cc] + pp_w(oy, 1, aa) * t1[2][cc];
+            const float w0 = pp_w(oy, 0, aa) * pp_w(ox, 0, cc);
+            const float4 v = cr[sl * ppipe::CSLOT + (Xb - 1 + ccr - X0) * PG + grp];
+            apc.x = fmaf(K, v.x, apc.x);
+            apc.y = fmaf(K, v.y, apc.y);
+            apc.z = fmaf(K, v.z, apc.z);
+            apc.w = fmaf(K, v.w, apc.w);
+            pc.x = fmaf(w0, v.x, pc.x);
+            pc.y = fmaf(w0, v.y, pc.y);
+            pc.z = fmaf(w0, v.z, pc.z);
+            pc.w = fmaf(w0, v.w, pc.w);
+          }
+        }
+        const float4 xv0 = xr[s1 * SLOT4 + (lx + 1) * PG + grp];
+        const float4 xv = make_float4(xv0.x + pc.x, xv0.y + pc.y, xv0.z + pc.z, xv0.w + pc.w);
+        const float4 bv = br[s1 * BSLOT4 + lx * PG + grp];
+        const float dd = om * dr[s1 * HX + lx + 1];
+        *reinterpret_cast<float4*>(out + ((size_t)y * nx + x) * wp + c) =
+            make_float4(xv.x + dd * (bv.x - (ax.x + apc.x)), xv.y + dd * (bv.y - (ax.y + apc.y)),
+                        xv.z + dd * (bv.z - (ax.z + apc.z)), xv.w + dd * (bv.w - (ax.w + apc.w)));
+      }
+    }
+    u += yb - ya;
+  }
+}
+
 // ------------------------------------------------------------ host side ---
 
 // Row-pipelined sweeps (k_pipe: the Jacobi sweeps and the two sweeps from
@@ -1730,7 +1902,18 @@ static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, 
   SG_TRY(launch_resid_restrict<T>(h, G, C, wp, st, b, cur, cb, iw.done, s));
   const T* xc = nullptr;
   SG_TRY(vcycle<T>(h, iw, g + 1, cb, (T*)iw.cx[g + 1], (T*)iw.cxt[g + 1], wp, o, s, nullptr, &xc));
-  if (o.nu == 1 && fdot) {
+  bool piped = false;
+  if constexpr (sizeof(T) == 4) {
+    if (use_pipe<T>(h, G, wp) && !(o.nu == 1 && fdot)) {
+      const size_t smem = ppipe_smem_bytes();
+      SG_TRY_CUDA(cudaFuncSetAttribute(k_pipe_prolong, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      { k_pipe_prolong<<<h->num_sms, pipe::NT, smem, s>>>(G.nx, G.ny, C.nx, C.ny, wp, st, dinv, cur, b, xc, oth, om); ::sghsc::note_launch(); }
+      SG_CHECK_LAUNCH();
+      piped = true;
+    }
+  }
+  if (piped) {
+  } else if (o.nu == 1 && fdot) {
     { k_prolong_jacobi<T, true><<<shd.grid, shd.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, wp, shd.k, st, dinv, b, cur, xc, oth, om, *fdot); ::sghsc::note_launch(); }
   } else {
     { const Shape f_ = fit(h, sh, k_prolong_jacobi<T, false>); k_prolong_jacobi<T, false><<<f_.grid, f_.bdim, 0, s>>>(G.nx, G.ny, C.nx, C.ny, wp, f_.k, st, dinv, b, cur, xc, oth, om, fz); ::sghsc::note_launch(); }
