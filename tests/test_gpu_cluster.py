@@ -147,6 +147,47 @@ def test_cluster_solve_to_1e8_matches_direct(lib):
     assert s1.inner_iters_total > 0 and s1.inner_iters_max >= 1
 
 
+@pytest.mark.parametrize("nu,omega", [(1, 0.8), (3, 0.7)])
+def test_wide_cluster_solver_smoothing_variants(lib, nu, omega):
+    """The wide solver with one and three smoothing sweeps (other weights):
+    fixed iteration counts against the oracle."""
+    import torch
+    prob, A, G, off = problem(128, 2, 1)
+    h = lib.SGProblem.from_inputs(prob, 1)
+    w = 90
+    if h.inner_path(w) != 2:
+        pytest.skip("the device holds too few clusters for the wide solver")
+    lv = gmg.hierarchy(A[0], 128)
+    B = S.random_block(prob.n, w, seed=80 + nu).astype(np.float32).astype(np.float64)
+    o = lib.prec_opts(inner_fixed_iters=2, nu=nu, omega=omega)
+    X, it = lib.sg_inner_solve(h, _t(B, torch.float32), o)
+    ref, it_ref = krylov.pcg_columns(lambda v: A[0] @ v, B, lambda r: gmg.vcycle(lv, r, nu=nu, omega=omega),
+                                     tol=0.0, maxit=2, fixed_iters=2)
+    assert list(it) == list(it_ref)
+    scale = np.abs(ref).max(axis=0, keepdims=True) + 1e-300
+    assert np.all(np.abs(_np(X) - ref) <= 1e-4 * scale)
+
+
+def test_hsc_top_level_on_wide_solver(lib):
+    """Algorithm 1 on the 128x128, M=6, p=4 workload (126-column top level on
+    the wide solver, its FP64-residual input variant in the pre-loop): the
+    mixed-precision application against the stand-alone kernels, and the
+    solve to 1e-8."""
+    prob, A, G, off = problem(128, 6, 4, 0.3, 1.0)
+    h1, h0 = _pair(lib, prob, 4)
+    if h1.inner_path(126) != 2:
+        pytest.skip("the device holds too few clusters for the wide solver")
+    R = S.random_block(prob.n, h1.P, seed=90)
+    o = lib.prec_opts(precision=lib.SG_F32, inner_fixed_iters=2)
+    Z1 = _np(lib.hsc_precond_apply(h1, _t(R), o))
+    Z0 = _np(lib.hsc_precond_apply(h0, _t(R), o))
+    assert np.abs(Z1 - Z0).max() <= 1e-4 * np.abs(Z0).max()
+    F = S.make_rhs(prob, 4)
+    U, st = lib.sg_solve(h1, _t(F), lib.solve_opts(lib.prec_opts(precision=lib.SG_F32), precond=lib.SG_PREC_HSC,
+                                                   tol=1e-8))
+    assert st.true_rel_res <= 1e-8 * 1.01 and st.iterations <= 10
+
+
 def test_wide_cluster_solver_parity(lib):
     """The 126-column top level of the 128x128, M=6 workload: more clusters
     than the on-chip solver keeps resident, so it takes the solver with the
