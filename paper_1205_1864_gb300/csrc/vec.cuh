@@ -77,17 +77,26 @@ __device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const Ou
 }
 
 
-// Exact FP32 -> FP64 conversion from the IEEE-754 layouts (sign kept,
-// exponent rebiased by 1023 - 127, mantissa shifted into the top bits), on the
-// integer pipe; subnormal inputs take the hardware conversion. The FP64 pipe
-// of this GPU is narrow, and the hardware conversion issues there.
+// Exact FP32 -> FP64 conversion from the IEEE-754 layouts, integer operations
+// only (the FP64 pipe of this GPU is narrow, and a hardware conversion issues
+// there): sign kept; a normal number's exponent rebiased by 1023 - 127 and its
+// 23-bit fraction shifted into the top of the 52-bit one; a subnormal m 2^-149
+// (m < 2^23) renormalised from its leading one at bit q: exponent q - 149 +
+// 1023, fraction m shifted so that bit q lands just above bit 51 (dropped);
+// zeros, infinities and NaNs keep their classes.
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-  if (e == 0u && m != 0u) return (double)f;
-  const unsigned ed = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
-  const unsigned hi = (u & 0x80000000u) | (ed << 20) | (m >> 3);
-  return __hiloint2double((int)hi, (int)(m << 29));
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned long long bits;
+  if (e == 0u && m != 0u) {
+    const unsigned q = 31u - (unsigned)__clz(m);
+    bits = sign | ((unsigned long long)(q + 874u) << 52) | (((unsigned long long)m << (52u - q)) & 0xfffffffffffffull);
+  } else {
+    const unsigned ed = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+    bits = sign | ((unsigned long long)ed << 52) | ((unsigned long long)m << 29);
+  }
+  return __longlong_as_double((long long)bits);
 }
 
 // v converted to TD; float -> double through f2d_bits.

@@ -388,3 +388,4 @@ def test_qoi_and_gradient_parity(lib):
     hk_ref = qoi.k_resolved_products(A, G, U, Lam)
     assert np.allclose(_np(hk), hk_ref, rtol=1e-12, atol=1e-12 * np.abs(hk_ref).max())
     assert np.allclose(_np(g), W @ hk_ref, rtol=1e-11, atol=1e-12 * np.abs(W @ hk_ref).max())
+
