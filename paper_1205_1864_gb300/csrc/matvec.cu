@@ -92,12 +92,23 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
       __syncthreads();
       gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
     }
+    // Y = beta Yin + alpha sum; the two forms the solver uses (Yin - sum, and
+    // the plain sum) without the multiplications (the FP64 pipe is the bound)
+    const bool sub = Yin && alpha == TAcc(-1) && beta == TAcc(1);
+    const bool plain = !Yin && alpha == TAcc(1);
 #pragma unroll
     for (int i = 0; i < MAXO; ++i) {
       const int l = lcol[i];
       if (l >= 0) {
-        TAcc v = alpha * acc[i];
-        if (Yin) v += beta * (TAcc)Yin[(size_t)r * ldyin + l];
+        TAcc v;
+        if (sub) {
+          v = (TAcc)Yin[(size_t)r * ldyin + l] - acc[i];
+        } else if (plain) {
+          v = acc[i];
+        } else {
+          v = alpha * acc[i];
+          if (Yin) v += beta * (TAcc)Yin[(size_t)r * ldyin + l];
+        }
         Y[(size_t)r * ldy + l] = (TO)v;
       }
     }
