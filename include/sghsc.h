@@ -211,9 +211,11 @@ int sg_inner_cluster(const sg_problem* h);
 /* sg_inner_path -- which solver a batched inner solve of w columns of element
  * type dtype takes on h: 0 the stand-alone kernels, 1 the cluster solver with
  * the whole multigrid hierarchy in shared memory (ceil(w/4) clusters of 8
- * blocks, all resident at once), 2 the cluster solver with the finest grid in
- * global memory and the coarse grids in shared memory (two blocks per SM, for
- * batches too wide for 1). h NULL or w <= 0: 0. */
+ * blocks, all resident at once), 3 the same with clusters of 16 blocks (half
+ * the rows per block; taken first when all ceil(w/4) of them are resident),
+ * 2 the cluster solver with the finest grid in global memory and the coarse
+ * grids in shared memory (two blocks per SM, for batches too wide for 1).
+ * h NULL or w <= 0: 0. */
 int sg_inner_path(const sg_problem* h, int w, int dtype);
 
 /* hsc_precond_apply -- Algorithm 1 (Sec. 4): Z = M_P R with the D_l^{-1}

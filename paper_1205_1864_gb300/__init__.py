@@ -121,7 +121,8 @@ class SGProblem:
 
     def inner_path(self, w: int, dtype: int = SG_F32) -> int:
         """Solver of a batched inner solve of w columns: 0 stand-alone kernels,
-        1 cluster solver on chip, 2 cluster solver with the finest grid in HBM."""
+        1 cluster solver on chip (clusters of 8), 3 the same with clusters of
+        16, 2 cluster solver with the finest grid in HBM."""
         return int(_lib.LIB.sg_inner_path(self.h, w, dtype))
 
     def close(self):

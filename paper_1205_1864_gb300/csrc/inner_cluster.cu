@@ -9,9 +9,11 @@
 // per-column stopping rule, status bits and iteration counts. What differs is
 // where the data lives:
 //
-// - A cluster of CLN = 8 CTAs owns 4 columns (one float4 per node). Every
-//   grid with at least CLN rows is split into row strips, strip c on CTA c;
-//   the smaller grids sit in CTA 0 alone. Each strip is stored with a ghost
+// - A cluster of CLN = 8 CTAs (or 16, where that many are resident: half the
+//   rows per CTA, for batches of at most 4 x the resident clusters) owns 4
+//   columns (one float4 per node). Every grid with at least as many rows as
+//   the cluster has CTAs is split into row strips, strip c on CTA c; the
+//   smaller grids sit in CTA 0 alone. Each strip is stored with a ghost
 //   row above and below and a ghost column left and right; ghosts outside the
 //   grid stay zero, so every stencil phase is branch-free.
 // - A phase that reads neighbours first copies the boundary rows it needs
@@ -20,7 +22,7 @@
 //   cluster barriers; the grids held by CTA 0 alone use block barriers.
 // - Per-column sums: the block's sum goes to a slot of its own (one slot per
 //   kind of sum, so a slot is never rewritten while another CTA may read it);
-//   after the cluster barrier every CTA adds the 8 slots in rank order, so all
+//   after the cluster barrier every CTA adds the slots in rank order, so all
 //   CTAs hold identical CG scalars and take the same loop decisions.
 // - On the finest grid each thread owns up to FINE_ITEMS nodes, one below the
 //   other (a stencil sweep rolls its 3 x 3 window down: 3 new loads per node),
@@ -354,15 +356,23 @@ struct CShared {
 };
 
 // After the cluster barrier that follows the slot writes: lanes 0..3 of warp 0
-// each add the 8 CTAs' slots in rank order and update their column (the
+// each add the CTAs' slots in rank order and update their column (the
 // scalar updates of the stand-alone finaliser: FP64 from the FP32 totals);
 // rank 0 reports status bits and iteration counts. Ends with a block barrier.
+// NCT: CTAs per cluster, 0 = read at run time (a kernel launched with either size).
+template <int NCT>
 __device__ void col_step(const cg::cluster_group& cl, CShared& S, int kind, const CArgs& a, int rank) {
   const int lane = threadIdx.x;
   if (lane < 4) {
     float4 tot = f4(0.f);
+    const int nct = NCT > 0 ? NCT : (int)cl.num_blocks();   // 8 or 16
+    for (int h = 0; h < nct; h += 8) {   // 8 remote loads in flight, then the sums in rank order
+      float4 v[8];
 #pragma unroll
-    for (int r = 0; r < CLN; ++r) tot = add4(tot, *cl.map_shared_rank(&S.slot[kind], r));
+      for (int r = 0; r < 8; ++r) v[r] = *cl.map_shared_rank(&S.slot[kind], h + r);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) tot = add4(tot, v[r]);
+    }
     const double s = (double)comp(tot, lane);
     const bool report = rank == 0;
     ColState c = S.cs[lane];
@@ -417,11 +427,12 @@ __device__ void col_step(const cg::cluster_group& cl, CShared& S, int kind, cons
 
 // Sum of the per-thread partials v over the cluster into the column scalars
 // (slot kind), then the column update: block sum, cluster barrier, col_step.
+template <int NCT>
 __device__ __forceinline__ void cluster_reduce(const cg::cluster_group& cl, CShared& S, int kind, const float4& v,
                                                const CArgs& a, int rank) {
   block_sum4(v, S.wred, &S.slot[kind]);
   cluster_sync_all();
-  col_step(cl, S, kind, a, rank);
+  col_step<NCT>(cl, S, kind, a, rank);
 }
 
 
@@ -580,12 +591,22 @@ __device__ void block_levels(const cg::cluster_group& cl, unsigned char* sm, con
     __syncthreads();
   }
   for (int g = G - 2; g >= gs; --g) level_up(cl, sm, L, g, G, 0, nu, om);
+  // each other CTA receives the rows of grid gs that the correction of its own
+  // rows y of grid gs - 1 reads: patch centres (y - 1) / 2, one row either side
   const CLevel& l = L[gs];
+  const CLevel& lf = L[gs - 1];
   float4* v = sp<float4>(sm, final_buf(l, gs == G - 1, nu));
-  const int W = l.nx + 2, m = l.ny * W;
-  for (int i = threadIdx.x; i < (CLN - 1) * m; i += blockDim.x) {
-    const int r = 1 + i / m, j = W + i % m;
-    cl.map_shared_rank(v, r)[j] = v[j];
+  // (at most K = rows / 2 + 4 rows per CTA; one flat loop over all of them)
+  const int W = l.nx + 2, nct = (int)cl.num_blocks(), K = lf.rows / 2 + 4;
+  for (int i = threadIdx.x; i < (nct - 1) * K * W; i += blockDim.x) {
+    const int r = 1 + i / (K * W), q = i % (K * W);
+    const Own of = own_rows(lf, r);
+    const int lo = max(0, ((of.r0 - 1) >> 1) - 1), hi = min(l.ny - 1, ((of.r0 + of.nr - 2) >> 1) + 1);
+    const int y = lo + q / W;
+    if (of.nr > 0 && y <= hi) {
+      const int j = (y + 1) * W + q % W;
+      cl.map_shared_rank(v, r)[j] = v[j];
+    }
   }
 }
 
@@ -628,7 +649,7 @@ __device__ __forceinline__ void fine_sweep(const float* __restrict__ ST, const f
 }
 
 // One column group's whole inner solve: gather, PCG iterations with the
-// V-cycle, scatter. Grid: CLN CTAs per 4 columns, clusters of CLN.
+// V-cycle, scatter. Grid: 8 or 16 CTAs per 4 columns, clusters of that size.
 template <typename TS, typename TD>
 __global__ void __launch_bounds__(CNT, 1)
     k_inner_cluster(const CPlan P, const TS* __restrict__ src, int lds, TD* __restrict__ dst, int ldd, int w,
@@ -638,7 +659,8 @@ __global__ void __launch_bounds__(CNT, 1)
   __shared__ CShared S;
   const cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int col0 = (int)(blockIdx.x / CLN) * 4;
+  const int cid = (int)(blockIdx.x / cl.num_blocks());   // column group (clusters of 8 or 16)
+  const int col0 = cid * 4;
   const int G = P.G, gs = P.gs, nu = a.nu;
   const float om = a.om;
 
@@ -695,8 +717,8 @@ __global__ void __launch_bounds__(CNT, 1)
   float4 r[FINE_ITEMS], po[FINE_ITEMS];   // the solution accumulates in a.xs
   float d0[FINE_ITEMS];
   // this CTA's nodes of the cluster's solution and A p scratch (recomputed where used)
-#define XG (a.xs + (size_t)(blockIdx.x / CLN) * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
-#define QG (a.qs + (size_t)(blockIdx.x / CLN) * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
+#define XG (a.xs + (size_t)cid * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
+#define QG (a.qs + (size_t)cid * P.L[0].nx * P.L[0].ny + (size_t)o0.r0 * nx0)
 #define FI(k) ((fy0 + (k)) * nx0 + fx)
   unsigned zo = L0.x, so = L0.y;
   float4 part = f4(0.f);
@@ -720,7 +742,7 @@ __global__ void __launch_bounds__(CNT, 1)
     }
   }
   copy_async_wait();
-  cluster_reduce(cl, S, RK_INIT, part, a, rank);
+  cluster_reduce<0>(cl, S, RK_INIT, part, a, rank);
 
   const int cap = (a.fixed > 0 ? a.fixed : a.maxit) + 1;
   for (int it = 0; it < cap && S.active; ++it) {
@@ -769,7 +791,7 @@ __global__ void __launch_bounds__(CNT, 1)
         put(cl, sm, L0, so, rank, o0, fy0 + k, fx, v);
         dot4(part, r[k], v);
       });
-      if (s == nu) cluster_reduce(cl, S, RK_RHO, part, a, rank);
+      if (s == nu) cluster_reduce<0>(cl, S, RK_RHO, part, a, rank);
       else cluster_sync_all();
       const unsigned t = zo; zo = so; so = t;
     }
@@ -792,7 +814,7 @@ __global__ void __launch_bounds__(CNT, 1)
         qg[FI(k)] = qv[k];
       });
     }
-    cluster_reduce(cl, S, RK_PQ, part, a, rank);
+    cluster_reduce<0>(cl, S, RK_PQ, part, a, rank);
     // ---- x += alpha p, r -= alpha q on the unfinished columns; r . r; the
     // next V-cycle's first sweep om D^-1 r
     {
@@ -827,7 +849,7 @@ __global__ void __launch_bounds__(CNT, 1)
         put(cl, sm, L0, zo, rank, o0, fy0 + k, fx, make_float4(dd * r[k].x, dd * r[k].y, dd * r[k].z, dd * r[k].w));
       }
     }
-    cluster_reduce(cl, S, RK_RR, part, a, rank);
+    cluster_reduce<0>(cl, S, RK_RR, part, a, rank);
   }
 
   // ---- the solution into the output block
@@ -974,7 +996,7 @@ __global__ void __launch_bounds__(CNT, 2)
     }
   }
   copy_async_wait();
-  cluster_reduce(cl, S, RK_INIT, part, a, rank);
+  cluster_reduce<CLN>(cl, S, RK_INIT, part, a, rank);
 
   const int cap = (a.fixed > 0 ? a.fixed : a.maxit) + 1;
   for (int it = 0; it < cap && S.active; ++it) {
@@ -1023,7 +1045,7 @@ __global__ void __launch_bounds__(CNT, 2)
         Sb[c] = v;
         dot4(part, r, v);
       });
-      if (s == nu) cluster_reduce(cl, S, RK_RHO, part, a, rank);
+      if (s == nu) cluster_reduce<CLN>(cl, S, RK_RHO, part, a, rank);
       else cluster_sync_all();
       float4* t = Z; Z = Sb; Sb = t;
     }
@@ -1044,7 +1066,7 @@ __global__ void __launch_bounds__(CNT, 2)
         dot4(part, p, q);
       });
     }
-    cluster_reduce(cl, S, RK_PQ, part, a, rank);
+    cluster_reduce<CLN>(cl, S, RK_PQ, part, a, rank);
     // ---- x += alpha p, r -= alpha q on the unfinished columns; r . r; the
     // next V-cycle's first sweep om D^-1 r
     {
@@ -1074,7 +1096,7 @@ __global__ void __launch_bounds__(CNT, 2)
         Z[FC(k)] = make_float4(dd * r.x, dd * r.y, dd * r.z, dd * r.w);
       }
     }
-    cluster_reduce(cl, S, RK_RR, part, a, rank);
+    cluster_reduce<CLN>(cl, S, RK_RR, part, a, rank);
   }
 
   // ---- the solution into the output block
@@ -1101,29 +1123,45 @@ __global__ void __launch_bounds__(CNT, 2)
 
 // Host-side state of the cluster solvers (h->cl_plan).
 struct ClusterSolver {
-  CPlan P{};                  // k_inner_cluster: the whole hierarchy on chip
+  CPlan P{};                  // k_inner_cluster, clusters of 8: the whole hierarchy on chip
+  CPlan P16{};                // k_inner_cluster, clusters of 16 (half the rows per CTA)
   CPlan Pw{};                 // k_inner_cluster_wide: the coarse grids on chip
-  int maxcl = 0, maxclw = 0;  // clusters resident at once
+  int maxcl = 0, maxcl16 = 0, maxclw = 0;   // clusters resident at once
+  int xcap = 0;               // clusters the x / A p scratch holds
   float4* xs = nullptr;       // k_inner_cluster: x and A p per cluster
   float4* wzs = nullptr;      // k_inner_cluster_wide: padded finest-grid iterates
   float4* wvecs = nullptr;    // k_inner_cluster_wide: r, p, x, A p
 };
 
-// Clusters of kernel kern resident at once with `bytes` of dynamic shared
-// memory (0 if it cannot run).
+// Raise kern's dynamic shared-memory limit to at least `bytes`. The limit
+// belongs to the function, not to a problem: it is never lowered, so the plan
+// of one problem does not invalidate the launches of another.
 template <typename K>
-static int max_clusters(K kern, unsigned bytes, int optin) {
+static bool allow_smem(K kern, unsigned bytes) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return false;
+  if (fa.maxDynamicSharedSizeBytes >= (int)bytes) return true;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
+
+// Clusters of `cln` CTAs of kernel kern resident at once with `bytes` of
+// dynamic shared memory (0 if it cannot run). Clusters of more than 8 CTAs
+// are a non-portable size the kernel has to opt in to.
+template <typename K>
+static int max_clusters(K kern, unsigned bytes, int optin, int cln) {
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 0;
   if ((long long)bytes + (long long)fa.sharedSizeBytes > optin) return 0;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return 0;
+  if (!allow_smem(kern, bytes)) return 0;
+  if (cln > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CLN);
+  cfg.gridDim = dim3(cln);
   cfg.blockDim = dim3(CNT);
   cfg.dynamicSmemBytes = bytes;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CLN;
+  at[0].val.clusterDim.x = cln;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -1133,95 +1171,103 @@ static int max_clusters(K kern, unsigned bytes, int optin) {
   return nclusters;
 }
 
-// Build the shared-memory plans of the hierarchy and decide which cluster
-// solver can run it (h->cl_plan stays null when neither can). Any CUDA error
-// on this path only disables the cluster solvers; it is cleared.
-int cluster_setup(sg_problem* h) {
-  const char* ev = getenv("SGHSC_NO_CLUSTER");
-  if (ev && ev[0] == '1') return SG_OK;
+// The shared-memory plan of the hierarchy for clusters of `cln` CTAs: grids
+// with at least cln rows in row strips of ceil(ny / cln) rows, the smaller
+// ones on CTA 0 alone; with `wide` the finest grid takes no shared memory.
+// False when the hierarchy does not fit the scheme (the caller then leaves
+// that solver out).
+static bool build_plan(const sg_problem* h, int cln, bool wide, CPlan& P) {
   const int G = (int)h->grids.size();
-  if (G < 2 || G > CMAXG) return SG_OK;
-  CPlan P{}, Pw{};
-  unsigned off = 0, offw = 0;
-  auto take = [](unsigned& o, size_t bytes) {
-    const unsigned r = o;
-    o += (unsigned)((bytes + 15) & ~(size_t)15);
+  if (G < 2 || G > CMAXG) return false;
+  P = CPlan{};
+  unsigned off = 0;
+  auto take = [&](size_t bytes) {
+    const unsigned r = off;
+    off += (unsigned)((bytes + 15) & ~(size_t)15);
     return r;
   };
   int gs = G;
   for (int g = 0; g < G; ++g) {
     const GridLevel& gr = h->grids[g];
     CLevel& l = P.L[g];
-    if (gr.nx != gr.ny || !gr.st32 || !gr.dinv32) return SG_OK;
+    if (gr.nx != gr.ny || !gr.st32 || !gr.dinv32) return false;
     l.nx = gr.nx;
     l.ny = gr.ny;
-    l.single = gr.ny < CLN;
-    l.rows = l.single ? gr.ny : (gr.ny + CLN - 1) / CLN;
+    l.single = gr.ny < cln;
+    l.rows = l.single ? gr.ny : (gr.ny + cln - 1) / cln;
     if (l.single) {
       if (gs == G) gs = g;
-    } else {
-      if (gs < G) return SG_OK;                 // strips below a grid held by CTA 0
+    } else if (gs < G) {
+      return false;   // strips below a grid held by CTA 0
     }
     const size_t vec = (size_t)(l.rows + 2) * (l.nx + 2) * 16;
     const size_t stb = (size_t)l.rows * l.nx * 9 * sizeof(float);
     const size_t dib = (size_t)(l.rows + 2) * (l.nx + 2) * sizeof(float);
-    l.b = g > 0 ? take(off, vec) : 0;
-    l.x = take(off, vec);
-    l.y = take(off, vec);
-    l.st = take(off, stb);
-    l.di = g > 0 ? take(off, dib) : 0;
     l.gst = gr.st32;
     l.gdi = gr.dinv32;
-    CLevel& lw = Pw.L[g];
-    lw = l;
-    if (g == 0) {
-      lw.b = lw.x = lw.y = lw.st = lw.di = 0;   // the finest grid lives in global memory
-    } else {
-      lw.b = take(offw, vec);
-      lw.x = take(offw, vec);
-      lw.y = take(offw, vec);
-      lw.st = take(offw, stb);
-      lw.di = take(offw, dib);
-    }
+    if (g == 0 && wide) continue;   // the finest grid lives in global memory
+    l.b = g > 0 ? take(vec) : 0;
+    l.x = take(vec);
+    l.y = take(vec);
+    l.st = take(stb);
+    l.di = g > 0 ? take(dib) : 0;
   }
-  if (gs == 0 || gs == G) return SG_OK;
-  if (P.L[0].nx > CNT) return SG_OK;
+  if (gs == 0 || gs == G) return false;
+  if (P.L[0].nx > CNT) return false;
   P.fine_h = (P.L[0].rows + CNT / P.L[0].nx - 1) / (CNT / P.L[0].nx);   // finest-grid rows per thread
-  if (P.fine_h > FINE_ITEMS) return SG_OK;
+  if (P.fine_h > FINE_ITEMS) return false;
   for (int g = 0; g + 1 < gs; ++g)   // strips of consecutive grids line up (row 2Y+1 over row Y)
-    if (P.L[g].rows != 2 * P.L[g + 1].rows || P.L[g + 1].nx != (P.L[g].nx - 1) / 2) return SG_OK;
-  P.G = Pw.G = G;
-  P.gs = Pw.gs = gs;
+    if (P.L[g].rows != 2 * P.L[g + 1].rows || P.L[g + 1].nx != (P.L[g].nx - 1) / 2) return false;
+  P.G = G;
+  P.gs = gs;
   P.bytes = off;
-  Pw.bytes = offw;
-  Pw.fine_h = P.fine_h;
+  return true;
+}
+
+// Build the shared-memory plans of the hierarchy and decide which cluster
+// solvers can run it (h->cl_plan stays null when none can). Any CUDA error
+// on this path only disables the cluster solvers; it is cleared.
+int cluster_setup(sg_problem* h) {
+  const char* ev = getenv("SGHSC_NO_CLUSTER");
+  if (ev && ev[0] == '1') return SG_OK;
+  const char* ev16 = getenv("SGHSC_NO_CLUSTER16");
+  CPlan P{}, P16{}, Pw{};
+  if (!build_plan(h, CLN, false, P) || !build_plan(h, CLN, true, Pw)) return SG_OK;
+  const bool try16 = !(ev16 && ev16[0] == '1') && build_plan(h, 2 * CLN, false, P16);
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
     cudaGetLastError();
     return SG_OK;
   }
   auto min4 = [](int a, int b, int c, int d) { return std::min(std::min(a, b), std::min(c, d)); };
-  const int maxcl = min4(max_clusters(k_inner_cluster<double, float>, off, optin),
-                         max_clusters(k_inner_cluster<float, float>, off, optin),
-                         max_clusters(k_inner_cluster<double, double>, off, optin),
-                         max_clusters(k_inner_cluster<float, double>, off, optin));
-  const int maxclw = min4(max_clusters(k_inner_cluster_wide<double, float>, offw, optin),
-                          max_clusters(k_inner_cluster_wide<float, float>, offw, optin),
-                          max_clusters(k_inner_cluster_wide<double, double>, offw, optin),
-                          max_clusters(k_inner_cluster_wide<float, double>, offw, optin));
+  auto onchip = [&](const CPlan& Q, int cln) {
+    return min4(max_clusters(k_inner_cluster<double, float>, Q.bytes, optin, cln),
+                max_clusters(k_inner_cluster<float, float>, Q.bytes, optin, cln),
+                max_clusters(k_inner_cluster<double, double>, Q.bytes, optin, cln),
+                max_clusters(k_inner_cluster<float, double>, Q.bytes, optin, cln));
+  };
+  const int maxcl = onchip(P, CLN);
+  const int maxcl16 = try16 ? onchip(P16, 2 * CLN) : 0;
+  const int maxclw = min4(max_clusters(k_inner_cluster_wide<double, float>, Pw.bytes, optin, CLN),
+                          max_clusters(k_inner_cluster_wide<float, float>, Pw.bytes, optin, CLN),
+                          max_clusters(k_inner_cluster_wide<double, double>, Pw.bytes, optin, CLN),
+                          max_clusters(k_inner_cluster_wide<float, double>, Pw.bytes, optin, CLN));
   cudaGetLastError();
-  if (maxcl < 1 && maxclw < 1) return SG_OK;
+  if (maxcl < 1 && maxclw < 1 && maxcl16 < 1) return SG_OK;
   ClusterSolver* cs = new ClusterSolver();
   cs->P = P;
+  cs->P16 = P16;
   cs->Pw = Pw;
   cs->maxcl = std::max(maxcl, 0);
+  cs->maxcl16 = std::max(maxcl16, 0);
   cs->maxclw = std::max(maxclw, 0);
-  P.maxcl = cs->maxcl;
   cs->P.maxcl = cs->maxcl;
+  cs->P16.maxcl = cs->maxcl16;
   cs->Pw.maxcl = cs->maxclw;
+  cs->xcap = std::max(cs->maxcl, cs->maxcl16);
   h->cl_plan = cs;   // owned from here on (cluster_free)
   const size_t n = (size_t)P.L[0].nx * P.L[0].ny, padn = (size_t)(P.L[0].ny + 2) * (P.L[0].nx + 2);
-  if (cs->maxcl > 0) SG_TRY_CUDA(cudaMalloc((void**)&cs->xs, 2 * (size_t)cs->maxcl * n * sizeof(float4)));
+  if (cs->xcap > 0) SG_TRY_CUDA(cudaMalloc((void**)&cs->xs, 2 * (size_t)cs->xcap * n * sizeof(float4)));
   if (cs->maxclw > 0) {
     SG_TRY_CUDA(cudaMalloc((void**)&cs->wzs, 2 * (size_t)cs->maxclw * padn * sizeof(float4)));
     SG_TRY_CUDA(cudaMemset(cs->wzs, 0, 2 * (size_t)cs->maxclw * padn * sizeof(float4)));   // zero borders
@@ -1240,14 +1286,17 @@ void cluster_free(sg_problem* h) {
   h->cl_plan = nullptr;
 }
 
-// Which cluster solver an FP32 batch of w columns takes: 1 = the on-chip one
-// when all its clusters are resident at once (a second wave would double the
-// latency-bound solve), 2 = the wide one (finest grid in global memory) when
-// its clusters are, 0 = neither (the stand-alone kernels).
+// Which cluster solver an FP32 batch of w columns takes: 3 = the on-chip one
+// with clusters of 16 CTAs when all of them are resident at once (half the
+// rows per CTA: the phases of the latency-bound solve are shorter), 1 = the
+// on-chip one with clusters of 8 when all of them are (a second wave would
+// double the solve), 2 = the wide one (finest grid in global memory) when its
+// clusters are, 0 = none of them (the stand-alone kernels).
 static int cluster_path(const sg_problem* h, int dtype, int w) {
   const ClusterSolver* cs = (const ClusterSolver*)h->cl_plan;
   if (dtype != SG_F32 || !cs) return 0;
   const int ncl = ceil_div(w, 4);
+  if (ncl <= cs->maxcl16) return 3;
   if (ncl <= cs->maxcl) return 1;
   if (ncl <= cs->maxclw) return 2;
   return 0;
@@ -1270,7 +1319,8 @@ int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void
                         const sg_prec_opts& o, cudaStream_t s) {
   const ClusterSolver& cs = *(const ClusterSolver*)h->cl_plan;
   const int path = cluster_path(h, SG_F32, w);
-  const CPlan& P = path == 2 ? cs.Pw : cs.P;
+  const CPlan& P = path == 2 ? cs.Pw : path == 3 ? cs.P16 : cs.P;
+  const int cln = path == 3 ? 2 * CLN : CLN;
   CArgs a;
   a.om = (float)o.omega;
   a.nu = o.nu;
@@ -1281,18 +1331,18 @@ int inner_solve_cluster(sg_problem* h, const void* src, int lds, int src_t, void
   a.iacc = h->iacc;
   a.iters = h->iw32.iters && h->iw32.wcap >= w ? h->iw32.iters : nullptr;
   a.xs = cs.xs;
-  a.qs = cs.xs ? cs.xs + (size_t)cs.maxcl * P.L[0].nx * P.L[0].ny : nullptr;
+  a.qs = cs.xs ? cs.xs + (size_t)cs.xcap * P.L[0].nx * P.L[0].ny : nullptr;
   WideArgs wa;
   wa.zs = cs.wzs;
   wa.vecs = cs.wvecs;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(ceil_div(w, 4) * CLN));
+  cfg.gridDim = dim3((unsigned)(ceil_div(w, 4) * cln));
   cfg.blockDim = dim3(CNT);
   cfg.dynamicSmemBytes = P.bytes;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CLN;
+  at[0].val.clusterDim.x = cln;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;

@@ -73,6 +73,41 @@ def test_cluster_fixed_iterations_parity(lib, ne, w, nu, omega):
     assert np.all(X[:, 2] == 0.0)
 
 
+@pytest.mark.parametrize("ne,w", [(32, 5), (64, 11), (128, 1), (128, 21)])
+def test_cluster16_fixed_iterations_parity(lib, ne, w):
+    """Clusters of 16 CTAs (half the rows of every strip grid per CTA, one
+    more grid on CTA 0 alone) against the column-wise oracle, and against
+    clusters of 8 within FP32 rounding (the cluster sums add 16 block sums
+    instead of 8)."""
+    import torch
+    prob, A, G, off = problem(ne, 2, 1)
+    h16 = lib.SGProblem.from_inputs(prob, 1)
+    if h16.inner_path(w) != 3:
+        pytest.skip("clusters of 16 CTAs are not resident on this device")
+    os.environ["SGHSC_NO_CLUSTER16"] = "1"
+    try:
+        h8 = lib.SGProblem.from_inputs(prob, 1)
+    finally:
+        del os.environ["SGHSC_NO_CLUSTER16"]
+    assert h8.inner_path(w) == 1
+    lv = gmg.hierarchy(A[0], ne)
+    B = S.random_block(prob.n, w, seed=51 + ne + w).astype(np.float32).astype(np.float64)
+    if w > 2:
+        B[:, 2] = 0.0
+    o = lib.prec_opts(inner_fixed_iters=3)
+    X16, it16 = lib.sg_inner_solve(h16, _t(B, torch.float32), o)
+    X8, it8 = lib.sg_inner_solve(h8, _t(B, torch.float32), o)
+    ref, it_ref = krylov.pcg_columns(lambda v: A[0] @ v, B, lambda r: gmg.vcycle(lv, r), tol=0.0, maxit=3,
+                                     fixed_iters=3)
+    assert list(it16) == list(it_ref) and list(it8) == list(it_ref)
+    X16, X8 = _np(X16), _np(X8)
+    scale = np.abs(ref).max(axis=0, keepdims=True) + 1e-300
+    assert np.all(np.abs(X16 - ref) <= 1e-4 * scale)
+    assert np.all(np.abs(X16 - X8) <= 1e-5 * scale)
+    if w > 2:
+        assert np.all(X16[:, 2] == 0.0)
+
+
 @pytest.mark.parametrize("tol", [1e-2, 1e-4])
 def test_cluster_tolerance_matches_stand_alone(lib, tol):
     """Degree-level widths of the 128x128, M=6 workload: every column reaches
