@@ -705,22 +705,6 @@ struct CoarseGrids {
   const void* dinv[MAX_LEVELS];
 };
 
-// Asynchronous global -> shared copy of one element (cp.async, completed by
-// cp_async_wait_all); all of a block's copies are in flight together.
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(T) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
 template <typename T>
 __device__ __forceinline__ void stage_async(T* __restrict__ dst, const T* __restrict__ src, int count) {
   for (int idx = threadIdx.x; idx < count; idx += blockDim.x) cp_async_elem(dst + idx, src + idx);

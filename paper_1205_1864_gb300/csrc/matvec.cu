@@ -31,6 +31,42 @@ __device__ __forceinline__ void output_columns(const int* __restrict__ eperm, in
   }
 }
 
+// Stage the chunk of nzc nonzeros starting at cs: the neighbour rows X(c, :)
+// (widened to TAcc) and the M+1 values of each nonzero. Same-type rows and
+// the values go by asynchronous copies (all in flight at once); a widened row
+// by batches of 4 loads in flight before the conversions. The caller waits
+// (cp_async_wait_all) and synchronises.
+template <typename TIn, typename TAcc>
+__device__ __forceinline__ void stage_chunk(int cs, int nzc, int M1, const int* __restrict__ colidx,
+                                            const TAcc* __restrict__ vals, const TIn* __restrict__ X, int ldx,
+                                            int wx, TAcc* Xs, TAcc* Vs) {
+  const int cnt = nzc * wx;
+  if constexpr (sizeof(TIn) == sizeof(TAcc)) {
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      const int e = idx / wx, j = idx - e * wx;
+      cp_async_elem(Xs + idx, X + (size_t)colidx[cs + e] * ldx + j);
+    }
+  } else {
+    for (int base = threadIdx.x; base < cnt; base += 4 * blockDim.x) {
+      TIn v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < cnt) {
+          const int e = idx / wx, j = idx - e * wx;
+          v[u] = X[(size_t)colidx[cs + e] * ldx + j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < cnt) Xs[idx] = widen<TAcc>(v[u]);
+      }
+    }
+  }
+  for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) cp_async_elem(Vs + idx, vals + (size_t)cs * M1 + idx);
+}
+
 // Accumulate the gather form for this thread's outputs over one staged chunk.
 template <typename TAcc, int MAXO, bool DIAG>
 __device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __restrict__ Vs,
@@ -84,11 +120,8 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
     for (int cs = rb; cs < re; cs += chunk) {
       const int nzc = min(chunk, re - cs);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nzc * wx; idx += blockDim.x) {
-        const int e = idx / wx, j = idx - e * wx;
-        Xs[idx] = widen<TAcc>(X[(size_t)colidx[cs + e] * ldx + j]);
-      }
-      for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
+      stage_chunk<TIn, TAcc>(cs, nzc, M1, colidx, vals, X, ldx, wx, Xs, Vs);
+      cp_async_wait_all();
       __syncthreads();
       gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
     }
@@ -145,11 +178,8 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
     for (int cs = rb; cs < re; cs += chunk) {
       const int nzc = min(chunk, re - cs);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nzc * P; idx += blockDim.x) {
-        const int e = idx / P, j = idx - e * P;
-        Xs[idx] = z[(size_t)colidx[cs + e] * P + j];
-      }
-      for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
+      stage_chunk<double, double>(cs, nzc, M1, colidx, vals, z, P, P, Xs, Vs);
+      cp_async_wait_all();
       __syncthreads();
       gather_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
     }

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "sghsc_internal.cuh"
+#include "vec.cuh"
 
 namespace sghsc {
 
@@ -58,9 +59,10 @@ __global__ void __launch_bounds__(256) k_grad(int n, int P, int M1, const int* _
       __syncthreads();
       for (int idx = threadIdx.x; idx < nzc * P; idx += blockDim.x) {
         const int e = idx / P, j = idx - e * P;
-        Xs[idx] = U[(size_t)colidx[cs + e] * P + j];
+        cp_async_elem(Xs + idx, U + (size_t)colidx[cs + e] * P + j);
       }
-      for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) Vs[idx] = vals[(size_t)cs * M1 + idx];
+      for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) cp_async_elem(Vs + idx, vals + (size_t)cs * M1 + idx);
+      cp_async_wait_all();
       __syncthreads();
       for (int l = threadIdx.x; l < P; l += blockDim.x) {
         const double lam = Lam[(size_t)r * P + l];

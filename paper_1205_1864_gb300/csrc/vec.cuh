@@ -106,6 +106,23 @@ __device__ __forceinline__ TD widen(TS v) {
   else return (TD)v;
 }
 
+// Asynchronous global -> shared copy of one 4- or 8-byte element (cp.async,
+// completed by cp_async_wait_all); all of a block's copies are in flight
+// together instead of one load latency per element.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 int vec_grid(long long N);
 
 // The outer CG step q = A p_new with p_new = z + beta p_old staged on the fly
