@@ -147,6 +147,7 @@ def run_ours(args, rank, world, dev):
     p = cfg["p"]
     h = L.SGProblem.from_inputs(prob, p)
     tuned = L.sg_autotune(h)   # block sizes of the SG product (FP64, FP32), part of setup
+    forms = L.sg_autotune_forms(h)   # pair (1) or gather (0) form: FP64, FP32, outer
     setup_s = time.time() - t0
     n, P, M, nnz = h.n, h.P, h.M, h.nnz
     alpha, off = h.chaos_table()
@@ -229,7 +230,8 @@ def run_ours(args, rank, world, dev):
     if args.profile:
         ts, st_h, launches = timed_solves(hsc_opts, args.steps, args.warmup)
         return {"profile": "solve", "workload": cfg["name"], "ms": float(np.mean(ts)), "iterations": st_h.iterations,
-                "launches_per_solve": int(launches / max(args.steps, 1))}
+                "launches_per_solve": int(launches / max(args.steps, 1)), "autotuned_threads_f64_f32": list(tuned),
+                "autotuned_pair_form_f64_f32_outer": list(forms)}
     # headline: mixed HSC-PCG
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
         ts, st_h, _ = timed_solves(hsc_opts, args.steps, args.warmup)
@@ -317,6 +319,7 @@ def run_ours(args, rank, world, dev):
                    "unknowns": n * P, "sigma": cfg["sigma"], "corr_len": cfg["corr_len"], "inner_tol": 1e-2,
                    "tol": 1e-8, "l2": "flushed between timed steps (256 MiB write, outside the events)",
                    "autotuned_threads_f64_f32": list(tuned),
+                   "autotuned_pair_form_f64_f32_outer": list(forms),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "hsc": {"ms": ms, "iterations": st_h.iterations, "true_rel_res": st_true.true_rel_res,
                 "kappa_est": st_h.kappa_est, "inner_iters_total": st_h.inner_iters_total,

@@ -240,12 +240,19 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
 
 /* sg_autotune -- time the candidate block sizes (64 to 1024 threads) of the
  * full SG product in FP64 and FP32, and separately of the outer solver's fused
- * product (SG product + CG update + p.q), on this problem and keep the fastest
- * for all later calls. Allocates two temporary n x P blocks and, if absent,
+ * product (SG product + CG update + p.q), each in two forms, on this problem
+ * and keep the fastest for all later calls. The forms: the pair form sums
+ * each distinct (k, j) of the couplings once per row and keeps those sums in
+ * shared memory (fewer multiply-adds); the gather form sums per coupling (no
+ * extra shared memory). Allocates two temporary n x P blocks and, if absent,
  * the outer solve buffers; invalidates the handle's cached solve graphs. */
 int sg_autotune(sg_problem* h, void* stream);
 /* Block sizes chosen by sg_autotune (0: not tuned, the built-in choice). */
 int sg_autotune_result(const sg_problem* h, int* threads_f64, int* threads_f32);
+/* Forms chosen by sg_autotune: 1 the pair form, 0 the gather form, for the
+ * full SG product in FP64 and FP32 and for the outer fused product (all 1
+ * before tuning). Any pointer may be NULL. */
+int sg_autotune_forms(const sg_problem* h, int* pairs_f64, int* pairs_f32, int* pairs_outer);
 
 /* Batched solves of many independent systems (uneven n, M, p): one graph
  * launch runs every system's whole solve (its outer flexible CG and nested

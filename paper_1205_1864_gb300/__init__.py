@@ -231,6 +231,14 @@ def sg_autotune(h: SGProblem):
     return a.value, b.value
 
 
+def sg_autotune_forms(h: SGProblem):
+    """Forms sg_autotune chose: ``(pairs_f64, pairs_f32, pairs_outer)``, 1 the
+    pair form, 0 the gather form."""
+    a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
+    check(_lib.LIB.sg_autotune_forms(h.h, C.byref(a), C.byref(b), C.byref(c)), "sg_autotune_forms")
+    return a.value, b.value, c.value
+
+
 class SGBatch:
     """Many independent SG systems solved by one graph launch (``sg_batch_*``).
     The problems stay owned by the caller and must outlive the batch."""

@@ -72,6 +72,7 @@ def _load():
         "sg_qoi": (i, [vp, vp, vp, vp, vp]),
         "sg_autotune": (i, [vp, vp]),
         "sg_autotune_result": (i, [vp, P(i), P(i)]),
+        "sg_autotune_forms": (i, [vp, P(i), P(i), P(i)]),
         "sg_batch_create": (i, [i, P(vp), P(vp)]),
         "sg_batch_solve": (i, [vp, P(vp), P(vp), P(sg_solve_opts), P(sg_solve_stats), vp]),
         "sg_batch_destroy": (None, [vp]),
@@ -101,6 +102,6 @@ def check(status: int, where: str):
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
     return ["sg_setup", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
-            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result",
+            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
             "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",
             "sg_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

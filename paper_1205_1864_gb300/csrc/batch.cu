@@ -112,7 +112,8 @@ static int batch_solve(sg_batch* b, const double* const* F, double* const* U, co
 
 // ---------------------------------------------------------------- autotune ---
 
-// Time the full SG product with each candidate block size and keep the fastest.
+// Time the full SG product with each candidate block size, in pair and in
+// gather form, and keep the fastest.
 static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
   const size_t es = dtype == SG_F64 ? 8 : 4;
   const size_t bytes = (size_t)h->n * h->P * es;
@@ -128,12 +129,14 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int cands[] = {64, 128, 256, 512, 1024};
-  int best = 0;
+  int best = 0, best_pairs = 1;
   float best_ms = 1e30f;
   int r = SG_OK;
-  for (int c : cands) {
+  for (int cand = 0; cand < 10 && r == SG_OK; ++cand) {
+    const int c = cands[cand % 5], pairs = cand < 5 ? 1 : 0;
     if ((h->P + c - 1) / c > 8) continue;   // at most 8 outputs per thread
     h->k1_threads[dtype] = c;
+    h->k1_pairs[dtype] = pairs;
     r = launch_block_matvec(h, dtype, dtype, dtype, dtype, X, h->P, h->P, h->all, true, nullptr, 0, 1.0, 0.0, Y,
                             h->P, s);
     if (r != SG_OK) break;
@@ -148,9 +151,11 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
     if (r == SG_OK && ms < best_ms) {
       best_ms = ms;
       best = c;
+      best_pairs = pairs;
     }
   }
   h->k1_threads[dtype] = best;
+  h->k1_pairs[dtype] = best_pairs;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(X);
@@ -159,8 +164,8 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
 }
 
 // Time the fused outer product (K1 with the CG update and p . q) with each
-// candidate block size on the handle's own outer buffers and keep the
-// fastest. It runs on whatever the buffers hold; every solve stages its
+// candidate block size, in pair and in gather form, on the handle's own outer
+// buffers and keep the fastest. It runs on whatever the buffers hold; every solve stages its
 // right-hand side and resets the outer state before it starts.
 static int autotune_outer(sg_problem* h, cudaStream_t s) {
   SG_TRY(ensure_outer(h));
@@ -171,13 +176,15 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int cands[] = {64, 128, 256, 512, 1024};
-  int best = 0;
+  int best = 0, best_pairs = 1;
   float best_ms = 1e30f;
   int r = SG_OK;
-  for (int c : cands) {
+  for (int cand = 0; cand < 10 && r == SG_OK; ++cand) {
+    const int c = cands[cand % 5], pairs = cand < 5 ? 1 : 0;
     const int maxo = (h->P + c - 1) / c;
     if (maxo > 8 || (c > 256 && maxo > 4)) continue;
     h->outer_threads = c;
+    h->outer_pairs = pairs;
     r = launch_outer_matvec(h, a, s);
     if (r != SG_OK) break;
     cudaEventRecord(e0, s);
@@ -189,9 +196,11 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
     if (r == SG_OK && ms < best_ms) {
       best_ms = ms;
       best = c;
+      best_pairs = pairs;
     }
   }
   h->outer_threads = best;
+  h->outer_pairs = best_pairs;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return r;
@@ -213,6 +222,17 @@ int sg_autotune(sg_problem* h, void* stream) {
   SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
   SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
   SG_TRY(autotune_outer(h, (cudaStream_t)stream));
+  return SG_OK;
+}
+
+int sg_autotune_forms(const sg_problem* h, int* pairs_f64, int* pairs_f32, int* pairs_outer) {
+  if (!h) {
+    set_error("sg_autotune_forms: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (pairs_f64) *pairs_f64 = h->k1_pairs[SG_F64];
+  if (pairs_f32) *pairs_f32 = h->k1_pairs[SG_F32];
+  if (pairs_outer) *pairs_outer = h->outer_pairs;
   return SG_OK;
 }
 

@@ -11,7 +11,9 @@
 //   Y(r,l) = sum_c a_0(r,c) U(c,l) + sum_{(k,j): alpha_j = alpha_l +- e_k}
 //            (G_k)_{lj} sum_c a_k(r,c) U(c,j).
 // Per nonzero that is P + n_m multiply-adds (n_m the off-diagonal G entries),
-// the smallest count of the contraction orders.
+// the smallest count of the contraction orders; the full product sums each
+// distinct (k, j) once (pair form below), P + npair per nonzero plus n_m per
+// row.
 #include <algorithm>
 
 #include "sghsc_internal.cuh"
@@ -67,7 +69,8 @@ __device__ __forceinline__ void stage_chunk(int cs, int nzc, int M1, const int* 
   for (int idx = threadIdx.x; idx < nzc * M1; idx += blockDim.x) cp_async_elem(Vs + idx, vals + (size_t)cs * M1 + idx);
 }
 
-// Accumulate the gather form for this thread's outputs over one staged chunk.
+// Accumulate the gather form for this thread's outputs over one staged chunk
+// (a level product names every pair (k, j) once: this is its form).
 template <typename TAcc, int MAXO, bool DIAG>
 __device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __restrict__ Vs,
                                              const TAcc* __restrict__ Xs, int wx, const int* __restrict__ eptr,
@@ -94,6 +97,55 @@ __device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __rest
   }
 }
 
+// The full SG product in pair form (DIAG): per staged chunk, the diagonal
+// term of this thread's outputs into acc, and for every distinct pair
+// q = (k, j) of the couplings s_q = sum_c a_k(r,c) U(c,j) into Ss (the first
+// chunk of a row stores, later ones add). A pair serves every coupling that
+// names it (an input column j coupled to two outputs in direction k is summed
+// once), so this does 9 (P + npair) multiply-adds per 9-point row instead of
+// 9 (P + n_m); consecutive pairs share k and take consecutive j. It needs
+// npair more values of shared memory, which can cost resident blocks: the
+// autotuner times both forms.
+template <typename TAcc, int MAXO>
+__device__ __forceinline__ void pair_chunk(int nzc, int M1, const TAcc* __restrict__ Vs, const TAcc* __restrict__ Xs,
+                                           int wx, int npair, const int* __restrict__ pk,
+                                           const int* __restrict__ pj, TAcc* Ss, bool first,
+                                           const int (&lcol)[MAXO], TAcc (&acc)[MAXO]) {
+#pragma unroll
+  for (int i = 0; i < MAXO; ++i) {
+    const int l = lcol[i];
+    if (l >= 0) {
+      TAcc a = TAcc(0);
+      for (int e = 0; e < nzc; ++e) a += Vs[e * M1] * Xs[e * wx + l];
+      acc[i] += a;
+    }
+  }
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+    const int k = pk[q], j = pj[q];
+    TAcc s = TAcc(0);
+    for (int e = 0; e < nzc; ++e) s += Vs[e * M1 + k] * Xs[e * wx + j];
+    Ss[q] = first ? s : Ss[q] + s;
+  }
+}
+
+// After the row's last chunk and a block barrier: the couplings of this
+// thread's outputs from the pair sums, in coupling order.
+template <typename TAcc, int MAXO>
+__device__ __forceinline__ void pair_couple(const int* __restrict__ eptr, const int* __restrict__ pair,
+                                            const TAcc* __restrict__ ec, const TAcc* Ss, const int (&lcol)[MAXO],
+                                            TAcc (&acc)[MAXO]) {
+#pragma unroll
+  for (int i = 0; i < MAXO; ++i) {
+    const int l = lcol[i];
+    if (l >= 0) {
+      TAcc a = acc[i];
+      const int t1 = eptr[l + 1];
+      for (int t = eptr[l]; t < t1; ++t) a += ec[t] * Ss[pair[t]];
+      acc[i] = a;
+    }
+  }
+}
+
 // LB: the largest block the instantiation is launched with. Blocks of up to
 // 256 threads with fewer than 4 outputs per thread keep the compiler's
 // register choice; with 4 or more (large P) they may use up to 64 registers
@@ -106,10 +158,13 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const TAcc* __restrict__ vals,
     int M1, const TIn* __restrict__ X, int ldx, int wx, const int* __restrict__ eptr,
     const int* __restrict__ eperm, const int* __restrict__ ek, const int* __restrict__ ej,
-    const TAcc* __restrict__ ec, int wy, const TB* Yin, int ldyin, TAcc alpha, TAcc beta, TO* Y, int ldy, int chunk) {
+    const TAcc* __restrict__ ec, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
+    const int* __restrict__ epair, int pairs, int wy, const TB* Yin, int ldyin, TAcc alpha, TAcc beta, TO* Y,
+    int ldy, int chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TAcc* Xs = reinterpret_cast<TAcc*>(smem_raw);
   TAcc* Vs = Xs + (size_t)chunk * wx;
+  TAcc* Ss = Vs + (size_t)chunk * M1;   // pair sums (DIAG)
   int lcol[MAXO];
   output_columns<MAXO>(eperm, wy, lcol);
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
@@ -123,7 +178,14 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
       stage_chunk<TIn, TAcc>(cs, nzc, M1, colidx, vals, X, ldx, wx, Xs, Vs);
       cp_async_wait_all();
       __syncthreads();
-      gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
+      if (DIAG && pairs)
+        pair_chunk<TAcc, MAXO>(nzc, M1, Vs, Xs, wx, npair, pk, pj, Ss, cs == rb, lcol, acc);
+      else
+        gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
+    }
+    if (DIAG && pairs && re > rb) {
+      __syncthreads();
+      pair_couple<TAcc, MAXO>(eptr, epair, ec, Ss, lcol, acc);
     }
     // Y = beta Yin + alpha sum; the two forms the solver uses (Yin - sum, and
     // the plain sum) without the multiplications (the FP64 pipe is the bound)
@@ -158,10 +220,12 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const double* __restrict__ vals,
     int M1, int P, const double* __restrict__ z, double* pA, double* pB, const int* __restrict__ eptr,
     const int* __restrict__ eperm, const int* __restrict__ ek, const int* __restrict__ ej,
-    const double* __restrict__ ec, double* __restrict__ q, int chunk, OuterArgs a) {
+    const double* __restrict__ ec, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
+    const int* __restrict__ epair, int pairs, double* __restrict__ q, int chunk, OuterArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* Xs = reinterpret_cast<double*>(smem_raw);
   double* Vs = Xs + (size_t)chunk * P;
+  double* Ss = Vs + (size_t)chunk * M1;
   int lcol[MAXO];
   output_columns<MAXO>(eperm, P, lcol);
   const int it = a.ctl->it;
@@ -181,7 +245,14 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
       stage_chunk<double, double>(cs, nzc, M1, colidx, vals, z, P, P, Xs, Vs);
       cp_async_wait_all();
       __syncthreads();
-      gather_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
+      if (pairs)
+        pair_chunk<double, MAXO>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, cs == rb, lcol, acc);
+      else
+        gather_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
+    }
+    if (pairs && re > rb) {
+      __syncthreads();
+      pair_couple<double, MAXO>(eptr, epair, ec, Ss, lcol, acc);
     }
 #pragma unroll
     for (int i = 0; i < MAXO; ++i) {
@@ -215,11 +286,16 @@ static int pick_threads(int wy) {
   return t;
 }
 
-static int pick_chunk(const sg_problem* h, int wx, size_t es, int M1, size_t* smem) {
+// Nonzeros staged per chunk: a whole row where 96 KB hold it, fewer for very
+// wide rows. `extra` bytes (the pair sums) come on top, within the device's
+// per-block limit.
+static int pick_chunk(const sg_problem* h, int wx, size_t es, int M1, size_t extra, size_t* smem) {
   const size_t smem_cap = 96 * 1024;
   const size_t per_nz = (size_t)(wx + M1) * es;
-  const int chunk = (int)std::min<size_t>((size_t)std::max(h->max_row_nnz, 1), smem_cap / per_nz);
-  *smem = (size_t)std::max(chunk, 1) * per_nz;
+  int chunk = (int)std::min<size_t>((size_t)std::max(h->max_row_nnz, 1), smem_cap / per_nz);
+  const size_t limit = (size_t)std::max(h->smem_optin, 48 * 1024) - 1024;
+  if (extra + (size_t)chunk * per_nz > limit) chunk = extra < limit ? (int)((limit - extra) / per_nz) : 0;
+  *smem = (size_t)std::max(chunk, 1) * per_nz + extra;
   return chunk;
 }
 
@@ -243,7 +319,8 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
   if (DIAG && tuned > 0) threads = tuned;   // the full SG product: autotuned block size
   const int maxo = (wy + threads - 1) / threads;
   size_t smem = 0;
-  const int chunk = pick_chunk(h, wx, sizeof(TAcc), M1, &smem);
+  const int pairs = DIAG && h->k1_pairs[sizeof(TAcc) == 8 ? SG_F64 : SG_F32] ? 1 : 0;
+  const int chunk = pick_chunk(h, wx, sizeof(TAcc), M1, pairs ? (size_t)E.npair * sizeof(TAcc) : 0, &smem);
   if (chunk < 1) {
     set_error("block matvec: row of %d values does not fit in shared memory", wx);
     return SG_ERR_UNSUPPORTED;
@@ -253,7 +330,7 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
-    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, vals, M1, X, ldx, wx, E.ptr, E.perm, E.k, E.j, ec, wy, Yin, ldyin, (TAcc)alpha, (TAcc)beta, Y, ldy, chunk); ::sghsc::note_launch(); }
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, vals, M1, X, ldx, wx, E.ptr, E.perm, E.k, E.j, ec, E.npair, E.pk, E.pj, E.pair, pairs, wy, Yin, ldyin, (TAcc)alpha, (TAcc)beta, Y, ldy, chunk); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
@@ -302,7 +379,8 @@ int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
   const int threads = h->outer_threads > 0 ? h->outer_threads : 256;
   const int maxo = (P + threads - 1) / threads;
   size_t smem = 0;
-  const int chunk = pick_chunk(h, P, sizeof(double), M1, &smem);
+  const int pairs = h->outer_pairs ? 1 : 0;
+  const int chunk = pick_chunk(h, P, sizeof(double), M1, pairs ? (size_t)h->all.npair * sizeof(double) : 0, &smem);
   if (chunk < 1) {
     set_error("outer matvec: P = %d does not fit in shared memory", P);
     return SG_ERR_UNSUPPORTED;
@@ -312,7 +390,7 @@ int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int grid = std::min(std::min(h->n, h->num_sms * std::max(per_sm, 1)), h->opart_blocks);
-    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, h->vals64, M1, P, h->fz, h->fpA, h->fpB, h->all.ptr, h->all.perm, h->all.k, h->all.j, h->all.c64, h->fq, chunk, a); ::sghsc::note_launch(); }
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, h->vals64, M1, P, h->fz, h->fpA, h->fpB, h->all.ptr, h->all.perm, h->all.k, h->all.j, h->all.c64, h->all.npair, h->all.pk, h->all.pj, h->all.pair, pairs, h->fq, chunk, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };

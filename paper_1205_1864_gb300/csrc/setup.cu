@@ -81,6 +81,19 @@ static int upload_edges(const HostEdges& he, EdgeList& E) {
   SG_TRY(upload(&E.j, he.j.data(), he.j.size()));
   SG_TRY(upload(&E.c64, he.c.data(), he.c.size()));
   SG_TRY(upload(&E.c32, c32.data(), c32.size()));
+  std::map<std::pair<int, int>, int> pairs;
+  for (int t = 0; t < E.nedges; ++t) pairs.emplace(std::make_pair(he.k[t], he.j[t]), 0);
+  std::vector<int> pk, pj, pair(E.nedges);
+  for (auto& kv : pairs) {
+    kv.second = (int)pk.size();
+    pk.push_back(kv.first.first);
+    pj.push_back(kv.first.second);
+  }
+  for (int t = 0; t < E.nedges; ++t) pair[t] = pairs.at(std::make_pair(he.k[t], he.j[t]));
+  E.npair = (int)pk.size();
+  SG_TRY(upload(&E.pk, pk.data(), pk.size()));
+  SG_TRY(upload(&E.pj, pj.data(), pj.size()));
+  SG_TRY(upload(&E.pair, pair.data(), pair.size()));
   return SG_OK;
 }
 
@@ -91,6 +104,9 @@ static void free_edges(EdgeList& E) {
   cudaFree(E.j);
   cudaFree(E.c64);
   cudaFree(E.c32);
+  cudaFree(E.pk);
+  cudaFree(E.pj);
+  cudaFree(E.pair);
   E = EdgeList();
 }
 
@@ -219,6 +235,7 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   h->max_row_nnz = max_row;
   SG_TRY_CUDA(cudaGetDevice(&h->device));
   SG_TRY_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  SG_TRY_CUDA(cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
 
   // chaos table
   h->off.assign(1, 0);
@@ -315,6 +332,10 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   {
     const char* ev = getenv("SGHSC_NO_PIPE");
     h->pipe_off = ev && ev[0] == '1';
+  }
+  {
+    const char* ev = getenv("SGHSC_GATHER_FORM");   // start from the gather form of the full product
+    if (ev && ev[0] == '1') h->k1_pairs[0] = h->k1_pairs[1] = h->outer_pairs = 0;
   }
   SG_TRY_CUDA(cudaMalloc((void**)&h->loopflags, 8 * sizeof(int)));
   SG_TRY_CUDA(cudaMemset(h->loopflags, 0, 8 * sizeof(int)));

@@ -55,6 +55,13 @@ struct EdgeList {
   int* j = nullptr;
   double* c64 = nullptr;
   float* c32 = nullptr;
+  // The distinct (k, j) of the couplings, ordered by k then j (a sum
+  // sum_c a_k(r,c) U(c,j) serves every coupling with that pair), and the
+  // pair of each coupling.
+  int npair = 0;
+  int* pk = nullptr;
+  int* pj = nullptr;
+  int* pair = nullptr;
 };
 
 // One grid of the geometric multigrid hierarchy: interior nodes nx*ny, x
@@ -112,6 +119,7 @@ struct sg_problem {
   int n = 0, nnz = 0, M = 0, p = 0, P = 0, family = 0;
   int nx = 0, ny = 0;                 // mesh interior size (0 if no mesh)
   int device = 0, num_sms = 0;
+  int smem_optin = 0;                 // shared memory a block may opt in to (bytes)
   std::vector<int> alpha;             // host P*M
   std::vector<int> off;               // host p+2
   // shared CSR pattern and KL values [nnz][M+1]
@@ -169,6 +177,8 @@ struct sg_problem {
   // autotuned block sizes of the full SG product (0: heuristic), per element type
   int k1_threads[2] = {0, 0};
   int outer_threads = 0;                    // block size of the fused outer product (0: 256)
+  int k1_pairs[2] = {1, 1};                 // full SG product in pair form (1) or gather form (0)
+  int outer_pairs = 1;                      // the same for the fused outer product
   long long ws_gen = 0;                     // bumped whenever captured graphs become invalid
 };
 

@@ -66,6 +66,36 @@ def test_sg_apply_parity(lib, ne, M, p, prec):
     assert np.all(np.abs(Y - ref) <= tol * bound + 1e-300), np.max(np.abs(Y - ref) / (bound + 1e-300))
 
 
+@pytest.mark.parametrize("ne,M,p", [(16, 6, 4), (32, 4, 3)])
+def test_sg_apply_pair_and_gather_forms_agree(lib, ne, M, p):
+    """The pair form (one sum per distinct (k, j), shared by the couplings
+    that name it) and the gather form (one sum per coupling) add the same
+    terms in the same order on rows of one chunk: identical bits, FP64 and
+    FP32, for the product and for a whole outer solve."""
+    import os
+
+    import torch
+    prob, A, G, off = problem(ne, M, p)
+    hp = lib.SGProblem.from_inputs(prob, p)
+    os.environ["SGHSC_GATHER_FORM"] = "1"
+    try:
+        hg = lib.SGProblem.from_inputs(prob, p)
+    finally:
+        del os.environ["SGHSC_GATHER_FORM"]
+    U = S.random_block(prob.n, hp.P, seed=77)
+    for dt in (torch.float64, torch.float32):
+        Yp = lib.sg_apply(hp, _t(U, dt))
+        Yg = lib.sg_apply(hg, _t(U, dt))
+        assert torch.equal(Yp, Yg)
+    ref = so.sg_apply(A, G, U)
+    assert np.all(np.abs(_np(lib.sg_apply(hp, _t(U))) - ref) <= TOL64 * abs_bound(A, G, U) + 1e-300)
+    F = S.make_rhs(prob, p)
+    o = lib.solve_opts(lib.prec_opts(precision=lib.SG_F32), precond=lib.SG_PREC_HSC, tol=1e-8)
+    Up, sp_ = lib.sg_solve(hp, _t(F), o)
+    Ug, sg_ = lib.sg_solve(hg, _t(F), o)
+    assert sp_.iterations == sg_.iterations and torch.equal(Up, Ug)
+
+
 def test_sg_apply_general_csr_ragged_rows(lib):
     """A random pattern with empty rows and rows longer than 9 nonzeros (no mesh)."""
     import torch
