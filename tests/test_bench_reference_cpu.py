@@ -23,3 +23,25 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"].startswith("cfg1")
+
+
+def test_pair_count_matches_enumeration():
+    """The closed form of the distinct (k, j) pairs used for the product's
+    flop count against the oracle's coupling lists, enumerated."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import chaos
+    for M in range(1, 7):
+        for p in range(0, 5):
+            alpha, _ = chaos.multi_indices(M, p)
+            alpha = [tuple(int(v) for v in a) for a in alpha]
+            index = {tuple(a): i for i, a in enumerate(alpha)}
+            pairs = set()
+            for a in alpha:
+                for k in range(M):
+                    for step in (-1, 1):
+                        b = list(a)
+                        b[k] += step
+                        if b[k] >= 0 and tuple(b) in index:
+                            pairs.add((k, tuple(b)))
+            assert bench.sg_pairs(M, p) == len(pairs), (M, p)
