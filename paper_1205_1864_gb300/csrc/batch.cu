@@ -112,6 +112,18 @@ static int batch_solve(sg_batch* b, const double* const* F, double* const* U, co
 
 // ---------------------------------------------------------------- autotune ---
 
+// Candidate block sizes of the full product: powers of two from 64 to 1024 and
+// the whole-warp sizes that give every thread 1, 2 or 4 outputs with at most
+// 31 idle lanes (224 for P = 210).
+static std::vector<int> block_candidates(int P) {
+  std::vector<int> c = {64, 128, 256, 512, 1024};
+  for (int m : {1, 2, 4}) {
+    const int t = 32 * ceil_div(P, 32 * m);
+    if (t >= 64 && t <= 1024 && std::find(c.begin(), c.end(), t) == c.end()) c.push_back(t);
+  }
+  return c;
+}
+
 // Time the full SG product with each candidate block size, in pair and in
 // gather form, and keep the fastest.
 static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
@@ -128,12 +140,13 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cands[] = {64, 128, 256, 512, 1024};
+  const std::vector<int> cands = block_candidates(h->P);
+  const int nc = (int)cands.size();
   int best = 0, best_pairs = 1;
   float best_ms = 1e30f;
   int r = SG_OK;
-  for (int cand = 0; cand < 10 && r == SG_OK; ++cand) {
-    const int c = cands[cand % 5], pairs = cand < 5 ? 1 : 0;
+  for (int cand = 0; cand < 2 * nc && r == SG_OK; ++cand) {
+    const int c = cands[cand % nc], pairs = cand < nc ? 1 : 0;
     if ((h->P + c - 1) / c > 8) continue;   // at most 8 outputs per thread
     h->k1_threads[dtype] = c;
     h->k1_pairs[dtype] = pairs;
@@ -175,12 +188,13 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cands[] = {64, 128, 256, 512, 1024};
+  const std::vector<int> cands = block_candidates(h->P);
+  const int nc = (int)cands.size();
   int best = 0, best_pairs = 1;
   float best_ms = 1e30f;
   int r = SG_OK;
-  for (int cand = 0; cand < 10 && r == SG_OK; ++cand) {
-    const int c = cands[cand % 5], pairs = cand < 5 ? 1 : 0;
+  for (int cand = 0; cand < 2 * nc && r == SG_OK; ++cand) {
+    const int c = cands[cand % nc], pairs = cand < nc ? 1 : 0;
     const int maxo = (h->P + c - 1) / c;
     if (maxo > 8 || (c > 256 && maxo > 4)) continue;
     h->outer_threads = c;

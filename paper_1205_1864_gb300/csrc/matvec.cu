@@ -280,11 +280,9 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
   }
 }
 
-static int pick_threads(int wy) {
-  int t = 32;  // a power of two (the fused dot uses a tree reduction)
-  while (t < wy && t < 256) t *= 2;
-  return t;
-}
+// Block size of a product with wy outputs: whole warps, one output per thread
+// up to 256 outputs (no idle warp and at most 31 idle lanes), 256 beyond.
+static int pick_threads(int wy) { return std::min(256, 32 * std::max(1, ceil_div(wy, 32))); }
 
 // Nonzeros staged per chunk: a whole row where 96 KB hold it, fewer for very
 // wide rows. `extra` bytes (the pair sums) come on top, within the device's
@@ -375,7 +373,7 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
 
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
   const int P = h->P, M1 = h->M + 1;
-  // a power of two <= 1024 for the fused reduction: the autotuned block size or 256
+  // whole warps, <= 1024: the autotuned block size or 256
   const int threads = h->outer_threads > 0 ? h->outer_threads : 256;
   const int maxo = (P + threads - 1) / threads;
   size_t smem = 0;

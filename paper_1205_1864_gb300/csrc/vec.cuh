@@ -30,22 +30,39 @@ __global__ void k_outer_update(long long N, const double* pA, const double* pB, 
                                double* r, OuterArgs a);
 __global__ void k_outer_true(long long N, const double* F, const double* Y, OuterArgs a);
 
-// Fixed-order block sum of (v0, v1) to part[blockIdx]; returns true in the last
-// block, whose threads then hold the totals (t0, t1) over all blocks (summed in
-// block order). blockDim must be a power of two <= 1024 for the tree below.
-__device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const OuterArgs& a, double& t0, double& t1) {
-  __shared__ double r0[1024], r1[1024];
-  __shared__ bool last;
-  r0[threadIdx.x] = v0;
-  r1[threadIdx.x] = v1;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+// Fixed-order tree sum of r0[0 .. blockDim), r1[...] into r0[0], r1[0]:
+// the entries above the largest power of two p2 <= blockDim are first added
+// to entries 0 .. blockDim - p2 (nothing for a power-of-two block), then the
+// halving tree over p2 entries.
+__device__ __forceinline__ void tree_sum2(double* r0, double* r1) {
+  int p2 = 1;
+  while (2 * p2 <= (int)blockDim.x) p2 *= 2;
+  if (p2 < (int)blockDim.x) {
+    if ((int)threadIdx.x < (int)blockDim.x - p2) {
+      r0[threadIdx.x] += r0[threadIdx.x + p2];
+      r1[threadIdx.x] += r1[threadIdx.x + p2];
+    }
+    __syncthreads();
+  }
+  for (int s = p2 / 2; s > 0; s >>= 1) {
     if ((int)threadIdx.x < s) {
       r0[threadIdx.x] += r0[threadIdx.x + s];
       r1[threadIdx.x] += r1[threadIdx.x + s];
     }
     __syncthreads();
   }
+}
+
+// Fixed-order block sum of (v0, v1) to part[blockIdx]; returns true in the last
+// block, whose threads then hold the totals (t0, t1) over all blocks (summed in
+// block order). blockDim <= 1024.
+__device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const OuterArgs& a, double& t0, double& t1) {
+  __shared__ double r0[1024], r1[1024];
+  __shared__ bool last;
+  r0[threadIdx.x] = v0;
+  r1[threadIdx.x] = v1;
+  __syncthreads();
+  tree_sum2(r0, r1);
   if (threadIdx.x == 0) {
     a.part[(size_t)blockIdx.x * 2 + 0] = r0[0];
     a.part[(size_t)blockIdx.x * 2 + 1] = r1[0];
@@ -63,13 +80,7 @@ __device__ __forceinline__ bool outer_reduce_last(double v0, double v1, const Ou
   r0[threadIdx.x] = s0;
   r1[threadIdx.x] = s1;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      r0[threadIdx.x] += r0[threadIdx.x + s];
-      r1[threadIdx.x] += r1[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
+  tree_sum2(r0, r1);
   t0 = r0[0];
   t1 = r1[0];
   if (threadIdx.x == 0) a.ctl->ticket = 0;
