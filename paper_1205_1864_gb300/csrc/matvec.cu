@@ -70,8 +70,9 @@ __device__ __forceinline__ void stage_chunk(int cs, int nzc, int M1, const int* 
 }
 
 // Accumulate the gather form for this thread's outputs over one staged chunk
-// (a level product names every pair (k, j) once: this is its form).
-template <typename TAcc, int MAXO, bool DIAG>
+// (a level product names every pair (k, j) once: this is its form). FIRST:
+// the row's first chunk stores its sums (no FP64 add of a zero).
+template <typename TAcc, int MAXO, bool DIAG, bool FIRST>
 __device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __restrict__ Vs,
                                              const TAcc* __restrict__ Xs, int wx, const int* __restrict__ eptr,
                                              const int* __restrict__ ek, const int* __restrict__ ej,
@@ -92,39 +93,48 @@ __device__ __forceinline__ void gather_chunk(int nzc, int M1, const TAcc* __rest
         for (int e = 0; e < nzc; ++e) s += Vs[e * M1 + k] * Xs[e * wx + j];
         a += ec[t] * s;
       }
-      acc[i] += a;
+      if (FIRST)
+        acc[i] = a;
+      else
+        acc[i] += a;
     }
   }
 }
 
 // The full SG product in pair form (DIAG): per staged chunk, the diagonal
 // term of this thread's outputs into acc, and for every distinct pair
-// q = (k, j) of the couplings s_q = sum_c a_k(r,c) U(c,j) into Ss (the first
-// chunk of a row stores, later ones add). A pair serves every coupling that
+// q = (k, j) of the couplings s_q = sum_c a_k(r,c) U(c,j) into Ss (FIRST: the
+// row's first chunk stores, later ones add). A pair serves every coupling that
 // names it (an input column j coupled to two outputs in direction k is summed
 // once), so this does 9 (P + npair) multiply-adds per 9-point row instead of
 // 9 (P + n_m); consecutive pairs share k and take consecutive j. It needs
 // npair more values of shared memory, which can cost resident blocks: the
 // autotuner times both forms.
-template <typename TAcc, int MAXO>
+template <typename TAcc, int MAXO, bool FIRST>
 __device__ __forceinline__ void pair_chunk(int nzc, int M1, const TAcc* __restrict__ Vs, const TAcc* __restrict__ Xs,
                                            int wx, int npair, const int* __restrict__ pk,
-                                           const int* __restrict__ pj, TAcc* Ss, bool first,
-                                           const int (&lcol)[MAXO], TAcc (&acc)[MAXO]) {
+                                           const int* __restrict__ pj, TAcc* Ss, const int (&lcol)[MAXO],
+                                           TAcc (&acc)[MAXO]) {
 #pragma unroll
   for (int i = 0; i < MAXO; ++i) {
     const int l = lcol[i];
     if (l >= 0) {
       TAcc a = TAcc(0);
       for (int e = 0; e < nzc; ++e) a += Vs[e * M1] * Xs[e * wx + l];
-      acc[i] += a;
+      if (FIRST)
+        acc[i] = a;
+      else
+        acc[i] += a;
     }
   }
   for (int q = threadIdx.x; q < npair; q += blockDim.x) {
     const int k = pk[q], j = pj[q];
     TAcc s = TAcc(0);
     for (int e = 0; e < nzc; ++e) s += Vs[e * M1 + k] * Xs[e * wx + j];
-    Ss[q] = first ? s : Ss[q] + s;
+    if (FIRST)
+      Ss[q] = s;
+    else
+      Ss[q] += s;
   }
 }
 
@@ -178,10 +188,16 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
       stage_chunk<TIn, TAcc>(cs, nzc, M1, colidx, vals, X, ldx, wx, Xs, Vs);
       cp_async_wait_all();
       __syncthreads();
-      if (DIAG && pairs)
-        pair_chunk<TAcc, MAXO>(nzc, M1, Vs, Xs, wx, npair, pk, pj, Ss, cs == rb, lcol, acc);
-      else
-        gather_chunk<TAcc, MAXO, DIAG>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
+      if (DIAG && pairs) {
+        if (cs == rb)
+          pair_chunk<TAcc, MAXO, true>(nzc, M1, Vs, Xs, wx, npair, pk, pj, Ss, lcol, acc);
+        else
+          pair_chunk<TAcc, MAXO, false>(nzc, M1, Vs, Xs, wx, npair, pk, pj, Ss, lcol, acc);
+      } else if (cs == rb) {
+        gather_chunk<TAcc, MAXO, DIAG, true>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
+      } else {
+        gather_chunk<TAcc, MAXO, DIAG, false>(nzc, M1, Vs, Xs, wx, eptr, ek, ej, ec, lcol, acc);
+      }
     }
     if (DIAG && pairs && re > rb) {
       __syncthreads();
@@ -245,10 +261,16 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
       stage_chunk<double, double>(cs, nzc, M1, colidx, vals, z, P, P, Xs, Vs);
       cp_async_wait_all();
       __syncthreads();
-      if (pairs)
-        pair_chunk<double, MAXO>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, cs == rb, lcol, acc);
-      else
-        gather_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
+      if (pairs) {
+        if (cs == rb)
+          pair_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, lcol, acc);
+        else
+          pair_chunk<double, MAXO, false>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, lcol, acc);
+      } else if (cs == rb) {
+        gather_chunk<double, MAXO, true, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
+      } else {
+        gather_chunk<double, MAXO, true, false>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
+      }
     }
     if (pairs && re > rb) {
       __syncthreads();
