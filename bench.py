@@ -63,7 +63,7 @@ FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12
 # DRAM bytes of one FP64 SG-product launch on the 128x128, M=6, p=4 workload:
 # dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of that launch
 # (L2 flushed before it, as before each timed launch here).
-K1_TRAFFIC = {"cfg2": 35822848 + 49664}
+K1_TRAFFIC = {"cfg2": 35833856 + 119040}
 
 
 class ClockSampler:
