@@ -3,17 +3,22 @@ residual 1e-8 with the hierarchical Schur complement preconditioner
 (mixed precision: FP32 inner loops, FP64 outer), against the all-FP64
 mean-based preconditioner on the same GPU, plus the SG matvec roofline.
 
-Workload (default): 128 x 128 Q1 grid (16129 interior dofs), M = 6 Legendre
-variables, p = 4 (P = 210, 3.39M unknowns), sigma = 0.3, correlation length
-1.0, f = 1; inner A_0 PCG with a multigrid V-cycle to 1e-2.
+Workload (default): 512 x 512 Q1 grid (261121 interior dofs), M = 10 Legendre
+variables, p = 4 (P = 1001, 261M unknowns, 2.09 GB per FP64 vector),
+sigma = 0.25, correlation length 0.5, f = 1; inner A_0 PCG with a multigrid
+V-cycle to 1e-2. ``--workload cfg2`` runs the 128 x 128, M = 6, p = 4 system,
+``cfg3`` the 64-system batch.
 
 One step = one full sg_solve (K1 SG matvec, K2 level products, K3/K4 batched
 inner PCG + V-cycle, K5 outer FCG) with F resident in HBM. L2 is flushed
-(256 MiB write) between timed steps, outside the timed events.
+(256 MiB write) between timed steps, outside the timed events. The same line
+carries the three comparator solves (mean-based FP64, HSC FP64, mean-based
+mixed), the SG product alone in FP64 and FP32 against the measured FP64/FP32
+ALU rates and the HBM peak, and the end-to-end time from host buffers.
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure) on a
-bounded sample of the same workload; that arm is the deliberately slow
-baseline, not a target.
+bounded sample of the same workload on all host cores; that arm is the
+deliberately slow baseline, not a target.
 """
 from __future__ import annotations
 
@@ -35,11 +40,15 @@ import numpy as np  # noqa: E402
 import sg_inputs as S  # noqa: E402
 
 METRIC = "time-to-solve at rel.res 1e-8, HSC-PCG vs mean-based PCG; SG matvec HBM GB/s"
+# hsc_iterations: outer HSC-FCG iterations of the timed solve (mixed, inner tol
+# 1e-2, rel.res 1e-8) as the GPU takes them; the oracle's time per iteration is
+# scaled by it in the reference arm, which runs without a GPU (checked by the
+# GPU parity tests against the library's own count).
 WORKLOADS = {
-    "cfg2": dict(name="cfg2_mixed_128x128_M6_p4", **S.CONFIGS["cfg2_mixed_128x128_M6_p4"]),
-    "cfg1": dict(name="cfg1_fp64_16x16_M3_p3", **S.CONFIGS["cfg1_fp64_16x16_M3_p3"]),
-    "cfg4": dict(name="cfg4_64x64_M4_p3", **S.CONFIGS["cfg4_grad_64x64_M4_p3"]),
-    "cfg5": dict(name="cfg5_large_512x512_M10_p4", **S.CONFIGS["cfg5_large_512x512_M10_p4"]),
+    "cfg2": dict(name="cfg2_mixed_128x128_M6_p4", hsc_iterations=8, **S.CONFIGS["cfg2_mixed_128x128_M6_p4"]),
+    "cfg1": dict(name="cfg1_fp64_16x16_M3_p3", hsc_iterations=6, **S.CONFIGS["cfg1_fp64_16x16_M3_p3"]),
+    "cfg4": dict(name="cfg4_64x64_M4_p3", hsc_iterations=6, **S.CONFIGS["cfg4_grad_64x64_M4_p3"]),
+    "cfg5": dict(name="cfg5_large_512x512_M10_p4", hsc_iterations=7, **S.CONFIGS["cfg5_large_512x512_M10_p4"]),
     # 64 independent systems (mesh, M, p, sigma, L drawn per system), one graph launch
     "cfg3": dict(name="cfg3_batch64_mixed", batch=True, count=64, seed=1864),
 }
@@ -54,11 +63,6 @@ def _peaks():
     except Exception:
         return 6800.0, "fallback"
 
-
-# FP64 ALU peak of the FP64-bound kernels: 152 SMs x 2070 MHz x 2 DFMA per
-# clock per SM x 2 flop = 1.259 TFLOP/s (the nominal GB300 FP64 rate of
-# 1.25 TFLOP/s at the maximum SM clock).
-FP64_PEAK_TFLOPS = 152 * 2070e6 * 2 * 2 / 1e12
 
 # DRAM bytes of one FP64 SG-product launch on the 128x128, M=6, p=4 workload:
 # dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of that launch
@@ -175,6 +179,10 @@ def run_ours(args, rank, world, dev):
                             precond=L.SG_PREC_HSC, tol=1e-8, maxit=500, check_true_residual=0)
     mean_opts = L.solve_opts(L.prec_opts(precision=L.SG_F64, inner_tol=1e-2), precond=L.SG_PREC_MEAN,
                              tol=1e-8, maxit=500, check_true_residual=0)
+    hsc64_opts = L.solve_opts(L.prec_opts(precision=L.SG_F64, inner_tol=1e-2), precond=L.SG_PREC_HSC,
+                              tol=1e-8, maxit=500, check_true_residual=0)
+    mean32_opts = L.solve_opts(L.prec_opts(precision=L.SG_F32, inner_tol=1e-2), precond=L.SG_PREC_MEAN,
+                               tol=1e-8, maxit=500, check_true_residual=0)
 
     def timed_solves(opts, steps, warmup, count_launches=False):
         for _ in range(warmup):
@@ -249,33 +257,42 @@ def run_ours(args, rank, world, dev):
     # headline: mixed HSC-PCG
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
         ts, st_h, _ = timed_solves(hsc_opts, args.steps, args.warmup)
+    ms = float(np.mean(ts))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    # validation solve (untimed): the true FP64 residual of the same HSC solve
+    _, st_true = L.sg_solve(h, F, L.solve_opts(hsc_opts.prec, precond=L.SG_PREC_HSC, tol=1e-8, maxit=500,
+                                               check_true_residual=1), U)
+    # comparators on the same GPU, each precision with each preconditioner, so
+    # that the speed-up splits into preconditioner and precision: the metric's
+    # own comparator is the all-FP64 mean-based PCG
+    cmp_steps = max(1, min(args.steps, 2))
+    comparators = {}
+    for key, opts in (("mean_fp64", mean_opts), ("hsc_fp64", hsc64_opts), ("mean_mixed", mean32_opts)):
+        ts_c, st_c, _ = timed_solves(opts, cmp_steps, 1)
+        comparators[key] = {"ms": float(np.mean(ts_c)), "iterations": st_c.iterations, "rel_res": st_c.rel_res,
+                            "kappa_est": st_c.kappa_est, "step_ms": ts_c}
+    comparators["hsc_mixed"] = {"ms": ms, "iterations": st_h.iterations, "rel_res": st_h.rel_res,
+                                "kappa_est": st_h.kappa_est}
+    ms_mean = comparators["mean_fp64"]["ms"]
+
     # kernels per solve: graph replays launch no host calls, so count them on a
     # second handle in eager mode, which runs the same kernels from host-driven loops
     os.environ["SGHSC_EAGER"] = "1"
     h_e = L.SGProblem.from_inputs(prob, p)
     os.environ.pop("SGHSC_EAGER")
     L.sg_autotune(h_e)
-    L.sg_solve(h_e, F, hsc_opts)
+    L.sg_solve(h_e, F, hsc_opts, U)
     l0 = L._lib.LIB.sg_kernel_launches()
-    L.sg_solve(h_e, F, hsc_opts)
+    L.sg_solve(h_e, F, hsc_opts, U)
     launches = L._lib.LIB.sg_kernel_launches() - l0
     h_e.close()
-    ms = float(np.mean(ts))
-    # validation solve (untimed): the true FP64 residual of the same HSC solve
-    _, st_true = L.sg_solve(h, F, L.solve_opts(hsc_opts.prec, precond=L.SG_PREC_HSC, tol=1e-8, maxit=500,
-                                               check_true_residual=1), U)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    # oracle-independent check of the result: true FP64 residual from the library
-    U_h = U.clone()
-    # comparator: all-FP64 mean-based PCG on the same GPU
-    ts_m, st_m, _ = timed_solves(mean_opts, max(1, min(args.steps, 3)), 1)
-    ms_mean = float(np.mean(ts_m))
+    del h_e
 
     # SG matvec roofline: K1 timed alone with events on the launching stream
-    def time_apply(dtype, reps=20):
+    def time_apply(dtype, reps=10):
         Ut = torch.tensor(S.random_block(n, P, seed=1205), dtype=dtype, device=dev)
         Yt = torch.empty_like(Ut)
         for _ in range(3):
@@ -290,24 +307,32 @@ def run_ours(args, rank, world, dev):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+        del Ut, Yt
         return float(np.mean(times))
 
     k1_64 = time_apply(torch.float64)
     k1_32 = time_apply(torch.float32)
     hbm, hbm_src = _peaks()
+    fp64_peak = L.sg_measure_alu_peak(L.SG_F64) / 1e12      # TFLOP/s, timed alone (burst)
+    fp32_peak = L.sg_measure_alu_peak(L.SG_F32) / 1e12
     b64 = sg_matvec_bytes(n, nnz, M, P, 8)
     b32 = sg_matvec_bytes(n, nnz, M, P, 4)
     fl = sg_matvec_flops(n, nnz, M, p, P, n_m)
     matvec = {
-        "fp64": {"ms": k1_64, "GB_s": b64 / k1_64 / 1e6, "TFLOP_s": fl / k1_64 / 1e9, "bytes": b64, "flops": fl},
-        "fp32": {"ms": k1_32, "GB_s": b32 / k1_32 / 1e6, "TFLOP_s": fl / k1_32 / 1e9, "bytes": b32, "flops": fl},
-        "hbm_peak_GB_s": hbm,
+        "fp64": {"ms": k1_64, "GB_s": b64 / k1_64 / 1e6, "TFLOP_s": fl / k1_64 / 1e9, "bytes": b64, "flops": fl,
+                 "frac_fp64_alu_measured": fl / k1_64 / 1e9 / fp64_peak, "frac_hbm": b64 / k1_64 / 1e6 / hbm},
+        "fp32": {"ms": k1_32, "GB_s": b32 / k1_32 / 1e6, "TFLOP_s": fl / k1_32 / 1e9, "bytes": b32, "flops": fl,
+                 "frac_fp32_alu_measured": fl / k1_32 / 1e9 / fp32_peak, "frac_hbm": b32 / k1_32 / 1e6 / hbm},
+        "hbm_peak_GB_s": hbm, "hbm_peak_source": hbm_src,
+        "fp64_alu_peak_TFLOP_s": fp64_peak, "fp32_alu_peak_TFLOP_s": fp32_peak,
     }
-    roofline = {"kernel": "k_block_matvec<double> (K1 FP64 SG product, outer CG)", "bound": "alu",
-                "achieved": fl / k1_64 / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (fl / k1_64 / 1e9) / FP64_PEAK_TFLOPS, "traffic": K1_TRAFFIC.get(args.workload),
+    roofline = {"kernel": "k_block_matvec<double> (K1 FP64 SG product, the arithmetic of the outer CG's fused "
+                          "product k_outer_matvec)", "bound": "alu",
+                "achieved": fl / k1_64 / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (fl / k1_64 / 1e9) / fp64_peak, "traffic": K1_TRAFFIC.get(args.workload),
                 "algorithmic_bytes": b64, "algorithmic_flops": fl,
-                "peak_source": "FP64 ALU: 152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop (nominal GB300 FP64 rate)"}
+                "peak_source": "measured: FP64 FMA-chain kernel (sg_measure_alu_peak) on this GPU, timed alone, "
+                               "of measured"}
 
     # end to end through the public API: host (pinned) F in, host U out
     F_host = torch.tensor(F_np, dtype=torch.float64).pin_memory()
@@ -318,11 +343,12 @@ def run_ours(args, rank, world, dev):
         torch.cuda.synchronize()
         t_a = time.perf_counter()
         Fd = F_host.to(dev, non_blocking=True)
-        Ud, _ = L.sg_solve(h, Fd, hsc_opts)
+        Ud, _ = L.sg_solve(h, Fd, hsc_opts, U)
         U_host.copy_(Ud, non_blocking=True)
         torch.cuda.synchronize()
         if i > 0:
             e2e_t.append((time.perf_counter() - t_a) * 1e3)
+        del Fd
     e2e_ms = float(np.mean(e2e_t))
 
     out = {
@@ -338,8 +364,15 @@ def run_ours(args, rank, world, dev):
         "hsc": {"ms": ms, "iterations": st_h.iterations, "true_rel_res": st_true.true_rel_res,
                 "kappa_est": st_h.kappa_est, "inner_iters_total": st_h.inner_iters_total,
                 "inner_iters_max": st_h.inner_iters_max, "step_ms": ts},
-        "mean_fp64": {"ms": ms_mean, "iterations": st_m.iterations, "rel_res": st_m.rel_res,
-                      "kappa_est": st_m.kappa_est, "speedup_hsc_vs_mean": ms_mean / ms},
+        "mean_fp64": {"ms": ms_mean, "iterations": comparators["mean_fp64"]["iterations"],
+                      "rel_res": comparators["mean_fp64"]["rel_res"],
+                      "kappa_est": comparators["mean_fp64"]["kappa_est"], "speedup_hsc_vs_mean": ms_mean / ms},
+        "comparators": comparators,
+        "speedups": {"hsc_mixed_vs_mean_fp64": ms_mean / ms,
+                     "preconditioner_fp64 (mean_fp64 / hsc_fp64)": ms_mean / comparators["hsc_fp64"]["ms"],
+                     "preconditioner_mixed (mean_mixed / hsc_mixed)": comparators["mean_mixed"]["ms"] / ms,
+                     "precision_hsc (hsc_fp64 / hsc_mixed)": comparators["hsc_fp64"]["ms"] / ms,
+                     "precision_mean (mean_fp64 / mean_mixed)": ms_mean / comparators["mean_mixed"]["ms"]},
         "sg_matvec": matvec,
         "roofline": roofline,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(F_host.numel() * 8),
@@ -352,7 +385,7 @@ def run_ours(args, rank, world, dev):
         "setup_s": setup_s,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(cfg, iterations=st_h.iterations, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(cfg, iterations=st_h.iterations)
     return out
 
 
@@ -456,10 +489,12 @@ def run_batch(args, rank, world, dev):
     k1 = float(np.mean([_events_time(lambda: L.sg_apply(hb, Ut, Yt), stream, flush)[0] for _ in range(20)]))
     M_b, p_b = hb.M, cfgs[mine[big]]["p"]
     fl = sg_matvec_flops(hb.n, hb.nnz, M_b, p_b, hb.P, int(2 * M_b * math.comb(M_b + p_b - 1, M_b)))
+    fp64_peak = L.sg_measure_alu_peak(L.SG_F64) / 1e12
     roofline = {"kernel": f"k_block_matvec<double> (K1 FP64 SG product) on the largest system (n={hb.n}, P={hb.P})",
-                "bound": "alu", "achieved": fl / k1 / 1e9, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (fl / k1 / 1e9) / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 ALU: 152 SMs x 2070 MHz x 2 DFMA/clk x 2 flop (nominal GB300 FP64 rate)"}
+                "bound": "alu", "achieved": fl / k1 / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (fl / k1 / 1e9) / fp64_peak, "traffic": None,
+                "peak_source": "measured: FP64 FMA-chain kernel (sg_measure_alu_peak) on this GPU, timed alone, "
+                               "of measured"}
     # end to end through the public API: host (pinned) right-hand sides in, solutions out
     F_host = [F.cpu().pin_memory() for F in Fs]
     U_host = [torch.empty_like(F).pin_memory() for F in F_host]
@@ -499,91 +534,182 @@ def run_batch(args, rank, world, dev):
         "setup_s": setup_s,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_batch(cfgs, [s.iterations for s in st], budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline_batch(cfgs, [s.iterations for s in st])
     batch.close()
     return out
 
 
-def cpu_baseline_batch(cfgs, iterations, budget_s=20.0):
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on all host cores
+# --------------------------------------------------------------------------
+#
+# One outer HSC-FCG iteration of the oracle is an SG product (oracle
+# sg_operator), the 2p level products of Algorithm 1 (sg_operator.level_apply)
+# and n_ds = 2 (P - 1) + 1 inner column solves (krylov.pcg_columns with one
+# gmg.vcycle per step, tolerance 1e-2: the algorithm the GPU runs). Each of
+# them is independent across spatial rows (products) or columns (inner solves),
+# so the host's cores each take a share: a pool of spawned processes, one per
+# core, each holding the problem. The sample times, on every core at once, one
+# block of rows of the products and one inner column solve, and scales them to
+# the whole iteration and to the solve's iteration count.
+
+_CPU = {}
+
+
+def _cpu_init(cfg):
+    from oracle import chaos, gmg, sg_operator as so
+    prob = S.make_problem(cfg["ne"], cfg["M"], cfg["sigma"], cfg["corr_len"])
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(cfg["M"], cfg["p"])
+    _, off = chaos.multi_indices(cfg["M"], cfg["p"])
+    P = G[0].shape[0]
+    # inputs: untouched zero pages until a row block reads them (the products'
+    # time does not depend on the values); one contiguous block per degree level
+    _CPU.update(A=A, G=G, off=off, n=prob.n, P=P, p=cfg["p"], lv=gmg.hierarchy(A[0], cfg["ne"]),
+                U=np.zeros((prob.n, P)), Ul=[np.zeros((prob.n, off[l + 1] - off[l])) for l in range(cfg["p"] + 1)])
+
+
+def _cpu_products(task):
+    """Wall time of the SG product and of the 2p level products on one block of rows."""
+    from oracle import sg_operator as so
+    start, count = task
+    c = _CPU
+    rows = np.arange(start, min(start + count, c["n"]))
+    t0 = time.perf_counter()
+    so.sg_apply_rows(c["A"], c["G"], c["U"], rows)
+    t1 = time.perf_counter()
+    off, p = c["off"], c["p"]
+    for l in range(1, p + 1):
+        for lo, li in ((l - 1, l), (l, l - 1)):
+            so.level_apply(c["A"], c["G"], off, lo, li, c["Ul"][li], rows=rows)
+    return t1 - t0, time.perf_counter() - t1
+
+
+def _cpu_column(seed):
+    """Wall time and iterations of one inner column solve (V-cycle PCG, tol 1e-2)."""
+    from oracle import gmg, krylov
+    c = _CPU
+    b = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(c["n"], 1))
+    A0, lv = c["A"][0], c["lv"]
+    t0 = time.perf_counter()
+    _, it = krylov.pcg_columns(lambda v: A0 @ v, b, lambda r: gmg.vcycle(lv, r, nu=2, omega=0.8), tol=1e-2,
+                               maxit=200)
+    return time.perf_counter() - t0, int(it[0])
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class CpuOracle:
+    """A pool of spawned processes, one per host core, each holding one
+    problem of the workload for the oracle's timed samples."""
+
+    def __init__(self, cfg, cores=None):
+        import multiprocessing as mp
+        self.cfg = cfg
+        self.cores = cores or host_cores()
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_cpu_init, initargs=(cfg,))
+        n = (cfg["ne"] - 1) ** 2
+        self.n = n
+        self.P = math.comb(cfg["M"] + cfg["p"], cfg["M"])
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+    def sample(self, iterations, rows_per_core=None):
+        """One bounded sample: every core times one block of rows of the
+        products and one inner column solve; returns the estimate of the
+        oracle's whole solve (ms) and what was sampled."""
+        cores, n, P = self.cores, self.n, self.P
+        B = rows_per_core or max(16, min(n // cores, max(1, 2_000_000 // max(P, 1))))
+        tasks = [((i * B) % max(n - B, 1), B) for i in range(cores)]
+        t0 = time.perf_counter()
+        prod = self.pool.map(_cpu_products, tasks, chunksize=1)
+        t1 = time.perf_counter()
+        cols = self.pool.map(_cpu_column, list(range(cores)), chunksize=1)
+        t2 = time.perf_counter()
+        # every core busy at once: the wall time of one round covers cores blocks / columns
+        rounds_rows = n / (B * cores)
+        t_apply = max(a for a, _ in prod) * rounds_rows
+        t_levels = max(b for _, b in prod) * rounds_rows
+        n_ds = 2 * (P - 1) + 1
+        t_inner = (t2 - t1) * math.ceil(n_ds / cores)
+        per_iter = t_apply + t_levels + t_inner
+        value_ms = per_iter * max(iterations, 1) * 1e3
+        its = sorted({i for _, i in cols})
+        desc = (f"FP64 oracle on {cores} host cores (one spawned process per core): per core {B} rows of the SG "
+                f"product and of the 2p level products of Algorithm 1 ({t1 - t0:.2f} s wall) and one inner "
+                f"V-cycle-PCG column solve at tol 1e-2 ({t2 - t1:.2f} s wall, {its} iterations); scaled to {n} "
+                f"rows and n_ds = {n_ds} column solves per HSC application: {per_iter:.2f} s per outer "
+                f"iteration (product {t_apply:.2f} s, level products {t_levels:.2f} s, inner solves "
+                f"{t_inner:.2f} s) x {iterations} iterations")
+        return value_ms, desc
+
+
+def cpu_baseline(cfg, iterations, oracle=None):
+    own = oracle is None
+    oracle = oracle or CpuOracle(cfg)
+    try:
+        t0 = time.perf_counter()
+        v, desc = oracle.sample(iterations)
+        return {"value": v, "unit": "ms", "cores": oracle.cores, "kind": "oracle", "sample": desc,
+                "wall_s": time.perf_counter() - t0}
+    finally:
+        if own:
+            oracle.close()
+
+
+def cpu_baseline_batch(cfgs, iterations):
     """The oracle on a bounded sample of the batch: per mesh size, the first
-    system of that size in draw order, timed for one outer HSC-FCG iteration;
-    every system's full solve is then estimated from its class's time per unit
-    of cost, times its own cost and GPU iteration count."""
+    system of that size in draw order, sampled on all host cores for one outer
+    iteration; every system's full solve is then estimated from its class's
+    time per unit of cost, times its own cost and GPU iteration count."""
     from paper_1205_1864_gb300 import shard
     costs = [shard.system_cost(c["ne"], c["M"], c["p"]) for c in cfgs]
     rate, sampled = {}, []
     t0 = time.perf_counter()
+    cores = host_cores()
     for ne in sorted({c["ne"] for c in cfgs}):
         i = next(j for j, c in enumerate(cfgs) if c["ne"] == ne)
         c = cfgs[i]
-        cb = cpu_baseline(dict(name=f"system {i}", **c), iterations=1, budget_s=budget_s / 4,
-                          prob=S.make_problem(c["ne"], c["M"], c["sigma"], c["corr_len"]))
+        cb = cpu_baseline(dict(name=f"system {i}", **c), iterations=1)
         rate[ne] = cb["value"] / costs[i]
         sampled.append(f"#{i} ({ne}x{ne}, M={c['M']}, p={c['p']}): {cb['value']:.0f} ms/iteration")
         cores = cb["cores"]
     value = sum(rate[c["ne"]] * costs[j] * max(iterations[j], 1) for j, c in enumerate(cfgs))
     return {"value": value, "unit": "ms", "cores": cores, "kind": "oracle",
-            "sample": "one outer HSC-FCG iteration of the FP64 oracle per mesh size (" + "; ".join(sampled) +
-                      "), scaled per system by cost and GPU iteration count to all systems",
-            "wall_s": time.perf_counter() - t0}
-
-
-def cpu_baseline(cfg, iterations, budget_s=20.0, prob=None):
-    """The FP64 oracle (exact inner solves) timed on the host on a bounded
-    sample: as many outer HSC-FCG iterations as fit the budget, scaled to the
-    iteration count of the full solve."""
-    from oracle import chaos, hsc, krylov, sg_operator as so
-    prob = prob or build_problem(cfg)
-    p = cfg["p"]
-    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
-    G = chaos.g_matrices(cfg["M"], p)
-    _, off = chaos.multi_indices(cfg["M"], p)
-    F = S.make_rhs(prob, p)
-    a0 = hsc.A0Solver(A[0])
-    ap = lambda X: so.sg_apply(A, G, X)
-    pre = lambda R: hsc.hsc_apply(A, G, off, R, a0solve=a0)
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        k += 1
-        t1 = time.perf_counter()
-        krylov.fcg(ap, F, pre, tol=0.0, maxit=k)
-        dt = time.perf_counter() - t1
-        if dt * (k + 1) / k > budget_s or k >= iterations:
-            break
-    per_iter = dt / k
-    value_ms = per_iter * max(iterations, 1) * 1e3
-    cores = 1
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([1] + [i.get("num_threads", 1) for i in threadpool_info()])
-    except Exception:
-        pass
-    return {"value": value_ms, "unit": "ms", "cores": cores, "kind": "oracle",
-            "sample": f"{k} outer HSC-FCG iterations of the FP64 oracle (exact sparse-LU inner solves) on "
-                      f"{cfg['name']}, {per_iter * 1e3:.1f} ms each, scaled to {iterations} iterations",
+            "sample": "one outer HSC-FCG iteration of the FP64 oracle per mesh size, sampled on all host cores (" +
+                      "; ".join(sampled) + "), scaled per system by cost and GPU iteration count to all systems",
             "wall_s": time.perf_counter() - t0}
 
 
 def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step is one bounded
+    sample of the workload's solve (see CpuOracle), on rank 0 only."""
     if rank != 0:
         return None
     cfg = WORKLOADS[args.workload]
     vals = []
-    budget = max(5.0, 150.0 / max(args.steps + args.warmup, 1))
     if cfg.get("batch"):
         cfgs = S.draw_batch_configs(cfg["count"], seed=cfg["seed"])
         for i in range(args.warmup + args.steps):
-            cb = cpu_baseline_batch(cfgs, [6] * len(cfgs), budget_s=budget)   # ~6 HSC-FCG iterations at 1e-8
+            cb = cpu_baseline_batch(cfgs, [6] * len(cfgs))   # ~6 HSC-FCG iterations at 1e-8
             if i >= args.warmup:
                 vals.append(cb["value"])
     else:
-        prob = build_problem(cfg)
-        iters = 7 if args.workload == "cfg2" else 6     # HSC-FCG iteration count of the full solve at 1e-8
-        for i in range(args.warmup + args.steps):
-            cb = cpu_baseline(cfg, iterations=iters, budget_s=budget, prob=prob)
-            if i >= args.warmup:
-                vals.append(cb["value"])
+        oracle = CpuOracle(cfg)
+        try:
+            for i in range(args.warmup + args.steps):
+                cb = cpu_baseline(cfg, iterations=cfg["hsc_iterations"], oracle=oracle)
+                if i >= args.warmup:
+                    vals.append(cb["value"])
+        finally:
+            oracle.close()
     v = float(np.mean(vals))
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
@@ -596,15 +722,14 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cfg5", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ne", type=int, default=None,
                     help="mesh override (elements per side, a power of two) for profiling a workload's kernel "
                          "shapes on a smaller case; the name gets an @ne suffix")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--profile", nargs="?", const="solve", default=None, choices=["solve", "apply", "inner"],
                     help="solve: only the warm-up and timed HSC solves; apply: only the SG product, FP64 then "
                          "FP32; inner: only the batched inner PCG on the widest level (for ncu captures); "

@@ -55,6 +55,10 @@ typedef enum {
 } sg_status;
 
 enum { SG_F64 = 0, SG_F32 = 1 };                     /* element type of a block */
+/* sg_level_apply only: X and Yout FP32, Yin FP64, products accumulated and
+ * subtracted in FP64 (the level-p products of the mixed preconditioner with
+ * top_level_f64, Algorithm 1). */
+enum { SG_F32_ACC64 = 2 };
 enum { SG_LEGENDRE = 0, SG_HERMITE = 1 };            /* chaos family */
 enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_HSC = 2 };
 
@@ -156,7 +160,9 @@ int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream);
  * pre-correction product B_l (out = l-1, in = l) and the post-correction
  * product C_l (out = l, in = l-1) of Algorithm 1.
  * X: device n x w_in packed; Yin, Yout: device n x w_out packed (may alias);
- * w_d = number of chaos polynomials of degree d. */
+ * w_d = number of chaos polynomials of degree d. dtype SG_F64 or SG_F32 for
+ * all three blocks, or SG_F32_ACC64: X and Yout FP32, Yin FP64 (required, not
+ * aliasing Yout), the sum accumulated in FP64. */
 int sg_level_apply(sg_problem* h, int lvl_out, int lvl_in, const void* X, const void* Yin,
                    void* Yout, int dtype, void* stream);
 
@@ -174,13 +180,17 @@ int sg_vcycle_apply(sg_problem* h, const void* B, void* X, int w, int dtype,
  * fixed 32 MiB array inside the library, which every GPU that loads the
  * library keeps until the process exits. Arguments and results are those of
  * sg_vcycle_apply (B, X: device n x w packed, w <= 1024, dtype SG_F64 or
- * SG_F32); the handle must come from sg_setup as usual. A batch whose buffers
- * exceed the 32 MiB -- about 2 n w + 3 (n/4 + n/16 + ...) w elements -- is
- * rejected with SG_ERR_INVALID_ARG. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current), so
- * make that first call before any stream capture. All calls on a device share
- * the array and it keeps the last call's contents: calls whose GPU work
- * overlaps race. */
+ * SG_F32); the handle must come from sg_setup as usual. The scratch of one
+ * call is, in elements of dtype, 3 n_0 wp + 3 (n_1 + n_2 + ...) wp plus wp
+ * ints, each of these 1 + 3 G blocks rounded up to 256 bytes, where n_g is
+ * the node count of multigrid grid g (n_0 = n, n_1 ~ n/4, ...) and wp is w
+ * rounded up to the vector width (4 columns in FP32, 2 in FP64). A batch whose
+ * scratch exceeds the 32 MiB is rejected with SG_ERR_INVALID_ARG. The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current), so make that first call before any stream
+ * capture; a lookup that fails is retried by the next call. All calls on a
+ * device share the array and it keeps the last call's contents: calls whose
+ * GPU work overlaps race. */
 int sg_vcycle_apply_static(sg_problem* h, const void* B, void* X, int w, int dtype,
                            const sg_prec_opts* opts, void* stream);
 
@@ -247,8 +257,21 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
  * extra shared memory). Allocates two temporary n x P blocks and, if absent,
  * the outer solve buffers; invalidates the handle's cached solve graphs. */
 int sg_autotune(sg_problem* h, void* stream);
+/* Results are cached per problem class (device, n, nnz, M, p, family and the
+ * longest row of the pattern): a later handle of a class already tuned in this
+ * process takes the cached shapes without timing anything. */
 /* Block sizes chosen by sg_autotune (0: not tuned, the built-in choice). */
 int sg_autotune_result(const sg_problem* h, int* threads_f64, int* threads_f32);
+/* Block size chosen for the outer solver's fused product (0: the built-in 256). */
+int sg_autotune_outer_result(const sg_problem* h, int* threads_outer);
+/* sg_autotune_set -- pin the shapes sg_autotune would choose, without timing:
+ * block sizes of the full SG product in FP64 and FP32 and of the outer fused
+ * product (0: the built-in choice; otherwise whole warps, 32..1024 threads,
+ * at most 8 outputs per thread, 4 above 256 threads), and the pair (1) or
+ * gather (0) form of each. SG_ERR_INVALID_ARG for an unusable block size.
+ * Invalidates the handle's cached solve graphs. */
+int sg_autotune_set(sg_problem* h, int threads_f64, int threads_f32, int threads_outer, int pairs_f64,
+                    int pairs_f32, int pairs_outer);
 /* Forms chosen by sg_autotune: 1 the pair form, 0 the gather form, for the
  * full SG product in FP64 and FP32 and for the outer fused product (all 1
  * before tuning). Any pointer may be NULL. */
@@ -279,6 +302,16 @@ int sg_qoi(sg_problem* h, const double* U, double* dQdU, double* q_out, void* st
  * double[M+1] or NULL. */
 int sg_qoi_grad(sg_problem* h, const double* U, const double* Lam, int nparam, const double* W,
                 double* grad, double* hk_out, void* stream);
+
+/* sg_measure_alu_peak -- measured multiply-add rate of the current device in
+ * FP64 (dtype SG_F64) or FP32 (SG_F32): one warm-up and one timed launch of a
+ * kernel made of independent FMA chains (8 per thread, every SM filled),
+ * timed with CUDA events on `stream` (synchronised). iters: chain steps per
+ * thread / 8 (for example 4096 in FP64, 131072 in FP32, about 0.1 s each on a
+ * GB300). flops_per_s: host, receives 2 x FMAs / second. The paper has no
+ * counterpart: this is the roofline denominator of the ALU-bound products,
+ * measured instead of derived from unit counts and clocks. */
+int sg_measure_alu_peak(int dtype, int iters, double* flops_per_s, void* stream);
 
 /* Thread-local message of the last failure ("" if none). */
 const char* sg_last_error(void);

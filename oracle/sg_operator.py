@@ -31,6 +31,18 @@ def sg_apply(A: Sequence[sp.spmatrix], G: Sequence[sp.spmatrix], U: np.ndarray) 
     return Y
 
 
+def sg_apply_rows(A: Sequence[sp.spmatrix], G: Sequence[sp.spmatrix], U: np.ndarray, rows) -> np.ndarray:
+    """Rows ``rows`` of the MAT-VEC of eq. (global-system):
+    ``Y[rows] = sum_k A_k[rows, :] U G_k^T``. Row ``r`` of the product needs
+    only row ``r`` of every ``A_k``, so a sample of rows (or a block of
+    them) is computed without the rest."""
+    rows = np.asarray(rows)
+    Y = np.zeros((len(rows), U.shape[1]))
+    for Ak, Gk in zip(A, G):
+        Y += (Gk @ (Ak[rows] @ U).T).T
+    return Y
+
+
 def global_matrix_chaos_major(A: Sequence[sp.spmatrix], G: Sequence[sp.spmatrix]) -> sp.csr_matrix:
     """Eq. (global-matrix): the block matrix with blocks
     ``K^(j,l) = sum_i c_ijl K_i`` (eq. (global-matrix-block)), unknowns
@@ -78,16 +90,19 @@ def direct_solve(A, G, F: np.ndarray) -> np.ndarray:
     return x.reshape(n, P)
 
 
-def level_apply(A, G, off, lvl_out: int, lvl_in: int, X: np.ndarray) -> np.ndarray:
+def level_apply(A, G, off, lvl_out: int, lvl_in: int, X: np.ndarray, rows=None) -> np.ndarray:
     """Off-diagonal block product between degree levels (Sec. 3,
     eq. (global-matrix-hierarchy)): output rows are the degree-``lvl_out``
     chaos columns, inputs the degree-``lvl_in`` ones; returns
-    ``sum_k A_k X G_k[out, in]^T`` of shape ``n x w_out``."""
+    ``sum_k A_k X G_k[out, in]^T`` of shape ``n x w_out`` (only the spatial
+    rows ``rows`` when given, from the same rows of the ``A_k``)."""
     o0, o1 = off[lvl_out], off[lvl_out + 1]
     i0, i1 = off[lvl_in], off[lvl_in + 1]
-    Y = np.zeros((A[0].shape[0], o1 - o0))
+    nr = A[0].shape[0] if rows is None else len(rows)
+    Y = np.zeros((nr, o1 - o0))
     for Ak, Gk in zip(A, G):
         sub = Gk[o0:o1, i0:i1]
         if sub.nnz:
-            Y += (sub @ (Ak @ X).T).T
+            Ar = Ak if rows is None else Ak[np.asarray(rows)]
+            Y += (sub @ (Ar @ X).T).T
     return Y

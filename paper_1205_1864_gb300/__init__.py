@@ -21,14 +21,15 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (SG_F32, SG_F64, SG_HERMITE, SG_LEGENDRE, SG_PREC_HSC, SG_PREC_MEAN, SG_PREC_NONE, SGError,
+from ._lib import (SG_F32, SG_F32_ACC64, SG_F64, SG_HERMITE, SG_LEGENDRE, SG_PREC_HSC, SG_PREC_MEAN, SG_PREC_NONE, SGError,
                    check)
 
 __all__ = [
     "SGProblem", "sg_setup", "sg_apply", "sg_level_apply", "sg_vcycle_apply", "sg_inner_solve",
     "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_qoi_grad", "prec_opts", "solve_opts",
     "sg_set_scales", "SGQoI", "kl_scales", "kl_chain_weights", "sg_qoi_value_and_grad_batch",
-    "SGError", "SG_F32", "SG_F64", "SG_PREC_HSC", "SG_PREC_MEAN", "SG_PREC_NONE", "SG_LEGENDRE", "SG_HERMITE",
+    "sg_autotune", "sg_autotune_forms", "sg_autotune_shapes", "sg_autotune_set", "sg_measure_alu_peak",
+    "SGError", "SG_F32", "SG_F32_ACC64", "SG_F64", "SG_PREC_HSC", "SG_PREC_MEAN", "SG_PREC_NONE", "SG_LEGENDRE", "SG_HERMITE",
 ]
 
 _DT = {torch.float64: SG_F64, torch.float32: SG_F32}
@@ -160,11 +161,15 @@ def sg_apply(h: SGProblem, U: torch.Tensor, Y: Optional[torch.Tensor] = None) ->
 
 def sg_level_apply(h: SGProblem, lvl_out: int, lvl_in: int, X: torch.Tensor, Yin: Optional[torch.Tensor],
                    Yout: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Yout = Yin - sum_k A_k X G_k[out, in]^T between adjacent degree levels (K2)."""
+    """Yout = Yin - sum_k A_k X G_k[out, in]^T between adjacent degree levels (K2).
+    An FP32 ``X`` with an FP64 ``Yin`` takes the FP64-accumulating product of
+    the mixed preconditioner's top level (``SG_F32_ACC64``, FP32 ``Yout``)."""
+    mixed = X.dtype == torch.float32 and Yin is not None and Yin.dtype == torch.float64
     if Yout is None:
         _, off = h.chaos_table()
         Yout = torch.empty((h.n, int(off[lvl_out + 1] - off[lvl_out])), dtype=X.dtype, device="cuda")
-    check(_lib.LIB.sg_level_apply(h.h, lvl_out, lvl_in, _ptr(X), _ptr(Yin), _ptr(Yout), _DT[X.dtype], _stream()),
+    code = SG_F32_ACC64 if mixed else _DT[X.dtype]
+    check(_lib.LIB.sg_level_apply(h.h, lvl_out, lvl_in, _ptr(X), _ptr(Yin), _ptr(Yout), code, _stream()),
           "sg_level_apply")
     return Yout
 
@@ -237,6 +242,30 @@ def sg_autotune_forms(h: SGProblem):
     a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
     check(_lib.LIB.sg_autotune_forms(h.h, C.byref(a), C.byref(b), C.byref(c)), "sg_autotune_forms")
     return a.value, b.value, c.value
+
+
+def sg_autotune_shapes(h: SGProblem):
+    """All tuned shapes: ``(threads_f64, threads_f32, threads_outer, pairs_f64,
+    pairs_f32, pairs_outer)`` (0 threads: the built-in choice)."""
+    a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
+    check(_lib.LIB.sg_autotune_result(h.h, C.byref(a), C.byref(b)), "sg_autotune_result")
+    check(_lib.LIB.sg_autotune_outer_result(h.h, C.byref(c)), "sg_autotune_outer_result")
+    return (a.value, b.value, c.value) + sg_autotune_forms(h)
+
+
+def sg_autotune_set(h: SGProblem, threads_f64=0, threads_f32=0, threads_outer=0, pairs_f64=1, pairs_f32=1,
+                    pairs_outer=1) -> None:
+    """Pin the SG-product shapes without timing (``sg_autotune_set``)."""
+    check(_lib.LIB.sg_autotune_set(h.h, threads_f64, threads_f32, threads_outer, pairs_f64, pairs_f32, pairs_outer),
+          "sg_autotune_set")
+
+
+def sg_measure_alu_peak(dtype: int = SG_F64, iters: Optional[int] = None) -> float:
+    """Measured FMA throughput of the current device in FLOP/s (FP64 or FP32)."""
+    it = iters if iters is not None else (4096 if dtype == SG_F64 else 131072)
+    out = C.c_double(0.0)
+    check(_lib.LIB.sg_measure_alu_peak(dtype, it, C.byref(out), _stream()), "sg_measure_alu_peak")
+    return out.value
 
 
 class SGBatch:

@@ -13,7 +13,7 @@ SG_OK, SG_ERR_INVALID_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_NOT_SPD, SG_ERR_BREAK
     SG_ERR_NO_CONVERGENCE, SG_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ERR_OOM", 4: "SG_ERR_NOT_SPD",
                 5: "SG_ERR_BREAKDOWN", 6: "SG_ERR_NO_CONVERGENCE", 7: "SG_ERR_UNSUPPORTED"}
-SG_F64, SG_F32 = 0, 1
+SG_F64, SG_F32, SG_F32_ACC64 = 0, 1, 2
 SG_LEGENDRE, SG_HERMITE = 0, 1
 SG_PREC_NONE, SG_PREC_MEAN, SG_PREC_HSC = 0, 1, 2
 SG_MAX_HIST = 1024
@@ -73,10 +73,13 @@ def _load():
         "sg_autotune": (i, [vp, vp]),
         "sg_autotune_result": (i, [vp, P(i), P(i)]),
         "sg_autotune_forms": (i, [vp, P(i), P(i), P(i)]),
+        "sg_autotune_outer_result": (i, [vp, P(i)]),
+        "sg_autotune_set": (i, [vp, i, i, i, i, i, i]),
         "sg_batch_create": (i, [i, P(vp), P(vp)]),
         "sg_batch_solve": (i, [vp, P(vp), P(vp), P(sg_solve_opts), P(sg_solve_stats), vp]),
         "sg_batch_destroy": (None, [vp]),
         "sg_qoi_grad": (i, [vp, vp, vp, i, P(C.c_double), vp, vp, vp]),
+        "sg_measure_alu_peak": (i, [i, i, P(C.c_double), vp]),
         "sg_last_error": (C.c_char_p, []),
         "sg_kernel_launches": (C.c_longlong, []),
         "sg_default_prec_opts": (None, [P(sg_prec_opts)]),
@@ -103,5 +106,6 @@ def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
     return ["sg_setup", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
             "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
+            "sg_autotune_outer_result", "sg_autotune_set",
             "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",
-            "sg_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]
+            "sg_qoi_grad", "sg_measure_alu_peak", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

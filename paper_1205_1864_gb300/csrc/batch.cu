@@ -12,6 +12,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "graph.cuh"
@@ -220,6 +223,34 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
   return r;
 }
 
+// Tuned shapes per problem class: problems with the same device, sizes, chaos
+// space and row lengths run the same launches, so a class is timed once per
+// process and later handles of that class take its shapes without timing.
+struct TuneKey {
+  int dev, n, nnz, M, p, family, max_row;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, n, nnz, M, p, family, max_row) <
+           std::tie(o.dev, o.n, o.nnz, o.M, o.p, o.family, o.max_row);
+  }
+};
+struct TuneVal {
+  int t64, t32, tout, p64, p32, pout;
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune_cache;
+
+static TuneKey tune_key(const sg_problem* h) {
+  return TuneKey{h->device, h->n, h->nnz, h->M, h->p, h->family, h->max_row_nnz};
+}
+
+// A block size the product kernels are instantiated for: whole warps, 32 to
+// 1024 threads, at most 8 outputs per thread (4 above 256 threads).
+static bool valid_block(int threads, int P) {
+  if (threads < 32 || threads > 1024 || threads % 32) return false;
+  const int maxo = (P + threads - 1) / threads;
+  return maxo <= (threads > 256 ? 4 : 8);
+}
+
 }  // namespace sghsc
 
 using namespace sghsc;
@@ -233,9 +264,58 @@ int sg_autotune(sg_problem* h, void* stream) {
     return SG_ERR_INVALID_ARG;
   }
   clear_graphs(h);  // captured graphs hold the old launch shapes
+  const TuneKey key = tune_key(h);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      const TuneVal& v = it->second;
+      h->k1_threads[SG_F64] = v.t64;
+      h->k1_threads[SG_F32] = v.t32;
+      h->outer_threads = v.tout;
+      h->k1_pairs[SG_F64] = v.p64;
+      h->k1_pairs[SG_F32] = v.p32;
+      h->outer_pairs = v.pout;
+      return SG_OK;
+    }
+  }
   SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
   SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
   SG_TRY(autotune_outer(h, (cudaStream_t)stream));
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = TuneVal{h->k1_threads[SG_F64], h->k1_threads[SG_F32], h->outer_threads,
+                              h->k1_pairs[SG_F64],   h->k1_pairs[SG_F32],   h->outer_pairs};
+  return SG_OK;
+}
+
+int sg_autotune_set(sg_problem* h, int threads_f64, int threads_f32, int threads_outer, int pairs_f64,
+                    int pairs_f32, int pairs_outer) {
+  set_error("");
+  if (!h) {
+    set_error("sg_autotune_set: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  for (int t : {threads_f64, threads_f32, threads_outer})
+    if (t != 0 && !valid_block(t, h->P)) {
+      set_error("sg_autotune_set: block size %d not usable for P = %d", t, h->P);
+      return SG_ERR_INVALID_ARG;
+    }
+  clear_graphs(h);
+  h->k1_threads[SG_F64] = threads_f64;
+  h->k1_threads[SG_F32] = threads_f32;
+  h->outer_threads = threads_outer;
+  h->k1_pairs[SG_F64] = pairs_f64 ? 1 : 0;
+  h->k1_pairs[SG_F32] = pairs_f32 ? 1 : 0;
+  h->outer_pairs = pairs_outer ? 1 : 0;
+  return SG_OK;
+}
+
+int sg_autotune_outer_result(const sg_problem* h, int* threads_outer) {
+  if (!h) {
+    set_error("sg_autotune_outer_result: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (threads_outer) *threads_outer = h->outer_threads;
   return SG_OK;
 }
 

@@ -2019,11 +2019,13 @@ static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_B
 
 constexpr int STATIC_MAX_DEVICES = 64;
 static void* g_static_scratch_ptr[STATIC_MAX_DEVICES];
-static cudaError_t g_static_scratch_err[STATIC_MAX_DEVICES];
-static std::once_flag g_static_scratch_once[STATIC_MAX_DEVICES];
+static std::mutex g_static_scratch_mu;
 
-// Device address of g_static_scratch on the current device; resolved once per
-// device (the name is only a host-side stand-in for the device array).
+// Device address of g_static_scratch on the current device (the name is only
+// a host-side stand-in for the device array). A successful lookup is kept for
+// the rest of the process; a failed one is not, so a later call retries it,
+// and the failed call's error is taken off the runtime's error state so that
+// it is not reported again by an unrelated launch check.
 static int static_scratch(void** out) {
   int dev = 0;
   SG_TRY_CUDA(cudaGetDevice(&dev));
@@ -2031,10 +2033,17 @@ static int static_scratch(void** out) {
     set_error("sg_vcycle_apply_static: device ordinal %d not supported", dev);
     return SG_ERR_UNSUPPORTED;
   }
-  std::call_once(g_static_scratch_once[dev], [dev]() {
-    g_static_scratch_err[dev] = cudaGetSymbolAddress(&g_static_scratch_ptr[dev], g_static_scratch);
-  });
-  SG_TRY_CUDA(g_static_scratch_err[dev]);
+  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+  if (!g_static_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      set_error("sg_vcycle_apply_static: cudaGetSymbolAddress failed on device %d: %s", dev, cudaGetErrorString(e));
+      return SG_ERR_CUDA;
+    }
+    g_static_scratch_ptr[dev] = ptr;
+  }
   *out = g_static_scratch_ptr[dev];
   return SG_OK;
 }

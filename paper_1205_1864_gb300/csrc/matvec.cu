@@ -447,14 +447,18 @@ int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream) {
 int sg_level_apply(sg_problem* h, int lvl_out, int lvl_in, const void* X, const void* Yin, void* Yout, int dtype,
                    void* stream) {
   set_error("");
-  if (!h || !X || !Yout || (dtype != SG_F64 && dtype != SG_F32) || lvl_out < 0 || lvl_in < 0 || lvl_out > h->p ||
-      lvl_in > h->p || (lvl_out - lvl_in != 1 && lvl_in - lvl_out != 1)) {
+  if (!h || !X || !Yout || (dtype != SG_F64 && dtype != SG_F32 && dtype != SG_F32_ACC64) || lvl_out < 0 ||
+      lvl_in < 0 || lvl_out > h->p || lvl_in > h->p || (lvl_out - lvl_in != 1 && lvl_in - lvl_out != 1) ||
+      (dtype == SG_F32_ACC64 && (!Yin || Yin == (const void*)Yout))) {
     set_error("sg_level_apply: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
   const EdgeList& E = lvl_in > lvl_out ? h->pre[lvl_in] : h->post[lvl_out];
   const int win = h->off[lvl_in + 1] - h->off[lvl_in];
   const int wout = h->off[lvl_out + 1] - h->off[lvl_out];
+  if (dtype == SG_F32_ACC64)   // the level-p products of the mixed preconditioner with an FP64 top level
+    return launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, X, win, win, E, false, Yin, wout, -1.0, 1.0, Yout,
+                               wout, (cudaStream_t)stream);
   return launch_block_matvec(h, dtype, dtype, dtype, dtype, X, win, win, E, false, Yin, wout, -1.0, 1.0, Yout, wout,
                              (cudaStream_t)stream);
 }

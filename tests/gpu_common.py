@@ -42,3 +42,31 @@ def random_csr(n, seed, max_row=14, empty_every=7):
     m = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
     m.sort_indices()
     return m.indptr.astype(np.int32), m.indices.astype(np.int32)
+
+
+def oracle_rel_residual(A, G, F, U, threads=16, block=8192):
+    """``||F - sum_k A_k U G_k^T|| / ||F||`` in FP64 by the oracle, one block of
+    spatial rows per task (row ``r`` of the product needs only row ``r`` of
+    each ``A_k``), the blocks on a thread pool (scipy's sparse products
+    release the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = F.shape[0]
+    starts = list(range(0, n, block))
+
+    def part(s):
+        rows = np.arange(s, min(s + block, n))
+        R = F[rows] - so.sg_apply_rows(A, G, U, rows)
+        return float(np.sum(R * R))
+
+    with ThreadPoolExecutor(threads) as ex:
+        ss = sum(ex.map(part, starts))
+    return float(np.sqrt(ss) / np.linalg.norm(F))
+
+
+def sample_rows(n, count=48, seed=0):
+    """Sorted spatial rows for element checks at full size: the first and last
+    rows, the rows next to them and a seeded spread over the rest."""
+    rng = np.random.default_rng(seed)
+    fixed = [0, 1, n // 2, n - 2, n - 1]
+    rest = rng.choice(n, size=max(count - len(fixed), 0), replace=False)
+    return np.unique(np.concatenate([fixed, rest]).astype(np.int64))

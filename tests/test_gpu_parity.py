@@ -391,13 +391,65 @@ def test_error_paths(lib):
         lib.SGProblem(8, 8, 2, 2, prob.rowptr, prob.colidx, prob.vals)
 
 
-def test_indefinite_operator_reports_not_spd_or_breakdown(lib):
-    """sigma far beyond ellipticity: the solver stops with a status, it does not hang."""
-    prob, A, G, off = problem(16, 2, 3, sigma=3.0)
-    h = lib.SGProblem.from_inputs(prob, 3)
+def test_indefinite_operator_reports_breakdown(lib):
+    """sigma far beyond ellipticity (Sec. 6: above CoV 55% A need not be
+    positive definite): the oracle finds a negative eigenvalue of the
+    assembled matrix and its CG meets p^T A p <= 0; the GPU solve must stop
+    with SG_ERR_BREAKDOWN, not report success, and leave the handle usable."""
+    prob, A, G, off = problem(8, 2, 3, sigma=3.0)
+    K = so.global_matrix_space_major(A, G).toarray()
+    assert np.linalg.eigvalsh(K)[0] < 0
     F = S.make_rhs(prob, 3)
-    U, st = lib.sg_solve(h, _t(F), lib.solve_opts(precond=lib.SG_PREC_NONE, maxit=400), raise_on_error=False)
-    assert st.status in (0, 5, 6)
+    _, info = krylov.fcg(lambda X: so.sg_apply(A, G, X), F, None, tol=1e-8, maxit=400)
+    assert info.get("breakdown") and not info["converged"]
+    h = lib.SGProblem.from_inputs(prob, 3)
+    for precond in (lib.SG_PREC_NONE, lib.SG_PREC_MEAN, lib.SG_PREC_HSC):
+        U, st = lib.sg_solve(h, _t(F), lib.solve_opts(precond=precond, maxit=400), raise_on_error=False)
+        if precond == lib.SG_PREC_NONE:
+            assert st.status == 5, st.status
+            assert st.iterations <= info["iters"] + 1
+        else:
+            assert st.status in (4, 5), st.status
+    prob2, A2, G2, off2 = problem(8, 2, 3, sigma=0.3)
+    h2 = lib.SGProblem.from_inputs(prob2, 3)
+    U, st = lib.sg_solve(h2, _t(S.make_rhs(prob2, 3)), lib.solve_opts())
+    assert st.status == 0
+
+
+def test_null_pointers_rejected_before_any_launch(lib):
+    """Every entry point rejects a NULL handle or buffer with SG_ERR_INVALID_ARG."""
+    import ctypes as C
+
+    import torch
+    from paper_1205_1864_gb300 import _lib
+    prob, A, G, off = problem(8, 2, 2)
+    h = lib.SGProblem.from_inputs(prob, 2)
+    F = _t(S.make_rhs(prob, 2))
+    U = torch.empty_like(F)
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    o = lib.solve_opts()
+    st = _lib.sg_solve_stats()
+    fp, up = C.c_void_p(F.data_ptr()), C.c_void_p(U.data_ptr())
+    LIB = _lib.LIB
+    assert LIB.sg_solve(h.h, None, up, C.byref(o), C.byref(st), s) == 1
+    assert LIB.sg_solve(h.h, fp, None, C.byref(o), C.byref(st), s) == 1
+    assert LIB.sg_solve(None, fp, up, C.byref(o), C.byref(st), s) == 1
+    assert LIB.sg_solve(h.h, fp, up, None, C.byref(st), s) == 1
+    assert LIB.sg_apply(h.h, None, up, 0, s) == 1
+    assert LIB.sg_apply(None, fp, up, 0, s) == 1
+    assert LIB.hsc_precond_apply(h.h, None, up, C.byref(o.prec), s) == 1
+    assert LIB.mean_precond_apply(h.h, fp, None, C.byref(o.prec), s) == 1
+    assert LIB.sg_level_apply(h.h, 0, 1, None, None, up, 0, s) == 1
+    assert LIB.sg_vcycle_apply(h.h, None, up, 1, 0, C.byref(o.prec), s) == 1
+    assert LIB.sg_inner_solve(h.h, fp, None, 1, 0, C.byref(o.prec), None, s) == 1
+    assert LIB.sg_qoi(h.h, None, None, up, s) == 1
+    out = C.c_void_p()
+    assert LIB.sg_setup(None, 2, 2, 0, prob.n, len(prob.colidx), None, None, None, None, C.byref(out)) == 1
+    assert LIB.sg_batch_create(1, None, C.byref(out)) == 1
+    assert LIB.sg_autotune(None, s) == 1
+    # nothing was launched by the rejected calls: the handle still solves
+    U2, st2 = lib.sg_solve(h, F, lib.solve_opts())
+    assert st2.status == 0
 
 
 # ------------------------------------------------------------------------ K7

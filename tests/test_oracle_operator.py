@@ -66,3 +66,25 @@ def test_level_blocks_sum_to_operator_without_diagonal():
             if abs(lo - li) == 1:
                 Y2[:, off[lo]:off[lo + 1]] += so.level_apply(A, G, off, lo, li, U[:, off[li]:off[li + 1]])
     assert np.allclose(Y, Y2, atol=1e-13)
+
+
+def test_row_sampled_products_match_the_explicit_global_matrix():
+    """The row-restricted products (used to check single rows of the
+    full-size GPU products) against rows of the assembled Kronecker matrix
+    sum_k A_k (x) G_k and of its level blocks (eq. (global-matrix-hierarchy))."""
+    prob, A, G, off = _small(8, 3, 3)
+    n, P = prob.n, G[0].shape[0]
+    U = S.random_block(n, P, seed=21)
+    rows = np.array([0, 5, 17, n - 1, 17])
+    Ks = so.global_matrix_space_major(A, G)
+    y = (Ks @ U.ravel()).reshape(n, P)
+    Yr = so.sg_apply_rows(A, G, U, rows)
+    assert np.allclose(Yr, y[rows], rtol=0, atol=1e-13 * np.abs(y).max())
+    K = so.global_matrix_chaos_major(A, G).toarray()
+    p = len(off) - 2
+    for lo, li in [(p - 1, p), (p, p - 1), (0, 1)]:
+        X = S.random_block(n, off[li + 1] - off[li], seed=lo + 7 * li)
+        blk = K[off[lo] * n:off[lo + 1] * n, off[li] * n:off[li + 1] * n]
+        y = (blk @ X.T.ravel()).reshape(off[lo + 1] - off[lo], n).T
+        assert np.allclose(so.level_apply(A, G, off, lo, li, X, rows=rows), y[rows], rtol=0,
+                           atol=1e-13 * np.abs(y).max())
