@@ -60,12 +60,13 @@ enum { SG_F64 = 0, SG_F32 = 1 };                     /* element type of a block 
  * top_level_f64, Algorithm 1). */
 enum { SG_F32_ACC64 = 2 };
 enum { SG_LEGENDRE = 0, SG_HERMITE = 1 };            /* chaos family */
-enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_HSC = 2 };
+enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_HSC = 2, SG_PREC_BGS = 3 };
 
 /* Uniform grid of ne_x x ne_y bilinear (Q1) elements on the unit square with
  * Dirichlet nodes eliminated: n = (ne_x-1)(ne_y-1) interior nodes, numbered
- * lexicographically with x fastest (Sec. 6 discretisation). The multigrid
- * inner preconditioner needs ne_x == ne_y, a power of two. */
+ * lexicographically with x fastest (Sec. 6 discretisation). The inner solves
+ * need it (and the 9-point pattern of the Q1 stencil); the multigrid inner
+ * preconditioner also needs ne_x == ne_y, a power of two. */
 typedef struct { int ne_x, ne_y; } sg_mesh;
 
 /* Options of one preconditioner application (Algorithm 1, Sec. 4; inner
@@ -80,11 +81,18 @@ typedef struct {
   int inner_fixed_iters;  /* > 0: run exactly this many inner iterations, no tolerance test */
   int nu;                 /* V-cycle: weighted-Jacobi sweeps before and after */
   double omega;           /* V-cycle: Jacobi damping */
+  int m0;                 /* mean-value preconditioner M_0 of the inner PCG (Sec. 5 leaves it
+                             open): SG_M0_VCYCLE one multigrid V-cycle (needs a power-of-two
+                             square mesh), SG_M0_DIAG the diagonal of A_0 (any mesh given to
+                             sg_setup whose pattern is the 9-point Q1 stencil) */
 } sg_prec_opts;
+
+enum { SG_M0_VCYCLE = 0, SG_M0_DIAG = 1 };
 
 /* Options of the outer flexible CG (Sec. 5-6). */
 typedef struct {
-  int precond;            /* SG_PREC_NONE, SG_PREC_MEAN (I (x) A_0^{-1}, Sec. 6) or SG_PREC_HSC */
+  int precond;            /* SG_PREC_NONE, SG_PREC_MEAN (I (x) A_0^{-1}, Sec. 6), SG_PREC_HSC
+                             (Algorithm 1) or SG_PREC_BGS (block symmetric Gauss-Seidel, Sec. 6) */
   sg_prec_opts prec;
   double tol;             /* stop at ||r||_2 <= tol ||f||_2 (recursive residual) */
   int maxit;
@@ -234,6 +242,17 @@ int sg_inner_path(const sg_problem* h, int w, int dtype);
 int hsc_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts,
                       void* stream);
 
+/* bgs_precond_apply -- block symmetric Gauss-Seidel with zero initial guess
+ * (M_bGS, the comparison preconditioner of Sec. 6): a forward and a backward
+ * sweep over the chaos blocks K^(j,l) = sum_k c_kjl A_k of eq. (global-matrix)
+ * in the graded chaos order, each diagonal block (A_0) solved by the batched
+ * inner PCG. Blocks of one degree do not couple, so each sweep runs level by
+ * level, a level's columns in one batch; the top level is solved once (its
+ * backward step equals its forward one). Precision options as for
+ * hsc_precond_apply (top_level_f64: the level-p forward product in FP64).
+ * R, Z: device n x P row-major FP64; must not alias. */
+int bgs_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts, void* stream);
+
 /* mean_precond_apply -- mean-based preconditioner I (x) A_0^{-1} (Sec. 6,
  * Powell-Elman) with the same inner PCG. R, Z: device n x P FP64. */
 int mean_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts,
@@ -312,6 +331,20 @@ int sg_qoi_grad(sg_problem* h, const double* U, const double* Lam, int nparam, c
  * counterpart: this is the roofline denominator of the ALU-bound products,
  * measured instead of derived from unit counts and clocks. */
 int sg_measure_alu_peak(int dtype, int iters, double* flops_per_s, void* stream);
+
+/* The gradient workload's parameterisation (the paper has no gradient): the
+ * handle holds the KL matrices with unit parameters (A_0 = L_h, A_k = Phi_k,
+ * i.e. assembled with a_mean = 1, sigma = 1, s_k = 1) and
+ * theta = (a_mean, sigma, s_1..s_M), host double[M+2], finite and nonzero,
+ * a_mean > 0, makes A_0 = a_mean L_h and A_k = sigma s_k Phi_k.
+ * sg_kl_set_theta -- sg_set_scales with those factors (synchronises).
+ * sg_kl_qoi_grad -- dQ/dtheta, device double[M+2], from the forward solution
+ * U and the adjoint solution Lam (device n x P FP64) of the current theta:
+ * dQ/dtheta_t = -sum_k (d log scale_k / d theta_t) <Lam, A_k U G_k^T>_F
+ * (sg_qoi_grad with those weights); hk_out as there. */
+int sg_kl_set_theta(sg_problem* h, const double* theta);
+int sg_kl_qoi_grad(sg_problem* h, const double* U, const double* Lam, const double* theta, double* grad,
+                   double* hk_out, void* stream);
 
 /* Thread-local message of the last failure ("" if none). */
 const char* sg_last_error(void);

@@ -100,6 +100,115 @@ def hsc_apply(A, G, off, R: np.ndarray, general: bool = False,
     return u
 
 
+def schur_reduced_solve(A, G, off, F: np.ndarray, tol: float = 1e-8, maxit: int = 500):
+    """The a-priori reduction of Sec. 5, eq. (global-Schur-system): eliminate
+    the degree-p unknowns ``u_P^P`` and iterate on
+    ``S_{p-1} u_{p-1} = g_{p-1}`` with ``S_{p-1} = A_{p-1} - B_p D_p^{-1} C_p``
+    and ``g_{p-1} = f^{p-1} - B_p D_p^{-1} f^p`` (exact ``D_p^{-1}``), by
+    flexible CG preconditioned with Algorithm 1 on the levels ``1..p-1``;
+    then recover ``u^p = D_p^{-1} (f^p - C_p u_{p-1})``. Returns the full
+    ``n x P`` solution and the CG information of the reduced iteration."""
+    from .krylov import fcg
+    p = len(off) - 2
+    if p < 1:
+        raise ValueError("the reduction needs p >= 1")
+    lo = off[p]
+    a0 = A0Solver(A[0])
+    dsolve = _diag_block_solver(A, G, off[p], off[p + 1], False, a0)
+    sub_G = [g[:lo, :lo] for g in G]
+    off_r = off[:p + 1]
+
+    def S(V):
+        y = sg_apply_sub(A, sub_G, V)
+        y -= _offdiag_apply(A, G, slice(0, lo), slice(lo, off[p + 1]),
+                            dsolve(_offdiag_apply(A, G, slice(lo, off[p + 1]), slice(0, lo), V)))
+        return y
+
+    g = F[:, :lo] - _offdiag_apply(A, G, slice(0, lo), slice(lo, off[p + 1]), dsolve(F[:, lo:]))
+    u_r, info = fcg(S, g, lambda R: hsc_apply(A, sub_G, off_r, R, a0solve=a0), tol=tol, maxit=maxit)
+    U = np.zeros_like(F)
+    U[:, :lo] = u_r
+    U[:, lo:] = dsolve(F[:, lo:] - _offdiag_apply(A, G, slice(lo, off[p + 1]), slice(0, lo), u_r))
+    return U, info
+
+
+def sg_apply_sub(A, G, U):
+    """``sum_k A_k U G_k^T`` (the MAT-VEC of eq. (global-system)) for blocks
+    ``G_k`` of any square size."""
+    Y = np.zeros((A[0].shape[0], U.shape[1]))
+    for Ak, Gk in zip(A, G):
+        if Gk.nnz:
+            Y += (Gk @ (Ak @ U).T).T
+    return Y
+
+
+def bgs_apply(A, G, R: np.ndarray, dsolve: Optional[Callable[[int, np.ndarray], np.ndarray]] = None) -> np.ndarray:
+    """Block symmetric Gauss-Seidel with zero initial guess, ``M_bGS`` of
+    Sec. 6 (the paper's main comparison preconditioner): the blocks are the
+    ``P x P`` blocks ``K^(j,l) = sum_k c_kjl A_k`` of eq. (global-matrix), one
+    per pair of chaos indices, swept in the chaos order, forward
+    ``j = 0..P-1`` and then backward ``j = P-1..0``:
+
+        forward   u_j = K_jj^{-1} (r_j - sum_{l<j} K_jl u_l)
+        backward  u_j = K_jj^{-1} (r_j - sum_{l<j} K_jl u_l - sum_{l>j} K_jl u_l)
+
+    where the backward sweep reads the forward values for ``l < j`` and its
+    own new values for ``l > j``. ``dsolve(j, x)`` replaces the exact
+    ``K_jj^{-1}`` (inexact inner solves)."""
+    n, P = R.shape
+    Gd = [g.toarray() for g in G]
+
+    def block(j, l):
+        out = None
+        for Ak, Gk in zip(A, Gd):
+            c = Gk[j, l]
+            if c != 0.0:
+                out = c * Ak if out is None else out + c * Ak
+        return out
+
+    if dsolve is None:
+        lus = {}
+
+        def dsolve(j, x):
+            key = tuple(Gk[j, j] for Gk in Gd)
+            if key not in lus:
+                lus[key] = spla.splu(sp.csc_matrix(block(j, j)))
+            return lus[key].solve(np.ascontiguousarray(x))
+
+    coupled = [[l for l in range(P) if l != j and any(Gk[j, l] != 0.0 for Gk in Gd)] for j in range(P)]
+    u = np.zeros((n, P))
+    for j in range(P):
+        t = R[:, j].copy()
+        for l in coupled[j]:
+            if l < j:
+                t -= block(j, l) @ u[:, l]
+        u[:, j] = np.asarray(dsolve(j, t)).reshape(n)
+    fwd = u.copy()
+    for j in range(P - 1, -1, -1):
+        t = R[:, j].copy()
+        for l in coupled[j]:
+            t -= block(j, l) @ (fwd[:, l] if l < j else u[:, l])
+        u[:, j] = np.asarray(dsolve(j, t)).reshape(n)
+    return u
+
+
+def bgs_dense(K: np.ndarray, n: int, P: int) -> np.ndarray:
+    """``M_bGS`` as a dense matrix (chaos-major ``K``): symmetric Gauss-Seidel
+    with zero initial guess is ``(D + U)^{-1} D (D + L)^{-1}`` for the block
+    diagonal ``D`` and the strictly lower / upper block parts ``L``, ``U``."""
+    D = np.zeros_like(K)
+    Lo = np.zeros_like(K)
+    for j in range(P):
+        for l in range(P):
+            blk = K[j * n:(j + 1) * n, l * n:(l + 1) * n]
+            if j == l:
+                D[j * n:(j + 1) * n, l * n:(l + 1) * n] = blk
+            elif l < j:
+                Lo[j * n:(j + 1) * n, l * n:(l + 1) * n] = blk
+    Up = K - D - Lo
+    return np.linalg.solve(D + Up, D @ np.linalg.inv(D + Lo))
+
+
 def mean_apply(A, R: np.ndarray, a0solve: Optional[A0Solver] = None) -> np.ndarray:
     """Mean-based preconditioner ``M_m = I (x) A_0^{-1}`` (Sec. 6): one exact
     mean-value solve per chaos column."""

@@ -21,13 +21,13 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (SG_F32, SG_F32_ACC64, SG_F64, SG_HERMITE, SG_LEGENDRE, SG_PREC_HSC, SG_PREC_MEAN, SG_PREC_NONE, SGError,
-                   check)
+from ._lib import (SG_F32, SG_F32_ACC64, SG_F64, SG_HERMITE, SG_LEGENDRE, SG_M0_DIAG, SG_M0_VCYCLE, SG_PREC_BGS,
+                   SG_PREC_HSC, SG_PREC_MEAN, SG_PREC_NONE, SGError, check)
 
 __all__ = [
     "SGProblem", "sg_setup", "sg_apply", "sg_level_apply", "sg_vcycle_apply", "sg_inner_solve",
-    "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_qoi_grad", "prec_opts", "solve_opts",
-    "sg_set_scales", "SGQoI", "kl_scales", "kl_chain_weights", "sg_qoi_value_and_grad_batch",
+    "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "SG_PREC_BGS", "SG_M0_VCYCLE", "SG_M0_DIAG", "sg_solve", "sg_qoi", "sg_qoi_grad", "prec_opts", "solve_opts",
+    "sg_set_scales", "SGQoI", "SGGradBatch", "sg_kl_set_theta", "sg_kl_qoi_grad", "sg_qoi_value_and_grad_batch",
     "sg_autotune", "sg_autotune_forms", "sg_autotune_shapes", "sg_autotune_set", "sg_measure_alu_peak",
     "SGError", "SG_F32", "SG_F32_ACC64", "SG_F64", "SG_PREC_HSC", "SG_PREC_MEAN", "SG_PREC_NONE", "SG_LEGENDRE", "SG_HERMITE",
 ]
@@ -199,6 +199,14 @@ def hsc_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torc
     return Z
 
 
+def bgs_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Z = M_bGS R (block symmetric Gauss-Seidel, zero initial guess)."""
+    Z = torch.empty_like(R) if Z is None else Z
+    o = opts or prec_opts()
+    check(_lib.LIB.bgs_precond_apply(h.h, _ptr(R), _ptr(Z), C.byref(o), _stream()), "bgs_precond_apply")
+    return Z
+
+
 def mean_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Z = (I (x) A_0^{-1}) R with the inner PCG."""
     Z = torch.empty_like(R) if Z is None else Z
@@ -338,25 +346,27 @@ def sg_set_scales(h: SGProblem, scale) -> None:
 # Quantity of interest Q = E[int u^2] and its adjoint gradient (K7)
 # ---------------------------------------------------------------------------
 
-def kl_scales(theta) -> np.ndarray:
-    """Scales of A_0..A_M for theta = (a_mean, sigma, s_1..s_M), relative to
-    matrices assembled with a_mean = 1, sigma = 1, s_k = 1: A_0 = a_mean L_h,
-    A_k = sigma s_k Phi_k."""
-    t = np.asarray(theta, dtype=np.float64)
-    return np.concatenate([[t[0]], t[1] * t[2:]])
+def _theta_arg(h: SGProblem, theta) -> np.ndarray:
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+    if th.shape != (h.M + 2,):
+        raise ValueError(f"theta must have M+2 = {h.M + 2} entries (a_mean, sigma, s_1..s_M)")
+    return th
 
 
-def kl_chain_weights(theta) -> np.ndarray:
-    """W[t][k] = -d log(scale_k) / d theta_t, so that
-    dQ/dtheta_t = sum_k W[t][k] <Lam, A_k U G_k^T>."""
-    t = np.asarray(theta, dtype=np.float64)
-    M = t.shape[0] - 2
-    W = np.zeros((M + 2, M + 1))
-    W[0, 0] = -1.0 / t[0]
-    W[1, 1:] = -1.0 / t[1]
-    for k in range(M):
-        W[2 + k, 1 + k] = -1.0 / t[2 + k]
-    return W
+def sg_kl_set_theta(h: SGProblem, theta) -> None:
+    """A_0 = a_mean L_h, A_k = sigma s_k Phi_k for theta = (a_mean, sigma,
+    s_1..s_M) on a handle holding the unit-parameter matrices."""
+    th = _theta_arg(h, theta)
+    check(_lib.LIB.sg_kl_set_theta(h.h, th.ctypes.data_as(C.POINTER(C.c_double))), "sg_kl_set_theta")
+
+
+def sg_kl_qoi_grad(h: SGProblem, U: torch.Tensor, Lam: torch.Tensor, theta) -> torch.Tensor:
+    """dQ/dtheta (device, M+2) from the forward and adjoint solutions."""
+    th = _theta_arg(h, theta)
+    grad = torch.empty(h.M + 2, dtype=torch.float64, device="cuda")
+    check(_lib.LIB.sg_kl_qoi_grad(h.h, _ptr(U), _ptr(Lam), th.ctypes.data_as(C.POINTER(C.c_double)), _ptr(grad),
+                                  None, _stream()), "sg_kl_qoi_grad")
+    return grad
 
 
 class SGQoI(torch.autograd.Function):
@@ -365,13 +375,13 @@ class SGQoI(torch.autograd.Function):
     Forward: one preconditioned solve and the mass contraction. Backward: the
     operator is symmetric, so the adjoint Lam solves the same system with the
     right-hand side dQ/du = 2 (M_h (x) I) u; the gradient is the fused K7
-    contraction sum_k W[t][k] <Lam, A_k U G_k^T>. The handle must hold the
-    unit-parameter matrices (a_mean = 1, sigma = 1, s_k = 1)."""
+    contraction (sg_kl_qoi_grad). The handle must hold the unit-parameter
+    matrices (a_mean = 1, sigma = 1, s_k = 1)."""
 
     @staticmethod
     def forward(ctx, theta, h, F, opts):
         th = theta.detach().double().cpu().numpy()
-        sg_set_scales(h, kl_scales(th))
+        sg_kl_set_theta(h, th)
         U, _ = sg_solve(h, F, opts)
         q, dq = sg_qoi(h, U)
         ctx.h, ctx.opts, ctx.th = h, opts, th
@@ -382,15 +392,60 @@ class SGQoI(torch.autograd.Function):
     def backward(ctx, gQ):
         U, dq = ctx.saved_tensors
         h = ctx.h
-        sg_set_scales(h, kl_scales(ctx.th))
+        sg_kl_set_theta(h, ctx.th)
         Lam, _ = sg_solve(h, dq, ctx.opts)
-        grad, _ = sg_qoi_grad(h, U, Lam, kl_chain_weights(ctx.th))
+        grad = sg_kl_qoi_grad(h, U, Lam, ctx.th)
         return (gQ.to(grad.dtype) * grad).to(gQ.dtype), None, None, None
 
 
+class SGGradBatch:
+    """Q and dQ/dtheta for a batch of parameter sets, batched on the device:
+    ``count`` handles of the same unit-parameter problem, each set to one
+    theta, solved together in one graph launch (SGBatch) for the forward
+    solves and in a second one for the adjoint solves, then the QoI and the K7
+    contraction per set."""
+
+    def __init__(self, ne_x: int, ne_y: int, M: int, p: int, rowptr, colidx, vals, mass, count: int,
+                 family: int = SG_LEGENDRE):
+        self.count = count
+        self.hs = [SGProblem(ne_x, ne_y, M, p, rowptr, colidx, vals, mass, family) for _ in range(count)]
+        self.batch = SGBatch(self.hs)
+        self.M = M
+
+    @classmethod
+    def from_inputs(cls, prob, p: int, count: int, family: int = SG_LEGENDRE) -> "SGGradBatch":
+        return cls(prob.ne, prob.ne, prob.M, p, prob.rowptr, prob.colidx, prob.vals, prob.mass, count, family)
+
+    def autotune(self):
+        """Tune the first handle; the others share its problem class (cached)."""
+        for h in self.hs:
+            sg_autotune(h)
+
+    def value_and_grad(self, thetas, F: torch.Tensor, opts=None):
+        """``(Q[count], dQ/dtheta[count, M+2])`` on the device for the rows of
+        ``thetas``; ``F`` is the right-hand side shared by every set."""
+        th = np.asarray(thetas, dtype=np.float64)
+        if th.shape != (self.count, self.M + 2):
+            raise ValueError(f"thetas must have shape ({self.count}, {self.M + 2})")
+        o = opts or solve_opts()
+        for h, t in zip(self.hs, th):
+            sg_kl_set_theta(h, t)
+        Us, _ = self.batch.solve([F] * self.count, o)
+        qs, dqs = zip(*[sg_qoi(h, U) for h, U in zip(self.hs, Us)])
+        Lams, _ = self.batch.solve(list(dqs), o)
+        grads = [sg_kl_qoi_grad(h, U, Lam, t) for h, U, Lam, t in zip(self.hs, Us, Lams, th)]
+        return torch.cat(qs), torch.stack(grads)
+
+    def close(self):
+        self.batch.close()
+        for h in self.hs:
+            h.close()
+
+
 def sg_qoi_value_and_grad_batch(h: SGProblem, thetas, F: torch.Tensor, opts=None):
-    """Q and dQ/dtheta for a batch of parameter sets (rows of ``thetas``),
-    one forward and one adjoint solve per set on the same handle."""
+    """Q and dQ/dtheta for a batch of parameter sets (rows of ``thetas``) on
+    one handle, one forward and one adjoint solve per set through SGQoI (the
+    autograd path); SGGradBatch runs the same sets batched on the device."""
     o = opts or solve_opts()
     out_q, out_g = [], []
     for th in np.asarray(thetas, dtype=np.float64):

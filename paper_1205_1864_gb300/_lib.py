@@ -15,7 +15,8 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ER
                 5: "SG_ERR_BREAKDOWN", 6: "SG_ERR_NO_CONVERGENCE", 7: "SG_ERR_UNSUPPORTED"}
 SG_F64, SG_F32, SG_F32_ACC64 = 0, 1, 2
 SG_LEGENDRE, SG_HERMITE = 0, 1
-SG_PREC_NONE, SG_PREC_MEAN, SG_PREC_HSC = 0, 1, 2
+SG_PREC_NONE, SG_PREC_MEAN, SG_PREC_HSC, SG_PREC_BGS = 0, 1, 2, 3
+SG_M0_VCYCLE, SG_M0_DIAG = 0, 1
 SG_MAX_HIST = 1024
 
 
@@ -25,7 +26,8 @@ class sg_mesh(C.Structure):
 
 class sg_prec_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("top_level_f64", C.c_int), ("inner_tol", C.c_double),
-                ("inner_maxit", C.c_int), ("inner_fixed_iters", C.c_int), ("nu", C.c_int), ("omega", C.c_double)]
+                ("inner_maxit", C.c_int), ("inner_fixed_iters", C.c_int), ("nu", C.c_int), ("omega", C.c_double),
+                ("m0", C.c_int)]
 
 
 class sg_solve_opts(C.Structure):
@@ -68,6 +70,7 @@ def _load():
         "sg_inner_path": (i, [vp, i, i]),
         "hsc_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "mean_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
+        "bgs_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "sg_solve": (i, [vp, vp, vp, P(sg_solve_opts), P(sg_solve_stats), vp]),
         "sg_qoi": (i, [vp, vp, vp, vp, vp]),
         "sg_autotune": (i, [vp, vp]),
@@ -80,6 +83,8 @@ def _load():
         "sg_batch_destroy": (None, [vp]),
         "sg_qoi_grad": (i, [vp, vp, vp, i, P(C.c_double), vp, vp, vp]),
         "sg_measure_alu_peak": (i, [i, i, P(C.c_double), vp]),
+        "sg_kl_set_theta": (i, [vp, P(C.c_double)]),
+        "sg_kl_qoi_grad": (i, [vp, vp, vp, P(C.c_double), vp, vp, vp]),
         "sg_last_error": (C.c_char_p, []),
         "sg_kernel_launches": (C.c_longlong, []),
         "sg_default_prec_opts": (None, [P(sg_prec_opts)]),
@@ -105,7 +110,7 @@ def check(status: int, where: str):
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
     return ["sg_setup", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
-            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
+            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
             "sg_autotune_outer_result", "sg_autotune_set",
             "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",
-            "sg_qoi_grad", "sg_measure_alu_peak", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]
+            "sg_qoi_grad", "sg_measure_alu_peak", "sg_kl_set_theta", "sg_kl_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

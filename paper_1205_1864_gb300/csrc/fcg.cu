@@ -105,6 +105,7 @@ static double lanczos_kappa(const double* alpha, const double* beta, int m) {
 static int precond(sg_problem* h, int kind, const double* r, double* z, const sg_prec_opts& o, cudaStream_t s) {
   if (kind == SG_PREC_HSC) return hsc_apply_impl(h, r, z, o, s);
   if (kind == SG_PREC_MEAN) return mean_apply_impl(h, r, z, o, s);
+  if (kind == SG_PREC_BGS) return bgs_apply_impl(h, r, z, o, s);
   SG_TRY_CUDA(cudaMemcpyAsync(z, r, (size_t)h->n * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return SG_OK;
 }
@@ -172,8 +173,8 @@ int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
 
 std::string opts_key(const sg_prec_opts& o) {
   char buf[256];
-  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g", o.precision, o.top_level_f64, o.inner_tol,
-           o.inner_maxit, o.inner_fixed_iters, o.nu, o.omega);
+  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d", o.precision, o.top_level_f64,
+           o.inner_tol, o.inner_maxit, o.inner_fixed_iters, o.nu, o.omega, o.m0);
   return buf;
 }
 
@@ -264,7 +265,8 @@ namespace sghsc {
 
 int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts) {
   if (!h || !opts || opts->maxit < 1 || !(opts->tol >= 0.0) ||
-      (opts->precond != SG_PREC_NONE && opts->precond != SG_PREC_MEAN && opts->precond != SG_PREC_HSC)) {
+      (opts->precond != SG_PREC_NONE && opts->precond != SG_PREC_MEAN && opts->precond != SG_PREC_HSC &&
+       opts->precond != SG_PREC_BGS)) {
     set_error("sg_solve: invalid options");
     return SG_ERR_INVALID_ARG;
   }
@@ -274,10 +276,7 @@ int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts) {
       return SG_ERR_INVALID_ARG;
     }
     SG_TRY(check_prec_opts(opts->prec));
-    if (h->grids.empty()) {
-      set_error("sg_solve: the preconditioners need the multigrid hierarchy (power-of-two square mesh)");
-      return SG_ERR_UNSUPPORTED;
-    }
+    SG_TRY(check_inner_support(h, opts->prec, "sg_solve"));
   }
   return SG_OK;
 }
@@ -290,7 +289,8 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
              void* stream) {
   set_error("");
   if (!h || !F || !U || !opts || F == U || opts->maxit < 1 || !(opts->tol >= 0.0) ||
-      (opts->precond != SG_PREC_NONE && opts->precond != SG_PREC_MEAN && opts->precond != SG_PREC_HSC)) {
+      (opts->precond != SG_PREC_NONE && opts->precond != SG_PREC_MEAN && opts->precond != SG_PREC_HSC &&
+       opts->precond != SG_PREC_BGS)) {
     set_error("sg_solve: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
@@ -300,10 +300,7 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
       return SG_ERR_INVALID_ARG;
     }
     SG_TRY(check_prec_opts(opts->prec));
-    if (h->grids.empty()) {
-      set_error("sg_solve: the preconditioners need the multigrid hierarchy (power-of-two square mesh)");
-      return SG_ERR_UNSUPPORTED;
-    }
+    SG_TRY(check_inner_support(h, opts->prec, "sg_solve"));
   }
   return solve_impl(h, F, U, *opts, stats, (cudaStream_t)stream);
 }

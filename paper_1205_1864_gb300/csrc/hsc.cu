@@ -44,7 +44,7 @@ static int ensure_hsc64(sg_problem* h) {
 int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o) {
   SG_TRY(check_prec_opts(o));
   const int dt = o.precision == SG_F32 ? SG_F32 : SG_F64;
-  if (kind == SG_PREC_HSC) {
+  if (kind == SG_PREC_HSC || kind == SG_PREC_BGS) {
     SG_TRY(ensure_inner_work(h, dt, h->wmax));
     SG_TRY(dt == SG_F32 ? ensure_hsc32(h) : ensure_hsc64(h));
   } else if (kind == SG_PREC_MEAN) {
@@ -116,6 +116,66 @@ int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts
   return SG_OK;
 }
 
+// Block symmetric Gauss-Seidel with zero initial guess (M_bGS, Sec. 6): a
+// forward sweep over the chaos blocks in graded order, then a backward one.
+// With the linear KL expansion a block of degree d couples only to degrees
+// d - 1 and d + 1 (the blocks of one degree do not couple), so the sweep over
+// chaos indices is a sweep over degree levels with all w_d solves of a level
+// in one batch:
+//   forward   T_d = R_d - C_d Z_{d-1},  Z_d = A_0^{-1} T_d          d = 0..p
+//   backward  Z_d = A_0^{-1} (T_d - B_{d+1} Z_{d+1})                d = p-1..0
+// (the backward step at d = p would repeat the forward one exactly). T_d is
+// kept from the forward sweep in the working residual (in place of R_d,
+// which is not needed again), so the C_d products are not recomputed: n_m
+// block products instead of the 1.5 n_m the paper counts, the same result.
+// Mixed precision as in Algorithm 1; with top_level_f64 the level-p forward
+// product reads the FP64 input and accumulates in FP64.
+int bgs_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
+  const int P = h->P, p = h->p, n = h->n;
+  const std::vector<int>& off = h->off;
+  if (o.precision == SG_F32) {
+    float* R32 = h->R32;
+    float* Z32 = h->Z32;
+    const bool top64 = o.top_level_f64 != 0;
+    SG_TRY(launch_cast(R, SG_F64, P, R32, SG_F32, P, n, P, s));
+    SG_TRY(inner_solve(h, SG_F32, R32, P, SG_F32, Z32, P, SG_F32, off[1] - off[0], o, s));
+    for (int d = 1; d <= p; ++d) {
+      const int lo = off[d], w = off[d + 1] - off[d], lo1 = off[d - 1], w1 = off[d] - off[d - 1];
+      if (d == p && top64)
+        SG_TRY(launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, Z32 + lo1, P, w1, h->post[d], false, R + lo, P,
+                                   -1.0, 1.0, R32 + lo, P, s));
+      else
+        SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo1, P, w1, h->post[d], false, R32 + lo,
+                                   P, -1.0, 1.0, R32 + lo, P, s));
+      SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
+    }
+    for (int d = p - 1; d >= 0; --d) {
+      const int lo = off[d], w = off[d + 1] - off[d], lo2 = off[d + 1], w2 = off[d + 2] - off[d + 1];
+      SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo2, P, w2, h->pre[d + 1], false, R32 + lo, P,
+                                 -1.0, 1.0, R32 + lo, P, s));
+      SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
+    }
+    SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));
+    return SG_OK;
+  }
+  double* Rw = h->R64w;
+  SG_TRY_CUDA(cudaMemcpyAsync(Rw, R, (size_t)n * P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  SG_TRY(inner_solve(h, SG_F64, Rw, P, SG_F64, Z, P, SG_F64, off[1] - off[0], o, s));
+  for (int d = 1; d <= p; ++d) {
+    const int lo = off[d], w = off[d + 1] - off[d], lo1 = off[d - 1], w1 = off[d] - off[d - 1];
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo1, P, w1, h->post[d], false, Rw + lo, P, -1.0,
+                               1.0, Rw + lo, P, s));
+    SG_TRY(inner_solve(h, SG_F64, Rw + lo, P, SG_F64, Z + lo, P, SG_F64, w, o, s));
+  }
+  for (int d = p - 1; d >= 0; --d) {
+    const int lo = off[d], w = off[d + 1] - off[d], lo2 = off[d + 1], w2 = off[d + 2] - off[d + 1];
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo2, P, w2, h->pre[d + 1], false, Rw + lo, P,
+                               -1.0, 1.0, Rw + lo, P, s));
+    SG_TRY(inner_solve(h, SG_F64, Rw + lo, P, SG_F64, Z + lo, P, SG_F64, w, o, s));
+  }
+  return SG_OK;
+}
+
 int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
   const int P = h->P;
   const int chunk = std::min(P, 1024);
@@ -133,11 +193,7 @@ static int check_prec_call(sg_problem* h, const void* R, const void* Z, const sg
     return SG_ERR_INVALID_ARG;
   }
   SG_TRY(check_prec_opts(*o));
-  if (h->grids.empty()) {
-    set_error("%s: the inner solves need the multigrid hierarchy (power-of-two square mesh)", name);
-    return SG_ERR_UNSUPPORTED;
-  }
-  return SG_OK;
+  return check_inner_support(h, *o, name);
 }
 
 static int finish_status(sg_problem* h, cudaStream_t s) {
@@ -159,9 +215,12 @@ static int precond_entry(sg_problem* h, int kind, const double* R, double* Z, co
   const size_t bytes = (size_t)h->n * h->P * sizeof(double);
   SG_TRY_CUDA(cudaMemcpyAsync(h->fr, R, bytes, cudaMemcpyDeviceToDevice, s));
   SG_TRY_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), s));
-  const std::string key = std::string(kind == SG_PREC_HSC ? "hsc|" : "mean|") + opts_key(o);
+  const std::string key = std::string(kind == SG_PREC_HSC ? "hsc|" : kind == SG_PREC_BGS ? "bgs|" : "mean|") +
+                          opts_key(o);
   SG_TRY(run_graph(h, key, [&](cudaStream_t cs) {
-    return kind == SG_PREC_HSC ? hsc_apply_impl(h, h->fr, h->fz, o, cs) : mean_apply_impl(h, h->fr, h->fz, o, cs);
+    if (kind == SG_PREC_HSC) return hsc_apply_impl(h, h->fr, h->fz, o, cs);
+    if (kind == SG_PREC_BGS) return bgs_apply_impl(h, h->fr, h->fz, o, cs);
+    return mean_apply_impl(h, h->fr, h->fz, o, cs);
   }, s));
   SG_TRY_CUDA(cudaMemcpyAsync(Z, h->fz, bytes, cudaMemcpyDeviceToDevice, s));
   return finish_status(h, s);
@@ -179,6 +238,12 @@ int hsc_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_o
   return precond_entry(h, SG_PREC_HSC, R, Z, *opts, (cudaStream_t)stream);
 }
 
+int bgs_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts, void* stream) {
+  set_error("");
+  SG_TRY(check_prec_call(h, R, Z, opts, "bgs_precond_apply"));
+  return precond_entry(h, SG_PREC_BGS, R, Z, *opts, (cudaStream_t)stream);
+}
+
 int mean_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_opts* opts, void* stream) {
   set_error("");
   SG_TRY(check_prec_call(h, R, Z, opts, "mean_precond_apply"));
@@ -192,7 +257,10 @@ int sg_vcycle_apply(sg_problem* h, const void* B, void* X, int w, int dtype, con
     set_error("sg_vcycle_apply: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
-  return inner_vcycle(h, dtype, B, X, w, *opts, (cudaStream_t)stream);
+  sg_prec_opts o = *opts;
+  o.m0 = SG_M0_VCYCLE;   // this entry point is the V-cycle itself
+  SG_TRY(check_inner_support(h, o, "sg_vcycle_apply"));
+  return inner_vcycle(h, dtype, B, X, w, o, (cudaStream_t)stream);
 }
 
 int sg_inner_solve(sg_problem* h, const void* B, void* X, int w, int dtype, const sg_prec_opts* opts, int* iters,
@@ -203,6 +271,7 @@ int sg_inner_solve(sg_problem* h, const void* B, void* X, int w, int dtype, cons
     return SG_ERR_INVALID_ARG;
   }
   SG_TRY(check_prec_opts(*opts));
+  SG_TRY(check_inner_support(h, *opts, "sg_inner_solve"));
   cudaStream_t s = (cudaStream_t)stream;
   SG_TRY(ensure_inner_work(h, dtype, std::max(w, h->wmax)));
   const size_t es = dtype == SG_F64 ? 8 : 4;

@@ -1728,9 +1728,22 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
 
 int check_prec_opts(const sg_prec_opts& o) {
   if (o.nu < 1 || o.nu > 16 || !(o.omega > 0.0) || o.inner_maxit < 1 || o.inner_fixed_iters < 0 ||
-      !(o.inner_tol >= 0.0)) {
-    set_error("prec opts: need 1 <= nu <= 16, omega > 0, inner_maxit >= 1, inner_tol >= 0");
+      !(o.inner_tol >= 0.0) || (o.m0 != SG_M0_VCYCLE && o.m0 != SG_M0_DIAG)) {
+    set_error("prec opts: need 1 <= nu <= 16, omega > 0, inner_maxit >= 1, inner_tol >= 0, m0 0 or 1");
     return SG_ERR_INVALID_ARG;
+  }
+  return SG_OK;
+}
+
+int check_inner_support(const sg_problem* h, const sg_prec_opts& o, const char* name) {
+  if (h->grids.empty()) {
+    set_error("%s: the inner solves need the Q1 grid of A_0 (a mesh given to sg_setup with the 9-point pattern)",
+              name);
+    return SG_ERR_UNSUPPORTED;
+  }
+  if (o.m0 == SG_M0_VCYCLE && !h->mg_full) {
+    set_error("%s: the multigrid M_0 needs a power-of-two square mesh (use m0 = SG_M0_DIAG)", name);
+    return SG_ERR_UNSUPPORTED;
   }
   return SG_OK;
 }
@@ -1849,6 +1862,21 @@ static int vcycle(sg_problem* h, InnerWork& iw, int g, const T* b, T* x, T* xt, 
   const int ng = wp / N;
   const T om = (T)o.omega;
   FinArgs fz = make_fin(h, iw, o);
+  if (o.m0 == SG_M0_DIAG) {
+    // the diagonal mean-value preconditioner (Sec. 6 tried none, diagonal and
+    // LU): x = D^{-1} b, the first Jacobi sweep from zero with unit damping
+    const GridLevel& G = h->grids[g];
+    const T* dinv = sizeof(T) == 8 ? (const T*)G.dinv64 : (const T*)G.dinv32;
+    const Shape sh = make_shape(h, G.n, ng);
+    { const Shape f_ = fit(h, sh, k_smooth0<T>); k_smooth0<T><<<f_.grid, f_.bdim, 0, s>>>(G.n, wp, f_.k, dinv, b, x, T(1), iw.done); ::sghsc::note_launch(); }
+    if (fdot) {
+      const Shape shd = make_shape(h, G.n, ng, 1);
+      { k_dot_fin<T><<<shd.grid, shd.bdim, 0, s>>>(G.n, wp, shd.k, b, x, *fdot, FIN_RHO); ::sghsc::note_launch(); }
+    }
+    SG_CHECK_LAUNCH();
+    *out = x;
+    return SG_OK;
+  }
   if (g >= h->cb_level) {
     SG_TRY(launch_coarse<T>(h, g, b, x, wp, o, iw.done, s));
     if (fdot) {
@@ -1968,7 +1996,8 @@ int inner_solve(sg_problem* h, int dtype, const void* src, int ld_src, int src_t
                 int w, const sg_prec_opts& o, cudaStream_t s) {
   SG_TRY(check_prec_opts(o));
   if (w <= 0) return SG_OK;
-  if (cluster_usable(h, dtype, w)) return inner_solve_cluster(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);
+  if (o.m0 == SG_M0_VCYCLE && cluster_usable(h, dtype, w))
+    return inner_solve_cluster(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);
   SG_TRY(ensure_inner_work(h, dtype, std::max(w, h->wmax)));
   if (dtype == SG_F64) return inner_solve_t<double>(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);
   return inner_solve_t<float>(h, src, ld_src, src_t, dst, ld_dst, dst_t, w, o, s);
@@ -1994,6 +2023,10 @@ static int vcycle_packed(sg_problem* h, InnerWork& iw, const T* B, T* bpad, T* X
 
 int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const sg_prec_opts& o, cudaStream_t s) {
   SG_TRY(check_prec_opts(o));
+  if (!h->mg_full || o.m0 != SG_M0_VCYCLE) {
+    set_error("V-cycle: needs the whole multigrid hierarchy (power-of-two square mesh)");
+    return SG_ERR_UNSUPPORTED;
+  }
   SG_TRY(ensure_inner_work(h, dtype, std::max(w, h->wmax)));
   InnerWork& iw = dtype == SG_F64 ? h->iw64 : h->iw32;
   { k_clear_done<<<1, 1024, 0, s>>>(iw.wcap, iw.done); ::sghsc::note_launch(); }
@@ -2062,7 +2095,7 @@ static size_t static_vcycle_bytes(const sg_problem* h, int wp, size_t es) {
 
 int vcycle_static(sg_problem* h, int dtype, const void* B, void* X, int w, const sg_prec_opts& o, cudaStream_t s) {
   SG_TRY(check_prec_opts(o));
-  if (h->grids.empty()) {
+  if (!h->mg_full || o.m0 != SG_M0_VCYCLE) {
     set_error("sg_vcycle_apply_static: no multigrid hierarchy (mesh missing or not a power-of-two square)");
     return SG_ERR_UNSUPPORTED;
   }

@@ -6,6 +6,7 @@
 // preconditioned solve with the same operator and dQ/dtheta =
 // -sum_k (d A_k / d theta) contracted as above.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "sghsc_internal.cuh"
@@ -127,6 +128,46 @@ static int ensure_part(sg_problem* h, size_t count) {
   return SG_OK;
 }
 
+// The gradient workload's parameters theta = (a_mean, sigma, s_1..s_M) act on
+// matrices given to sg_setup with unit parameters (A_0 = L_h, A_k = Phi_k):
+// A_0(theta) = a_mean L_h and A_k(theta) = sigma s_k Phi_k. scale[k] is the
+// factor of A_k; W[t][k] = -d log(scale[k]) / d theta_t turns the contractions
+// h_k = <Lam, A_k U G_k^T> into dQ/dtheta_t = sum_k W[t][k] h_k (the adjoint
+// formula dQ/dtheta = -Lam^T (dA/dtheta) U with dA_k/dtheta_t = A_k d log
+// scale[k] / d theta_t).
+static int theta_check(const sg_problem* h, const double* theta, const char* name) {
+  if (!h || !theta) {
+    set_error("%s: invalid arguments", name);
+    return SG_ERR_INVALID_ARG;
+  }
+  for (int t = 0; t < h->M + 2; ++t)
+    if (!std::isfinite(theta[t]) || theta[t] == 0.0) {
+      set_error("%s: theta[%d] must be finite and nonzero", name, t);
+      return SG_ERR_INVALID_ARG;
+    }
+  if (!(theta[0] > 0.0)) {
+    set_error("%s: a_mean = theta[0] must be positive", name);
+    return SG_ERR_INVALID_ARG;
+  }
+  return SG_OK;
+}
+
+static void theta_scales(int M, const double* theta, std::vector<double>& scale) {
+  scale.assign(M + 1, 0.0);
+  scale[0] = theta[0];
+  for (int k = 1; k <= M; ++k) scale[k] = theta[1] * theta[1 + k];
+}
+
+static void theta_weights(int M, const double* theta, std::vector<double>& W) {
+  const int M1 = M + 1;
+  W.assign((size_t)(M + 2) * M1, 0.0);
+  W[0] = -1.0 / theta[0];
+  for (int k = 1; k <= M; ++k) {
+    W[(size_t)1 * M1 + k] = -1.0 / theta[1];
+    W[(size_t)(1 + k) * M1 + k] = -1.0 / theta[1 + k];
+  }
+}
+
 }  // namespace sghsc
 
 using namespace sghsc;
@@ -183,6 +224,23 @@ int sg_qoi_grad(sg_problem* h, const double* U, const double* Lam, int nparam, c
   // W is a host buffer: keep it alive until the copy above has run
   SG_TRY_CUDA(cudaStreamSynchronize(s));
   return SG_OK;
+}
+
+int sg_kl_set_theta(sg_problem* h, const double* theta) {
+  set_error("");
+  SG_TRY(theta_check(h, theta, "sg_kl_set_theta"));
+  std::vector<double> scale;
+  theta_scales(h->M, theta, scale);
+  return sg_set_scales(h, scale.data());
+}
+
+int sg_kl_qoi_grad(sg_problem* h, const double* U, const double* Lam, const double* theta, double* grad,
+                   double* hk_out, void* stream) {
+  set_error("");
+  SG_TRY(theta_check(h, theta, "sg_kl_qoi_grad"));
+  std::vector<double> W;
+  theta_weights(h->M, theta, W);
+  return sg_qoi_grad(h, U, Lam, h->M + 2, W.data(), grad, hk_out, stream);
 }
 
 }  // extern "C"

@@ -289,7 +289,10 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
       return SG_ERR_INVALID_ARG;
     }
     const int ne = mesh->ne_x;
-    bool ok = mesh->ne_x == mesh->ne_y && (ne & (ne - 1)) == 0;
+    // the inner solves need the 9-point stencil of A_0 on the grid; the
+    // multigrid hierarchy also a power-of-two square mesh
+    const bool pow2 = mesh->ne_x == mesh->ne_y && (ne & (ne - 1)) == 0;
+    bool ok = true;
     std::vector<double> st((size_t)n * 9, 0.0);
     for (int r = 0; r < n && ok; ++r) {
       const int x = r % nx, y = r / nx;
@@ -310,7 +313,11 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
         g.nx = gx; g.ny = gy; g.n = gx * gy;
         SG_TRY(upload_grid(g, st));
         h->grids.push_back(g);
-        if (gx <= 1) break;
+        if (!pow2) break;            // the finest grid alone: diagonal M_0 only
+        if (gx <= 1) {
+          h->mg_full = true;
+          break;
+        }
         const int nxc = (gx - 1) / 2, nyc = (gy - 1) / 2;
         std::vector<double> stc;
         galerkin_coarsen(gx, gy, st, nxc, nyc, stc);
@@ -323,7 +330,7 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   h->cb_level = (int)h->grids.size();
   for (int g = 0; g < (int)h->grids.size(); ++g)
     if (h->grids[g].n <= 1024) { h->cb_level = g; break; }
-  SG_TRY(cluster_setup(h));
+  if (h->mg_full) SG_TRY(cluster_setup(h));
   for (auto& cs : h->cap) SG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   {
     const char* ev = getenv("SGHSC_EAGER");
@@ -419,6 +426,7 @@ void sg_default_prec_opts(sg_prec_opts* o) {
   o->inner_fixed_iters = 0;
   o->nu = 2;
   o->omega = 0.8;
+  o->m0 = SG_M0_VCYCLE;
 }
 
 void sg_default_solve_opts(sg_solve_opts* o) {

@@ -138,6 +138,7 @@ struct sg_problem {
   std::vector<sghsc::EdgeList> post;        // post[l]: out level l,   in level l-1 (C_l), l = 1..p
   // multigrid
   std::vector<sghsc::GridLevel> grids;
+  bool mg_full = false;                     // the hierarchy reaches the one-node grid (V-cycle usable)
   int cb_level = 0;                         // first grid handled by the in-block coarse V-cycle
   void* cl_plan = nullptr;                  // cluster inner solvers: plans and scratch (null: not usable)
   bool pipe_off = false;                    // SGHSC_NO_PIPE=1: no row-pipelined sweeps on large grids
@@ -203,6 +204,10 @@ int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const 
 int inner_solve(sg_problem* h, int dtype, const void* src, int ld_src, int src_t, void* dst,
                 int ld_dst, int dst_t, int w, const sg_prec_opts& o, cudaStream_t s);
 int check_prec_opts(const sg_prec_opts& o);
+// The inner solves of o can run on h (grids for the diagonal M_0, the whole
+// hierarchy for the V-cycle); sets the error message and returns
+// SG_ERR_UNSUPPORTED otherwise.
+int check_inner_support(const sg_problem* h, const sg_prec_opts& o, const char* name);
 
 // ---- cluster-resident inner solver (inner_cluster.cu) ----
 // Plan the on-chip hierarchy after the grids are built (leaves cl_plan null
@@ -219,6 +224,7 @@ int inner_solve_cluster(sg_problem* h, const void* src, int ld_src, int src_t, v
 int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o);
 int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
+int bgs_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 
 // ---- outer solver (fcg.cu) ----
 int ensure_outer(sg_problem* h);

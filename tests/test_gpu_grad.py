@@ -51,7 +51,7 @@ def test_set_scales_matches_reassembled_problem(lib):
     unit = S.make_unit_problem(16, 3, 0.5)
     real = S.make_problem(16, 3, 0.23, 0.5, a_mean=1.1)
     h = lib.SGProblem.from_inputs(unit, 2)
-    lib.sg_set_scales(h, lib.kl_scales(S.theta_of(real)))
+    lib.sg_kl_set_theta(h, S.theta_of(real))
     U = S.random_block(unit.n, h.P, seed=4)
     Y = lib.sg_apply(h, _t(U)).cpu().numpy()
     A = so.kl_matrices(real.rowptr, real.colidx, real.vals)
@@ -105,18 +105,39 @@ def test_gradient_matches_central_differences(lib):
 
 def test_gradient_batch_of_16_cfg4(lib):
     """Gradient workload: 64x64 grid, M = 4, p = 3, sixteen seeded parameter
-    sets; two of them checked against the oracle."""
+    sets evaluated batched on the device (forward and adjoint solves of all
+    sets in one graph launch each); every set against the oracle's adjoint
+    gradient, and the batch against the one-set-at-a-time autograd path."""
+    from concurrent.futures import ThreadPoolExecutor
     c = S.CONFIGS["cfg4_grad_64x64_M4_p3"]
     unit = S.make_unit_problem(c["ne"], c["M"], c["corr_len"])
     base_s = S.theta_of(S.make_problem(c["ne"], c["M"], 1.0, c["corr_len"]))[2:]
     sets = S.draw_grad_params(c["M"], 16)
     thetas = np.array([np.concatenate([[d["a_mean"], d["sigma"]], base_s * d["sqrt_lambda_scale"]]) for d in sets])
-    h = lib.SGProblem.from_inputs(unit, c["p"])
     F = _t(S.make_rhs(unit, c["p"]))
-    Q, G = lib.sg_qoi_value_and_grad_batch(h, thetas, F, _tight(lib))
+    gb = lib.SGGradBatch.from_inputs(unit, c["p"], 16)
+    gb.autotune()
+    Q, G = gb.value_and_grad(thetas, F, _tight(lib))
     Q, G = Q.cpu().numpy(), G.cpu().numpy()
+    gb.close()
     assert Q.shape == (16,) and G.shape == (16, c["M"] + 2)
-    for i in (0, 7):
-        q_ref, g_ref = _oracle_grad(unit, thetas[i], c["p"])
-        assert Q[i] == pytest.approx(q_ref, rel=1e-10)
-        assert np.abs(G[i] - g_ref).max() <= 1e-6 * np.abs(g_ref).max()
+    with ThreadPoolExecutor(8) as ex:
+        refs = list(ex.map(lambda th: _oracle_grad(unit, th, c["p"]), thetas))
+    for i, (q_ref, g_ref) in enumerate(refs):
+        assert Q[i] == pytest.approx(q_ref, rel=1e-10), i
+        assert np.abs(G[i] - g_ref).max() <= 1e-6 * np.abs(g_ref).max(), i
+    h = lib.SGProblem.from_inputs(unit, c["p"])
+    Q1, G1 = lib.sg_qoi_value_and_grad_batch(h, thetas[:3], F, _tight(lib))
+    assert np.allclose(Q1.cpu().numpy(), Q[:3], rtol=1e-12, atol=0)
+    assert np.allclose(G1.cpu().numpy(), G[:3], rtol=1e-10, atol=1e-12 * np.abs(G).max())
+
+
+def test_theta_entry_points_reject_bad_parameters(lib):
+    unit = S.make_unit_problem(8, 2, 0.5)
+    h = lib.SGProblem.from_inputs(unit, 2)
+    for bad in ([0.0, 0.2, 1.0, 1.0], [-1.0, 0.2, 1.0, 1.0], [1.0, 0.0, 1.0, 1.0], [1.0, 0.2, np.nan, 1.0]):
+        with pytest.raises(lib.SGError) as e:
+            lib.sg_kl_set_theta(h, bad)
+        assert e.value.status == 1
+    with pytest.raises(ValueError):
+        lib.sg_kl_set_theta(h, [1.0, 0.2, 1.0])

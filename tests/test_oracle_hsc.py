@@ -91,3 +91,54 @@ def test_mean_preconditioner_is_blockwise_A0_inverse():
     R = S.random_block(n, P, seed=3)
     Z = hsc.mean_apply(A, R)
     assert np.abs(A[0] @ Z - R).max() < 1e-12
+
+
+@pytest.mark.parametrize("M,p", [(2, 2), (3, 2), (1, 3)])
+def test_bgs_matches_block_triangular_solves(M, p):
+    """M_bGS (Sec. 6, zero initial guess) against its closed form
+    (D + U)^{-1} D (D + L)^{-1} built from the dense chaos-major matrix; it is
+    symmetric and positive definite, and with the linear KL expansion the
+    blocks of one degree do not couple (so a level-batched sweep is the same
+    sweep)."""
+    prob = S.make_problem(4, M, 0.3, 0.5)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(M, p)
+    _, off = chaos.multi_indices(M, p)
+    n, P = prob.n, G[0].shape[0]
+    K = so.global_matrix_chaos_major(A, G).toarray()
+    Mb = hsc.bgs_dense(K, n, P)
+    R = S.random_block(n, P, seed=3)
+    ref = (Mb @ R.T.ravel()).reshape(P, n).T
+    U = hsc.bgs_apply(A, G, R)
+    assert np.abs(U - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(Mb - Mb.T).max() <= 1e-12 * np.abs(Mb).max()
+    assert np.linalg.eigvalsh(0.5 * (Mb + Mb.T))[0] > 0
+    for d in range(p + 1):
+        for j in range(off[d], off[d + 1]):
+            for l in range(off[d], off[d + 1]):
+                if j != l:
+                    assert all(Gk[j, l] == 0.0 for Gk in G)
+
+
+@pytest.mark.parametrize("M,p", [(2, 2), (3, 3), (2, 1)])
+def test_schur_reduced_solve_recovers_the_full_solution(M, p):
+    """Sec. 5, eq. (global-Schur-system): with exact D_p solves the reduced
+    iteration and the recovery of u^p give the solution of the full system
+    (the direct solve), and the Schur complement S_{p-1} = A_{p-1} - B_p
+    D_p^{-1} C_p has a condition number no larger than A's (dense, tiny)."""
+    prob = S.make_problem(8, M, 0.3, 0.5)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(M, p)
+    _, off = chaos.multi_indices(M, p)
+    F = S.make_rhs(prob, p)
+    F[:, -1] = S.random_block(prob.n, 1, seed=5)[:, 0]     # a nonzero degree-p part exercises g and the recovery
+    U, info = hsc.schur_reduced_solve(A, G, off, F, tol=1e-13)
+    ref = so.direct_solve(A, G, F)
+    assert info["converged"]
+    assert np.abs(U - ref).max() <= 1e-10 * np.abs(ref).max()
+    n = prob.n
+    K = so.global_matrix_chaos_major(A, G).toarray()
+    e = n * off[p]
+    Sd = K[:e, :e] - K[:e, e:] @ np.linalg.solve(K[e:, e:], K[e:, :e])
+    evs, eva = np.linalg.eigvalsh(0.5 * (Sd + Sd.T)), np.linalg.eigvalsh(K)
+    assert evs[-1] / evs[0] <= eva[-1] / eva[0] * (1 + 1e-12)

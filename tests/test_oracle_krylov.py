@@ -74,7 +74,8 @@ def _paper_run(M, p, cov):
     ap = lambda U: so.sg_apply(A, G, U)
     out = {}
     for name, prec in (("mean", lambda R: hsc.mean_apply(A, R, a0)),
-                       ("hsc", lambda R: hsc.hsc_apply(A, G, off, R, a0solve=a0))):
+                       ("hsc", lambda R: hsc.hsc_apply(A, G, off, R, a0solve=a0)),
+                       ("bgs", lambda R: hsc.bgs_apply(A, G, R, dsolve=lambda j, x: a0(x[:, None])[:, 0]))):
         _, info = krylov.fcg(ap, F, prec, tol=1e-8, maxit=500)
         out[name] = (info["iters"], krylov.lanczos_kappa(info["alpha"], info["beta"]))
     return out
@@ -97,12 +98,14 @@ def test_paper_table3_soft(row):
 
 @pytest.mark.parametrize("row", _read("table1_vary_N.txt"))
 def test_paper_table1_soft(row):
-    N, m_it, m_k, _, _, h_it, h_k = row
+    N, m_it, m_k, b_it, b_k, h_it, h_k = row
     out = _paper_run(int(N), 4, 0.5)
     assert abs(out["mean"][0] - m_it) <= 2
     assert abs(out["hsc"][0] - h_it) <= 2
+    assert abs(out["bgs"][0] - b_it) <= 2
     assert out["mean"][1] == pytest.approx(m_k, rel=0.10)
     assert out["hsc"][1] == pytest.approx(h_k, rel=0.10)
+    assert out["bgs"][1] == pytest.approx(b_k, rel=0.10)
 
 
 def test_pcg_columns_conventions():
