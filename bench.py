@@ -719,6 +719,48 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _golden(name):
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+def run_tables(dev):
+    """The paper's Tables 1-4 (Sec. 6) on the GPU: outer iterations and Lanczos
+    condition estimates of flexible CG to 1e-8 with M_m, M_bGS and M_HS (all
+    FP64, inner PCG with the diagonal M_0 to 1e-8), next to the printed values."""
+    import paper_1205_1864_gb300 as L
+    import torch
+    code = {"mean": L.SG_PREC_MEAN, "bgs": L.SG_PREC_BGS, "hsc": L.SG_PREC_HSC}
+    specs = [("table1_vary_N", "sec6_table1_vary_N_full.txt", lambda r: (10, int(r[0]), 4, 0.5)),
+             ("table2_vary_P", "sec6_table2_vary_P.txt", lambda r: (10, 4, int(r[0]), 0.5)),
+             ("table3_vary_cov", "sec6_table3_vary_cov_full.txt", lambda r: (10, 4, 4, r[0] / 100.0)),
+             ("table4_vary_h", "sec6_table4_vary_h.txt", lambda r: (int(r[0]), 4, 4, 0.5))]
+    out = {"profile": "tables", "setting": "Sec. 6: k0 = 1, L = 0.5, f = 1, sigma = CoV/sqrt(3), FP64, inner PCG "
+                                           "with diagonal M_0 to 1e-8, outer flexible CG to 1e-8"}
+    for name, fname, setting in specs:
+        rows = []
+        for r in _golden(fname):
+            ne, M, p, cov = setting(r)
+            prob = S.make_problem(ne, M, cov / math.sqrt(3.0), 0.5)
+            h = L.SGProblem.from_inputs(prob, p)
+            F = torch.tensor(S.make_rhs(prob, p), dtype=torch.float64, device=dev)
+            row = {"key": r[0], "ndof_interior": h.n * h.P}
+            for k, col in (("mean", 4), ("bgs", 6), ("hsc", 8)):
+                o = L.solve_opts(L.prec_opts(precision=L.SG_F64, m0=L.SG_M0_DIAG, inner_tol=1e-8, inner_maxit=1000),
+                                 precond=code[k], tol=1e-8, maxit=1000)
+                _, st = L.sg_solve(h, F, o)
+                row[k] = [st.iterations, round(st.kappa_est, 4)]
+                row[k + "_paper"] = [int(r[col]), r[col + 1]]
+            rows.append(row)
+            h.close()
+        out[name] = rows
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -730,9 +772,11 @@ def main():
     ap.add_argument("--ne", type=int, default=None,
                     help="mesh override (elements per side, a power of two) for profiling a workload's kernel "
                          "shapes on a smaller case; the name gets an @ne suffix")
-    ap.add_argument("--profile", nargs="?", const="solve", default=None, choices=["solve", "apply", "inner"],
+    ap.add_argument("--profile", nargs="?", const="solve", default=None,
+                    choices=["solve", "apply", "inner", "tables"],
                     help="solve: only the warm-up and timed HSC solves; apply: only the SG product, FP64 then "
                          "FP32; inner: only the batched inner PCG on the widest level (for ncu captures); "
+                         "tables: the paper's Tables 1-4 on the GPU next to the printed values; "
                          "prints one short line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -755,8 +799,11 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
-    out = run_batch(args, rank, world, dev) if WORKLOADS[args.workload].get("batch") else \
-        run_ours(args, rank, world, dev)
+    if args.profile == "tables":
+        out = run_tables(dev)
+    else:
+        out = run_batch(args, rank, world, dev) if WORKLOADS[args.workload].get("batch") else \
+            run_ours(args, rank, world, dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

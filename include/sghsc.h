@@ -100,6 +100,15 @@ typedef struct {
   int use_x0;             /* 1: U holds the initial guess on entry */
   int check_true_residual;/* 1: recompute ||f - A u|| / ||f|| in FP64 after the loop
                              (one more SG product) into stats->true_rel_res */
+  int schur_reduced;      /* 1: iterate on the Schur-reduced system of Sec. 5,
+                             eq. (global-Schur-system): S_{p-1} u_{p-1} = g_{p-1} with
+                             S_{p-1} = A_{p-1} - B_p D_p^{-1} C_p, g_{p-1} = f^{p-1} - B_p D_p^{-1} f^p,
+                             the preconditioner on levels 0..p-1 only, then
+                             u^p = D_p^{-1} (f^p - C_p u_{p-1}). Needs p >= 1 and use_x0 = 0;
+                             tol, iterations, rel_res and kappa_est refer to the reduced system,
+                             true_rel_res to the full one. */
+  double schur_inner_tol; /* relative tolerance of the FP64 inner solves that apply D_p^{-1}
+                             inside S_{p-1} (the reduction assumes exact solves, Sec. 5) */
 } sg_solve_opts;
 
 #define SG_MAX_HIST 1024

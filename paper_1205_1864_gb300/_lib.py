@@ -32,7 +32,8 @@ class sg_prec_opts(C.Structure):
 
 class sg_solve_opts(C.Structure):
     _fields_ = [("precond", C.c_int), ("prec", sg_prec_opts), ("tol", C.c_double), ("maxit", C.c_int),
-                ("flexible", C.c_int), ("use_x0", C.c_int), ("check_true_residual", C.c_int)]
+                ("flexible", C.c_int), ("use_x0", C.c_int), ("check_true_residual", C.c_int),
+                ("schur_reduced", C.c_int), ("schur_inner_tol", C.c_double)]
 
 
 class sg_solve_stats(C.Structure):

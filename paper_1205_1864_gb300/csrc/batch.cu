@@ -379,6 +379,10 @@ int sg_batch_solve(sg_batch* b, const double* const* F, double* const* U, const 
     set_error("sg_batch_solve: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
+  if (opts->schur_reduced) {
+    set_error("sg_batch_solve: the Schur-reduced system is solved by sg_solve only");
+    return SG_ERR_UNSUPPORTED;
+  }
   for (size_t i = 0; i < b->hs.size(); ++i)
     if (!F[i] || !U[i] || F[i] == U[i]) {
       set_error("sg_batch_solve: invalid buffers for system %zu", i);

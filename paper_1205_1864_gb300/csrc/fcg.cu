@@ -171,6 +171,82 @@ int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
   return SG_OK;
 }
 
+// The a-priori reduction of Sec. 5 (eq. (global-Schur-system)): flexible CG
+// on S_{p-1} u_{p-1} = g_{p-1}, S_{p-1} = A_{p-1} - B_p D_p^{-1} C_p, over the
+// n x Pr blocks of levels 0..p-1 (leading dimension Pr = off[p]); then
+// u^p = D_p^{-1} (f^p - C_p u_{p-1}). The D_p^{-1} actions inside the operator
+// are FP64 inner solves to schur_inner_tol (the reduction assumes exact
+// ones). The iteration keeps p in one buffer (fpA) and q in fq; the assembled
+// n x P solution ends in fz.
+static int enqueue_schur_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
+  const int P = h->P, p = h->p, n = h->n;
+  const int Pr = h->off[p], wp = P - Pr, lo1 = h->off[p - 1], w1 = Pr - lo1;
+  const long long N = (long long)n * Pr;
+  const int vg = std::min(vec_grid(N), h->opart_blocks);
+  sg_prec_opts dop = o.prec;     // the exact-solve stand-in for D_p^{-1}
+  dop.precision = SG_F64;
+  dop.inner_tol = o.schur_inner_tol;
+  dop.inner_fixed_iters = 0;
+  dop.inner_maxit = std::max(o.prec.inner_maxit, 1000);
+  double* Y = h->R64w;           // n x wp: D_p^{-1} of a level-p block
+  double* T = h->T64;            // n x wp: a level-p block
+  const OuterArgs a0 = outer_args(h, o);
+  auto with = [&](const LoopCtl& lc) {
+    OuterArgs a = a0;
+    a.cond = lc.cond;
+    a.has_cond = lc.has_cond;
+    a.flag = lc.flag;
+    return a;
+  };
+  auto pre = [&](cudaStream_t ps, const LoopCtl& lc) -> int {
+    const OuterArgs a = with(lc);
+    // g = f^{<p} - B_p D_p^{-1} f^p
+    SG_TRY(launch_cast(h->fF, SG_F64, P, h->fG, SG_F64, Pr, n, Pr, ps));
+    SG_TRY(inner_solve(h, SG_F64, h->fF + Pr, P, SG_F64, Y, wp, SG_F64, wp, dop, ps));
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Y, wp, wp, h->pre[p], false, h->fG + lo1, Pr, -1.0,
+                               1.0, h->fG + lo1, Pr, ps));
+    SG_TRY_CUDA(cudaMemsetAsync(h->fx, 0, N * sizeof(double), ps));
+    { k_outer_init<<<vg, 256, 0, ps>>>(N, h->fG, nullptr, h->fr, a); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+    return SG_OK;
+  };
+  auto body = [&](cudaStream_t bs, const LoopCtl& lc) -> int {
+    const OuterArgs a = with(lc);
+    if (o.precond == SG_PREC_HSC) SG_TRY(hsc_apply_lv(h, h->fr, h->fz, o.prec, bs, p - 1, Pr));
+    else if (o.precond == SG_PREC_BGS) SG_TRY(bgs_apply_lv(h, h->fr, h->fz, o.prec, bs, p - 1, Pr));
+    else if (o.precond == SG_PREC_MEAN) SG_TRY(mean_apply_lv(h, h->fr, h->fz, o.prec, bs, Pr));
+    else SG_TRY_CUDA(cudaMemcpyAsync(h->fz, h->fr, N * sizeof(double), cudaMemcpyDeviceToDevice, bs));
+    { k_outer_dots<<<vg, 256, 0, bs>>>(N, h->fz, h->fr, h->fq, a); ::sghsc::note_launch(); }
+    { k_schur_p<<<vg, 256, 0, bs>>>(N, h->fz, h->fpA, a); ::sghsc::note_launch(); }
+    // q = A_{p-1} p - B_p D_p^{-1} C_p p
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, h->fpA, Pr, Pr, h->sub, true, nullptr, 0, 1.0, 0.0,
+                               h->fq, Pr, bs));
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, h->fpA + lo1, Pr, w1, h->post[p], false, nullptr, 0,
+                               1.0, 0.0, T, wp, bs));
+    SG_TRY(inner_solve(h, SG_F64, T, wp, SG_F64, Y, wp, SG_F64, wp, dop, bs));
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Y, wp, wp, h->pre[p], false, h->fq + lo1, Pr, -1.0,
+                               1.0, h->fq + lo1, Pr, bs));
+    { k_schur_pq<<<vg, 256, 0, bs>>>(N, h->fpA, h->fq, a); ::sghsc::note_launch(); }
+    { k_outer_update<<<vg, 256, 0, bs>>>(N, h->fpA, h->fpA, h->fq, h->fx, h->fr, a); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+    return SG_OK;
+  };
+  SG_TRY(capture_while(h, s, pre, body));
+  // recovery: u^p = D_p^{-1} (f^p - C_p u_{p-1}), assembled with u_{p-1} in fz
+  SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, h->fx + lo1, Pr, w1, h->post[p], false, h->fF + Pr, P,
+                             -1.0, 1.0, T, wp, s));
+  SG_TRY(inner_solve(h, SG_F64, T, wp, SG_F64, h->fz + Pr, P, SG_F64, wp, dop, s));
+  SG_TRY(launch_cast(h->fx, SG_F64, Pr, h->fz, SG_F64, P, n, Pr, s));
+  if (o.check_true_residual) {
+    const long long NF = (long long)n * P;
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, h->fz, P, P, h->all, true, nullptr, 0, 1.0, 0.0,
+                               h->fq, P, s));
+    { k_outer_true<<<std::min(vec_grid(NF), h->opart_blocks), 256, 0, s>>>(NF, h->fF, h->fq, a0); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+  }
+  return SG_OK;
+}
+
 std::string opts_key(const sg_prec_opts& o) {
   char buf[256];
   snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d", o.precision, o.top_level_f64,
@@ -181,14 +257,27 @@ std::string opts_key(const sg_prec_opts& o) {
 int solve_prepare(sg_problem* h, const sg_solve_opts& o) {
   SG_TRY(ensure_outer(h));
   if (o.precond != SG_PREC_NONE) SG_TRY(prepare_precond(h, o.precond, o.prec));
+  if (o.schur_reduced) {
+    // FP64 inner solves of the level-p blocks and their buffers, the reduced right-hand side
+    sg_prec_opts dop = o.prec;
+    dop.precision = SG_F64;
+    SG_TRY(prepare_precond(h, SG_PREC_HSC, dop));
+    if (!h->fG) {
+      if (h->capturing) {
+        set_error("outer buffers must be allocated before graph capture");
+        return SG_ERR_UNSUPPORTED;
+      }
+      SG_TRY_CUDA(cudaMalloc((void**)&h->fG, (size_t)h->n * h->off[h->p] * sizeof(double)));
+    }
+  }
   return SG_OK;
 }
 
 std::string solve_key(const sg_solve_opts& o) {
   char key[512];
-  snprintf(key, sizeof key, "solve|k%d|%s|tol%.17g|mi%d|fl%d|x0%d|tr%d", o.precond,
-           o.precond == SG_PREC_NONE ? "-" : opts_key(o.prec).c_str(), o.tol, o.maxit, o.flexible, o.use_x0,
-           o.check_true_residual);
+  snprintf(key, sizeof key, "solve|k%d|%s|tol%.17g|mi%d|fl%d|x0%d|tr%d|sr%d|st%.17g", o.precond,
+           o.precond == SG_PREC_NONE && !o.schur_reduced ? "-" : opts_key(o.prec).c_str(), o.tol, o.maxit, o.flexible,
+           o.use_x0, o.check_true_residual, o.schur_reduced, o.schur_reduced ? o.schur_inner_tol : 0.0);
   return key;
 }
 
@@ -250,8 +339,11 @@ static int solve_impl(sg_problem* h, const double* F, double* U, const sg_solve_
   const auto t0 = std::chrono::steady_clock::now();
   SG_TRY(solve_prepare(h, o));
   SG_TRY(solve_stage_in(h, F, U, o, s));
-  SG_TRY(run_graph(h, solve_key(o), [&](cudaStream_t cs) { return enqueue_solve(h, o, cs); }, s));
-  SG_TRY_CUDA(cudaMemcpyAsync(U, h->fx, (size_t)h->n * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  SG_TRY(run_graph(h, solve_key(o), [&](cudaStream_t cs) {
+    return o.schur_reduced ? enqueue_schur_solve(h, o, cs) : enqueue_solve(h, o, cs);
+  }, s));
+  SG_TRY_CUDA(cudaMemcpyAsync(U, o.schur_reduced ? h->fz : h->fx, (size_t)h->n * h->P * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
   SG_TRY_CUDA(cudaStreamSynchronize(s));
   return solve_collect(h, o, st,
                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
@@ -270,13 +362,17 @@ int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts) {
     set_error("sg_solve: invalid options");
     return SG_ERR_INVALID_ARG;
   }
-  if (opts->precond != SG_PREC_NONE) {
+  if (opts->precond != SG_PREC_NONE || opts->schur_reduced) {
     if (opts->prec.precision != SG_F32 && opts->prec.precision != SG_F64) {
       set_error("sg_solve: invalid preconditioner precision");
       return SG_ERR_INVALID_ARG;
     }
     SG_TRY(check_prec_opts(opts->prec));
     SG_TRY(check_inner_support(h, opts->prec, "sg_solve"));
+  }
+  if (opts->schur_reduced && (h->p < 1 || opts->use_x0 || !(opts->schur_inner_tol >= 0.0))) {
+    set_error("sg_solve: the Schur-reduced system needs p >= 1, use_x0 = 0 and schur_inner_tol >= 0");
+    return SG_ERR_INVALID_ARG;
   }
   return SG_OK;
 }
@@ -294,13 +390,17 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
     set_error("sg_solve: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
-  if (opts->precond != SG_PREC_NONE) {
+  if (opts->precond != SG_PREC_NONE || opts->schur_reduced) {
     if (opts->prec.precision != SG_F32 && opts->prec.precision != SG_F64) {
       set_error("sg_solve: invalid preconditioner precision");
       return SG_ERR_INVALID_ARG;
     }
     SG_TRY(check_prec_opts(opts->prec));
     SG_TRY(check_inner_support(h, opts->prec, "sg_solve"));
+  }
+  if (opts->schur_reduced && (h->p < 1 || opts->use_x0 || !(opts->schur_inner_tol >= 0.0))) {
+    set_error("sg_solve: the Schur-reduced system needs p >= 1, use_x0 = 0 and schur_inner_tol >= 0");
+    return SG_ERR_INVALID_ARG;
   }
   return solve_impl(h, F, U, *opts, stats, (cudaStream_t)stream);
 }

@@ -53,8 +53,11 @@ int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o) {
   return SG_OK;
 }
 
-int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
-  const int P = h->P, p = h->p, n = h->n;
+// Algorithm 1 on the hierarchy of levels 0..p of blocks with leading
+// dimension P (p = h->p, P = h->P for the full system; p - 1 and the width of
+// levels 0..p-1 for the Schur-reduced one).
+int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s, int p, int P) {
+  const int n = h->n;
   const std::vector<int>& off = h->off;
   if (o.precision == SG_F32) {
     float* R32 = h->R32;
@@ -130,8 +133,8 @@ int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts
 // block products instead of the 1.5 n_m the paper counts, the same result.
 // Mixed precision as in Algorithm 1; with top_level_f64 the level-p forward
 // product reads the FP64 input and accumulates in FP64.
-int bgs_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
-  const int P = h->P, p = h->p, n = h->n;
+int bgs_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s, int p, int P) {
+  const int n = h->n;
   const std::vector<int>& off = h->off;
   if (o.precision == SG_F32) {
     float* R32 = h->R32;
@@ -176,8 +179,16 @@ int bgs_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts
   return SG_OK;
 }
 
-int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
-  const int P = h->P;
+int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
+  return hsc_apply_lv(h, R, Z, o, s, h->p, h->P);
+}
+
+int bgs_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
+  return bgs_apply_lv(h, R, Z, o, s, h->p, h->P);
+}
+
+// I (x) A_0^{-1} on the P columns of a block with leading dimension P.
+int mean_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s, int P) {
   const int chunk = std::min(P, 1024);
   const int dt = o.precision == SG_F32 ? SG_F32 : SG_F64;
   for (int c0 = 0; c0 < P; c0 += chunk) {
@@ -185,6 +196,10 @@ int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opt
     SG_TRY(inner_solve(h, dt, R + c0, P, SG_F64, Z + c0, P, SG_F64, w, o, s));
   }
   return SG_OK;
+}
+
+int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s) {
+  return mean_apply_lv(h, R, Z, o, s, h->P);
 }
 
 static int check_prec_call(sg_problem* h, const void* R, const void* Z, const sg_prec_opts* o, const char* name) {

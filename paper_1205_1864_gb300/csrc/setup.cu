@@ -267,6 +267,7 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
     SG_TRY(upload_edges(build_edges(h, index, h->off[l - 1], h->off[l], h->off[l], h->off[l + 1]), h->pre[l]));
     SG_TRY(upload_edges(build_edges(h, index, h->off[l], h->off[l + 1], h->off[l - 1], h->off[l]), h->post[l]));
   }
+  if (p >= 1) SG_TRY(upload_edges(build_edges(h, index, 0, h->off[p], 0, h->off[p]), h->sub));
 
   // matrices
   SG_TRY(upload(&h->rowptr, rowptr, (size_t)n + 1));
@@ -438,6 +439,8 @@ void sg_default_solve_opts(sg_solve_opts* o) {
   o->flexible = 1;
   o->use_x0 = 0;
   o->check_true_residual = 1;
+  o->schur_reduced = 0;
+  o->schur_inner_tol = 1e-11;
 }
 
 int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz, const int* rowptr,
@@ -463,6 +466,7 @@ void sg_destroy(sg_problem* h) {
   free_edges(h->all);
   for (auto& e : h->pre) free_edges(e);
   for (auto& e : h->post) free_edges(e);
+  free_edges(h->sub);
   for (auto& g : h->grids) {
     cudaFree(g.st_base); cudaFree(g.st64); cudaFree(g.st32); cudaFree(g.dinv64); cudaFree(g.dinv32);
   }
@@ -472,7 +476,7 @@ void sg_destroy(sg_problem* h) {
   cluster_free(h);
   void* bufs[] = {h->rowptr, h->colidx, h->vals64, h->vals32, h->mass64, h->R32, h->Z32, h->T32, h->R64w,
                   h->T64, h->fF, h->fx, h->fr, h->fz, h->fpA, h->fpB, h->fq, h->opart, h->osc, h->octl,
-                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev};
+                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev, h->fG};
   for (void* b : bufs) cudaFree(b);
   for (auto& cs : h->cap)
     if (cs) cudaStreamDestroy(cs);

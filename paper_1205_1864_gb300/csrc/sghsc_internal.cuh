@@ -136,6 +136,8 @@ struct sg_problem {
   sghsc::EdgeList all;                      // outputs 0..P-1, inputs 0..P-1
   std::vector<sghsc::EdgeList> pre;         // pre[l]:  out level l-1, in level l   (B_l), l = 1..p
   std::vector<sghsc::EdgeList> post;        // post[l]: out level l,   in level l-1 (C_l), l = 1..p
+  sghsc::EdgeList sub;                      // levels 0..p-1 among themselves (A_{p-1}, Schur-reduced system)
+  double* fG = nullptr;                     // n x off[p] right-hand side g_{p-1} of the reduced system
   // multigrid
   std::vector<sghsc::GridLevel> grids;
   bool mg_full = false;                     // the hierarchy reaches the one-node grid (V-cycle usable)
@@ -225,6 +227,11 @@ int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o);
 int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 int bgs_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
+// The same on the hierarchy of levels 0..p with leading dimension P (the
+// Schur-reduced system uses p = h->p - 1 and P = h->off[h->p]).
+int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s, int p, int P);
+int bgs_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s, int p, int P);
+int mean_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s, int P);
 
 // ---- outer solver (fcg.cu) ----
 int ensure_outer(sg_problem* h);

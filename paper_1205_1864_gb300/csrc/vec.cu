@@ -118,6 +118,35 @@ __global__ void __launch_bounds__(256) k_outer_update(long long N, const double*
   }
 }
 
+// Schur-reduced iteration: p = z (first iteration) or z + beta p, in place
+__global__ void __launch_bounds__(256) k_schur_p(long long N, const double* __restrict__ z, double* __restrict__ p,
+                                                 OuterArgs a) {
+  const bool first = a.ctl->it == 0;
+  const double beta = first ? 0.0 : a.sc[SC_BETA];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : z[i] + beta * p[i];
+}
+
+// Schur-reduced iteration: p . q and alpha = rho / (p . q) (as the fused
+// product of the full system does in its epilogue)
+__global__ void __launch_bounds__(256) k_schur_pq(long long N, const double* __restrict__ p,
+                                                  const double* __restrict__ q, OuterArgs a) {
+  double s0 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    s0 += p[i] * q[i];
+  double pq, unused;
+  if (outer_reduce_last(s0, 0.0, a, pq, unused) && threadIdx.x == 0) {
+    a.sc[SC_PQ] = pq;
+    if (!(pq > 0.0)) {
+      atomicOr(a.status, ST_OUTER_BREAKDOWN);
+      a.sc[SC_ALPHA] = 0.0;
+    } else {
+      a.sc[SC_ALPHA] = a.sc[SC_RHO] / pq;
+    }
+    a.hist_alpha[a.ctl->it] = a.sc[SC_ALPHA];
+  }
+}
+
 // true relative residual ||F - Y|| / ||F|| with Y = A x
 __global__ void __launch_bounds__(256) k_outer_true(long long N, const double* __restrict__ F,
                                                     const double* __restrict__ Y, OuterArgs a) {

@@ -29,6 +29,8 @@ __global__ void k_outer_dots(long long N, const double* z, const double* r, cons
 __global__ void k_outer_update(long long N, const double* pA, const double* pB, const double* q, double* x,
                                double* r, OuterArgs a);
 __global__ void k_outer_true(long long N, const double* F, const double* Y, OuterArgs a);
+__global__ void k_schur_p(long long N, const double* z, double* p, OuterArgs a);
+__global__ void k_schur_pq(long long N, const double* p, const double* q, OuterArgs a);
 
 // Fixed-order tree sum of r0[0 .. blockDim), r1[...] into r0[0], r1[0]:
 // the entries above the largest power of two p2 <= blockDim are first added
