@@ -85,6 +85,11 @@ typedef struct {
                              open): SG_M0_VCYCLE one multigrid V-cycle (needs a power-of-two
                              square mesh), SG_M0_DIAG the diagonal of A_0 (any mesh given to
                              sg_setup whose pattern is the 9-point Q1 stencil) */
+  double level_tol;       /* gPC coefficient (sg_setup_gpc) only: D_l is not block diagonal
+                             (Sec. 6, lognormal case), so D_l^{-1} is a nested flexible CG on
+                             the level block, preconditioned by the inner PCG on A_0 per
+                             column, to this relative residual */
+  int level_maxit;        /* cap on the iterations of that nested CG */
 } sg_prec_opts;
 
 enum { SG_M0_VCYCLE = 0, SG_M0_DIAG = 1 };
@@ -149,11 +154,32 @@ int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz,
              const int* rowptr, const int* colidx, const double* vals,
              const double* mass_vals, sg_problem** out);
 
+/* sg_setup_gpc -- a handle for a coefficient given by its generalised
+ * polynomial chaos expansion k = sum_i k_i(x) psi_i(xi) (Remark K-L of Sec. 2;
+ * Sec. 6, the lognormal case): vals host double[nnz][nterm] holds the
+ * stiffness matrices of the nterm = C(M+q, M) coefficient terms k_i, in the
+ * graded chaos order (term 0 the mean, whose matrix is A_0), and the
+ * operator is sum_i G_i (x) A_i with (G_i)_{jl} = E[psi_i psi_j psi_l]
+ * (the paper expands the lognormal coefficient to q = 2p). Only Hermite
+ * chaos (family SG_HERMITE, xi ~ N(0,1)); q <= 16, nterm <= 4096. The
+ * coupling is block dense: B_l and C_l reach every lower degree, D_l is not
+ * block diagonal (hsc_precond_apply solves with it by a nested CG,
+ * sg_prec_opts.level_tol; FP64 only; bgs_precond_apply and the
+ * Schur-reduced system return SG_ERR_UNSUPPORTED). Other arguments and
+ * errors as sg_setup; SG_ERR_UNSUPPORTED for another family. */
+int sg_setup_gpc(const sg_mesh* mesh, int M, int p, int q, int family, int n, int nnz, const int* rowptr,
+                 const int* colidx, const double* vals, const double* mass_vals, sg_problem** out);
+
+/* Value terms per nonzero of a handle (M+1, or C(M+q, M) for sg_setup_gpc)
+ * and its coefficient degree q (-1 for the linear KL expansion). */
+int sg_problem_terms(const sg_problem* h, int* nterm, int* q);
+
 void sg_destroy(sg_problem* h);
 
 /* sg_set_scales -- A_k := scale[k] * A_k(as given to sg_setup), k = 0..M, for
  * parameterised KL matrices (A_0 = a_mean L_h, A_k = sigma s_k Phi_k): one
- * handle then serves every parameter set. scale: host double[M+1], finite,
+ * handle then serves every parameter set. scale: host double[M+1] (one per
+ * value term: nterm for sg_setup_gpc), finite,
  * scale[0] > 0 when the multigrid hierarchy exists (it is rescaled too).
  * Synchronises the device. */
 int sg_set_scales(sg_problem* h, const double* scale);

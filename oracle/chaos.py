@@ -115,3 +115,51 @@ def block_counts(M: int, p: int, family: str = LEGENDRE) -> dict:
     n_b = int(pattern.nnz)
     n_db = int(Gs[0].shape[0])
     return dict(n_b=n_b, n_db=n_db, n_m=n_b - n_db, n_ds=2 * (n_db - 1) + 1)
+
+
+# ---------------------------------------------------------------------------
+# General gPC coefficient expansions (Remark K-L, Sec. 6 lognormal case)
+# ---------------------------------------------------------------------------
+
+def hermite_triple_1d(a: int, b: int, c: int) -> float:
+    """``E[psi_a psi_b psi_c]`` for the normalised Hermite polynomials
+    ``psi_m = He_m / sqrt(m!)`` of ``xi ~ N(0,1)``: with ``s = (a+b+c)/2`` it is
+    ``sqrt(a! b! c!) / ((s-a)! (s-b)! (s-c)!)`` when ``s`` is an integer not
+    below any of ``a, b, c``, and zero otherwise (the classical product formula
+    of Hermite polynomials)."""
+    t = a + b + c
+    if t % 2:
+        return 0.0
+    s2 = t // 2
+    if s2 < a or s2 < b or s2 < c:
+        return 0.0
+    return math.sqrt(math.factorial(a) * math.factorial(b) * math.factorial(c)) / (
+        math.factorial(s2 - a) * math.factorial(s2 - b) * math.factorial(s2 - c))
+
+
+def gpc_g_matrices(M: int, p: int, q: int) -> List[sp.csr_matrix]:
+    """``[G_i]`` for the coefficient basis of total degree ``<= q`` (graded
+    order, as the solution basis) with ``(G_i)_{jl} = E[psi_i psi_j psi_l]``
+    over the solution basis of degree ``<= p``, normalised Hermite chaos:
+    the SG matrix of eq. (global-system) for a gPC-expanded coefficient
+    ``k = sum_i k_i psi_i`` (Remark K-L). The triple product of tensor-product
+    polynomials is the product of the 1-D ones over the coordinates."""
+    alpha, _ = multi_indices(M, p)
+    gamma, _ = multi_indices(M, q)
+    P = alpha.shape[0]
+    out = []
+    for g in gamma:
+        rows, cols, vals = [], [], []
+        for j in range(P):
+            for l in range(P):
+                v = 1.0
+                for k in range(M):
+                    v *= hermite_triple_1d(int(g[k]), int(alpha[j][k]), int(alpha[l][k]))
+                    if v == 0.0:
+                        break
+                if v != 0.0:
+                    rows.append(j)
+                    cols.append(l)
+                    vals.append(v)
+        out.append(sp.csr_matrix((vals, (rows, cols)), shape=(P, P)))
+    return out

@@ -87,14 +87,19 @@ class SGProblem:
     """Owner of an ``sg_problem`` handle (``sg_setup`` / ``sg_destroy``)."""
 
     def __init__(self, ne_x: int, ne_y: int, M: int, p: int, rowptr, colidx, vals, mass=None,
-                 family: int = SG_LEGENDRE):
+                 family: int = SG_LEGENDRE, q: int = -1):
+        """``q < 0``: the linear KL expansion (``vals`` is ``nnz x (M+1)``,
+        ``sg_setup``); ``q >= 0``: a gPC coefficient of total degree ``q``
+        (``vals`` is ``nnz x C(M+q, M)``, ``sg_setup_gpc``, Hermite chaos)."""
+        import math
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
         colidx = np.ascontiguousarray(colidx, dtype=np.int32)
         vals = np.ascontiguousarray(vals, dtype=np.float64)
         n = rowptr.shape[0] - 1
         nnz = colidx.shape[0]
-        if vals.shape != (nnz, M + 1):
-            raise ValueError(f"vals must have shape (nnz, M+1) = ({nnz}, {M + 1})")
+        nterm = M + 1 if q < 0 else math.comb(M + q, M)
+        if vals.shape != (nnz, nterm):
+            raise ValueError(f"vals must have shape (nnz, terms) = ({nnz}, {nterm})")
         mesh = _lib.sg_mesh(ne_x, ne_y)
         mp = None
         if mass is not None:
@@ -102,18 +107,28 @@ class SGProblem:
             mp = mass.ctypes.data_as(C.POINTER(C.c_double))
         h = C.c_void_p()
         torch.cuda.init()
-        check(_lib.LIB.sg_setup(C.byref(mesh), M, p, family, n, nnz,
-                                rowptr.ctypes.data_as(C.POINTER(C.c_int)), colidx.ctypes.data_as(C.POINTER(C.c_int)),
-                                vals.ctypes.data_as(C.POINTER(C.c_double)), mp, C.byref(h)), "sg_setup")
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+        dp = vals.ctypes.data_as(C.POINTER(C.c_double))
+        if q < 0:
+            check(_lib.LIB.sg_setup(C.byref(mesh), M, p, family, n, nnz, ip(rowptr), ip(colidx), dp, mp, C.byref(h)),
+                  "sg_setup")
+        else:
+            check(_lib.LIB.sg_setup_gpc(C.byref(mesh), M, p, q, family, n, nnz, ip(rowptr), ip(colidx), dp, mp,
+                                        C.byref(h)), "sg_setup_gpc")
         self.h = h
         dims = [C.c_int() for _ in range(5)]
         check(_lib.LIB.sg_problem_dims(h, *[C.byref(x) for x in dims]), "sg_problem_dims")
         self.n, self.P, self.M, self.p, self.nnz = (d.value for d in dims)
+        self.q, self.nterm = q, nterm
 
     @classmethod
     def from_inputs(cls, prob, p: int, family: int = SG_LEGENDRE) -> "SGProblem":
-        """From an ``sg_inputs.Problem`` (seeded synthetic problem)."""
-        return cls(prob.ne, prob.ne, prob.M, p, prob.rowptr, prob.colidx, prob.vals, prob.mass, family)
+        """From an ``sg_inputs.Problem`` (seeded synthetic problem); a gPC
+        (lognormal) problem takes Hermite chaos."""
+        q = getattr(prob, "coef_degree", -1)
+        if q >= 0:
+            family = SG_HERMITE
+        return cls(prob.ne, prob.ne, prob.M, p, prob.rowptr, prob.colidx, prob.vals, prob.mass, family, q)
 
     @property
     def inner_cluster(self) -> bool:

@@ -27,7 +27,7 @@ class sg_mesh(C.Structure):
 class sg_prec_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("top_level_f64", C.c_int), ("inner_tol", C.c_double),
                 ("inner_maxit", C.c_int), ("inner_fixed_iters", C.c_int), ("nu", C.c_int), ("omega", C.c_double),
-                ("m0", C.c_int)]
+                ("m0", C.c_int), ("level_tol", C.c_double), ("level_maxit", C.c_int)]
 
 
 class sg_solve_opts(C.Structure):
@@ -58,6 +58,9 @@ def _load():
     P = C.POINTER
     sig = {
         "sg_setup": (i, [P(sg_mesh), i, i, i, i, i, P(C.c_int), P(C.c_int), P(C.c_double), P(C.c_double), P(vp)]),
+        "sg_setup_gpc": (i, [P(sg_mesh), i, i, i, i, i, i, P(C.c_int), P(C.c_int), P(C.c_double), P(C.c_double),
+                             P(vp)]),
+        "sg_problem_terms": (i, [vp, P(i), P(i)]),
         "sg_destroy": (None, [vp]),
         "sg_set_scales": (i, [vp, P(C.c_double)]),
         "sg_problem_dims": (i, [vp, P(i), P(i), P(i), P(i), P(i)]),
@@ -110,7 +113,7 @@ def check(status: int, where: str):
 
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
-    return ["sg_setup", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
+    return ["sg_setup", "sg_setup_gpc", "sg_problem_terms", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
             "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
             "sg_autotune_outer_result", "sg_autotune_set",
             "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",

@@ -151,6 +151,7 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
   for (int cand = 0; cand < 2 * nc && r == SG_OK; ++cand) {
     const int c = cands[cand % nc], pairs = cand < nc ? 1 : 0;
     if ((h->P + c - 1) / c > 8) continue;   // at most 8 outputs per thread
+    if (pairs && h->q >= 0) continue;       // gPC: gather form only
     h->k1_threads[dtype] = c;
     h->k1_pairs[dtype] = pairs;
     r = launch_block_matvec(h, dtype, dtype, dtype, dtype, X, h->P, h->P, h->all, true, nullptr, 0, 1.0, 0.0, Y,
@@ -171,7 +172,7 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
     }
   }
   h->k1_threads[dtype] = best;
-  h->k1_pairs[dtype] = best_pairs;
+  h->k1_pairs[dtype] = h->q >= 0 ? 0 : best_pairs;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(X);
@@ -200,6 +201,7 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
     const int c = cands[cand % nc], pairs = cand < nc ? 1 : 0;
     const int maxo = (h->P + c - 1) / c;
     if (maxo > 8 || (c > 256 && maxo > 4)) continue;
+    if (pairs && h->q >= 0) continue;
     h->outer_threads = c;
     h->outer_pairs = pairs;
     r = launch_outer_matvec(h, a, s);
@@ -217,7 +219,7 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
     }
   }
   h->outer_threads = best;
-  h->outer_pairs = best_pairs;
+  h->outer_pairs = h->q >= 0 ? 0 : best_pairs;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return r;
@@ -227,10 +229,10 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
 // space and row lengths run the same launches, so a class is timed once per
 // process and later handles of that class take its shapes without timing.
 struct TuneKey {
-  int dev, n, nnz, M, p, family, max_row;
+  int dev, n, nnz, M, p, family, max_row, q;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, n, nnz, M, p, family, max_row) <
-           std::tie(o.dev, o.n, o.nnz, o.M, o.p, o.family, o.max_row);
+    return std::tie(dev, n, nnz, M, p, family, max_row, q) <
+           std::tie(o.dev, o.n, o.nnz, o.M, o.p, o.family, o.max_row, o.q);
   }
 };
 struct TuneVal {
@@ -240,7 +242,7 @@ static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
 static TuneKey tune_key(const sg_problem* h) {
-  return TuneKey{h->device, h->n, h->nnz, h->M, h->p, h->family, h->max_row_nnz};
+  return TuneKey{h->device, h->n, h->nnz, h->M, h->p, h->family, h->max_row_nnz, h->q};
 }
 
 // A block size the product kernels are instantiated for: whole warps, 32 to
@@ -304,9 +306,9 @@ int sg_autotune_set(sg_problem* h, int threads_f64, int threads_f32, int threads
   h->k1_threads[SG_F64] = threads_f64;
   h->k1_threads[SG_F32] = threads_f32;
   h->outer_threads = threads_outer;
-  h->k1_pairs[SG_F64] = pairs_f64 ? 1 : 0;
-  h->k1_pairs[SG_F32] = pairs_f32 ? 1 : 0;
-  h->outer_pairs = pairs_outer ? 1 : 0;
+  h->k1_pairs[SG_F64] = pairs_f64 && h->q < 0 ? 1 : 0;   // gPC: gather form only
+  h->k1_pairs[SG_F32] = pairs_f32 && h->q < 0 ? 1 : 0;
+  h->outer_pairs = pairs_outer && h->q < 0 ? 1 : 0;
   return SG_OK;
 }
 

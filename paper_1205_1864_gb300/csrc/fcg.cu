@@ -249,8 +249,9 @@ static int enqueue_schur_solve(sg_problem* h, const sg_solve_opts& o, cudaStream
 
 std::string opts_key(const sg_prec_opts& o) {
   char buf[256];
-  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d", o.precision, o.top_level_f64,
-           o.inner_tol, o.inner_maxit, o.inner_fixed_iters, o.nu, o.omega, o.m0);
+  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d|lt%.17g|lm%d", o.precision,
+           o.top_level_f64, o.inner_tol, o.inner_maxit, o.inner_fixed_iters, o.nu, o.omega, o.m0, o.level_tol,
+           o.level_maxit);
   return buf;
 }
 
@@ -370,6 +371,10 @@ int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts) {
     SG_TRY(check_prec_opts(opts->prec));
     SG_TRY(check_inner_support(h, opts->prec, "sg_solve"));
   }
+  if (opts->schur_reduced && h->q >= 0) {
+    set_error("sg_solve: the Schur-reduced system is built for the linear KL expansion only");
+    return SG_ERR_UNSUPPORTED;
+  }
   if (opts->schur_reduced && (h->p < 1 || opts->use_x0 || !(opts->schur_inner_tol >= 0.0))) {
     set_error("sg_solve: the Schur-reduced system needs p >= 1, use_x0 = 0 and schur_inner_tol >= 0");
     return SG_ERR_INVALID_ARG;
@@ -397,6 +402,10 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
     }
     SG_TRY(check_prec_opts(opts->prec));
     SG_TRY(check_inner_support(h, opts->prec, "sg_solve"));
+  }
+  if (opts->schur_reduced && h->q >= 0) {
+    set_error("sg_solve: the Schur-reduced system is built for the linear KL expansion only");
+    return SG_ERR_UNSUPPORTED;
   }
   if (opts->schur_reduced && (h->p < 1 || opts->use_x0 || !(opts->schur_inner_tol >= 0.0))) {
     set_error("sg_solve: the Schur-reduced system needs p >= 1, use_x0 = 0 and schur_inner_tol >= 0");

@@ -20,8 +20,102 @@
 
 #include "graph.cuh"
 #include "sghsc_internal.cuh"
+#include "vec.cuh"
 
 namespace sghsc {
+
+// Workspace of the nested D_l solves of the gPC case (before any capture).
+static int ensure_level(sg_problem* h, const sg_prec_opts& o) {
+  const int cap = std::min(o.level_maxit, 100000) + 2;
+  if (h->lx && h->lhist_cap >= cap) return SG_OK;
+  if (h->capturing) {
+    set_error("level workspace must be allocated before graph capture");
+    return SG_ERR_UNSUPPORTED;
+  }
+  if (h->lx) {
+    clear_graphs(h);
+    SG_TRY_CUDA(cudaDeviceSynchronize());
+  }
+  for (void* b : {(void*)h->lx, (void*)h->lr, (void*)h->lz, (void*)h->lp, (void*)h->lq, (void*)h->lb, (void*)h->lctl,
+                  (void*)h->lsc, (void*)h->lhist_alpha, (void*)h->lhist_beta, (void*)h->lhist_res})
+    cudaFree(b);
+  const size_t bytes = (size_t)h->n * std::max(h->wmax, 1) * sizeof(double);
+  for (double** b : {&h->lx, &h->lr, &h->lz, &h->lp, &h->lq, &h->lb}) SG_TRY_CUDA(cudaMalloc((void**)b, bytes));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->lctl, sizeof(OuterCtl)));
+  SG_TRY_CUDA(cudaMemset(h->lctl, 0, sizeof(OuterCtl)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->lsc, SC_COUNT * sizeof(double)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->lhist_alpha, cap * sizeof(double)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->lhist_beta, cap * sizeof(double)));
+  SG_TRY_CUDA(cudaMalloc((void**)&h->lhist_res, cap * sizeof(double)));
+  h->lhist_cap = cap;
+  return SG_OK;
+}
+
+// D_l^{-1} of the gPC case (Sec. 6, lognormal: D_l = sum_i A_i (x) G_i[l, l]
+// is not block diagonal, so "the solves involving D_l" are iterative): a
+// flexible CG on the n x w_l level block with the operator D_l (the SG product
+// restricted to the level, its i = 0 term the identity in chaos) and the
+// mean-based preconditioner I (x) A_0^{-1} (the batched inner PCG on A_0,
+// inner_tol), zero start, to level_tol. It reuses the outer iteration's
+// kernels with its own control block and scalars, one nesting level deeper.
+static int level_solve(sg_problem* h, int l, const double* src, int lds, double* dst, int ldd, const sg_prec_opts& o,
+                       cudaStream_t s) {
+  const int n = h->n, w = h->off[l + 1] - h->off[l];
+  if (w <= 0) return SG_OK;
+  const long long N = (long long)n * w;
+  const int vg = std::min(vec_grid(N), h->opart_blocks);
+  OuterArgs a0;
+  a0.part = h->opart;
+  a0.ctl = h->lctl;
+  a0.sc = h->lsc;
+  a0.hist_alpha = h->lhist_alpha;
+  a0.hist_beta = h->lhist_beta;
+  a0.hist_res = h->lhist_res;
+  a0.status = h->status;
+  a0.flexible = 1;
+  a0.maxit = std::min(o.level_maxit, h->lhist_cap - 2);
+  a0.tol = o.level_tol;
+  a0.cond = 0;
+  a0.has_cond = 0;
+  a0.flag = nullptr;
+  auto with = [&](const LoopCtl& lc) {
+    OuterArgs a = a0;
+    a.cond = lc.cond;
+    a.has_cond = lc.has_cond;
+    a.flag = lc.flag;
+    return a;
+  };
+  SG_TRY(launch_cast(src, SG_F64, lds, h->lb, SG_F64, w, n, w, s));
+  auto pre = [&](cudaStream_t ps, const LoopCtl& lc) -> int {
+    const OuterArgs a = with(lc);
+    SG_TRY_CUDA(cudaMemsetAsync(h->lx, 0, N * sizeof(double), ps));
+    { k_outer_init<<<vg, 256, 0, ps>>>(N, h->lb, nullptr, h->lr, a); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+    return SG_OK;
+  };
+  auto body = [&](cudaStream_t bs, const LoopCtl& lc) -> int {
+    const OuterArgs a = with(lc);
+    SG_TRY(inner_solve(h, SG_F64, h->lr, w, SG_F64, h->lz, w, SG_F64, w, o, bs));
+    { k_outer_dots<<<vg, 256, 0, bs>>>(N, h->lz, h->lr, h->lq, a); ::sghsc::note_launch(); }
+    { k_schur_p<<<vg, 256, 0, bs>>>(N, h->lz, h->lp, a); ::sghsc::note_launch(); }
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, h->lp, w, w, h->dlev[l], true, nullptr, 0, 1.0, 0.0,
+                               h->lq, w, bs));
+    { k_schur_pq<<<vg, 256, 0, bs>>>(N, h->lp, h->lq, a); ::sghsc::note_launch(); }
+    { k_outer_update<<<vg, 256, 0, bs>>>(N, h->lp, h->lp, h->lq, h->lx, h->lr, a); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+    return SG_OK;
+  };
+  SG_TRY(capture_while(h, s, pre, body));
+  return launch_cast(h->lx, SG_F64, w, dst, SG_F64, ldd, n, w, s);
+}
+
+// D_l^{-1}: the batched inner PCG on A_0 (linear KL expansion, Lemma of Sec. 3)
+// or the nested level CG (gPC coefficient).
+static int dsolve64(sg_problem* h, int l, const double* src, int lds, double* dst, int ldd, const sg_prec_opts& o,
+                    cudaStream_t s) {
+  if (h->q >= 0 && l >= 1) return level_solve(h, l, src, lds, dst, ldd, o, s);
+  return inner_solve(h, SG_F64, src, lds, SG_F64, dst, ldd, SG_F64, h->off[l + 1] - h->off[l], o, s);
+}
 
 static int ensure_hsc32(sg_problem* h) {
   if (h->R32) return SG_OK;
@@ -44,6 +138,11 @@ static int ensure_hsc64(sg_problem* h) {
 int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o) {
   SG_TRY(check_prec_opts(o));
   const int dt = o.precision == SG_F32 ? SG_F32 : SG_F64;
+  if (h->q >= 0 && (kind == SG_PREC_BGS || (kind == SG_PREC_HSC && dt == SG_F32))) {
+    set_error("gPC coefficient: Algorithm 1 runs in FP64 (nested D_l solves); block Gauss-Seidel is not built");
+    return SG_ERR_UNSUPPORTED;
+  }
+  if (h->q >= 0 && kind == SG_PREC_HSC) SG_TRY(ensure_level(h, o));
   if (kind == SG_PREC_HSC || kind == SG_PREC_BGS) {
     SG_TRY(ensure_inner_work(h, dt, h->wmax));
     SG_TRY(dt == SG_F32 ? ensure_hsc32(h) : ensure_hsc64(h));
@@ -100,21 +199,24 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
     SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));
     return SG_OK;
   }
-  // all FP64
+  // all FP64 (the pre-correction product writes the lower levels it reaches:
+  // level l-1 for the linear KL expansion, every lower level for a gPC one)
   double* Rw = h->R64w;
   SG_TRY_CUDA(cudaMemcpyAsync(Rw, R, (size_t)n * P * sizeof(double), cudaMemcpyDeviceToDevice, s));
   for (int l = p; l >= 1; --l) {
-    const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1];
-    SG_TRY(inner_solve(h, SG_F64, Rw + lo, P, SG_F64, Z + lo, P, SG_F64, w, o, s));
-    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo, P, w, h->pre[l], false, Rw + lo1, P, -1.0,
-                               1.0, Rw + lo1, P, s));
+    const int lo = off[l], w = off[l + 1] - off[l];
+    const EdgeList& B = h->pre[l];
+    SG_TRY(dsolve64(h, l, Rw + lo, P, Z + lo, P, o, s));
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo, P, w, B, false, Rw + B.out0, P, -1.0,
+                               1.0, Rw + B.out0, P, s));
   }
-  SG_TRY(inner_solve(h, SG_F64, Rw, P, SG_F64, Z, P, SG_F64, off[1] - off[0], o, s));
+  SG_TRY(dsolve64(h, 0, Rw, P, Z, P, o, s));
   for (int l = 1; l <= p; ++l) {
-    const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1], w1 = off[l] - off[l - 1];
-    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo1, P, w1, h->post[l], false, Rw + lo, P, -1.0,
+    const int lo = off[l], w = off[l + 1] - off[l];
+    const EdgeList& C = h->post[l];
+    SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + C.in0, P, C.nin, C, false, Rw + lo, P, -1.0,
                                1.0, h->T64, w, s));
-    SG_TRY(inner_solve(h, SG_F64, h->T64, w, SG_F64, Z + lo, P, SG_F64, w, o, s));
+    SG_TRY(dsolve64(h, l, h->T64, w, Z + lo, P, o, s));
   }
   return SG_OK;
 }

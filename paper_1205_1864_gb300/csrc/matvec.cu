@@ -324,7 +324,7 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
                     double alpha, double beta, TO* Y, int ldy, cudaStream_t s) {
   const int wy = E.nout;
   if (wy == 0) return SG_OK;
-  const int M1 = h->M + 1;
+  const int M1 = h->nterm;
   const TAcc* vals = nullptr;
   const TAcc* ec = nullptr;
   if constexpr (sizeof(TAcc) == 8) {
@@ -394,7 +394,7 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
 }
 
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
-  const int P = h->P, M1 = h->M + 1;
+  const int P = h->P, M1 = h->nterm;
   // whole warps, <= 1024: the autotuned block size or 256
   const int threads = h->outer_threads > 0 ? h->outer_threads : 256;
   const int maxo = (P + threads - 1) / threads;

@@ -140,6 +140,10 @@ static int theta_check(const sg_problem* h, const double* theta, const char* nam
     set_error("%s: invalid arguments", name);
     return SG_ERR_INVALID_ARG;
   }
+  if (h->q >= 0) {
+    set_error("%s: the parameterisation is that of the linear KL expansion", name);
+    return SG_ERR_UNSUPPORTED;
+  }
   for (int t = 0; t < h->M + 2; ++t)
     if (!std::isfinite(theta[t]) || theta[t] == 0.0) {
       set_error("%s: theta[%d] must be finite and nonzero", name, t);
@@ -192,9 +196,9 @@ int sg_qoi(sg_problem* h, const double* U, double* dQdU, double* q_out, void* st
 int sg_qoi_grad(sg_problem* h, const double* U, const double* Lam, int nparam, const double* W, double* grad,
                 double* hk_out, void* stream) {
   set_error("");
-  const int M1 = h ? h->M + 1 : 0;
+  const int M1 = h ? h->nterm : 0;
   if (!h || !U || !Lam || !W || !grad || nparam < 1 || M1 > QOI_MAXK) {
-    set_error("sg_qoi_grad: invalid arguments (M+1 must be <= %d)", QOI_MAXK);
+    set_error("sg_qoi_grad: invalid arguments (the value terms, M+1, must be <= %d)", QOI_MAXK);
     return SG_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;

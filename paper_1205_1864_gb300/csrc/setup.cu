@@ -64,7 +64,10 @@ struct HostEdges {
   std::vector<double> c;
 };
 
-static int upload_edges(const HostEdges& he, EdgeList& E) {
+static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 = 0, int nin = 0) {
+  E.out0 = out0;
+  E.in0 = in0;
+  E.nin = nin;
   E.nout = (int)he.ptr.size() - 1;
   E.nedges = (int)he.k.size();
   std::vector<float> c32(he.c.begin(), he.c.end());
@@ -108,6 +111,44 @@ static void free_edges(EdgeList& E) {
   cudaFree(E.pj);
   cudaFree(E.pair);
   E = EdgeList();
+}
+
+// E[psi_a psi_b psi_c] of normalised 1-D Hermite polynomials: with s = (a+b+c)/2,
+// sqrt(a! b! c!) / ((s-a)! (s-b)! (s-c)!) when s is an integer >= a, b, c, else 0.
+static double hermite_triple(int a, int b, int c) {
+  const int t = a + b + c;
+  if (t & 1) return 0.0;
+  const int s = t / 2;
+  if (s < a || s < b || s < c) return 0.0;
+  return std::exp(0.5 * (std::lgamma(a + 1.0) + std::lgamma(b + 1.0) + std::lgamma(c + 1.0)) -
+                  std::lgamma(s - a + 1.0) - std::lgamma(s - b + 1.0) - std::lgamma(s - c + 1.0));
+}
+
+// Couplings of a gPC-expanded coefficient (Remark K-L): for every output l of
+// [lo_out, hi_out) and input j of [lo_in, hi_in), every coefficient term
+// i >= 1 with c = E[psi_i psi_j psi_l] != 0 (the product of the 1-D Hermite
+// triple products over the coordinates). The term i = 0 is the identity
+// (E[psi_j psi_l] = delta_jl): the diagonal part of the product kernels.
+static HostEdges build_edges_gpc(const sg_problem* h, int lo_out, int hi_out, int lo_in, int hi_in) {
+  HostEdges he;
+  const int M = h->M;
+  for (int l = lo_out; l < hi_out; ++l) {
+    const int* al = h->alpha.data() + (size_t)l * M;
+    for (int j = lo_in; j < hi_in; ++j) {
+      const int* aj = h->alpha.data() + (size_t)j * M;
+      for (int i = 1; i < h->nterm; ++i) {
+        const int* gi = h->gamma.data() + (size_t)i * M;
+        double c = 1.0;
+        for (int k = 0; k < M && c != 0.0; ++k) c *= hermite_triple(gi[k], aj[k], al[k]);
+        if (c == 0.0) continue;
+        he.k.push_back(i);
+        he.j.push_back(j - lo_in);
+        he.c.push_back(c);
+      }
+    }
+    he.ptr.push_back((int)he.k.size());
+  }
+  return he;
 }
 
 // Build the gather-form couplings. For every output column l of [lo_out, hi_out)
@@ -193,7 +234,11 @@ static int upload_grid(GridLevel& g, const std::vector<double>& st) {
 }
 
 static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int nnz, const int* rowptr,
-                      const int* colidx, const double* vals, const double* mass_vals, sg_problem* h) {
+                      const int* colidx, const double* vals, const double* mass_vals, sg_problem* h, int q) {
+  if (q >= 0 && (family != SG_HERMITE || M < 1 || q > 16)) {
+    set_error("sg_setup_gpc: the gPC coefficient needs Hermite chaos, M >= 1 and a degree q <= 16");
+    return q >= 0 && family != SG_HERMITE ? SG_ERR_UNSUPPORTED : SG_ERR_INVALID_ARG;
+  }
   if (M < 0 || p < 0 || n <= 0 || nnz <= 0 || !rowptr || !colidx || !vals) {
     set_error("sg_setup: invalid sizes or null pointers (M=%d p=%d n=%d nnz=%d)", M, p, n, nnz);
     return SG_ERR_INVALID_ARG;
@@ -220,7 +265,19 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
       }
     }
   }
-  const size_t nv = (size_t)nnz * (M + 1);
+  // value terms per nonzero: the linear KL expansion has M + 1, the gPC one C(M + q, M)
+  long long nterm = M + 1;
+  if (q >= 0) {
+    nterm = 1;
+    for (int i = 1; i <= M; ++i) nterm = nterm * (q + i) / i;
+    if (nterm > 4096) {
+      set_error("sg_setup_gpc: %lld coefficient terms exceed the supported 4096", nterm);
+      return SG_ERR_UNSUPPORTED;
+    }
+  }
+  h->q = q;
+  h->nterm = (int)nterm;
+  const size_t nv = (size_t)nnz * nterm;
   for (size_t i = 0; i < nv; ++i) {
     if (!std::isfinite(vals[i])) {
       set_error("sg_setup: non-finite matrix value at %zu", i);
@@ -260,21 +317,43 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   std::map<std::vector<int>, int> index;
   for (int l = 0; l < h->P; ++l)
     index[std::vector<int>(h->alpha.begin() + (size_t)l * M, h->alpha.begin() + (size_t)(l + 1) * M)] = l;
-  SG_TRY(upload_edges(build_edges(h, index, 0, h->P, 0, h->P), h->all));
+  const std::vector<int>& off = h->off;
   h->pre.resize(p + 1);
   h->post.resize(p + 1);
-  for (int l = 1; l <= p; ++l) {
-    SG_TRY(upload_edges(build_edges(h, index, h->off[l - 1], h->off[l], h->off[l], h->off[l + 1]), h->pre[l]));
-    SG_TRY(upload_edges(build_edges(h, index, h->off[l], h->off[l + 1], h->off[l - 1], h->off[l]), h->post[l]));
+  if (q < 0) {
+    SG_TRY(upload_edges(build_edges(h, index, 0, h->P, 0, h->P), h->all, 0, 0, h->P));
+    for (int l = 1; l <= p; ++l) {
+      SG_TRY(upload_edges(build_edges(h, index, off[l - 1], off[l], off[l], off[l + 1]), h->pre[l], off[l - 1],
+                          off[l], off[l + 1] - off[l]));
+      SG_TRY(upload_edges(build_edges(h, index, off[l], off[l + 1], off[l - 1], off[l]), h->post[l], off[l],
+                          off[l - 1], off[l] - off[l - 1]));
+    }
+    if (p >= 1) SG_TRY(upload_edges(build_edges(h, index, 0, off[p], 0, off[p]), h->sub, 0, 0, off[p]));
+  } else {
+    // the coefficient terms in the same graded order
+    std::vector<int> cur(M);
+    for (int d = 0; d <= q; ++d) emit_degree(M, 0, d, cur, h->gamma);
+    SG_TRY(upload_edges(build_edges_gpc(h, 0, h->P, 0, h->P), h->all, 0, 0, h->P));
+    h->dlev.resize(p + 1);
+    for (int l = 1; l <= p; ++l) {
+      // B_l: every lower level from level l; C_l: level l from every lower level; D_l: level l with itself
+      SG_TRY(upload_edges(build_edges_gpc(h, 0, off[l], off[l], off[l + 1]), h->pre[l], 0, off[l],
+                          off[l + 1] - off[l]));
+      SG_TRY(upload_edges(build_edges_gpc(h, off[l], off[l + 1], 0, off[l]), h->post[l], off[l], 0, off[l]));
+      SG_TRY(upload_edges(build_edges_gpc(h, off[l], off[l + 1], off[l], off[l + 1]), h->dlev[l], off[l], off[l],
+                          off[l + 1] - off[l]));
+    }
+    // the pair form keeps one sum per distinct (term, input) in shared memory:
+    // too many with a dense coupling, so the gPC products use the gather form
+    h->k1_pairs[0] = h->k1_pairs[1] = h->outer_pairs = 0;
   }
-  if (p >= 1) SG_TRY(upload_edges(build_edges(h, index, 0, h->off[p], 0, h->off[p]), h->sub));
 
   // matrices
   SG_TRY(upload(&h->rowptr, rowptr, (size_t)n + 1));
   SG_TRY(upload(&h->colidx, colidx, (size_t)nnz));
   SG_TRY(upload(&h->vals64, vals, nv));
   SG_TRY(upload(&h->vals_base, vals, nv));
-  h->scales.assign(M + 1, 1.0);
+  h->scales.assign(h->nterm, 1.0);
   SG_TRY(upload(&h->scales_dev, h->scales.data(), h->scales.size()));
   {
     std::vector<float> v32(vals, vals + nv);
@@ -301,7 +380,7 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
         const int c = colidx[e], cx = c % nx, cy = c / nx;
         const int dx = cx - x, dy = cy - y;
         if (dx < -1 || dx > 1 || dy < -1 || dy > 1) { ok = false; break; }
-        st[(size_t)r * 9 + (dy + 1) * 3 + (dx + 1)] += vals[(size_t)e * (M + 1)];
+        st[(size_t)r * 9 + (dy + 1) * 3 + (dx + 1)] += vals[(size_t)e * h->nterm];
       }
       if (ok && !(st[(size_t)r * 9 + 4] > 0.0)) ok = false;
     }
@@ -392,7 +471,7 @@ int sg_set_scales(sg_problem* h, const double* scale) {
     set_error("sg_set_scales: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
-  for (int k = 0; k <= h->M; ++k)
+  for (int k = 0; k < h->nterm; ++k)
     if (!std::isfinite(scale[k])) {
       set_error("sg_set_scales: non-finite scale %d", k);
       return SG_ERR_INVALID_ARG;
@@ -402,10 +481,10 @@ int sg_set_scales(sg_problem* h, const double* scale) {
     return SG_ERR_INVALID_ARG;
   }
   SG_TRY_CUDA(cudaDeviceSynchronize());   // no solve may be reading the values
-  h->scales.assign(scale, scale + h->M + 1);
-  SG_TRY_CUDA(cudaMemcpy(h->scales_dev, scale, (h->M + 1) * sizeof(double), cudaMemcpyHostToDevice));
-  const long long count = (long long)h->nnz * (h->M + 1);
-  { k_scale_vals<<<(int)std::min<long long>((count + 255) / 256, 4096), 256>>>(count, h->M + 1, h->vals_base, h->scales_dev, h->vals64, h->vals32); ::sghsc::note_launch(); }
+  h->scales.assign(scale, scale + h->nterm);
+  SG_TRY_CUDA(cudaMemcpy(h->scales_dev, scale, h->nterm * sizeof(double), cudaMemcpyHostToDevice));
+  const long long count = (long long)h->nnz * h->nterm;
+  { k_scale_vals<<<(int)std::min<long long>((count + 255) / 256, 4096), 256>>>(count, h->nterm, h->vals_base, h->scales_dev, h->vals64, h->vals32); ::sghsc::note_launch(); }
   for (auto& g : h->grids)
     { k_scale_grid<<<std::min((g.n * 9 + 255) / 256, 4096), 256>>>(g.n, g.st_base, scale[0], g.st64, g.st32, g.dinv64, g.dinv32); ::sghsc::note_launch(); }
   SG_TRY_CUDA(cudaGetLastError());
@@ -428,6 +507,8 @@ void sg_default_prec_opts(sg_prec_opts* o) {
   o->nu = 2;
   o->omega = 0.8;
   o->m0 = SG_M0_VCYCLE;
+  o->level_tol = 1e-8;
+  o->level_maxit = 500;
 }
 
 void sg_default_solve_opts(sg_solve_opts* o) {
@@ -452,12 +533,40 @@ int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz, cons
   }
   *out = nullptr;
   sg_problem* h = new sg_problem();
-  int st = setup_impl(mesh, M, p, family, n, nnz, rowptr, colidx, vals, mass_vals, h);
+  int st = setup_impl(mesh, M, p, family, n, nnz, rowptr, colidx, vals, mass_vals, h, -1);
   if (st != SG_OK) {
     sg_destroy(h);
     return st;
   }
   *out = h;
+  return SG_OK;
+}
+
+int sg_setup_gpc(const sg_mesh* mesh, int M, int p, int q, int family, int n, int nnz, const int* rowptr,
+                 const int* colidx, const double* vals, const double* mass_vals, sg_problem** out) {
+  set_error("");
+  if (!out || q < 0) {
+    set_error("sg_setup_gpc: out is null or q < 0");
+    return SG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  sg_problem* h = new sg_problem();
+  int st = setup_impl(mesh, M, p, family, n, nnz, rowptr, colidx, vals, mass_vals, h, q);
+  if (st != SG_OK) {
+    sg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return SG_OK;
+}
+
+int sg_problem_terms(const sg_problem* h, int* nterm, int* q) {
+  if (!h) {
+    set_error("sg_problem_terms: null handle");
+    return SG_ERR_INVALID_ARG;
+  }
+  if (nterm) *nterm = h->nterm;
+  if (q) *q = h->q;
   return SG_OK;
 }
 
@@ -467,6 +576,7 @@ void sg_destroy(sg_problem* h) {
   for (auto& e : h->pre) free_edges(e);
   for (auto& e : h->post) free_edges(e);
   free_edges(h->sub);
+  for (auto& e : h->dlev) free_edges(e);
   for (auto& g : h->grids) {
     cudaFree(g.st_base); cudaFree(g.st64); cudaFree(g.st32); cudaFree(g.dinv64); cudaFree(g.dinv32);
   }
@@ -476,7 +586,9 @@ void sg_destroy(sg_problem* h) {
   cluster_free(h);
   void* bufs[] = {h->rowptr, h->colidx, h->vals64, h->vals32, h->mass64, h->R32, h->Z32, h->T32, h->R64w,
                   h->T64, h->fF, h->fx, h->fr, h->fz, h->fpA, h->fpB, h->fq, h->opart, h->osc, h->octl,
-                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev, h->fG};
+                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev, h->fG,
+                  h->lx, h->lr, h->lz, h->lp, h->lq, h->lb, h->lctl, h->lsc, h->lhist_alpha, h->lhist_beta,
+                  h->lhist_res};
   for (void* b : bufs) cudaFree(b);
   for (auto& cs : h->cap)
     if (cs) cudaStreamDestroy(cs);

@@ -49,6 +49,7 @@ enum : int {
 // column j (local index in the input range) and coefficient c = (G_k)_{lj}.
 struct EdgeList {
   int nout = 0, nedges = 0;
+  int out0 = 0, in0 = 0, nin = 0;   // chaos columns [out0, out0 + nout) from [in0, in0 + nin)
   int* ptr = nullptr;
   int* perm = nullptr;   // thread slot -> output column, by coupling count (descending, stable)
   int* k = nullptr;
@@ -117,6 +118,8 @@ struct GraphEntry {
 
 struct sg_problem {
   int n = 0, nnz = 0, M = 0, p = 0, P = 0, family = 0;
+  int q = -1;                         // -1: linear KL expansion; >= 0: gPC coefficient of total degree q
+  int nterm = 0;                      // value terms per nonzero: M + 1, or C(M + q, M) for the gPC case
   int nx = 0, ny = 0;                 // mesh interior size (0 if no mesh)
   int device = 0, num_sms = 0;
   int smem_optin = 0;                 // shared memory a block may opt in to (bytes)
@@ -137,6 +140,16 @@ struct sg_problem {
   std::vector<sghsc::EdgeList> pre;         // pre[l]:  out level l-1, in level l   (B_l), l = 1..p
   std::vector<sghsc::EdgeList> post;        // post[l]: out level l,   in level l-1 (C_l), l = 1..p
   sghsc::EdgeList sub;                      // levels 0..p-1 among themselves (A_{p-1}, Schur-reduced system)
+  // gPC coefficient (q >= 0): B_l reaches every lower level and D_l is not block
+  // diagonal; dlev[l] holds the couplings of level l with itself (i >= 1)
+  std::vector<sghsc::EdgeList> dlev;
+  std::vector<int> gamma;                   // host nterm*M: multi-indices of the coefficient terms
+  // nested Krylov solves with D_l (gPC case): FP64 blocks n x wmax and their CG control
+  double *lx = nullptr, *lr = nullptr, *lz = nullptr, *lp = nullptr, *lq = nullptr, *lb = nullptr;
+  sghsc::OuterCtl* lctl = nullptr;
+  double* lsc = nullptr;
+  double *lhist_alpha = nullptr, *lhist_beta = nullptr, *lhist_res = nullptr;
+  int lhist_cap = 0;
   double* fG = nullptr;                     // n x off[p] right-hand side g_{p-1} of the reduced system
   // multigrid
   std::vector<sghsc::GridLevel> grids;

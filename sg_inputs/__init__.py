@@ -38,6 +38,7 @@ from scipy.optimize import brentq
 __all__ = [
     "kl_1d", "kl_2d", "Problem", "make_problem", "make_rhs", "random_block",
     "CONFIGS", "draw_batch_configs", "draw_grad_params", "chaos_count", "make_unit_problem", "theta_of",
+    "make_lognormal_problem",
 ]
 
 
@@ -192,6 +193,8 @@ class Problem:
     vals: np.ndarray             # (nnz, M+1) float64: A_0 .. A_M on the shared pattern
     mass: np.ndarray             # (nnz,) float64: consistent Q1 mass matrix
     f0: np.ndarray               # (n,) float64: load vector of f = 1
+    coef_degree: int = -1        # -1: linear KL expansion (vals has M+1 terms); q >= 0: gPC expansion of
+                                 # the coefficient to total degree q (vals has C(M+q, M) terms, graded order)
 
     @property
     def n(self) -> int:
@@ -238,6 +241,71 @@ def make_problem(ne: int, M: int, sigma: float, corr_len: float, a_mean: float =
     f0 = np.full(n, h * h)
     return Problem(ne=ne, M=M, sigma=sigma, corr_len=corr_len, a_mean=a_mean, sqrt_lambda=s,
                    rowptr=rowptr, colidx=colidx, vals=vals, mass=mass[:, 0].copy(), f0=f0)
+
+
+def _graded_indices(M: int, q: int) -> List[tuple]:
+    """Multi-indices of total degree <= q: degrees ascending, descending
+    lexicographic order inside a degree (the chaos order of the solver)."""
+    def desc(d, m):
+        if m == 1:
+            yield (d,)
+            return
+        for a in range(d, -1, -1):
+            for rest in desc(d - a, m - 1):
+                yield (a,) + rest
+    out = []
+    for d in range(q + 1):
+        out.extend(desc(d, M) if M > 0 else ([()] if d == 0 else []))
+    return out
+
+
+def make_lognormal_problem(ne: int, M: int, cov: float, corr_len: float, q: int) -> Problem:
+    """Stiffness matrices of the gPC expansion of a lognormal coefficient
+    (Sec. 6, second set of experiments; Remark K-L).
+
+    ``k(x, xi) = exp(g(x, xi))`` with the Gaussian field
+    ``g = mu_g + sigma_g sum_k s_k phi_k(x) xi_k``, ``xi_k ~ N(0,1)``, the same
+    separable exponential-covariance KL pairs as the uniform case. Reading of
+    the paper's "CoV = sigma_log / mu_log" (the mean and standard deviation of
+    ``k`` itself, mean 1): ``sigma_g^2 = ln(1 + CoV^2)``, ``mu_g = -sigma_g^2/2``.
+    Its expansion in normalised Hermite polynomials ``psi_gamma`` has the
+    closed-form coefficients
+    ``k_gamma(x) = exp(mu_g + sum_k a_k(x)^2 / 2) prod_k a_k(x)^gamma_k / sqrt(gamma_k!)``
+    with ``a_k = sigma_g s_k phi_k`` (the generating function of Hermite
+    polynomials). The expansion is kept to total degree ``q`` (the paper uses
+    twice the degree of the solution); ``vals[:, i]`` is the stiffness matrix of
+    ``k_gamma_i``, ``gamma_i`` in the graded chaos order.
+    """
+    if ne < 2:
+        raise ValueError("ne must be >= 2")
+    h = 1.0 / ne
+    kl = kl_2d(corr_len, M) if M > 0 else []
+    s = np.array([math.sqrt(lam) for lam, _, _ in kl], dtype=np.float64)
+    sig2 = math.log(1.0 + cov * cov)
+    sig_g, mu_g = math.sqrt(sig2), -0.5 * sig2
+    ex = np.arange(ne)
+    gx = np.stack([(ex + (1 + xi) / 2) * h for xi, _ in _GP], axis=-1)
+    gy = np.stack([(ex + (1 + eta) / 2) * h for _, eta in _GP], axis=-1)
+    a = np.empty((M, ne, ne, 4))
+    for k, (lam, mx, my) in enumerate(kl):
+        a[k] = sig_g * s[k] * eval_kl_1d(my, gy)[:, None, :] * eval_kl_1d(mx, gx)[None, :, :]
+    mean = np.exp(mu_g + 0.5 * np.sum(a * a, axis=0)) if M > 0 else np.full((ne, ne, 4), math.exp(mu_g))
+    gammas = _graded_indices(M, q)
+    kappa = np.empty((len(gammas), ne, ne, 4))
+    for i, g in enumerate(gammas):
+        v = mean.copy()
+        for k, gk in enumerate(g):
+            if gk:
+                v *= a[k] ** gk / math.sqrt(math.factorial(gk))
+        kappa[i] = v
+    B, Mm = _element_tables()
+    S = _assemble_stencils(ne, kappa, B, 1.0)
+    rowptr, colidx, vals = _interior_csr(ne, S)
+    Sm = _assemble_stencils(ne, np.ones((1, ne, ne, 4)), Mm, h * h / 4.0)
+    _, _, mass = _interior_csr(ne, Sm)
+    n = (ne - 1) ** 2
+    return Problem(ne=ne, M=M, sigma=sig_g, corr_len=corr_len, a_mean=1.0, sqrt_lambda=s, rowptr=rowptr,
+                   colidx=colidx, vals=vals, mass=mass[:, 0].copy(), f0=np.full(n, h * h), coef_degree=q)
 
 
 def make_unit_problem(ne: int, M: int, corr_len: float) -> Problem:

@@ -81,3 +81,39 @@ def test_draws_seeded_and_in_range():
         assert 0.1 <= c["sigma"] <= 0.3 and 0.3 <= c["corr_len"] <= 1.5
     g = S.draw_grad_params(4, 16)
     assert len(g) == 16 and all(0.1 <= d["sigma"] <= 0.25 for d in g)
+
+
+def test_lognormal_gpc_coefficients_reproduce_the_field():
+    """The closed-form gPC coefficients of the lognormal coefficient: at an
+    interior Gauss point, sum_i k_i(x) psi_i(xi) approaches exp(g(x, xi)) as
+    the expansion degree grows, and k_0 is the mean of exp(g)."""
+    import math as _m
+
+    from numpy.polynomial import hermite_e as He
+    ne, M, cov, L = 4, 2, 1.0, 0.5
+    sig2 = _m.log(1 + cov * cov)
+    kl = S.kl_2d(L, M)
+    hx = 1.0 / ne
+    g0 = (1 - 1 / _m.sqrt(3)) / 2 * hx                      # first Gauss point of the first element
+    a = np.array([_m.sqrt(sig2) * _m.sqrt(lam) * S.eval_kl_1d(mx, g0) * S.eval_kl_1d(my, g0) for lam, mx, my in kl])
+    rng = np.random.default_rng(3)
+    xi = rng.standard_normal(M) * 0.8
+    exact = _m.exp(-0.5 * sig2 + float(a @ xi))
+    assert S._graded_indices(M, 1) == [(0, 0), (1, 0), (0, 1)]
+    errs = []
+    for q in (2, 6, 12):
+        gam = S._graded_indices(M, q)
+        mean = _m.exp(-0.5 * sig2 + 0.5 * float(a @ a))
+        tot = 0.0
+        for g in gam:
+            ki = mean * np.prod([a[k] ** g[k] / _m.sqrt(_m.factorial(g[k])) for k in range(M)])
+            psi = np.prod([He.hermeval(xi[k], [0] * g[k] + [1]) / _m.sqrt(_m.factorial(g[k])) for k in range(M)])
+            tot += ki * psi
+        errs.append(abs(tot - exact) / exact)
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-9
+    prob = S.make_lognormal_problem(ne, M, cov, L, 4)
+    assert prob.vals.shape[1] == _m.comb(M + 4, M) and prob.coef_degree == 4
+    # the mean matrix is a stiffness matrix of a positive coefficient: symmetric, positive diagonal
+    import scipy.sparse as sp
+    A0 = sp.csr_matrix((prob.vals[:, 0], prob.colidx, prob.rowptr), shape=(prob.n, prob.n))
+    assert abs(A0 - A0.T).max() < 1e-14 and np.all(A0.diagonal() > 0)

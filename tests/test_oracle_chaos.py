@@ -132,3 +132,39 @@ def test_block_count_closed_forms(M, p):
     c = chaos.block_counts(M, p)
     assert c["n_db"] == math.comb(M + p, M)
     assert c["n_m"] == 2 * M * math.comb(M + p - 1, M)
+
+
+def test_hermite_triple_products_against_quadrature():
+    """The closed-form normalised Hermite triple products against Gauss-Hermite
+    quadrature (probabilists' weight), all orders up to 8."""
+    from numpy.polynomial import hermite_e as He
+    x, w = He.hermegauss(40)
+    w = w / np.sqrt(2 * np.pi)
+    psi = [He.hermeval(x, [0] * m + [1]) / math.sqrt(math.factorial(m)) for m in range(9)]
+    for a in range(9):
+        for b in range(9):
+            for c in range(9):
+                ref = float(np.sum(w * psi[a] * psi[b] * psi[c]))
+                assert chaos.hermite_triple_1d(a, b, c) == pytest.approx(ref, abs=1e-9 * max(1.0, abs(ref)))
+
+
+@pytest.mark.parametrize("M,p", [(2, 3), (3, 2)])
+def test_gpc_matrices_reduce_to_the_linear_expansion(M, p):
+    """With the coefficient expanded to degree 1 the gPC matrices are the KL
+    ones of the Hermite family: G_0 = I and G_{e_k} = E[xi_k psi_j psi_l]; for
+    any degree each G_i is symmetric and couples j, l only when the degrees
+    allow it (|alpha_j| - |alpha_l| <= |gamma_i| <= |alpha_j| + |alpha_l|)."""
+    G1 = chaos.gpc_g_matrices(M, p, 1)
+    Gk = chaos.g_matrices(M, p, chaos.HERMITE)
+    assert len(G1) == len(Gk)
+    for a, b in zip(G1, Gk):
+        assert abs(a - b).max() < 1e-14
+    Gq = chaos.gpc_g_matrices(M, p, 2 * p)
+    alpha, _ = chaos.multi_indices(M, p)
+    gamma, _ = chaos.multi_indices(M, 2 * p)
+    for g, G in zip(gamma, Gq):
+        assert abs(G - G.T).max() < 1e-14
+        C = G.tocoo()
+        for j, l in zip(C.row, C.col):
+            dj, dl, dg = alpha[j].sum(), alpha[l].sum(), g.sum()
+            assert abs(dj - dl) <= dg <= dj + dl

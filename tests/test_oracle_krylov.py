@@ -125,3 +125,52 @@ def test_pcg_columns_conventions():
     Xs, it = krylov.pcg_columns(lambda v: A @ v, B, lambda r: r.copy(), tol=1e-3, maxit=100)
     for s in (0, 1, 3):
         assert np.linalg.norm(B[:, s] - A @ Xs[:, s]) <= 1e-3 * np.linalg.norm(B[:, s]) * (1 + 1e-9)
+
+
+def _lognormal_run(M, p, cov, ne=10):
+    """Sec. 6 lognormal setting: 10x10 mesh, L = 0.5, gPC expansion of the
+    coefficient to degree 2p (Hermite chaos), exact inner solves; D_l is not
+    block diagonal, so Algorithm 1 factors each D_l as it stands."""
+    prob = S.make_lognormal_problem(ne, M, cov, 0.5, 2 * p)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.gpc_g_matrices(M, p, 2 * p)
+    _, off = chaos.multi_indices(M, p)
+    F = S.make_rhs(prob, p)
+    a0 = hsc.A0Solver(A[0])
+    ap = lambda U: so.sg_apply(A, G, U)
+    out = {}
+    for name, prec in (("mean", lambda R: hsc.mean_apply(A, R, a0)),
+                       ("hsc", lambda R: hsc.hsc_apply(A, G, off, R, general=True, a0solve=a0)),
+                       ("bgs", lambda R: hsc.bgs_apply(A, G, R))):
+        _, info = krylov.fcg(ap, F, prec, tol=1e-8, maxit=1000)
+        out[name] = (info["iters"], krylov.lanczos_kappa(info["alpha"], info["beta"]))
+    return out
+
+
+def lognormal_soft(out, m_it, m_k, b_it, b_k, h_it, h_k):
+    """Soft agreement with the paper's lognormal tables: its field came from a
+    discretised KL eigenproblem and its CoV reading is not stated, so the
+    values agree to within 25 % in kappa and 25 % (at least 3) in
+    iterations; the paper's findings hold exactly: M_HS has the smallest
+    condition estimate, needs at most one iteration more than M_bGS, and both
+    need far fewer than M_m."""
+    for (it, k), (pit, pk) in ((out["mean"], (m_it, m_k)), (out["bgs"], (b_it, b_k)), (out["hsc"], (h_it, h_k))):
+        assert abs(it - pit) <= max(3, 0.25 * pit)
+        assert k == pytest.approx(pk, rel=0.25)
+    assert out["hsc"][1] < out["bgs"][1] < out["mean"][1]
+    assert out["hsc"][0] <= out["bgs"][0] + 1
+    assert 2 * max(out["hsc"][0], out["bgs"][0]) < out["mean"][0] + 2
+
+
+@pytest.mark.parametrize("row", [r for r in _read("sec6_table6_lognormal_vary_N.txt") if r[0] <= 2],
+                         ids=lambda r: f"N{int(r[0])}")
+def test_paper_table6_lognormal_soft(row):
+    N, _, _, _, m_it, m_k, b_it, b_k, h_it, h_k = row
+    lognormal_soft(_lognormal_run(int(N), 4, 1.0), m_it, m_k, b_it, b_k, h_it, h_k)
+
+
+@pytest.mark.parametrize("row", [r for r in _read("sec6_table7_lognormal_vary_P.txt") if r[0] <= 3],
+                         ids=lambda r: f"P{int(r[0])}")
+def test_paper_table7_lognormal_soft(row):
+    p, _, _, _, m_it, m_k, b_it, b_k, h_it, h_k = row
+    lognormal_soft(_lognormal_run(4, int(p), 1.0), m_it, m_k, b_it, b_k, h_it, h_k)
