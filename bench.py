@@ -175,13 +175,16 @@ def run_ours(args, rank, world, dev):
     U = torch.empty_like(F)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    hsc_opts = L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=1e-2),
+    # headline: mixed HSC, the products that read the FP32 preconditioner output in double-float arithmetic
+    hsc_opts = L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=1e-2, df64=1),
                             precond=L.SG_PREC_HSC, tol=1e-8, maxit=500, check_true_residual=0)
+    hsc_f64prod_opts = L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=1e-2, df64=0),
+                                    precond=L.SG_PREC_HSC, tol=1e-8, maxit=500, check_true_residual=0)
     mean_opts = L.solve_opts(L.prec_opts(precision=L.SG_F64, inner_tol=1e-2), precond=L.SG_PREC_MEAN,
                              tol=1e-8, maxit=500, check_true_residual=0)
     hsc64_opts = L.solve_opts(L.prec_opts(precision=L.SG_F64, inner_tol=1e-2), precond=L.SG_PREC_HSC,
                               tol=1e-8, maxit=500, check_true_residual=0)
-    mean32_opts = L.solve_opts(L.prec_opts(precision=L.SG_F32, inner_tol=1e-2), precond=L.SG_PREC_MEAN,
+    mean32_opts = L.solve_opts(L.prec_opts(precision=L.SG_F32, inner_tol=1e-2, df64=1), precond=L.SG_PREC_MEAN,
                                tol=1e-8, maxit=500, check_true_residual=0)
 
     def timed_solves(opts, steps, warmup, count_launches=False):
@@ -265,12 +268,17 @@ def run_ours(args, rank, world, dev):
     # validation solve (untimed): the true FP64 residual of the same HSC solve
     _, st_true = L.sg_solve(h, F, L.solve_opts(hsc_opts.prec, precond=L.SG_PREC_HSC, tol=1e-8, maxit=500,
                                                check_true_residual=1), U)
+    # the solution's residual by the oracle (FP64, host cores; the solve is not timed)
+    oracle_res = None
+    if rank == 0 and not args.no_cpu_baseline:
+        oracle_res = oracle_residual(prob, p, F_np, U.cpu().numpy())
     # comparators on the same GPU, each precision with each preconditioner, so
     # that the speed-up splits into preconditioner and precision: the metric's
     # own comparator is the all-FP64 mean-based PCG
     cmp_steps = max(1, min(args.steps, 2))
     comparators = {}
-    for key, opts in (("mean_fp64", mean_opts), ("hsc_fp64", hsc64_opts), ("mean_mixed", mean32_opts)):
+    for key, opts in (("mean_fp64", mean_opts), ("hsc_fp64", hsc64_opts), ("mean_mixed", mean32_opts),
+                      ("hsc_mixed_fp64_products", hsc_f64prod_opts)):
         ts_c, st_c, _ = timed_solves(opts, cmp_steps, 1)
         comparators[key] = {"ms": float(np.mean(ts_c)), "iterations": st_c.iterations, "rel_res": st_c.rel_res,
                             "kappa_est": st_c.kappa_est, "step_ms": ts_c}
@@ -354,7 +362,7 @@ def run_ours(args, rank, world, dev):
     out = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 outer / f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
+        "dtype": "f64 outer CG, df64 (FP32-pair) outer/top-level products, f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
         "config": {"workload": cfg["name"], "ne": cfg["ne"], "M": M, "p": p, "P": P, "n": n,
                    "unknowns": n * P, "sigma": cfg["sigma"], "corr_len": cfg["corr_len"], "inner_tol": 1e-2,
                    "tol": 1e-8, "l2": "flushed between timed steps (256 MiB write, outside the events)",
@@ -362,6 +370,8 @@ def run_ours(args, rank, world, dev):
                    "autotuned_pair_form_f64_f32_outer": list(forms),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "hsc": {"ms": ms, "iterations": st_h.iterations, "true_rel_res": st_true.true_rel_res,
+                "oracle_rel_res": oracle_res, "arithmetic": "FP32 inner solves and level products < p; outer CG "
+                "FP64; outer SG product and level-p products in double-float (df64) on the FP32 units",
                 "kappa_est": st_h.kappa_est, "inner_iters_total": st_h.inner_iters_total,
                 "inner_iters_max": st_h.inner_iters_max, "step_ms": ts},
         "mean_fp64": {"ms": ms_mean, "iterations": comparators["mean_fp64"]["iterations"],
@@ -372,7 +382,9 @@ def run_ours(args, rank, world, dev):
                      "preconditioner_fp64 (mean_fp64 / hsc_fp64)": ms_mean / comparators["hsc_fp64"]["ms"],
                      "preconditioner_mixed (mean_mixed / hsc_mixed)": comparators["mean_mixed"]["ms"] / ms,
                      "precision_hsc (hsc_fp64 / hsc_mixed)": comparators["hsc_fp64"]["ms"] / ms,
-                     "precision_mean (mean_fp64 / mean_mixed)": ms_mean / comparators["mean_mixed"]["ms"]},
+                     "precision_mean (mean_fp64 / mean_mixed)": ms_mean / comparators["mean_mixed"]["ms"],
+                     "double_float_products (hsc_mixed_fp64_products / hsc_mixed)":
+                         comparators["hsc_mixed_fp64_products"]["ms"] / ms},
         "sg_matvec": matvec,
         "roofline": roofline,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(F_host.numel() * 8),
@@ -389,8 +401,27 @@ def run_ours(args, rank, world, dev):
     return out
 
 
+def oracle_residual(prob, p, F, U):
+    """||F - A U|| / ||F|| by the FP64 oracle, blocks of rows on a thread pool."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import chaos, sg_operator as so
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(prob.M, p)
+    n, blk = F.shape[0], 8192
+
+    def part(s0):
+        rows = np.arange(s0, min(s0 + blk, n))
+        R = F[rows] - so.sg_apply_rows(A, G, U, rows)
+        return float(np.sum(R * R))
+
+    with ThreadPoolExecutor(host_cores()) as ex:
+        ss = sum(ex.map(part, range(0, n, blk)))
+    return float(np.sqrt(ss) / np.linalg.norm(F))
+
+
 def _hsc_opts(L, check=0):
-    return L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=1e-2),
+    return L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=1e-2, df64=1),
                         precond=L.SG_PREC_HSC, tol=1e-8, maxit=500, check_true_residual=check)
 
 
@@ -515,7 +546,7 @@ def run_batch(args, rank, world, dev):
     out = {
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
-        "dtype": "f64 outer / f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
+        "dtype": "f64 outer CG, df64 (FP32-pair) outer/top-level products, f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
         "config": {"workload": cfg["name"], "systems": len(cfgs), "systems_this_rank": len(mine),
                    "unknowns_this_rank": unknowns, "draw_seed": cfg["seed"], "tol": 1e-8, "inner_tol": 1e-2,
                    "l2": "flushed between timed steps (256 MiB write, outside the events)",

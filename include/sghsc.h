@@ -57,8 +57,9 @@ typedef enum {
 enum { SG_F64 = 0, SG_F32 = 1 };                     /* element type of a block */
 /* sg_level_apply only: X and Yout FP32, Yin FP64, products accumulated and
  * subtracted in FP64 (the level-p products of the mixed preconditioner with
- * top_level_f64, Algorithm 1). */
-enum { SG_F32_ACC64 = 2 };
+ * top_level_f64, Algorithm 1), or in double-float arithmetic on the FP32
+ * units (the same with sg_prec_opts.df64). */
+enum { SG_F32_ACC64 = 2, SG_F32_ACCDF64 = 3 };
 enum { SG_LEGENDRE = 0, SG_HERMITE = 1 };            /* chaos family */
 enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_HSC = 2, SG_PREC_BGS = 3 };
 
@@ -90,6 +91,14 @@ typedef struct {
                              the level block, preconditioned by the inner PCG on A_0 per
                              column, to this relative residual */
   int level_maxit;        /* cap on the iterations of that nested CG */
+  int df64;               /* with precision SG_F32: 1 runs the FP64-accurate products that read
+                             the FP32 preconditioner's output -- the level-p products of
+                             Algorithm 1 (top_level_f64) and, in sg_solve, the outer SG product
+                             q = A p -- in double-float arithmetic (pairs of FP32 numbers, a
+                             48-bit significand; products and sums by error-free
+                             transformations) on the FP32 units, whose multiply-add rate on this
+                             GPU is about 70 times the FP64 one; each output is finished in
+                             FP64. 0: FP64 arithmetic. */
 } sg_prec_opts;
 
 enum { SG_M0_VCYCLE = 0, SG_M0_DIAG = 1 };
@@ -204,8 +213,9 @@ int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream);
  * product C_l (out = l, in = l-1) of Algorithm 1.
  * X: device n x w_in packed; Yin, Yout: device n x w_out packed (may alias);
  * w_d = number of chaos polynomials of degree d. dtype SG_F64 or SG_F32 for
- * all three blocks, or SG_F32_ACC64: X and Yout FP32, Yin FP64 (required, not
- * aliasing Yout), the sum accumulated in FP64. */
+ * all three blocks, or SG_F32_ACC64 / SG_F32_ACCDF64: X and Yout FP32, Yin
+ * FP64 (required, not aliasing Yout), the sum accumulated in FP64 or in
+ * double-float arithmetic. */
 int sg_level_apply(sg_problem* h, int lvl_out, int lvl_in, const void* X, const void* Yin,
                    void* Yout, int dtype, void* stream);
 
@@ -304,7 +314,8 @@ int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opt
 
 /* sg_autotune -- time the candidate block sizes (64 to 1024 threads) of the
  * full SG product in FP64 and FP32, and separately of the outer solver's fused
- * product (SG product + CG update + p.q), each in two forms, on this problem
+ * product (SG product + CG update + p.q, in FP64 and in its double-float
+ * variant, sg_prec_opts.df64), each in two forms, on this problem
  * and keep the fastest for all later calls. The forms: the pair form sums
  * each distinct (k, j) of the couplings once per row and keeps those sums in
  * shared memory (fewer multiply-adds); the gather form sums per coupling (no
@@ -322,7 +333,8 @@ int sg_autotune_outer_result(const sg_problem* h, int* threads_outer);
  * block sizes of the full SG product in FP64 and FP32 and of the outer fused
  * product (0: the built-in choice; otherwise whole warps, 32..1024 threads,
  * at most 8 outputs per thread, 4 above 256 threads), and the pair (1) or
- * gather (0) form of each. SG_ERR_INVALID_ARG for an unusable block size.
+ * gather (0) form of each (the outer shape applies to its FP64 and its
+ * double-float variant). SG_ERR_INVALID_ARG for an unusable block size.
  * Invalidates the handle's cached solve graphs. */
 int sg_autotune_set(sg_problem* h, int threads_f64, int threads_f32, int threads_outer, int pairs_f64,
                     int pairs_f32, int pairs_outer);

@@ -175,15 +175,16 @@ def sg_apply(h: SGProblem, U: torch.Tensor, Y: Optional[torch.Tensor] = None) ->
 
 
 def sg_level_apply(h: SGProblem, lvl_out: int, lvl_in: int, X: torch.Tensor, Yin: Optional[torch.Tensor],
-                   Yout: Optional[torch.Tensor] = None) -> torch.Tensor:
+                   Yout: Optional[torch.Tensor] = None, df64: bool = False) -> torch.Tensor:
     """Yout = Yin - sum_k A_k X G_k[out, in]^T between adjacent degree levels (K2).
-    An FP32 ``X`` with an FP64 ``Yin`` takes the FP64-accumulating product of
-    the mixed preconditioner's top level (``SG_F32_ACC64``, FP32 ``Yout``)."""
+    An FP32 ``X`` with an FP64 ``Yin`` takes the FP64-accurate product of
+    the mixed preconditioner's top level (``SG_F32_ACC64``, FP32 ``Yout``;
+    ``df64``: double-float accumulation, ``SG_F32_ACCDF64``)."""
     mixed = X.dtype == torch.float32 and Yin is not None and Yin.dtype == torch.float64
     if Yout is None:
         _, off = h.chaos_table()
         Yout = torch.empty((h.n, int(off[lvl_out + 1] - off[lvl_out])), dtype=X.dtype, device="cuda")
-    code = SG_F32_ACC64 if mixed else _DT[X.dtype]
+    code = (_lib.SG_F32_ACCDF64 if df64 else SG_F32_ACC64) if mixed else _DT[X.dtype]
     check(_lib.LIB.sg_level_apply(h.h, lvl_out, lvl_in, _ptr(X), _ptr(Yin), _ptr(Yout), code, _stream()),
           "sg_level_apply")
     return Yout

@@ -13,7 +13,7 @@ SG_OK, SG_ERR_INVALID_ARG, SG_ERR_CUDA, SG_ERR_OOM, SG_ERR_NOT_SPD, SG_ERR_BREAK
     SG_ERR_NO_CONVERGENCE, SG_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = {0: "SG_OK", 1: "SG_ERR_INVALID_ARG", 2: "SG_ERR_CUDA", 3: "SG_ERR_OOM", 4: "SG_ERR_NOT_SPD",
                 5: "SG_ERR_BREAKDOWN", 6: "SG_ERR_NO_CONVERGENCE", 7: "SG_ERR_UNSUPPORTED"}
-SG_F64, SG_F32, SG_F32_ACC64 = 0, 1, 2
+SG_F64, SG_F32, SG_F32_ACC64, SG_F32_ACCDF64 = 0, 1, 2, 3
 SG_LEGENDRE, SG_HERMITE = 0, 1
 SG_PREC_NONE, SG_PREC_MEAN, SG_PREC_HSC, SG_PREC_BGS = 0, 1, 2, 3
 SG_M0_VCYCLE, SG_M0_DIAG = 0, 1
@@ -27,7 +27,7 @@ class sg_mesh(C.Structure):
 class sg_prec_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("top_level_f64", C.c_int), ("inner_tol", C.c_double),
                 ("inner_maxit", C.c_int), ("inner_fixed_iters", C.c_int), ("nu", C.c_int), ("omega", C.c_double),
-                ("m0", C.c_int), ("level_tol", C.c_double), ("level_maxit", C.c_int)]
+                ("m0", C.c_int), ("level_tol", C.c_double), ("level_maxit", C.c_int), ("df64", C.c_int)]
 
 
 class sg_solve_opts(C.Structure):

@@ -182,13 +182,16 @@ static int autotune_k1(sg_problem* h, int dtype, cudaStream_t s) {
 
 // Time the fused outer product (K1 with the CG update and p . q) with each
 // candidate block size, in pair and in gather form, on the handle's own outer
-// buffers and keep the fastest. It runs on whatever the buffers hold; every solve stages its
-// right-hand side and resets the outer state before it starts.
-static int autotune_outer(sg_problem* h, cudaStream_t s) {
+// buffers and keep the fastest, for the FP64 product and separately for its
+// double-float variant (df). It runs on whatever the buffers hold; every solve
+// stages its right-hand side and resets the outer state before it starts.
+static int autotune_outer(sg_problem* h, cudaStream_t s, bool df) {
   SG_TRY(ensure_outer(h));
   sg_solve_opts o;
   sg_default_solve_opts(&o);
   const OuterArgs a = outer_args(h, o);
+  int& t_out = df ? h->outer_threads_df : h->outer_threads;
+  int& p_out = df ? h->outer_pairs_df : h->outer_pairs;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -202,12 +205,12 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
     const int maxo = (h->P + c - 1) / c;
     if (maxo > 8 || (c > 256 && maxo > 4)) continue;
     if (pairs && h->q >= 0) continue;
-    h->outer_threads = c;
-    h->outer_pairs = pairs;
-    r = launch_outer_matvec(h, a, s);
+    t_out = c;
+    p_out = pairs;
+    r = launch_outer_matvec(h, a, s, df);
     if (r != SG_OK) break;
     cudaEventRecord(e0, s);
-    for (int rep = 0; rep < 5 && r == SG_OK; ++rep) r = launch_outer_matvec(h, a, s);
+    for (int rep = 0; rep < 5 && r == SG_OK; ++rep) r = launch_outer_matvec(h, a, s, df);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -218,8 +221,8 @@ static int autotune_outer(sg_problem* h, cudaStream_t s) {
       best_pairs = pairs;
     }
   }
-  h->outer_threads = best;
-  h->outer_pairs = h->q >= 0 ? 0 : best_pairs;
+  t_out = best;
+  p_out = h->q >= 0 ? 0 : best_pairs;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return r;
@@ -236,7 +239,7 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int t64, t32, tout, p64, p32, pout;
+  int t64, t32, tout, p64, p32, pout, tdf, pdf;
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune_cache;
@@ -278,15 +281,19 @@ int sg_autotune(sg_problem* h, void* stream) {
       h->k1_pairs[SG_F64] = v.p64;
       h->k1_pairs[SG_F32] = v.p32;
       h->outer_pairs = v.pout;
+      h->outer_threads_df = v.tdf;
+      h->outer_pairs_df = v.pdf;
       return SG_OK;
     }
   }
   SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
   SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
-  SG_TRY(autotune_outer(h, (cudaStream_t)stream));
+  SG_TRY(autotune_outer(h, (cudaStream_t)stream, false));
+  SG_TRY(autotune_outer(h, (cudaStream_t)stream, true));
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = TuneVal{h->k1_threads[SG_F64], h->k1_threads[SG_F32], h->outer_threads,
-                              h->k1_pairs[SG_F64],   h->k1_pairs[SG_F32],   h->outer_pairs};
+                              h->k1_pairs[SG_F64],   h->k1_pairs[SG_F32],   h->outer_pairs,
+                              h->outer_threads_df,   h->outer_pairs_df};
   return SG_OK;
 }
 
@@ -309,6 +316,8 @@ int sg_autotune_set(sg_problem* h, int threads_f64, int threads_f32, int threads
   h->k1_pairs[SG_F64] = pairs_f64 && h->q < 0 ? 1 : 0;   // gPC: gather form only
   h->k1_pairs[SG_F32] = pairs_f32 && h->q < 0 ? 1 : 0;
   h->outer_pairs = pairs_outer && h->q < 0 ? 1 : 0;
+  h->outer_threads_df = threads_outer;      // the double-float variant takes the same shape
+  h->outer_pairs_df = h->outer_pairs;
   return SG_OK;
 }
 

@@ -156,7 +156,9 @@ int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
     a.flag = lc.flag;
     SG_TRY(precond(h, o.precond, h->fr, h->fz, o.prec, bs));
     { k_outer_dots<<<vg, 256, 0, bs>>>(N, h->fz, h->fr, h->fq, a); ::sghsc::note_launch(); }
-    SG_TRY(launch_outer_matvec(h, a, bs));
+    // with an FP32 preconditioner and df64, the outer product runs in double-float arithmetic
+    const bool df = o.precond != SG_PREC_NONE && o.prec.precision == SG_F32 && o.prec.df64;
+    SG_TRY(launch_outer_matvec(h, a, bs, df));
     { k_outer_update<<<vg, 256, 0, bs>>>(N, h->fpA, h->fpB, h->fq, h->fx, h->fr, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
@@ -249,9 +251,9 @@ static int enqueue_schur_solve(sg_problem* h, const sg_solve_opts& o, cudaStream
 
 std::string opts_key(const sg_prec_opts& o) {
   char buf[256];
-  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d|lt%.17g|lm%d", o.precision,
+  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d|lt%.17g|lm%d|df%d", o.precision,
            o.top_level_f64, o.inner_tol, o.inner_maxit, o.inner_fixed_iters, o.nu, o.omega, o.m0, o.level_tol,
-           o.level_maxit);
+           o.level_maxit, o.df64);
   return buf;
 }
 

@@ -162,6 +162,7 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
     float* R32 = h->R32;
     float* Z32 = h->Z32;
     const bool top64 = o.top_level_f64 != 0;
+    const int acc64 = o.df64 ? ACC_DF64 : SG_F64;   // FP64-accurate accumulation: FP64 or double-float
     // With the FP64 top level only levels 0..p-2 of R are needed in FP32 (the
     // pre-correction at level l reads level l-1 in place): the degree-p solve
     // gathers its columns from R (converting on the way), and the top-level
@@ -177,7 +178,7 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
       else
         SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
       if (l == p && top64)
-        SG_TRY(launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, Z32 + lo, P, w, h->pre[l], false, R + lo1, P,
+        SG_TRY(launch_block_matvec(h, SG_F32, acc64, SG_F64, SG_F32, Z32 + lo, P, w, h->pre[l], false, R + lo1, P,
                                    -1.0, 1.0, R32 + lo1, P, s));
       else
         SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo, P, w, h->pre[l], false, R32 + lo1, P,
@@ -189,7 +190,7 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
     for (int l = 1; l <= p; ++l) {
       const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1], w1 = off[l] - off[l - 1];
       if (l == p && top64)
-        SG_TRY(launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, Z32 + lo1, P, w1, h->post[l], false, R + lo, P,
+        SG_TRY(launch_block_matvec(h, SG_F32, acc64, SG_F64, SG_F32, Z32 + lo1, P, w1, h->post[l], false, R + lo, P,
                                    -1.0, 1.0, h->T32, w, s));
       else
         SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo1, P, w1, h->post[l], false, R32 + lo,
@@ -247,8 +248,8 @@ int bgs_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
     for (int d = 1; d <= p; ++d) {
       const int lo = off[d], w = off[d + 1] - off[d], lo1 = off[d - 1], w1 = off[d] - off[d - 1];
       if (d == p && top64)
-        SG_TRY(launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, Z32 + lo1, P, w1, h->post[d], false, R + lo, P,
-                                   -1.0, 1.0, R32 + lo, P, s));
+        SG_TRY(launch_block_matvec(h, SG_F32, o.df64 ? ACC_DF64 : SG_F64, SG_F64, SG_F32, Z32 + lo1, P, w1,
+                                   h->post[d], false, R + lo, P, -1.0, 1.0, R32 + lo, P, s));
       else
         SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo1, P, w1, h->post[d], false, R32 + lo,
                                    P, -1.0, 1.0, R32 + lo, P, s));

@@ -1729,9 +1729,9 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
 int check_prec_opts(const sg_prec_opts& o) {
   if (o.nu < 1 || o.nu > 16 || !(o.omega > 0.0) || o.inner_maxit < 1 || o.inner_fixed_iters < 0 ||
       !(o.inner_tol >= 0.0) || (o.m0 != SG_M0_VCYCLE && o.m0 != SG_M0_DIAG) || !(o.level_tol >= 0.0) ||
-      o.level_maxit < 1 || o.level_maxit > 100000) {
+      o.level_maxit < 1 || o.level_maxit > 100000 || (o.df64 != 0 && o.df64 != 1)) {
     set_error("prec opts: need 1 <= nu <= 16, omega > 0, inner_maxit >= 1, inner_tol >= 0, m0 0 or 1, "
-              "level_tol >= 0, 1 <= level_maxit <= 100000");
+              "level_tol >= 0, 1 <= level_maxit <= 100000, df64 0 or 1");
     return SG_ERR_INVALID_ARG;
   }
   return SG_OK;

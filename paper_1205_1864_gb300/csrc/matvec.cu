@@ -15,11 +15,36 @@
 // distinct (k, j) once (pair form below), P + npair per nonzero plus n_m per
 // row.
 #include <algorithm>
+#include <type_traits>
 
+#include "df64.cuh"
 #include "sghsc_internal.cuh"
 #include "vec.cuh"
 
 namespace sghsc {
+
+// An input element in the accumulation type: FP32 -> FP64 by integer
+// widening, FP32/FP64 -> double-float by exact splitting (no FP64 operation).
+template <typename TAcc, typename TIn>
+__device__ __forceinline__ TAcc to_acc(TIn v) {
+  if constexpr (std::is_same_v<TAcc, df64>) {
+    if constexpr (sizeof(TIn) == 4) return df_from_float(v);
+    else return df_from_double(v);
+  } else {
+    return widen<TAcc>(v);
+  }
+}
+
+// An accumulated value as FP64 (double-float: two integer widenings, one add).
+template <typename TAcc>
+__device__ __forceinline__ double acc_to_double(const TAcc& v) {
+  if constexpr (std::is_same_v<TAcc, df64>) {
+    const df64 x = df_norm(v);
+    return f2d_bits(x.hi) + f2d_bits(x.lo);
+  } else {
+    return (double)v;
+  }
+}
 
 // This thread's output columns: slot threadIdx + i * blockDim takes column
 // eperm[slot] (outputs ordered by coupling count, so the lanes of a warp run
@@ -43,7 +68,7 @@ __device__ __forceinline__ void stage_chunk(int cs, int nzc, int M1, const int* 
                                             const TAcc* __restrict__ vals, const TIn* __restrict__ X, int ldx,
                                             int wx, TAcc* Xs, TAcc* Vs) {
   const int cnt = nzc * wx;
-  if constexpr (sizeof(TIn) == sizeof(TAcc)) {
+  if constexpr (std::is_same_v<TIn, TAcc>) {
     for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
       const int e = idx / wx, j = idx - e * wx;
       cp_async_elem(Xs + idx, X + (size_t)colidx[cs + e] * ldx + j);
@@ -62,7 +87,7 @@ __device__ __forceinline__ void stage_chunk(int cs, int nzc, int M1, const int* 
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int idx = base + u * blockDim.x;
-        if (idx < cnt) Xs[idx] = widen<TAcc>(v[u]);
+        if (idx < cnt) Xs[idx] = to_acc<TAcc>(v[u]);
       }
     }
   }
@@ -156,6 +181,15 @@ __device__ __forceinline__ void pair_couple(const int* __restrict__ eptr, const 
   }
 }
 
+// alpha, beta of the product's epilogue: a test against a small integer and the
+// value in FP64 (double-float scalars carry their value in hi).
+template <typename T>
+__device__ __forceinline__ bool is_value(const T& x, float v) {
+  if constexpr (std::is_same_v<T, df64>) return x.hi == v && x.lo == 0.f;
+  else return x == (T)v;
+}
+__device__ __forceinline__ double df_to_scale(const df64& x) { return f2d_bits(x.hi) + f2d_bits(x.lo); }
+
 // LB: the largest block the instantiation is launched with. Blocks of up to
 // 256 threads with fewer than 4 outputs per thread keep the compiler's
 // register choice; with 4 or more (large P) they may use up to 64 registers
@@ -205,22 +239,32 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
     }
     // Y = beta Yin + alpha sum; the two forms the solver uses (Yin - sum, and
     // the plain sum) without the multiplications (the FP64 pipe is the bound)
-    const bool sub = Yin && alpha == TAcc(-1) && beta == TAcc(1);
-    const bool plain = !Yin && alpha == TAcc(1);
+    const bool sub = Yin && is_value(alpha, -1.f) && is_value(beta, 1.f);
+    const bool plain = !Yin && is_value(alpha, 1.f);
 #pragma unroll
     for (int i = 0; i < MAXO; ++i) {
       const int l = lcol[i];
       if (l >= 0) {
-        TAcc v;
-        if (sub) {
-          v = (TAcc)Yin[(size_t)r * ldyin + l] - acc[i];
-        } else if (plain) {
-          v = acc[i];
+        if constexpr (std::is_same_v<TAcc, df64>) {
+          // double-float sums finish in FP64 (one add per output)
+          const double a = acc_to_double(acc[i]);
+          double v;
+          if (sub) v = (double)Yin[(size_t)r * ldyin + l] - a;
+          else if (plain) v = a;
+          else v = df_to_scale(alpha) * a + (Yin ? df_to_scale(beta) * (double)Yin[(size_t)r * ldyin + l] : 0.0);
+          Y[(size_t)r * ldy + l] = (TO)v;
         } else {
-          v = alpha * acc[i];
-          if (Yin) v += beta * (TAcc)Yin[(size_t)r * ldyin + l];
+          TAcc v;
+          if (sub) {
+            v = (TAcc)Yin[(size_t)r * ldyin + l] - acc[i];
+          } else if (plain) {
+            v = acc[i];
+          } else {
+            v = alpha * acc[i];
+            if (Yin) v += beta * (TAcc)Yin[(size_t)r * ldyin + l];
+          }
+          Y[(size_t)r * ldy + l] = (TO)v;
         }
-        Y[(size_t)r * ldy + l] = (TO)v;
       }
     }
   }
@@ -231,17 +275,20 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_block_matvec(
 // the FP64 update is done once per output rather than once per staged
 // neighbour), p_new and q written for the block's own rows, p_new . q reduced
 // and alpha = rho / (p_new . q) set by the last block.
-template <int MAXO, int LB>
+// TAcc double: FP64 arithmetic; df64: double-float products and sums on the
+// FP32 units (z split exactly on staging, the values and couplings from their
+// double-float copies), each output's sum finished in FP64.
+template <int MAXO, int LB, typename TAcc>
 __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
-    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const double* __restrict__ vals,
+    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const TAcc* __restrict__ vals,
     int M1, int P, const double* __restrict__ z, double* pA, double* pB, const int* __restrict__ eptr,
     const int* __restrict__ eperm, const int* __restrict__ ek, const int* __restrict__ ej,
-    const double* __restrict__ ec, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
+    const TAcc* __restrict__ ec, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
     const int* __restrict__ epair, int pairs, double* __restrict__ q, int chunk, OuterArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* Xs = reinterpret_cast<double*>(smem_raw);
-  double* Vs = Xs + (size_t)chunk * P;
-  double* Ss = Vs + (size_t)chunk * M1;
+  TAcc* Xs = reinterpret_cast<TAcc*>(smem_raw);
+  TAcc* Vs = Xs + (size_t)chunk * P;
+  TAcc* Ss = Vs + (size_t)chunk * M1;
   int lcol[MAXO];
   output_columns<MAXO>(eperm, P, lcol);
   const int it = a.ctl->it;
@@ -251,38 +298,39 @@ __global__ void SG_MATVEC_BOUNDS(LB, MAXO) k_outer_matvec(
   double* __restrict__ pnew = (it & 1) ? pA : pB;
   double dot = 0.0;
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
-    double acc[MAXO];
+    TAcc acc[MAXO];
 #pragma unroll
-    for (int i = 0; i < MAXO; ++i) acc[i] = 0.0;
+    for (int i = 0; i < MAXO; ++i) acc[i] = TAcc(0);
     const int rb = rowptr[r], re = rowptr[r + 1];
     for (int cs = rb; cs < re; cs += chunk) {
       const int nzc = min(chunk, re - cs);
       __syncthreads();
-      stage_chunk<double, double>(cs, nzc, M1, colidx, vals, z, P, P, Xs, Vs);
+      stage_chunk<double, TAcc>(cs, nzc, M1, colidx, vals, z, P, P, Xs, Vs);
       cp_async_wait_all();
       __syncthreads();
       if (pairs) {
         if (cs == rb)
-          pair_chunk<double, MAXO, true>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, lcol, acc);
+          pair_chunk<TAcc, MAXO, true>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, lcol, acc);
         else
-          pair_chunk<double, MAXO, false>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, lcol, acc);
+          pair_chunk<TAcc, MAXO, false>(nzc, M1, Vs, Xs, P, npair, pk, pj, Ss, lcol, acc);
       } else if (cs == rb) {
-        gather_chunk<double, MAXO, true, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
+        gather_chunk<TAcc, MAXO, true, true>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
       } else {
-        gather_chunk<double, MAXO, true, false>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
+        gather_chunk<TAcc, MAXO, true, false>(nzc, M1, Vs, Xs, P, eptr, ek, ej, ec, lcol, acc);
       }
     }
     if (pairs && re > rb) {
       __syncthreads();
-      pair_couple<double, MAXO>(eptr, epair, ec, Ss, lcol, acc);
+      pair_couple<TAcc, MAXO>(eptr, epair, ec, Ss, lcol, acc);
     }
 #pragma unroll
     for (int i = 0; i < MAXO; ++i) {
       const int l = lcol[i];
       if (l >= 0) {
         const size_t g = (size_t)r * P + l;
+        const double av = acc_to_double(acc[i]);
         const double pv = first ? z[g] : z[g] + beta * pold[g];
-        const double qv = first ? acc[i] : acc[i] + beta * q[g];
+        const double qv = first ? av : av + beta * q[g];
         pnew[g] = pv;
         q[g] = qv;
         dot += pv * qv;
@@ -327,7 +375,12 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
   const int M1 = h->nterm;
   const TAcc* vals = nullptr;
   const TAcc* ec = nullptr;
-  if constexpr (sizeof(TAcc) == 8) {
+  constexpr bool DF = std::is_same_v<TAcc, df64>;
+  constexpr int tk = (sizeof(TAcc) == 8 && !DF) ? SG_F64 : SG_F32;   // tuned shapes: FP64, or FP32 units
+  if constexpr (DF) {
+    vals = (const TAcc*)h->vals_df;
+    ec = (const TAcc*)E.cdf;
+  } else if constexpr (sizeof(TAcc) == 8) {
     vals = (const TAcc*)h->vals64;
     ec = (const TAcc*)E.c64;
   } else {
@@ -335,11 +388,11 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
     ec = (const TAcc*)E.c32;
   }
   int threads = pick_threads(wy);
-  const int tuned = h->k1_threads[sizeof(TAcc) == 8 ? SG_F64 : SG_F32];
+  const int tuned = h->k1_threads[tk];
   if (DIAG && tuned > 0) threads = tuned;   // the full SG product: autotuned block size
   const int maxo = (wy + threads - 1) / threads;
   size_t smem = 0;
-  const int pairs = DIAG && h->k1_pairs[sizeof(TAcc) == 8 ? SG_F64 : SG_F32] ? 1 : 0;
+  const int pairs = DIAG && h->k1_pairs[tk] ? 1 : 0;
   const int chunk = pick_chunk(h, wx, sizeof(TAcc), M1, pairs ? (size_t)E.npair * sizeof(TAcc) : 0, &smem);
   if (chunk < 1) {
     set_error("block matvec: row of %d values does not fit in shared memory", wx);
@@ -389,43 +442,57 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
     return launch_t<float, double, double, float, false>(h, (const float*)X, ldx, wx, E, (const double*)Yin, ldyin,
                                                          alpha, beta, (float*)Y, ldy, s);
   }
+  if (tin == SG_F32 && tacc == ACC_DF64 && tb == SG_F64 && tout == SG_F32 && !diag) {
+    return launch_t<float, df64, double, float, false>(h, (const float*)X, ldx, wx, E, (const double*)Yin, ldyin,
+                                                       alpha, beta, (float*)Y, ldy, s);
+  }
   set_error("block matvec: unsupported type combination");
   return SG_ERR_UNSUPPORTED;
 }
 
-int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
+template <typename TAcc>
+static int launch_outer_t(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
+  constexpr bool DF = std::is_same_v<TAcc, df64>;
   const int P = h->P, M1 = h->nterm;
-  // whole warps, <= 1024: the autotuned block size or 256
-  const int threads = h->outer_threads > 0 ? h->outer_threads : 256;
+  // whole warps, <= 1024: the autotuned block size or 256 (the double-float
+  // form has its own tuned shape)
+  const int tuned = DF ? h->outer_threads_df : h->outer_threads;
+  const int threads = tuned > 0 ? tuned : 256;
   const int maxo = (P + threads - 1) / threads;
   size_t smem = 0;
-  const int pairs = h->outer_pairs ? 1 : 0;
-  const int chunk = pick_chunk(h, P, sizeof(double), M1, pairs ? (size_t)h->all.npair * sizeof(double) : 0, &smem);
+  const int pairs = (DF ? h->outer_pairs_df : h->outer_pairs) ? 1 : 0;
+  const int chunk = pick_chunk(h, P, sizeof(TAcc), M1, pairs ? (size_t)h->all.npair * sizeof(TAcc) : 0, &smem);
   if (chunk < 1) {
     set_error("outer matvec: P = %d does not fit in shared memory", P);
     return SG_ERR_UNSUPPORTED;
   }
+  const TAcc* vals = DF ? (const TAcc*)h->vals_df : (const TAcc*)h->vals64;
+  const TAcc* ec = DF ? (const TAcc*)h->all.cdf : (const TAcc*)h->all.c64;
   auto go = [&](auto kern) -> int {
     SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int grid = std::min(std::min(h->n, h->num_sms * std::max(per_sm, 1)), h->opart_blocks);
-    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, h->vals64, M1, P, h->fz, h->fpA, h->fpB, h->all.ptr, h->all.perm, h->all.k, h->all.j, h->all.c64, h->all.npair, h->all.pk, h->all.pj, h->all.pair, pairs, h->fq, chunk, a); ::sghsc::note_launch(); }
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, vals, M1, P, h->fz, h->fpA, h->fpB, h->all.ptr, h->all.perm, h->all.k, h->all.j, ec, h->all.npair, h->all.pk, h->all.pj, h->all.pair, pairs, h->fq, chunk, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
   if (threads > 256) {
-    if (maxo <= 1) return go(k_outer_matvec<1, 1024>);
-    if (maxo <= 2) return go(k_outer_matvec<2, 1024>);
-    if (maxo <= 4) return go(k_outer_matvec<4, 1024>);
+    if (maxo <= 1) return go(k_outer_matvec<1, 1024, TAcc>);
+    if (maxo <= 2) return go(k_outer_matvec<2, 1024, TAcc>);
+    if (maxo <= 4) return go(k_outer_matvec<4, 1024, TAcc>);
   } else {
-    if (maxo <= 1) return go(k_outer_matvec<1, 256>);
-    if (maxo <= 2) return go(k_outer_matvec<2, 256>);
-    if (maxo <= 4) return go(k_outer_matvec<4, 256>);
-    if (maxo <= 8) return go(k_outer_matvec<8, 256>);
+    if (maxo <= 1) return go(k_outer_matvec<1, 256, TAcc>);
+    if (maxo <= 2) return go(k_outer_matvec<2, 256, TAcc>);
+    if (maxo <= 4) return go(k_outer_matvec<4, 256, TAcc>);
+    if (maxo <= 8) return go(k_outer_matvec<8, 256, TAcc>);
   }
   set_error("outer matvec: P = %d exceeds the supported 2048", P);
   return SG_ERR_UNSUPPORTED;
+}
+
+int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df) {
+  return df ? launch_outer_t<df64>(h, a, s) : launch_outer_t<double>(h, a, s);
 }
 
 }  // namespace sghsc
@@ -447,18 +514,19 @@ int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream) {
 int sg_level_apply(sg_problem* h, int lvl_out, int lvl_in, const void* X, const void* Yin, void* Yout, int dtype,
                    void* stream) {
   set_error("");
-  if (!h || !X || !Yout || (dtype != SG_F64 && dtype != SG_F32 && dtype != SG_F32_ACC64) || lvl_out < 0 ||
-      lvl_in < 0 || lvl_out > h->p || lvl_in > h->p || (lvl_out - lvl_in != 1 && lvl_in - lvl_out != 1) ||
-      (dtype == SG_F32_ACC64 && (!Yin || Yin == (const void*)Yout))) {
+  const bool mixed = dtype == SG_F32_ACC64 || dtype == SG_F32_ACCDF64;
+  if (!h || !X || !Yout || (dtype != SG_F64 && dtype != SG_F32 && !mixed) || lvl_out < 0 || lvl_in < 0 ||
+      lvl_out > h->p || lvl_in > h->p || (lvl_out - lvl_in != 1 && lvl_in - lvl_out != 1) ||
+      (mixed && (!Yin || Yin == (const void*)Yout))) {
     set_error("sg_level_apply: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
   const EdgeList& E = lvl_in > lvl_out ? h->pre[lvl_in] : h->post[lvl_out];
   const int win = h->off[lvl_in + 1] - h->off[lvl_in];
   const int wout = h->off[lvl_out + 1] - h->off[lvl_out];
-  if (dtype == SG_F32_ACC64)   // the level-p products of the mixed preconditioner with an FP64 top level
-    return launch_block_matvec(h, SG_F32, SG_F64, SG_F64, SG_F32, X, win, win, E, false, Yin, wout, -1.0, 1.0, Yout,
-                               wout, (cudaStream_t)stream);
+  if (mixed)   // the level-p products of the mixed preconditioner with an FP64-accurate top level
+    return launch_block_matvec(h, SG_F32, dtype == SG_F32_ACC64 ? SG_F64 : ACC_DF64, SG_F64, SG_F32, X, win, win, E,
+                               false, Yin, wout, -1.0, 1.0, Yout, wout, (cudaStream_t)stream);
   return launch_block_matvec(h, dtype, dtype, dtype, dtype, X, win, win, E, false, Yin, wout, -1.0, 1.0, Yout, wout,
                              (cudaStream_t)stream);
 }

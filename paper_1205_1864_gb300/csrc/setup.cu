@@ -10,6 +10,7 @@
 #include <atomic>
 #include <map>
 
+#include "df64.cuh"
 #include "graph.cuh"
 #include "sghsc_internal.cuh"
 
@@ -84,6 +85,13 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
   SG_TRY(upload(&E.j, he.j.data(), he.j.size()));
   SG_TRY(upload(&E.c64, he.c.data(), he.c.size()));
   SG_TRY(upload(&E.c32, c32.data(), c32.size()));
+  {
+    std::vector<df64> cdf(he.c.size());
+    for (size_t t = 0; t < he.c.size(); ++t) cdf[t] = df_split_host(he.c[t]);
+    df64* d = nullptr;
+    SG_TRY(upload(&d, cdf.data(), cdf.size()));
+    E.cdf = d;
+  }
   std::map<std::pair<int, int>, int> pairs;
   for (int t = 0; t < E.nedges; ++t) pairs.emplace(std::make_pair(he.k[t], he.j[t]), 0);
   std::vector<int> pk, pj, pair(E.nedges);
@@ -107,6 +115,7 @@ static void free_edges(EdgeList& E) {
   cudaFree(E.j);
   cudaFree(E.c64);
   cudaFree(E.c32);
+  cudaFree(E.cdf);
   cudaFree(E.pk);
   cudaFree(E.pj);
   cudaFree(E.pair);
@@ -358,6 +367,11 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   {
     std::vector<float> v32(vals, vals + nv);
     SG_TRY(upload(&h->vals32, v32.data(), nv));
+    std::vector<df64> vdf(nv);
+    for (size_t i = 0; i < nv; ++i) vdf[i] = df_split_host(vals[i]);
+    df64* d = nullptr;
+    SG_TRY(upload(&d, vdf.data(), nv));
+    h->vals_df = d;
   }
   if (mass_vals) SG_TRY(upload(&h->mass64, mass_vals, (size_t)nnz));
 
@@ -422,7 +436,7 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   }
   {
     const char* ev = getenv("SGHSC_GATHER_FORM");   // start from the gather form of the full product
-    if (ev && ev[0] == '1') h->k1_pairs[0] = h->k1_pairs[1] = h->outer_pairs = 0;
+    if (ev && ev[0] == '1') h->k1_pairs[0] = h->k1_pairs[1] = h->outer_pairs = h->outer_pairs_df = 0;
   }
   SG_TRY_CUDA(cudaMalloc((void**)&h->loopflags, 8 * sizeof(int)));
   SG_TRY_CUDA(cudaMemset(h->loopflags, 0, 8 * sizeof(int)));
@@ -437,11 +451,13 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
 
 // vals = base * scale[k] for every nonzero (FP64 and FP32 copies)
 __global__ void k_scale_vals(long long count, int M1, const double* __restrict__ base, const double* __restrict__ scale,
-                             double* __restrict__ v64, float* __restrict__ v32) {
+                             double* __restrict__ v64, float* __restrict__ v32, df64* __restrict__ vdf) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
     const double v = base[i] * scale[i % M1];
     v64[i] = v;
     v32[i] = (float)v;
+    const float h = __double2float_rn(v);
+    vdf[i] = df64(h, __double2float_rn(v - (double)h));
   }
 }
 
@@ -484,7 +500,7 @@ int sg_set_scales(sg_problem* h, const double* scale) {
   h->scales.assign(scale, scale + h->nterm);
   SG_TRY_CUDA(cudaMemcpy(h->scales_dev, scale, h->nterm * sizeof(double), cudaMemcpyHostToDevice));
   const long long count = (long long)h->nnz * h->nterm;
-  { k_scale_vals<<<(int)std::min<long long>((count + 255) / 256, 4096), 256>>>(count, h->nterm, h->vals_base, h->scales_dev, h->vals64, h->vals32); ::sghsc::note_launch(); }
+  { k_scale_vals<<<(int)std::min<long long>((count + 255) / 256, 4096), 256>>>(count, h->nterm, h->vals_base, h->scales_dev, h->vals64, h->vals32, (df64*)h->vals_df); ::sghsc::note_launch(); }
   for (auto& g : h->grids)
     { k_scale_grid<<<std::min((g.n * 9 + 255) / 256, 4096), 256>>>(g.n, g.st_base, scale[0], g.st64, g.st32, g.dinv64, g.dinv32); ::sghsc::note_launch(); }
   SG_TRY_CUDA(cudaGetLastError());
@@ -509,6 +525,7 @@ void sg_default_prec_opts(sg_prec_opts* o) {
   o->m0 = SG_M0_VCYCLE;
   o->level_tol = 1e-8;
   o->level_maxit = 500;
+  o->df64 = 0;
 }
 
 void sg_default_solve_opts(sg_solve_opts* o) {
@@ -586,7 +603,7 @@ void sg_destroy(sg_problem* h) {
   cluster_free(h);
   void* bufs[] = {h->rowptr, h->colidx, h->vals64, h->vals32, h->mass64, h->R32, h->Z32, h->T32, h->R64w,
                   h->T64, h->fF, h->fx, h->fr, h->fz, h->fpA, h->fpB, h->fq, h->opart, h->osc, h->octl,
-                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev, h->fG,
+                  h->hist_alpha, h->hist_beta, h->hist_res, h->io_in, h->io_out, h->status, h->iacc, h->wdev, h->loopflags, h->vals_base, h->scales_dev, h->fG, h->vals_df,
                   h->lx, h->lr, h->lz, h->lp, h->lq, h->lb, h->lctl, h->lsc, h->lhist_alpha, h->lhist_beta,
                   h->lhist_res};
   for (void* b : bufs) cudaFree(b);

@@ -56,6 +56,7 @@ struct EdgeList {
   int* j = nullptr;
   double* c64 = nullptr;
   float* c32 = nullptr;
+  void* cdf = nullptr;   // the coefficients as double-float pairs (df64)
   // The distinct (k, j) of the couplings, ordered by k then j (a sum
   // sum_c a_k(r,c) U(c,j) serves every coupling with that pair), and the
   // pair of each coupling.
@@ -131,6 +132,7 @@ struct sg_problem {
   double* vals64 = nullptr;
   float* vals32 = nullptr;
   double* vals_base = nullptr;        // [nnz][M+1] as given to sg_setup (scales 1)
+  void* vals_df = nullptr;            // [nnz][M+1] double-float pairs (df64) of vals64
   double* scales_dev = nullptr;       // current scale of each A_k
   std::vector<double> scales;         // host copy
   double* mass64 = nullptr;
@@ -195,10 +197,16 @@ struct sg_problem {
   int outer_threads = 0;                    // block size of the fused outer product (0: 256)
   int k1_pairs[2] = {1, 1};                 // full SG product in pair form (1) or gather form (0)
   int outer_pairs = 1;                      // the same for the fused outer product
+  int outer_threads_df = 0;                 // block size and form of its double-float variant
+  int outer_pairs_df = 1;
   long long ws_gen = 0;                     // bumped whenever captured graphs become invalid
 };
 
 namespace sghsc {
+
+// Accumulation type code of launch_block_matvec beside SG_F64 / SG_F32:
+// double-float pairs on the FP32 units (df64.cuh).
+enum { ACC_DF64 = 16 };
 
 // ---- launchers (matvec.cu) ----
 // Generic block product used for the full operator (K1) and the level products (K2):

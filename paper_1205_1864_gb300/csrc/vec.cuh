@@ -141,7 +141,8 @@ int vec_grid(long long N);
 // The outer CG step q = A p_new with p_new = z + beta p_old staged on the fly
 // (ping-pong p buffers chosen by the device iteration counter), the fused
 // p_new . q reduction and the alpha update by the last block (matvec.cu).
-int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s);
+// df: the product in double-float arithmetic on the FP32 units.
+int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df = false);
 // Arguments of the outer-iteration kernels for this handle and options (fcg.cu).
 OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o);
 

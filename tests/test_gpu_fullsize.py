@@ -49,8 +49,8 @@ def _np(t):
     return t.double().cpu().numpy()
 
 
-def _timed_opts(L, check=0):
-    return L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=TIMED["inner_tol"]),
+def _timed_opts(L, check=0, df64=0):
+    return L.solve_opts(L.prec_opts(precision=L.SG_F32, top_level_f64=1, inner_tol=TIMED["inner_tol"], df64=df64),
                         precond=L.SG_PREC_HSC, tol=TIMED["tol"], maxit=500, check_true_residual=check)
 
 
@@ -85,10 +85,13 @@ def cfg2(lib):
     return k
 
 
-def test_cfg2_mixed_solve_matches_oracle(lib, cfg2):
+@pytest.mark.parametrize("df64", [0, 1])
+def test_cfg2_mixed_solve_matches_oracle(lib, cfg2, df64):
     """Mixed precision (FP32 inner solves and level products, FP64 outer CG and
-    top level) solved to 1e-12: within 1e-7 of the oracle's solution."""
-    o = lib.solve_opts(lib.prec_opts(precision=lib.SG_F32, top_level_f64=1, inner_tol=1e-2),
+    top level; df64: the outer product and the level-p products in
+    double-float arithmetic) solved to 1e-12: within 1e-7 of the oracle's
+    solution."""
+    o = lib.solve_opts(lib.prec_opts(precision=lib.SG_F32, top_level_f64=1, inner_tol=1e-2, df64=df64),
                        precond=lib.SG_PREC_HSC, tol=1e-12, maxit=200)
     U, st = lib.sg_solve(cfg2.h, _t(cfg2.F), o)
     U = _np(U)
@@ -107,11 +110,12 @@ def test_cfg2_fp64_solve_matches_oracle(lib, cfg2):
     assert np.abs(U - cfg2.ref).max() <= 1e-10 * scale, np.abs(U - cfg2.ref).max() / scale
 
 
-def test_cfg2_timed_solve_oracle_residual(lib, cfg2):
+@pytest.mark.parametrize("df64", [0, 1])
+def test_cfg2_timed_solve_oracle_residual(lib, cfg2, df64):
     """The benchmark's solve (rel.res 1e-8): the oracle's FP64 residual of the
     GPU solution, and the iteration count the CPU baseline is scaled by."""
     import bench
-    U, st = lib.sg_solve(cfg2.h, _t(cfg2.F), _timed_opts(lib, check=1))
+    U, st = lib.sg_solve(cfg2.h, _t(cfg2.F), _timed_opts(lib, check=1, df64=df64))
     res = oracle_rel_residual(cfg2.A, cfg2.G, cfg2.F, _np(U))
     assert res <= 1.5e-8, res
     assert st.true_rel_res == pytest.approx(res, rel=1e-3)
@@ -172,18 +176,19 @@ def test_cfg5_sg_apply_sampled_rows(lib, cfg5, shape, prec):
         lib.sg_autotune_set(h, *cfg5.tuned)
 
 
+@pytest.mark.parametrize("df64", [0, 1])
 @pytest.mark.parametrize("lvl", ["pre", "post"])
-def test_cfg5_top_level_products_sampled_rows(lib, cfg5, lvl):
-    """The level-p products of the mixed preconditioner (FP32 input, FP64
-    accumulation and residual, FP32 output): B_p (715 -> 220 columns) and C_p
-    (220 -> 715) at M = 10, p = 4, on sampled rows."""
+def test_cfg5_top_level_products_sampled_rows(lib, cfg5, lvl, df64):
+    """The level-p products of the mixed preconditioner (FP32 input, FP64 or
+    double-float accumulation, FP64 residual, FP32 output): B_p (715 -> 220
+    columns) and C_p (220 -> 715) at M = 10, p = 4, on sampled rows."""
     import torch
     p, off = cfg5.cfg["p"], cfg5.off
     lo, li = (p - 1, p) if lvl == "pre" else (p, p - 1)
     win, wout = off[li + 1] - off[li], off[lo + 1] - off[lo]
     X = S.random_block(cfg5.prob.n, win, seed=31).astype(np.float32)
     Yin = S.random_block(cfg5.prob.n, wout, seed=32)
-    Y = lib.sg_level_apply(cfg5.h, lo, li, _t(X, torch.float32), _t(Yin))
+    Y = lib.sg_level_apply(cfg5.h, lo, li, _t(X, torch.float32), _t(Yin), df64=bool(df64))
     assert Y.dtype == torch.float32
     rows = sample_rows(cfg5.prob.n, seed=6)
     Yr = _np(Y[torch.as_tensor(rows, device="cuda")])
@@ -191,31 +196,35 @@ def test_cfg5_top_level_products_sampled_rows(lib, cfg5, lvl):
     exact = Yin[rows] - so.level_apply(cfg5.A, cfg5.G, off, lo, li, X, rows=rows)
     bound = np.abs(Yin[rows]) + so.level_apply([abs(a) for a in cfg5.A], [abs(g) for g in cfg5.G], off, lo, li,
                                                np.abs(X), rows=rows)
-    # FP64 arithmetic, then one rounding of the result to FP32
+    # FP64 (or double-float: m 2^-46 per sum of m <= 99 products here) arithmetic,
+    # then one rounding of the result to FP32
     err = np.abs(Yr - exact)
-    assert np.all(err <= TOL64 * bound + 6e-8 * np.abs(exact) + 1e-300)
+    tol = TOL64 if not df64 else 99 * 2.0 ** -46
+    assert np.all(err <= tol * bound + 6e-8 * np.abs(exact) + 1e-300)
 
 
-@pytest.mark.parametrize("outer", ["tuned", "t512_pair1"])
+@pytest.mark.parametrize("outer", ["tuned", "t512_pair1", "tuned_df64", "t512_pair1_df64"])
 def test_cfg5_timed_solve_oracle_residual(lib, cfg5, outer):
     """The benchmark's mixed solve at 512 x 512, M = 10, p = 4 (261M unknowns)
     stopped at 1e-8: the oracle's FP64 residual of the GPU solution. The
-    second case pins the fused outer product to 512 threads in pair form (two
-    outputs per thread)."""
+    t512 cases pin the fused outer product to 512 threads in pair form (two
+    outputs per thread); the df64 cases run the outer product and the level-p
+    products in double-float arithmetic (the benchmark's headline solve)."""
     import bench
     h = cfg5.h
-    if outer != "tuned":
+    df64 = 1 if outer.endswith("df64") else 0
+    if outer.startswith("t512"):
         t = cfg5.tuned
         lib.sg_autotune_set(h, t[0], t[1], 512, t[3], t[4], 1)
     try:
-        U, st = lib.sg_solve(h, _t(cfg5.F), _timed_opts(lib, check=1))
+        U, st = lib.sg_solve(h, _t(cfg5.F), _timed_opts(lib, check=1, df64=df64))
         res = oracle_rel_residual(cfg5.A, cfg5.G, cfg5.F, _np(U))
         del U
     finally:
         lib.sg_autotune_set(h, *cfg5.tuned)
     assert res <= 1.5e-8, res
     assert st.true_rel_res == pytest.approx(res, rel=1e-3)
-    if outer == "tuned":
+    if outer in ("tuned", "tuned_df64"):
         assert st.iterations == bench.WORKLOADS["cfg5"]["hsc_iterations"]
 
 
