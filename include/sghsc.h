@@ -91,6 +91,13 @@ typedef struct {
                              the level block, preconditioned by the inner PCG on A_0 per
                              column, to this relative residual */
   int level_maxit;        /* cap on the iterations of that nested CG */
+  int md_m0;              /* variants of eq. (general-prec), Sec. 5: bit 0 replaces M_D^1 (the
+                             D_l^{-1} of the pre-correction) and bit 1 replaces M_D^2 = M_D^3
+                             (the D_l^{-1} of the post-correction, applied to r_l - C_l u) by
+                             the mean-value preconditioner M_0 alone (one V-cycle or the
+                             diagonal, per m0) instead of the inner PCG; 0 is Algorithm 1.
+                             Linear KL expansion only (the D_l of a gPC coefficient is not
+                             I (x) A_0). */
   int df64;               /* with precision SG_F32: 1 runs the FP64-accurate products that read
                              the FP32 preconditioner's output -- the level-p products of
                              Algorithm 1 (top_level_f64) and, in sg_solve, the outer SG product

@@ -68,12 +68,18 @@ def _diag_block_solver(A, G, lo: int, hi: int, general: bool, a0solve: A0Solver)
 
 def hsc_apply(A, G, off, R: np.ndarray, general: bool = False,
               a0solve: Optional[A0Solver] = None,
-              dsolve: Optional[Callable[[int, np.ndarray], np.ndarray]] = None) -> np.ndarray:
+              dsolve: Optional[Callable[[int, np.ndarray], np.ndarray]] = None,
+              dsolve_pre: Optional[Callable[[int, np.ndarray], np.ndarray]] = None,
+              dsolve_post: Optional[Callable[[int, np.ndarray], np.ndarray]] = None) -> np.ndarray:
     """Algorithm 1: ``M_P : r_P -> u_P``.
 
     ``off`` are the degree offsets of the chaos columns. ``dsolve(l, X)``
     replaces the exact ``D_l^{-1}`` (and ``A_0^{-1}`` for ``l = 0``) when given,
-    which is how the inexact inner solves are modelled.
+    which is how the inexact inner solves are modelled. ``dsolve_pre`` and
+    ``dsolve_post`` replace it in the pre-correction (``M_D^1`` of eq.
+    (general-prec), Sec. 5) and in the post-correction (``M_D^2 = M_D^3``,
+    applied to ``r_l - C_l u``) only, for the variants of Sec. 5 that use, e.g.,
+    the mean-value preconditioner ``M_0`` there.
     """
     n, P = R.shape
     p = len(off) - 2
@@ -83,11 +89,13 @@ def hsc_apply(A, G, off, R: np.ndarray, general: bool = False,
         solvers = {l: _diag_block_solver(A, G, off[l], off[l + 1], general, a0solve) for l in range(1, p + 1)}
         solvers[0] = a0solve
         dsolve = lambda l, X: solvers[l](X)
+    pre_solve = dsolve_pre or dsolve
+    post_solve = dsolve_post or dsolve
     r = np.array(R, dtype=np.float64, copy=True)
     # first loop, l = P..1: pre-correction
     for l in range(p, 0, -1):
         lo, hi = off[l], off[l + 1]
-        y = dsolve(l, r[:, lo:hi])                                   # D_l^{-1} r_l^l
+        y = pre_solve(l, r[:, lo:hi])                                # D_l^{-1} r_l^l (M_D^1)
         r[:, :lo] -= _offdiag_apply(A, G, slice(0, lo), slice(lo, hi), y)   # g_{l-1}
     # mean-value problem A_0 u_0 = g_0
     u = np.zeros((n, P))
@@ -96,7 +104,7 @@ def hsc_apply(A, G, off, R: np.ndarray, general: bool = False,
     for l in range(1, p + 1):
         lo, hi = off[l], off[l + 1]
         t = r[:, lo:hi] - _offdiag_apply(A, G, slice(lo, hi), slice(0, lo), u[:, :lo])
-        u[:, lo:hi] = dsolve(l, t)
+        u[:, lo:hi] = post_solve(l, t)                               # M_D^2 = M_D^3
     return u
 
 
@@ -234,6 +242,19 @@ def block_inverse(A: np.ndarray, B: np.ndarray, C: np.ndarray, D: np.ndarray,
     post = np.block([[np.eye(na), np.zeros((na, nd))], [-Dinv @ C, np.eye(nd)]])
     mid = np.block([[S_inv, np.zeros((na, nd))], [np.zeros((nd, na)), Dinv]])
     pre = np.block([[np.eye(na), -B @ Dinv], [np.zeros((nd, na)), np.eye(nd)]])
+    return post @ mid @ pre
+
+
+def general_prec(A: np.ndarray, B: np.ndarray, C: np.ndarray, MS: np.ndarray, MD1: np.ndarray,
+                 MD2: np.ndarray, MD3: np.ndarray) -> np.ndarray:
+    """Eq. (general-prec) of Sec. 5 as a dense matrix: the post-correction
+    factor with ``M_D^3``, the middle factor ``diag(M_S, M_D^2)`` and the
+    pre-correction factor with ``M_D^1`` (``A`` only fixes the size of the
+    first block)."""
+    na, nd = A.shape[0], MD2.shape[0]
+    post = np.block([[np.eye(na), np.zeros((na, nd))], [-MD3 @ C, np.eye(nd)]])
+    mid = np.block([[MS, np.zeros((na, nd))], [np.zeros((nd, na)), MD2]])
+    pre = np.block([[np.eye(na), -B @ MD1], [np.zeros((nd, na)), np.eye(nd)]])
     return post @ mid @ pre
 
 

@@ -27,7 +27,8 @@ class sg_mesh(C.Structure):
 class sg_prec_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("top_level_f64", C.c_int), ("inner_tol", C.c_double),
                 ("inner_maxit", C.c_int), ("inner_fixed_iters", C.c_int), ("nu", C.c_int), ("omega", C.c_double),
-                ("m0", C.c_int), ("level_tol", C.c_double), ("level_maxit", C.c_int), ("df64", C.c_int)]
+                ("m0", C.c_int), ("level_tol", C.c_double), ("level_maxit", C.c_int), ("md_m0", C.c_int),
+                ("df64", C.c_int)]
 
 
 class sg_solve_opts(C.Structure):

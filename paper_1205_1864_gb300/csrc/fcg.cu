@@ -251,9 +251,9 @@ static int enqueue_schur_solve(sg_problem* h, const sg_solve_opts& o, cudaStream
 
 std::string opts_key(const sg_prec_opts& o) {
   char buf[256];
-  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d|lt%.17g|lm%d|df%d", o.precision,
+  snprintf(buf, sizeof buf, "p%d|t%d|tol%.17g|mi%d|fx%d|nu%d|om%.17g|m%d|lt%.17g|lm%d|md%d|df%d", o.precision,
            o.top_level_f64, o.inner_tol, o.inner_maxit, o.inner_fixed_iters, o.nu, o.omega, o.m0, o.level_tol,
-           o.level_maxit, o.df64);
+           o.level_maxit, o.md_m0, o.df64);
   return buf;
 }
 

@@ -142,6 +142,10 @@ int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o) {
     set_error("gPC coefficient: Algorithm 1 runs in FP64 (nested D_l solves); block Gauss-Seidel is not built");
     return SG_ERR_UNSUPPORTED;
   }
+  if (h->q >= 0 && kind == SG_PREC_HSC && o.md_m0) {
+    set_error("gPC coefficient: D_l is not I (x) A_0, so M_0 cannot stand in for D_l^{-1} (md_m0)");
+    return SG_ERR_UNSUPPORTED;
+  }
   if (h->q >= 0 && kind == SG_PREC_HSC) SG_TRY(ensure_level(h, o));
   if (kind == SG_PREC_HSC || kind == SG_PREC_BGS) {
     SG_TRY(ensure_inner_work(h, dt, h->wmax));
@@ -167,13 +171,16 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
     // pre-correction at level l reads level l-1 in place): the degree-p solve
     // gathers its columns from R (converting on the way), and the top-level
     // pre-correction writes level p-1 from R itself.
-    const bool cast_all = !(top64 && p >= 1);
+    const bool m0_pre = (o.md_m0 & 1) != 0, m0_post = (o.md_m0 & 2) != 0;   // eq. (general-prec) variants
+    const bool cast_all = !(top64 && p >= 1) || m0_pre;
     const int cast_cols = cast_all ? P : off[std::max(p - 1, 0)];
     if (cast_cols > 0) SG_TRY(launch_cast(R, SG_F64, P, R32, SG_F32, P, n, cast_cols, s));
     // first loop, l = p..1: D_l^{-1} on the degree-l columns, then the pre-correction
     for (int l = p; l >= 1; --l) {
       const int lo = off[l], w = off[l + 1] - off[l], lo1 = off[l - 1];
-      if (l == p && !cast_all)
+      if (m0_pre)
+        SG_TRY(m0_apply(h, SG_F32, R32 + lo, P, Z32 + lo, P, w, o, s));
+      else if (l == p && !cast_all)
         SG_TRY(inner_solve(h, SG_F32, R + lo, P, SG_F64, Z32 + lo, P, SG_F32, w, o, s));
       else
         SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
@@ -195,7 +202,10 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
       else
         SG_TRY(launch_block_matvec(h, SG_F32, SG_F32, SG_F32, SG_F32, Z32 + lo1, P, w1, h->post[l], false, R32 + lo,
                                    P, -1.0, 1.0, h->T32, w, s));
-      SG_TRY(inner_solve(h, SG_F32, h->T32, w, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
+      if (m0_post)
+        SG_TRY(m0_apply(h, SG_F32, h->T32, w, Z32 + lo, P, w, o, s));
+      else
+        SG_TRY(inner_solve(h, SG_F32, h->T32, w, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
     }
     SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));
     return SG_OK;
@@ -207,7 +217,10 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
   for (int l = p; l >= 1; --l) {
     const int lo = off[l], w = off[l + 1] - off[l];
     const EdgeList& B = h->pre[l];
-    SG_TRY(dsolve64(h, l, Rw + lo, P, Z + lo, P, o, s));
+    if (o.md_m0 & 1)
+      SG_TRY(m0_apply(h, SG_F64, Rw + lo, P, Z + lo, P, w, o, s));
+    else
+      SG_TRY(dsolve64(h, l, Rw + lo, P, Z + lo, P, o, s));
     SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + lo, P, w, B, false, Rw + B.out0, P, -1.0,
                                1.0, Rw + B.out0, P, s));
   }
@@ -217,7 +230,10 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
     const EdgeList& C = h->post[l];
     SG_TRY(launch_block_matvec(h, SG_F64, SG_F64, SG_F64, SG_F64, Z + C.in0, P, C.nin, C, false, Rw + lo, P, -1.0,
                                1.0, h->T64, w, s));
-    SG_TRY(dsolve64(h, l, h->T64, w, Z + lo, P, o, s));
+    if (o.md_m0 & 2)
+      SG_TRY(m0_apply(h, SG_F64, h->T64, w, Z + lo, P, w, o, s));
+    else
+      SG_TRY(dsolve64(h, l, h->T64, w, Z + lo, P, o, s));
   }
   return SG_OK;
 }

@@ -1729,9 +1729,9 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
 int check_prec_opts(const sg_prec_opts& o) {
   if (o.nu < 1 || o.nu > 16 || !(o.omega > 0.0) || o.inner_maxit < 1 || o.inner_fixed_iters < 0 ||
       !(o.inner_tol >= 0.0) || (o.m0 != SG_M0_VCYCLE && o.m0 != SG_M0_DIAG) || !(o.level_tol >= 0.0) ||
-      o.level_maxit < 1 || o.level_maxit > 100000 || (o.df64 != 0 && o.df64 != 1)) {
+      o.level_maxit < 1 || o.level_maxit > 100000 || (o.df64 != 0 && o.df64 != 1) || o.md_m0 < 0 || o.md_m0 > 3) {
     set_error("prec opts: need 1 <= nu <= 16, omega > 0, inner_maxit >= 1, inner_tol >= 0, m0 0 or 1, "
-              "level_tol >= 0, 1 <= level_maxit <= 100000, df64 0 or 1");
+              "level_tol >= 0, 1 <= level_maxit <= 100000, df64 0 or 1, md_m0 0..3");
     return SG_ERR_INVALID_ARG;
   }
   return SG_OK;
@@ -2021,6 +2021,34 @@ static int vcycle_packed(sg_problem* h, InnerWork& iw, const T* B, T* bpad, T* X
   { k_scatter<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, res, X, w); ::sghsc::note_launch(); }
   SG_CHECK_LAUNCH();
   return SG_OK;
+}
+
+// The mean-value preconditioner M_0 alone (one V-cycle, or D^{-1} with the
+// diagonal M_0) on the w columns of a strided block: src, dst with leading
+// dimensions lds, ldd, element type dtype on both sides.
+template <typename T>
+static int m0_apply_t(sg_problem* h, const T* src, int lds, T* dst, int ldd, int w, const sg_prec_opts& o,
+                      cudaStream_t s) {
+  constexpr int N = VW<T>::N;
+  InnerWork& iw = sizeof(T) == 8 ? h->iw64 : h->iw32;
+  const GridLevel& G = h->grids[0];
+  const int wp = padded_width<T>(w);
+  const Shape sh = make_shape(h, G.n, wp / N);
+  { k_clear_done<<<1, 1024, 0, s>>>(iw.wcap, iw.done); ::sghsc::note_launch(); }
+  { k_pack<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, src, lds, (T*)iw.r); ::sghsc::note_launch(); }
+  const T* res = nullptr;
+  SG_TRY(vcycle<T>(h, iw, 0, (const T*)iw.r, (T*)iw.z, (T*)iw.zt, wp, o, s, nullptr, &res));
+  { k_scatter<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, res, dst, ldd); ::sghsc::note_launch(); }
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
+int m0_apply(sg_problem* h, int dtype, const void* src, int lds, void* dst, int ldd, int w, const sg_prec_opts& o,
+             cudaStream_t s) {
+  if (w <= 0) return SG_OK;
+  SG_TRY(ensure_inner_work(h, dtype, std::max(w, h->wmax)));
+  if (dtype == SG_F64) return m0_apply_t<double>(h, (const double*)src, lds, (double*)dst, ldd, w, o, s);
+  return m0_apply_t<float>(h, (const float*)src, lds, (float*)dst, ldd, w, o, s);
 }
 
 int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const sg_prec_opts& o, cudaStream_t s) {

@@ -525,6 +525,7 @@ void sg_default_prec_opts(sg_prec_opts* o) {
   o->m0 = SG_M0_VCYCLE;
   o->level_tol = 1e-8;
   o->level_maxit = 500;
+  o->md_m0 = 0;
   o->df64 = 0;
 }
 

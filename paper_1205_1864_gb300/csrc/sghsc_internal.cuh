@@ -227,6 +227,9 @@ int inner_vcycle(sg_problem* h, int dtype, const void* B, void* X, int w, const 
 int inner_solve(sg_problem* h, int dtype, const void* src, int ld_src, int src_t, void* dst,
                 int ld_dst, int dst_t, int w, const sg_prec_opts& o, cudaStream_t s);
 int check_prec_opts(const sg_prec_opts& o);
+// M_0 alone (one V-cycle, or the diagonal) on w strided columns, same type in and out.
+int m0_apply(sg_problem* h, int dtype, const void* src, int lds, void* dst, int ldd, int w, const sg_prec_opts& o,
+             cudaStream_t s);
 // The inner solves of o can run on h (grids for the diagonal M_0, the whole
 // hierarchy for the V-cycle); sets the error message and returns
 // SG_ERR_UNSUPPORTED otherwise.

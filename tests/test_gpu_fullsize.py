@@ -97,7 +97,10 @@ def test_cfg2_mixed_solve_matches_oracle(lib, cfg2, df64):
     U = _np(U)
     scale = np.abs(cfg2.ref).max()
     assert np.abs(U - cfg2.ref).max() <= 1e-7 * scale, np.abs(U - cfg2.ref).max() / scale
-    assert oracle_rel_residual(cfg2.A, cfg2.G, cfg2.F, U) <= 1.5e-12
+    # attainable true residual: the outer product's rounding relative to the
+    # stencil's cancellation (sum |terms| / |result| ~ 1/h^2 = 1.6e4 here) times
+    # 2^-53 (FP64) or 2^-47 (double-float)
+    assert oracle_rel_residual(cfg2.A, cfg2.G, cfg2.F, U) <= (1.5e-12 if not df64 else 2e-11)
 
 
 def test_cfg2_fp64_solve_matches_oracle(lib, cfg2):

@@ -142,3 +142,33 @@ def test_schur_reduced_solve_recovers_the_full_solution(M, p):
     Sd = K[:e, :e] - K[:e, e:] @ np.linalg.solve(K[e:, e:], K[e:, :e])
     evs, eva = np.linalg.eigvalsh(0.5 * (Sd + Sd.T)), np.linalg.eigvalsh(K)
     assert evs[-1] / evs[0] <= eva[-1] / eva[0] * (1 + 1e-12)
+
+
+def test_general_prec_variants_match_the_paper_formula():
+    """Sec. 5, eq. (general-prec): Algorithm 1 with the pre-correction's
+    D^{-1} replaced by an operator M1 and the post-correction's by M2 (= M_D^2
+    = M_D^3) equals the dense product of the three factors, at one level
+    (p = 1, M_S = A_0^{-1}); with exact D^{-1} in both places it is the
+    block inverse with S replaced by A_0."""
+    import scipy.sparse as sp
+    prob = S.make_problem(4, 2, 0.3, 0.5)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(2, 1)
+    _, off = chaos.multi_indices(2, 1)
+    n, P = prob.n, G[0].shape[0]
+    K = so.global_matrix_chaos_major(A, G).toarray()
+    e = n * off[1]
+    A0, B, C, D = K[:e, :e], K[:e, e:], K[e:, :e], K[e:, e:]
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((D.shape[0], D.shape[0]))
+    M1 = np.linalg.inv(D) + 1e-2 * (X + X.T)         # two different symmetric approximations of D^{-1}
+    M2 = np.diag(1.0 / np.diag(D))
+    blk = lambda Md: (lambda l, Y: (Md @ Y.T.ravel()).reshape(Y.shape[1], n).T)
+    R = S.random_block(n, P, seed=2)
+    U = hsc.hsc_apply(A, G, off, R, dsolve_pre=blk(M1), dsolve_post=blk(M2))
+    Md = hsc.general_prec(A0, B, C, np.linalg.inv(A0), M1, M2, M2)
+    ref = (Md @ R.T.ravel()).reshape(P, n).T
+    assert np.abs(U - ref).max() <= 1e-12 * np.abs(ref).max()
+    Dinv = np.linalg.inv(D)
+    exact = hsc.general_prec(A0, B, C, np.linalg.inv(A0), Dinv, Dinv, Dinv)
+    assert np.abs(exact - hsc.block_inverse(A0, B, C, D, S_inv=np.linalg.inv(A0))).max() <= 1e-12 * np.abs(exact).max()
