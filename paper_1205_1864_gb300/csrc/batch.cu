@@ -289,7 +289,8 @@ int sg_autotune(sg_problem* h, void* stream) {
   SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
   SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
   SG_TRY(autotune_outer(h, (cudaStream_t)stream, false));
-  SG_TRY(autotune_outer(h, (cudaStream_t)stream, true));
+  // the double-float pair-form kernel has a fixed shape; tune the general one only when it stands in
+  if (!df_pairs_usable(h, h->all, h->P)) SG_TRY(autotune_outer(h, (cudaStream_t)stream, true));
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = TuneVal{h->k1_threads[SG_F64], h->k1_threads[SG_F32], h->outer_threads,
                               h->k1_pairs[SG_F64],   h->k1_pairs[SG_F32],   h->outer_pairs,

@@ -1,0 +1,251 @@
+// Double-float SG products whose input block holds FP32 values (the output
+// of the mixed-precision preconditioner): the outer solver's fused product
+// q = A p (eq. (global-system) in MAT-VEC form, with the CG update) and the
+// level-p products B_p, C_p of Algorithm 1. The arithmetic is double-float
+// (df64.cuh) on the FP32 units; this file lays the work out for those units.
+//
+// Pair form, one spatial row at a time per block (grid-stride over rows):
+//   stage   the row's values a_k(r, c) as [k][e] and the input rows X(c, :)
+//           as [j][e] (e the nonzero, CH = 9 slots, zero-filled), so the
+//           inner loop over the 9 nonzeros uses constant offsets only and the
+//           lanes of a warp (consecutive pairs: the same k, consecutive j)
+//           read one broadcast value and 32 distinct banks (stride 9 words);
+//   pairs   every distinct (k, j) of the couplings: S_q = sum_e a_k(e) X(e, j)
+//           into shared memory, each thread keeping its pairs in registers;
+//           with DIAG also the k = 0 term of its own outputs;
+//   couple  Y(r, l) = diag + sum_t c_t S_pair(t) over the couplings of l.
+// Rows longer than CH are done in chunks of CH (the first chunk stores, later
+// ones add).
+#include <algorithm>
+#include <type_traits>
+
+#include "df64.cuh"
+#include "sghsc_internal.cuh"
+#include "vec.cuh"
+
+namespace sghsc {
+
+constexpr int DF_CH = 9;       // nonzeros per staged chunk (the Q1 stencil row)
+constexpr int DF_MAXQ = 16;    // pairs per thread kept in registers
+
+// FP32 value of an input element that is FP32-exact: a float as it is, a
+// double (the FP64 widening of an FP32 number) re-packed with integer
+// operations (truncating the fraction, which is exact for such values).
+__device__ __forceinline__ float exact_float(float v) { return v; }
+__device__ __forceinline__ float exact_float(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ff);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if (E == 0) return __uint_as_float(sign);
+  const int ef = E - 1023 + 127;
+  if (ef < 1 || ef > 254) return __double2float_rn(v);   // outside the normal FP32 range (not expected)
+  return __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+// a (double-float) times x (FP32): exact product of a.hi and x plus a.lo x
+__device__ __forceinline__ df64 df_mul_f(const df64& a, float x) {
+  const float p = a.hi * x;
+  float e = fmaf(a.hi, x, -p);
+  e = fmaf(a.lo, x, e);
+  return df64(p, e);
+}
+
+// Stage chunk cs..cs+nzc-1 (nzc <= DF_CH): values [k][e], inputs [j][e],
+// slots e >= nzc zero. Loads four at a time in flight before the stores.
+template <typename TX>
+__device__ __forceinline__ void df_stage(int cs, int nzc, int M1, const int* __restrict__ colidx,
+                                         const df64* __restrict__ vals, const TX* __restrict__ X, int ldx, int wx,
+                                         df64* Vt, float* Xt) {
+  for (int idx = threadIdx.x; idx < M1 * DF_CH; idx += blockDim.x) {
+    const int e = idx / M1, k = idx - e * M1;
+    Vt[k * DF_CH + e] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : df64(0.f, 0.f);
+  }
+  const int cnt = DF_CH * wx;
+  for (int base = threadIdx.x; base < cnt; base += 4 * blockDim.x) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      v[u] = 0.f;
+      if (idx < cnt) {
+        const int e = idx / wx, j = idx - e * wx;
+        if (e < nzc) v[u] = exact_float(X[(size_t)colidx[cs + e] * ldx + j]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < cnt) {
+        const int e = idx / wx, j = idx - e * wx;
+        Xt[j * DF_CH + e] = v[u];
+      }
+    }
+  }
+}
+
+// sum_e a[e] x[e] over the DF_CH slots (constant offsets)
+__device__ __forceinline__ df64 df_dot9(const df64* __restrict__ a, const float* __restrict__ x) {
+  df64 s = df_mul_f(a[0], x[0]);
+#pragma unroll
+  for (int e = 1; e < DF_CH; ++e) s += df_mul_f(a[e], x[e]);
+  return s;
+}
+
+// OUTER = false: level product, Y = Yin - sum (Yin FP64, Y FP32), all in
+// double-float arithmetic. OUTER = true: the outer CG step (as k_outer_matvec):
+// p_new = z + beta p_old, q = A z + beta q_old, p_new . q and alpha, with
+// X = z (FP64 storage of FP32 values).
+template <int MAXO, bool DIAG, bool OUTER, typename TX>
+__global__ void __launch_bounds__(512, 2) k_df_pairs(
+    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const df64* __restrict__ vals, int M1,
+    const TX* __restrict__ X, int ldx, int wx, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
+    const int* __restrict__ eptr, const int* __restrict__ eperm, const int* __restrict__ epair,
+    const df64* __restrict__ ec, int wy, const double* __restrict__ Yin, int ldyin, float* __restrict__ Y, int ldy,
+    double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  df64* Ss = reinterpret_cast<df64*>(smem_raw);
+  df64* Vt = Ss + npair;
+  float* Xt = reinterpret_cast<float*>(Vt + (size_t)M1 * DF_CH);
+  // this thread's pairs (consecutive threads: consecutive pairs) and outputs
+  unsigned qkj[DF_MAXQ];   // k << 16 | j
+#pragma unroll
+  for (int i = 0; i < DF_MAXQ; ++i) {
+    const int qi = threadIdx.x + i * blockDim.x;
+    qkj[i] = qi < npair ? ((unsigned)pk[qi] << 16) | (unsigned)pj[qi] : 0u;
+  }
+  int lcol[MAXO];
+#pragma unroll
+  for (int i = 0; i < MAXO; ++i) {
+    const int slot = threadIdx.x + i * blockDim.x;
+    lcol[i] = slot < wy ? eperm[slot] : -1;
+  }
+  int it = 0;
+  double beta = 0.0, dot = 0.0;
+  const double* pold = nullptr;
+  double* pnew = nullptr;
+  if constexpr (OUTER) {
+    it = a.ctl->it;
+    beta = it == 0 ? 0.0 : a.sc[SC_BETA];
+    pold = (it & 1) ? pB : pA;
+    pnew = (it & 1) ? pA : pB;
+  }
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    df64 dacc[MAXO];
+    const int rb = rowptr[r], re = rowptr[r + 1];
+    for (int cs = rb; cs < re; cs += DF_CH) {
+      const int nzc = min(DF_CH, re - cs);
+      __syncthreads();
+      df_stage<TX>(cs, nzc, M1, colidx, vals, X, ldx, wx, Vt, Xt);
+      __syncthreads();
+      const bool first = cs == rb;
+      if (DIAG) {
+#pragma unroll
+        for (int i = 0; i < MAXO; ++i) {
+          const int l = lcol[i];
+          if (l >= 0) {
+            const df64 d = df_dot9(Vt, Xt + l * DF_CH);
+            if (first) dacc[i] = d; else dacc[i] += d;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < DF_MAXQ; ++i) {
+        const int qi = threadIdx.x + i * blockDim.x;
+        if (qi < npair) {
+          const df64 s = df_dot9(Vt + (qkj[i] >> 16) * DF_CH, Xt + (qkj[i] & 0xffffu) * DF_CH);
+          if (first) Ss[qi] = s; else Ss[qi] += s;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MAXO; ++i) {
+      const int l = lcol[i];
+      if (l < 0) continue;
+      df64 acc = (DIAG && re > rb) ? dacc[i] : df64(0.f, 0.f);
+      if (re > rb) {
+        const int t1 = eptr[l + 1];
+        for (int t = eptr[l]; t < t1; ++t) acc += ec[t] * Ss[epair[t]];
+      }
+      acc = df_norm(acc);
+      if constexpr (OUTER) {
+        const size_t g = (size_t)r * wx + l;
+        const double av = f2d_bits(acc.hi) + f2d_bits(acc.lo);
+        const double zv = X[g];
+        const double pv = it == 0 ? zv : zv + beta * pold[g];
+        const double qv = it == 0 ? av : av + beta * q[g];
+        pnew[g] = pv;
+        q[g] = qv;
+        dot += pv * qv;
+      } else {
+        // Yin - sum in double-float, rounded once to FP32
+        df64 v = df_from_double(Yin[(size_t)r * ldyin + l]);
+        v += df64(-acc.hi, -acc.lo);
+        Y[(size_t)r * ldy + l] = v.hi + v.lo;
+      }
+    }
+  }
+  if constexpr (OUTER) {
+    double pq, unused;
+    if (outer_reduce_last(dot, 0.0, a, pq, unused) && threadIdx.x == 0) {
+      a.sc[SC_PQ] = pq;
+      if (!(pq > 0.0)) {
+        atomicOr(a.status, ST_OUTER_BREAKDOWN);
+        a.sc[SC_ALPHA] = 0.0;
+      } else {
+        a.sc[SC_ALPHA] = a.sc[SC_RHO] / pq;
+      }
+      a.hist_alpha[it] = a.sc[SC_ALPHA];
+    }
+  }
+}
+
+static size_t df_smem(int npair, int M1, int wx) {
+  return (size_t)npair * sizeof(df64) + (size_t)M1 * DF_CH * sizeof(df64) + (size_t)wx * DF_CH * sizeof(float);
+}
+
+// Usable when every thread's pairs fit its registers and the staging fits a
+// block's shared memory.
+bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx) {
+  return E.npair <= DF_MAXQ * 512 && h->nterm < 65536 && wx < 65536 &&
+         df_smem(E.npair, h->nterm, wx) <= (size_t)std::max(h->smem_optin, 48 * 1024);
+}
+
+template <bool DIAG, bool OUTER, typename TX>
+static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int wx, const double* Yin, int ldyin,
+                     float* Y, int ldy, const OuterArgs* oa, cudaStream_t s) {
+  const int wy = E.nout;
+  if (wy == 0) return SG_OK;
+  const int threads = 512;
+  const int maxo = (wy + threads - 1) / threads;
+  const size_t smem = df_smem(E.npair, h->nterm, wx);
+  OuterArgs a = oa ? *oa : OuterArgs{};
+  auto go = [&](auto kern) -> int {
+    SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
+    if (OUTER) grid = std::min(grid, h->opart_blocks);
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, (const df64*)h->vals_df, h->nterm, X, ldx, wx,
+                                       E.npair, E.pk, E.pj, E.ptr, E.perm, E.pair, (const df64*)E.cdf, wy, Yin, ldyin,
+                                       Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
+    SG_CHECK_LAUNCH();
+    return SG_OK;
+  };
+  if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX>);
+  if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX>);
+  if (maxo <= 4) return go(k_df_pairs<4, DIAG, OUTER, TX>);
+  set_error("double-float product: %d outputs exceed the supported 2048", wy);
+  return SG_ERR_UNSUPPORTED;
+}
+
+int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
+                    float* Y, int ldy, cudaStream_t s) {
+  return launch_df<false, false, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
+}
+
+int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
+  return launch_df<true, true, double>(h, h->all, h->fz, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
+}
+
+}  // namespace sghsc

@@ -443,6 +443,8 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
                                                          alpha, beta, (float*)Y, ldy, s);
   }
   if (tin == SG_F32 && tacc == ACC_DF64 && tb == SG_F64 && tout == SG_F32 && !diag) {
+    if (Yin && alpha == -1.0 && beta == 1.0 && df_pairs_usable(h, E, wx))
+      return launch_df_level(h, E, (const float*)X, ldx, wx, (const double*)Yin, ldyin, (float*)Y, ldy, s);
     return launch_t<float, df64, double, float, false>(h, (const float*)X, ldx, wx, E, (const double*)Yin, ldyin,
                                                        alpha, beta, (float*)Y, ldy, s);
   }
@@ -492,6 +494,7 @@ static int launch_outer_t(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
 }
 
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df) {
+  if (df && df_pairs_usable(h, h->all, h->P)) return launch_df_outer(h, a, s);
   return df ? launch_outer_t<df64>(h, a, s) : launch_outer_t<double>(h, a, s);
 }
 

@@ -217,6 +217,13 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
                         int wx, const EdgeList& E, bool diag, const void* Yin, int ldyin,
                         double alpha, double beta, void* Y, int ldy, cudaStream_t s);
 
+// ---- double-float pair-form products (dfprod.cu) ----
+// The input block holds FP32 values; usable when the pairs and the staging fit.
+bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx);
+// Y = Yin - sum_k A_k X G_k[out, in]^T: X FP32, Yin FP64, Y FP32.
+int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
+                    float* Y, int ldy, cudaStream_t s);
+
 // ---- inner solver (inner.cu) ----
 int ensure_inner_work(sg_problem* h, int dtype, int wcap);
 void free_inner_work(sg_problem* h);

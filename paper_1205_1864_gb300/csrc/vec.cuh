@@ -143,6 +143,8 @@ int vec_grid(long long N);
 // p_new . q reduction and the alpha update by the last block (matvec.cu).
 // df: the product in double-float arithmetic on the FP32 units.
 int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df = false);
+// The same in the double-float pair form (dfprod.cu); z must hold FP32 values.
+int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s);
 // Arguments of the outer-iteration kernels for this handle and options (fcg.cu).
 OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o);
 
