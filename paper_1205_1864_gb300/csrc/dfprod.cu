@@ -26,7 +26,7 @@
 namespace sghsc {
 
 constexpr int DF_CH = 9;       // nonzeros per staged chunk (the Q1 stencil row)
-constexpr int DF_MAXQ = 16;    // pairs per thread kept in registers
+constexpr int DF_MAXQ = 12;    // pairs per thread kept in registers
 
 // FP32 value of an input element that is FP32-exact: a float as it is, a
 // double (the FP64 widening of an FP32 number) re-packed with integer
@@ -51,35 +51,26 @@ __device__ __forceinline__ df64 df_mul_f(const df64& a, float x) {
 }
 
 // Stage chunk cs..cs+nzc-1 (nzc <= DF_CH): values [k][e], inputs [j][e],
-// slots e >= nzc zero. Loads four at a time in flight before the stores.
+// slots e >= nzc zero. The input rows go column position by column position
+// (no integer division), the loads of all slots of a position in flight
+// before their stores.
 template <typename TX>
 __device__ __forceinline__ void df_stage(int cs, int nzc, int M1, const int* __restrict__ colidx,
                                          const df64* __restrict__ vals, const TX* __restrict__ X, int ldx, int wx,
                                          df64* Vt, float* Xt) {
-  for (int idx = threadIdx.x; idx < M1 * DF_CH; idx += blockDim.x) {
-    const int e = idx / M1, k = idx - e * M1;
-    Vt[k * DF_CH + e] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : df64(0.f, 0.f);
+  for (int k = threadIdx.x; k < M1; k += blockDim.x) {
+#pragma unroll
+    for (int e = 0; e < DF_CH; ++e) Vt[k * DF_CH + e] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : df64(0.f, 0.f);
   }
-  const int cnt = DF_CH * wx;
-  for (int base = threadIdx.x; base < cnt; base += 4 * blockDim.x) {
-    float v[4];
+  int col[DF_CH];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = base + u * blockDim.x;
-      v[u] = 0.f;
-      if (idx < cnt) {
-        const int e = idx / wx, j = idx - e * wx;
-        if (e < nzc) v[u] = exact_float(X[(size_t)colidx[cs + e] * ldx + j]);
-      }
-    }
+  for (int e = 0; e < DF_CH; ++e) col[e] = e < nzc ? colidx[cs + e] : -1;
+  for (int j = threadIdx.x; j < wx; j += blockDim.x) {
+    float v[DF_CH];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx < cnt) {
-        const int e = idx / wx, j = idx - e * wx;
-        Xt[j * DF_CH + e] = v[u];
-      }
-    }
+    for (int e = 0; e < DF_CH; ++e) v[e] = col[e] >= 0 ? exact_float(X[(size_t)col[e] * ldx + j]) : 0.f;
+#pragma unroll
+    for (int e = 0; e < DF_CH; ++e) Xt[j * DF_CH + e] = v[e];
   }
 }
 
