@@ -42,6 +42,10 @@ __device__ __forceinline__ float exact_float(double v) {
   return __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffffu));
 }
 
+// an input element as FP64: a float widened with integer operations, a double as it is
+__device__ __forceinline__ double widen_exact(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double widen_exact(double v) { return v; }
+
 // a (double-float) times x (FP32): exact product of a.hi and x plus a.lo x
 __device__ __forceinline__ df64 df_mul_f(const df64& a, float x) {
   const float p = a.hi * x;
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(512, 2) k_df_pairs(
       if constexpr (OUTER) {
         const size_t g = (size_t)r * wx + l;
         const double av = f2d_bits(acc.hi) + f2d_bits(acc.lo);
-        const double zv = X[g];
+        const double zv = widen_exact(X[g]);
         const double pv = it == 0 ? zv : zv + beta * pold[g];
         const double qv = it == 0 ? av : av + beta * q[g];
         pnew[g] = pv;
@@ -235,7 +239,9 @@ int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, i
   return launch_df<false, false, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
 }
 
-int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
+int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s, const float* z32) {
+  // z itself in FP32 when the preconditioner leaves it there (half the staging reads, no conversion)
+  if (z32) return launch_df<true, true, float>(h, h->all, z32, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
   return launch_df<true, true, double>(h, h->all, h->fz, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
 }
 

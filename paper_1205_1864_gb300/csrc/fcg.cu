@@ -158,7 +158,9 @@ int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
     { k_outer_dots<<<vg, 256, 0, bs>>>(N, h->fz, h->fr, h->fq, a); ::sghsc::note_launch(); }
     // with an FP32 preconditioner and df64, the outer product runs in double-float arithmetic
     const bool df = o.precond != SG_PREC_NONE && o.prec.precision == SG_F32 && o.prec.df64;
-    SG_TRY(launch_outer_matvec(h, a, bs, df));
+    // Algorithm 1 and block Gauss-Seidel in FP32 leave z in h->Z32 before widening it
+    const float* z32 = df && (o.precond == SG_PREC_HSC || o.precond == SG_PREC_BGS) ? h->Z32 : nullptr;
+    SG_TRY(launch_outer_matvec(h, a, bs, df, z32));
     { k_outer_update<<<vg, 256, 0, bs>>>(N, h->fpA, h->fpB, h->fq, h->fx, h->fr, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;

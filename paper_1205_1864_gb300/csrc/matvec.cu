@@ -493,8 +493,8 @@ static int launch_outer_t(sg_problem* h, const OuterArgs& a, cudaStream_t s) {
   return SG_ERR_UNSUPPORTED;
 }
 
-int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df) {
-  if (df && df_pairs_usable(h, h->all, h->P)) return launch_df_outer(h, a, s);
+int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df, const float* z32) {
+  if (df && df_pairs_usable(h, h->all, h->P)) return launch_df_outer(h, a, s, z32);
   return df ? launch_outer_t<df64>(h, a, s) : launch_outer_t<double>(h, a, s);
 }
 

@@ -141,10 +141,13 @@ int vec_grid(long long N);
 // The outer CG step q = A p_new with p_new = z + beta p_old staged on the fly
 // (ping-pong p buffers chosen by the device iteration counter), the fused
 // p_new . q reduction and the alpha update by the last block (matvec.cu).
-// df: the product in double-float arithmetic on the FP32 units.
-int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df = false);
-// The same in the double-float pair form (dfprod.cu); z must hold FP32 values.
-int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s);
+// df: the product in double-float arithmetic on the FP32 units (z32: the
+// preconditioned residual in FP32 when the preconditioner leaves it there).
+int launch_outer_matvec(sg_problem* h, const OuterArgs& a, cudaStream_t s, bool df = false,
+                        const float* z32 = nullptr);
+// The same in the double-float pair form (dfprod.cu); z must hold FP32 values,
+// which z32 (n x P FP32, or null: read z) holds as well.
+int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s, const float* z32);
 // Arguments of the outer-iteration kernels for this handle and options (fcg.cu).
 OuterArgs outer_args(sg_problem* h, const sg_solve_opts& o);
 
