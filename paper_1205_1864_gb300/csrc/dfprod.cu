@@ -195,189 +195,6 @@ __global__ void __launch_bounds__(512, 2) k_df_pairs(
   }
 }
 
-// ---------------------------------------------------------------------------
-// Pipelined variant for FP32 inputs: the chunks of a block's rows are staged
-// by asynchronous copies into two buffers (the next chunk in flight while the
-// current one is computed), the input rows kept as they are in memory ([e][j],
-// so the copies need no conversion and no transposition), and the loop over
-// the nonzeros outside the loop over a thread's pairs: the nine input rows are
-// uniform addresses and each pair keeps its sum in registers across them.
-// One block of 1024 threads per SM; values still [k][e] (copied transposed).
-
-template <typename T>
-__device__ __forceinline__ void cp_async_zfill(T* dst, const T* src, bool valid) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const int n = valid ? (int)sizeof(T) : 0;   // 0: nothing is read, the slot is zero-filled
-  if constexpr (sizeof(T) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Issue the copies of chunk (cs, nzc) into buffer (Vb, Xb); slots e >= nzc zero.
-__device__ __forceinline__ void df_stage_async(int cs, int nzc, int M1, const int* __restrict__ colidx,
-                                               const df64* __restrict__ vals, const float* __restrict__ X, int ldx,
-                                               int wx, df64* Vb, float* Xb) {
-  for (int idx = threadIdx.x; idx < M1 * DF_CH; idx += blockDim.x) {
-    const int k = idx / DF_CH, e = idx - k * DF_CH;
-    cp_async_zfill(Vb + idx, vals + (size_t)(cs + (e < nzc ? e : 0)) * M1 + k, e < nzc);
-  }
-  for (int e = 0; e < DF_CH; ++e) {
-    const bool ok = e < nzc;
-    const float* src = X + (ok ? (size_t)colidx[cs + e] * ldx : 0);   // not read when !ok
-    for (int j = threadIdx.x; j < wx; j += blockDim.x) cp_async_zfill(Xb + e * wx + j, src + j, ok);
-  }
-}
-
-template <int MAXO, int MAXQ, bool DIAG, bool OUTER>
-__global__ void __launch_bounds__(1024, 1) k_df_pairs_pipe(
-    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const df64* __restrict__ vals, int M1,
-    const float* __restrict__ X, int ldx, int wx, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
-    const int* __restrict__ eptr, const int* __restrict__ eperm, const int* __restrict__ epair,
-    const df64* __restrict__ ec, int wy, const double* __restrict__ Yin, int ldyin, float* __restrict__ Y, int ldy,
-    double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  df64* Ss = reinterpret_cast<df64*>(smem_raw);
-  df64* Vb0 = Ss + npair;
-  df64* Vb1 = Vb0 + (size_t)M1 * DF_CH;
-  float* Xb0 = reinterpret_cast<float*>(Vb1 + (size_t)M1 * DF_CH);
-  float* Xb1 = Xb0 + (size_t)DF_CH * wx;
-  int qv[MAXQ], qx[MAXQ];   // this thread's pairs: value offset k * DF_CH, input column j
-  const int nq = threadIdx.x < npair ? (npair - 1 - (int)threadIdx.x) / (int)blockDim.x + 1 : 0;
-#pragma unroll
-  for (int i = 0; i < MAXQ; ++i) {
-    const int qi = threadIdx.x + i * blockDim.x;
-    qv[i] = i < nq ? pk[qi] * DF_CH : 0;
-    qx[i] = i < nq ? pj[qi] : 0;
-  }
-  int lcol[MAXO];
-#pragma unroll
-  for (int i = 0; i < MAXO; ++i) {
-    const int slot = threadIdx.x + i * blockDim.x;
-    lcol[i] = slot < wy ? eperm[slot] : -1;
-  }
-  int it = 0;
-  double beta = 0.0, dot = 0.0;
-  const double* pold = nullptr;
-  double* pnew = nullptr;
-  if constexpr (OUTER) {
-    it = a.ctl->it;
-    beta = it == 0 ? 0.0 : a.sc[SC_BETA];
-    pold = (it & 1) ? pB : pA;
-    pnew = (it & 1) ? pA : pB;
-  }
-  // the chunk sequence of this block: (row, first nonzero of the chunk)
-  int r = blockIdx.x, cs = r < n ? rowptr[r] : 0, re = r < n ? rowptr[r + 1] : 0;
-  auto advance = [&](int& rr, int& cc, int& ee) {
-    cc += DF_CH;
-    if (cc >= ee) {
-      rr += gridDim.x;
-      cc = rr < n ? rowptr[rr] : 0;
-      ee = rr < n ? rowptr[rr + 1] : 0;
-    }
-  };
-  // rows without nonzeros still produce their outputs: a chunk of zero
-  // nonzeros stands for them (nzc = 0: everything zero-filled)
-  if (r < n) df_stage_async(cs, min(DF_CH, re - cs), M1, colidx, vals, X, ldx, wx, Vb0, Xb0);
-  cp_async_commit();
-  int buf = 0;
-  df64 dacc[MAXO];
-  while (r < n) {
-    // issue the next chunk into the other buffer
-    int r2 = r, c2 = cs, e2 = re;
-    advance(r2, c2, e2);
-    if (r2 < n) df_stage_async(c2, min(DF_CH, e2 - c2), M1, colidx, vals, X, ldx, wx, buf ? Vb0 : Vb1, buf ? Xb0 : Xb1);
-    cp_async_commit();
-    cp_async_wait_one();
-    __syncthreads();
-    const df64* Vb = buf ? Vb1 : Vb0;
-    const float* Xb = buf ? Xb1 : Xb0;
-    const bool first = cs == rowptr[r];
-    if (DIAG) {
-#pragma unroll
-      for (int i = 0; i < MAXO; ++i) {
-        const int l = lcol[i];
-        if (l >= 0) {
-          df64 d = df_mul_f(Vb[0], Xb[l]);
-#pragma unroll
-          for (int e = 1; e < DF_CH; ++e) d += df_mul_f(Vb[e], Xb[e * wx + l]);
-          if (first) dacc[i] = d; else dacc[i] += d;
-        }
-      }
-    }
-    df64 S[MAXQ];
-#pragma unroll
-    for (int i = 0; i < MAXQ; ++i)
-      if (i < nq) S[i] = df_mul_f(Vb[qv[i]], Xb[qx[i]]);
-#pragma unroll
-    for (int e = 1; e < DF_CH; ++e) {
-      const float* xr = Xb + e * wx;
-#pragma unroll
-      for (int i = 0; i < MAXQ; ++i)
-        if (i < nq) S[i] += df_mul_f(Vb[qv[i] + e], xr[qx[i]]);
-    }
-#pragma unroll
-    for (int i = 0; i < MAXQ; ++i) {
-      const int qi = threadIdx.x + i * blockDim.x;
-      if (i < nq) {
-        if (first) Ss[qi] = S[i]; else Ss[qi] += S[i];
-      }
-    }
-    const bool last = cs + DF_CH >= re;
-    if (last) {
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < MAXO; ++i) {
-        const int l = lcol[i];
-        if (l < 0) continue;
-        df64 acc = DIAG ? dacc[i] : df64(0.f, 0.f);
-        const int t1 = eptr[l + 1];
-        for (int t = eptr[l]; t < t1; ++t) acc += ec[t] * Ss[epair[t]];
-        acc = df_norm(acc);
-        if constexpr (OUTER) {
-          const size_t g = (size_t)r * wx + l;
-          const double av = f2d_bits(acc.hi) + f2d_bits(acc.lo);
-          const double zv = f2d_bits(X[g]);
-          const double pv = it == 0 ? zv : zv + beta * pold[g];
-          const double qq = it == 0 ? av : av + beta * q[g];
-          pnew[g] = pv;
-          q[g] = qq;
-          dot += pv * qq;
-        } else {
-          df64 v = df_from_double(Yin[(size_t)r * ldyin + l]);
-          v += df64(-acc.hi, -acc.lo);
-          Y[(size_t)r * ldy + l] = v.hi + v.lo;
-        }
-      }
-    }
-    __syncthreads();   // the buffer just read is the next one staged into
-    r = r2;
-    cs = c2;
-    re = e2;
-    buf ^= 1;
-  }
-  if constexpr (OUTER) {
-    double pq, unused;
-    if (outer_reduce_last(dot, 0.0, a, pq, unused) && threadIdx.x == 0) {
-      a.sc[SC_PQ] = pq;
-      if (!(pq > 0.0)) {
-        atomicOr(a.status, ST_OUTER_BREAKDOWN);
-        a.sc[SC_ALPHA] = 0.0;
-      } else {
-        a.sc[SC_ALPHA] = a.sc[SC_RHO] / pq;
-      }
-      a.hist_alpha[it] = a.sc[SC_ALPHA];
-    }
-  }
-}
-
-static size_t df_smem_pipe(int npair, int M1, int wx) {
-  return (size_t)npair * sizeof(df64) + 2 * (size_t)M1 * DF_CH * sizeof(df64) + 2 * (size_t)wx * DF_CH * sizeof(float);
-}
-
 static size_t df_smem(int npair, int M1, int wx) {
   return (size_t)npair * sizeof(df64) + (size_t)M1 * DF_CH * sizeof(df64) + (size_t)wx * DF_CH * sizeof(float);
 }
@@ -417,56 +234,13 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
   return SG_ERR_UNSUPPORTED;
 }
 
-template <bool DIAG, bool OUTER>
-static int launch_df_pipe(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin,
-                          int ldyin, float* Y, int ldy, const OuterArgs* oa, cudaStream_t s) {
-  const int wy = E.nout;
-  if (wy == 0) return SG_OK;
-  const int threads = 1024;
-  const int maxo = (wy + threads - 1) / threads, maxq = (E.npair + threads - 1) / threads;
-  const size_t smem = df_smem_pipe(E.npair, h->nterm, wx);
-  OuterArgs a = oa ? *oa : OuterArgs{};
-  auto go = [&](auto kern) -> int {
-    SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
-    if (OUTER) grid = std::min(grid, h->opart_blocks);
-    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, (const df64*)h->vals_df, h->nterm, X, ldx, wx,
-                                       E.npair, E.pk, E.pj, E.ptr, E.perm, E.pair, (const df64*)E.cdf, wy, Yin, ldyin,
-                                       Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
-    SG_CHECK_LAUNCH();
-    return SG_OK;
-  };
-  auto by_q = [&](auto o_tag) -> int {
-    constexpr int MO = decltype(o_tag)::value;
-    if (maxq <= 1) return go(k_df_pairs_pipe<MO, 1, DIAG, OUTER>);
-    if (maxq <= 2) return go(k_df_pairs_pipe<MO, 2, DIAG, OUTER>);
-    if (maxq <= 4) return go(k_df_pairs_pipe<MO, 4, DIAG, OUTER>);
-    if (maxq <= 8) return go(k_df_pairs_pipe<MO, 8, DIAG, OUTER>);
-    set_error("double-float product: %d pairs exceed the supported 8192", E.npair);
-    return SG_ERR_UNSUPPORTED;
-  };
-  if (maxo <= 1) return by_q(std::integral_constant<int, 1>{});
-  if (maxo <= 2) return by_q(std::integral_constant<int, 2>{});
-  set_error("double-float product: %d outputs exceed the supported 2048", wy);
-  return SG_ERR_UNSUPPORTED;
-}
-
-static bool df_pipe_usable(const sg_problem* h, const EdgeList& E, int wx) {
-  return E.npair <= 8 * 1024 && df_smem_pipe(E.npair, h->nterm, wx) <= (size_t)std::max(h->smem_optin, 48 * 1024);
-}
-
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
                     float* Y, int ldy, cudaStream_t s) {
-  if (df_pipe_usable(h, E, wx)) return launch_df_pipe<false, false>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
   return launch_df<false, false, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
 }
 
 int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s, const float* z32) {
   // z itself in FP32 when the preconditioner leaves it there (half the staging reads, no conversion)
-  if (z32 && df_pipe_usable(h, h->all, h->P))
-    return launch_df_pipe<true, true>(h, h->all, z32, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
   if (z32) return launch_df<true, true, float>(h, h->all, z32, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
   return launch_df<true, true, double>(h, h->all, h->fz, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
 }
