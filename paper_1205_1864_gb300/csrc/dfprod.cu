@@ -89,18 +89,27 @@ __device__ __forceinline__ df64 df_dot9(const df64* __restrict__ a, const float*
 // OUTER = false: level product, Y = Yin - sum (Yin FP64, Y FP32), all in
 // double-float arithmetic. OUTER = true: the outer CG step (as k_outer_matvec):
 // p_new = z + beta p_old, q = A z + beta q_old, p_new . q and alpha, with
-// X = z (FP64 storage of FP32 values).
-template <int MAXO, bool DIAG, bool OUTER, typename TX>
-__global__ void __launch_bounds__(512, 2) k_df_pairs(
+// X = z (FP32, or FP64 storage of FP32 values).
+// Shared memory: pair sums Ss[npair], diagonal terms Ds[wy] (DIAG, by output
+// column in natural order, so the lanes of a warp read consecutive inputs),
+// the compact coupling table Ct[nedges] and its coefficients Ctab[ncls]
+// (loaded once per block), then the staged chunk Vt, Xt.
+template <int MAXO, bool DIAG, bool OUTER, typename TX, int LB>
+__global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const df64* __restrict__ vals, int M1,
     const TX* __restrict__ X, int ldx, int wx, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
-    const int* __restrict__ eptr, const int* __restrict__ eperm, const int* __restrict__ epair,
-    const df64* __restrict__ ec, int wy, const double* __restrict__ Yin, int ldyin, float* __restrict__ Y, int ldy,
-    double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
+    const int* __restrict__ eptr, const int* __restrict__ eperm, const unsigned* __restrict__ cpack,
+    const df64* __restrict__ ctab, int ncls, int nedges, int wy, const double* __restrict__ Yin, int ldyin,
+    float* __restrict__ Y, int ldy, double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   df64* Ss = reinterpret_cast<df64*>(smem_raw);
-  df64* Vt = Ss + npair;
-  float* Xt = reinterpret_cast<float*>(Vt + (size_t)M1 * DF_CH);
+  df64* Ds = Ss + npair;
+  df64* Ctab = Ds + (DIAG ? wy : 0);
+  df64* Vt = Ctab + ncls;
+  unsigned* Ct = reinterpret_cast<unsigned*>(Vt + (size_t)M1 * DF_CH);
+  float* Xt = reinterpret_cast<float*>(Ct + ((nedges + 1) & ~1));
+  for (int t = threadIdx.x; t < nedges; t += blockDim.x) Ct[t] = cpack[t];
+  for (int t = threadIdx.x; t < ncls; t += blockDim.x) Ctab[t] = ctab[t];
   // this thread's pairs (consecutive threads: consecutive pairs) and outputs
   unsigned qkj[DF_MAXQ];   // k << 16 | j
 #pragma unroll
@@ -108,11 +117,13 @@ __global__ void __launch_bounds__(512, 2) k_df_pairs(
     const int qi = threadIdx.x + i * blockDim.x;
     qkj[i] = qi < npair ? ((unsigned)pk[qi] << 16) | (unsigned)pj[qi] : 0u;
   }
-  int lcol[MAXO];
+  int lcol[MAXO], t0[MAXO], t1[MAXO];
 #pragma unroll
   for (int i = 0; i < MAXO; ++i) {
     const int slot = threadIdx.x + i * blockDim.x;
     lcol[i] = slot < wy ? eperm[slot] : -1;
+    t0[i] = lcol[i] >= 0 ? eptr[lcol[i]] : 0;
+    t1[i] = lcol[i] >= 0 ? eptr[lcol[i] + 1] : 0;
   }
   int it = 0;
   double beta = 0.0, dot = 0.0;
@@ -125,7 +136,6 @@ __global__ void __launch_bounds__(512, 2) k_df_pairs(
     pnew = (it & 1) ? pA : pB;
   }
   for (int r = blockIdx.x; r < n; r += gridDim.x) {
-    df64 dacc[MAXO];
     const int rb = rowptr[r], re = rowptr[r + 1];
     for (int cs = rb; cs < re; cs += DF_CH) {
       const int nzc = min(DF_CH, re - cs);
@@ -136,10 +146,10 @@ __global__ void __launch_bounds__(512, 2) k_df_pairs(
       if (DIAG) {
 #pragma unroll
         for (int i = 0; i < MAXO; ++i) {
-          const int l = lcol[i];
-          if (l >= 0) {
+          const int l = threadIdx.x + i * blockDim.x;
+          if (l < wy) {
             const df64 d = df_dot9(Vt, Xt + l * DF_CH);
-            if (first) dacc[i] = d; else dacc[i] += d;
+            if (first) Ds[l] = d; else Ds[l] += d;
           }
         }
       }
@@ -157,10 +167,12 @@ __global__ void __launch_bounds__(512, 2) k_df_pairs(
     for (int i = 0; i < MAXO; ++i) {
       const int l = lcol[i];
       if (l < 0) continue;
-      df64 acc = (DIAG && re > rb) ? dacc[i] : df64(0.f, 0.f);
+      df64 acc = (DIAG && re > rb) ? Ds[l] : df64(0.f, 0.f);
       if (re > rb) {
-        const int t1 = eptr[l + 1];
-        for (int t = eptr[l]; t < t1; ++t) acc += ec[t] * Ss[epair[t]];
+        for (int t = t0[i]; t < t1[i]; ++t) {
+          const unsigned w = Ct[t];
+          acc += Ctab[w & 0xffu] * Ss[w >> 8];
+        }
       }
       acc = df_norm(acc);
       if constexpr (OUTER) {
@@ -195,15 +207,21 @@ __global__ void __launch_bounds__(512, 2) k_df_pairs(
   }
 }
 
-static size_t df_smem(int npair, int M1, int wx) {
-  return (size_t)npair * sizeof(df64) + (size_t)M1 * DF_CH * sizeof(df64) + (size_t)wx * DF_CH * sizeof(float);
+static size_t df_smem(const EdgeList& E, int M1, int wx, bool diag) {
+  return ((size_t)E.npair + (diag ? E.nout : 0) + E.ncls + (size_t)M1 * DF_CH) * sizeof(df64) +
+         (size_t)((E.nedges + 1) & ~1) * sizeof(unsigned) + (size_t)wx * DF_CH * sizeof(float);
 }
 
-// Usable when every thread's pairs fit its registers and the staging fits a
-// block's shared memory.
+// Block size: 256 threads when the pairs and two outputs per thread fit, else
+// 512 (more, smaller blocks hide the row barriers better; more outputs per
+// thread would spill).
+static int df_threads(const EdgeList& E) { return E.npair <= DF_MAXQ * 256 && E.nout <= 512 ? 256 : 512; }
+
+// Usable when every thread's pairs fit its registers, the couplings have a
+// compact table and the staging fits a block's shared memory.
 bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx) {
-  return E.npair <= DF_MAXQ * 512 && h->nterm < 65536 && wx < 65536 &&
-         df_smem(E.npair, h->nterm, wx) <= (size_t)std::max(h->smem_optin, 48 * 1024);
+  return E.npair <= DF_MAXQ * 512 && E.ncls > 0 && h->nterm < 65536 && wx < 65536 &&
+         df_smem(E, h->nterm, wx, true) <= (size_t)std::max(h->smem_optin, 48 * 1024);
 }
 
 template <bool DIAG, bool OUTER, typename TX>
@@ -211,9 +229,9 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
                      float* Y, int ldy, const OuterArgs* oa, cudaStream_t s) {
   const int wy = E.nout;
   if (wy == 0) return SG_OK;
-  const int threads = 512;
+  const int threads = df_threads(E);
   const int maxo = (wy + threads - 1) / threads;
-  const size_t smem = df_smem(E.npair, h->nterm, wx);
+  const size_t smem = df_smem(E, h->nterm, wx, DIAG);
   OuterArgs a = oa ? *oa : OuterArgs{};
   auto go = [&](auto kern) -> int {
     SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -222,14 +240,19 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
     int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
     if (OUTER) grid = std::min(grid, h->opart_blocks);
     { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, (const df64*)h->vals_df, h->nterm, X, ldx, wx,
-                                       E.npair, E.pk, E.pj, E.ptr, E.perm, E.pair, (const df64*)E.cdf, wy, Yin, ldyin,
-                                       Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
+                                       E.npair, E.pk, E.pj, E.ptr, E.perm, E.cpack, (const df64*)E.ctab, E.ncls,
+                                       E.nedges, wy, Yin, ldyin, Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
-  if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX>);
-  if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX>);
-  if (maxo <= 4) return go(k_df_pairs<4, DIAG, OUTER, TX>);
+  if (threads == 256) {
+    if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX, 256>);
+    if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX, 256>);
+  } else {
+    if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX, 512>);
+    if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX, 512>);
+    if (maxo <= 4) return go(k_df_pairs<4, DIAG, OUTER, TX, 512>);
+  }
   set_error("double-float product: %d outputs exceed the supported 2048", wy);
   return SG_ERR_UNSUPPORTED;
 }

@@ -102,6 +102,24 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
   }
   for (int t = 0; t < E.nedges; ++t) pair[t] = pairs.at(std::make_pair(he.k[t], he.j[t]));
   E.npair = (int)pk.size();
+  {
+    std::map<double, int> cls;
+    for (double c : he.c) cls.emplace(c, 0);
+    if (cls.size() <= 256 && E.npair < (1 << 24)) {
+      std::vector<df64> tab;
+      for (auto& kv : cls) {
+        kv.second = (int)tab.size();
+        tab.push_back(df_split_host(kv.first));
+      }
+      std::vector<unsigned> packed(E.nedges);
+      for (int t = 0; t < E.nedges; ++t) packed[t] = ((unsigned)pair[t] << 8) | (unsigned)cls.at(he.c[t]);
+      df64* dt = nullptr;
+      SG_TRY(upload(&E.cpack, packed.data(), packed.size()));
+      SG_TRY(upload(&dt, tab.data(), tab.size()));
+      E.ctab = dt;
+      E.ncls = (int)tab.size();
+    }
+  }
   SG_TRY(upload(&E.pk, pk.data(), pk.size()));
   SG_TRY(upload(&E.pj, pj.data(), pj.size()));
   SG_TRY(upload(&E.pair, pair.data(), pair.size()));
@@ -116,6 +134,8 @@ static void free_edges(EdgeList& E) {
   cudaFree(E.c64);
   cudaFree(E.c32);
   cudaFree(E.cdf);
+  cudaFree(E.cpack);
+  cudaFree(E.ctab);
   cudaFree(E.pk);
   cudaFree(E.pj);
   cudaFree(E.pair);

@@ -64,6 +64,13 @@ struct EdgeList {
   int* pk = nullptr;
   int* pj = nullptr;
   int* pair = nullptr;
+  // Compact coupling table: pair << 8 | class per coupling, the coefficient of
+  // class c in ctab[c] (df64). The coefficients of the linear KL expansion take
+  // one value per 1-D degree, so a few classes cover them; ncls = 0 when the
+  // table does not compress (more than 256 distinct coefficients).
+  unsigned* cpack = nullptr;
+  void* ctab = nullptr;
+  int ncls = 0;
 };
 
 // One grid of the geometric multigrid hierarchy: interior nodes nx*ny, x
