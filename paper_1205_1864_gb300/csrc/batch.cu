@@ -232,10 +232,10 @@ static int autotune_outer(sg_problem* h, cudaStream_t s, bool df) {
 // space and row lengths run the same launches, so a class is timed once per
 // process and later handles of that class take its shapes without timing.
 struct TuneKey {
-  int dev, n, nnz, M, p, family, max_row, q;
+  int dev, n, nnz, M, p, family, max_row, q, staged;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, n, nnz, M, p, family, max_row, q) <
-           std::tie(o.dev, o.n, o.nnz, o.M, o.p, o.family, o.max_row, o.q);
+    return std::tie(dev, n, nnz, M, p, family, max_row, q, staged) <
+           std::tie(o.dev, o.n, o.nnz, o.M, o.p, o.family, o.max_row, o.q, o.staged);
   }
 };
 struct TuneVal {
@@ -245,7 +245,7 @@ static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
 static TuneKey tune_key(const sg_problem* h) {
-  return TuneKey{h->device, h->n, h->nnz, h->M, h->p, h->family, h->max_row_nnz, h->q};
+  return TuneKey{h->device, h->n, h->nnz, h->M, h->p, h->family, h->max_row_nnz, h->q, h->staged_pairs};
 }
 
 // A block size the product kernels are instantiated for: whole warps, 32 to
@@ -287,7 +287,8 @@ int sg_autotune(sg_problem* h, void* stream) {
     }
   }
   SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
-  SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
+  // the FP32 full product takes the staged kernel (fixed shape) where it applies
+  if (!f32_pairs_usable(h, h->all, h->P)) SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
   SG_TRY(autotune_outer(h, (cudaStream_t)stream, false));
   // the double-float pair-form kernel has a fixed shape; tune the general one only when it stands in
   if (!df_pairs_usable(h, h->all, h->P)) SG_TRY(autotune_outer(h, (cudaStream_t)stream, true));

@@ -107,14 +107,32 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
     for (double c : he.c) cls.emplace(c, 0);
     if (cls.size() <= 256 && E.npair < (1 << 24)) {
       std::vector<df64> tab;
+      std::vector<float> tab32;
       for (auto& kv : cls) {
         kv.second = (int)tab.size();
         tab.push_back(df_split_host(kv.first));
+        tab32.push_back((float)kv.first);
       }
-      std::vector<unsigned> packed(E.nedges);
-      for (int t = 0; t < E.nedges; ++t) packed[t] = ((unsigned)pair[t] << 8) | (unsigned)cls.at(he.c[t]);
+      SG_TRY(upload(&E.ctab32, tab32.data(), tab32.size()));
+      // slot-transposed packing: warp w (slots 32w .. 32w+31, counts sorted
+      // descending) takes 32 words per coupling of its first slot
+      std::vector<int> tb(E.nout);
+      size_t total = 0;
+      for (int w0 = 0; w0 < E.nout; w0 += 32) {
+        const int cmax = he.ptr[perm[w0] + 1] - he.ptr[perm[w0]];
+        for (int sl = w0; sl < std::min(w0 + 32, E.nout); ++sl) tb[sl] = (int)total + (sl - w0);
+        total += (size_t)32 * cmax;
+      }
+      if (total >= (size_t)1 << 31) return SG_ERR_UNSUPPORTED;
+      std::vector<unsigned> packed(std::max<size_t>(total, 1), 0u);
+      for (int sl = 0; sl < E.nout; ++sl) {
+        const int l = perm[sl];
+        for (int t = he.ptr[l]; t < he.ptr[l + 1]; ++t)
+          packed[tb[sl] + 32 * (t - he.ptr[l])] = ((unsigned)pair[t] << 8) | (unsigned)cls.at(he.c[t]);
+      }
       df64* dt = nullptr;
-      SG_TRY(upload(&E.cpack, packed.data(), packed.size()));
+      SG_TRY(upload(&E.ctr, packed.data(), packed.size()));
+      SG_TRY(upload(&E.tb, tb.data(), tb.size()));
       SG_TRY(upload(&dt, tab.data(), tab.size()));
       E.ctab = dt;
       E.ncls = (int)tab.size();
@@ -134,8 +152,10 @@ static void free_edges(EdgeList& E) {
   cudaFree(E.c64);
   cudaFree(E.c32);
   cudaFree(E.cdf);
-  cudaFree(E.cpack);
+  cudaFree(E.ctr);
+  cudaFree(E.tb);
   cudaFree(E.ctab);
+  cudaFree(E.ctab32);
   cudaFree(E.pk);
   cudaFree(E.pj);
   cudaFree(E.pair);
@@ -457,6 +477,8 @@ static int setup_impl(const sg_mesh* mesh, int M, int p, int family, int n, int 
   {
     const char* ev = getenv("SGHSC_GATHER_FORM");   // start from the gather form of the full product
     if (ev && ev[0] == '1') h->k1_pairs[0] = h->k1_pairs[1] = h->outer_pairs = h->outer_pairs_df = 0;
+    const char* eg = getenv("SGHSC_GENERIC_PRODUCTS");   // the one-row-at-a-time kernels only
+    if ((ev && ev[0] == '1') || (eg && eg[0] == '1')) h->staged_pairs = 0;
   }
   SG_TRY_CUDA(cudaMalloc((void**)&h->loopflags, 8 * sizeof(int)));
   SG_TRY_CUDA(cudaMemset(h->loopflags, 0, 8 * sizeof(int)));

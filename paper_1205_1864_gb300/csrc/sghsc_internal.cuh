@@ -68,8 +68,13 @@ struct EdgeList {
   // class c in ctab[c] (df64). The coefficients of the linear KL expansion take
   // one value per 1-D degree, so a few classes cover them; ncls = 0 when the
   // table does not compress (more than 256 distinct coefficients).
-  unsigned* cpack = nullptr;
-  void* ctab = nullptr;
+  // couplings packed (pair << 8 | coefficient class), slot-transposed: the
+  // c-th coupling of output slot s (perm order) at ctr[tb[s] + 32 c], so the
+  // lanes of a warp (32 consecutive slots) read consecutive words
+  unsigned* ctr = nullptr;
+  int* tb = nullptr;
+  void* ctab = nullptr;      // df64
+  float* ctab32 = nullptr;   // the same coefficients in FP32
   int ncls = 0;
 };
 
@@ -206,6 +211,7 @@ struct sg_problem {
   int outer_pairs = 1;                      // the same for the fused outer product
   int outer_threads_df = 0;                 // block size and form of its double-float variant
   int outer_pairs_df = 1;
+  int staged_pairs = 1;                     // the staged pair kernels of dfprod.cu where usable
   long long ws_gen = 0;                     // bumped whenever captured graphs become invalid
 };
 
@@ -230,6 +236,13 @@ bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx);
 // Y = Yin - sum_k A_k X G_k[out, in]^T: X FP32, Yin FP64, Y FP32.
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
                     float* Y, int ldy, cudaStream_t s);
+// The same layout in FP32 arithmetic: the full product (diag, Yin null:
+// Y = sum) or a level product (Y = Yin - sum; Yin may alias Y).
+int launch_f32_pairs(sg_problem* h, const EdgeList& E, bool diag, const float* X, int ldx, int wx, const float* Yin,
+                     int ldyin, float* Y, int ldy, cudaStream_t s);
+// FP32 pair kernel usable and preferred for E (compact table, sizes, inputs
+// at least 512 columns wide).
+bool f32_pairs_usable(const sg_problem* h, const EdgeList& E, int wx);
 
 // ---- inner solver (inner.cu) ----
 int ensure_inner_work(sg_problem* h, int dtype, int wcap);

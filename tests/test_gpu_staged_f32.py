@@ -1,0 +1,102 @@
+"""The staged pair kernel in FP32 arithmetic: the full SG product (eq. (3)'s
+sum over the KL terms) and the level products B_l, C_l of Algorithm 1 whose
+input level has at least 512 columns, against the oracle within the FP32
+rounding bound, against the row-per-warp kernels (the same products with the
+staged kernels switched off), and inside the FP32 preconditioner."""
+import numpy as np
+import pytest
+
+import sg_inputs as S
+from oracle import gmg, hsc, krylov, sg_operator as so
+from tests.gpu_common import abs_bound, problem
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1205_1864_gb300 as L
+    return L
+
+
+def _t(x, dtype=None):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype or torch.float64, device="cuda")
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+# P = 1001, 924 and 680 columns; 9 x 9, 8 x 8 (not a power of two) and 5 x 5 nodes
+SHAPES = [(8, 10, 4), (7, 6, 6), (4, 14, 3)]
+
+
+@pytest.mark.parametrize("ne,M,p", SHAPES)
+def test_staged_f32_full_product(lib, ne, M, p, monkeypatch):
+    """Y = sum_k A_k U G_k^T in FP32: within m u sum|terms| of the exact
+    product (m: the longest chain of roundings, nine nonzeros per pair sum
+    plus the 2M + 1 couplings of an output), and within twice that of the
+    row-per-warp kernel."""
+    import torch
+    prob, A, G, off = problem(ne, M, p)
+    h = lib.SGProblem.from_inputs(prob, p)
+    assert h.P >= 512
+    U = S.random_block(prob.n, h.P, seed=11).astype(np.float32)
+    Y = _np(lib.sg_apply(h, _t(U, torch.float32)))
+    U = U.astype(np.float64)
+    ref = so.sg_apply(A, G, U)
+    bound = abs_bound(A, G, U)
+    m = 9 + 2 * M + 2
+    assert np.all(np.abs(Y - ref) <= m * U32 * bound + 1e-300)
+    monkeypatch.setenv("SGHSC_GENERIC_PRODUCTS", "1")
+    hg = lib.SGProblem.from_inputs(prob, p)
+    Yg = _np(lib.sg_apply(hg, _t(U, torch.float32)))
+    assert np.all(np.abs(Y - Yg) <= 2 * m * U32 * bound + 1e-300)
+    h.close()
+    hg.close()
+
+
+@pytest.mark.parametrize("ne,M,p", [(8, 10, 4), (4, 14, 3)])
+def test_staged_f32_wide_level_products(lib, ne, M, p):
+    """Y = Yin - sum_k A_k X G_k[out, in]^T in FP32 between the two top
+    levels in both directions (the input level of the pre product has 715 and
+    560 columns), within the FP32 bound of the exact value."""
+    import torch
+    prob, A, G, off = problem(ne, M, p)
+    h = lib.SGProblem.from_inputs(prob, p)
+    m = 9 + 2 * M + 3
+    for lo, li in ((p - 1, p), (p, p - 1)):
+        win, wout = off[li + 1] - off[li], off[lo + 1] - off[lo]
+        X = S.random_block(prob.n, win, seed=lo + 10 * li).astype(np.float32)
+        Yin = S.random_block(prob.n, wout, seed=5 + lo).astype(np.float32)
+        Y = _np(lib.sg_level_apply(h, lo, li, _t(X, torch.float32), _t(Yin, torch.float32)))
+        X, Yin = X.astype(np.float64), Yin.astype(np.float64)
+        exact = Yin - so.level_apply(A, G, off, lo, li, X)
+        bound = np.abs(Yin) + so.level_apply([abs(a) for a in A], [abs(g) for g in G], off, lo, li, np.abs(X))
+        assert np.all(np.abs(Y - exact) <= m * U32 * bound + 1e-300), (lo, li)
+    h.close()
+
+
+def test_staged_f32_inside_the_fp32_preconditioner(lib):
+    """Algorithm 1 in FP32 at P = 1001 (its level-4 pre product on the staged
+    kernel, in place) against the oracle's Algorithm 1 with the identical
+    inner solver (four V-cycle-preconditioned CG steps per D_l solve)."""
+    prob, A, G, off = problem(8, 10, 4)
+    h = lib.SGProblem.from_inputs(prob, 4)
+    lv = gmg.hierarchy(A[0], 8)
+
+    def dsolve(l, X):
+        return krylov.pcg_columns(lambda v: A[0] @ v, X, lambda r: gmg.vcycle(lv, r), tol=0.0, maxit=4,
+                                  fixed_iters=4)[0]
+
+    R = S.random_block(prob.n, h.P, seed=9)
+    o = lib.prec_opts(precision=lib.SG_F32, inner_fixed_iters=4)
+    Z = _np(lib.hsc_precond_apply(h, _t(R), o))
+    ref = hsc.hsc_apply(A, G, off, R, dsolve=dsolve)
+    assert np.abs(Z - ref).max() <= 2e-5 * np.abs(ref).max()
+    h.close()
