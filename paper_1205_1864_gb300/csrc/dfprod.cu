@@ -58,13 +58,13 @@ __device__ __forceinline__ df64 df_mul_f(const df64& a, float x) {
 // slots e >= nzc zero. The input rows go column position by column position
 // (no integer division), the loads of all slots of a position in flight
 // before their stores.
-template <typename TA, typename TX>
+template <typename TX>
 __device__ __forceinline__ void df_stage(int cs, int nzc, int M1, const int* __restrict__ colidx,
-                                         const TA* __restrict__ vals, const TX* __restrict__ X, int ldx, int wx,
-                                         TA* Vt, float* Xt) {
+                                         const df64* __restrict__ vals, const TX* __restrict__ X, int ldx, int wx,
+                                         df64* Vt, float* Xt) {
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
 #pragma unroll
-    for (int e = 0; e < DF_CH; ++e) Vt[k * DF_CH + e] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : TA(0.f);
+    for (int e = 0; e < DF_CH; ++e) Vt[k * DF_CH + e] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : df64(0.f, 0.f);
   }
   int col[DF_CH];
 #pragma unroll
@@ -78,55 +78,36 @@ __device__ __forceinline__ void df_stage(int cs, int nzc, int M1, const int* __r
   }
 }
 
-// sum_e a[e] x[e] over the DF_CH slots (constant offsets): double-float, or
-// FP32 multiply-adds
+// sum_e a[e] x[e] over the DF_CH slots (constant offsets)
 __device__ __forceinline__ df64 df_dot9(const df64* __restrict__ a, const float* __restrict__ x) {
   df64 s = df_mul_f(a[0], x[0]);
 #pragma unroll
   for (int e = 1; e < DF_CH; ++e) s += df_mul_f(a[e], x[e]);
   return s;
 }
-__device__ __forceinline__ float df_dot9(const float* __restrict__ a, const float* __restrict__ x) {
-  float s = a[0] * x[0];
-#pragma unroll
-  for (int e = 1; e < DF_CH; ++e) s = fmaf(a[e], x[e], s);
-  return s;
-}
 
-__device__ __forceinline__ df64 prod(const df64& c, const df64& s) { return c * s; }
-__device__ __forceinline__ float prod(float c, float s) { return c * s; }
-__device__ __forceinline__ void add_to(df64& acc, const df64& v) { acc += v; }
-__device__ __forceinline__ void add_to(float& acc, float v) { acc += v; }
-__device__ __forceinline__ df64 finish(const df64& v) { return df_norm(v); }
-__device__ __forceinline__ float finish(float v) { return v; }
-
-enum { DF_SUB = 0, DF_PLAIN = 1, DF_OUTER = 2 };   // Y = Yin - sum; Y = sum; the outer CG step
-
-// TA df64: double-float arithmetic, TA float: FP32 arithmetic (same layout).
-// MODE DF_SUB: Y = Yin - sum (a level product; double-float: Yin FP64, the
-// difference in double-float, rounded once to FP32); DF_PLAIN: Y = sum (the
-// full SG product); DF_OUTER (double-float): the outer CG step as
-// k_outer_matvec: p_new = z + beta p_old, q = A z + beta q_old, p_new . q and
-// alpha, with X = z (FP32, or FP64 storage of FP32 values).
+// OUTER = false: level product, Y = Yin - sum (Yin FP64, Y FP32), the
+// difference in double-float, rounded once to FP32. OUTER = true: the outer
+// CG step (as k_outer_matvec): p_new = z + beta p_old, q = A z + beta q_old,
+// p_new . q and alpha, with X = z (FP32, or FP64 storage of FP32 values).
 // Shared memory: pair sums Ss[npair], diagonal terms Ds[wy] (DIAG, by output
 // column in natural order, so the lanes of a warp read consecutive inputs),
 // the coefficient classes Ctab[ncls] (loaded once per block), then the
 // staged chunk Vt, Xt. The packed couplings stay in global memory, read
 // coalesced through L1 (in shared memory they held a block to one per SM at
 // P = 1001).
-template <typename TA, int MAXO, bool DIAG, int MODE, typename TX, typename TYin, int LB>
+template <int MAXO, bool DIAG, bool OUTER, typename TX, int LB>
 __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
-    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const TA* __restrict__ vals, int M1,
+    int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const df64* __restrict__ vals, int M1,
     const TX* __restrict__ X, int ldx, int wx, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
     const int* __restrict__ eptr, const int* __restrict__ eperm, const unsigned* __restrict__ ctr,
-    const int* __restrict__ etb, const TA* __restrict__ ctab, int ncls, int wy, const TYin* Yin, int ldyin,
-    float* Y, int ldy, double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
-  constexpr bool OUTER = MODE == DF_OUTER;
+    const int* __restrict__ etb, const df64* __restrict__ ctab, int ncls, int wy, const double* __restrict__ Yin,
+    int ldyin, float* __restrict__ Y, int ldy, double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TA* Ss = reinterpret_cast<TA*>(smem_raw);
-  TA* Ds = Ss + npair;
-  TA* Ctab = Ds + (DIAG ? wy : 0);
-  TA* Vt = Ctab + ncls;
+  df64* Ss = reinterpret_cast<df64*>(smem_raw);
+  df64* Ds = Ss + npair;
+  df64* Ctab = Ds + (DIAG ? wy : 0);
+  df64* Vt = Ctab + ncls;
   float* Xt = reinterpret_cast<float*>(Vt + (size_t)M1 * DF_CH);
   for (int t = threadIdx.x; t < ncls; t += blockDim.x) Ctab[t] = ctab[t];
   // this thread's pairs (consecutive threads: consecutive pairs) and outputs
@@ -161,7 +142,7 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
     for (int cs = rb; cs < re; cs += DF_CH) {
       const int nzc = min(DF_CH, re - cs);
       __syncthreads();
-      df_stage<TA, TX>(cs, nzc, M1, colidx, vals, X, ldx, wx, Vt, Xt);
+      df_stage<TX>(cs, nzc, M1, colidx, vals, X, ldx, wx, Vt, Xt);
       __syncthreads();
       const bool first = cs == rb;
       if (DIAG) {
@@ -169,8 +150,8 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
         for (int i = 0; i < MAXO; ++i) {
           const int l = threadIdx.x + i * blockDim.x;
           if (l < wy) {
-            const TA d = df_dot9(Vt, Xt + l * DF_CH);
-            if (first) Ds[l] = d; else add_to(Ds[l], d);
+            const df64 d = df_dot9(Vt, Xt + l * DF_CH);
+            if (first) Ds[l] = d; else Ds[l] += d;
           }
         }
       }
@@ -178,8 +159,8 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
       for (int i = 0; i < DF_MAXQ; ++i) {
         const int qi = threadIdx.x + i * blockDim.x;
         if (qi < npair) {
-          const TA s = df_dot9(Vt + (qkj[i] >> 16) * DF_CH, Xt + (qkj[i] & 0xffffu) * DF_CH);
-          if (first) Ss[qi] = s; else add_to(Ss[qi], s);
+          const df64 s = df_dot9(Vt + (qkj[i] >> 16) * DF_CH, Xt + (qkj[i] & 0xffffu) * DF_CH);
+          if (first) Ss[qi] = s; else Ss[qi] += s;
         }
       }
     }
@@ -188,23 +169,17 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
     for (int i = 0; i < MAXO; ++i) {
       const int l = lcol[i];
       if (l < 0) continue;
-      TA acc = (DIAG && re > rb) ? Ds[l] : TA(0.f);
+      df64 acc = (DIAG && re > rb) ? Ds[l] : df64(0.f, 0.f);
       if (re > rb) {
         const unsigned* cw = ctr + t0[i];
 #pragma unroll 4
         for (int c = 0; c < nc[i]; ++c) {
           const unsigned w = __ldg(cw + 32 * c);
-          add_to(acc, prod(Ctab[w & 0xffu], Ss[w >> 8]));
+          acc += Ctab[w & 0xffu] * Ss[w >> 8];
         }
       }
-      acc = finish(acc);
-      if constexpr (std::is_same_v<TA, float>) {
-        // FP32: the sum, or Yin minus it
-        if constexpr (MODE == DF_PLAIN) Y[(size_t)r * ldy + l] = acc;
-        else Y[(size_t)r * ldy + l] = (float)Yin[(size_t)r * ldyin + l] - acc;
-      } else if constexpr (MODE == DF_PLAIN) {
-        Y[(size_t)r * ldy + l] = acc.hi + acc.lo;
-      } else if constexpr (OUTER) {
+      acc = df_norm(acc);
+      if constexpr (OUTER) {
         const size_t g = (size_t)r * wx + l;
         const double av = f2d_bits(acc.hi) + f2d_bits(acc.lo);
         const double zv = widen_exact(X[g]);
@@ -215,7 +190,7 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
         dot += pv * qv;
       } else {
         // Yin - sum in double-float, rounded once to FP32
-        df64 v = df_from_double((double)Yin[(size_t)r * ldyin + l]);
+        df64 v = df_from_double(Yin[(size_t)r * ldyin + l]);
         v += df64(-acc.hi, -acc.lo);
         Y[(size_t)r * ldy + l] = v.hi + v.lo;
       }
@@ -236,8 +211,8 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
   }
 }
 
-static size_t df_smem(const EdgeList& E, int M1, int wx, bool diag, size_t es = sizeof(df64)) {
-  return ((size_t)E.npair + (diag ? E.nout : 0) + E.ncls + (size_t)M1 * DF_CH) * es +
+static size_t df_smem(const EdgeList& E, int M1, int wx, bool diag) {
+  return ((size_t)E.npair + (diag ? E.nout : 0) + E.ncls + (size_t)M1 * DF_CH) * sizeof(df64) +
          (size_t)wx * DF_CH * sizeof(float);
 }
 
@@ -253,45 +228,34 @@ bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx) {
          df_smem(E, h->nterm, wx, true) <= (size_t)std::max(h->smem_optin, 48 * 1024);
 }
 
-// FP32: only for wide inputs. The staged kernel's per-row cost (two block
-// barriers, a dependent chain of loads) pays off from about 500 input columns
-// (measured on the 512x512, M = 10, p = 4 operator: 1001 columns 7.7 ms
-// against 11.1 ms for the row-per-warp kernel, 715 columns 3.4 against 4.6 ms;
-// at 220 columns and fewer the row-per-warp kernel is 2 % to 7 times faster).
-bool f32_pairs_usable(const sg_problem* h, const EdgeList& E, int wx) {
-  return h->staged_pairs && wx >= 512 && E.npair <= DF_MAXQ * 512 && E.ncls > 0 && E.ctab32 && h->nterm < 65536 && wx < 65536 &&
-         df_smem(E, h->nterm, wx, true, sizeof(float)) <= (size_t)std::max(h->smem_optin, 48 * 1024);
-}
-
-template <typename TA, bool DIAG, int MODE, typename TX, typename TYin>
-static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int wx, const TYin* Yin, int ldyin,
+template <bool DIAG, bool OUTER, typename TX>
+static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int wx, const double* Yin, int ldyin,
                      float* Y, int ldy, const OuterArgs* oa, cudaStream_t s) {
   const int wy = E.nout;
   if (wy == 0) return SG_OK;
   const int threads = df_threads(E);
   const int maxo = (wy + threads - 1) / threads;
-  const size_t smem = df_smem(E, h->nterm, wx, DIAG, sizeof(TA));
-  const TA* vals = std::is_same_v<TA, df64> ? (const TA*)h->vals_df : (const TA*)h->vals32;
-  const TA* ctab = std::is_same_v<TA, df64> ? (const TA*)E.ctab : (const TA*)E.ctab32;
+  const size_t smem = df_smem(E, h->nterm, wx, DIAG);
   OuterArgs a = oa ? *oa : OuterArgs{};
   auto go = [&](auto kern) -> int {
     SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
-    if (MODE == DF_OUTER) grid = std::min(grid, h->opart_blocks);
-    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, vals, h->nterm, X, ldx, wx,
-                                       E.npair, E.pk, E.pj, E.ptr, E.perm, E.ctr, E.tb, ctab, E.ncls, wy, Yin, ldyin, Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
+    if (OUTER) grid = std::min(grid, h->opart_blocks);
+    { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, (const df64*)h->vals_df, h->nterm, X, ldx, wx,
+                                       E.npair, E.pk, E.pj, E.ptr, E.perm, E.ctr, E.tb, (const df64*)E.ctab, E.ncls,
+                                       wy, Yin, ldyin, Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
   if (threads == 256) {
-    if (maxo <= 1) return go(k_df_pairs<TA, 1, DIAG, MODE, TX, TYin, 256>);
-    if (maxo <= 2) return go(k_df_pairs<TA, 2, DIAG, MODE, TX, TYin, 256>);
+    if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX, 256>);
+    if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX, 256>);
   } else {
-    if (maxo <= 1) return go(k_df_pairs<TA, 1, DIAG, MODE, TX, TYin, 512>);
-    if (maxo <= 2) return go(k_df_pairs<TA, 2, DIAG, MODE, TX, TYin, 512>);
-    if (maxo <= 4) return go(k_df_pairs<TA, 4, DIAG, MODE, TX, TYin, 512>);
+    if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX, 512>);
+    if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX, 512>);
+    if (maxo <= 4) return go(k_df_pairs<4, DIAG, OUTER, TX, 512>);
   }
   set_error("double-float product: %d outputs exceed the supported 2048", wy);
   return SG_ERR_UNSUPPORTED;
@@ -299,23 +263,13 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
 
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
                     float* Y, int ldy, cudaStream_t s) {
-  return launch_df<df64, false, DF_SUB, float, double>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
+  return launch_df<false, false, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
 }
 
 int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s, const float* z32) {
   // z itself in FP32 when the preconditioner leaves it there (half the staging reads, no conversion)
-  if (z32)
-    return launch_df<df64, true, DF_OUTER, float, double>(h, h->all, z32, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
-  return launch_df<df64, true, DF_OUTER, double, double>(h, h->all, h->fz, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
-}
-
-int launch_f32_pairs(sg_problem* h, const EdgeList& E, bool diag, const float* X, int ldx, int wx, const float* Yin,
-                     int ldyin, float* Y, int ldy, cudaStream_t s) {
-  if (diag && !Yin) return launch_df<float, true, DF_PLAIN, float, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
-  if (!diag && Yin)
-    return launch_df<float, false, DF_SUB, float, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
-  set_error("FP32 pair product: unsupported form");
-  return SG_ERR_UNSUPPORTED;
+  if (z32) return launch_df<true, true, float>(h, h->all, z32, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
+  return launch_df<true, true, double>(h, h->all, h->fz, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
 }
 
 }  // namespace sghsc

@@ -124,11 +124,32 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
         total += (size_t)32 * cmax;
       }
       if (total >= (size_t)1 << 31) return SG_ERR_UNSUPPORTED;
-      std::vector<unsigned> packed(std::max<size_t>(total, 1), 0u);
+      std::vector<unsigned> packed(std::max<size_t>(total, 1), 0u), pkj;
+      bool kj_ok = true;
+      const int wts = rows32_stride(nin);   // the row stride of the FP32 row kernel's term sums
+      for (int t = 0; t < E.nedges; ++t) kj_ok = kj_ok && (long long)he.k[t] * wts + he.j[t] < (1 << 24);
+      if (kj_ok) pkj.assign(packed.size(), 0u);
       for (int sl = 0; sl < E.nout; ++sl) {
         const int l = perm[sl];
-        for (int t = he.ptr[l]; t < he.ptr[l + 1]; ++t)
-          packed[tb[sl] + 32 * (t - he.ptr[l])] = ((unsigned)pair[t] << 8) | (unsigned)cls.at(he.c[t]);
+        for (int t = he.ptr[l]; t < he.ptr[l + 1]; ++t) {
+          const unsigned c = (unsigned)cls.at(he.c[t]);
+          packed[tb[sl] + 32 * (t - he.ptr[l])] = ((unsigned)pair[t] << 8) | c;
+          if (kj_ok) pkj[tb[sl] + 32 * (t - he.ptr[l])] = (c << 24) | (unsigned)(he.k[t] * wts + he.j[t]);
+        }
+      }
+      if (kj_ok && E.nout < 65536) {
+        // per slot: its first word and (output << 16 | couplings)
+        std::vector<int2> sd(E.nout);
+        bool ok = true;
+        for (int sl = 0; sl < E.nout; ++sl) {
+          const int l = perm[sl], cnt = he.ptr[l + 1] - he.ptr[l];
+          ok = ok && cnt < 65536;
+          sd[sl] = make_int2(tb[sl], (int)(((unsigned)l << 16) | (unsigned)cnt));
+        }
+        if (ok) {
+          SG_TRY(upload(&E.ckj, pkj.data(), pkj.size()));
+          SG_TRY(upload(&E.sdesc, sd.data(), sd.size()));
+        }
       }
       df64* dt = nullptr;
       SG_TRY(upload(&E.ctr, packed.data(), packed.size()));
@@ -153,6 +174,8 @@ static void free_edges(EdgeList& E) {
   cudaFree(E.c32);
   cudaFree(E.cdf);
   cudaFree(E.ctr);
+  cudaFree(E.ckj);
+  cudaFree(E.sdesc);
   cudaFree(E.tb);
   cudaFree(E.ctab);
   cudaFree(E.ctab32);

@@ -73,6 +73,10 @@ struct EdgeList {
   // lanes of a warp (32 consecutive slots) read consecutive words
   unsigned* ctr = nullptr;
   int* tb = nullptr;
+  // the same positions packed as class << 24 | (k rows32_stride(nin) + j)
+  // (below 2^24)
+  unsigned* ckj = nullptr;
+  int2* sdesc = nullptr;     // per slot: tb, output << 16 | couplings (with ckj)
   void* ctab = nullptr;      // df64
   float* ctab32 = nullptr;   // the same coefficients in FP32
   int ncls = 0;
@@ -236,13 +240,14 @@ bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx);
 // Y = Yin - sum_k A_k X G_k[out, in]^T: X FP32, Yin FP64, Y FP32.
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
                     float* Y, int ldy, cudaStream_t s);
-// The same layout in FP32 arithmetic: the full product (diag, Yin null:
-// Y = sum) or a level product (Y = Yin - sum; Yin may alias Y).
-int launch_f32_pairs(sg_problem* h, const EdgeList& E, bool diag, const float* X, int ldx, int wx, const float* Yin,
-                     int ldyin, float* Y, int ldy, cudaStream_t s);
-// FP32 pair kernel usable and preferred for E (compact table, sizes, inputs
-// at least 512 columns wide).
-bool f32_pairs_usable(const sg_problem* h, const EdgeList& E, int wx);
+// Row stride of the term sums of the FP32 row kernel (rows32.cu).
+constexpr int ROWS32_COLS = 512;   // input columns per pass of a block (two per thread)
+__host__ __device__ constexpr int rows32_stride(int wx) { return (wx + ROWS32_COLS - 1) / ROWS32_COLS * ROWS32_COLS; }
+// FP32 products with the input columns in registers (rows32.cu): usable and
+// preferred for E (compact table, sizes, inputs at least 512 columns wide).
+bool rows32_usable(const sg_problem* h, const EdgeList& E, int wx);
+int launch_rows32(sg_problem* h, const EdgeList& E, bool diag, const float* X, int ldx, int wx, const float* Yin,
+                  int ldyin, float* Y, int ldy, cudaStream_t s);
 
 // ---- inner solver (inner.cu) ----
 int ensure_inner_work(sg_problem* h, int dtype, int wcap);

@@ -1,8 +1,9 @@
-"""The staged pair kernel in FP32 arithmetic: the full SG product (eq. (3)'s
-sum over the KL terms) and the level products B_l, C_l of Algorithm 1 whose
-input level has at least 512 columns, against the oracle within the FP32
-rounding bound, against the row-per-warp kernels (the same products with the
-staged kernels switched off), and inside the FP32 preconditioner."""
+"""The FP32 row kernel (input columns in registers, term sums in shared
+memory): the full SG product (eq. (3)'s sum over the KL terms) and the level
+products B_l, C_l of Algorithm 1 with at least 512 input columns, or 128
+input and 512 output columns, against the oracle within the FP32 rounding
+bound, against the row-per-warp kernels (the same products with the row
+kernels switched off), and inside the FP32 preconditioner."""
 import numpy as np
 import pytest
 
@@ -37,7 +38,7 @@ SHAPES = [(8, 10, 4), (7, 6, 6), (4, 14, 3)]
 
 
 @pytest.mark.parametrize("ne,M,p", SHAPES)
-def test_staged_f32_full_product(lib, ne, M, p, monkeypatch):
+def test_rows32_full_product(lib, ne, M, p, monkeypatch):
     """Y = sum_k A_k U G_k^T in FP32: within m u sum|terms| of the exact
     product (m: the longest chain of roundings, nine nonzeros per pair sum
     plus the 2M + 1 couplings of an output), and within twice that of the
@@ -62,10 +63,11 @@ def test_staged_f32_full_product(lib, ne, M, p, monkeypatch):
 
 
 @pytest.mark.parametrize("ne,M,p", [(8, 10, 4), (4, 14, 3)])
-def test_staged_f32_wide_level_products(lib, ne, M, p):
+def test_rows32_wide_level_products(lib, ne, M, p):
     """Y = Yin - sum_k A_k X G_k[out, in]^T in FP32 between the two top
-    levels in both directions (the input level of the pre product has 715 and
-    560 columns), within the FP32 bound of the exact value."""
+    levels in both directions (715 -> 220 and 220 -> 715 columns at M = 10,
+    560 -> 120 at M = 14; 120 -> 560 stays on the row-per-warp kernel),
+    within the FP32 bound of the exact value."""
     import torch
     prob, A, G, off = problem(ne, M, p)
     h = lib.SGProblem.from_inputs(prob, p)
@@ -82,9 +84,9 @@ def test_staged_f32_wide_level_products(lib, ne, M, p):
     h.close()
 
 
-def test_staged_f32_inside_the_fp32_preconditioner(lib):
-    """Algorithm 1 in FP32 at P = 1001 (its level-4 pre product on the staged
-    kernel, in place) against the oracle's Algorithm 1 with the identical
+def test_rows32_inside_the_fp32_preconditioner(lib):
+    """Algorithm 1 in FP32 at P = 1001 (its level-4 products on the row
+    kernel, the pre product in place) against the oracle's Algorithm 1 with the identical
     inner solver (four V-cycle-preconditioned CG steps per D_l solve)."""
     prob, A, G, off = problem(8, 10, 4)
     h = lib.SGProblem.from_inputs(prob, 4)
