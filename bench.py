@@ -68,6 +68,19 @@ def _peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of that launch
 # (L2 flushed before it, as before each timed launch here).
 K1_TRAFFIC = {"cfg2": 35833856 + 119040}
+# DRAM bytes of one double-float SG-product launch (sg_apply SG_F32_ACCDF64):
+# dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture on the 255^2
+# grid of the same operator (444059136 + 475183872 bytes, L2 flushed before
+# the launch), scaled by the rows to the 511^2 grid (x 261121 / 65025; the
+# traffic is per row: the row's values, its neighbour rows of U from L2, its
+# row of Y).
+DF_TRAFFIC = {"cfg5": int((444059136 + 475183872) * 261121 / 65025)}
+# FP32 operations of one double-float multiply-add a * x + s (a double-float,
+# x FP32): the exact product (FMUL, FFMA for its error, FFMA for a.lo x) and
+# the two-sum accumulation (six FADD for the hi parts and their error, two
+# for the lo parts). The double-float peak is the measured FP32 FMA-chain rate
+# (two flops per FMA) divided by this count.
+DF_OPS_PER_MAC = 11
 
 
 class ClockSampler:
@@ -129,6 +142,13 @@ def sg_matvec_bytes(n, nnz, M, P, es):
     """Algorithmic bytes of one SG product: pattern once, M+1 values per
     nonzero, U read once, Y written once."""
     return 4 * (n + 1) + 4 * nnz + es * (M + 1) * nnz + 2 * es * n * P
+
+
+def sg_matvec_bytes_df(n, nnz, M, P):
+    """Algorithmic bytes of the double-float product: pattern once, M+1
+    double-float values (8 bytes) per nonzero, FP32 U read once, FP64 Y
+    written once."""
+    return 4 * (n + 1) + 4 * nnz + 8 * (M + 1) * nnz + 4 * n * P + 8 * n * P
 
 
 def _comb(a, b):
@@ -211,25 +231,28 @@ def run_ours(args, rank, world, dev):
         return ts, stats, launches
 
     if args.profile == "apply":
-        # the SG product alone, FP64 then FP32 (warm-up + timed launches each)
+        # the SG product alone, FP64, FP32, then FP32 in / double-float sums /
+        # FP64 out (warm-up + timed launches each)
         out = {"profile": "apply", "workload": cfg["name"], "n": n, "P": P, "nnz": nnz}
-        for name, dt, es in (("fp64", torch.float64, 8), ("fp32", torch.float32, 4)):
+        for name, dt, es, df in (("fp64", torch.float64, 8, False), ("fp32", torch.float32, 4, False),
+                                 ("df64", torch.float32, 0, True)):
             Ut = torch.tensor(S.random_block(n, P, seed=1205), dtype=dt, device=dev)
-            Yt = torch.empty_like(Ut)
+            Yt = torch.empty(Ut.shape, dtype=torch.float64 if df else dt, device=dev)
             for _ in range(args.warmup):
-                L.sg_apply(h, Ut, Yt)
+                L.sg_apply(h, Ut, Yt, df64=df)
             ts = []
             for _ in range(args.steps):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                L.sg_apply(h, Ut, Yt)
+                L.sg_apply(h, Ut, Yt, df64=df)
                 e1.record(stream)
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
             k = float(np.mean(ts))
-            b, fl = sg_matvec_bytes(n, nnz, M, P, es), sg_matvec_flops(n, nnz, M, p, P, n_m)
+            b = sg_matvec_bytes_df(n, nnz, M, P) if df else sg_matvec_bytes(n, nnz, M, P, es)
+            fl = sg_matvec_flops(n, nnz, M, p, P, n_m)
             out[name] = {"ms": k, "GB_s": b / k / 1e6, "TFLOP_s": fl / k / 1e9, "bytes": b, "flops": fl}
             del Ut, Yt
         return out
@@ -321,18 +344,18 @@ def run_ours(args, rank, world, dev):
     del h_e
 
     # SG matvec roofline: K1 timed alone with events on the launching stream
-    def time_apply(dtype, reps=10):
+    def time_apply(dtype, reps=10, df64=False):
         Ut = torch.tensor(S.random_block(n, P, seed=1205), dtype=dtype, device=dev)
-        Yt = torch.empty_like(Ut)
+        Yt = torch.empty(Ut.shape, dtype=torch.float64 if df64 else dtype, device=dev)
         for _ in range(3):
-            L.sg_apply(h, Ut, Yt)
+            L.sg_apply(h, Ut, Yt, df64=df64)
         times = []
         for _ in range(reps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            L.sg_apply(h, Ut, Yt)
+            L.sg_apply(h, Ut, Yt, df64=df64)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -341,27 +364,37 @@ def run_ours(args, rank, world, dev):
 
     k1_64 = time_apply(torch.float64)
     k1_32 = time_apply(torch.float32)
+    k1_df = time_apply(torch.float32, df64=True)
     hbm, hbm_src = _peaks()
     fp64_peak = L.sg_measure_alu_peak(L.SG_F64) / 1e12      # TFLOP/s, timed alone (burst)
     fp32_peak = L.sg_measure_alu_peak(L.SG_F32) / 1e12
     b64 = sg_matvec_bytes(n, nnz, M, P, 8)
     b32 = sg_matvec_bytes(n, nnz, M, P, 4)
+    bdf = sg_matvec_bytes_df(n, nnz, M, P)
     fl = sg_matvec_flops(n, nnz, M, p, P, n_m)
+    df_peak = fp32_peak / DF_OPS_PER_MAC
     matvec = {
         "fp64": {"ms": k1_64, "GB_s": b64 / k1_64 / 1e6, "TFLOP_s": fl / k1_64 / 1e9, "bytes": b64, "flops": fl,
                  "frac_fp64_alu_measured": fl / k1_64 / 1e9 / fp64_peak, "frac_hbm": b64 / k1_64 / 1e6 / hbm},
         "fp32": {"ms": k1_32, "GB_s": b32 / k1_32 / 1e6, "TFLOP_s": fl / k1_32 / 1e9, "bytes": b32, "flops": fl,
                  "frac_fp32_alu_measured": fl / k1_32 / 1e9 / fp32_peak, "frac_hbm": b32 / k1_32 / 1e6 / hbm},
+        "df64": {"ms": k1_df, "GB_s": bdf / k1_df / 1e6, "TFLOP_s": fl / k1_df / 1e9, "bytes": bdf, "flops": fl,
+                 "frac_df64_alu": fl / k1_df / 1e9 / df_peak, "frac_hbm": bdf / k1_df / 1e6 / hbm,
+                 "note": "FP32 U, double-float sums, FP64 Y: the product of the outer CG step (k_df_pairs)"},
         "hbm_peak_GB_s": hbm, "hbm_peak_source": hbm_src,
         "fp64_alu_peak_TFLOP_s": fp64_peak, "fp32_alu_peak_TFLOP_s": fp32_peak,
+        "df64_alu_peak_TFLOP_s": df_peak,
     }
-    roofline = {"kernel": "k_block_matvec<double> (K1 FP64 SG product, the arithmetic of the outer CG's fused "
-                          "product k_outer_matvec)", "bound": "alu",
-                "achieved": fl / k1_64 / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (fl / k1_64 / 1e9) / fp64_peak, "traffic": K1_TRAFFIC.get(args.workload),
-                "algorithmic_bytes": b64, "algorithmic_flops": fl,
-                "peak_source": "measured: FP64 FMA-chain kernel (sg_measure_alu_peak) on this GPU, timed alone, "
-                               "of measured"}
+    # the dominant kernel of the timed solve: the double-float SG product of
+    # the outer CG step (its product timed alone through sg_apply, the same
+    # kernel body with a plain epilogue)
+    roofline = {"kernel": "k_df_pairs (double-float SG product of the outer CG step; timed alone as sg_apply "
+                          "SG_F32_ACCDF64)", "bound": "alu",
+                "achieved": fl / k1_df / 1e9, "peak": df_peak, "unit": "TFLOP/s",
+                "frac": (fl / k1_df / 1e9) / df_peak, "traffic": DF_TRAFFIC.get(args.workload),
+                "algorithmic_bytes": bdf, "algorithmic_flops": fl,
+                "peak_source": f"measured FP32 FMA-chain rate (sg_measure_alu_peak, timed alone, of measured) / "
+                               f"{DF_OPS_PER_MAC} FP32 operations per double-float multiply-add"}
 
 
     out = {

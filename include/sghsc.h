@@ -210,7 +210,10 @@ int sg_chaos_table(const sg_problem* h, int* alpha, int* level_offsets);
 /* sg_apply -- MAT-VEC of eq. (global-system) (the remark after
  * eq. (global-matrix-block)): Y = sum_k A_k U G_k^T.
  * U, Y: device n x P row-major of element type dtype (SG_F64 or SG_F32);
- * Y must not alias U. */
+ * or dtype SG_F32_ACCDF64: U FP32, Y FP64, the sums in double-float
+ * arithmetic (FP32 pairs: within about m 2^-46 of the sum of the magnitudes
+ * of the m terms of an entry) -- the product the mixed solver applies to the
+ * FP32 output of its preconditioner. Y must not alias U. */
 int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream);
 
 /* sg_level_apply -- one off-diagonal block product of the hierarchy

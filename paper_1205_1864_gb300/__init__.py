@@ -167,10 +167,18 @@ def sg_setup(ne_x, ne_y, M, p, rowptr, colidx, vals, mass=None, family=SG_LEGEND
     return SGProblem(ne_x, ne_y, M, p, rowptr, colidx, vals, mass, family)
 
 
-def sg_apply(h: SGProblem, U: torch.Tensor, Y: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Y = sum_k A_k U G_k^T (K1)."""
-    Y = torch.empty_like(U) if Y is None else Y
-    check(_lib.LIB.sg_apply(h.h, _ptr(U), _ptr(Y), _DT[U.dtype], _stream()), "sg_apply")
+def sg_apply(h: SGProblem, U: torch.Tensor, Y: Optional[torch.Tensor] = None, df64: bool = False) -> torch.Tensor:
+    """Y = sum_k A_k U G_k^T (K1). ``df64``: FP32 ``U``, sums in double-float
+    arithmetic, FP64 ``Y`` (``SG_F32_ACCDF64``)."""
+    if df64:
+        if U.dtype != torch.float32:
+            raise ValueError("sg_apply: df64 takes an FP32 U")
+        Y = torch.empty(U.shape, dtype=torch.float64, device=U.device) if Y is None else Y
+        code = _lib.SG_F32_ACCDF64
+    else:
+        Y = torch.empty_like(U) if Y is None else Y
+        code = _DT[U.dtype]
+    check(_lib.LIB.sg_apply(h.h, _ptr(U), _ptr(Y), code, _stream()), "sg_apply")
     return Y
 
 

@@ -86,23 +86,28 @@ __device__ __forceinline__ df64 df_dot9(const df64* __restrict__ a, const float*
   return s;
 }
 
-// OUTER = false: level product, Y = Yin - sum (Yin FP64, Y FP32), the
-// difference in double-float, rounded once to FP32. OUTER = true: the outer
-// CG step (as k_outer_matvec): p_new = z + beta p_old, q = A z + beta q_old,
-// p_new . q and alpha, with X = z (FP32, or FP64 storage of FP32 values).
+enum { DF_SUB = 0, DF_PLAIN = 1, DF_OUTER = 2 };
+
+// MODE DF_SUB: a level product, Y = Yin - sum (Yin FP64, Y FP32), the
+// difference in double-float, rounded once to FP32. DF_PLAIN: the full
+// product, Y = sum (FP64, one add of the pair per output). DF_OUTER: the
+// outer CG step (as k_outer_matvec): p_new = z + beta p_old, q = A z + beta
+// q_old, p_new . q and alpha, with X = z (FP32, or FP64 storage of FP32
+// values).
 // Shared memory: pair sums Ss[npair], diagonal terms Ds[wy] (DIAG, by output
 // column in natural order, so the lanes of a warp read consecutive inputs),
 // the coefficient classes Ctab[ncls] (loaded once per block), then the
 // staged chunk Vt, Xt. The packed couplings stay in global memory, read
 // coalesced through L1 (in shared memory they held a block to one per SM at
 // P = 1001).
-template <int MAXO, bool DIAG, bool OUTER, typename TX, int LB>
+template <int MAXO, bool DIAG, int MODE, typename TX, typename TY, int LB>
 __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const df64* __restrict__ vals, int M1,
     const TX* __restrict__ X, int ldx, int wx, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
     const int* __restrict__ eptr, const int* __restrict__ eperm, const unsigned* __restrict__ ctr,
     const int* __restrict__ etb, const df64* __restrict__ ctab, int ncls, int wy, const double* __restrict__ Yin,
-    int ldyin, float* __restrict__ Y, int ldy, double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
+    int ldyin, TY* __restrict__ Y, int ldy, double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
+  constexpr bool OUTER = MODE == DF_OUTER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   df64* Ss = reinterpret_cast<df64*>(smem_raw);
   df64* Ds = Ss + npair;
@@ -188,6 +193,8 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
         pnew[g] = pv;
         q[g] = qv;
         dot += pv * qv;
+      } else if constexpr (MODE == DF_PLAIN) {
+        Y[(size_t)r * ldy + l] = f2d_bits(acc.hi) + f2d_bits(acc.lo);
       } else {
         // Yin - sum in double-float, rounded once to FP32
         df64 v = df_from_double(Yin[(size_t)r * ldyin + l]);
@@ -228,9 +235,9 @@ bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx) {
          df_smem(E, h->nterm, wx, true) <= (size_t)std::max(h->smem_optin, 48 * 1024);
 }
 
-template <bool DIAG, bool OUTER, typename TX>
+template <bool DIAG, int MODE, typename TX, typename TY>
 static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int wx, const double* Yin, int ldyin,
-                     float* Y, int ldy, const OuterArgs* oa, cudaStream_t s) {
+                     TY* Y, int ldy, const OuterArgs* oa, cudaStream_t s) {
   const int wy = E.nout;
   if (wy == 0) return SG_OK;
   const int threads = df_threads(E);
@@ -242,7 +249,7 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
-    if (OUTER) grid = std::min(grid, h->opart_blocks);
+    if (MODE == DF_OUTER) grid = std::min(grid, h->opart_blocks);
     { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, (const df64*)h->vals_df, h->nterm, X, ldx, wx,
                                        E.npair, E.pk, E.pj, E.ptr, E.perm, E.ctr, E.tb, (const df64*)E.ctab, E.ncls,
                                        wy, Yin, ldyin, Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
@@ -250,12 +257,12 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
     return SG_OK;
   };
   if (threads == 256) {
-    if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX, 256>);
-    if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX, 256>);
+    if (maxo <= 1) return go(k_df_pairs<1, DIAG, MODE, TX, TY, 256>);
+    if (maxo <= 2) return go(k_df_pairs<2, DIAG, MODE, TX, TY, 256>);
   } else {
-    if (maxo <= 1) return go(k_df_pairs<1, DIAG, OUTER, TX, 512>);
-    if (maxo <= 2) return go(k_df_pairs<2, DIAG, OUTER, TX, 512>);
-    if (maxo <= 4) return go(k_df_pairs<4, DIAG, OUTER, TX, 512>);
+    if (maxo <= 1) return go(k_df_pairs<1, DIAG, MODE, TX, TY, 512>);
+    if (maxo <= 2) return go(k_df_pairs<2, DIAG, MODE, TX, TY, 512>);
+    if (maxo <= 4) return go(k_df_pairs<4, DIAG, MODE, TX, TY, 512>);
   }
   set_error("double-float product: %d outputs exceed the supported 2048", wy);
   return SG_ERR_UNSUPPORTED;
@@ -263,13 +270,18 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
 
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
                     float* Y, int ldy, cudaStream_t s) {
-  return launch_df<false, false, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
+  return launch_df<false, DF_SUB, float, float>(h, E, X, ldx, wx, Yin, ldyin, Y, ldy, nullptr, s);
 }
 
 int launch_df_outer(sg_problem* h, const OuterArgs& a, cudaStream_t s, const float* z32) {
   // z itself in FP32 when the preconditioner leaves it there (half the staging reads, no conversion)
-  if (z32) return launch_df<true, true, float>(h, h->all, z32, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
-  return launch_df<true, true, double>(h, h->all, h->fz, h->P, h->P, nullptr, 0, nullptr, 0, &a, s);
+  float* none = nullptr;
+  if (z32) return launch_df<true, DF_OUTER, float, float>(h, h->all, z32, h->P, h->P, nullptr, 0, none, 0, &a, s);
+  return launch_df<true, DF_OUTER, double, float>(h, h->all, h->fz, h->P, h->P, nullptr, 0, none, 0, &a, s);
+}
+
+int launch_df_apply(sg_problem* h, const float* U, double* Y, cudaStream_t s) {
+  return launch_df<true, DF_PLAIN, float, double>(h, h->all, U, h->P, h->P, nullptr, 0, Y, h->P, nullptr, s);
 }
 
 }  // namespace sghsc

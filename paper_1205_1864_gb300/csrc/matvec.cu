@@ -447,6 +447,12 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
     return launch_t<float, double, double, float, false>(h, (const float*)X, ldx, wx, E, (const double*)Yin, ldyin,
                                                          alpha, beta, (float*)Y, ldy, s);
   }
+  if (tin == SG_F32 && tacc == ACC_DF64 && tout == SG_F64 && diag && !Yin) {
+    if (alpha == 1.0 && df_pairs_usable(h, E, wx) && &E == &h->all && wx == h->P && ldx == h->P && ldy == h->P)
+      return launch_df_apply(h, (const float*)X, (double*)Y, s);
+    return launch_t<float, df64, double, double, true>(h, (const float*)X, ldx, wx, E, nullptr, 0, alpha, beta,
+                                                       (double*)Y, ldy, s);
+  }
   if (tin == SG_F32 && tacc == ACC_DF64 && tb == SG_F64 && tout == SG_F32 && !diag) {
     if (Yin && alpha == -1.0 && beta == 1.0 && df_pairs_usable(h, E, wx))
       return launch_df_level(h, E, (const float*)X, ldx, wx, (const double*)Yin, ldyin, (float*)Y, ldy, s);
@@ -511,10 +517,13 @@ extern "C" {
 
 int sg_apply(sg_problem* h, const void* U, void* Y, int dtype, void* stream) {
   set_error("");
-  if (!h || !U || !Y || (dtype != SG_F64 && dtype != SG_F32) || U == Y) {
+  if (!h || !U || !Y || (dtype != SG_F64 && dtype != SG_F32 && dtype != SG_F32_ACCDF64) || U == Y) {
     set_error("sg_apply: invalid arguments");
     return SG_ERR_INVALID_ARG;
   }
+  if (dtype == SG_F32_ACCDF64)   // FP32 U, FP64-accurate sums, FP64 Y
+    return launch_block_matvec(h, SG_F32, ACC_DF64, SG_F64, SG_F64, U, h->P, h->P, h->all, true, nullptr, 0, 1.0, 0.0,
+                               Y, h->P, (cudaStream_t)stream);
   return launch_block_matvec(h, dtype, dtype, dtype, dtype, U, h->P, h->P, h->all, true, nullptr, 0, 1.0, 0.0, Y,
                              h->P, (cudaStream_t)stream);
 }

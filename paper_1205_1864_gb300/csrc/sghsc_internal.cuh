@@ -237,6 +237,8 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
 // ---- double-float pair-form products (dfprod.cu) ----
 // The input block holds FP32 values; usable when the pairs and the staging fit.
 bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx);
+// Y = sum_k A_k U G_k^T: U FP32, double-float sums, Y FP64.
+int launch_df_apply(sg_problem* h, const float* U, double* Y, cudaStream_t s);
 // Y = Yin - sum_k A_k X G_k[out, in]^T: X FP32, Yin FP64, Y FP32.
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
                     float* Y, int ldy, cudaStream_t s);

@@ -54,6 +54,37 @@ def test_df64_level_products_against_oracle(lib, ne, M, p):
         assert np.mean(Y == Y64) > 0.99
 
 
+@pytest.mark.parametrize("ne,M,p,gpc,generic", [(16, 3, 3, False, False), (8, 10, 4, False, False),
+                                                (7, 6, 6, False, False), (8, 10, 4, False, True),
+                                                (8, 3, 2, True, False)])
+def test_df64_full_product_against_oracle(lib, ne, M, p, gpc, generic, monkeypatch):
+    """Y = sum_k A_k U G_k^T with FP32 U, double-float sums, FP64 Y: within
+    m 2^-46 sum|terms| (m the products of an entry) of the exact product, on
+    the staged pair kernel (P = 84, 1001, 924, and the gPC coefficient's
+    dense coupling) and on the row-per-warp kernel (staged kernels off)."""
+    import torch
+    if generic:
+        monkeypatch.setenv("SGHSC_GENERIC_PRODUCTS", "1")
+    if gpc:
+        from tests.test_gpu_lognormal import _case
+        prob, A, G, off = _case(ne, M, p)
+    else:
+        prob, A, G, off = problem(ne, M, p)
+    h = lib.SGProblem.from_inputs(prob, p)
+    rng = np.random.default_rng(3)
+    U = (S.random_block(prob.n, h.P, seed=4) * 10.0 ** rng.integers(-3, 4, size=h.P)).astype(np.float32)
+    Y = _np(lib.sg_apply(h, _t(U, torch.float32), df64=True))
+    U = U.astype(np.float64)
+    exact = so.sg_apply(A, G, U)
+    bound = so.sg_apply([abs(a) for a in A], [abs(g) for g in G], np.abs(U))
+    per_out = max(int(sum((g != 0).sum(axis=1).max() for g in G)), 1)
+    m = 9 * (per_out + 1)
+    assert np.all(np.abs(Y - exact) <= m * 2.0 ** -46 * bound + 2.0 ** -52 * np.abs(exact) + 1e-300)
+    with pytest.raises(ValueError):
+        lib.sg_apply(h, _t(U), df64=True)
+    h.close()
+
+
 @pytest.mark.parametrize("precond", ["hsc", "bgs"])
 def test_df64_mixed_solve_matches_oracle(lib, precond):
     """Mixed solves with the double-float outer and top-level products to
