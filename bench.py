@@ -47,12 +47,28 @@ METRIC = "time-to-solve at rel.res 1e-8, HSC-PCG vs mean-based PCG; SG matvec HB
 WORKLOADS = {
     "cfg2": dict(name="cfg2_mixed_128x128_M6_p4", hsc_iterations=8, **S.CONFIGS["cfg2_mixed_128x128_M6_p4"]),
     "cfg1": dict(name="cfg1_fp64_16x16_M3_p3", hsc_iterations=6, **S.CONFIGS["cfg1_fp64_16x16_M3_p3"]),
-    "cfg4": dict(name="cfg4_64x64_M4_p3", hsc_iterations=6, **S.CONFIGS["cfg4_grad_64x64_M4_p3"]),
+    "cfg4": dict(name="cfg4_64x64_M4_p3", hsc_iterations=6, grad=True, **S.CONFIGS["cfg4_grad_64x64_M4_p3"]),
     "cfg5": dict(name="cfg5_large_512x512_M10_p4", hsc_iterations=7, **S.CONFIGS["cfg5_large_512x512_M10_p4"]),
     # 64 independent systems (mesh, M, p, sigma, L drawn per system), one graph launch
     "cfg3": dict(name="cfg3_batch64_mixed", batch=True, count=64, seed=1864),
 }
 L2_FLUSH_BYTES = 256 << 20
+
+
+L2_NOTE = "flushed between timed steps (256 MiB write, outside the events)"
+
+
+def workload_config(cfg, world):
+    """The config object of a workload's line, the same for both arms."""
+    if cfg.get("batch"):
+        return {"workload": cfg["name"], "systems": cfg["count"], "draw_seed": cfg["seed"], "tol": 1e-8,
+                "inner_tol": 1e-2, "l2": L2_NOTE,
+                "parallelism": f"systems split over {world} ranks" if world > 1 else "single GPU"}
+    P = math.comb(cfg["M"] + cfg["p"], cfg["p"])
+    n = (cfg["ne"] - 1) ** 2
+    return {"workload": cfg["name"], "ne": cfg["ne"], "M": cfg["M"], "p": cfg["p"], "P": P, "n": n,
+            "unknowns": n * P, "sigma": cfg["sigma"], "corr_len": cfg["corr_len"], "inner_tol": 1e-2, "tol": 1e-8,
+            "l2": L2_NOTE, "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def _peaks():
@@ -401,12 +417,8 @@ def run_ours(args, rank, world, dev):
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 outer CG, df64 (FP32-pair) outer/top-level products, f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
-        "config": {"workload": cfg["name"], "ne": cfg["ne"], "M": M, "p": p, "P": P, "n": n,
-                   "unknowns": n * P, "sigma": cfg["sigma"], "corr_len": cfg["corr_len"], "inner_tol": 1e-2,
-                   "tol": 1e-8, "l2": "flushed between timed steps (256 MiB write, outside the events)",
-                   "autotuned_threads_f64_f32": list(tuned),
-                   "autotuned_pair_form_f64_f32_outer": list(forms),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(cfg, world),
+        "autotune": {"threads_f64_f32": list(tuned), "pair_form_f64_f32_outer": list(forms)},
         "hsc": {"ms": ms, "iterations": st_h.iterations, "true_rel_res": st_true.true_rel_res,
                 "oracle_rel_res": oracle_res, "arithmetic": "FP32 inner solves and level products < p; outer CG "
                 "FP64; outer SG product and level-p products in double-float (df64) on the FP32 units",
@@ -434,9 +446,55 @@ def run_ours(args, rank, world, dev):
         "clocks": clk.summary(),
         "setup_s": setup_s,
     }
+    if cfg.get("grad"):
+        out["grad_batch"] = run_grad_batch(cfg, args, dev, flush, hsc_opts)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, iterations=st_h.iterations)
     return out
+
+
+def run_grad_batch(cfg, args, dev, flush, opts):
+    """The gradient workload: Q and dQ/dtheta (theta = mean coefficient, sigma,
+    sqrt(lambda_k) scales) for 16 seeded parameter sets, the forward and the
+    adjoint solves of all sets batched on the device (SGGradBatch: one graph
+    launch each, then the K7 contraction per set), against the same sets one
+    after another through the autograd Function. Wall-clock ms per batch with
+    the device synchronised on both sides (the call returns results to the
+    host)."""
+    import paper_1205_1864_gb300 as L
+    import torch
+    count = 16
+    unit = S.make_unit_problem(cfg["ne"], cfg["M"], cfg["corr_len"])
+    base_s = S.theta_of(S.make_problem(cfg["ne"], cfg["M"], 1.0, cfg["corr_len"]))[2:]
+    sets = S.draw_grad_params(cfg["M"], count)
+    thetas = np.array([np.concatenate([[d["a_mean"], d["sigma"]], base_s * d["sqrt_lambda_scale"]]) for d in sets])
+    F = torch.tensor(S.make_rhs(unit, cfg["p"]), dtype=torch.float64, device=dev)
+    gb = L.SGGradBatch.from_inputs(unit, cfg["p"], count)
+    gb.autotune()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return ts
+
+    ts = timed(lambda: gb.value_and_grad(thetas, F, opts), args.steps, args.warmup)
+    Q, G = gb.value_and_grad(thetas, F, opts)
+    gb.close()
+    h = L.SGProblem.from_inputs(unit, cfg["p"])
+    L.sg_autotune(h)
+    ts_seq = timed(lambda: L.sg_qoi_value_and_grad_batch(h, thetas, F, opts), 1, 1)
+    h.close()
+    return {"sets": count, "params_per_set": cfg["M"] + 2, "ms": float(np.mean(ts)), "step_ms": ts,
+            "sequential_autograd_ms": ts_seq[0], "speedup_batch_vs_sequential": ts_seq[0] / float(np.mean(ts)),
+            "Q_range": [float(Q.min()), float(Q.max())], "grad_norm_max": float(G.abs().max())}
 
 
 def oracle_residual(prob, p, F, U):
@@ -585,11 +643,9 @@ def run_batch(args, rank, world, dev):
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
         "dtype": "f64 outer CG, df64 (FP32-pair) outer/top-level products, f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
-        "config": {"workload": cfg["name"], "systems": len(cfgs), "systems_this_rank": len(mine),
-                   "unknowns_this_rank": unknowns, "draw_seed": cfg["seed"], "tol": 1e-8, "inner_tol": 1e-2,
-                   "l2": "flushed between timed steps (256 MiB write, outside the events)",
-                   "parallelism": f"systems split over {world} ranks" if world > 1 else "single GPU"},
-        "batch": {"ms": ms, "step_ms": ts, "iterations": [s.iterations for s in st],
+        "config": workload_config(cfg, world),
+        "batch": {"ms": ms, "step_ms": ts, "systems_this_rank": len(mine), "unknowns_this_rank": unknowns,
+                  "iterations": [s.iterations for s in st],
                   "status": [s.status for s in st], "max_true_rel_res": max(s.true_rel_res for s in st_true),
                   "autotuned_threads_f64_f32": tuned, "sequential_ms": ms_seq,
                   "speedup_batch_vs_sequential": ms_seq / float(np.mean(ts))},
@@ -783,7 +839,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
-            "config": {"workload": cfg["name"]},
+            "config": workload_config(cfg, world),
             "cpu_baseline": {"value": v, "unit": "ms", "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -54,17 +54,24 @@ __device__ __forceinline__ df64 df_mul_f(const df64& a, float x) {
   return df64(p, e);
 }
 
+// Row strides of the staged chunk: a term's nine values padded to ten
+// double-float slots (80 bytes: five 16-byte loads), an input column's nine
+// values padded to twelve floats (48 bytes: three 16-byte loads; a warp's
+// eight-lane phases of consecutive columns then hit distinct bank groups).
+constexpr int DF_VS = 10;
+constexpr int DF_XS = 12;
+
 // Stage chunk cs..cs+nzc-1 (nzc <= DF_CH): values [k][e], inputs [j][e],
 // slots e >= nzc zero. The input rows go column position by column position
 // (no integer division), the loads of all slots of a position in flight
-// before their stores.
+// before their 16-byte stores.
 template <typename TX>
 __device__ __forceinline__ void df_stage(int cs, int nzc, int M1, const int* __restrict__ colidx,
                                          const df64* __restrict__ vals, const TX* __restrict__ X, int ldx, int wx,
                                          df64* Vt, float* Xt) {
   for (int k = threadIdx.x; k < M1; k += blockDim.x) {
 #pragma unroll
-    for (int e = 0; e < DF_CH; ++e) Vt[k * DF_CH + e] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : df64(0.f, 0.f);
+    for (int e = 0; e < DF_VS; ++e) Vt[k * DF_VS + e] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : df64(0.f, 0.f);
   }
   int col[DF_CH];
 #pragma unroll
@@ -73,16 +80,33 @@ __device__ __forceinline__ void df_stage(int cs, int nzc, int M1, const int* __r
     float v[DF_CH];
 #pragma unroll
     for (int e = 0; e < DF_CH; ++e) v[e] = col[e] >= 0 ? exact_float(X[(size_t)col[e] * ldx + j]) : 0.f;
-#pragma unroll
-    for (int e = 0; e < DF_CH; ++e) Xt[j * DF_CH + e] = v[e];
+    float4* xr = reinterpret_cast<float4*>(Xt + j * DF_XS);
+    xr[0] = make_float4(v[0], v[1], v[2], v[3]);
+    xr[1] = make_float4(v[4], v[5], v[6], v[7]);
+    xr[2] = make_float4(v[8], 0.f, 0.f, 0.f);
   }
 }
 
-// sum_e a[e] x[e] over the DF_CH slots (constant offsets)
+// sum_e a[e] x[e] over the DF_CH slots of one staged term row and one staged
+// input column, both read as 16-byte vectors
 __device__ __forceinline__ df64 df_dot9(const df64* __restrict__ a, const float* __restrict__ x) {
-  df64 s = df_mul_f(a[0], x[0]);
-#pragma unroll
-  for (int e = 1; e < DF_CH; ++e) s += df_mul_f(a[e], x[e]);
+  const float4* av = reinterpret_cast<const float4*>(a);   // two double-float values each
+  const float4* xv = reinterpret_cast<const float4*>(x);
+  const float4 x0 = xv[0], x1 = xv[1], x2 = xv[2];
+  float4 v = av[0];
+  df64 s = df_mul_f(df64(v.x, v.y), x0.x);
+  s += df_mul_f(df64(v.z, v.w), x0.y);
+  v = av[1];
+  s += df_mul_f(df64(v.x, v.y), x0.z);
+  s += df_mul_f(df64(v.z, v.w), x0.w);
+  v = av[2];
+  s += df_mul_f(df64(v.x, v.y), x1.x);
+  s += df_mul_f(df64(v.z, v.w), x1.y);
+  v = av[3];
+  s += df_mul_f(df64(v.x, v.y), x1.z);
+  s += df_mul_f(df64(v.z, v.w), x1.w);
+  v = av[4];
+  s += df_mul_f(df64(v.x, v.y), x2.x);
   return s;
 }
 
@@ -94,43 +118,35 @@ enum { DF_SUB = 0, DF_PLAIN = 1, DF_OUTER = 2 };
 // outer CG step (as k_outer_matvec): p_new = z + beta p_old, q = A z + beta
 // q_old, p_new . q and alpha, with X = z (FP32, or FP64 storage of FP32
 // values).
-// Shared memory: pair sums Ss[npair], diagonal terms Ds[wy] (DIAG, by output
-// column in natural order, so the lanes of a warp read consecutive inputs),
-// the coefficient classes Ctab[ncls] (loaded once per block), then the
-// staged chunk Vt, Xt. The packed couplings stay in global memory, read
-// coalesced through L1 (in shared memory they held a block to one per SM at
-// P = 1001).
-template <int MAXO, bool DIAG, int MODE, typename TX, typename TY, int LB>
+// Shared memory (16-byte aligned parts): pair sums Ss[npair], diagonal terms
+// Ds[wy] (DIAG, by output column in natural order, so the lanes of a warp
+// read consecutive inputs), the coefficient classes Ctab[ncls] (loaded once
+// per block), then the staged chunk Vt, Xt. The packed couplings stay in
+// global memory, read coalesced through L1 (in shared memory they held a
+// block to one per SM at P = 1001); each output slot's first word and count
+// come from a descriptor, so a thread takes any number of outputs.
+template <bool DIAG, int MODE, typename TX, typename TY, int LB>
 __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const df64* __restrict__ vals, int M1,
     const TX* __restrict__ X, int ldx, int wx, int npair, const int* __restrict__ pk, const int* __restrict__ pj,
-    const int* __restrict__ eptr, const int* __restrict__ eperm, const unsigned* __restrict__ ctr,
-    const int* __restrict__ etb, const df64* __restrict__ ctab, int ncls, int wy, const double* __restrict__ Yin,
-    int ldyin, TY* __restrict__ Y, int ldy, double* pA, double* pB, double* __restrict__ q, OuterArgs a) {
+    const unsigned* __restrict__ ctr, const int2* __restrict__ sdesc, const df64* __restrict__ ctab, int ncls, int wy,
+    const double* __restrict__ Yin, int ldyin, TY* __restrict__ Y, int ldy, double* pA, double* pB,
+    double* __restrict__ q, OuterArgs a) {
   constexpr bool OUTER = MODE == DF_OUTER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   df64* Ss = reinterpret_cast<df64*>(smem_raw);
-  df64* Ds = Ss + npair;
-  df64* Ctab = Ds + (DIAG ? wy : 0);
-  df64* Vt = Ctab + ncls;
-  float* Xt = reinterpret_cast<float*>(Vt + (size_t)M1 * DF_CH);
+  df64* Ds = Ss + ((npair + 1) & ~1);
+  df64* Ctab = Ds + (DIAG ? ((wy + 1) & ~1) : 0);
+  df64* Vt = Ctab + ((ncls + 1) & ~1);
+  float* Xt = reinterpret_cast<float*>(Vt + (size_t)M1 * DF_VS);
   for (int t = threadIdx.x; t < ncls; t += blockDim.x) Ctab[t] = ctab[t];
-  // this thread's pairs (consecutive threads: consecutive pairs) and outputs
-  unsigned qkj[DF_MAXQ];   // k << 16 | j
+  // this thread's pairs (consecutive threads: consecutive pairs), as the
+  // staged offsets of their term row and input column
+  unsigned qkj[DF_MAXQ];   // k DF_VS << 16 | j DF_XS
 #pragma unroll
   for (int i = 0; i < DF_MAXQ; ++i) {
     const int qi = threadIdx.x + i * blockDim.x;
-    qkj[i] = qi < npair ? ((unsigned)pk[qi] << 16) | (unsigned)pj[qi] : 0u;
-  }
-  // the couplings of this thread's outputs: slot-transposed in global memory
-  // (the table is the same for every block and row, so it stays in L1)
-  int lcol[MAXO], t0[MAXO], nc[MAXO];
-#pragma unroll
-  for (int i = 0; i < MAXO; ++i) {
-    const int slot = threadIdx.x + i * blockDim.x;
-    lcol[i] = slot < wy ? eperm[slot] : -1;
-    t0[i] = lcol[i] >= 0 ? etb[slot] : 0;
-    nc[i] = lcol[i] >= 0 ? eptr[lcol[i] + 1] - eptr[lcol[i]] : 0;
+    qkj[i] = qi < npair ? ((unsigned)(pk[qi] * DF_VS) << 16) | (unsigned)(pj[qi] * DF_XS) : 0u;
   }
   int it = 0;
   double beta = 0.0, dot = 0.0;
@@ -151,34 +167,29 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
       __syncthreads();
       const bool first = cs == rb;
       if (DIAG) {
-#pragma unroll
-        for (int i = 0; i < MAXO; ++i) {
-          const int l = threadIdx.x + i * blockDim.x;
-          if (l < wy) {
-            const df64 d = df_dot9(Vt, Xt + l * DF_CH);
-            if (first) Ds[l] = d; else Ds[l] += d;
-          }
+        for (int l = threadIdx.x; l < wy; l += blockDim.x) {
+          const df64 d = df_dot9(Vt, Xt + l * DF_XS);
+          if (first) Ds[l] = d; else Ds[l] += d;
         }
       }
 #pragma unroll
       for (int i = 0; i < DF_MAXQ; ++i) {
         const int qi = threadIdx.x + i * blockDim.x;
         if (qi < npair) {
-          const df64 s = df_dot9(Vt + (qkj[i] >> 16) * DF_CH, Xt + (qkj[i] & 0xffffu) * DF_CH);
+          const df64 s = df_dot9(Vt + (qkj[i] >> 16), Xt + (qkj[i] & 0xffffu));
           if (first) Ss[qi] = s; else Ss[qi] += s;
         }
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int i = 0; i < MAXO; ++i) {
-      const int l = lcol[i];
-      if (l < 0) continue;
+    for (int slot = threadIdx.x; slot < wy; slot += blockDim.x) {
+      const int2 d = __ldg(sdesc + slot);
+      const int l = (int)((unsigned)d.y >> 16), ncl = d.y & 0xffff;
       df64 acc = (DIAG && re > rb) ? Ds[l] : df64(0.f, 0.f);
       if (re > rb) {
-        const unsigned* cw = ctr + t0[i];
+        const unsigned* cw = ctr + d.x;
 #pragma unroll 4
-        for (int c = 0; c < nc[i]; ++c) {
+        for (int c = 0; c < ncl; ++c) {
           const unsigned w = __ldg(cw + 32 * c);
           acc += Ctab[w & 0xffu] * Ss[w >> 8];
         }
@@ -219,20 +230,21 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
 }
 
 static size_t df_smem(const EdgeList& E, int M1, int wx, bool diag) {
-  return ((size_t)E.npair + (diag ? E.nout : 0) + E.ncls + (size_t)M1 * DF_CH) * sizeof(df64) +
-         (size_t)wx * DF_CH * sizeof(float);
+  auto even = [](size_t v) { return (v + 1) & ~(size_t)1; };
+  return (even(E.npair) + (diag ? even(E.nout) : 0) + even(E.ncls) + (size_t)M1 * DF_VS) * sizeof(df64) +
+         (size_t)wx * DF_XS * sizeof(float);
 }
 
-// Block size: 256 threads when the pairs and two outputs per thread fit, else
-// 512 (more, smaller blocks hide the row barriers better; more outputs per
-// thread would spill).
-static int df_threads(const EdgeList& E) { return E.npair <= DF_MAXQ * 256 && E.nout <= 512 ? 256 : 512; }
+// Block size: 256 threads when every thread's pairs fit its registers, else
+// 512 (more, smaller blocks hide the row barriers better).
+static int df_threads(const EdgeList& E) { return E.npair <= DF_MAXQ * 256 ? 256 : 512; }
 
 // Usable when every thread's pairs fit its registers, the couplings have a
-// compact table and the staging fits a block's shared memory.
+// compact table with slot descriptors and the staging fits a block's shared
+// memory.
 bool df_pairs_usable(const sg_problem* h, const EdgeList& E, int wx) {
-  return h->staged_pairs && E.npair <= DF_MAXQ * 512 && E.ncls > 0 && h->nterm < 65536 && wx < 65536 &&
-         df_smem(E, h->nterm, wx, true) <= (size_t)std::max(h->smem_optin, 48 * 1024);
+  return h->staged_pairs && E.npair <= DF_MAXQ * 512 && E.ncls > 0 && E.sdesc && h->nterm * DF_VS < 65536 &&
+         wx * DF_XS < 65536 && df_smem(E, h->nterm, wx, true) <= (size_t)std::max(h->smem_optin, 48 * 1024);
 }
 
 template <bool DIAG, int MODE, typename TX, typename TY>
@@ -241,7 +253,6 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
   const int wy = E.nout;
   if (wy == 0) return SG_OK;
   const int threads = df_threads(E);
-  const int maxo = (wy + threads - 1) / threads;
   const size_t smem = df_smem(E, h->nterm, wx, DIAG);
   OuterArgs a = oa ? *oa : OuterArgs{};
   auto go = [&](auto kern) -> int {
@@ -251,21 +262,13 @@ static int launch_df(sg_problem* h, const EdgeList& E, const TX* X, int ldx, int
     int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
     if (MODE == DF_OUTER) grid = std::min(grid, h->opart_blocks);
     { kern<<<grid, threads, smem, s>>>(h->n, h->rowptr, h->colidx, (const df64*)h->vals_df, h->nterm, X, ldx, wx,
-                                       E.npair, E.pk, E.pj, E.ptr, E.perm, E.ctr, E.tb, (const df64*)E.ctab, E.ncls,
-                                       wy, Yin, ldyin, Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
+                                       E.npair, E.pk, E.pj, E.ctr, E.sdesc, (const df64*)E.ctab, E.ncls, wy, Yin,
+                                       ldyin, Y, ldy, h->fpA, h->fpB, h->fq, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
-  if (threads == 256) {
-    if (maxo <= 1) return go(k_df_pairs<1, DIAG, MODE, TX, TY, 256>);
-    if (maxo <= 2) return go(k_df_pairs<2, DIAG, MODE, TX, TY, 256>);
-  } else {
-    if (maxo <= 1) return go(k_df_pairs<1, DIAG, MODE, TX, TY, 512>);
-    if (maxo <= 2) return go(k_df_pairs<2, DIAG, MODE, TX, TY, 512>);
-    if (maxo <= 4) return go(k_df_pairs<4, DIAG, MODE, TX, TY, 512>);
-  }
-  set_error("double-float product: %d outputs exceed the supported 2048", wy);
-  return SG_ERR_UNSUPPORTED;
+  if (threads == 256) return go(k_df_pairs<DIAG, MODE, TX, TY, 256>);
+  return go(k_df_pairs<DIAG, MODE, TX, TY, 512>);
 }
 
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,

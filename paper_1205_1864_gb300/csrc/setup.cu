@@ -137,7 +137,7 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
           if (kj_ok) pkj[tb[sl] + 32 * (t - he.ptr[l])] = (c << 24) | (unsigned)(he.k[t] * wts + he.j[t]);
         }
       }
-      if (kj_ok && E.nout < 65536) {
+      if (E.nout < 65536) {
         // per slot: its first word and (output << 16 | couplings)
         std::vector<int2> sd(E.nout);
         bool ok = true;
@@ -147,13 +147,12 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
           sd[sl] = make_int2(tb[sl], (int)(((unsigned)l << 16) | (unsigned)cnt));
         }
         if (ok) {
-          SG_TRY(upload(&E.ckj, pkj.data(), pkj.size()));
           SG_TRY(upload(&E.sdesc, sd.data(), sd.size()));
+          if (kj_ok) SG_TRY(upload(&E.ckj, pkj.data(), pkj.size()));
         }
       }
       df64* dt = nullptr;
       SG_TRY(upload(&E.ctr, packed.data(), packed.size()));
-      SG_TRY(upload(&E.tb, tb.data(), tb.size()));
       SG_TRY(upload(&dt, tab.data(), tab.size()));
       E.ctab = dt;
       E.ncls = (int)tab.size();
@@ -176,7 +175,6 @@ static void free_edges(EdgeList& E) {
   cudaFree(E.ctr);
   cudaFree(E.ckj);
   cudaFree(E.sdesc);
-  cudaFree(E.tb);
   cudaFree(E.ctab);
   cudaFree(E.ctab32);
   cudaFree(E.pk);

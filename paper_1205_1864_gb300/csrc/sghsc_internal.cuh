@@ -69,14 +69,14 @@ struct EdgeList {
   // one value per 1-D degree, so a few classes cover them; ncls = 0 when the
   // table does not compress (more than 256 distinct coefficients).
   // couplings packed (pair << 8 | coefficient class), slot-transposed: the
-  // c-th coupling of output slot s (perm order) at ctr[tb[s] + 32 c], so the
-  // lanes of a warp (32 consecutive slots) read consecutive words
+  // c-th coupling of output slot s (perm order) at ctr[tb(s) + 32 c], so the
+  // lanes of a warp (32 consecutive slots) read consecutive words; tb(s) is
+  // in the slot's descriptor (sdesc)
   unsigned* ctr = nullptr;
-  int* tb = nullptr;
   // the same positions packed as class << 24 | (k rows32_stride(nin) + j)
   // (below 2^24)
   unsigned* ckj = nullptr;
-  int2* sdesc = nullptr;     // per slot: tb, output << 16 | couplings (with ckj)
+  int2* sdesc = nullptr;     // per slot: tb(s), output << 16 | couplings
   void* ctab = nullptr;      // df64
   float* ctab32 = nullptr;   // the same coefficients in FP32
   int ncls = 0;
