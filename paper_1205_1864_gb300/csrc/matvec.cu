@@ -424,6 +424,14 @@ static int launch_t(sg_problem* h, const TIn* X, int ldx, int wx, const EdgeList
 int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, const void* X, int ldx, int wx,
                         const EdgeList& E, bool diag, const void* Yin, int ldyin, double alpha, double beta,
                         void* Y, int ldy, cudaStream_t s) {
+  // the narrow level products: one thread per (row, output)
+  const bool sub_form = !diag && Yin && alpha == -1.0 && beta == 1.0;
+  if (sub_form && tin == tacc && tin == tb && tin == tout && (tin == SG_F64 || tin == SG_F32) &&
+      narrow_usable(h, E, wx)) {
+    if (tin == SG_F64)
+      return launch_level_narrow<double>(h, E, (const double*)X, ldx, (const double*)Yin, ldyin, (double*)Y, ldy, s);
+    return launch_level_narrow<float>(h, E, (const float*)X, ldx, (const float*)Yin, ldyin, (float*)Y, ldy, s);
+  }
   if (tin == SG_F64 && tacc == SG_F64 && tb == SG_F64 && tout == SG_F64) {
     auto Xp = (const double*)X;
     auto Bp = (const double*)Yin;

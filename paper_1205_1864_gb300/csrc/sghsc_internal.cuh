@@ -242,6 +242,13 @@ int launch_df_apply(sg_problem* h, const float* U, double* Y, cudaStream_t s);
 // Y = Yin - sum_k A_k X G_k[out, in]^T: X FP32, Yin FP64, Y FP32.
 int launch_df_level(sg_problem* h, const EdgeList& E, const float* X, int ldx, int wx, const double* Yin, int ldyin,
                     float* Y, int ldy, cudaStream_t s);
+// Level products with at most 16 output columns and fewer than 512 input
+// columns, one thread per (row, output) (levelnarrow.cu): Y = Yin - sum
+// (Yin may alias Y).
+bool narrow_usable(const sg_problem* h, const EdgeList& E, int wx);
+template <typename T>
+int launch_level_narrow(sg_problem* h, const EdgeList& E, const T* X, int ldx, const T* Yin, int ldyin, T* Y, int ldy,
+                        cudaStream_t s);
 // Row stride of the term sums of the FP32 row kernel (rows32.cu).
 constexpr int ROWS32_COLS = 512;   // input columns per pass of a block (two per thread)
 __host__ __device__ constexpr int rows32_stride(int wx) { return (wx + ROWS32_COLS - 1) / ROWS32_COLS * ROWS32_COLS; }

@@ -1,9 +1,11 @@
-"""The FP32 row kernel (input columns in registers, term sums in shared
-memory): the full SG product (eq. (3)'s sum over the KL terms) and the level
-products B_l, C_l of Algorithm 1 with at least 512 input columns, or 128
-input and 512 output columns, against the oracle within the FP32 rounding
-bound, against the row-per-warp kernels (the same products with the row
-kernels switched off), and inside the FP32 preconditioner."""
+"""The product kernels chosen by shape: the FP32 row kernel (input columns in
+registers, term sums in shared memory) for the full SG product (eq. (3)'s sum
+over the KL terms) and the level products B_l, C_l of Algorithm 1 with at
+least 512 input columns, or 128 input and 512 output columns; the
+thread-per-output kernel for level products into at most 16 columns. Against
+the oracle within the rounding bound, against the row-per-warp kernels (the
+same products with the shape-specific kernels switched off), and inside the
+FP32 preconditioner."""
 import numpy as np
 import pytest
 
@@ -102,3 +104,37 @@ def test_rows32_inside_the_fp32_preconditioner(lib):
     ref = hsc.hsc_apply(A, G, off, R, dsolve=dsolve)
     assert np.abs(Z - ref).max() <= 2e-5 * np.abs(ref).max()
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("ne,M,p", [(8, 10, 4), (7, 3, 3)])
+def test_narrow_level_products(lib, ne, M, p, prec, monkeypatch):
+    """The level products into at most 16 columns (one thread per row and
+    output: B_1, C_1, B_2 at M = 10; every level at M = 3), in place as the
+    preconditioner applies them, against the oracle within m u sum|terms| and
+    against the staged kernels."""
+    import torch
+    prob, A, G, off = problem(ne, M, p)
+    h = lib.SGProblem.from_inputs(prob, p)
+    monkeypatch.setenv("SGHSC_GENERIC_PRODUCTS", "1")
+    hg = lib.SGProblem.from_inputs(prob, p)
+    dt, u = (torch.float64, 2.0 ** -53) if prec == "f64" else (torch.float32, U32)
+    m = 9 * (2 * M + 1) + 2
+    for lo, li in [(l - 1, l) for l in range(1, p + 1)] + [(l, l - 1) for l in range(1, p + 1)]:
+        win, wout = off[li + 1] - off[li], off[lo + 1] - off[lo]
+        if wout > 16:
+            continue
+        X = S.random_block(prob.n, win, seed=lo + 10 * li)
+        Yin = S.random_block(prob.n, wout, seed=5 + lo)
+        if prec == "f32":
+            X, Yin = X.astype(np.float32).astype(np.float64), Yin.astype(np.float32).astype(np.float64)
+        Yt = _t(Yin, dt)
+        lib.sg_level_apply(h, lo, li, _t(X, dt), Yt, Yt)       # in place
+        Y = _np(Yt)
+        Yg = _np(lib.sg_level_apply(hg, lo, li, _t(X, dt), _t(Yin, dt)))
+        exact = Yin - so.level_apply(A, G, off, lo, li, X)
+        bound = np.abs(Yin) + so.level_apply([abs(a) for a in A], [abs(g) for g in G], off, lo, li, np.abs(X))
+        assert np.all(np.abs(Y - exact) <= m * u * bound + 1e-300), (lo, li)
+        assert np.all(np.abs(Y - Yg) <= 2 * m * u * bound + 1e-300), (lo, li)
+    h.close()
+    hg.close()
