@@ -154,12 +154,19 @@ int enqueue_solve(sg_problem* h, const sg_solve_opts& o, cudaStream_t s) {
     a.cond = lc.cond;
     a.has_cond = lc.has_cond;
     a.flag = lc.flag;
-    SG_TRY(precond(h, o.precond, h->fr, h->fz, o.prec, bs));
-    { k_outer_dots<<<vg, 256, 0, bs>>>(N, h->fz, h->fr, h->fq, a); ::sghsc::note_launch(); }
     // with an FP32 preconditioner and df64, the outer product runs in double-float arithmetic
     const bool df = o.precond != SG_PREC_NONE && o.prec.precision == SG_F32 && o.prec.df64;
-    // Algorithm 1 and block Gauss-Seidel in FP32 leave z in h->Z32 before widening it
-    const float* z32 = df && (o.precond == SG_PREC_HSC || o.precond == SG_PREC_BGS) ? h->Z32 : nullptr;
+    // Algorithm 1 and block Gauss-Seidel in FP32 leave z in h->Z32: the dots
+    // and the outer product read it there (widened exactly on the fly), so z
+    // is never written in FP64
+    // (the staged outer product reads z32; the row-per-warp one reads FP64 z)
+    const float* z32 = df && (o.precond == SG_PREC_HSC || o.precond == SG_PREC_BGS) &&
+                               df_pairs_usable(h, h->all, h->P) ? h->Z32 : nullptr;
+    SG_TRY(precond(h, o.precond, h->fr, z32 ? nullptr : h->fz, o.prec, bs));
+    if (z32)
+      { k_outer_dots32<<<vg, 256, 0, bs>>>(N, z32, h->fr, h->fq, a); ::sghsc::note_launch(); }
+    else
+      { k_outer_dots<<<vg, 256, 0, bs>>>(N, h->fz, h->fr, h->fq, a); ::sghsc::note_launch(); }
     SG_TRY(launch_outer_matvec(h, a, bs, df, z32));
     { k_outer_update<<<vg, 256, 0, bs>>>(N, h->fpA, h->fpB, h->fq, h->fx, h->fr, a); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();

@@ -207,7 +207,7 @@ int hsc_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
       else
         SG_TRY(inner_solve(h, SG_F32, h->T32, w, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
     }
-    SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));
+    if (Z) SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));   // Z null: z stays in Z32
     return SG_OK;
   }
   // all FP64 (the pre-correction product writes the lower levels it reaches:
@@ -277,7 +277,7 @@ int bgs_apply_lv(sg_problem* h, const double* R, double* Z, const sg_prec_opts& 
                                  -1.0, 1.0, R32 + lo, P, s));
       SG_TRY(inner_solve(h, SG_F32, R32 + lo, P, SG_F32, Z32 + lo, P, SG_F32, w, o, s));
     }
-    SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));
+    if (Z) SG_TRY(launch_cast(Z32, SG_F32, P, Z, SG_F64, P, n, P, s));   // Z null: z stays in Z32
     return SG_OK;
   }
   double* Rw = h->R64w;

@@ -289,6 +289,8 @@ int inner_solve_cluster(sg_problem* h, const void* src, int ld_src, int src_t, v
 
 // ---- HSC / mean preconditioner (hsc.cu) ----
 int prepare_precond(sg_problem* h, int kind, const sg_prec_opts& o);
+// With o.precision == SG_F32 a null Z leaves the result in h->Z32 (FP32)
+// without widening it (the outer solver then reads z there).
 int hsc_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 int mean_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);
 int bgs_apply_impl(sg_problem* h, const double* R, double* Z, const sg_prec_opts& o, cudaStream_t s);

@@ -67,13 +67,13 @@ __global__ void __launch_bounds__(256) k_outer_init(long long N, const double* _
 
 // z.r and z.q: beta (0 on the first iteration; flexible: z_{k+1}.(r_{k+1}-r_k)/(z_k.r_k)
 // with r_{k+1} - r_k = -alpha_k q_k) and rho = z.r
-__global__ void __launch_bounds__(256) k_outer_dots(long long N, const double* __restrict__ z,
-                                                    const double* __restrict__ r, const double* __restrict__ q,
-                                                    OuterArgs a) {
+template <typename TZ>
+__device__ __forceinline__ void outer_dots(long long N, const TZ* __restrict__ z, const double* __restrict__ r,
+                                           const double* __restrict__ q, const OuterArgs& a) {
   const int it = a.ctl->it;
   double s0 = 0.0, s1 = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const double zv = z[i];
+    const double zv = widen<double>(z[i]);   // an FP32 z exactly, with integer operations
     s0 += zv * r[i];
     if (it > 0) s1 += zv * q[i];
   }
@@ -88,6 +88,17 @@ __global__ void __launch_bounds__(256) k_outer_dots(long long N, const double* _
     a.sc[SC_RHO] = zr;
     if (!(zr == zr) || !(beta == beta)) atomicOr(a.status, ST_OUTER_BREAKDOWN);
   }
+}
+
+__global__ void __launch_bounds__(256) k_outer_dots(long long N, const double* __restrict__ z,
+                                                    const double* __restrict__ r, const double* __restrict__ q,
+                                                    OuterArgs a) {
+  outer_dots(N, z, r, q, a);
+}
+__global__ void __launch_bounds__(256) k_outer_dots32(long long N, const float* __restrict__ z,
+                                                      const double* __restrict__ r, const double* __restrict__ q,
+                                                      OuterArgs a) {
+  outer_dots(N, z, r, q, a);
 }
 
 // x += alpha p_new; r -= alpha q; r.r -> relative residual, it += 1, loop condition

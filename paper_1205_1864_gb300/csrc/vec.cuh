@@ -26,6 +26,8 @@ struct OuterArgs {
 
 __global__ void k_outer_init(long long N, const double* F, const double* Y, double* r, OuterArgs a);
 __global__ void k_outer_dots(long long N, const double* z, const double* r, const double* q, OuterArgs a);
+// the same with the FP32 z of the mixed preconditioners
+__global__ void k_outer_dots32(long long N, const float* z, const double* r, const double* q, OuterArgs a);
 __global__ void k_outer_update(long long N, const double* pA, const double* pB, const double* q, double* x,
                                double* r, OuterArgs a);
 __global__ void k_outer_true(long long N, const double* F, const double* Y, OuterArgs a);
