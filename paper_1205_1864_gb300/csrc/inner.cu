@@ -864,10 +864,12 @@ __device__ void ph_coarse(Blk Bk, const CoarseGrids& L, int tot, int wp, const T
   }
 }
 
-// r = src (cast; padded columns w..wp-1 zero), x = 0; acc = ||b||^2 partials
+// r = src (cast; padded columns w..wp-1 zero); acc = ||b||^2 partials. x is
+// not cleared: the first update writes it (x = alpha p), and a batch that
+// ends before its first iteration scatters zeros.
 template <typename TS, typename T>
 __device__ __forceinline__ void ph_gather(Blk B, int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
-                                          T* __restrict__ r, T* __restrict__ x, T (&acc)[VW<T>::N]) {
+                                          T* __restrict__ r, T (&acc)[VW<T>::N]) {
   constexpr int N = VW<T>::N;
 #pragma unroll
   for (int u = 0; u < N; ++u) acc[u] = T(0);
@@ -881,22 +883,23 @@ __device__ __forceinline__ void ph_gather(Blk B, int n, int w, int wp, int k, co
       v.a[u] = c0 + u < w ? widen<T>(src[(size_t)node * lds + c0 + u]) : T(0);
       acc[u] += v.a[u] * v.a[u];
     }
-    const int i = node * wp + c0;
-    vst(r + i, v);
-    vst(x + i, vzero<T>());
+    vst(r + node * wp + c0, v);
   }
 }
 
-// x (wp columns) -> dst (leading dimension ldd, first w columns)
+// x (wp columns) -> dst (leading dimension ldd, first w columns); with ctl,
+// the PCG iterate: zeros if the batch ended before its first iteration (x
+// then was never written)
 template <typename T, typename TD>
 __device__ __forceinline__ void ph_scatter(Blk B, int n, int w, int wp, int k, const T* __restrict__ x,
-                                           TD* __restrict__ dst, int ldd) {
+                                           TD* __restrict__ dst, int ldd, const InnerCtl* ctl) {
   constexpr int N = VW<T>::N;
   int cg, node, nstep;
   if (!thread_pos(wp / N, k, B, cg, node, nstep)) return;
   const int c0 = cg * N;
+  const bool zero = ctl && ctl->it == 0;
   for (; node < n; node += nstep) {
-    const Vec<T> v = vld(x + node * wp + c0);
+    const Vec<T> v = zero ? vzero<T>() : vld(x + node * wp + c0);
 #pragma unroll
     for (int u = 0; u < N; ++u)
       if (c0 + u < w) dst[(size_t)node * ldd + c0 + u] = (TD)v.a[u];
@@ -967,7 +970,7 @@ __device__ __forceinline__ void ph_matvec_p(Blk B, int nx, int ny, int wp, int k
 template <typename T>
 __device__ __forceinline__ void ph_update_xr(Blk B, int n, int wp, int k, const T* __restrict__ pnew,
                                              const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
-                                             const T* __restrict__ alpha, const int* __restrict__ done,
+                                             const T* __restrict__ alpha, const int* __restrict__ done, bool first,
                                              T (&acc)[VW<T>::N]) {
   constexpr int N = VW<T>::N;
 #pragma unroll
@@ -976,13 +979,18 @@ __device__ __forceinline__ void ph_update_xr(Blk B, int n, int wp, int k, const 
   if (!thread_pos(wp / N, k, B, cg, node, nstep)) return;
   const int c0 = cg * N;
   const unsigned dm = done_mask<N>(done, c0);
-  if (dm == (1u << N) - 1) return;
+  if (dm == (1u << N) - 1) {
+    if (first)   // columns done at entry: x_0 = 0
+      for (; node < n; node += nstep) vst(x + node * wp + c0, vzero<T>());
+    return;
+  }
   T a[N];
 #pragma unroll
   for (int u = 0; u < N; ++u) a[u] = (dm >> u) & 1u ? T(0) : alpha[c0 + u];
   for (; node < n; node += nstep) {
     const int i = node * wp + c0;
-    Vec<T> xv = vld(x + i), rv = vld(r + i);
+    Vec<T> xv = first ? vzero<T>() : vld(x + i);   // the first update writes x (x_0 = 0, not stored)
+    Vec<T> rv = vld(r + i);
     const Vec<T> pv = vld(pnew + i), qv = vld(q + i);
 #pragma unroll
     for (int u = 0; u < N; ++u) {
@@ -1061,13 +1069,13 @@ __global__ void __launch_bounds__(1024) k_vcycle_coarse(CoarseGrids L, int tot, 
   ph_coarse<T>(this_grid(), L, tot, wp, bg, xg, om, nu, done, smem_raw);
 }
 
-// r = src, x = 0, ||b||^2 -> FIN_INIT (sets the loop condition; zero columns,
-// the padded ones included, are done)
+// r = src, ||b||^2 -> FIN_INIT (sets the loop condition; zero columns, the
+// padded ones included, are done); x is written by the first update
 template <typename TS, typename T>
 __global__ void __launch_bounds__(1024) k_gather(int n, int w, int wp, int k, const TS* __restrict__ src, int lds,
-                                                 T* __restrict__ r, T* __restrict__ x, FinArgs f) {
+                                                 T* __restrict__ r, FinArgs f) {
   T acc[VW<T>::N];
-  ph_gather<TS, T>(this_grid(), n, w, wp, k, src, lds, r, x, acc);
+  ph_gather<TS, T>(this_grid(), n, w, wp, k, src, lds, r, acc);
   reduce_finalize<T, VW<T>::N>(f, acc, wp, k, FIN_INIT);
 }
 
@@ -1089,8 +1097,8 @@ __global__ void __launch_bounds__(1024) k_pack(int n, int w, int wp, int k, cons
 
 template <typename T, typename TD>
 __global__ void __launch_bounds__(1024) k_scatter(int n, int w, int wp, int k, const T* __restrict__ x,
-                                                  TD* __restrict__ dst, int ldd) {
-  ph_scatter<T, TD>(this_grid(), n, w, wp, k, x, dst, ldd);
+                                                  TD* __restrict__ dst, int ldd, const InnerCtl* ctl) {
+  ph_scatter<T, TD>(this_grid(), n, w, wp, k, x, dst, ldd, ctl);
 }
 
 // a . b per column -> op (used when the finest grid is inside the coarse block)
@@ -1120,7 +1128,8 @@ __global__ void __launch_bounds__(1024) k_update_xr(int n, int wp, int k, const 
                                                     const T* __restrict__ pB, const T* __restrict__ q,
                                                     T* __restrict__ x, T* __restrict__ r, FinArgs f) {
   T acc[VW<T>::N];
-  ph_update_xr<T>(this_grid(), n, wp, k, (f.ctl->it & 1) ? pA : pB, q, x, r, alpha_of<T>(f), f.done, acc);
+  const int it = f.ctl->it;
+  ph_update_xr<T>(this_grid(), n, wp, k, (it & 1) ? pA : pB, q, x, r, alpha_of<T>(f), f.done, it == 0, acc);
   reduce_finalize<T, VW<T>::N>(f, acc, wp, k, FIN_CONV);
 }
 
@@ -1967,9 +1976,9 @@ static int inner_solve_t(sg_problem* h, const void* src, int ld_src, int src_t, 
     f.has_cond = lc.has_cond;
     f.flag = lc.flag;
     if (src_t == SG_F64)
-      { k_gather<double, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, wp, sh.k, (const double*)src, ld_src, r, x, f); ::sghsc::note_launch(); }
+      { k_gather<double, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, wp, sh.k, (const double*)src, ld_src, r, f); ::sghsc::note_launch(); }
     else
-      { k_gather<float, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, wp, sh.k, (const float*)src, ld_src, r, x, f); ::sghsc::note_launch(); }
+      { k_gather<float, T><<<sh.grid, sh.bdim, 0, ps>>>(G.n, w, wp, sh.k, (const float*)src, ld_src, r, f); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
@@ -1987,9 +1996,9 @@ static int inner_solve_t(sg_problem* h, const void* src, int ld_src, int src_t, 
   };
   SG_TRY(capture_while(h, s, pre, body));
   if (dst_t == SG_F64)
-    { k_scatter<T, double><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, wp, shs.k, x, (double*)dst, ld_dst); ::sghsc::note_launch(); }
+    { k_scatter<T, double><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, wp, shs.k, x, (double*)dst, ld_dst, fa.ctl); ::sghsc::note_launch(); }
   else
-    { k_scatter<T, float><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, wp, shs.k, x, (float*)dst, ld_dst); ::sghsc::note_launch(); }
+    { k_scatter<T, float><<<shs.grid, shs.bdim, 0, s>>>(G.n, w, wp, shs.k, x, (float*)dst, ld_dst, fa.ctl); ::sghsc::note_launch(); }
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -2018,7 +2027,7 @@ static int vcycle_packed(sg_problem* h, InnerWork& iw, const T* B, T* bpad, T* X
   { k_pack<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, B, w, bpad); ::sghsc::note_launch(); }
   const T* res = nullptr;
   SG_TRY(vcycle<T>(h, iw, 0, bpad, (T*)iw.z, (T*)iw.zt, wp, o, s, nullptr, &res));
-  { k_scatter<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, res, X, w); ::sghsc::note_launch(); }
+  { k_scatter<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, res, X, w, nullptr); ::sghsc::note_launch(); }
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
@@ -2038,7 +2047,7 @@ static int m0_apply_t(sg_problem* h, const T* src, int lds, T* dst, int ldd, int
   { k_pack<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, src, lds, (T*)iw.r); ::sghsc::note_launch(); }
   const T* res = nullptr;
   SG_TRY(vcycle<T>(h, iw, 0, (const T*)iw.r, (T*)iw.z, (T*)iw.zt, wp, o, s, nullptr, &res));
-  { k_scatter<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, res, dst, ldd); ::sghsc::note_launch(); }
+  { k_scatter<T, T><<<sh.grid, sh.bdim, 0, s>>>(G.n, w, wp, sh.k, res, dst, ldd, nullptr); ::sghsc::note_launch(); }
   SG_CHECK_LAUNCH();
   return SG_OK;
 }
