@@ -288,7 +288,7 @@ int sg_autotune(sg_problem* h, void* stream) {
   }
   SG_TRY(autotune_k1(h, SG_F64, (cudaStream_t)stream));
   // the FP32 full product takes the row kernel (fixed shape) where it applies
-  if (!rows32_usable(h, h->all, h->P)) SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
+  if (!rows32_usable(h, h->all, h->P, true)) SG_TRY(autotune_k1(h, SG_F32, (cudaStream_t)stream));
   SG_TRY(autotune_outer(h, (cudaStream_t)stream, false));
   // the double-float pair-form kernel has a fixed shape; tune the general one only when it stands in
   if (!df_pairs_usable(h, h->all, h->P)) SG_TRY(autotune_outer(h, (cudaStream_t)stream, true));

@@ -446,7 +446,7 @@ int launch_block_matvec(sg_problem* h, int tin, int tacc, int tb, int tout, cons
     // the row kernel with input columns in registers for the full product and the wide level products
     const bool plain = diag && !Yin && alpha == 1.0 && beta == 0.0;
     const bool sub = !diag && Yin && alpha == -1.0 && beta == 1.0;
-    if ((plain || sub) && rows32_usable(h, E, wx))
+    if ((plain || sub) && rows32_usable(h, E, wx, diag))
       return launch_rows32(h, E, diag, Xp, ldx, wx, Bp, ldyin, Yp, ldy, s);
     if (diag) return launch_t<float, float, float, float, true>(h, Xp, ldx, wx, E, Bp, ldyin, alpha, beta, Yp, ldy, s);
     return launch_t<float, float, float, float, false>(h, Xp, ldx, wx, E, Bp, ldyin, alpha, beta, Yp, ldy, s);

@@ -2,7 +2,7 @@
 // level product B_l / C_l of Algorithm 1) with every input column in
 // registers.
 //
-// One block per matrix row r at a time. For each chunk of up to nine
+// One block per matrix row r at a time (two on narrower levels). For each chunk of up to nine
 // nonzeros c_e of the row (the Q1 stencil row is one chunk) the block stages
 // the KL-term values a_k(r, c_e) in shared memory, padded to three float4 per
 // term; thread j then loads X(c_e, j) for its input column from global memory
@@ -12,8 +12,8 @@
 // shared loads per nine FMAs. T (M+1 x wx, FP32) is the only large shared
 // array. Then output l sums its couplings c * T(k, j) (and T(0, l) for the
 // identity of G_0 in the full product) from a slot-transposed table of
-// packed (class, offset of T(k, j)) words read coalesced through L1, and writes Y(r, l) or
-// Yin(r, l) - that.
+// packed (class, offset of T(k, j)) words read coalesced through L1, and
+// writes Y(r, l) or Yin(r, l) - that.
 //
 // T is formed for every (k, j) although the couplings use about half of them
 // at M = 10, p = 4: the extra FMAs cost less than the per-pair bookkeeping
@@ -60,38 +60,52 @@ __device__ __forceinline__ void term_sum2(const float4* v, const float (&x)[rows
 
 // DIAG: add T(0, l) (full product); SUB: Y = Yin - sum (Yin may alias Y:
 // each entry is read, then written, by the same thread), else Y = sum.
-template <bool DIAG, bool SUB>
+// ROWS rows at a time, RG = NT / ROWS threads per row (a multiple of 32, so
+// the slot-transposed couplings still give a warp consecutive words): on
+// narrow levels several rows share the block's barriers.
+template <bool DIAG, bool SUB, int ROWS>
 __global__ void __launch_bounds__(rows32::NT, 4) k_rows32(
     int n, const int* __restrict__ rowptr, const int* __restrict__ colidx, const float* __restrict__ vals, int M1,
     const float* __restrict__ X, int ldx, int wx, const unsigned* __restrict__ ckj, const int2* __restrict__ sdesc,
     const float* __restrict__ ctab, int ncls, int wy, const float* Yin, int ldyin, float* Y, int ldy) {
   using namespace rows32;
+  constexpr int RG = NT / ROWS;
   extern __shared__ __align__(16) float4 sm4[];
-  float4* Vt = sm4;                                            // [M1][VS4]
-  float* Ctab = reinterpret_cast<float*>(Vt + (size_t)M1 * VS4);   // [ncls]
-  float* Ts = Ctab + ((ncls + 3) & ~3);                        // [M1][wts]
-  float* Vf = reinterpret_cast<float*>(Vt);
-  const int tid = threadIdx.x;
   const int wts = rows32_stride(wx);
+  float* Ctab = reinterpret_cast<float*>(sm4);                        // [ncls]
+  float4* Vall = sm4 + (ncls + 3) / 4;                                 // [ROWS][M1][VS4]
+  float* Tall = reinterpret_cast<float*>(Vall + (size_t)ROWS * M1 * VS4);   // [ROWS][M1][wts]
+  const int tid = threadIdx.x, g = tid / RG, lt = tid - g * RG;
+  float4* Vt = Vall + (size_t)g * M1 * VS4;
+  float* Vf = reinterpret_cast<float*>(Vt);
+  float* Ts = Tall + (size_t)g * M1 * wts;
   for (int t = tid; t < ncls; t += NT) Ctab[t] = ctab[t];
-  for (int r = blockIdx.x; r < n; r += gridDim.x) {
-    const int rb = rowptr[r], re = rowptr[r + 1];
-    for (int cs = rb; cs < re; cs += CH) {
-      const int nzc = min(CH, re - cs);
-      __syncthreads();   // Vt (previous chunk) and T (previous row's couplings) are read no more
-      for (int t = tid; t < M1 * VS4 * 4; t += NT) {
+  for (long long rbase = (long long)blockIdx.x * ROWS; rbase < n; rbase += (long long)gridDim.x * ROWS) {
+    const int r = (int)rbase + g;
+    const bool rv = r < n;
+    const int rb = rv ? rowptr[r] : 0, re = rv ? rowptr[r + 1] : 0;
+    int maxnz = re - rb;   // chunks of the block's longest row: every thread runs the same barriers
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      const long long rq = rbase + q;
+      if (ROWS > 1 && rq < n) maxnz = max(maxnz, rowptr[rq + 1] - rowptr[rq]);
+    }
+    for (int cs = 0; cs < maxnz; cs += CH) {
+      const int nzc = max(0, min(CH, re - rb - cs));
+      __syncthreads();   // Vt (previous chunk) and T (previous rows' couplings) are read no more
+      for (int t = lt; t < M1 * VS4 * 4; t += RG) {
         const int k = t / (VS4 * 4), e = t - k * (VS4 * 4);
-        Vf[t] = e < nzc ? vals[(size_t)(cs + e) * M1 + k] : 0.f;
+        Vf[t] = e < nzc ? vals[(size_t)(rb + cs + e) * M1 + k] : 0.f;
       }
       int col[CH];
 #pragma unroll
-      for (int e = 0; e < CH; ++e) col[e] = e < nzc ? colidx[cs + e] : -1;
+      for (int e = 0; e < CH; ++e) col[e] = e < nzc ? colidx[rb + cs + e] : -1;
       __syncthreads();
-      const bool first = cs == rb;
-      // two input columns per thread (j0, j0 + NT): each staged term row feeds
+      const bool first = cs == 0;
+      // two input columns per thread (j0, j0 + RG): each staged term row feeds
       // 18 FMAs; columns past wx read nothing and fill the padding of T
-      for (int j0 = tid; j0 < wx; j0 += 2 * NT) {
-        const int j1 = j0 + NT;
+      for (int j0 = lt; j0 < wx; j0 += 2 * RG) {
+        const int j1 = j0 + RG;
         float x0[CH], x1[CH];
 #pragma unroll
         for (int e = 0; e < CH; ++e) {
@@ -105,7 +119,7 @@ __global__ void __launch_bounds__(rows32::NT, 4) k_rows32(
             float s0, s1;
             term_sum2(Vt + k * VS4, x0, x1, s0, s1);
             tp[0] = s0;
-            tp[NT] = s1;
+            tp[RG] = s1;
           }
         } else {
 #pragma unroll 2
@@ -113,14 +127,15 @@ __global__ void __launch_bounds__(rows32::NT, 4) k_rows32(
             float s0, s1;
             term_sum2(Vt + k * VS4, x0, x1, s0, s1);
             tp[0] += s0;
-            tp[NT] += s1;
+            tp[RG] += s1;
           }
         }
       }
     }
     __syncthreads();
+    if (!rv) continue;
     // outputs by slot (sorted by coupling count, so a warp's loops end together)
-    for (int slot = tid; slot < wy; slot += NT) {
+    for (int slot = lt; slot < wy; slot += RG) {
       const int2 d = __ldg(sdesc + slot);
       const int l = (int)((unsigned)d.y >> 16), ncl = d.y & 0xffff;
       float acc = 0.f;
@@ -146,19 +161,33 @@ __global__ void __launch_bounds__(rows32::NT, 4) k_rows32(
   }
 }
 
-static size_t rows32_smem(const EdgeList& E, int M1, int wx) {
-  return (size_t)M1 * rows32::VS4 * 16 + (size_t)((E.ncls + 3) & ~3) * 4 + (size_t)M1 * rows32_stride(wx) * 4;
+static size_t rows32_smem(const EdgeList& E, int M1, int wx, int rows) {
+  return (size_t)((E.ncls + 3) & ~3) * 4 +
+         (size_t)rows * ((size_t)M1 * rows32::VS4 * 16 + (size_t)M1 * rows32_stride(wx) * 4);
+}
+
+// Rows per block: one for the wide products, two for the level products
+// between 32 and 512 columns each way (at 511^2 rows, M = 10: 55 <- 220
+// columns 0.95 against 1.36 ms for the row-per-warp kernel, 220 <- 55 0.90
+// against 0.98 ms; four rows per block: 1.10 and 1.12 ms); 0 where this
+// kernel is not taken.
+static int rows32_rows(const EdgeList& E, int wx, bool diag) {
+  if (wx >= 512 || E.nout >= 512) return 1;
+  return !diag && wx >= 32 && E.nout >= 32 ? 2 : 0;
 }
 
 // FP32 products take this kernel for inputs from 512 columns, or from 128
 // input columns with at least 512 outputs (measured on the 512x512, M = 10,
 // p = 4 operator: 1001 -> 1001 columns 3.7 ms against 11.1 ms for the
 // row-per-warp kernel, 715 -> 220 2.7 against 4.6 ms, 220 -> 715 2.0 against
-// 3.4 ms; 220 -> 55 1.16 against 0.99 ms and narrower levels lose more:
-// their rows are too short to amortise the block barriers).
-bool rows32_usable(const sg_problem* h, const EdgeList& E, int wx) {
-  return h->staged_pairs && (wx >= 512 || (E.nout >= 512 && wx >= 128)) && wx == E.nin && E.ckj && E.sdesc &&
-         E.ncls > 0 && h->nterm <= 256 && rows32_smem(E, h->nterm, wx) <= (size_t)std::max(h->smem_optin, 48 * 1024);
+// 3.4 ms), and with two rows per block for level products of 32 to 512
+// columns each way (one row per block there: 220 -> 55 1.16 against
+// 0.99 ms, the rows too short to amortise the block barriers).
+bool rows32_usable(const sg_problem* h, const EdgeList& E, int wx, bool diag) {
+  const int rows = rows32_rows(E, wx, diag);
+  const bool shape = wx >= 512 || (E.nout >= 512 && wx >= 128) || rows > 1;
+  return h->staged_pairs && shape && wx == E.nin && E.ckj && E.sdesc && E.ncls > 0 && h->nterm <= 256 &&
+         rows32_smem(E, h->nterm, wx, std::max(rows, 1)) <= (size_t)std::max(h->smem_optin, 48 * 1024);
 }
 
 int launch_rows32(sg_problem* h, const EdgeList& E, bool diag, const float* X, int ldx, int wx, const float* Yin,
@@ -170,18 +199,21 @@ int launch_rows32(sg_problem* h, const EdgeList& E, bool diag, const float* X, i
     set_error("FP32 row product: unsupported form");
     return SG_ERR_UNSUPPORTED;
   }
-  const size_t smem = rows32_smem(E, h->nterm, wx);
+  const int rows = std::max(rows32_rows(E, wx, diag), 1);
+  const size_t smem = rows32_smem(E, h->nterm, wx, rows);
   auto go = [&](auto kern) -> int {
     SG_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-    const int grid = std::min(h->n, h->num_sms * std::max(per_sm, 1));
+    const int grid = std::min((h->n + rows - 1) / rows, h->num_sms * std::max(per_sm, 1));
     { kern<<<grid, NT, smem, s>>>(h->n, h->rowptr, h->colidx, h->vals32, h->nterm, X, ldx, wx, E.ckj, E.sdesc,
                                   E.ctab32, E.ncls, wy, Yin, ldyin, Y, ldy); ::sghsc::note_launch(); }
     SG_CHECK_LAUNCH();
     return SG_OK;
   };
-  return diag ? go(k_rows32<true, false>) : go(k_rows32<false, true>);
+  if (diag) return go(k_rows32<true, false, 1>);
+  if (rows == 2) return go(k_rows32<false, true, 2>);
+  return go(k_rows32<false, true, 1>);
 }
 
 }  // namespace sghsc

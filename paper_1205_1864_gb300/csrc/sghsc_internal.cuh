@@ -254,7 +254,7 @@ constexpr int ROWS32_COLS = 512;   // input columns per pass of a block (two per
 __host__ __device__ constexpr int rows32_stride(int wx) { return (wx + ROWS32_COLS - 1) / ROWS32_COLS * ROWS32_COLS; }
 // FP32 products with the input columns in registers (rows32.cu): usable and
 // preferred for E (compact table, sizes, inputs at least 512 columns wide).
-bool rows32_usable(const sg_problem* h, const EdgeList& E, int wx);
+bool rows32_usable(const sg_problem* h, const EdgeList& E, int wx, bool diag);
 int launch_rows32(sg_problem* h, const EdgeList& E, bool diag, const float* X, int ldx, int wx, const float* Yin,
                   int ldyin, float* Y, int ldy, cudaStream_t s);
 

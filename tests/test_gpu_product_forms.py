@@ -138,3 +138,37 @@ def test_narrow_level_products(lib, ne, M, p, prec, monkeypatch):
         assert np.all(np.abs(Y - Yg) <= 2 * m * u * bound + 1e-300), (lo, li)
     h.close()
     hg.close()
+
+
+@pytest.mark.parametrize("M,p,n", [(6, 4, 203), (10, 4, 61)])
+def test_ragged_rows_on_the_row_kernels(lib, M, p, n, monkeypatch):
+    """Ragged CSR rows (empty rows, rows of up to 23 nonzeros: several chunks
+    of nine) through the FP32 row kernel at every shape it takes (two rows per
+    block at 56 <-> 126 columns, one row per block on the full product and at
+    715 <-> 220), and the narrow kernel, against the oracle, with an odd row
+    count so the last block holds a single row."""
+    import torch
+    from tests.gpu_common import random_csr
+    from oracle import chaos
+    rowptr, colidx = random_csr(n, seed=8, max_row=23)
+    rng = np.random.default_rng(9)
+    vals = rng.uniform(-1, 1, size=(len(colidx), M + 1))
+    h = lib.SGProblem(0, 0, M, p, rowptr, colidx, vals)
+    A = so.kl_matrices(rowptr, colidx, vals)
+    G = chaos.g_matrices(M, p)
+    _, off = chaos.multi_indices(M, p)
+    m = 23 + 2 * M + 3
+    U = S.random_block(n, h.P, seed=3).astype(np.float32)
+    Y = _np(lib.sg_apply(h, _t(U, torch.float32)))
+    U = U.astype(np.float64)
+    assert np.all(np.abs(Y - so.sg_apply(A, G, U)) <= m * U32 * abs_bound(A, G, U) + 1e-300)
+    assert np.all(Y[3::7] == 0.0)
+    for lo, li in [(l - 1, l) for l in range(1, p + 1)] + [(l, l - 1) for l in range(1, p + 1)]:
+        win, wout = off[li + 1] - off[li], off[lo + 1] - off[lo]
+        X = S.random_block(n, win, seed=lo + 10 * li).astype(np.float32).astype(np.float64)
+        Yin = S.random_block(n, wout, seed=5 + lo).astype(np.float32).astype(np.float64)
+        Yl = _np(lib.sg_level_apply(h, lo, li, _t(X, torch.float32), _t(Yin, torch.float32)))
+        exact = Yin - so.level_apply(A, G, off, lo, li, X)
+        bound = np.abs(Yin) + so.level_apply([abs(a) for a in A], [abs(g) for g in G], off, lo, li, np.abs(X))
+        assert np.all(np.abs(Yl - exact) <= m * U32 * bound + 1e-300), (lo, li)
+    h.close()
