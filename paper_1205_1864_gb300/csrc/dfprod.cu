@@ -134,9 +134,13 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
     double* __restrict__ q, OuterArgs a) {
   constexpr bool OUTER = MODE == DF_OUTER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // pairs and diagonal outputs padded to whole passes of the block, so every
+  // warp runs the same loops (the padding pairs read staged slot 0 and write
+  // sums nothing reads)
+  const int nq = (npair + LB - 1) / LB, nd = DIAG ? (wy + LB - 1) / LB : 0;
   df64* Ss = reinterpret_cast<df64*>(smem_raw);
-  df64* Ds = Ss + ((npair + 1) & ~1);
-  df64* Ctab = Ds + (DIAG ? ((wy + 1) & ~1) : 0);
+  df64* Ds = Ss + (size_t)nq * LB;
+  df64* Ctab = Ds + (size_t)nd * LB;
   df64* Vt = Ctab + ((ncls + 1) & ~1);
   float* Xt = reinterpret_cast<float*>(Vt + (size_t)M1 * DF_VS);
   for (int t = threadIdx.x; t < ncls; t += blockDim.x) Ctab[t] = ctab[t];
@@ -167,24 +171,25 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
       __syncthreads();
       const bool first = cs == rb;
       if (DIAG) {
-        for (int l = threadIdx.x; l < wy; l += blockDim.x) {
-          const df64 d = df_dot9(Vt, Xt + l * DF_XS);
+        for (int i = 0; i < nd; ++i) {
+          const int l = threadIdx.x + i * LB;
+          const df64 d = df_dot9(Vt, Xt + min(l, wx - 1) * DF_XS);
           if (first) Ds[l] = d; else Ds[l] += d;
         }
       }
 #pragma unroll
       for (int i = 0; i < DF_MAXQ; ++i) {
-        const int qi = threadIdx.x + i * blockDim.x;
-        if (qi < npair) {
+        if (i < nq) {   // the same for the whole block
+          const int qi = threadIdx.x + i * LB;
           const df64 s = df_dot9(Vt + (qkj[i] >> 16), Xt + (qkj[i] & 0xffffu));
           if (first) Ss[qi] = s; else Ss[qi] += s;
         }
       }
     }
     __syncthreads();
-    for (int slot = threadIdx.x; slot < wy; slot += blockDim.x) {
+    for (int slot = threadIdx.x; slot < wy; slot += LB) {
       const int2 d = __ldg(sdesc + slot);
-      const int l = (int)((unsigned)d.y >> 16), ncl = d.y & 0xffff;
+      const int l = (int)((unsigned)d.y >> 16), ncl = d.y & 0xffff;   // ncl: the warp's count
       df64 acc = (DIAG && re > rb) ? Ds[l] : df64(0.f, 0.f);
       if (re > rb) {
         const unsigned* cw = ctr + d.x;
@@ -229,15 +234,16 @@ __global__ void __launch_bounds__(LB, LB <= 256 ? 4 : 2) k_df_pairs(
   }
 }
 
-static size_t df_smem(const EdgeList& E, int M1, int wx, bool diag) {
-  auto even = [](size_t v) { return (v + 1) & ~(size_t)1; };
-  return (even(E.npair) + (diag ? even(E.nout) : 0) + even(E.ncls) + (size_t)M1 * DF_VS) * sizeof(df64) +
-         (size_t)wx * DF_XS * sizeof(float);
-}
-
 // Block size: 256 threads when every thread's pairs fit its registers, else
 // 512 (more, smaller blocks hide the row barriers better).
 static int df_threads(const EdgeList& E) { return E.npair <= DF_MAXQ * 256 ? 256 : 512; }
+
+static size_t df_smem(const EdgeList& E, int M1, int wx, bool diag) {
+  const size_t t = (size_t)df_threads(E);
+  auto pad = [t](size_t v) { return (v + t - 1) / t * t; };
+  return (pad(E.npair) + (diag ? pad(E.nout) : 0) + ((E.ncls + 1) & ~1) + (size_t)M1 * DF_VS) * sizeof(df64) +
+         (size_t)wx * DF_XS * sizeof(float);
+}
 
 // Usable when every thread's pairs fit its registers, the couplings have a
 // compact table with slot descriptors and the staging fits a block's shared

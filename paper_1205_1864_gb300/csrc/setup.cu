@@ -103,12 +103,15 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
   for (int t = 0; t < E.nedges; ++t) pair[t] = pairs.at(std::make_pair(he.k[t], he.j[t]));
   E.npair = (int)pk.size();
   {
+    // coefficient classes; class 0 is the coefficient 0, which pads the
+    // shorter slots of a warp to the warp's longest (a zero word adds 0)
     std::map<double, int> cls;
     for (double c : he.c) cls.emplace(c, 0);
-    if (cls.size() <= 256 && E.npair < (1 << 24)) {
-      std::vector<df64> tab;
-      std::vector<float> tab32;
+    if (cls.size() + (cls.count(0.0) ? 0 : 1) <= 256 && E.npair < (1 << 24)) {
+      std::vector<df64> tab{df64(0.f, 0.f)};
+      std::vector<float> tab32{0.f};
       for (auto& kv : cls) {
+        if (kv.first == 0.0) continue;
         kv.second = (int)tab.size();
         tab.push_back(df_split_host(kv.first));
         tab32.push_back((float)kv.first);
@@ -138,11 +141,14 @@ static int upload_edges(const HostEdges& he, EdgeList& E, int out0 = 0, int in0 
         }
       }
       if (E.nout < 65536) {
-        // per slot: its first word and (output << 16 | couplings)
+        // per slot: its first word and (output << 16 | couplings of the
+        // warp's longest slot, the others padded with zero words), so the
+        // lanes of a warp run the same coupling loop
         std::vector<int2> sd(E.nout);
         bool ok = true;
         for (int sl = 0; sl < E.nout; ++sl) {
-          const int l = perm[sl], cnt = he.ptr[l + 1] - he.ptr[l];
+          const int l = perm[sl], l0 = perm[sl & ~31];
+          const int cnt = he.ptr[l0 + 1] - he.ptr[l0];
           ok = ok && cnt < 65536;
           sd[sl] = make_int2(tb[sl], (int)(((unsigned)l << 16) | (unsigned)cnt));
         }
