@@ -272,6 +272,40 @@ def run_ours(args, rank, world, dev):
             out[name] = {"ms": k, "GB_s": b / k / 1e6, "TFLOP_s": fl / k / 1e9, "bytes": b, "flops": fl}
             del Ut, Yt
         return out
+    if args.profile == "levels":
+        # every level product B_l, C_l alone: FP32, FP64, FP32 in with FP64
+        # sums and with double-float sums (warm-up + timed launches each)
+        alpha, off = h.chaos_table()
+        out = {"profile": "levels", "workload": cfg["name"], "n": n, "nnz": nnz, "products": []}
+        for lo, li in [(l - 1, l) for l in range(1, p + 1)] + [(l, l - 1) for l in range(1, p + 1)]:
+            win, wout = int(off[li + 1] - off[li]), int(off[lo + 1] - off[lo])
+            ai, ao = alpha[off[li]:off[li + 1]], alpha[off[lo]:off[lo + 1]]
+            couplings = sum(int((np.abs(ao - a).sum(axis=1) == 1).sum()) for a in ai)   # alpha_out = alpha_in +- e_k
+            rec = {"out": lo, "in": li, "w_out": wout, "w_in": win, "couplings": couplings,
+                   "gather_flops": 2 * nnz * couplings}
+            for name, tx, ty, df in (("fp32", torch.float32, torch.float32, False),
+                                     ("fp64", torch.float64, torch.float64, False),
+                                     ("fp32_acc64", torch.float32, torch.float64, False),
+                                     ("fp32_accdf64", torch.float32, torch.float64, True)):
+                X = torch.tensor(S.random_block(n, win, seed=lo + 10 * li), dtype=tx, device=dev)
+                Yin = torch.tensor(S.random_block(n, wout, seed=5 + lo), dtype=ty, device=dev)
+                Yo = torch.empty((n, wout), dtype=tx, device=dev)
+                for _ in range(args.warmup):
+                    L.sg_level_apply(h, lo, li, X, Yin, Yo, df64=df)
+                ts = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    L.sg_level_apply(h, lo, li, X, Yin, Yo, df64=df)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                rec[name + "_ms"] = float(np.mean(ts))
+                del X, Yin, Yo
+            out["products"].append(rec)
+        return out
     if args.profile == "inner":
         # the batched inner PCG on A_0 alone, FP32, one batch as wide as the widest degree level
         wmax = max(int(math.comb(M + l - 1, l)) for l in range(1, p + 1))
@@ -925,9 +959,10 @@ def main():
                     help="mesh override (elements per side, a power of two) for profiling a workload's kernel "
                          "shapes on a smaller case; the name gets an @ne suffix")
     ap.add_argument("--profile", nargs="?", const="solve", default=None,
-                    choices=["solve", "apply", "inner", "tables"],
-                    help="solve: only the warm-up and timed HSC solves; apply: only the SG product, FP64 then "
-                         "FP32; inner: only the batched inner PCG on the widest level (for ncu captures); "
+                    choices=["solve", "apply", "levels", "inner", "tables"],
+                    help="solve: only the warm-up and timed HSC solves; apply: only the SG product, FP64, "
+                         "FP32 and FP32 with double-float sums; levels: every level product in each arithmetic; "
+                         "inner: only the batched inner PCG on the widest level (for ncu captures); "
                          "tables: the paper's Tables 1-4 on the GPU next to the printed values; "
                          "prints one short line")
     args = ap.parse_args()
