@@ -202,6 +202,10 @@ def run_ours(args, rank, world, dev):
     h = L.SGProblem.from_inputs(prob, p)
     tuned = L.sg_autotune(h)   # block sizes of the SG product (FP64, FP32), part of setup
     forms = L.sg_autotune_forms(h)   # pair (1) or gather (0) form: FP64, FP32, outer
+    # inner solver per degree-level width: 0 stand-alone kernels, 1 / 3 on-chip
+    # cluster solver with 8 / 16 CTAs, 2 the wide one
+    _, _off = h.chaos_table()
+    inner_paths = {int(_off[l + 1] - _off[l]): h.inner_path(int(_off[l + 1] - _off[l])) for l in range(p + 1)}
     setup_s = time.time() - t0
     n, P, M, nnz = h.n, h.P, h.M, h.nnz
     alpha, off = h.chaos_table()
@@ -452,7 +456,8 @@ def run_ours(args, rank, world, dev):
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 outer CG, df64 (FP32-pair) outer/top-level products, f32 inner", "data": "synthetic (seeded Q1 + exponential-covariance KL, f = 1)",
         "config": workload_config(cfg, world),
-        "autotune": {"threads_f64_f32": list(tuned), "pair_form_f64_f32_outer": list(forms)},
+        "autotune": {"threads_f64_f32": list(tuned), "pair_form_f64_f32_outer": list(forms),
+                     "inner_solver_by_width": inner_paths},
         "hsc": {"ms": ms, "iterations": st_h.iterations, "true_rel_res": st_true.true_rel_res,
                 "oracle_rel_res": oracle_res, "arithmetic": "FP32 inner solves and level products < p; outer CG "
                 "FP64; outer SG product and level-p products in double-float (df64) on the FP32 units",

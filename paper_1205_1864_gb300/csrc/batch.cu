@@ -240,6 +240,7 @@ struct TuneKey {
 };
 struct TuneVal {
   int t64, t32, tout, p64, p32, pout, tdf, pdf;
+  std::map<int, int> inner;   // FP32 batch width -> inner solver
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune_cache;
@@ -262,6 +263,71 @@ using namespace sghsc;
 
 extern "C" {
 
+// The inner solver of each degree-level width, where several can run the
+// batch (cluster solvers on grids up to 127^2): each candidate solves an FP32
+// batch of that width (a constant right-hand side, two fixed PCG iterations,
+// the default V-cycle) captured as a graph, timed over three replays after a
+// first one; the fastest is kept for the width.
+static int autotune_inner(sg_problem* h, cudaStream_t s) {
+  if (!h->cl_plan) return SG_OK;
+  std::vector<int> widths;
+  for (int l = 0; l <= h->p; ++l) {
+    const int w = h->off[l + 1] - h->off[l];
+    if (w > 0 && std::find(widths.begin(), widths.end(), w) == widths.end()) widths.push_back(w);
+  }
+  const int wmax = *std::max_element(widths.begin(), widths.end());
+  SG_TRY(ensure_inner_work(h, SG_F32, std::max(wmax, h->wmax)));   // no allocation under capture
+  const size_t bytes = (size_t)h->n * wmax * sizeof(float);
+  float *B = nullptr, *X = nullptr;
+  SG_TRY_CUDA(cudaMalloc((void**)&B, bytes));
+  cudaError_t ce = cudaMalloc((void**)&X, bytes);
+  if (ce != cudaSuccess) {
+    cudaFree(B);
+    SG_TRY_CUDA(ce);
+  }
+  cudaMemsetAsync(B, 0x3f, bytes, s);   // every value 0.747f
+  sg_prec_opts o;
+  sg_default_prec_opts(&o);
+  o.precision = SG_F32;
+  o.inner_fixed_iters = 2;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int r = SG_OK;
+  for (const int w : widths) {
+    const std::vector<int> cands = inner_path_candidates(h, w);
+    if (cands.size() < 2) continue;
+    int best = cands[0];
+    float best_ms = 1e30f;
+    for (const int c : cands) {
+      h->inner_pick[w] = c;
+      clear_graphs(h);
+      auto enq = [&](cudaStream_t cs) { return inner_solve(h, SG_F32, B, w, SG_F32, X, w, SG_F32, w, o, cs); };
+      r = run_graph(h, "tune_inner", enq, s);
+      if (r != SG_OK) break;
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3 && r == SG_OK; ++rep) r = run_graph(h, "tune_inner", enq, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r == SG_OK && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (r != SG_OK) break;
+    h->inner_pick[w] = best;
+  }
+  clear_graphs(h);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(B);
+  cudaFree(X);
+  if (r == SG_OK) SG_TRY_CUDA(cudaGetLastError());
+  return r;
+}
+
 int sg_autotune(sg_problem* h, void* stream) {
   set_error("");
   if (!h) {
@@ -283,6 +349,7 @@ int sg_autotune(sg_problem* h, void* stream) {
       h->outer_pairs = v.pout;
       h->outer_threads_df = v.tdf;
       h->outer_pairs_df = v.pdf;
+      h->inner_pick = v.inner;
       return SG_OK;
     }
   }
@@ -292,10 +359,11 @@ int sg_autotune(sg_problem* h, void* stream) {
   SG_TRY(autotune_outer(h, (cudaStream_t)stream, false));
   // the double-float pair-form kernel has a fixed shape; tune the general one only when it stands in
   if (!df_pairs_usable(h, h->all, h->P)) SG_TRY(autotune_outer(h, (cudaStream_t)stream, true));
+  SG_TRY(autotune_inner(h, (cudaStream_t)stream));
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = TuneVal{h->k1_threads[SG_F64], h->k1_threads[SG_F32], h->outer_threads,
                               h->k1_pairs[SG_F64],   h->k1_pairs[SG_F32],   h->outer_pairs,
-                              h->outer_threads_df,   h->outer_pairs_df};
+                              h->outer_threads_df,   h->outer_pairs_df,     h->inner_pick};
   return SG_OK;
 }
 

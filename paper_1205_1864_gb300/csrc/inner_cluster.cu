@@ -1292,14 +1292,33 @@ void cluster_free(sg_problem* h) {
 // on-chip one with clusters of 8 when all of them are (a second wave would
 // double the solve), 2 = the wide one (finest grid in global memory) when its
 // clusters are, 0 = none of them (the stand-alone kernels).
+// The autotuner's choice for the width (sg_autotune) takes precedence when
+// it is one of the eligible solvers.
+static bool path_eligible(const ClusterSolver* cs, int w, int path) {
+  const int ncl = ceil_div(w, 4);
+  if (path == 3) return ncl <= cs->maxcl16;
+  if (path == 1) return ncl <= cs->maxcl;
+  if (path == 2) return ncl <= cs->maxclw;
+  return path == 0;
+}
+
 static int cluster_path(const sg_problem* h, int dtype, int w) {
   const ClusterSolver* cs = (const ClusterSolver*)h->cl_plan;
   if (dtype != SG_F32 || !cs) return 0;
-  const int ncl = ceil_div(w, 4);
-  if (ncl <= cs->maxcl16) return 3;
-  if (ncl <= cs->maxcl) return 1;
-  if (ncl <= cs->maxclw) return 2;
+  const auto it = h->inner_pick.find(w);
+  if (it != h->inner_pick.end() && path_eligible(cs, w, it->second)) return it->second;
+  for (int path : {3, 1, 2})
+    if (path_eligible(cs, w, path)) return path;
   return 0;
+}
+
+std::vector<int> inner_path_candidates(const sg_problem* h, int w) {
+  std::vector<int> c{0};
+  const ClusterSolver* cs = (const ClusterSolver*)h->cl_plan;
+  if (!cs) return c;
+  for (int path : {3, 1, 2})
+    if (path_eligible(cs, w, path)) c.push_back(path);
+  return c;
 }
 
 bool cluster_usable(const sg_problem* h, int dtype, int w) { return cluster_path(h, dtype, w) != 0; }

@@ -174,6 +174,7 @@ struct sg_problem {
   bool mg_full = false;                     // the hierarchy reaches the one-node grid (V-cycle usable)
   int cb_level = 0;                         // first grid handled by the in-block coarse V-cycle
   void* cl_plan = nullptr;                  // cluster inner solvers: plans and scratch (null: not usable)
+  std::map<int, int> inner_pick;            // FP32 batch width -> inner solver chosen by the autotuner
   bool pipe_off = false;                    // SGHSC_NO_PIPE=1: no row-pipelined sweeps on large grids
   // workspace
   sghsc::InnerWork iw32, iw64;
@@ -283,6 +284,9 @@ int cluster_setup(sg_problem* h);
 void cluster_free(sg_problem* h);
 // True when an FP32 batch of w columns takes the cluster solver.
 bool cluster_usable(const sg_problem* h, int dtype, int w);
+// The inner solvers an FP32 batch of w columns may take (0 the stand-alone
+// kernels, 1 / 3 the on-chip cluster solver with 8 / 16 CTAs, 2 the wide one).
+std::vector<int> inner_path_candidates(const sg_problem* h, int w);
 // inner_solve for FP32 on a usable handle: one cluster launch per solve.
 int inner_solve_cluster(sg_problem* h, const void* src, int ld_src, int src_t, void* dst, int ld_dst, int dst_t,
                         int w, const sg_prec_opts& o, cudaStream_t s);

@@ -256,3 +256,25 @@ def test_wide_cluster_solver_parity(lib):
     B32 = Bt.astype(np.float32).astype(np.float64)
     res = np.linalg.norm(B32 - A[0] @ _np(Xt), axis=0) / np.linalg.norm(B32, axis=0)
     assert np.all(res <= 2e-2)
+
+
+def test_autotune_picks_inner_solvers(lib):
+    """sg_autotune times every solver that can run each degree-level batch
+    (stand-alone, 8- and 16-CTA clusters, the wide variant) and keeps one per
+    width; a second handle of the same class takes the cached choice, and the
+    mixed solve on the tuned handle still meets 1e-8 against the oracle."""
+    from tests.gpu_common import oracle_rel_residual
+    prob, A, G, off = problem(64, 4, 3, 0.2, 0.5)
+    h = lib.SGProblem.from_inputs(prob, 3)
+    rule = {int(off[l + 1] - off[l]): h.inner_path(int(off[l + 1] - off[l])) for l in range(4)}
+    lib.sg_autotune(h)
+    picks = {w: h.inner_path(w) for w in rule}
+    assert all(v in (0, 1, 2, 3) for v in picks.values())
+    h2 = lib.SGProblem.from_inputs(prob, 3)
+    lib.sg_autotune(h2)
+    assert {w: h2.inner_path(w) for w in rule} == picks
+    F = S.make_rhs(prob, 3)
+    o = lib.solve_opts(lib.prec_opts(precision=lib.SG_F32, df64=1), precond=lib.SG_PREC_HSC, tol=1e-8)
+    U, st = lib.sg_solve(h, _t(F), o)
+    assert st.status == 0
+    assert oracle_rel_residual(A, G, F, _np(U)) <= 1.5e-8
