@@ -322,6 +322,17 @@ int mean_precond_apply(sg_problem* h, const double* R, double* Z, const sg_prec_
 int sg_solve(sg_problem* h, const double* F, double* U, const sg_solve_opts* opts,
              sg_solve_stats* stats, void* stream);
 
+/* sg_solve_host -- sg_solve with the right-hand side and the solution in host
+ * memory: F_host (n x P FP64, read) and U_host (n x P FP64, written; read as
+ * the initial guess when opts->use_x0), both owned by the caller, row-major.
+ * Page-locked buffers (cudaHostAlloc, cudaHostRegister; torch pin_memory)
+ * are read and written by the library's kernels through their device mapping,
+ * over the host link; other host memory goes through cudaMemcpyAsync. Returns
+ * when U_host holds the result (the call synchronises the stream). Errors as
+ * sg_solve. No counterpart in the paper (the end-to-end entry). */
+int sg_solve_host(sg_problem* h, const double* F_host, double* U_host, const sg_solve_opts* opts,
+                  sg_solve_stats* stats, void* stream);
+
 /* sg_autotune -- time the candidate block sizes (64 to 1024 threads) of the
  * full SG product in FP64 and FP32, and separately of the outer solver's fused
  * product (SG product + CG update + p.q, in FP64 and in its double-float

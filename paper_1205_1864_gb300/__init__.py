@@ -26,7 +26,7 @@ from ._lib import (SG_F32, SG_F32_ACC64, SG_F64, SG_HERMITE, SG_LEGENDRE, SG_M0_
 
 __all__ = [
     "SGProblem", "sg_setup", "sg_apply", "sg_level_apply", "sg_vcycle_apply", "sg_inner_solve",
-    "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "SG_PREC_BGS", "SG_M0_VCYCLE", "SG_M0_DIAG", "sg_solve", "sg_qoi", "sg_qoi_grad", "prec_opts", "solve_opts",
+    "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "SG_PREC_BGS", "SG_M0_VCYCLE", "SG_M0_DIAG", "sg_solve", "sg_solve_host", "sg_qoi", "sg_qoi_grad", "prec_opts", "solve_opts",
     "sg_set_scales", "SGQoI", "SGGradBatch", "sg_kl_set_theta", "sg_kl_qoi_grad", "sg_qoi_value_and_grad_batch",
     "sg_autotune", "sg_autotune_forms", "sg_autotune_shapes", "sg_autotune_set", "sg_measure_alu_peak",
     "SGError", "SG_F32", "SG_F32_ACC64", "SG_F64", "SG_PREC_HSC", "SG_PREC_MEAN", "SG_PREC_NONE", "SG_LEGENDRE", "SG_HERMITE",
@@ -256,6 +256,26 @@ def sg_solve(h: SGProblem, F: torch.Tensor, opts=None, U: Optional[torch.Tensor]
     stats = _stats(status, st)
     if raise_on_error:
         check(status, "sg_solve")
+    return U, stats
+
+
+def sg_solve_host(h: SGProblem, F: torch.Tensor, opts=None, U: Optional[torch.Tensor] = None,
+                  raise_on_error=True):
+    """``sg_solve`` on host (CPU) blocks: ``F`` in, ``U`` out, both contiguous
+    FP64 CPU tensors (pinned ones are read and written by the library's
+    kernels directly); returns ``(U, SolveStats)`` when ``U`` is filled."""
+    if F.is_cuda or not F.is_contiguous() or F.dtype != torch.float64:
+        raise ValueError("sg_solve_host: F must be a contiguous FP64 CPU tensor")
+    U = torch.empty_like(F) if U is None else U
+    if U.is_cuda or not U.is_contiguous() or U.dtype != torch.float64 or U.shape != F.shape:
+        raise ValueError("sg_solve_host: U must be a contiguous FP64 CPU tensor shaped like F")
+    o = opts or solve_opts()
+    st = _lib.sg_solve_stats()
+    status = _lib.LIB.sg_solve_host(h.h, C.c_void_p(F.data_ptr()), C.c_void_p(U.data_ptr()), C.byref(o),
+                                    C.byref(st), _stream())
+    stats = _stats(status, st)
+    if raise_on_error:
+        check(status, "sg_solve_host")
     return U, stats
 
 

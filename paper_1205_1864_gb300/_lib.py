@@ -77,6 +77,7 @@ def _load():
         "mean_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "bgs_precond_apply": (i, [vp, vp, vp, P(sg_prec_opts), vp]),
         "sg_solve": (i, [vp, vp, vp, P(sg_solve_opts), P(sg_solve_stats), vp]),
+        "sg_solve_host": (i, [vp, vp, vp, P(sg_solve_opts), P(sg_solve_stats), vp]),
         "sg_qoi": (i, [vp, vp, vp, vp, vp]),
         "sg_autotune": (i, [vp, vp]),
         "sg_autotune_result": (i, [vp, P(i), P(i)]),
@@ -115,7 +116,7 @@ def check(status: int, where: str):
 def exported_symbols():
     """Names the header declares (used by the CPU test of the library)."""
     return ["sg_setup", "sg_setup_gpc", "sg_problem_terms", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
-            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "sg_solve", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
+            "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "sg_solve", "sg_solve_host", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
             "sg_autotune_outer_result", "sg_autotune_set",
             "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",
             "sg_qoi_grad", "sg_measure_alu_peak", "sg_kl_set_theta", "sg_kl_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

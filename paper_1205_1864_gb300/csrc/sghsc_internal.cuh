@@ -315,6 +315,8 @@ int solve_collect(sg_problem* h, const sg_solve_opts& o, sg_solve_stats* st, dou
 int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts);
 
 // ---- small elementwise kernels (vec.cu) ----
+// dst = src, n doubles, by a kernel (either side may be page-locked host memory)
+int launch_copy64(const double* src, double* dst, long long n, int num_sms, cudaStream_t s);
 int launch_cast(const void* src, int src_t, int lds, void* dst, int dst_t, int ldd, int rows,
                 int cols, cudaStream_t s);
 

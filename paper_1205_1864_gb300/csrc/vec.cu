@@ -19,6 +19,33 @@ __global__ void k_cast(const TS* __restrict__ src, int lds, TD* __restrict__ dst
   }
 }
 
+// dst = src, n doubles; 16-byte pieces when both are 16-byte aligned. Either
+// side may be page-locked host memory (mapped into the device's address
+// space): the SMs then move the data over the host link themselves.
+__global__ void __launch_bounds__(512) k_copy64(const double* __restrict__ src, double* __restrict__ dst,
+                                                long long n, int vec) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (vec) {
+    const long long n2 = n / 2;
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    for (long long i = t; i < n2; i += stride) d2[i] = s2[i];
+    if (t == 0 && (n & 1)) dst[n - 1] = src[n - 1];
+  } else {
+    for (long long i = t; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
+int launch_copy64(const double* src, double* dst, long long n, int num_sms, cudaStream_t s) {
+  if (n <= 0) return SG_OK;
+  const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+  const int grid = (int)std::min<long long>((n / (vec ? 2 : 1) + 511) / 512, (long long)num_sms * 8);
+  { k_copy64<<<std::max(grid, 1), 512, 0, s>>>(src, dst, n, vec); ::sghsc::note_launch(); }
+  SG_CHECK_LAUNCH();
+  return SG_OK;
+}
+
 int launch_cast(const void* src, int src_t, int lds, void* dst, int dst_t, int ldd, int rows, int cols,
                 cudaStream_t s) {
   const long long total = (long long)rows * cols;

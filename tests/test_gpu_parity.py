@@ -471,3 +471,32 @@ def test_qoi_and_gradient_parity(lib):
     assert np.allclose(_np(hk), hk_ref, rtol=1e-12, atol=1e-12 * np.abs(hk_ref).max())
     assert np.allclose(_np(g), W @ hk_ref, rtol=1e-11, atol=1e-12 * np.abs(W @ hk_ref).max())
 
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_matches_device_solve(lib, pinned):
+    """sg_solve_host on host blocks (page-locked: moved by the library's
+    kernels; pageable: by cudaMemcpyAsync) gives the device entry's solution
+    bit for bit, with an initial guess read from the host block too; the
+    result is against the dense direct solve."""
+    import torch
+    c = S.CONFIGS["cfg1_fp64_16x16_M3_p3"]
+    prob, A, G, off = problem(c["ne"], c["M"], c["p"], c["sigma"], c["corr_len"])
+    h = lib.SGProblem.from_inputs(prob, c["p"])
+    F = S.make_rhs(prob, c["p"])
+    o = lib.solve_opts(lib.prec_opts(precision=lib.SG_F32, df64=1), precond=lib.SG_PREC_HSC, tol=1e-12)
+    Ud, sd = lib.sg_solve(h, _t(F), o)
+    Fh = torch.tensor(F, dtype=torch.float64)
+    Uh = torch.full_like(Fh, 7.0)
+    if pinned:
+        Fh, Uh = Fh.pin_memory(), Uh.pin_memory()
+    Uh, sh = lib.sg_solve_host(h, Fh, o, Uh)
+    assert np.array_equal(Uh.numpy(), _np(Ud)) and sh.iterations == sd.iterations
+    ref = so.direct_solve(A, G, F)
+    assert np.abs(Uh.numpy() - ref).max() <= 1e-7 * np.abs(ref).max()
+    # initial guess from the host block: the solution itself converges at once
+    o0 = lib.solve_opts(o.prec, precond=lib.SG_PREC_HSC, tol=1e-10, use_x0=1)
+    U2, s2 = lib.sg_solve_host(h, Fh, o0, Uh.clone() if not pinned else Uh.clone().pin_memory())
+    assert s2.iterations <= 1
+    with pytest.raises(ValueError):
+        lib.sg_solve_host(h, _t(F), o)
