@@ -375,6 +375,10 @@ int sg_batch_create(int count, sg_problem* const* problems, sg_batch** out);
  * converged, else the first failure (per-system status in stats). */
 int sg_batch_solve(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts* opts,
                    sg_solve_stats* stats, void* stream);
+/* sg_batch_solve_host -- sg_batch_solve with host blocks F_host[i], U_host[i]
+ * (moved as by sg_solve_host: page-locked ones by the library's kernels). */
+int sg_batch_solve_host(sg_batch* b, const double* const* F_host, double* const* U_host,
+                        const sg_solve_opts* opts, sg_solve_stats* stats, void* stream);
 void sg_batch_destroy(sg_batch* b);
 
 /* sg_qoi -- Q = sum_j u_j^T M_h u_j = E[int u^2] for the orthonormal chaos

@@ -347,6 +347,26 @@ class SGBatch:
             check(status, "sg_batch_solve")
         return Us, stats
 
+    def solve_host(self, Fs, opts=None, Us=None, raise_on_error=True):
+        """``solve`` on host blocks (contiguous FP64 CPU tensors; pinned ones
+        are read and written by the library's kernels directly)."""
+        count = len(self.problems)
+        if len(Fs) != count:
+            raise ValueError(f"need {count} right-hand sides")
+        Us = [torch.empty_like(F) for F in Fs] if Us is None else list(Us)
+        for T in list(Fs) + Us:
+            if T.is_cuda or not T.is_contiguous() or T.dtype != torch.float64:
+                raise ValueError("solve_host: blocks must be contiguous FP64 CPU tensors")
+        o = opts or solve_opts()
+        st = (_lib.sg_solve_stats * count)()
+        fp = (C.c_void_p * count)(*[C.c_void_p(F.data_ptr()) for F in Fs])
+        up = (C.c_void_p * count)(*[C.c_void_p(U.data_ptr()) for U in Us])
+        status = _lib.LIB.sg_batch_solve_host(self.b, fp, up, C.byref(o), st, _stream())
+        stats = [_stats(st[i].status, st[i]) for i in range(count)]
+        if raise_on_error:
+            check(status, "sg_batch_solve_host")
+        return Us, stats
+
     def close(self):
         if getattr(self, "b", None):
             _lib.LIB.sg_batch_destroy(self.b)

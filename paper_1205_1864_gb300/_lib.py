@@ -86,6 +86,7 @@ def _load():
         "sg_autotune_set": (i, [vp, i, i, i, i, i, i]),
         "sg_batch_create": (i, [i, P(vp), P(vp)]),
         "sg_batch_solve": (i, [vp, P(vp), P(vp), P(sg_solve_opts), P(sg_solve_stats), vp]),
+        "sg_batch_solve_host": (i, [vp, P(vp), P(vp), P(sg_solve_opts), P(sg_solve_stats), vp]),
         "sg_batch_destroy": (None, [vp]),
         "sg_qoi_grad": (i, [vp, vp, vp, i, P(C.c_double), vp, vp, vp]),
         "sg_measure_alu_peak": (i, [i, i, P(C.c_double), vp]),
@@ -118,5 +119,5 @@ def exported_symbols():
     return ["sg_setup", "sg_setup_gpc", "sg_problem_terms", "sg_destroy", "sg_set_scales", "sg_problem_dims", "sg_chaos_table", "sg_apply", "sg_level_apply",
             "sg_vcycle_apply", "sg_vcycle_apply_static", "sg_inner_solve", "sg_inner_cluster", "sg_inner_path", "hsc_precond_apply", "mean_precond_apply", "bgs_precond_apply", "sg_solve", "sg_solve_host", "sg_qoi", "sg_autotune", "sg_autotune_result", "sg_autotune_forms",
             "sg_autotune_outer_result", "sg_autotune_set",
-            "sg_batch_create", "sg_batch_solve", "sg_batch_destroy",
+            "sg_batch_create", "sg_batch_solve", "sg_batch_solve_host", "sg_batch_destroy",
             "sg_qoi_grad", "sg_measure_alu_peak", "sg_kl_set_theta", "sg_kl_qoi_grad", "sg_last_error", "sg_kernel_launches", "sg_default_prec_opts", "sg_default_solve_opts"]

@@ -68,14 +68,25 @@ static int batch_build(sg_batch* b, const sg_solve_opts& o, cudaGraph_t* out) {
   return SG_OK;
 }
 
+// host: F[i], U[i] are host blocks (copy_host), else device blocks
 static int batch_solve(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts& o,
-                       sg_solve_stats* stats, cudaStream_t s) {
+                       sg_solve_stats* stats, cudaStream_t s, bool host = false) {
   const auto t0 = std::chrono::steady_clock::now();
   for (sg_problem* h : b->hs) {
     SG_TRY(check_solve_opts(h, &o));
     SG_TRY(solve_prepare(h, o));
   }
-  for (size_t i = 0; i < b->hs.size(); ++i) SG_TRY(solve_stage_in(b->hs[i], F[i], U[i], o, s));
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    sg_problem* h = b->hs[i];
+    if (host) {
+      const size_t N = (size_t)h->n * h->P;
+      SG_TRY(copy_host(h, F[i], h->fF, N, true, s));
+      if (o.use_x0) SG_TRY(copy_host(h, U[i], h->fx, N, true, s));
+      SG_TRY(solve_stage_in(h, h->fF, h->fx, o, s));
+    } else {
+      SG_TRY(solve_stage_in(h, F[i], U[i], o, s));
+    }
+  }
   // a workspace reallocation in any handle invalidates the captured graphs
   bool stale = b->gens.size() != b->hs.size();
   for (size_t i = 0; !stale && i < b->hs.size(); ++i) stale = b->gens[i] != b->hs[i]->ws_gen;
@@ -100,7 +111,10 @@ static int batch_solve(sg_batch* b, const double* const* F, double* const* U, co
   { SG_TRY_CUDA(cudaGraphLaunch(it->second.exec, s)); }
   for (size_t i = 0; i < b->hs.size(); ++i) {
     sg_problem* h = b->hs[i];
-    SG_TRY_CUDA(cudaMemcpyAsync(U[i], h->fx, (size_t)h->n * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (host)
+      SG_TRY(copy_host(h, h->fx, U[i], (size_t)h->n * h->P, false, s));
+    else
+      SG_TRY_CUDA(cudaMemcpyAsync(U[i], h->fx, (size_t)h->n * h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   SG_TRY_CUDA(cudaStreamSynchronize(s));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -453,9 +467,7 @@ int sg_batch_create(int count, sg_problem* const* problems, sg_batch** out) {
   return SG_OK;
 }
 
-int sg_batch_solve(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts* opts,
-                   sg_solve_stats* stats, void* stream) {
-  set_error("");
+static int check_batch_call(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts* opts) {
   if (!b || !F || !U || !opts) {
     set_error("sg_batch_solve: invalid arguments");
     return SG_ERR_INVALID_ARG;
@@ -469,7 +481,21 @@ int sg_batch_solve(sg_batch* b, const double* const* F, double* const* U, const 
       set_error("sg_batch_solve: invalid buffers for system %zu", i);
       return SG_ERR_INVALID_ARG;
     }
+  return SG_OK;
+}
+
+int sg_batch_solve(sg_batch* b, const double* const* F, double* const* U, const sg_solve_opts* opts,
+                   sg_solve_stats* stats, void* stream) {
+  set_error("");
+  SG_TRY(check_batch_call(b, F, U, opts));
   return batch_solve(b, F, U, *opts, stats, (cudaStream_t)stream);
+}
+
+int sg_batch_solve_host(sg_batch* b, const double* const* F_host, double* const* U_host, const sg_solve_opts* opts,
+                        sg_solve_stats* stats, void* stream) {
+  set_error("");
+  SG_TRY(check_batch_call(b, F_host, U_host, opts));
+  return batch_solve(b, F_host, U_host, *opts, stats, (cudaStream_t)stream, true);
 }
 
 void sg_batch_destroy(sg_batch* b) {

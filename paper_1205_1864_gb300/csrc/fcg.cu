@@ -352,7 +352,7 @@ int solve_collect(sg_problem* h, const sg_solve_opts& o, sg_solve_stats* st, dou
 // cudaMemcpyAsync. After the solve's kernels, the copy engine moved a 2.09 GB
 // block in 130-147 ms where the SMs took 10-12 ms (the link's rate, about
 // 210 GB/s), so the SMs do it.
-static int copy_host(sg_problem* h, const double* src, double* dst, size_t n, bool to_device, cudaStream_t s) {
+int copy_host(sg_problem* h, const double* src, double* dst, size_t n, bool to_device, cudaStream_t s) {
   const void* host = to_device ? (const void*)src : (const void*)dst;
   cudaPointerAttributes at;
   const bool pinned = cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost &&

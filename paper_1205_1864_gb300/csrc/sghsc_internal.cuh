@@ -315,6 +315,10 @@ int solve_collect(sg_problem* h, const sg_solve_opts& o, sg_solve_stats* st, dou
 int check_solve_opts(const sg_problem* h, const sg_solve_opts* opts);
 
 // ---- small elementwise kernels (vec.cu) ----
+// n doubles between a host block (src when to_device, else dst) and a device
+// block: page-locked host memory by a kernel through its device mapping,
+// other host memory by cudaMemcpyAsync (fcg.cu)
+int copy_host(sg_problem* h, const double* src, double* dst, size_t n, bool to_device, cudaStream_t s);
 // dst = src, n doubles, by a kernel (either side may be page-locked host memory)
 int launch_copy64(const double* src, double* dst, long long n, int num_sms, cudaStream_t s);
 int launch_cast(const void* src, int src_t, int lds, void* dst, int dst_t, int ldd, int rows,

@@ -115,3 +115,20 @@ def test_autotune_keeps_the_product_exact(lib):
     # 80k unknowns: the oracle checks the FP64 residual instead of a direct solve
     res = np.linalg.norm(F - so.sg_apply(A, G, _np(Us))) / np.linalg.norm(F)
     assert res <= 1.5e-10
+
+
+def test_batch_on_host_blocks_matches_device_blocks(lib, systems):
+    """SGBatch.solve_host (pinned blocks moved by the library's kernels, and
+    pageable ones by the copy engine) gives the device-block solve's bits."""
+    import torch
+    b = lib.SGBatch([s["h"] for s in systems])
+    Ud, _ = b.solve([_t(s["F"]) for s in systems], _opts(lib))
+    for pinned in (True, False):
+        Fh = [torch.tensor(s["F"], dtype=torch.float64) for s in systems]
+        Uh = [torch.empty_like(F) for F in Fh]
+        if pinned:
+            Fh, Uh = [F.pin_memory() for F in Fh], [U.pin_memory() for U in Uh]
+        Uh, st = b.solve_host(Fh, _opts(lib), Uh)
+        for a, c, s in zip(Uh, Ud, st):
+            assert s.status == 0 and np.array_equal(a.numpy(), _np(c))
+    b.close()
