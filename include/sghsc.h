@@ -288,6 +288,8 @@ int sg_inner_cluster(const sg_problem* h);
  * the rows per block; taken first when all ceil(w/4) of them are resident),
  * 2 the cluster solver with the finest grid in global memory and the coarse
  * grids in shared memory (two blocks per SM, for batches too wide for 1).
+ * After sg_autotune, the solver it timed fastest for that width (one of those
+ * eligible); else the first eligible of 3, 1, 2, then 0.
  * h NULL or w <= 0: 0. */
 int sg_inner_path(const sg_problem* h, int w, int dtype);
 
@@ -337,15 +339,22 @@ int sg_solve_host(sg_problem* h, const double* F_host, double* U_host, const sg_
  * full SG product in FP64 and FP32, and separately of the outer solver's fused
  * product (SG product + CG update + p.q, in FP64 and in its double-float
  * variant, sg_prec_opts.df64), each in two forms, on this problem
- * and keep the fastest for all later calls. The forms: the pair form sums
- * each distinct (k, j) of the couplings once per row and keeps those sums in
- * shared memory (fewer multiply-adds); the gather form sums per coupling (no
- * extra shared memory). Allocates two temporary n x P blocks and, if absent,
- * the outer solve buffers; invalidates the handle's cached solve graphs. */
+ * and keep the fastest for all later calls (products that take a fixed-shape
+ * kernel -- the FP32 row kernel, the staged double-float kernel -- are not
+ * timed). The forms: the pair form sums each distinct (k, j) of the couplings
+ * once per row and keeps those sums in shared memory (fewer multiply-adds);
+ * the gather form sums per coupling (no extra shared memory). Where several
+ * inner solvers can run a degree level's FP32 batch (grids up to 127 x 127:
+ * the stand-alone kernels, the 8- and 16-CTA cluster solvers, the wide one),
+ * each is timed on a batch of that width (two fixed PCG iterations) and the
+ * fastest is kept (sg_inner_path reports it). Allocates temporary blocks and,
+ * if absent, the outer solve buffers; invalidates the handle's cached solve
+ * graphs. */
 int sg_autotune(sg_problem* h, void* stream);
-/* Results are cached per problem class (device, n, nnz, M, p, family and the
- * longest row of the pattern): a later handle of a class already tuned in this
- * process takes the cached shapes without timing anything. */
+/* Results are cached per problem class (device, n, nnz, M, p, family, the
+ * longest row of the pattern and the coefficient degree): a later handle of a
+ * class already tuned in this process takes the cached choices without timing
+ * anything. */
 /* Block sizes chosen by sg_autotune (0: not tuned, the built-in choice). */
 int sg_autotune_result(const sg_problem* h, int* threads_f64, int* threads_f32);
 /* Block size chosen for the outer solver's fused product (0: the built-in 256). */
