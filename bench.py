@@ -85,12 +85,12 @@ def _peaks():
 # (L2 flushed before it, as before each timed launch here).
 K1_TRAFFIC = {"cfg2": 35833856 + 119040}
 # DRAM bytes of one double-float SG-product launch (sg_apply SG_F32_ACCDF64):
-# dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture on the 255^2
-# grid of the same operator (444059136 + 475183872 bytes, L2 flushed before
-# the launch), scaled by the rows to the 511^2 grid (x 261121 / 65025; the
-# traffic is per row: the row's values, its neighbour rows of U from L2, its
-# row of Y).
-DF_TRAFFIC = {"cfg5": int((444059136 + 475183872) * 261121 / 65025)}
+# dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of the current
+# kernel on the 255^2 grid of the same operator (447176192 + 475274752 bytes,
+# L2 flushed before the launch), scaled by the rows to the 511^2 grid
+# (x 261121 / 65025; the traffic is per row: the row's values, its neighbour
+# rows of U from L2, its row of Y).
+DF_TRAFFIC = {"cfg5": int((447176192 + 475274752) * 261121 / 65025)}
 # FP32 operations of one double-float multiply-add a * x + s (a double-float,
 # x FP32): the exact product (FMUL, FFMA for its error, FFMA for a.lo x) and
 # the two-sum accumulation (six FADD for the hi parts and their error, two
