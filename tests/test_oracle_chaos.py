@@ -168,3 +168,31 @@ def test_gpc_matrices_reduce_to_the_linear_expansion(M, p):
         for j, l in zip(C.row, C.col):
             dj, dl, dg = alpha[j].sum(), alpha[l].sum(), g.sum()
             assert abs(dj - dl) <= dg <= dj + dl
+
+
+@pytest.mark.parametrize("M,p,q", [(2, 2, 4), (3, 1, 2), (1, 3, 6)])
+def test_gpc_triple_products_match_brute_force_quadrature(M, p, q):
+    """(G_i)_{jl} = E[psi_i psi_j psi_l] for every coefficient polynomial psi_i
+    of total degree <= q (the lognormal case expands the coefficient to
+    q = 2p), by tensor Gauss-Hermite quadrature of the M-dimensional integrand
+    with the polynomials evaluated from numpy; the rule is exact for the
+    integrand's degree q + 2p per coordinate."""
+    alpha, _ = chaos.multi_indices(M, p)
+    gamma, _ = chaos.multi_indices(M, q)
+    Gq = chaos.gpc_g_matrices(M, p, q)
+    assert len(Gq) == math.comb(M + q, M)
+    x1, w1 = _quad_1d(chaos.HERMITE, p + q // 2 + 2)
+    pts = np.array(list(itertools.product(x1, repeat=M)))
+    wts = np.prod(np.array(list(itertools.product(w1, repeat=M))), axis=1)
+
+    def table(idx):
+        out = np.ones((idx.shape[0], pts.shape[0]))
+        for j in range(idx.shape[0]):
+            for i in range(M):
+                out[j] *= _psi_1d(chaos.HERMITE, idx[j, i], pts[:, i])
+        return out
+
+    psi, phi = table(alpha), table(gamma)
+    for i in range(gamma.shape[0]):
+        E = (psi * wts * phi[i]) @ psi.T
+        assert np.allclose(E, Gq[i].toarray(), rtol=0, atol=1e-10 * max(1.0, np.abs(E).max())), i

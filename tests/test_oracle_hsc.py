@@ -172,3 +172,31 @@ def test_general_prec_variants_match_the_paper_formula():
     Dinv = np.linalg.inv(D)
     exact = hsc.general_prec(A0, B, C, np.linalg.inv(A0), Dinv, Dinv, Dinv)
     assert np.abs(exact - hsc.block_inverse(A0, B, C, D, S_inv=np.linalg.inv(A0))).max() <= 1e-12 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("M,p", [(2, 2), (2, 3), (3, 2)])
+def test_algorithm1_gpc_equals_recursive_block_inverse(M, p):
+    """Sec. 6, lognormal case (Remark K-L): with the coefficient expanded to
+    degree 2p in Hermite chaos the global matrix is block dense, B_l and C_l
+    couple degree l with every lower degree and D_l couples the chaos
+    polynomials of one degree. Algorithm 1 with the assembled D_l solves equals
+    the dense recursion of eq. (block-inverse) with S_{l-1} -> A_{l-1}, and
+    M_bGS equals its closed form (D + U)^{-1} D (D + L)^{-1}."""
+    prob = S.make_lognormal_problem(4, M, 0.5, 0.5, 2 * p)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.gpc_g_matrices(M, p, 2 * p)
+    _, off = chaos.multi_indices(M, p)
+    n, P = prob.n, G[0].shape[0]
+    # the general case: D_p is not block diagonal and B_p reaches degree p - 2
+    Dp = [g[off[p]:off[p + 1], off[p]:off[p + 1]].toarray() for g in G]
+    assert any(np.abs(d - np.diag(np.diag(d))).max() > 0 for d in Dp)
+    assert any(g[off[p - 2]:off[p - 1], off[p]:off[p + 1]].nnz for g in G)
+    K = so.global_matrix_chaos_major(A, G).toarray()
+    R = S.random_block(n, P, seed=31)
+    Z = hsc.hsc_apply(A, G, off, R, general=True)
+    Md = hsc.hsc_dense_recursive(K, n, off)
+    z = (Md @ R.T.ravel()).reshape(P, n).T
+    assert np.abs(Z - z).max() <= 1e-11 * np.abs(z).max()
+    Mb = hsc.bgs_dense(K, n, P)
+    ref = (Mb @ R.T.ravel()).reshape(P, n).T
+    assert np.abs(hsc.bgs_apply(A, G, R) - ref).max() <= 1e-11 * np.abs(ref).max()

@@ -174,3 +174,70 @@ def test_paper_table6_lognormal_soft(row):
 def test_paper_table7_lognormal_soft(row):
     p, _, _, _, m_it, m_k, b_it, b_k, h_it, h_k = row
     lognormal_soft(_lognormal_run(4, int(p), 1.0), m_it, m_k, b_it, b_k, h_it, h_k)
+
+
+def test_flexible_cg_keeps_consecutive_directions_conjugate():
+    """Flexible CG (Sec. 5, for a preconditioner that changes from one
+    application to the next): the flexible beta z_{k+1}^T (r_{k+1} - r_k) /
+    rho_k is the one that makes each new search direction A-conjugate to the
+    previous one, p_{k+1}^T A p_k = 0, whatever the preconditioner did; the
+    standard beta rho_{k+1} / rho_k does not under a changing preconditioner.
+    The search directions are the operator's inputs, recorded as it is called."""
+    m = 30
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((m, m))
+    A = X @ X.T / m + np.eye(m)
+    f = rng.standard_normal(m)
+
+    def run(flexible):
+        dirs, prng = [], np.random.default_rng(8)
+
+        def apply_A(v):
+            dirs.append(v.copy())
+            return A @ v
+
+        def apply_M(r):                                # a different SPD operator at every call
+            Y = prng.standard_normal((m, m))
+            return (Y @ Y.T / m + 0.5 * np.eye(m)) @ r
+
+        x, info = krylov.fcg(apply_A, f, apply_M, tol=1e-12, maxit=12, flexible=flexible)
+        cos = [abs(a @ A @ b) / np.sqrt((a @ A @ a) * (b @ A @ b)) for a, b in zip(dirs[1:], dirs[:-1])]
+        return x, info, cos
+
+    x, info, cos = run(True)
+    assert len(cos) >= 8 and max(cos) < 1e-10
+    # the recursively updated residual is the true one
+    assert info["res"][-1] == pytest.approx(np.linalg.norm(f - A @ x) / np.linalg.norm(f), rel=1e-6)
+    _, _, cos_std = run(False)
+    assert max(cos_std) > 1e-3
+
+
+def test_pcg_iterates_minimise_the_energy_error_over_the_krylov_space():
+    """Brute force of what k steps of preconditioned CG from zero compute: the
+    x in span{M b, (M A) M b, ..., (M A)^{k-1} M b} that minimises the A-norm
+    of the error, i.e. the Galerkin solution x = V y with V^T A V y = V^T b
+    for a basis V of that space. Checked for the inner column PCG with a fixed
+    iteration count and for the outer CG (standard and flexible, which coincide
+    for a fixed preconditioner), with an SPD preconditioner that is neither the
+    identity nor A^{-1}."""
+    m = 24
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    A = (Q * np.linspace(1.0, 40.0, m)) @ Q.T
+    Y = rng.standard_normal((m, m))
+    Mp = Y @ Y.T / m + 0.3 * np.eye(m)
+    b = rng.standard_normal(m)
+    for k in range(1, 7):
+        cols = [Mp @ b]
+        for _ in range(k - 1):
+            cols.append(Mp @ (A @ cols[-1]))
+        V, _ = np.linalg.qr(np.array(cols).T)
+        x_ref = V @ np.linalg.solve(V.T @ A @ V, V.T @ b)
+        scale = np.abs(x_ref).max()
+        X, it = krylov.pcg_columns(lambda v: A @ v, b[:, None], lambda r: Mp @ r, tol=0.0, maxit=k, fixed_iters=k)
+        assert it[0] == k
+        assert np.abs(X[:, 0] - x_ref).max() <= 1e-9 * scale, k
+        for flexible in (False, True):
+            x, info = krylov.fcg(lambda v: A @ v, b, lambda r: Mp @ r, tol=0.0, maxit=k, flexible=flexible)
+            assert info["iters"] == k
+            assert np.abs(x - x_ref).max() <= 1e-9 * scale, (k, flexible)
