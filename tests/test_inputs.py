@@ -117,3 +117,103 @@ def test_lognormal_gpc_coefficients_reproduce_the_field():
     import scipy.sparse as sp
     A0 = sp.csr_matrix((prob.vals[:, 0], prob.colidx, prob.rowptr), shape=(prob.n, prob.n))
     assert abs(A0 - A0.T).max() < 1e-14 and np.all(A0.diagonal() > 0)
+
+
+def _q1_entry(ne, kappa, i, j, dx, dy, npts=2):
+    """int kappa grad N_r . grad N_c over the unit square for the interior
+    nodes r = (i, j) and c = (i + dx, j + dy) of the ne x ne Q1 grid, by
+    npts x npts Gauss-Legendre quadrature on every element of the common
+    support, with the bilinear hats written out: N(x, y) = t(x) t(y) with
+    t(s) = 1 - |s - s_node| / h."""
+    from numpy.polynomial import legendre as Leg
+    h = 1.0 / ne
+    t, w = Leg.leggauss(npts)
+    tot = 0.0
+    for ex in set((i - 1, i)) & set((i + dx - 1, i + dx)):
+        for ey in set((j - 1, j)) & set((j + dy - 1, j + dy)):
+            X, Y = np.meshgrid((ex + (t + 1) / 2) * h, (ey + (t + 1) / 2) * h, indexing="ij")
+            W = np.outer(w, w) * h * h / 4
+
+            def grad(a, b):
+                sx, sy = X - a * h, Y - b * h
+                hx, hy = 1 - np.abs(sx) / h, 1 - np.abs(sy) / h
+                return -np.sign(sx) / h * hy, -np.sign(sy) / h * hx
+
+            gr, gc = grad(i, j), grad(i + dx, j + dy)
+            tot += float(np.sum(W * kappa(X, Y) * (gr[0] * gc[0] + gr[1] * gc[1])))
+    return tot
+
+
+def test_kl_stiffness_matrices_match_direct_integration():
+    """Eq. (global-system): A_k = sigma s_k int phi_k grad N_r . grad N_c with
+    phi_k(x, y) = e_a(x) e_b(y) the k-th 2-D KL pair and s_k = sqrt(lambda_k),
+    and A_0 = a_mean int grad N_r . grad N_c: every entry of a few rows against
+    the integral written out here in physical coordinates with the generator's
+    quadrature (2 x 2 Gauss points per element), so the two agree to rounding;
+    with 6 x 6 points they agree to the quadrature error (below 1 %)."""
+    ne, M, sigma, L, a_mean = 8, 4, 0.3, 0.5, 1.7
+    prob = S.make_problem(ne, M, sigma, L, a_mean=a_mean)
+    kl = S.kl_2d(L, M)
+    assert np.allclose(prob.sqrt_lambda, [math.sqrt(lam) for lam, _, _ in kl], rtol=0, atol=1e-15)
+    assert any(mx is not my for _, mx, my in kl)          # some phi_k not symmetric in x and y
+    m = ne - 1
+    for (i, j) in [(1, 1), (3, 4), (6, 2)]:
+        r = (j - 1) * m + (i - 1)
+        for k in range(M + 1):
+            if k == 0:
+                kap = lambda X, Y: a_mean + 0 * X
+            else:
+                lam, mx, my = kl[k - 1]
+                kap = lambda X, Y, lam=lam, mx=mx, my=my: sigma * math.sqrt(lam) * S.eval_kl_1d(mx, X) * S.eval_kl_1d(my, Y)
+            got = {int(c): prob.vals[e, k] for e, c in zip(range(prob.rowptr[r], prob.rowptr[r + 1]),
+                                                          prob.colidx[prob.rowptr[r]:prob.rowptr[r + 1]])}
+            want = {}
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if 1 <= i + dx <= m and 1 <= j + dy <= m:
+                        want[(j + dy - 1) * m + (i + dx - 1)] = _q1_entry(ne, kap, i, j, dx, dy)
+            assert set(got) == set(want)
+            scale = max(abs(v) for v in want.values())
+            for c in want:
+                assert abs(got[c] - want[c]) <= 1e-13 * scale, (i, j, k, c, got[c], want[c])
+                fine = _q1_entry(ne, kap, i, j, c % m + 1 - i, c // m + 1 - j, npts=6)
+                assert abs(got[c] - fine) <= 1e-2 * scale, (i, j, k, c, got[c], fine)
+
+
+def test_lognormal_matrices_expand_the_stiffness_of_exp_g():
+    """Sec. 6, lognormal case: sum_i A_i psi_i(xi), with the generator's gPC
+    matrices up to degree q, approaches the stiffness matrix of the coefficient
+    exp(g(x, xi)) itself, g = mu_g + sigma_g sum_k s_k phi_k(x) xi_k with
+    sigma_g^2 = ln(1 + CoV^2) and mu_g = -sigma_g^2 / 2 (mean of exp(g) one),
+    assembled here entry by entry by direct integration with the generator's
+    2 x 2 Gauss points per element; what remains is the truncation of the
+    expansion at degree q."""
+    from numpy.polynomial import hermite_e as He
+    ne, M, cov, L, q = 4, 2, 0.8, 0.5, 12
+    prob = S.make_lognormal_problem(ne, M, cov, L, q)
+    sig2 = math.log(1 + cov * cov)
+    kl = S.kl_2d(L, M)
+    xi = np.array([0.7, -1.1])
+
+    def kap(X, Y):
+        g = -0.5 * sig2 + 0.0 * X
+        for k, (lam, mx, my) in enumerate(kl):
+            g = g + math.sqrt(sig2) * math.sqrt(lam) * S.eval_kl_1d(mx, X) * S.eval_kl_1d(my, Y) * xi[k]
+        return np.exp(g)
+
+    gam = S._graded_indices(M, q)
+    assert prob.vals.shape[1] == len(gam)
+    psi = np.array([np.prod([He.hermeval(xi[k], [0] * g[k] + [1]) / math.sqrt(math.factorial(g[k]))
+                             for k in range(M)]) for g in gam])
+    Axi = prob.vals @ psi
+    m = ne - 1
+    for (i, j) in [(1, 1), (2, 2), (3, 1)]:
+        r = (j - 1) * m + (i - 1)
+        scale = 0.0
+        errs = []
+        for e in range(prob.rowptr[r], prob.rowptr[r + 1]):
+            c = int(prob.colidx[e])
+            want = _q1_entry(ne, kap, i, j, c % m + 1 - i, c // m + 1 - j)
+            scale = max(scale, abs(want))
+            errs.append(abs(Axi[e] - want))
+        assert max(errs) <= 1e-8 * scale, (i, j, max(errs) / scale)

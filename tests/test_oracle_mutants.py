@@ -1,11 +1,15 @@
-"""Planted mistakes in the oracle: each case edits one line of one oracle
+"""Planted mistakes in the oracle and in the seeded input generator that the
+oracle and the CUDA path both consume: each case edits one line of one
 function in memory (a dropped term, a wrong sign, a wrong index or operand
 order, a loop run the wrong way), installs the edited function in place of the
 original for the duration of the case, and runs the pins of that module
 (the ``-m "not gpu"`` tests that tie it to closed forms, brute force, the
 paper's printed numbers and identities of the mathematics). The case passes
 only if one of those pins fails with an assertion, i.e. the pins are strong
-enough to see that mistake. Nothing here touches the CUDA path.
+enough to see that mistake. Nothing here touches the CUDA path. A mistake in
+the input generator would reach both sides of a parity test alike, so its
+pins (the KL pairs against a Nystrom discretisation, the stiffness matrices
+against their integrals written out) are what keep the workload the paper's.
 
 The edit is textual on the function's own source, so every case states the
 exact fragment it replaces; a fragment that no longer occurs (the oracle was
@@ -20,8 +24,10 @@ from typing import Callable, Sequence
 
 import pytest
 
+import sg_inputs
 from oracle import chaos, gmg, hsc, krylov, qoi, sg_operator
 
+import test_inputs as ti
 import test_oracle_chaos as tc
 import test_oracle_gmg as tg
 import test_oracle_hsc as th
@@ -79,6 +85,15 @@ GMG_PINS = (
 )
 QOI_PINS = (
     lambda: tq.test_adjoint_gradient_matches_central_differences(),
+)
+INPUT_PINS = (
+    lambda: ti.test_kl_2d_products_sorted(),
+    lambda: ti.test_q1_mean_matrix_is_textbook_stencil(),
+    lambda: ti.test_kl_stiffness_is_weighted_laplacian(),
+    lambda: tq.test_mass_matrix_integrates_constants(),
+    lambda: ti.test_kl_1d_closed_form_matches_nystrom(0.5),
+    lambda: ti.test_kl_stiffness_matrices_match_direct_integration(),
+    lambda: ti.test_lognormal_matrices_expand_the_stiffness_of_exp_g(),
 )
 
 
@@ -239,6 +254,33 @@ MUTANTS = [
            "Q without the mass matrix"),
     Mutant("k-products-operand", qoi, "k_resolved_products", "sg_apply([Ak], [Gk], U)",
            "sg_apply([Ak], [Gk], Lam)", QOI_PINS, "h_k = <Lam, A_k Lam G_k^T>"),
+    # --- seeded inputs: KL expansion (eq. (cov), (KL-expansion)), Q1 assembly, lognormal gPC coefficient
+    Mutant("kl-eigenvalue", sg_inputs, "kl_1d", "out.append((2 * c / (w * w + c * c), w, 0, nrm))",
+           "out.append((c / (w * w + c * c), w, 0, nrm))", INPUT_PINS, "even KL eigenvalues halved"),
+    Mutant("kl-odd-normalisation", sg_inputs, "kl_1d", "a - math.sin(2 * w * a) / (2 * w)",
+           "a + math.sin(2 * w * a) / (2 * w)", INPUT_PINS, "odd KL modes normalised with the even modes' norm"),
+    Mutant("kl-2d-ascending", sg_inputs, "kl_2d", "-round(t[0], 14)", "round(t[0], 14)", INPUT_PINS,
+           "2-D KL pairs kept from the smallest eigenvalue"),
+    Mutant("q1-gradient", sg_inputs, "_shape", ", sa * (1 + sb * eta) / 4.0", ", sa * (1 + sb * eta) / 2.0",
+           INPUT_PINS, "x derivative of the bilinear shape function twice too large"),
+    Mutant("q1-mass-table", sg_inputs, "_element_tables", "Mm[g, p, q] = vals[p][0] * vals[q][0]",
+           "Mm[g, p, q] = vals[p][0]", INPUT_PINS, "mass integrand N_p instead of N_p N_q"),
+    Mutant("stencil-slot-xy", sg_inputs, "_assemble_stencils", "slot = (bq - bp + 1) * 3 + (aq - ap + 1)",
+           "slot = (aq - ap + 1) * 3 + (bq - bp + 1)", INPUT_PINS, "stencil offsets with x and y exchanged"),
+    Mutant("csr-column-xy", sg_inputs, "_interior_csr", "cols.append((cy - 1) * m + (cx - 1))",
+           "cols.append((cx - 1) * m + (cy - 1))", INPUT_PINS, "column nodes numbered y fastest"),
+    Mutant("load-scale", sg_inputs, "make_problem", "f0 = np.full(n, h * h)", "f0 = np.full(n, h)", INPUT_PINS,
+           "load vector of f = 1 scaled by h instead of h^2"),
+    Mutant("mass-scale", sg_inputs, "make_problem", "h * h / 4.0)", "h * h)", INPUT_PINS,
+           "mass matrix without the reference-element Jacobian"),
+    Mutant("gauss-point-location", sg_inputs, "make_problem", "gx = np.stack([(ex + (1 + xi) / 2) * h",
+           "gx = np.stack([(ex + xi / 2) * h", INPUT_PINS, "KL functions evaluated at shifted x Gauss points"),
+    Mutant("kl-mode-xy", sg_inputs, "make_problem", "fy[:, None, :] * fx[None, :, :]",
+           "fx[:, None, :] * fy[None, :, :]", INPUT_PINS, "phi_k(x, y) = e_a(y) e_b(x)"),
+    Mutant("kl-amplitude", sg_inputs, "make_problem", "kappa[k] = sigma * s[k - 1] *",
+           "kappa[k] = sigma * s[k - 1] ** 2 *", INPUT_PINS, "KL term scaled by lambda_k instead of sqrt(lambda_k)"),
+    Mutant("lognormal-mean", sg_inputs, "make_lognormal_problem", "sig_g, mu_g = math.sqrt(sig2), -0.5 * sig2",
+           "sig_g, mu_g = math.sqrt(sig2), 0.0", INPUT_PINS, "Gaussian field without the -sigma_g^2/2 shift"),
 ]
 
 
