@@ -19,6 +19,7 @@ def test_multi_index_table_is_graded_complete_and_ordered(M, p):
     alpha, off = chaos.multi_indices(M, p)
     # eq. (gPC-u): (M+p)!/(M!p!) polynomials
     assert alpha.shape == (math.comb(M + p, M), M)
+    assert chaos.chaos_count(M, p) == alpha.shape[0]
     assert off[-1] == alpha.shape[0]
     deg = alpha.sum(axis=1)
     for d in range(p + 1):

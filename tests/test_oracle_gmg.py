@@ -71,3 +71,33 @@ def test_vcycle_columns_independent():
     Xb = gmg.vcycle(lv, B)
     for s in range(3):
         assert np.abs(Xb[:, s] - gmg.vcycle(lv, B[:, s])).max() < 1e-15
+
+
+@pytest.mark.parametrize("ne,nu,omega", [(8, 2, 0.8), (16, 1, 0.7), (16, 3, 0.6)])
+def test_vcycle_equals_error_propagation_recursion(ne, nu, omega):
+    """The V-cycle as a matrix, from the textbook recursion of its error
+    propagation rather than the procedure: with the damped Jacobi operator
+    S_g = I - omega D_g^{-1} A_g, nu smoothing steps on each side of the coarse
+    correction and the next grid's cycle E_{g+1} standing in for its exact
+    solve, E_g = S_g^nu (I - P_g (I - E_{g+1}) A_{g+1}^{-1} P_g^T A_g) S_g^nu,
+    E = 0 on the coarsest grid (solved exactly), and the cycle is
+    V_g = (I - E_g) A_g^{-1}."""
+    prob = S.make_problem(ne, 2, 0.3, 0.5)
+    A0 = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)[0]
+    lv = gmg.hierarchy(A0, ne)
+
+    def E(g):
+        Ag = lv[g].A.toarray()
+        if g == len(lv) - 1:
+            return np.zeros_like(Ag)
+        Sg = np.eye(Ag.shape[0]) - omega * (Ag / np.diag(Ag)[:, None])
+        Pg = lv[g].P.toarray()
+        Ac = lv[g + 1].A.toarray()
+        cgc = np.eye(Ag.shape[0]) - Pg @ (np.eye(Ac.shape[0]) - E(g + 1)) @ np.linalg.solve(Ac, Pg.T @ Ag)
+        Sn = np.linalg.matrix_power(Sg, nu)
+        return Sn @ cgc @ Sn
+
+    Ad = A0.toarray()
+    V_ref = (np.eye(prob.n) - E(0)) @ np.linalg.inv(Ad)
+    V = gmg.vcycle(lv, np.eye(prob.n), nu=nu, omega=omega)
+    assert np.abs(V - V_ref).max() <= 1e-11 * np.abs(V_ref).max()

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import sg_inputs as S
-from oracle import chaos, hsc, sg_operator as so
+from oracle import chaos, hsc, krylov, sg_operator as so
 
 
 def _setup(ne=4, M=2, p=3, sigma=0.4, corr=0.5):
@@ -200,3 +200,54 @@ def test_algorithm1_gpc_equals_recursive_block_inverse(M, p):
     Mb = hsc.bgs_dense(K, n, P)
     ref = (Mb @ R.T.ravel()).reshape(P, n).T
     assert np.abs(hsc.bgs_apply(A, G, R) - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("M,p", [(2, 2), (3, 2)])
+def test_schur_reduced_iteration_is_preconditioned_by_algorithm1(M, p):
+    """Sec. 5, eq. (global-Schur-system): the reduced iteration on S_{p-1} is
+    preconditioned by Algorithm 1 on the levels 0..p-1; run to full accuracy
+    on a tiny system its Lanczos estimate is the condition number of
+    M_{p-1} S_{p-1} formed densely (eq. (block-inverse) recursion for M_{p-1},
+    S_{p-1} = A_{p-1} - B_p D_p^{-1} C_p from the assembled matrix). The Ritz
+    values lie inside the spectrum, so the estimate is at most that number
+    and, after the few iterations a tiny system needs, within 1 % below it;
+    the mean-based preconditioner would give about twice the value."""
+    prob = S.make_problem(4, M, 0.4, 0.5)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(M, p)
+    _, off = chaos.multi_indices(M, p)
+    n = prob.n
+    F = S.random_block(n, G[0].shape[0], seed=12)
+    _, info = hsc.schur_reduced_solve(A, G, off, F, tol=1e-14, maxit=200)
+    K = so.global_matrix_chaos_major(A, G).toarray()
+    e = n * off[p]
+    Sd = K[:e, :e] - K[:e, e:] @ np.linalg.solve(K[e:, e:], K[e:, :e])
+    Mr = hsc.hsc_dense_recursive(K[:e, :e], n, off[:p + 1])
+    ev = np.sort(np.linalg.eigvals(Mr @ Sd).real)
+    kappa = ev[-1] / ev[0]
+    est = krylov.lanczos_kappa(info["alpha"], info["beta"])
+    assert 0.99 * kappa <= est <= kappa * (1 + 1e-9)
+    evm = np.sort(np.linalg.eigvals(np.kron(np.eye(off[p]), np.linalg.inv(A[0].toarray())) @ Sd).real)
+    assert evm[-1] / evm[0] > 1.5 * kappa
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_schur_constants_are_the_spectrum_of_one_level(M):
+    """Eq. (AS-ineq) at one level (p = 1): A_1 = L diag(S_0, D_1) L^T with
+    M_1 = L^{-T} diag(A_0^{-1}, D_1^{-1}) L^{-1} gives spec(M_1 A_1) =
+    spec(A_0^{-1} S_0) U {1}, the eigenvalue 1 once per degree-1 unknown; so
+    the pencil constants (c_{0,1}, c_{0,2}) are the smallest and the largest
+    eigenvalue of M_1 A_1 once the unit ones are set aside."""
+    prob = S.make_problem(4, M, 0.5, 0.5)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    G = chaos.g_matrices(M, 1)
+    _, off = chaos.multi_indices(M, 1)
+    n = prob.n
+    K = so.global_matrix_chaos_major(A, G).toarray()
+    ev = np.sort(np.linalg.eigvals(hsc.hsc_dense_recursive(K, n, off) @ K).real)
+    unit = np.abs(ev - 1.0) < 1e-9
+    assert unit.sum() == n * M
+    rest = ev[~unit]
+    (c1, c2), = hsc.schur_constants(K, n, off)
+    assert rest.size == n and c2 < 1 - 1e-6
+    assert c1 == pytest.approx(rest[0], rel=1e-10) and c2 == pytest.approx(rest[-1], rel=1e-10)

@@ -241,3 +241,27 @@ def test_pcg_iterates_minimise_the_energy_error_over_the_krylov_space():
             x, info = krylov.fcg(lambda v: A @ v, b, lambda r: Mp @ r, tol=0.0, maxit=k, flexible=flexible)
             assert info["iters"] == k
             assert np.abs(x - x_ref).max() <= 1e-9 * scale, (k, flexible)
+
+
+def test_fcg_initial_guess_zero_right_hand_side_and_breakdown():
+    """The edges of the outer CG: a zero right-hand side is solved at entry
+    (x = 0, no iteration); an initial guess starts from r = f - A x0 (the exact
+    solution needs no iteration, a perturbed one converges to the same x); a
+    direction with p^T A p <= 0 (an indefinite operator) stops the iteration
+    with the breakdown flag; no CG step gives the condition estimate 1."""
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((10, 10))
+    A = X @ X.T + 10 * np.eye(10)
+    f = rng.standard_normal(10)
+    x, info = krylov.fcg(lambda v: A @ v, np.zeros(10), None, tol=1e-10)
+    assert info["converged"] and info["iters"] == 0 and not np.any(x)
+    xs = np.linalg.solve(A, f)
+    x, info = krylov.fcg(lambda v: A @ v, f, None, tol=1e-10, x0=xs)
+    assert info["converged"] and info["iters"] == 0 and info["res"][0] < 1e-12
+    x0 = xs + 0.1 * rng.standard_normal(10)
+    x, info = krylov.fcg(lambda v: A @ v, f, None, tol=1e-12, x0=x0)
+    assert info["res"][0] == pytest.approx(np.linalg.norm(f - A @ x0) / np.linalg.norm(f), rel=1e-12)
+    assert info["converged"] and np.abs(x - xs).max() < 1e-10 * np.abs(xs).max()
+    x, info = krylov.fcg(lambda v: np.array([1.0, -2.0]) * v, np.array([1.0, 1.0]), None, tol=1e-10)
+    assert info.get("breakdown") and not info["converged"] and info["iters"] == 0
+    assert krylov.lanczos_kappa([], []) == 1.0

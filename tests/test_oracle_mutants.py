@@ -56,6 +56,7 @@ OPERATOR_PINS = (
     lambda: to.test_row_sampled_products_match_the_explicit_global_matrix(),
     lambda: to.test_direct_solve_residual_and_linearity(),
     lambda: to.test_global_matrix_symmetric_positive_definite_cfg1_small(),
+    lambda: to.test_kl_matrices_hold_each_term_column(),
 )
 HSC_PINS = (
     lambda: th.test_block_inverse_with_true_schur_is_exact_inverse(),
@@ -67,6 +68,8 @@ HSC_PINS = (
     lambda: th.test_bgs_matches_block_triangular_solves(2, 2),
     lambda: th.test_theorem1_spectrum(4, 2, 3, 0.4),
     lambda: th.test_schur_reduced_solve_recovers_the_full_solution(2, 2),
+    lambda: th.test_schur_reduced_iteration_is_preconditioned_by_algorithm1(2, 2),
+    lambda: th.test_schur_constants_are_the_spectrum_of_one_level(2),
 )
 KRYLOV_PINS = (
     lambda: tk.test_cg_on_known_spectrum_and_lanczos_estimate(),
@@ -74,6 +77,7 @@ KRYLOV_PINS = (
     lambda: tk.test_pcg_columns_conventions(),
     lambda: tk.test_flexible_cg_keeps_consecutive_directions_conjugate(),
     lambda: tk.test_pcg_iterates_minimise_the_energy_error_over_the_krylov_space(),
+    lambda: tk.test_fcg_initial_guess_zero_right_hand_side_and_breakdown(),
     lambda: tk.test_fcg_sg_solution_matches_direct_solve(),
 )
 GMG_PINS = (
@@ -82,6 +86,7 @@ GMG_PINS = (
     lambda: tg.test_vcycle_symmetric_positive_definite(),
     lambda: tg.test_vcycle_columns_independent(),
     lambda: tg.test_vcycle_contraction_h_independent(16),
+    lambda: tg.test_vcycle_equals_error_propagation_recursion(8, 2, 0.8),
 )
 QOI_PINS = (
     lambda: tq.test_adjoint_gradient_matches_central_differences(),
@@ -133,9 +138,13 @@ MUTANTS = [
     Mutant("gpc-coefficient-truncated", chaos, "gpc_g_matrices", "gamma, _ = multi_indices(M, q)",
            "gamma, _ = multi_indices(M, min(q, p))", CHAOS_PINS,
            "coefficient expanded to degree p instead of q = 2p"),
+    Mutant("chaos-count", chaos, "chaos_count", "math.comb(M + p, M)", "math.comb(M + p, M - 1)", CHAOS_PINS,
+           "(M+p)!/((M-1)!(p+1)!) polynomials"),
     Mutant("gpc-wrong-index", chaos, "gpc_g_matrices", "int(alpha[l][k])", "int(alpha[j][k])",
            CHAOS_PINS, "second polynomial index read as the first"),
     # --- SG operator (eq. (global-system), (global-matrix), (global-matrix-hierarchy))
+    Mutant("kl-matrix-term-column", sg_operator, "kl_matrices", "vals[:, k]", "vals[:, min(k, 1)]", OPERATOR_PINS,
+           "every A_k with k >= 1 read from the first KL term's values"),
     Mutant("apply-last-term-dropped", sg_operator, "sg_apply", "zip(A, G)", "zip(A[:-1], G[:-1])",
            OPERATOR_PINS, "the k = M term of sum_k A_k U G_k^T left out"),
     Mutant("apply-rows-last-term-dropped", sg_operator, "sg_apply_rows", "zip(A, G)", "zip(A[:-1], G[:-1])",
@@ -196,6 +205,10 @@ MUTANTS = [
     Mutant("schur-recovery", hsc, "schur_reduced_solve",
            "dsolve(F[:, lo:] - _offdiag_apply(A, G, slice(lo, off[p + 1]), slice(0, lo), u_r))",
            "dsolve(F[:, lo:])", HSC_PINS, "u^p recovered without the C_p u_p-1 correction"),
+    Mutant("schur-preconditioner-mean", hsc, "schur_reduced_solve", "hsc_apply(A, sub_G, off_r, R, a0solve=a0)",
+           "mean_apply(A, R, a0)", HSC_PINS, "reduced system preconditioned with the mean-based M_m"),
+    Mutant("schur-constant-upper", hsc, "schur_constants", "out.append((float(mu[0]), float(mu[-1])))",
+           "out.append((float(mu[0]), float(mu[-2])))", HSC_PINS, "c_l,2 read one eigenvalue below the largest"),
     Mutant("bgs-backward-stale", hsc, "bgs_apply", "(fwd[:, l] if l < j else u[:, l])", "fwd[:, l]",
            HSC_PINS, "backward sweep reads the forward values for l > j"),
     Mutant("bgs-forward-upper", hsc, "bgs_apply", "            if l < j:\n", "            if l > j:\n",
@@ -206,6 +219,14 @@ MUTANTS = [
     Mutant("mean-wrong-matrix", hsc, "mean_apply", "A0Solver(A[0])", "A0Solver(A[1])", HSC_PINS,
            "mean-based preconditioner with A_1 instead of A_0"),
     # --- flexible CG, Lanczos estimate, inner PCG (Sec. 5, 6)
+    Mutant("fcg-initial-residual-sign", krylov, "fcg", "r = f - apply_A(x) if x0 is not None",
+           "r = f + apply_A(x) if x0 is not None", KRYLOV_PINS, "initial residual f + A x0"),
+    Mutant("fcg-no-breakdown-check", krylov, "fcg", "if not pq > 0:", "if pq < -1e300:", KRYLOV_PINS,
+           "p^T A p <= 0 not detected"),
+    Mutant("fcg-zero-rhs", krylov, "fcg", "converged=res[0] <= tol", "converged=False", KRYLOV_PINS,
+           "a zero right-hand side iterated instead of solved at entry"),
+    Mutant("lanczos-no-steps", krylov, "lanczos_kappa", "if m == 0:\n        return 1.0", "if m == 0:\n        return 0.0",
+           KRYLOV_PINS, "condition estimate 0 without a CG step"),
     Mutant("fcg-direction", krylov, "fcg", "p = z + beta * p", "p = z + beta * z", KRYLOV_PINS,
            "search direction not conjugated (steepest descent)"),
     Mutant("fcg-beta-denominator", krylov, "fcg", "if flexible else rho_new) / rho",
@@ -241,6 +262,8 @@ MUTANTS = [
     Mutant("vcycle-no-post-smoothing", gmg, "vcycle",
            "x = x + L.P @ xc\n    for _ in range(nu):", "x = x + L.P @ xc\n    for _ in range(0):",
            GMG_PINS, "post-smoothing left out (non-symmetric cycle)"),
+    Mutant("vcycle-coarse-sweeps", gmg, "vcycle", "xc = vcycle(levels, L.P.T @ r, nu, omega, g + 1)",
+           "xc = vcycle(levels, L.P.T @ r, 1, omega, g + 1)", GMG_PINS, "one smoothing step on the coarser grids"),
     Mutant("vcycle-restrict-rhs", gmg, "vcycle", "L.P.T @ r", "L.P.T @ b", GMG_PINS,
            "restriction of b instead of the residual"),
     Mutant("jacobi-no-accumulate", gmg, "vcycle", "x = x + omega * dinv * (b - L.A @ x)",

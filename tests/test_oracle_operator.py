@@ -88,3 +88,19 @@ def test_row_sampled_products_match_the_explicit_global_matrix():
         y = (blk @ X.T.ravel()).reshape(off[lo + 1] - off[lo], n).T
         assert np.allclose(so.level_apply(A, G, off, lo, li, X, rows=rows), y[rows], rtol=0,
                            atol=1e-13 * np.abs(y).max())
+
+
+def test_kl_matrices_hold_each_term_column():
+    """Brute force over the stored nonzeros: (A_k)_{r, c_e} is vals[e, k] for
+    every term k, and nothing else is stored."""
+    prob = S.make_problem(4, 3, 0.3, 0.5)
+    A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
+    assert len(A) == 4
+    for k, Ak in enumerate(A):
+        D = Ak.toarray()
+        seen = np.zeros_like(D, dtype=bool)
+        for r in range(prob.n):
+            for e in range(prob.rowptr[r], prob.rowptr[r + 1]):
+                assert D[r, prob.colidx[e]] == prob.vals[e, k]
+                seen[r, prob.colidx[e]] = True
+        assert not np.any(D[~seen])
