@@ -73,16 +73,21 @@ def test_vcycle_columns_independent():
         assert np.abs(Xb[:, s] - gmg.vcycle(lv, B[:, s])).max() < 1e-15
 
 
-@pytest.mark.parametrize("ne,nu,omega", [(8, 2, 0.8), (16, 1, 0.7), (16, 3, 0.6)])
-def test_vcycle_equals_error_propagation_recursion(ne, nu, omega):
+@pytest.mark.parametrize("ne,nu,omega,coef", [(8, 2, 0.8, "kl"), (16, 1, 0.7, "kl"), (16, 3, 0.6, "kl"),
+                                             (8, 2, 0.8, "lognormal")])
+def test_vcycle_equals_error_propagation_recursion(ne, nu, omega, coef):
     """The V-cycle as a matrix, from the textbook recursion of its error
     propagation rather than the procedure: with the damped Jacobi operator
     S_g = I - omega D_g^{-1} A_g, nu smoothing steps on each side of the coarse
     correction and the next grid's cycle E_{g+1} standing in for its exact
     solve, E_g = S_g^nu (I - P_g (I - E_{g+1}) A_{g+1}^{-1} P_g^T A_g) S_g^nu,
     E = 0 on the coarsest grid (solved exactly), and the cycle is
-    V_g = (I - E_g) A_g^{-1}."""
-    prob = S.make_problem(ne, 2, 0.3, 0.5)
+    V_g = (I - E_g) A_g^{-1}. The lognormal case's mean matrix has a
+    spatially varying coefficient, hence a varying diagonal on every grid."""
+    if coef == "kl":
+        prob = S.make_problem(ne, 2, 0.3, 0.5)
+    else:
+        prob = S.make_lognormal_problem(ne, 2, 1.0, 0.5, 2)
     A0 = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)[0]
     lv = gmg.hierarchy(A0, ne)
 

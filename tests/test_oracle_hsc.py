@@ -251,3 +251,25 @@ def test_schur_constants_are_the_spectrum_of_one_level(M):
     (c1, c2), = hsc.schur_constants(K, n, off)
     assert rest.size == n and c2 < 1 - 1e-6
     assert c1 == pytest.approx(rest[0], rel=1e-10) and c2 == pytest.approx(rest[-1], rel=1e-10)
+
+
+def test_general_prec_factors_sit_where_the_paper_puts_them():
+    """Eq. (general-prec) with three different approximations M_D^1, M_D^2,
+    M_D^3 of D^{-1}: on [0; y] with C = 0 the product gives
+    [-M_S B M_D^1 y; M_D^2 y] (M_D^1 in the pre-correction, M_D^2 in the middle
+    factor), and on [x; 0] with B = 0 it gives [M_S x; -M_D^3 C M_S x] (M_D^3 in
+    the post-correction)."""
+    rng = np.random.default_rng(9)
+    na, nd = 4, 3
+    A0 = rng.standard_normal((na, na))
+    B = rng.standard_normal((na, nd))
+    C = rng.standard_normal((nd, na))
+    MS = rng.standard_normal((na, na))
+    M1, M2, M3 = (rng.standard_normal((nd, nd)) for _ in range(3))
+    x, y = rng.standard_normal(na), rng.standard_normal(nd)
+    P = hsc.general_prec(A0, B, np.zeros_like(C), MS, M1, M2, M3)
+    assert np.allclose(P @ np.concatenate([np.zeros(na), y]), np.concatenate([-MS @ B @ M1 @ y, M2 @ y]),
+                       rtol=0, atol=1e-13)
+    P = hsc.general_prec(A0, np.zeros_like(B), C, MS, M1, M2, M3)
+    assert np.allclose(P @ np.concatenate([x, np.zeros(nd)]), np.concatenate([MS @ x, -M3 @ C @ MS @ x]),
+                       rtol=0, atol=1e-13)

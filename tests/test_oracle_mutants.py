@@ -65,6 +65,7 @@ HSC_PINS = (
     lambda: th.test_algorithm1_gpc_equals_recursive_block_inverse(2, 2),
     lambda: th.test_hsc_symmetric_positive_definite(),
     lambda: th.test_general_prec_variants_match_the_paper_formula(),
+    lambda: th.test_general_prec_factors_sit_where_the_paper_puts_them(),
     lambda: th.test_bgs_matches_block_triangular_solves(2, 2),
     lambda: th.test_theorem1_spectrum(4, 2, 3, 0.4),
     lambda: th.test_schur_reduced_solve_recovers_the_full_solution(2, 2),
@@ -86,7 +87,8 @@ GMG_PINS = (
     lambda: tg.test_vcycle_symmetric_positive_definite(),
     lambda: tg.test_vcycle_columns_independent(),
     lambda: tg.test_vcycle_contraction_h_independent(16),
-    lambda: tg.test_vcycle_equals_error_propagation_recursion(8, 2, 0.8),
+    lambda: tg.test_vcycle_equals_error_propagation_recursion(8, 2, 0.8, "kl"),
+    lambda: tg.test_vcycle_equals_error_propagation_recursion(8, 2, 0.8, "lognormal"),
 )
 QOI_PINS = (
     lambda: tq.test_adjoint_gradient_matches_central_differences(),
@@ -194,6 +196,8 @@ MUTANTS = [
            HSC_PINS, "pre-correction factor with the wrong sign"),
     Mutant("general-prec-factor", hsc, "general_prec", "[-MD3 @ C, np.eye(nd)]", "[-MD1 @ C, np.eye(nd)]",
            HSC_PINS, "M_D^1 used in the post-correction factor of eq. (general-prec)"),
+    Mutant("general-prec-middle", hsc, "general_prec", "[np.zeros((nd, na)), MD2]", "[np.zeros((nd, na)), MD3]",
+           HSC_PINS, "M_D^3 in the middle factor of eq. (general-prec)"),
     Mutant("recursion-exact-schur", hsc, "hsc_dense_recursive", "S_inv=M(l - 1)", "S_inv=None", HSC_PINS,
            "dense recursion with the exact Schur complement instead of M_l-1"),
     Mutant("schur-constants-no-pencil", hsc, "schur_constants",
@@ -264,6 +268,9 @@ MUTANTS = [
            GMG_PINS, "post-smoothing left out (non-symmetric cycle)"),
     Mutant("vcycle-coarse-sweeps", gmg, "vcycle", "xc = vcycle(levels, L.P.T @ r, nu, omega, g + 1)",
            "xc = vcycle(levels, L.P.T @ r, 1, omega, g + 1)", GMG_PINS, "one smoothing step on the coarser grids"),
+    Mutant("jacobi-first-diagonal", gmg, "vcycle", "dinv = L.dinv if b.ndim == 1 else L.dinv[:, None]",
+           "dinv = L.dinv if b.ndim == 1 else L.dinv[None, :1]", GMG_PINS,
+           "Jacobi scaled by the first diagonal entry (right only for a constant diagonal)"),
     Mutant("vcycle-restrict-rhs", gmg, "vcycle", "L.P.T @ r", "L.P.T @ b", GMG_PINS,
            "restriction of b instead of the residual"),
     Mutant("jacobi-no-accumulate", gmg, "vcycle", "x = x + omega * dinv * (b - L.A @ x)",
