@@ -150,6 +150,14 @@ typedef struct {
   double beta[SG_MAX_HIST];
 } sg_solve_stats;
 
+/* sg_default_prec_opts, sg_default_solve_opts -- fill an options struct with
+ * the library defaults (host memory; a NULL pointer is ignored; no device
+ * call). Preconditioner: precision SG_F32, top_level_f64 1, inner_tol 1e-2,
+ * inner_maxit 200, inner_fixed_iters 0, nu 2, omega 0.8, m0 SG_M0_VCYCLE,
+ * level_tol 1e-8, level_maxit 500, md_m0 0 (Algorithm 1 itself), df64 0.
+ * Solve: precond SG_PREC_HSC, prec as above, tol 1e-8 (the stopping test of
+ * Sec. 6), maxit 500, flexible 1, use_x0 0, check_true_residual 1,
+ * schur_reduced 0, schur_inner_tol 1e-11. */
 void sg_default_prec_opts(sg_prec_opts* o);
 void sg_default_solve_opts(sg_solve_opts* o);
 
@@ -164,8 +172,10 @@ void sg_default_solve_opts(sg_solve_opts* o);
  *           pattern (needed by sg_qoi / sg_qoi_grad).
  * out       receives the handle. The chaos tables (multi-indices, the sparse
  *           G_k) and the multigrid hierarchy are built here.
- * Returns SG_ERR_INVALID_ARG for a malformed pattern or sizes, SG_ERR_OOM if
- * device memory runs out. */
+ * Returns SG_ERR_INVALID_ARG for a malformed pattern or sizes (checked on
+ * the host before any device call), SG_ERR_OOM if device memory runs out,
+ * SG_ERR_CUDA without a usable CUDA device (there is no CPU fallback); on any
+ * error *out is NULL. */
 int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz,
              const int* rowptr, const int* colidx, const double* vals,
              const double* mass_vals, sg_problem** out);

@@ -632,11 +632,15 @@ int sg_setup(const sg_mesh* mesh, int M, int p, int family, int n, int nnz, cons
 int sg_setup_gpc(const sg_mesh* mesh, int M, int p, int q, int family, int n, int nnz, const int* rowptr,
                  const int* colidx, const double* vals, const double* mass_vals, sg_problem** out) {
   set_error("");
-  if (!out || q < 0) {
-    set_error("sg_setup_gpc: out is null or q < 0");
+  if (!out) {
+    set_error("sg_setup_gpc: out is null");
     return SG_ERR_INVALID_ARG;
   }
   *out = nullptr;
+  if (q < 0) {
+    set_error("sg_setup_gpc: q < 0");
+    return SG_ERR_INVALID_ARG;
+  }
   sg_problem* h = new sg_problem();
   int st = setup_impl(mesh, M, p, family, n, nnz, rowptr, colidx, vals, mass_vals, h, q);
   if (st != SG_OK) {
