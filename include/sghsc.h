@@ -388,6 +388,9 @@ int sg_autotune_forms(const sg_problem* h, int* pairs_f64, int* pairs_f32, int* 
  * inner loops) as an independent branch. The handles stay owned by the
  * caller and must outlive the batch; a handle may belong to one batch. */
 typedef struct sg_batch sg_batch;
+/* problems: host array of count >= 1 distinct, non-NULL handles. *out is the
+ * batch, or NULL on any error (SG_ERR_INVALID_ARG for a NULL or repeated
+ * handle, SG_ERR_CUDA if its streams cannot be created). */
 int sg_batch_create(int count, sg_problem* const* problems, sg_batch** out);
 /* F, U: host arrays of count device pointers (n_i x P_i FP64 each);
  * stats: host array of count entries or NULL. Returns SG_OK when every system

@@ -437,17 +437,23 @@ int sg_autotune_result(const sg_problem* h, int* threads_f64, int* threads_f32) 
 
 int sg_batch_create(int count, sg_problem* const* problems, sg_batch** out) {
   set_error("");
-  if (!out || count < 1 || !problems) {
-    set_error("sg_batch_create: invalid arguments");
+  if (!out) {
+    set_error("sg_batch_create: out is null");
     return SG_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  for (int i = 0; i < count; ++i)
-    for (int j = 0; j < i; ++j)
-      if (!problems[i] || problems[i] == problems[j]) {
-        set_error("sg_batch_create: null or repeated handle at %d", i);
-        return SG_ERR_INVALID_ARG;
-      }
+  if (count < 1 || !problems) {
+    set_error("sg_batch_create: invalid arguments");
+    return SG_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < count; ++i) {
+    bool bad = !problems[i];
+    for (int j = 0; j < i && !bad; ++j) bad = problems[i] == problems[j];
+    if (bad) {
+      set_error("sg_batch_create: null or repeated handle at %d", i);
+      return SG_ERR_INVALID_ARG;
+    }
+  }
   sg_batch* b = new sg_batch();
   b->hs.assign(problems, problems + count);
   b->branch.assign(count, nullptr);

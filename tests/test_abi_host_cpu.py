@@ -172,3 +172,18 @@ def test_without_a_gpu_setup_fails_loudly(L):
     assert _err(L)
     out = C.c_double()
     assert L.LIB.sg_measure_alu_peak(SG_F64, 1, C.byref(out), None) == SG_ERR_CUDA
+
+
+def test_batch_create_refuses_null_and_repeated_handles(L):
+    """sg_batch_create checks its handle list on the host and leaves *out NULL:
+    a NULL handle in any position (the first included) and a handle listed
+    twice are refused before any device call. The non-NULL values here are
+    never dereferenced: the check compares pointers only."""
+    lib = L.LIB
+    fake = C.c_void_p(0x1000)
+    for count, hs in [(1, [None]), (2, [None, fake]), (2, [fake, None]), (2, [fake, fake]), (0, [fake])]:
+        arr = (C.c_void_p * max(len(hs), 1))(*hs)
+        out = C.c_void_p(12345)
+        assert lib.sg_batch_create(count, arr, C.byref(out)) == SG_ERR_INVALID_ARG, hs
+        assert out.value is None and "sg_batch_create" in _err(L)
+    assert lib.sg_batch_create(1, None, None) == SG_ERR_INVALID_ARG
