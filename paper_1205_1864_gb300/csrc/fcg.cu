@@ -56,8 +56,10 @@ int ensure_outer(sg_problem* h) {
       SG_TRY_CUDA(cudaDeviceSynchronize());
     }
     cudaFree(h->opart);
+    h->opart = nullptr;   // a failed allocation leaves no stale buffer behind
+    h->opart_blocks = 0;
+    SG_TRY_CUDA(cudaMalloc((void**)&h->opart, (size_t)need * 2 * sizeof(double)));
     h->opart_blocks = need;
-    SG_TRY_CUDA(cudaMalloc((void**)&h->opart, (size_t)h->opart_blocks * 2 * sizeof(double)));
   }
   return SG_OK;
 }

@@ -39,6 +39,11 @@ static int ensure_level(sg_problem* h, const sg_prec_opts& o) {
   for (void* b : {(void*)h->lx, (void*)h->lr, (void*)h->lz, (void*)h->lp, (void*)h->lq, (void*)h->lb, (void*)h->lctl,
                   (void*)h->lsc, (void*)h->lhist_alpha, (void*)h->lhist_beta, (void*)h->lhist_res})
     cudaFree(b);
+  // a failed allocation below leaves null pointers and no capacity, never a freed buffer
+  h->lx = h->lr = h->lz = h->lp = h->lq = h->lb = nullptr;
+  h->lctl = nullptr;
+  h->lsc = h->lhist_alpha = h->lhist_beta = h->lhist_res = nullptr;
+  h->lhist_cap = 0;
   const size_t bytes = (size_t)h->n * std::max(h->wmax, 1) * sizeof(double);
   for (double** b : {&h->lx, &h->lr, &h->lz, &h->lp, &h->lq, &h->lb}) SG_TRY_CUDA(cudaMalloc((void**)b, bytes));
   SG_TRY_CUDA(cudaMalloc((void**)&h->lctl, sizeof(OuterCtl)));
@@ -416,6 +421,7 @@ int sg_inner_solve(sg_problem* h, const void* B, void* X, int w, int dtype, cons
     cudaFree(h->io_in);
     cudaFree(h->io_out);
     h->io_in = h->io_out = nullptr;
+    h->io_bytes = 0;
     SG_TRY_CUDA(cudaMalloc(&h->io_in, bytes));
     SG_TRY_CUDA(cudaMalloc(&h->io_out, bytes));
     h->io_bytes = bytes;

@@ -1708,7 +1708,6 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
   free_inner_bufs(iw);
   const size_t es = dtype == SG_F64 ? 8 : 4;
   iw.esize = es;
-  iw.wcap = wcap;
   const size_t nb = (size_t)h->grids[0].n * wcap * es;
   for (void** b : {&iw.x, &iw.r, &iw.z, &iw.zt, &iw.pA, &iw.pB, &iw.q}) SG_TRY(alloc_block(b, nb));
   const int G = (int)h->grids.size();
@@ -1732,6 +1731,7 @@ int ensure_inner_work(sg_problem* h, int dtype, int wcap) {
   SG_TRY_CUDA(cudaMemset(iw.ctl, 0, sizeof(InnerCtl)));
   SG_TRY_CUDA(cudaMemset(iw.done, 0, (size_t)wcap * sizeof(int)));
   SG_TRY_CUDA(cudaMemset(iw.iters, 0, (size_t)wcap * sizeof(int)));
+  iw.wcap = wcap;   // only once every buffer exists: a failed allocation leaves no capacity
   return SG_OK;
 }
 

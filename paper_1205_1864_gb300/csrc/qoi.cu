@@ -123,8 +123,11 @@ static int ensure_part(sg_problem* h, size_t count) {
   clear_graphs(h);   // captured solve graphs use the partial-sum buffer
   SG_TRY_CUDA(cudaDeviceSynchronize());
   cudaFree(h->opart);
-  h->opart_blocks = (int)std::max<size_t>((count + 1) / 2, (size_t)h->num_sms * 16);
-  SG_TRY_CUDA(cudaMalloc((void**)&h->opart, (size_t)h->opart_blocks * 2 * sizeof(double)));
+  h->opart = nullptr;
+  h->opart_blocks = 0;
+  const int blocks = (int)std::max<size_t>((count + 1) / 2, (size_t)h->num_sms * 16);
+  SG_TRY_CUDA(cudaMalloc((void**)&h->opart, (size_t)blocks * 2 * sizeof(double)));
+  h->opart_blocks = blocks;
   return SG_OK;
 }
 
@@ -205,6 +208,8 @@ int sg_qoi_grad(sg_problem* h, const double* U, const double* Lam, int nparam, c
   const size_t wcount = (size_t)nparam * M1;
   if ((size_t)h->wdev_cap < wcount) {
     cudaFree(h->wdev);
+    h->wdev = nullptr;
+    h->wdev_cap = 0;
     SG_TRY_CUDA(cudaMalloc((void**)&h->wdev, wcount * sizeof(double)));
     h->wdev_cap = (int)wcount;
   }
