@@ -1,4 +1,5 @@
-"""The error bound of the double-float parity tests, checked on the CPU.
+"""The error bounds of the FP32 and double-float product parity tests,
+checked on the CPU.
 
 The GPU tests accept a double-float SG product entry when it lies within
 m 2^-46 sum|terms| (+ 2^-52 |exact|) of the exact value, m the products of the
@@ -11,7 +12,7 @@ multiply-add evaluated exactly and rounded once, and compared with the exact
 rational value on rows and outputs of the 10-variable, degree-4 operator
 (P = 1001). The model stays well inside the bar, and the same sums with the
 low parts dropped (plain FP32 accumulation) break it, so the bar separates
-the two arithmetics.
+the two arithmetics. The FP32 row kernel's bar is checked the same way.
 """
 from fractions import Fraction as Fr
 
@@ -109,3 +110,44 @@ def test_double_float_product_error_within_the_parity_bar():
             worst_fp32 = max(worst_fp32, float(abs(Fr(_entry(A, U, l, coup, False)) - exact) / bar))
     assert worst < 0.25, worst            # the model's largest error is a small part of the bar
     assert worst_fp32 > 1e3, worst_fp32   # FP32 accumulation is far outside it
+
+
+def test_fp32_row_product_error_within_the_parity_bar():
+    """The FP32 product's bar, m u sum|terms| with u = 2^-24 and m = 9 + 2M + 2
+    (nine stencil terms, up to 2M couplings and the diagonal term, and the FP32
+    roundings of the matrix values and coupling weights), against the row
+    kernel's operations: each term sum T(k, j) is a product followed by a
+    chain of fused multiply-adds over the row's nonzeros, and an output is
+    T(0, l) followed by one fused multiply-add c T(k, j) per coupling."""
+    M, p = 10, 4
+    G = chaos.g_matrices(M, p)
+    _, off = chaos.multi_indices(M, p)
+    P = G[0].shape[0]
+    prob = S.make_problem(16, M, 0.3, 0.5)
+    rng = np.random.default_rng(1205)
+    u, m = Fr(2) ** -24, 9 + 2 * M + 2
+    worst = 0.0
+    for trial in range(150):
+        r = int(rng.integers(0, prob.n))
+        A = prob.vals[prob.rowptr[r]:prob.rowptr[r + 1]]
+        nz = A.shape[0]
+        l = int(rng.integers(off[1], off[p])) if trial % 2 else int(rng.integers(0, P))
+        coup = [(k, int(j), float(G[k][l, j])) for k in range(1, M + 1) for j in G[k][l].indices]
+        U = {j: rng.standard_normal(nz).astype(np.float32) for j in [l] + [j for _, j, _ in coup]}
+
+        def T(k, j):
+            s = f32(A[0, k]) * U[j][0]
+            for e in range(1, nz):
+                s = _fma(f32(A[e, k]), U[j][e], s)
+            return s
+
+        acc = T(0, l)
+        for k, j, c in coup:
+            acc = _fma(f32(c), T(k, j), acc)
+        exact, mag = Fr(0), Fr(0)
+        for k, j, c in [(0, l, 1.0)] + coup:
+            t = [Fr(float(A[e, k])) * Fr(float(U[j][e])) for e in range(nz)]
+            exact += Fr(c) * sum(t)
+            mag += abs(Fr(c)) * sum(abs(v) for v in t)
+        worst = max(worst, float(abs(Fr(float(acc)) - exact) / (m * u * mag)))
+    assert worst < 0.5, worst
