@@ -61,11 +61,12 @@ def _read(name):
     return rows
 
 
-def _paper_run(M, p, cov):
-    """Sec. 6 setting: 10x10 Q1 mesh, L = 0.5, k0 = 1. The reading of the
-    garbled distribution of xi (printed ``U[0,1]``) is ``U(-1, 1)``: in this
-    build's unit-variance variables that is sigma = CoV / sqrt(3)."""
-    prob = S.make_problem(10, M, cov / math.sqrt(3.0), 0.5)
+def _paper_run(M, p, cov, ne=10):
+    """Sec. 6 setting: 10x10 Q1 mesh (Table 4: ne x ne), L = 0.5, k0 = 1. The
+    reading of the garbled distribution of xi (printed ``U[0,1]``) is
+    ``U(-1, 1)``: in this build's unit-variance variables that is
+    sigma = CoV / sqrt(3)."""
+    prob = S.make_problem(ne, M, cov / math.sqrt(3.0), 0.5)
     A = so.kl_matrices(prob.rowptr, prob.colidx, prob.vals)
     G = chaos.g_matrices(M, p)
     _, off = chaos.multi_indices(M, p)
@@ -106,6 +107,33 @@ def test_paper_table1_soft(row):
     assert out["mean"][1] == pytest.approx(m_k, rel=0.10)
     assert out["hsc"][1] == pytest.approx(h_k, rel=0.10)
     assert out["bgs"][1] == pytest.approx(b_k, rel=0.10)
+
+
+def _uniform_soft(out, m_it, m_k, b_it, b_k, h_it, h_k):
+    assert abs(out["mean"][0] - m_it) <= 2
+    assert abs(out["bgs"][0] - b_it) <= 2
+    assert abs(out["hsc"][0] - h_it) <= 2
+    assert out["mean"][1] == pytest.approx(m_k, rel=0.10)
+    assert out["bgs"][1] == pytest.approx(b_k, rel=0.10)
+    assert out["hsc"][1] == pytest.approx(h_k, rel=0.10)
+
+
+@pytest.mark.parametrize("row", _read("sec6_table2_vary_P.txt"),
+                         ids=lambda r: f"p{int(r[0])}")
+def test_paper_table2_soft(row):
+    """Table 2 (N = 4, CoV 50 %, chaos degree varied), same soft bounds as
+    Tables 1 and 3."""
+    p, _, _, _, m_it, m_k, b_it, b_k, h_it, h_k = row
+    _uniform_soft(_paper_run(4, int(p), 0.5), m_it, m_k, b_it, b_k, h_it, h_k)
+
+
+@pytest.mark.parametrize("row", _read("sec6_table4_vary_h.txt"),
+                         ids=lambda r: f"h1_{int(r[0])}")
+def test_paper_table4_soft(row):
+    """Table 4 (N = p = 4, CoV 50 %, mesh 1/h x 1/h varied): the counts do not
+    grow with the mesh, within the same soft bounds."""
+    inv_h, _, _, _, m_it, m_k, b_it, b_k, h_it, h_k = row
+    _uniform_soft(_paper_run(4, 4, 0.5, ne=int(inv_h)), m_it, m_k, b_it, b_k, h_it, h_k)
 
 
 def test_pcg_columns_conventions():
