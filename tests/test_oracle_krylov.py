@@ -82,31 +82,22 @@ def _paper_run(M, p, cov, ne=10):
     return out
 
 
-@pytest.mark.parametrize("row", _read("table3_cov.txt"))
+@pytest.mark.parametrize("row", _read("sec6_table3_vary_cov_full.txt"), ids=lambda r: f"cov{int(r[0])}")
 def test_paper_table3_soft(row):
     """Iterations within 2 and kappa within 10 % of Table 3 (the paper's KL is
     a discrete eigenproblem on its mesh and its dof count includes boundary
     nodes, so equality is not expected)."""
-    cov, m_it, m_k, h_it, h_k = row
+    cov, _, _, m_it, m_k, b_it, b_k, h_it, h_k = row
     out = _paper_run(4, 4, cov / 100.0)
-    assert abs(out["mean"][0] - m_it) <= 2
-    assert abs(out["hsc"][0] - h_it) <= 2
-    assert out["mean"][1] == pytest.approx(m_k, rel=0.10)
-    assert out["hsc"][1] == pytest.approx(h_k, rel=0.10)
+    _uniform_soft(out, m_it, m_k, b_it, b_k, h_it, h_k)
     # the method's claim: HSC needs fewer iterations than the mean-based one
     assert out["hsc"][0] < out["mean"][0]
 
 
-@pytest.mark.parametrize("row", _read("table1_vary_N.txt"))
+@pytest.mark.parametrize("row", _read("sec6_table1_vary_N_full.txt"), ids=lambda r: f"N{int(r[0])}")
 def test_paper_table1_soft(row):
-    N, m_it, m_k, b_it, b_k, h_it, h_k = row
-    out = _paper_run(int(N), 4, 0.5)
-    assert abs(out["mean"][0] - m_it) <= 2
-    assert abs(out["hsc"][0] - h_it) <= 2
-    assert abs(out["bgs"][0] - b_it) <= 2
-    assert out["mean"][1] == pytest.approx(m_k, rel=0.10)
-    assert out["hsc"][1] == pytest.approx(h_k, rel=0.10)
-    assert out["bgs"][1] == pytest.approx(b_k, rel=0.10)
+    N, _, _, _, m_it, m_k, b_it, b_k, h_it, h_k = row
+    _uniform_soft(_paper_run(int(N), 4, 0.5), m_it, m_k, b_it, b_k, h_it, h_k)
 
 
 def _uniform_soft(out, m_it, m_k, b_it, b_k, h_it, h_k):
