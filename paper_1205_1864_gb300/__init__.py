@@ -39,6 +39,20 @@ def _stream() -> C.c_void_p:
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _block(h: "SGProblem", t, name: str, cols: Optional[int] = None, dtypes=(torch.float64,)) -> None:
+    """Refuse a block whose shape or element type is not what the call reads
+    or writes: the library takes bare pointers and touches exactly n x cols
+    elements (cols = P by default), so a smaller tensor would be overrun.
+    ``None`` passes (optional arguments)."""
+    if t is None:
+        return
+    want = (h.n, h.P if cols is None else cols)
+    if tuple(t.shape) != want or t.dtype not in dtypes:
+        kinds = " or ".join(str(d).replace("torch.", "") for d in dtypes)
+        raise ValueError(f"{name}: expected a {want[0]} x {want[1]} {kinds} block, got "
+                         f"{tuple(t.shape)} {str(t.dtype).replace('torch.', '')}")
+
+
 def _ptr(t: Optional[torch.Tensor]) -> Optional[C.c_void_p]:
     if t is None:
         return None
@@ -120,6 +134,7 @@ class SGProblem:
         check(_lib.LIB.sg_problem_dims(h, *[C.byref(x) for x in dims]), "sg_problem_dims")
         self.n, self.P, self.M, self.p, self.nnz = (d.value for d in dims)
         self.q, self.nterm = q, nterm
+        self.off = [int(v) for v in self.chaos_table()[1]]   # degree d occupies columns off[d]:off[d+1]
 
     @classmethod
     def from_inputs(cls, prob, p: int, family: int = SG_LEGENDRE) -> "SGProblem":
@@ -173,9 +188,13 @@ def sg_apply(h: SGProblem, U: torch.Tensor, Y: Optional[torch.Tensor] = None, df
     if df64:
         if U.dtype != torch.float32:
             raise ValueError("sg_apply: df64 takes an FP32 U")
+        _block(h, U, "sg_apply: U", dtypes=(torch.float32,))
+        _block(h, Y, "sg_apply: Y", dtypes=(torch.float64,))
         Y = torch.empty(U.shape, dtype=torch.float64, device=U.device) if Y is None else Y
         code = _lib.SG_F32_ACCDF64
     else:
+        _block(h, U, "sg_apply: U", dtypes=(torch.float64, torch.float32))
+        _block(h, Y, "sg_apply: Y", dtypes=(U.dtype,))
         Y = torch.empty_like(U) if Y is None else Y
         code = _DT[U.dtype]
     check(_lib.LIB.sg_apply(h.h, _ptr(U), _ptr(Y), code, _stream()), "sg_apply")
@@ -189,9 +208,14 @@ def sg_level_apply(h: SGProblem, lvl_out: int, lvl_in: int, X: torch.Tensor, Yin
     the mixed preconditioner's top level (``SG_F32_ACC64``, FP32 ``Yout``;
     ``df64``: double-float accumulation, ``SG_F32_ACCDF64``)."""
     mixed = X.dtype == torch.float32 and Yin is not None and Yin.dtype == torch.float64
-    if Yout is None:
-        _, off = h.chaos_table()
-        Yout = torch.empty((h.n, int(off[lvl_out + 1] - off[lvl_out])), dtype=X.dtype, device="cuda")
+    if 0 <= lvl_in <= h.p and 0 <= lvl_out <= h.p:   # other levels: refused by the library
+        off = h.off
+        w_in, w_out = off[lvl_in + 1] - off[lvl_in], off[lvl_out + 1] - off[lvl_out]
+        _block(h, X, "sg_level_apply: X", w_in, (torch.float64, torch.float32))
+        _block(h, Yin, "sg_level_apply: Yin", w_out, (torch.float64,) if mixed else (X.dtype,))
+        _block(h, Yout, "sg_level_apply: Yout", w_out, (X.dtype,))
+        if Yout is None:
+            Yout = torch.empty((h.n, w_out), dtype=X.dtype, device="cuda")
     code = (_lib.SG_F32_ACCDF64 if df64 else SG_F32_ACC64) if mixed else _DT[X.dtype]
     check(_lib.LIB.sg_level_apply(h.h, lvl_out, lvl_in, _ptr(X), _ptr(Yin), _ptr(Yout), code, _stream()),
           "sg_level_apply")
@@ -199,6 +223,7 @@ def sg_level_apply(h: SGProblem, lvl_out: int, lvl_in: int, X: torch.Tensor, Yin
 
 
 def sg_vcycle_apply(h: SGProblem, B: torch.Tensor, opts=None) -> torch.Tensor:
+    _block(h, B, "sg_vcycle_apply: B", B.shape[1] if len(B.shape) == 2 else -1, (torch.float64, torch.float32))
     X = torch.empty_like(B)
     o = opts or prec_opts()
     check(_lib.LIB.sg_vcycle_apply(h.h, _ptr(B), _ptr(X), B.shape[1], _DT[B.dtype], C.byref(o), _stream()),
@@ -207,6 +232,7 @@ def sg_vcycle_apply(h: SGProblem, B: torch.Tensor, opts=None) -> torch.Tensor:
 
 
 def sg_inner_solve(h: SGProblem, B: torch.Tensor, opts=None):
+    _block(h, B, "sg_inner_solve: B", B.shape[1] if len(B.shape) == 2 else -1, (torch.float64, torch.float32))
     X = torch.empty_like(B)
     o = opts or prec_opts()
     it = np.zeros(B.shape[1], dtype=np.int32)
@@ -217,6 +243,8 @@ def sg_inner_solve(h: SGProblem, B: torch.Tensor, opts=None):
 
 def hsc_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Z = M_P R (Algorithm 1)."""
+    _block(h, R, "hsc_precond_apply: R")
+    _block(h, Z, "hsc_precond_apply: Z")
     Z = torch.empty_like(R) if Z is None else Z
     o = opts or prec_opts()
     check(_lib.LIB.hsc_precond_apply(h.h, _ptr(R), _ptr(Z), C.byref(o), _stream()), "hsc_precond_apply")
@@ -225,6 +253,8 @@ def hsc_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torc
 
 def bgs_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Z = M_bGS R (block symmetric Gauss-Seidel, zero initial guess)."""
+    _block(h, R, "bgs_precond_apply: R")
+    _block(h, Z, "bgs_precond_apply: Z")
     Z = torch.empty_like(R) if Z is None else Z
     o = opts or prec_opts()
     check(_lib.LIB.bgs_precond_apply(h.h, _ptr(R), _ptr(Z), C.byref(o), _stream()), "bgs_precond_apply")
@@ -233,6 +263,8 @@ def bgs_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torc
 
 def mean_precond_apply(h: SGProblem, R: torch.Tensor, opts=None, Z: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Z = (I (x) A_0^{-1}) R with the inner PCG."""
+    _block(h, R, "mean_precond_apply: R")
+    _block(h, Z, "mean_precond_apply: Z")
     Z = torch.empty_like(R) if Z is None else Z
     o = opts or prec_opts()
     check(_lib.LIB.mean_precond_apply(h.h, _ptr(R), _ptr(Z), C.byref(o), _stream()), "mean_precond_apply")
@@ -249,6 +281,8 @@ def _stats(status, st) -> "SolveStats":
 
 def sg_solve(h: SGProblem, F: torch.Tensor, opts=None, U: Optional[torch.Tensor] = None, raise_on_error=True):
     """Flexible CG on the SG system; returns ``(U, SolveStats)``."""
+    _block(h, F, "sg_solve: F")
+    _block(h, U, "sg_solve: U")
     U = torch.empty_like(F) if U is None else U
     o = opts or solve_opts()
     st = _lib.sg_solve_stats()
@@ -266,6 +300,7 @@ def sg_solve_host(h: SGProblem, F: torch.Tensor, opts=None, U: Optional[torch.Te
     kernels directly); returns ``(U, SolveStats)`` when ``U`` is filled."""
     if F.is_cuda or not F.is_contiguous() or F.dtype != torch.float64:
         raise ValueError("sg_solve_host: F must be a contiguous FP64 CPU tensor")
+    _block(h, F, "sg_solve_host: F")
     U = torch.empty_like(F) if U is None else U
     if U.is_cuda or not U.is_contiguous() or U.dtype != torch.float64 or U.shape != F.shape:
         raise ValueError("sg_solve_host: U must be a contiguous FP64 CPU tensor shaped like F")
@@ -334,8 +369,11 @@ class SGBatch:
     def solve(self, Fs, opts=None, Us=None, raise_on_error=True):
         """Solve every system; returns ``(list of U, list of SolveStats)``."""
         count = len(self.problems)
-        if len(Fs) != count:
-            raise ValueError(f"need {count} right-hand sides")
+        if len(Fs) != count or (Us is not None and len(Us) != count):
+            raise ValueError(f"need {count} right-hand sides (and solution blocks)")
+        for i, h in enumerate(self.problems):
+            _block(h, Fs[i], f"SGBatch.solve: F[{i}]")
+            _block(h, None if Us is None else Us[i], f"SGBatch.solve: U[{i}]")
         Us = [torch.empty_like(F) for F in Fs] if Us is None else list(Us)
         o = opts or solve_opts()
         st = (_lib.sg_solve_stats * count)()
@@ -351,12 +389,15 @@ class SGBatch:
         """``solve`` on host blocks (contiguous FP64 CPU tensors; pinned ones
         are read and written by the library's kernels directly)."""
         count = len(self.problems)
-        if len(Fs) != count:
-            raise ValueError(f"need {count} right-hand sides")
+        if len(Fs) != count or (Us is not None and len(Us) != count):
+            raise ValueError(f"need {count} right-hand sides (and solution blocks)")
         Us = [torch.empty_like(F) for F in Fs] if Us is None else list(Us)
         for T in list(Fs) + Us:
             if T.is_cuda or not T.is_contiguous() or T.dtype != torch.float64:
                 raise ValueError("solve_host: blocks must be contiguous FP64 CPU tensors")
+        for i, h in enumerate(self.problems):
+            _block(h, Fs[i], f"SGBatch.solve_host: F[{i}]")
+            _block(h, Us[i], f"SGBatch.solve_host: U[{i}]")
         o = opts or solve_opts()
         st = (_lib.sg_solve_stats * count)()
         fp = (C.c_void_p * count)(*[C.c_void_p(F.data_ptr()) for F in Fs])
@@ -381,6 +422,7 @@ class SGBatch:
 
 def sg_qoi(h: SGProblem, U: torch.Tensor, want_grad: bool = True):
     """``Q = sum_j u_j^T M_h u_j`` (device scalar) and ``dQ/dU = 2 M_h U``."""
+    _block(h, U, "sg_qoi: U")
     q = torch.empty(1, dtype=torch.float64, device="cuda")
     dq = torch.empty_like(U) if want_grad else None
     check(_lib.LIB.sg_qoi(h.h, _ptr(U), _ptr(dq), _ptr(q), _stream()), "sg_qoi")
@@ -390,9 +432,13 @@ def sg_qoi(h: SGProblem, U: torch.Tensor, want_grad: bool = True):
 def sg_qoi_grad(h: SGProblem, U: torch.Tensor, Lam: torch.Tensor, W: np.ndarray):
     """``grad[t] = sum_k W[t,k] <Lam, A_k U G_k^T>``; returns ``(grad, h_k)``."""
     W = np.ascontiguousarray(W, dtype=np.float64)
+    if W.ndim != 2 or W.shape[1] != h.nterm or W.shape[0] < 1:
+        raise ValueError(f"sg_qoi_grad: W must have shape (parameters, {h.nterm}) (one column per value term)")
+    _block(h, U, "sg_qoi_grad: U")
+    _block(h, Lam, "sg_qoi_grad: Lam")
     nparam = W.shape[0]
     grad = torch.empty(nparam, dtype=torch.float64, device="cuda")
-    hk = torch.empty(h.M + 1, dtype=torch.float64, device="cuda")
+    hk = torch.empty(h.nterm, dtype=torch.float64, device="cuda")
     check(_lib.LIB.sg_qoi_grad(h.h, _ptr(U), _ptr(Lam), nparam, W.ctypes.data_as(C.POINTER(C.c_double)),
                                _ptr(grad), _ptr(hk), _stream()), "sg_qoi_grad")
     return grad, hk
@@ -401,8 +447,8 @@ def sg_qoi_grad(h: SGProblem, U: torch.Tensor, Lam: torch.Tensor, W: np.ndarray)
 def sg_set_scales(h: SGProblem, scale) -> None:
     """``A_k := scale[k] * A_k`` (relative to the matrices given to sg_setup)."""
     sc = np.ascontiguousarray(scale, dtype=np.float64)
-    if sc.shape != (h.M + 1,):
-        raise ValueError(f"need M+1 = {h.M + 1} scales")
+    if sc.shape != (h.nterm,):
+        raise ValueError(f"need one scale per value term ({h.nterm}: M+1, or C(M+q, M) for a gPC coefficient)")
     check(_lib.LIB.sg_set_scales(h.h, sc.ctypes.data_as(C.POINTER(C.c_double))), "sg_set_scales")
 
 
@@ -427,6 +473,8 @@ def sg_kl_set_theta(h: SGProblem, theta) -> None:
 def sg_kl_qoi_grad(h: SGProblem, U: torch.Tensor, Lam: torch.Tensor, theta) -> torch.Tensor:
     """dQ/dtheta (device, M+2) from the forward and adjoint solutions."""
     th = _theta_arg(h, theta)
+    _block(h, U, "sg_kl_qoi_grad: U")
+    _block(h, Lam, "sg_kl_qoi_grad: Lam")
     grad = torch.empty(h.M + 2, dtype=torch.float64, device="cuda")
     check(_lib.LIB.sg_kl_qoi_grad(h.h, _ptr(U), _ptr(Lam), th.ctypes.data_as(C.POINTER(C.c_double)), _ptr(grad),
                                   None, _stream()), "sg_kl_qoi_grad")
