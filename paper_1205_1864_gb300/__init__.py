@@ -118,6 +118,8 @@ class SGProblem:
         mp = None
         if mass is not None:
             mass = np.ascontiguousarray(mass, dtype=np.float64)
+            if mass.shape != (nnz,):
+                raise ValueError(f"mass must hold one value per nonzero ({nnz})")
             mp = mass.ctypes.data_as(C.POINTER(C.c_double))
         h = C.c_void_p()
         torch.cuda.init()

@@ -184,3 +184,16 @@ def test_gradient_and_scales_follow_the_value_terms(L):
         L.sg_set_scales(g, np.ones(g.M + 1))
     with pytest.raises(ValueError):
         L.sg_qoi_grad(g, FakeBlock((g.n, g.P)), FakeBlock((g.n, g.P)), np.ones((2, g.M + 1)))
+
+
+def test_setup_arrays_are_sized_before_the_library_reads_them(L):
+    """SGProblem hands the pattern, the values and the mass matrix to
+    sg_setup as bare host pointers: values of the wrong term count and a mass
+    array of the wrong length are refused first."""
+    import sg_inputs as S
+    prob = S.make_problem(4, 2, 0.3, 0.5)
+    with pytest.raises(ValueError):
+        L.SGProblem(4, 4, 2, 2, prob.rowptr, prob.colidx, prob.vals[:, :2], prob.mass)
+    with pytest.raises(ValueError):
+        L.SGProblem(4, 4, 2, 2, prob.rowptr, prob.colidx, prob.vals, prob.mass[:-1])
+    assert "sg_setup" not in L._lib.LIB.calls
