@@ -330,7 +330,10 @@ static int autotune_inner(sg_problem* h, cudaStream_t s) {
         best = c;
       }
     }
-    if (r != SG_OK) break;
+    if (r != SG_OK) {
+      h->inner_pick.erase(w);   // no choice left behind from a failed trial
+      break;
+    }
     h->inner_pick[w] = best;
   }
   clear_graphs(h);
