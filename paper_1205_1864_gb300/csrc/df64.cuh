@@ -61,10 +61,11 @@ __device__ __forceinline__ df64 df_from_float(float x) { return df64(x, 0.f); }
 // FP64 -> double-float with integer operations only (the FP64 pipe is the
 // narrow one): hi takes the sign, exponent and top 23 fraction bits of x
 // (truncation, so hi is exact), lo the remaining 29 fraction bits, normalised
-// from their leading one and truncated to 24 bits (relative error of the pair
-// below 2^-47). Zeros give zeros; magnitudes outside the normal FP32 range of
-// hi (below 2^-126 or above 2^127) take the rounded FP32 conversion with a
-// zero lo.
+// from their leading one and truncated to 24 bits: the pair is within
+// 2^-47 |x| + 2^-125 of x (a lo that would fall under the normal FP32 range
+// is dropped; from |x| >= 2^-79 on the error is below 2^-47 |x|). Zeros give
+// zeros; magnitudes outside the normal FP32 range of hi (below 2^-126 or
+// above 2^127) take the rounded FP32 conversion with a zero lo.
 __device__ __forceinline__ df64 df_from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7ff);
