@@ -187,3 +187,85 @@ def test_batch_create_refuses_null_and_repeated_handles(L):
         assert lib.sg_batch_create(count, arr, C.byref(out)) == SG_ERR_INVALID_ARG, hs
         assert out.value is None and "sg_batch_create" in _err(L)
     assert lib.sg_batch_create(1, None, None) == SG_ERR_INVALID_ARG
+
+
+def _header_structs():
+    """Field names and C types of the typedef'd structs in include/sghsc.h, in order."""
+    import re
+    src = open(os.path.join(ROOT, "include", "sghsc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"(.+?)\s+(\w+(?:\s*,\s*\w+)*)\s*(\[[^\]]*\])?$", decl)
+            ctype, names, arr = m.group(1), m.group(2), m.group(3)
+            for nm in (x.strip() for x in names.split(",")):
+                fields.append((nm, ctype, arr))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_and_constants_match_the_header(L):
+    """The ctypes mirrors of the option and statistics structs have the
+    header's fields, in the header's order, with matching C types (a
+    mismatch would shift every later field), and the status, precision and
+    family constants have the header's values."""
+    import re
+    ctype_of = {"int": C.c_int, "double": C.c_double, "long long": C.c_longlong, "sg_prec_opts": L.sg_prec_opts}
+    structs = _header_structs()
+    for name in ("sg_mesh", "sg_prec_opts", "sg_solve_opts", "sg_solve_stats"):
+        want = structs[name]
+        got = getattr(L, name)._fields_
+        assert [f[0] for f in got] == [f[0] for f in want], name
+        for (fname, ftype), (_, ctype, arr) in zip(got, want):
+            base = ctype_of[ctype]
+            if arr:
+                assert issubclass(ftype, C.Array) and ftype._type_ is base, (name, fname)
+                n = eval(arr[1:-1].replace("SG_MAX_HIST", str(L.SG_MAX_HIST)))
+                assert ftype._length_ == n, (name, fname)
+            else:
+                assert ftype is base, (name, fname)
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sghsc.h")).read(), flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(SG_[A-Z0-9_]+)\s*=\s*(\d+)", src))
+    consts["SG_MAX_HIST"] = int(re.search(r"#define SG_MAX_HIST (\d+)", src).group(1))
+    for k, v in consts.items():
+        assert getattr(L, k) == v, k
+    assert len(consts) >= 20
+
+
+def test_binding_prototypes_match_the_header(L):
+    """Every entry point's ctypes declaration takes as many arguments as the
+    header's prototype, with the same kind (pointer, int, double, long long)
+    in each position, and the same kind of result."""
+    import re
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sghsc.h")).read(), flags=re.S)
+    protos = re.findall(r"^\s*([A-Za-z_][\w \*]*?)\s*\b((?:sg|hsc|mean|bgs)_\w+)\s*\(([^;{]*?)\)\s*;", src, flags=re.M | re.S)
+    assert len(protos) >= 30
+
+    def kind(ctype_text):
+        t = " ".join(ctype_text.replace("const", " ").split())
+        if "*" in t:
+            return "ptr"
+        return {"int": "int", "double": "double", "long long": "longlong", "void": "void"}[t]
+
+    def ckind(ct):
+        if ct is None:
+            return "void"
+        if ct in (C.c_int,):
+            return "int"
+        if ct is C.c_double:
+            return "double"
+        if ct is C.c_longlong:
+            return "longlong"
+        return "ptr"                       # c_void_p, c_char_p and POINTER(...)
+
+    for ret, name, params in protos:
+        fn = getattr(L.LIB, name)
+        args = [] if params.strip() in ("", "void") else [a.strip() for a in params.split(",")]
+        want = [kind(re.sub(r"\b\w+\s*$", "", a) if re.search(r"[\w\*]\s+\**\w+\s*$", a) else a) for a in args]
+        assert [ckind(t) for t in fn.argtypes] == want, name
+        assert ckind(fn.restype) == kind(ret), name
